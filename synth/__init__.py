@@ -1,0 +1,178 @@
+"""Seeded synthetic inputs shared by the tests, the benchmark and the oracle checks.
+
+This module only builds input arrays (vertex positions, sign-encoded stencil
+tuples, index spaces).  It holds none of the method's arithmetic: no gap
+function, barrier, derivative or eigensystem is computed here.
+
+Stencil tuples use the sign encoding of the paper's Sec. 7.2 with -(i+1) for a
+negative slot and INT32_MIN for the '#' placeholder.
+"""
+import math
+
+import numpy as np
+
+NULL = -2147483648
+TYPE_IDS = {"PT": 0, "EE": 1, "PE": 2, "PP": 3, "EE_PAR": 4, "PE_PAR": 5, "PP_PAR": 6}
+
+# Unit-set mix: 40% PT, 40% EE of which a quarter nearly parallel (those split 60/20/20
+# into EE-par, PE-par and PP-par by where their closest points fall), 10% PE, 10% PP.
+DEFAULT_MIX = (("PT", 0.40), ("EE", 0.30), ("PE", 0.10), ("PP", 0.10),
+               ("EE_PAR", 0.06), ("PE_PAR", 0.02), ("PP_PAR", 0.02))
+
+UNIT_DHAT = math.sqrt(3.0) * 1e-3     # 1e-3 x bbox diagonal of [0,1]^3
+
+
+def _unit(rng):
+    while True:
+        v = rng.normal(size=3)
+        n = np.linalg.norm(v)
+        if n > 1e-3:
+            return v / n
+
+
+def _perp(rng, u):
+    while True:
+        v = np.cross(u, _unit(rng))
+        n = np.linalg.norm(v)
+        if n > 1e-2:
+            return v / n
+
+
+def _distance(rng, dhat):
+    """d = dhat * 10^U(-4, 0), kept away from the filter threshold 0.1 dhat and from dhat."""
+    while True:
+        r = 10.0 ** rng.uniform(-4.0, 0.0)
+        if abs(r - 0.1) > 1e-9 and r < 1.0 - 1e-9:
+            return dhat * r
+
+
+def _segment(rng, min_len=0.1):
+    while True:
+        a, b = rng.uniform(0.0, 1.0, 3), rng.uniform(0.0, 1.0, 3)
+        if np.linalg.norm(b - a) >= min_len:
+            return a, b
+
+
+def _triangle(rng):
+    """Triangle with all angles >= 10 degrees and area >= 1e-3 in the unit cube."""
+    while True:
+        P = rng.uniform(0.0, 1.0, (3, 3))
+        area = 0.5 * np.linalg.norm(np.cross(P[1] - P[0], P[2] - P[0]))
+        if area < 1e-3:
+            continue
+        ok = True
+        for i in range(3):
+            u, v = P[(i + 1) % 3] - P[i], P[(i + 2) % 3] - P[i]
+            cosang = np.dot(u, v) / (np.linalg.norm(u) * np.linalg.norm(v))
+            if cosang > math.cos(math.radians(10.0)):
+                ok = False
+        if ok:
+            return P
+
+
+def _parallel_angle(rng):
+    return 10.0 ** rng.uniform(-7.0, -2.0)
+
+
+def make_stencil(kind, rng, dhat):
+    """Vertices (s x 3, slot order) of one stencil of the given kind with a target distance."""
+    d = _distance(rng, dhat)
+    if kind == "PT":
+        T = _triangle(rng)
+        while True:
+            beta = rng.dirichlet((1.0, 1.0, 1.0))
+            if beta.min() >= 0.05:
+                break
+        foot = beta @ T
+        n = np.cross(T[1] - T[0], T[2] - T[0])
+        n /= np.linalg.norm(n)
+        p = foot + rng.choice((-1.0, 1.0)) * d * n
+        return np.stack([p, T[0], T[1], T[2]])
+    if kind in ("EE", "EE_PAR"):
+        a0, a1 = _segment(rng)
+        e1 = (a1 - a0) / np.linalg.norm(a1 - a0)
+        p1 = a0 + rng.uniform(0.1, 0.9) * (a1 - a0)
+        nrm = _perp(rng, e1)
+        m = np.cross(e1, nrm)
+        th = _parallel_angle(rng) if kind == "EE_PAR" else rng.uniform(0.05, math.pi / 2)
+        e2 = math.cos(th) * e1 + math.sin(th) * m
+        p2 = p1 + rng.choice((-1.0, 1.0)) * d * nrm
+        L2 = rng.uniform(0.1, 0.8)
+        g2 = rng.uniform(0.1, 0.9)
+        b0 = p2 - g2 * L2 * e2
+        return np.stack([a0, a1, b0, b0 + L2 * e2])
+    if kind in ("PE", "PE_PAR"):
+        e0, e1p = _segment(rng)
+        ed = (e1p - e0) / np.linalg.norm(e1p - e0)
+        foot = e0 + rng.uniform(0.1, 0.9) * (e1p - e0)
+        nrm = _perp(rng, ed)
+        p = foot + d * nrm
+        if kind == "PE":
+            return np.stack([p, e0, e1p])
+        th = _parallel_angle(rng)
+        L1 = rng.uniform(0.1, 0.8)
+        direction = math.cos(th) * rng.choice((-1.0, 1.0)) * ed + math.sin(th) * nrm
+        return np.stack([p, p + L1 * direction, e0, e1p])
+    if kind in ("PP", "PP_PAR"):
+        p = rng.uniform(0.0, 1.0, 3)
+        a = _unit(rng)
+        q = p + d * a
+        if kind == "PP":
+            return np.stack([p, q])
+        th = _parallel_angle(rng)
+        m = _perp(rng, a)
+        L1, L2 = rng.uniform(0.1, 0.8), rng.uniform(0.1, 0.8)
+        return np.stack([p, p - L1 * a, q, q + L2 * (math.cos(th) * a + math.sin(th) * m)])
+    raise ValueError(kind)
+
+
+def encode(kind, ids):
+    """Sign-encoded tuple for vertex ids in slot order (Sec. 7.2)."""
+    neg = lambda i: -(int(i) + 1)
+    if kind == "PT":
+        return (neg(ids[0]), ids[1], ids[2], ids[3])
+    if kind == "EE":
+        return (ids[0], ids[1], ids[2], ids[3])
+    if kind == "PE":
+        return (neg(ids[0]), ids[1], ids[2], NULL)
+    if kind == "PP":
+        return (neg(ids[0]), ids[1], NULL, NULL)
+    if kind == "EE_PAR":
+        return (ids[0], neg(ids[1]), ids[2], ids[3])
+    if kind == "PE_PAR":
+        return (neg(ids[0]), neg(ids[1]), ids[2], neg(ids[3]))
+    if kind == "PP_PAR":
+        return (neg(ids[0]), neg(ids[1]), neg(ids[2]), neg(ids[3]))
+    raise ValueError(kind)
+
+
+def type_counts(k, mix=DEFAULT_MIX):
+    counts = [int(round(k * f)) for _, f in mix]
+    counts[0] += k - sum(counts)
+    return [(kind, c) for (kind, _), c in zip(mix, counts)]
+
+
+def unit_stencils(k=10000, seed=20230809, mix=DEFAULT_MIX, dhat=UNIT_DHAT, shuffle=False):
+    """Random stencil set in which every stencil owns its vertices.
+
+    Returns dict(x=(3, n) float64 SoA positions, stencils=(4, k) int32, dhat, kinds=list).
+    Stencils come grouped by kind in the order of ``mix`` unless ``shuffle``.
+    """
+    rng = np.random.default_rng(seed)
+    verts, tuples, kinds = [], [], []
+    nv = 0
+    for kind, cnt in type_counts(k, mix):
+        for _ in range(cnt):
+            P = make_stencil(kind, rng, dhat)
+            ids = list(range(nv, nv + len(P)))
+            nv += len(P)
+            verts.append(P)
+            tuples.append(encode(kind, ids))
+            kinds.append(kind)
+    x = np.ascontiguousarray(np.concatenate(verts).T)
+    st = np.array(tuples, dtype=np.int64).T.astype(np.int32)
+    if shuffle:
+        perm = rng.permutation(k)
+        st = np.ascontiguousarray(st[:, perm])
+        kinds = [kinds[i] for i in perm]
+    return {"x": x, "stencils": np.ascontiguousarray(st), "dhat": dhat, "kinds": kinds}
