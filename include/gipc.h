@@ -1,0 +1,159 @@
+/*
+ * gipc.h -- C ABI of the GB300 Gauss-Newton IPC hot path.
+ *
+ * The library evaluates the rewritten simplicial-measure contact barrier of
+ * Huang et al., "GIPC: Fast and stable Gauss-Newton optimization of IPC
+ * barrier energy" (the paper), its gradient and its analytically PSD-projected
+ * Hessian per contact stencil, and the pieces of the Gauss-Newton step that
+ * consume them.
+ *
+ * Conventions shared by every call
+ *  - Pointers are DEVICE pointers unless the name ends in `_h` (host).
+ *  - The caller owns every input and output buffer.  A context owns only its
+ *    own scratch memory.
+ *  - Every call enqueues its work on `stream` (a cudaStream_t; NULL is the
+ *    legacy default stream), returns without synchronising unless its comment
+ *    says otherwise, and never calls cudaDeviceSynchronize.
+ *  - Positions are float64 structure-of-arrays: x[0*n + i], x[1*n + i],
+ *    x[2*n + i] are the x, y, z coordinates of vertex i.
+ *  - Per-stencil outputs are "entry-major": entry j of stencil i is stored at
+ *    out[j*k + i], so one warp writes 32 consecutive values of one entry.
+ *  - Every call returns a gipc_status.  On failure gipc_last_error() gives a
+ *    message (per host thread).  Arguments are checked on the host before
+ *    any launch; a call that fails its checks enqueues nothing.
+ */
+#ifndef GIPC_H
+#define GIPC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GIPC_OK = 0,
+    GIPC_ERR_INVALID_ARG = -1,   /* a pointer, size or option failed the host checks   */
+    GIPC_ERR_CUDA = -2,          /* a CUDA runtime call or kernel launch failed          */
+    GIPC_ERR_OOM = -3,           /* device scratch could not be allocated                */
+    GIPC_ERR_NOT_CONVERGED = -4, /* an iteration cap was reached                         */
+    GIPC_ERR_NONFINITE = -5,     /* a NaN or Inf was detected in device data             */
+    GIPC_ERR_TIMEOUT = -6,       /* a bounded device wait expired                        */
+    GIPC_ERR_CAPACITY = -7       /* an output buffer is smaller than the result          */
+} gipc_status;
+
+/* Contact stencil types.  The type is carried by the signs of the stencil's
+ * four vertex indices (paper Sec. 7.2, "Data structures"):
+ *   EE [+,+,+,+]  PT [-,+,+,+]  PE [-,+,+,#]  PP [-,+,#,#]
+ *   nearly parallel: EE [+,-,+,+]  PE [-,-,+,-]  PP [-,-,-,-]
+ * A negative slot stores -(i+1) (= ~i), so vertex 0 can carry a sign; '#'
+ * is GIPC_NULL_INDEX.  Vertex slot order after decoding:
+ *   PT      point, triangle v0, v1, v2
+ *   EE      edge-a end 0, edge-a end 1, edge-b end 0, edge-b end 1
+ *   PE      point, edge end 0, edge end 1
+ *   PP      point a, point b
+ *   EE_PAR  as EE
+ *   PE_PAR  point, other end of the point's edge, edge end 0, edge end 1
+ *   PP_PAR  point a, other end of a's edge, point b, other end of b's edge
+ * The distance of PE_PAR is between slots 0 and (2,3); of PP_PAR between
+ * slots 0 and 2; the parallel measure c always uses the edges (0,1), (2,3). */
+typedef enum {
+    GIPC_PT = 0, GIPC_EE = 1, GIPC_PE = 2, GIPC_PP = 3,
+    GIPC_EE_PAR = 4, GIPC_PE_PAR = 5, GIPC_PP_PAR = 6
+} gipc_stencil_type;
+
+#define GIPC_NULL_INDEX ((int32_t)(-2147483647 - 1))
+
+/* Per-stencil flag bits written by gipc_eval_stencils. */
+#define GIPC_FLAG_ACTIVE    0x01u   /* d < dhat: the barrier is non-zero                    */
+#define GIPC_FLAG_FILTERED  0x02u   /* g < eps_g: Eq. 23 replaced lambda_1 by lambda_1^thr  */
+#define GIPC_FLAG_MOLLIFIED 0x04u   /* c < eps_x: the mollifier of Eq. 25 is active         */
+#define GIPC_FLAG_INVALID   0x80u   /* malformed tuple or index >= n: outputs left zero     */
+
+typedef enum { GIPC_FP64 = 0, GIPC_MIXED = 1 } gipc_precision;
+
+typedef enum {
+    GIPC_HESS_DENSE = 0,   /* the full 3s x 3s block per stencil                        */
+    GIPC_HESS_RANK1 = 1    /* (lambda, w) with block = lambda * w w^T                    */
+} gipc_hess_mode;
+
+/* Parameters of the barrier (paper Sec. 5.3-5.4, 6.1).  Lengths are in the
+ * units of the positions. */
+typedef struct {
+    double dhat;          /* computational accuracy target d-hat (> 0)                   */
+    double kappa;         /* barrier stiffness multiplying every stencil energy (>= 0)   */
+    double d_thr_ratio;   /* d_thr / dhat of the proximal filter (paper: 0.1), in (0,1)  */
+} gipc_barrier_params;
+
+typedef struct gipc_ctx gipc_ctx;
+
+/* Create / destroy a context.  A context holds scratch for the calls that need
+ * it and binds to the device that is current at creation. */
+gipc_status gipc_create(gipc_ctx** ctx_out_h);
+gipc_status gipc_destroy(gipc_ctx* ctx);
+
+/* Message of the last failure on the calling host thread ("" if none). */
+const char* gipc_last_error(void);
+
+/* eps_x of the nearly-parallel mollifier (paper Sec. 6.1, below Eq. 25):
+ *   eps_x = 1e-3 * ||xbar_{12} - xbar_{11}||^2 * ||xbar_{22} - xbar_{21}||^2
+ * from REST positions `rest_x` ([3][n] float64) for the two edges of every
+ * EE-derived stencil (slots (0,1) and (2,3)); 0 for PT, PE and PP.
+ *   stencils   int32 [4][k], sign-encoded (see gipc_stencil_type)
+ *   eps_x_out  float64 [k]
+ * Malformed tuples or indices >= n give eps_x = 0 (no read out of range).
+ * Errors: GIPC_ERR_INVALID_ARG for n < 0, k < 0 or a null pointer with k > 0. */
+gipc_status gipc_compute_eps_x(const double* rest_x, int64_t n, const int32_t* stencils,
+                               int64_t k, double* eps_x_out, void* stream);
+
+/* Barrier energy, gradient and PSD-projected Hessian of every stencil
+ * (paper Alg. 2 per pair; Eq. 7-36).
+ *
+ * For each stencil with vertices x_s (s = 2, 3 or 4):
+ *   g = d^2 / dhat^2 with d the distance of its type (Eq. 4-5, Eq. 9-11);
+ *   inactive (all outputs 0, flags 0) when g >= 1;
+ *   b(g) = dhat^4 (1-g)^2 ln^2 g (Eq. 24), energy = kappa * b;
+ *   plain types:   grad = kappa * b_g * dg/dx,
+ *                  H = kappa * lambda1_hat * w w^T with w = df/dx, f = sqrt(g),
+ *                  lambda1 = 4 g b_gg + 2 b_g (Eq. 18), replaced by its value at
+ *                  g = eps_g = d_thr_ratio^2 when g < eps_g (Eq. 23);
+ *   parallel types: btilde = e(c) b(g) with the mollifier of Eq. 25 (c the
+ *                  parallel measure, eps_x as given), grad = kappa * dbtilde/dx,
+ *                  H = kappa * lambda8' * w w^T (Eq. 36) with
+ *                  w = q0 * dsqrt(c)/dx + q1 * df/dx, (q0, q1) the unit
+ *                  eigenvector of [[lambda_gamma1, 4t], [4t, lambda_g1]] for its
+ *                  larger eigenvalue lambda8' (Eq. 33-35), q1 >= 0.  The filter of
+ *                  Eq. 23 is applied to lambda_g1.
+ * Geometry (distances, cross products, the parallel measure) is evaluated with
+ * error-free transformations in double-double precision, so g and c are
+ * correctly rounded float64 values except in rare rounding ties.
+ *
+ * Arguments
+ *   x          float64 [3][n] positions
+ *   stencils   int32 [4][k] sign-encoded tuples
+ *   eps_x      float64 [k] (from gipc_compute_eps_x); may be NULL when the list
+ *              holds no parallel types (then eps_x = 0: mollifier inactive)
+ *   prm_h      barrier parameters (host)
+ *   prec       GIPC_FP64, or GIPC_MIXED (Hessian blocks / w written as float32)
+ *   mode       GIPC_HESS_DENSE or GIPC_HESS_RANK1
+ *   energy     float64 [k] or NULL
+ *   grad       float64 [12][k] or NULL; entries j < 3s used (slot-major x,y,z)
+ *   hess       DENSE: [144][k] entries a*3s+b for a, b < 3s (row-major block);
+ *              RANK1: [12][k] holding w (entries j < 3s);
+ *              float64 for GIPC_FP64, float32 for GIPC_MIXED; or NULL
+ *   lam        float64 [k] (RANK1 only; kappa * lambda) or NULL
+ *   flags      uint8 [k] (GIPC_FLAG_*) or NULL
+ * Entries beyond a stencil's 3s (or (3s)^2) are not written.
+ * Errors: GIPC_ERR_INVALID_ARG (bad sizes, null x/stencils with k > 0,
+ * dhat <= 0, kappa < 0, d_thr_ratio outside (0,1), unknown prec/mode),
+ * GIPC_ERR_CUDA (launch failure). */
+gipc_status gipc_eval_stencils(const double* x, int64_t n, const int32_t* stencils, int64_t k,
+                               const double* eps_x, const gipc_barrier_params* prm_h,
+                               int prec, int mode, double* energy, double* grad, void* hess,
+                               double* lam, uint8_t* flags, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GIPC_H */

@@ -1,0 +1,70 @@
+"""ctypes view of the C ABI in include/gipc.h (argument marshalling only).
+
+Loading fails loudly when the in-tree library has not been built: there is no
+fallback implementation.
+"""
+import ctypes
+import os
+
+from .build import LIB
+
+GIPC_OK = 0
+STATUS_NAMES = {0: "GIPC_OK", -1: "GIPC_ERR_INVALID_ARG", -2: "GIPC_ERR_CUDA", -3: "GIPC_ERR_OOM",
+                -4: "GIPC_ERR_NOT_CONVERGED", -5: "GIPC_ERR_NONFINITE", -6: "GIPC_ERR_TIMEOUT",
+                -7: "GIPC_ERR_CAPACITY"}
+
+GIPC_FP64, GIPC_MIXED = 0, 1
+GIPC_HESS_DENSE, GIPC_HESS_RANK1 = 0, 1
+
+FLAG_ACTIVE, FLAG_FILTERED, FLAG_MOLLIFIED, FLAG_INVALID = 0x01, 0x02, 0x04, 0x80
+
+
+class BarrierParams(ctypes.Structure):
+    _fields_ = [("dhat", ctypes.c_double), ("kappa", ctypes.c_double), ("d_thr_ratio", ctypes.c_double)]
+
+
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_D = ctypes.c_double
+_INT = ctypes.c_int
+
+# name -> (restype, argtypes)
+SIGNATURES = {
+    "gipc_create": (_INT, [ctypes.POINTER(_P)]),
+    "gipc_destroy": (_INT, [_P]),
+    "gipc_last_error": (ctypes.c_char_p, []),
+    "gipc_compute_eps_x": (_INT, [_P, _I64, _P, _I64, _P, _P]),
+    "gipc_eval_stencils": (_INT, [_P, _I64, _P, _I64, _P, ctypes.POINTER(BarrierParams), _INT, _INT,
+                                  _P, _P, _P, _P, _P, _P]),
+}
+
+_lib = None
+
+
+class GipcError(RuntimeError):
+    def __init__(self, fn, status):
+        msg = lib().gipc_last_error().decode(errors="replace")
+        super().__init__(f"{fn} -> {STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def lib():
+    """The loaded library (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB):
+            raise ImportError(f"GIPC CUDA library not built ({LIB}); run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def call(name, *args):
+    st = getattr(lib(), name)(*args)
+    if st != GIPC_OK:
+        raise GipcError(name, st)
+    return st

@@ -1,0 +1,49 @@
+// Context lifetime and error reporting of the GIPC C ABI.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "common.cuh"
+#include "context.cuh"
+
+namespace gipc {
+
+static thread_local char g_last_error[512] = "";
+
+gipc_status fail(gipc_status st, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+gipc_status check_launch(const char* what) {
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(GIPC_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+    return GIPC_OK;
+}
+
+}  // namespace gipc
+
+extern "C" const char* gipc_last_error(void) { return gipc::g_last_error; }
+
+extern "C" gipc_status gipc_create(gipc_ctx** ctx_out_h) {
+    if (!ctx_out_h) return gipc::fail(GIPC_ERR_INVALID_ARG, "gipc_create: null output pointer");
+    gipc_ctx* c = new (std::nothrow) gipc_ctx();
+    if (!c) return gipc::fail(GIPC_ERR_OOM, "gipc_create: host allocation failed");
+    if (cudaGetDevice(&c->device) != cudaSuccess) {
+        delete c;
+        return gipc::fail(GIPC_ERR_CUDA, "gipc_create: no current CUDA device");
+    }
+    *ctx_out_h = c;
+    return GIPC_OK;
+}
+
+extern "C" gipc_status gipc_destroy(gipc_ctx* ctx) {
+    if (!ctx) return GIPC_OK;
+    ctx->release_all();
+    delete ctx;
+    return GIPC_OK;
+}

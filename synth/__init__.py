@@ -176,3 +176,147 @@ def unit_stencils(k=10000, seed=20230809, mix=DEFAULT_MIX, dhat=UNIT_DHAT, shuff
         st = np.ascontiguousarray(st[:, perm])
         kinds = [kinds[i] for i in perm]
     return {"x": x, "stencils": np.ascontiguousarray(st), "dhat": dhat, "kinds": kinds}
+
+
+# ----------------------------------------------------------------------------- vectorised batch
+def _v_unit(rng, m):
+    v = rng.normal(size=(m, 3))
+    return v / np.linalg.norm(v, axis=1, keepdims=True)
+
+
+def _v_perp(rng, u):
+    w = np.cross(u, _v_unit(rng, len(u)))
+    return w / np.linalg.norm(w, axis=1, keepdims=True)
+
+
+def _v_distance(rng, m, dhat):
+    r = 10.0 ** rng.uniform(-4.0, 0.0, m)
+    bad = (np.abs(r - 0.1) <= 1e-9) | (r >= 1.0 - 1e-9)
+    r[bad] = 0.5
+    return dhat * r
+
+
+def _v_segments(rng, m, min_len=0.1):
+    a, b = rng.uniform(0, 1, (m, 3)), rng.uniform(0, 1, (m, 3))
+    short = np.linalg.norm(b - a, axis=1) < min_len
+    while short.any():
+        a[short], b[short] = rng.uniform(0, 1, (short.sum(), 3)), rng.uniform(0, 1, (short.sum(), 3))
+        short = np.linalg.norm(b - a, axis=1) < min_len
+    return a, b
+
+
+def _v_triangles(rng, m):
+    out = np.empty((m, 3, 3))
+    filled = 0
+    cmin = math.cos(math.radians(10.0))
+    while filled < m:
+        P = rng.uniform(0, 1, (2 * (m - filled) + 16, 3, 3))
+        area = 0.5 * np.linalg.norm(np.cross(P[:, 1] - P[:, 0], P[:, 2] - P[:, 0]), axis=1)
+        ok = area >= 1e-3
+        for i in range(3):
+            u, v = P[:, (i + 1) % 3] - P[:, i], P[:, (i + 2) % 3] - P[:, i]
+            cosang = (u * v).sum(1) / (np.linalg.norm(u, axis=1) * np.linalg.norm(v, axis=1))
+            ok &= cosang <= cmin
+        P = P[ok][: m - filled]
+        out[filled:filled + len(P)] = P
+        filled += len(P)
+    return out
+
+
+def _v_bary(rng, m):
+    out = np.empty((m, 3))
+    filled = 0
+    while filled < m:
+        b = rng.dirichlet((1.0, 1.0, 1.0), 2 * (m - filled) + 16)
+        b = b[b.min(1) >= 0.05][: m - filled]
+        out[filled:filled + len(b)] = b
+        filled += len(b)
+    return out
+
+
+def _v_make(kind, rng, m, dhat):
+    """Vertices (m, s, 3) of m stencils of one kind (same recipe as ``make_stencil``)."""
+    d = _v_distance(rng, m, dhat)[:, None]
+    sign = rng.choice((-1.0, 1.0), (m, 1))
+    if kind == "PT":
+        T = _v_triangles(rng, m)
+        foot = np.einsum("mi,mij->mj", _v_bary(rng, m), T)
+        n = np.cross(T[:, 1] - T[:, 0], T[:, 2] - T[:, 0])
+        n /= np.linalg.norm(n, axis=1, keepdims=True)
+        return np.stack([foot + sign * d * n, T[:, 0], T[:, 1], T[:, 2]], 1)
+    if kind in ("EE", "EE_PAR"):
+        a0, a1 = _v_segments(rng, m)
+        e1 = (a1 - a0) / np.linalg.norm(a1 - a0, axis=1, keepdims=True)
+        p1 = a0 + rng.uniform(0.1, 0.9, (m, 1)) * (a1 - a0)
+        nrm = _v_perp(rng, e1)
+        mm = np.cross(e1, nrm)
+        th = (10.0 ** rng.uniform(-7, -2, (m, 1))) if kind == "EE_PAR" else rng.uniform(0.05, math.pi / 2, (m, 1))
+        e2 = np.cos(th) * e1 + np.sin(th) * mm
+        p2 = p1 + sign * d * nrm
+        L2 = rng.uniform(0.1, 0.8, (m, 1))
+        b0 = p2 - rng.uniform(0.1, 0.9, (m, 1)) * L2 * e2
+        return np.stack([a0, a1, b0, b0 + L2 * e2], 1)
+    if kind in ("PE", "PE_PAR"):
+        e0, e1 = _v_segments(rng, m)
+        ed = (e1 - e0) / np.linalg.norm(e1 - e0, axis=1, keepdims=True)
+        nrm = _v_perp(rng, ed)
+        p = e0 + rng.uniform(0.1, 0.9, (m, 1)) * (e1 - e0) + d * nrm
+        if kind == "PE":
+            return np.stack([p, e0, e1], 1)
+        th = 10.0 ** rng.uniform(-7, -2, (m, 1))
+        L1 = rng.uniform(0.1, 0.8, (m, 1))
+        direction = np.cos(th) * sign * ed + np.sin(th) * nrm
+        return np.stack([p, p + L1 * direction, e0, e1], 1)
+    if kind in ("PP", "PP_PAR"):
+        p = rng.uniform(0, 1, (m, 3))
+        a = _v_unit(rng, m)
+        q = p + d * a
+        if kind == "PP":
+            return np.stack([p, q], 1)
+        th = 10.0 ** rng.uniform(-7, -2, (m, 1))
+        mm = _v_perp(rng, a)
+        L1, L2 = rng.uniform(0.1, 0.8, (m, 1)), rng.uniform(0.1, 0.8, (m, 1))
+        return np.stack([p, p - L1 * a, q, q + L2 * (np.cos(th) * a + np.sin(th) * mm)], 1)
+    raise ValueError(kind)
+
+
+def _v_encode(kind, ids):
+    """Sign-encoded tuples (4, m) for vertex ids (m, s) in slot order."""
+    m = ids.shape[0]
+    t = np.full((4, m), NULL, dtype=np.int64)
+    neg = lambda a: -(a + 1)
+    if kind == "PT":
+        t[0], t[1], t[2], t[3] = neg(ids[:, 0]), ids[:, 1], ids[:, 2], ids[:, 3]
+    elif kind == "EE":
+        t[:] = ids.T
+    elif kind == "PE":
+        t[0], t[1], t[2] = neg(ids[:, 0]), ids[:, 1], ids[:, 2]
+    elif kind == "PP":
+        t[0], t[1] = neg(ids[:, 0]), ids[:, 1]
+    elif kind == "EE_PAR":
+        t[0], t[1], t[2], t[3] = ids[:, 0], neg(ids[:, 1]), ids[:, 2], ids[:, 3]
+    elif kind == "PE_PAR":
+        t[0], t[1], t[2], t[3] = neg(ids[:, 0]), neg(ids[:, 1]), ids[:, 2], neg(ids[:, 3])
+    elif kind == "PP_PAR":
+        t[:] = neg(ids.T)
+    return t
+
+
+def batch_stencils(k, seed=20230810, mix=DEFAULT_MIX, dhat=UNIT_DHAT):
+    """Vectorised generator of the same recipe as ``unit_stencils`` for large k (own vertices)."""
+    rng = np.random.default_rng(seed)
+    xs, ts, kinds = [], [], []
+    nv = 0
+    for kind, cnt in type_counts(k, mix):
+        if cnt == 0:
+            continue
+        P = _v_make(kind, rng, cnt, dhat)
+        s = P.shape[1]
+        ids = nv + np.arange(cnt * s, dtype=np.int64).reshape(cnt, s)
+        nv += cnt * s
+        xs.append(P.reshape(-1, 3))
+        ts.append(_v_encode(kind, ids))
+        kinds.append((kind, cnt))
+    x = np.ascontiguousarray(np.concatenate(xs).T)
+    st = np.ascontiguousarray(np.concatenate(ts, axis=1).astype(np.int32))
+    return {"x": x, "stencils": st, "dhat": dhat, "kind_counts": kinds}
