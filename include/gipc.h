@@ -69,7 +69,7 @@ typedef enum {
 #define GIPC_FLAG_ACTIVE    0x01u   /* d < dhat: the barrier is non-zero                    */
 #define GIPC_FLAG_FILTERED  0x02u   /* g < eps_g: Eq. 23 replaced lambda_1 by lambda_1^thr  */
 #define GIPC_FLAG_MOLLIFIED 0x04u   /* c < eps_x: the mollifier of Eq. 25 is active         */
-#define GIPC_FLAG_INVALID   0x80u   /* malformed tuple or index >= n: outputs left zero     */
+#define GIPC_FLAG_INVALID   0x80u   /* malformed tuple or index >= n: energy/lam 0, rest unwritten */
 
 typedef enum { GIPC_FP64 = 0, GIPC_MIXED = 1 } gipc_precision;
 
@@ -144,7 +144,8 @@ gipc_status gipc_compute_eps_x(const double* rest_x, int64_t n, const int32_t* s
  *              float64 for GIPC_FP64, float32 for GIPC_MIXED; or NULL
  *   lam        float64 [k] (RANK1 only; kappa * lambda) or NULL
  *   flags      uint8 [k] (GIPC_FLAG_*) or NULL
- * Entries beyond a stencil's 3s (or (3s)^2) are not written.
+ * Entries beyond a stencil's 3s (or (3s)^2) are not written, nor are the
+ * gradient / Hessian entries of an invalid stencil (GIPC_FLAG_INVALID).
  * Errors: GIPC_ERR_INVALID_ARG (bad sizes, null x/stencils with k > 0,
  * dhat <= 0, kappa < 0, d_thr_ratio outside (0,1), unknown prec/mode),
  * GIPC_ERR_CUDA (launch failure). */
@@ -152,6 +153,58 @@ gipc_status gipc_eval_stencils(const double* x, int64_t n, const int32_t* stenci
                                const double* eps_x, const gipc_barrier_params* prm_h,
                                int prec, int mode, double* energy, double* grad, void* hess,
                                double* lam, uint8_t* flags, void* stream);
+
+/* ------------------------------------------------------------------ assembly */
+
+/* A square 3x3-block sparse matrix (BSR) over n block rows.  Block p of row r
+ * (rowptr[r] <= p < rowptr[r+1]) sits at block column colidx[p], columns
+ * ascending within a row; its 9 values are vals[9p + 3i + j] (row-major). */
+typedef struct {
+    int64_t n;         /* block rows (= vertices); set by gipc_assemble_bsr      */
+    int64_t nnzb;      /* stored blocks; set by gipc_assemble_bsr                */
+    int64_t capacity;  /* capacity of colidx / vals in blocks (caller)           */
+    int32_t* rowptr;   /* [n+1]                                                  */
+    int32_t* colidx;   /* [capacity]                                             */
+    void* vals;        /* [capacity][9]: float64 (GIPC_FP64) or float32 (GIPC_MIXED) */
+    int prec;          /* GIPC_FP64 or GIPC_MIXED (caller)                       */
+} gipc_bsr;
+
+/* One list of elements with their local blocks, in the layout
+ * gipc_eval_stencils (stencils) or gipc_eval_tets (tetrahedra) writes. */
+typedef struct {
+    const int32_t* idx;   /* stencils: int32 [4][count] sign-encoded; tets: int32 [4][count] vertex ids */
+    int64_t count;
+    int hess_mode;        /* GIPC_HESS_DENSE ([144][count]) or, stencils only, GIPC_HESS_RANK1     */
+    const void* hess;     /* dense blocks or w [12][count]; float64 / float32 as the BSR's prec     */
+    const double* lam;    /* RANK1: lambda [count] (block = lam * w w^T)                              */
+    const double* grad;   /* float64 [12][count] element gradients, or NULL                          */
+} gipc_elements;
+
+/* Assemble H = M + sum_e P_e^T H_e P_e into `bsr` and, if grad_out is given,
+ * g = grad_base + sum_e P_e^T g_e into grad_out (float64 [3][n]).
+ * (Paper: the Newton system of Alg. 1, lines "g <- dI/dx" and
+ * "H <- M + getPSDForceJacobian(...)"; the local-to-global decomposition of
+ * the system matrix in supplement Sec. S6.)
+ *
+ * Pattern: every ordered vertex pair of every element plus (i, i) for each
+ * vertex when `mass` is given, built by a key sort; identical on every run.
+ * Values: each block sums, in this order, m_i I_3 (diagonal, if mass), then
+ * the sub-blocks of its tetrahedra in ascending index, then those of its
+ * stencils in ascending index -- a fixed order, so results are reproducible
+ * bit for bit.  Elements that are malformed or reference a vertex >= n are
+ * skipped.  `stencils_h` / `tets_h` (host structs) may be NULL.
+ *
+ *   mass       float64 [n] lumped vertex masses, or NULL (no diagonal terms)
+ *   grad_base  float64 [3][n] added first to the gradient (e.g. inertia), or NULL
+ *
+ * Blocks until the pattern size is known (one stream synchronisation), then
+ * enqueues the value pass.  Scratch is owned by ctx and reused across calls.
+ * Errors: GIPC_ERR_INVALID_ARG; GIPC_ERR_CAPACITY when nnzb > bsr->capacity
+ * (bsr->nnzb then holds the required count and rowptr is valid) or when a row
+ * receives more than 8192 contributions; GIPC_ERR_OOM; GIPC_ERR_CUDA. */
+gipc_status gipc_assemble_bsr(gipc_ctx* ctx, int64_t n, const gipc_elements* stencils_h,
+                              const gipc_elements* tets_h, const double* mass, const double* grad_base,
+                              gipc_bsr* bsr_h, double* grad_out, void* stream);
 
 #ifdef __cplusplus
 }

@@ -15,7 +15,7 @@ from ._abi import (FLAG_ACTIVE, FLAG_FILTERED, FLAG_INVALID, FLAG_MOLLIFIED, Gip
 TYPE_IDS = {"PT": 0, "EE": 1, "PE": 2, "PP": 3, "EE_PAR": 4, "PE_PAR": 5, "PP_PAR": 6}
 NULL_INDEX = -2147483648
 
-__all__ = ["compute_eps_x", "eval_stencils", "GipcError", "FLAG_ACTIVE", "FLAG_FILTERED",
+__all__ = ["compute_eps_x", "eval_stencils", "assemble_bsr", "Context", "default_context", "GipcError", "FLAG_ACTIVE", "FLAG_FILTERED",
            "FLAG_MOLLIFIED", "FLAG_INVALID", "TYPE_IDS", "NULL_INDEX"]
 
 
@@ -86,3 +86,92 @@ def eval_stencils(x, stencils, eps_x, dhat, kappa, d_thr_ratio=0.1, precision="f
               prec, md, _ptr(out.get("energy")), _ptr(out.get("grad")), _ptr(out.get("hess")),
               _ptr(out.get("lam")), _ptr(out.get("flags")), _stream(stream))
     return out
+
+
+class Context:
+    """Owns a gipc_ctx (device scratch for assembly and the solver)."""
+
+    def __init__(self):
+        self._h = ctypes.c_void_p()
+        _abi.call("gipc_create", ctypes.byref(self._h))
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            _abi.lib().gipc_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+_contexts = {}
+
+
+def default_context(device=None):
+    dev = torch.cuda.current_device() if device is None else torch.device(device).index
+    if dev not in _contexts:
+        with torch.cuda.device(dev):
+            _contexts[dev] = Context()
+    return _contexts[dev]
+
+
+def _elements(idx, blocks, mode, lam, grad):
+    if idx is None:
+        return None
+    _check(idx, "element indices", torch.int32, 4)
+    return _abi.Elements(idx.data_ptr(), idx.shape[1], {"dense": 0, "rank1": 1}[mode],
+                         blocks.data_ptr() if blocks is not None else 0,
+                         lam.data_ptr() if lam is not None else 0,
+                         grad.data_ptr() if grad is not None else 0)
+
+
+def assemble_bsr(n, stencils=None, stencil_hess=None, stencil_mode="dense", stencil_lam=None,
+                 stencil_grad=None, tets=None, tet_hess=None, tet_grad=None, mass=None, grad_base=None,
+                 precision="fp64", want_grad=True, capacity=None, ctx=None, stream=None, out=None):
+    """Assemble the BSR Hessian and the gradient (gipc_assemble_bsr).
+
+    Returns dict(rowptr [n+1] i32, colidx [nnzb] i32, vals [nnzb, 9] f64/f32, grad [3, n] f64, nnzb).
+    ``out`` may hold preallocated colidx/vals (capacity = their length) and rowptr/grad.
+    """
+    ctx = ctx or default_context()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    prec = {"fp64": _abi.GIPC_FP64, "mixed": _abi.GIPC_MIXED}[precision]
+    vdt = torch.float64 if prec == _abi.GIPC_FP64 else torch.float32
+    se = _elements(stencils, stencil_hess, stencil_mode, stencil_lam, stencil_grad)
+    te = _elements(tets, tet_hess, "dense", None, tet_grad)
+    ne = (0 if stencils is None else stencils.shape[1]) + (0 if tets is None else tets.shape[1])
+    out = dict(out or {})
+    rowptr = out.get("rowptr")
+    if rowptr is None:
+        rowptr = torch.empty(n + 1, dtype=torch.int32, device=dev)
+    grad = out.get("grad") if want_grad else None
+    if want_grad and grad is None:
+        grad = torch.empty((3, n), dtype=torch.float64, device=dev)
+    colidx, vals = out.get("colidx"), out.get("vals")
+    if colidx is None:
+        cap = capacity if capacity is not None else max(1, min(16 * ne + n, 6 * ne + n))
+        colidx = torch.empty(cap, dtype=torch.int32, device=dev)
+        vals = torch.empty((cap, 9), dtype=vdt, device=dev)
+    for attempt in range(2):
+        bsr = _abi.Bsr(n, 0, colidx.shape[0], rowptr.data_ptr(), colidx.data_ptr(), vals.data_ptr(), prec)
+        st = _abi.call_status("gipc_assemble_bsr", ctx.handle, n,
+                              ctypes.byref(se) if se is not None else None,
+                              ctypes.byref(te) if te is not None else None,
+                              _ptr(mass), _ptr(grad_base), ctypes.byref(bsr), _ptr(grad), _stream(stream))
+        if st == _abi.GIPC_ERR_CAPACITY and attempt == 0 and bsr.nnzb > colidx.shape[0]:
+            colidx = torch.empty(int(bsr.nnzb), dtype=torch.int32, device=dev)
+            vals = torch.empty((int(bsr.nnzb), 9), dtype=vdt, device=dev)
+            continue
+        if st != _abi.GIPC_OK:
+            raise GipcError("gipc_assemble_bsr", st)
+        break
+    nnzb = int(bsr.nnzb)
+    return {"rowptr": rowptr, "colidx": colidx[:nnzb], "vals": vals[:nnzb], "grad": grad, "nnzb": nnzb,
+            "n": n, "precision": precision}

@@ -23,6 +23,17 @@ class BarrierParams(ctypes.Structure):
     _fields_ = [("dhat", ctypes.c_double), ("kappa", ctypes.c_double), ("d_thr_ratio", ctypes.c_double)]
 
 
+class Bsr(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nnzb", ctypes.c_int64), ("capacity", ctypes.c_int64),
+                ("rowptr", ctypes.c_void_p), ("colidx", ctypes.c_void_p), ("vals", ctypes.c_void_p),
+                ("prec", ctypes.c_int)]
+
+
+class Elements(ctypes.Structure):
+    _fields_ = [("idx", ctypes.c_void_p), ("count", ctypes.c_int64), ("hess_mode", ctypes.c_int),
+                ("hess", ctypes.c_void_p), ("lam", ctypes.c_void_p), ("grad", ctypes.c_void_p)]
+
+
 _P = ctypes.c_void_p
 _I64 = ctypes.c_int64
 _D = ctypes.c_double
@@ -36,6 +47,8 @@ SIGNATURES = {
     "gipc_compute_eps_x": (_INT, [_P, _I64, _P, _I64, _P, _P]),
     "gipc_eval_stencils": (_INT, [_P, _I64, _P, _I64, _P, ctypes.POINTER(BarrierParams), _INT, _INT,
                                   _P, _P, _P, _P, _P, _P]),
+    "gipc_assemble_bsr": (_INT, [_P, _I64, ctypes.POINTER(Elements), ctypes.POINTER(Elements), _P, _P,
+                                 ctypes.POINTER(Bsr), _P, _P]),
 }
 
 _lib = None
@@ -61,6 +74,14 @@ def lib():
             fn.argtypes = args
         _lib = L
     return _lib
+
+
+GIPC_ERR_CAPACITY = -7
+
+
+def call_status(name, *args):
+    """Call without raising; returns the status."""
+    return getattr(lib(), name)(*args)
 
 
 def call(name, *args):

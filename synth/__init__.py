@@ -320,3 +320,114 @@ def batch_stencils(k, seed=20230810, mix=DEFAULT_MIX, dhat=UNIT_DHAT):
     x = np.ascontiguousarray(np.concatenate(xs).T)
     st = np.ascontiguousarray(np.concatenate(ts, axis=1).astype(np.int32))
     return {"x": x, "stencils": st, "dhat": dhat, "kind_counts": kinds}
+
+
+# ----------------------------------------------------------------------------- two-sheet index space
+def sheet_index_space(k, seed=20230811, side=388, radius=0, mix=DEFAULT_MIX):
+    """Stencil tuples over two triangulated side x side vertex grids (ids [0, 2 side^2)).
+
+    Each stencil couples a primitive of one sheet with a primitive of the other
+    within ``radius`` cells of the same grid cell (a point, a grid edge or a grid
+    triangle as its type needs), so the index pattern is that of two sheets in
+    contact.  Used for assembly and SpMV workloads; the block values come from
+    the own-vertex geometry of ``batch_stencils`` with the same type counts.
+    Returns (4, k) int32 tuples (same type order as ``type_counts``) and n.
+    """
+    rng = np.random.default_rng(seed)
+    N = side
+    n = 2 * N * N
+
+    def vid(sheet, i, j):
+        return sheet * N * N + i * N + j
+
+    def cells(m):
+        return rng.integers(0, N - 1, m), rng.integers(0, N - 1, m)
+
+    def partner(i, j):
+        pi = np.clip(i + rng.integers(-radius, radius + 1, len(i)), 0, N - 2)
+        pj = np.clip(j + rng.integers(-radius, radius + 1, len(j)), 0, N - 2)
+        return pi, pj
+
+    def point(sheet, i, j):
+        di, dj = rng.integers(0, 2, len(i)), rng.integers(0, 2, len(i))
+        return vid(sheet, i + di, j + dj)[:, None]
+
+    def edge(sheet, i, j):
+        kind = rng.integers(0, 3, len(i))
+        a = vid(sheet, i, j)
+        b = np.where(kind == 0, vid(sheet, i + 1, j), np.where(kind == 1, vid(sheet, i, j + 1),
+                                                                 vid(sheet, i + 1, j + 1)))
+        return np.stack([a, b], 1)
+
+    def tri(sheet, i, j):
+        up = rng.integers(0, 2, len(i)).astype(bool)
+        a = vid(sheet, i, j)
+        b = np.where(up, vid(sheet, i + 1, j), vid(sheet, i + 1, j + 1))
+        c = np.where(up, vid(sheet, i + 1, j + 1), vid(sheet, i, j + 1))
+        return np.stack([a, b, c], 1)
+
+    ts = []
+    for kind, cnt in type_counts(k, mix):
+        if cnt == 0:
+            continue
+        i, j = cells(cnt)
+        pi, pj = partner(i, j)
+        sa = rng.integers(0, 2, cnt)
+        sb = 1 - sa
+        if kind == "PT":
+            ids = np.concatenate([point(sa, i, j), tri(sb, pi, pj)], 1)
+        elif kind == "PE":
+            ids = np.concatenate([point(sa, i, j), edge(sb, pi, pj)], 1)
+        elif kind == "PP":
+            ids = np.concatenate([point(sa, i, j), point(sb, pi, pj)], 1)
+        else:  # EE-derived: two edges
+            ids = np.concatenate([edge(sa, i, j), edge(sb, pi, pj)], 1)
+        ts.append(_v_encode(kind, ids.astype(np.int64)))
+    return np.ascontiguousarray(np.concatenate(ts, axis=1).astype(np.int32)), n
+
+
+def sheet_mass(side=388, density=1000.0):
+    """Lumped vertex masses of the two sheets: density x (spacing^3) per vertex (unit-square sheets
+    of thickness one grid spacing)."""
+    h = 1.0 / (side - 1)
+    return np.full(2 * side * side, density * h ** 3)
+
+
+# ----------------------------------------------------------------------------- assembly inputs
+def random_elements(n, k, T, seed=7, mix=DEFAULT_MIX, hub=None, hub_count=0):
+    """Random element lists over vertex ids [0, n) with random local blocks (assembly tests).
+
+    Stencils follow ``mix`` with distinct vertices per stencil; tetrahedra are 4 distinct
+    ids.  ``hub``: optionally force ``hub_count`` PT stencils to use vertex ``hub`` as their
+    point (long rows).  Returns dict of numpy arrays: stencils (4,k) i32, tets (4,T) i32,
+    dense stencil blocks hess (144,k), rank-one lam (k), w (12,k), grad (12,k), tet_hess
+    (144,T), tet_grad (12,T), mass (n), grad_base (3,n).
+    """
+    rng = np.random.default_rng(seed)
+    ts = []
+    for kind, cnt in type_counts(k, mix):
+        if cnt == 0:
+            continue
+        s = {"PT": 4, "EE": 4, "PE": 3, "PP": 2}.get(kind, 4)
+        ids = np.argsort(rng.random((cnt, n)), axis=1)[:, :s] if n <= 64 else \
+            np.stack([rng.choice(n, s, replace=False) for _ in range(cnt)])
+        if kind == "PT" and hub is not None:
+            m = min(hub_count, cnt)
+            for r in range(m):
+                row = [v for v in ids[r] if v != hub][:3]
+                while len(row) < 3:
+                    c = int(rng.integers(0, n))
+                    if c != hub and c not in row:
+                        row.append(c)
+                ids[r] = [hub] + row
+        ts.append(_v_encode(kind, ids.astype(np.int64)))
+    st = np.ascontiguousarray(np.concatenate(ts, axis=1).astype(np.int32)) if ts else np.zeros((4, 0), np.int32)
+    tets = np.stack([rng.choice(n, 4, replace=False) for _ in range(T)], 1).astype(np.int32) if T else \
+        np.zeros((4, 0), np.int32)
+    return {
+        "stencils": st, "tets": np.ascontiguousarray(tets),
+        "hess": rng.normal(size=(144, k)), "lam": rng.uniform(0.1, 2.0, k), "w": rng.normal(size=(12, k)),
+        "grad": rng.normal(size=(12, k)), "tet_hess": rng.normal(size=(144, T)),
+        "tet_grad": rng.normal(size=(12, T)), "mass": rng.uniform(0.5, 1.5, n),
+        "grad_base": rng.normal(size=(3, n)),
+    }
