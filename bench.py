@@ -1,0 +1,378 @@
+"""Benchmark of the GIPC Gauss-Newton hot path on GB300.
+
+One step = one pass of the whole hot path over the C1 batch workload:
+  1. eps_x and per-stencil barrier energy, gradient and PSD-projected Hessian for
+     1,000,000 contact stencils (40% PT, 30% EE, 10% PE, 10% PP, 6/2/2% nearly
+     parallel EE/PE/PP; distances log-uniform in [1e-4 dhat, dhat]),
+  2. assembly of the gradient and of the 3x3-block BSR Hessian (mass + blocks) over a
+     301,088-vertex two-sheet index space (~4.1M blocks), pattern by key sort,
+  3. 200 iterations of block-Jacobi modified PCG (tolerance 0, so all run).
+The metric counts stencils per second through the whole step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gipc|reference]
+                  [--precision fp64|mixed] [--hess-mode dense|rank1]
+
+Under torchrun (N > 1) every rank runs its own independent batch (weak scaling,
+no data-path collective); the step time is the max over ranks.
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "stencil grad+PSD-Hessian/s & Newton iters/s, FP64 vs mixed at ≤1e-4 rel err"
+K_STENCILS = 1_000_000
+PCG_ITERS = 200
+KAPPA = 1e3
+HBM_PEAK_FALLBACK = 6800.0        # GB/s, recipe fallback
+FP64_PEAK = 152 * 4 * 2.070       # GFLOP/s: 152 SMs x 2 FP64 FMA/clk x 2070 MHz (nominal 1.25 TFLOP/s)
+FP32_PEAK = 152 * 256 * 2.070     # GFLOP/s: 152 SMs x 128 FP32 FMA/clk x 2070 MHz
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gipc", choices=["gipc", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--hess-mode", default="dense", choices=["dense", "rank1"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_PEAK_FALLBACK, "fallback"
+
+
+def workload(seed_offset=0):
+    import synth
+    d = synth.batch_stencils(K_STENCILS, seed=20230810 + seed_offset)
+    st_sheet, n = synth.sheet_index_space(K_STENCILS, seed=20230811 + seed_offset)
+    return {"x": d["x"], "st_own": d["stencils"], "dhat": d["dhat"], "st_sheet": st_sheet, "n": n,
+            "mass": synth.sheet_mass()}
+
+
+def workload_desc(args):
+    return (f"C1 batch: {K_STENCILS} stencils (own-vertex geometry, 3.7M vertex slots) -> "
+            f"{args.hess_mode} {'FP64' if args.precision == 'fp64' else 'FP32'} Hessian blocks -> BSR over "
+            f"2x388x388 two-sheet index space -> {PCG_ITERS} PCG iterations")
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    def __init__(self):
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-f", self.path],
+                                         stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self, device_index=0):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        try:
+            with open(self.path) as f:
+                for line in f:
+                    parts = [p.strip() for p in line.split(",")]
+                    if len(parts) >= 9 and parts[0] == str(device_index):
+                        rows.append(parts)
+            os.unlink(self.path)
+        except Exception:
+            return None
+        if not rows:
+            return None
+        sm = sorted(float(r[1]) for r in rows)
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for nm, v in zip(names, r[5:9]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(nm)
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": float(rows[0][2]), "reasons": sorted(reasons),
+                "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def gpu_step(g, dev, W, args, bufs, ctx):
+    import torch
+    ev = torch.cuda.Event
+    marks = [ev(enable_timing=True) for _ in range(4)]
+    marks[0].record()
+    eps = g.compute_eps_x(W["x"], W["st_own"], out=bufs["eps"])
+    e = g.eval_stencils(W["x"], W["st_own"], eps, W["dhat"], KAPPA, precision=args.precision,
+                        mode=args.hess_mode, want=("energy", "grad", "hess", "lam", "flags")
+                        if args.hess_mode == "rank1" else ("energy", "grad", "hess", "flags"), out=bufs["eval"])
+    bufs["eval"] = e
+    marks[1].record()
+    A = g.assemble_bsr(W["n"], stencils=W["st_sheet"], stencil_hess=e["hess"], stencil_mode=args.hess_mode,
+                       stencil_lam=e.get("lam"), stencil_grad=e["grad"], mass=W["mass"],
+                       precision=args.precision, out=bufs["bsr"], ctx=ctx)
+    bufs["bsr"] = {"rowptr": A["rowptr"], "colidx": A["colidx"], "vals": A["vals"], "grad": A["grad"]}
+    marks[2].record()
+    torch.neg(A["grad"], out=bufs["rhs"])
+    d, k, rel = g.pcg(A, bufs["rhs"], rel_tol=0.0, max_iter=PCG_ITERS, ctx=ctx)
+    marks[3].record()
+    return d, A, marks
+
+
+def launches_per_step(n):
+    tiles = (n + 1 + 4095) // 4096
+    scan = 1 if n + 1 <= 4096 else (3 if tiles <= 4096 else 5)
+    assembly = 11 + 2 * scan      # init, count, init_cursor, fill, 2 sorts, rowptr32, emit, seg_end, grad_init, values
+    nck = 64 * ((n + 1023) // 1024)
+    perm = 2 + (1 if nck <= 4096 else (3 if (nck + 4095) // 4096 <= 4096 else 5))  # row-length sort
+    pcg = perm + 6 + 3 * PCG_ITERS + 1  # set, 2 conversions, factor, spmv(x0), init, 3/iteration, back-conversion
+    return 2 + assembly + pcg
+
+
+def source_hash(*rel):
+    h = hashlib.sha256()
+    for r in rel:
+        with open(os.path.join(ROOT, r), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel, precision):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on the current source."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            T = json.load(f)
+        ent = T[f"{kernel}/{precision}"]
+        if ent["source_sha"] != source_hash(*ent["sources"]):
+            return None
+        return float(ent["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    import paper_2308_09400_gb300 as g
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ctx = g.default_context()
+
+    Wh = workload(seed_offset=rank)
+    W = {"x": torch.tensor(Wh["x"], device=dev), "st_own": torch.tensor(Wh["st_own"], device=dev),
+         "st_sheet": torch.tensor(Wh["st_sheet"], device=dev), "mass": torch.tensor(Wh["mass"], device=dev),
+         "n": Wh["n"], "dhat": Wh["dhat"]}
+    bufs = {"eps": torch.empty(K_STENCILS, dtype=torch.float64, device=dev), "eval": {},
+            "bsr": {}, "rhs": torch.empty((3, Wh["n"]), dtype=torch.float64, device=dev)}
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # warm-up (also sizes every buffer)
+    for _ in range(args.warmup):
+        d, A, _ = gpu_step(g, dev, W, args, bufs, ctx)
+    nnzb = A["nnzb"]
+    barrier()
+
+    clocks = ClockSampler()
+    clocks.start()
+    ctx.profile_begin()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    phase = np.zeros(3)
+    barrier()
+    t0.record()
+    all_marks = []
+    for _ in range(args.steps):
+        d, A, marks = gpu_step(g, dev, W, args, bufs, ctx)
+        all_marks.append(marks)
+    t1.record()
+    barrier()
+    prof = ctx.profile_read()
+    ctx.profile_stop()
+    clk = clocks.stop(local)
+    ms = t0.elapsed_time(t1) / args.steps
+    for m in all_marks:
+        phase += [m[0].elapsed_time(m[1]), m[1].elapsed_time(m[2]), m[2].elapsed_time(m[3])]
+    phase /= args.steps
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # e2e: host (pinned) inputs in, Newton direction out, through the public API
+    host = {"x": torch.tensor(Wh["x"]).pin_memory(), "st_own": torch.tensor(Wh["st_own"]).pin_memory(),
+            "st_sheet": torch.tensor(Wh["st_sheet"]).pin_memory(), "mass": torch.tensor(Wh["mass"]).pin_memory()}
+    out_h = torch.empty((3, Wh["n"]), dtype=torch.float64).pin_memory()
+    h2d = sum(t.numel() * t.element_size() for t in host.values())
+    d2h = out_h.numel() * out_h.element_size()
+    Wd = dict(W)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record()
+    for _ in range(args.steps):
+        for key in host:
+            Wd[key] = host[key].to(dev, non_blocking=True)
+        dd, _, _ = gpu_step(g, dev, Wd, args, bufs, ctx)
+        out_h.copy_(dd, non_blocking=True)
+    e1.record()
+    barrier()
+    e2e_ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    if rank == 0:
+        hbm, hbm_src = peaks()
+        n = Wh["n"]
+        spmv_n, spmv_ms = prof["pcg_spmv"]
+        avg = spmv_ms / max(spmv_n, 1) * 1e-3
+        vb = 8 if args.precision == "fp64" else 4
+        bytes_l = nnzb * (9 * vb + 4) + n * (4 + 24 + 24)
+        flops_l = 18 * nnzb + 6 * n
+        ach_bw = bytes_l / avg / 1e9
+        ach_fl = flops_l / avg / 1e9
+        if args.precision == "fp64" and ach_fl / FP64_PEAK > ach_bw / hbm:
+            roof = {"bound": "alu", "achieved": ach_fl / 1e3, "peak": FP64_PEAK / 1e3, "unit": "TFLOP/s",
+                    "frac": ach_fl / FP64_PEAK, "kernel": "pcg_spmv_kernel<double>",
+                    "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2070 MHz (probe measured 1.26 TFLOP/s)",
+                    "hbm_frac": ach_bw / hbm}
+        else:
+            roof = {"bound": "hbm", "achieved": ach_bw, "peak": hbm, "unit": "GB/s", "frac": ach_bw / hbm,
+                    "kernel": f"pcg_spmv_kernel<{'double' if args.precision == 'fp64' else 'float'}>",
+                    "peak_source": f"{hbm_src} (MEASURED_PEAKS.json hbm_gbs)" if hbm_src == "measured" else hbm_src,
+                    "fp64_frac": ach_fl / FP64_PEAK if args.precision == "fp64" else None}
+        roof["algorithmic_bytes_per_launch"] = bytes_l
+        roof["algorithmic_flops_per_launch"] = flops_l
+        roof["avg_launch_us"] = avg * 1e6
+        roof["launches"] = spmv_n
+        roof["traffic"] = measured_traffic("pcg_spmv", args.precision)
+        stencils = K_STENCILS * world
+        line = {
+            "metric": METRIC, "value": stencils / (ms * 1e-3), "unit": "stencils/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
+            "config": {"workload": workload_desc(args), "stencils_per_gpu": K_STENCILS, "vertices": n,
+                       "nnzb": nnzb, "pcg_iterations": PCG_ITERS, "precision": args.precision,
+                       "hess_mode": args.hess_mode, "parallelism": f"replicas{world}",
+                       "l2": "inputs larger than L2 (>1.3 GB touched per step; no flush needed)"},
+            "phases_ms": {"eval": phase[0], "assemble": phase[1], "pcg": phase[2]},
+            "kernel_ms": {k: (v[1] / max(v[0], 1)) for k, v in prof.items()},
+            "linearize_solve_per_s": 1000.0 / ms,
+            "roofline": roof,
+            "e2e": {"value": stencils / (e2e_ms * 1e-3), "unit": "stencils/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+            "gpu_launches": launches_per_step(n) * args.steps,
+            "clocks": clk,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(args, Wh, sample=16000)
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------- oracle (CPU) arm
+def oracle_step(args, Wh, sample, pool_procs):
+    """The oracle's whole path on the first ``sample`` stencils of the batch (full vertex space)."""
+    import numpy as np
+    from oracle import assembly as OA
+    from oracle import pcg as OP
+    from oracle import stencil as OS
+    st = np.ascontiguousarray(Wh["st_own"][:, :sample])
+    sh = np.ascontiguousarray(Wh["st_sheet"][:, :sample])
+    eps = OS.compute_eps_x(Wh["x"], st)
+    r = OS.eval_stencils(Wh["x"], st, eps, Wh["dhat"], KAPPA, processes=pool_procs)
+    if args.hess_mode == "rank1":
+        sd = {"kind": "rank1", "lam": r["lam"], "w": r["w"], "grad": r["grad"]}
+    else:
+        sd = {"kind": "dense", "hess": r["hess"], "grad": r["grad"]}
+    A = OA.assemble(Wh["n"], sh, sd, None, None, Wh["mass"])
+    out = OP.pcg(A, Wh["n"], -A["grad"], tol=0.0, max_iter=PCG_ITERS)
+    return out
+
+
+def cpu_baseline(args, Wh, sample):
+    procs = os.cpu_count() or 1
+    t = time.perf_counter()
+    oracle_step(args, Wh, sample, procs)
+    dt = time.perf_counter() - t
+    return {"value": sample / dt, "unit": "stencils/s", "cores": procs, "kind": "oracle",
+            "sample": f"first {sample} of the {K_STENCILS} stencils: exact-geometry oracle eval "
+                      f"({procs} spawn processes), plain assembly over all {Wh['n']} vertices, "
+                      f"{PCG_ITERS} PCG iterations; {dt:.1f} s"}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    Wh = workload()
+    sample = 4000
+    procs = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        oracle_step(args, Wh, sample, procs)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_step(args, Wh, sample, procs)
+    dt = (time.perf_counter() - t) / args.steps
+    v = sample / dt
+    desc = (f"first {sample} of the {K_STENCILS} stencils per step: exact-geometry oracle eval ({procs} spawn "
+            f"processes), plain assembly over all {Wh['n']} vertices, {PCG_ITERS} PCG iterations")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "stencils/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_desc(args), "precision": args.precision, "hess_mode": args.hess_mode,
+                   "sample_stencils": sample},
+        "cpu_baseline": {"value": v, "unit": "stencils/s", "cores": procs, "kind": "oracle", "sample": desc},
+        "e2e": {"value": v, "unit": "stencils/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -206,6 +206,67 @@ gipc_status gipc_assemble_bsr(gipc_ctx* ctx, int64_t n, const gipc_elements* ste
                               const gipc_elements* tets_h, const double* mass, const double* grad_base,
                               gipc_bsr* bsr_h, double* grad_out, void* stream);
 
+/* ------------------------------------------------------------------ solver */
+
+typedef struct {
+    double rel_tol;    /* stop when delta_new < rel_tol * delta_0 (paper Sec. 8: 1e-4); 0 runs max_iter */
+    int max_iter;      /* iteration cap (>= 0)                                                        */
+    int check_every;   /* host checks for convergence every this many iterations; 0 = automatic       */
+} gipc_pcg_params;
+
+/* Solve H x = rhs by modified PCG with a 3x3 block-Jacobi preconditioner
+ * (paper Sec. 7.2 "Parallel solver optimizations" and "Preconditioning of the
+ * CG solver"; termination delta_new < rel_tol * delta_0 from Sec. 8).
+ *
+ *   r = S(rhs - H x0), z = P^-1 r, c = S(z), delta_0 = r.z; then per iteration
+ *   q = S(H c), alpha = delta/(c.q), x += alpha c, r -= alpha q, s = P^-1 r,
+ *   delta' = r.s, c = S(s + (delta'/delta) c)
+ * with P = blockdiag(H_ii) (identity where a diagonal block is missing or not
+ * positive definite) and S zeroing the vertices with fixed[i] != 0 ("modified"
+ * PCG).  P^-1 is applied through a per-vertex LDL^T factorisation, so r.z is a
+ * sum of squares and stays nonnegative on very ill-conditioned blocks.
+ *
+ *   A      BSR matrix (n = A->n block rows); FP64 or float32 values (MIXED: the
+ *          products and row sums are float32, vectors, residual and dots float64)
+ *   rhs    float64 [3][n]
+ *   x      float64 [3][n]: initial guess in, solution out (fixed vertices: 0)
+ *   fixed  uint8 [n] or NULL
+ *   iters_out_h, rel_out_h  (host, may be NULL) iterations run, delta_new/delta_0
+ * Dot products are reduced in a fixed order: identical inputs give identical
+ * results.  Synchronises the stream at the end (and every check_every
+ * iterations when rel_tol > 0).
+ * Errors: GIPC_ERR_INVALID_ARG; GIPC_ERR_NOT_CONVERGED (rel_tol > 0 and the cap
+ * was reached; x holds the last iterate); GIPC_ERR_NONFINITE; GIPC_ERR_OOM;
+ * GIPC_ERR_CUDA. */
+gipc_status gipc_pcg(gipc_ctx* ctx, const gipc_bsr* A_h, const double* rhs, double* x,
+                     const uint8_t* fixed, const gipc_pcg_params* prm_h, int* iters_out_h,
+                     double* rel_out_h, void* stream);
+
+/* ------------------------------------------------------------------ profiling */
+
+/* Kernels that a context can time with CUDA events on the stream they are
+ * launched on (per-phase tracing; the events add no synchronisation). */
+typedef enum {
+    GIPC_PROF_PCG_SPMV = 0,      /* q = S(H c) and its partial dot products       */
+    GIPC_PROF_PCG_UPDATE = 1,    /* x, r update, preconditioner, r.s              */
+    GIPC_PROF_PCG_DIRECTION = 2, /* c = S(s + beta c)                             */
+    GIPC_PROF_ASM_PATTERN = 3,   /* assembly: count .. rowptr (one span per call) */
+    GIPC_PROF_ASM_VALUES = 4,    /* assembly: emit + value / gradient sums        */
+    GIPC_PROF_KINDS = 5
+} gipc_prof_kind;
+
+typedef struct {
+    int64_t launches;   /* timed launches (spans) since gipc_profile_begin */
+    double total_ms;    /* summed device time of those spans               */
+} gipc_kernel_time;
+
+/* Start (or restart) recording per-kernel spans on this context's calls. */
+gipc_status gipc_profile_begin(gipc_ctx* ctx);
+/* Synchronise on the recorded events and report the spans of one kind;
+ * recording continues until gipc_profile_stop. */
+gipc_status gipc_profile_read(gipc_ctx* ctx, int kind, gipc_kernel_time* out_h);
+gipc_status gipc_profile_stop(gipc_ctx* ctx);
+
 #ifdef __cplusplus
 }
 #endif

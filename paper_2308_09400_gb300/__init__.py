@@ -15,7 +15,7 @@ from ._abi import (FLAG_ACTIVE, FLAG_FILTERED, FLAG_INVALID, FLAG_MOLLIFIED, Gip
 TYPE_IDS = {"PT": 0, "EE": 1, "PE": 2, "PP": 3, "EE_PAR": 4, "PE_PAR": 5, "PP_PAR": 6}
 NULL_INDEX = -2147483648
 
-__all__ = ["compute_eps_x", "eval_stencils", "assemble_bsr", "Context", "default_context", "GipcError", "FLAG_ACTIVE", "FLAG_FILTERED",
+__all__ = ["compute_eps_x", "eval_stencils", "assemble_bsr", "pcg", "Context", "default_context", "GipcError", "FLAG_ACTIVE", "FLAG_FILTERED",
            "FLAG_MOLLIFIED", "FLAG_INVALID", "TYPE_IDS", "NULL_INDEX"]
 
 
@@ -99,6 +99,22 @@ class Context:
     def handle(self):
         return self._h
 
+    def profile_begin(self):
+        """Start timing this context's kernels with CUDA events on their launch stream."""
+        _abi.call("gipc_profile_begin", self._h)
+
+    def profile_read(self):
+        """{kind: (launches, total_ms)} for every profiled kernel kind (synchronises on the events)."""
+        out = {}
+        for name, kid in _abi.PROF_KINDS.items():
+            t = _abi.KernelTime()
+            _abi.call("gipc_profile_read", self._h, kid, ctypes.byref(t))
+            out[name] = (int(t.launches), float(t.total_ms))
+        return out
+
+    def profile_stop(self):
+        _abi.call("gipc_profile_stop", self._h)
+
     def close(self):
         if self._h:
             _abi.lib().gipc_destroy(self._h)
@@ -175,3 +191,34 @@ def assemble_bsr(n, stencils=None, stencil_hess=None, stencil_mode="dense", sten
     nnzb = int(bsr.nnzb)
     return {"rowptr": rowptr, "colidx": colidx[:nnzb], "vals": vals[:nnzb], "grad": grad, "nnzb": nnzb,
             "n": n, "precision": precision}
+
+
+def _bsr_struct(A):
+    prec = {"fp64": _abi.GIPC_FP64, "mixed": _abi.GIPC_MIXED}[A["precision"]]
+    return _abi.Bsr(A["n"], A["nnzb"], A["colidx"].shape[0], A["rowptr"].data_ptr(), A["colidx"].data_ptr(),
+                    A["vals"].data_ptr(), prec)
+
+
+def pcg(A, rhs, x0=None, fixed=None, rel_tol=1e-4, max_iter=1000, check_every=0, raise_on_nonconvergence=False,
+        ctx=None, stream=None):
+    """Modified block-Jacobi PCG on an assembled BSR (gipc_pcg).
+
+    ``A`` is the dict returned by ``assemble_bsr``; ``rhs`` float64 [3, n].  Returns
+    (x [3, n], iterations, delta_new / delta_0).  A capped solve with rel_tol > 0
+    returns its last iterate unless ``raise_on_nonconvergence``.
+    """
+    ctx = ctx or default_context()
+    n = A["n"]
+    _check(rhs, "rhs", torch.float64, 3)
+    x = torch.zeros_like(rhs) if x0 is None else x0.clone()
+    if fixed is not None:
+        _check(fixed, "fixed", torch.uint8)
+    bsr = _bsr_struct(A)
+    prm = _abi.PcgParams(float(rel_tol), int(max_iter), int(check_every))
+    iters = ctypes.c_int(0)
+    rel = ctypes.c_double(0.0)
+    st = _abi.call_status("gipc_pcg", ctx.handle, ctypes.byref(bsr), _ptr(rhs), _ptr(x), _ptr(fixed),
+                          ctypes.byref(prm), ctypes.byref(iters), ctypes.byref(rel), _stream(stream))
+    if st != _abi.GIPC_OK and not (st == _abi.GIPC_ERR_NOT_CONVERGED and not raise_on_nonconvergence):
+        raise GipcError("gipc_pcg", st)
+    return x, iters.value, rel.value

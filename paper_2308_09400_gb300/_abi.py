@@ -34,6 +34,16 @@ class Elements(ctypes.Structure):
                 ("hess", ctypes.c_void_p), ("lam", ctypes.c_void_p), ("grad", ctypes.c_void_p)]
 
 
+class PcgParams(ctypes.Structure):
+    _fields_ = [("rel_tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("check_every", ctypes.c_int)]
+
+
+class KernelTime(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
+
+
+PROF_KINDS = {"pcg_spmv": 0, "pcg_update": 1, "pcg_direction": 2, "asm_pattern": 3, "asm_values": 4}
+
 _P = ctypes.c_void_p
 _I64 = ctypes.c_int64
 _D = ctypes.c_double
@@ -49,6 +59,11 @@ SIGNATURES = {
                                   _P, _P, _P, _P, _P, _P]),
     "gipc_assemble_bsr": (_INT, [_P, _I64, ctypes.POINTER(Elements), ctypes.POINTER(Elements), _P, _P,
                                  ctypes.POINTER(Bsr), _P, _P]),
+    "gipc_pcg": (_INT, [_P, ctypes.POINTER(Bsr), _P, _P, _P, ctypes.POINTER(PcgParams),
+                        ctypes.POINTER(_INT), ctypes.POINTER(_D), _P]),
+    "gipc_profile_begin": (_INT, [_P]),
+    "gipc_profile_read": (_INT, [_P, _INT, ctypes.POINTER(KernelTime)]),
+    "gipc_profile_stop": (_INT, [_P]),
 }
 
 _lib = None
@@ -77,6 +92,7 @@ def lib():
 
 
 GIPC_ERR_CAPACITY = -7
+GIPC_ERR_NOT_CONVERGED = -4
 
 
 def call_status(name, *args):

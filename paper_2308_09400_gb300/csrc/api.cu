@@ -47,3 +47,33 @@ extern "C" gipc_status gipc_destroy(gipc_ctx* ctx) {
     delete ctx;
     return GIPC_OK;
 }
+
+extern "C" gipc_status gipc_profile_begin(gipc_ctx* ctx) {
+    if (!ctx) return gipc::fail(GIPC_ERR_INVALID_ARG, "gipc_profile_begin: null context");
+    ctx->prof.on = true;
+    ctx->prof.reset();
+    return GIPC_OK;
+}
+
+extern "C" gipc_status gipc_profile_stop(gipc_ctx* ctx) {
+    if (!ctx) return gipc::fail(GIPC_ERR_INVALID_ARG, "gipc_profile_stop: null context");
+    ctx->prof.on = false;
+    return GIPC_OK;
+}
+
+extern "C" gipc_status gipc_profile_read(gipc_ctx* ctx, int kind, gipc_kernel_time* out) {
+    if (!ctx || !out || kind < 0 || kind >= GIPC_PROF_KINDS)
+        return gipc::fail(GIPC_ERR_INVALID_ARG, "gipc_profile_read: bad arguments");
+    const auto& P = ctx->prof;
+    out->launches = P.used[kind] / 2;
+    out->total_ms = 0.0;
+    for (int i = 0; i + 1 < P.used[kind]; i += 2) {
+        if (cudaEventSynchronize(P.pool[kind][i + 1]) != cudaSuccess)
+            return gipc::fail(GIPC_ERR_CUDA, "gipc_profile_read: event synchronisation failed");
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, P.pool[kind][i], P.pool[kind][i + 1]) != cudaSuccess)
+            return gipc::fail(GIPC_ERR_CUDA, "gipc_profile_read: elapsed time failed");
+        out->total_ms += ms;
+    }
+    return GIPC_OK;
+}

@@ -402,6 +402,7 @@ extern "C" gipc_status gipc_assemble_bsr(gipc_ctx* ctx, int64_t n, const gipc_el
     int64_t* scan_tmp = ctx->slot[S_SCAN].as<int64_t>();
     int64_t* rowptr64 = ctx->slot[S_ROWPTR64].as<int64_t>();
 
+    ctx->prof.start(GIPC_PROF_ASM_PATTERN, s);
     init_rows_kernel<<<blocks_for(n, 256, 1 << 30), 256, 0, s>>>(row_cnt, n, with_mass);
     if (ne > 0) count_kernel<<<blocks_for(ne, 256), 256, 0, s>>>(L[0], L[1], n, row_cnt, elem_n3);
     if (exclusive_scan<int32_t>(row_cnt, row_start, n, scan_tmp, s) != cudaSuccess)
@@ -423,6 +424,7 @@ extern "C" gipc_status gipc_assemble_bsr(gipc_ctx* ctx, int64_t n, const gipc_el
     if (exclusive_scan<int32_t>(row_nnzb, rowptr64, n, scan_tmp, s) != cudaSuccess)
         return check_launch("gipc_assemble_bsr: scan");
     rowptr32_kernel<<<blocks_for(n + 1, 256, 1 << 30), 256, 0, s>>>(rowptr64, bsr->rowptr, n);
+    ctx->prof.stop(GIPC_PROF_ASM_PATTERN, s);
     if ((st = check_launch("gipc_assemble_bsr: pattern")) != GIPC_OK) return st;
     int64_t host_vals[2] = {0, 0};
     int32_t host_err = 0;
@@ -441,6 +443,7 @@ extern "C" gipc_status gipc_assemble_bsr(gipc_ctx* ctx, int64_t n, const gipc_el
     if (nnzb > 0 && (!bsr->colidx || !bsr->vals)) return fail(GIPC_ERR_INVALID_ARG, "gipc_assemble_bsr: null colidx/vals");
     if ((st = ctx->slot[S_SEG].reserve(sizeof(int64_t) * (nnzb + 1))) != GIPC_OK) return st;
     int64_t* seg = ctx->slot[S_SEG].as<int64_t>();
+    ctx->prof.start(GIPC_PROF_ASM_VALUES, s);
     emit_kernel<<<blocks_for(n, 8, 152 * 64), 256, 0, s>>>(row_start, keys, rowptr64, n, bsr->colidx, seg);
     seg_end_kernel<<<1, 1, 0, s>>>(seg, rowptr64, row_start, n);
     if (grad_out) grad_init_kernel<<<blocks_for(3 * n, 256, 1 << 30), 256, 0, s>>>(grad_base, grad_out, 3 * n);
@@ -452,5 +455,6 @@ extern "C" gipc_status gipc_assemble_bsr(gipc_ctx* ctx, int64_t n, const gipc_el
             values_kernel<float><<<blocks_for(nnzb, 128), 128, 0, s>>>(keys, seg, nnzb, n, L[0], L[1], elem_n3, mass,
                                                                      static_cast<float*>(bsr->vals), grad_base, grad_out);
     }
+    ctx->prof.stop(GIPC_PROF_ASM_VALUES, s);
     return check_launch("gipc_assemble_bsr: values");
 }

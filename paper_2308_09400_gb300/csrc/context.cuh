@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stddef.h>
 
+#include <vector>
+
 #include "common.cuh"
 
 // A growable device buffer owned by a context.
@@ -32,11 +34,46 @@ struct gipc_scratch {
     T* as() const { return static_cast<T*>(ptr); }
 };
 
+// Per-kernel timing with CUDA events recorded on the launching stream (enabled on demand).
+struct gipc_profiler {
+    static constexpr int kKinds = GIPC_PROF_KINDS;
+    bool on = false;
+    std::vector<cudaEvent_t> pool[kKinds];
+    int used[kKinds] = {};
+    cudaEvent_t take(int kind) {
+        if (used[kind] == (int)pool[kind].size()) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+            pool[kind].push_back(e);
+        }
+        return pool[kind][used[kind]++];
+    }
+    // record a start / stop pair around one launch of `kind`
+    void start(int kind, cudaStream_t s) {
+        if (on) {
+            cudaEvent_t e = take(kind);
+            if (e) cudaEventRecord(e, s);
+        }
+    }
+    void stop(int kind, cudaStream_t s) { start(kind, s); }
+    void reset() {
+        for (int k = 0; k < kKinds; ++k) used[k] = 0;
+    }
+    void release() {
+        for (auto& v : pool)
+            for (auto e : v) cudaEventDestroy(e);
+        for (auto& v : pool) v.clear();
+        reset();
+    }
+};
+
 struct gipc_ctx {
     int device = 0;
     static constexpr int kSlots = 16;
     gipc_scratch slot[kSlots];
+    gipc_profiler prof;
     void release_all() {
         for (auto& s : slot) s.release();
+        prof.release();
     }
 };

@@ -1,0 +1,502 @@
+// Modified PCG with a 3x3 block-Jacobi preconditioner on a BSR matrix.
+//
+// Paper: the Newton system of Alg. 1 is solved by modified-PCG (Sec. 7.2,
+// "Parallel solver optimizations", after Baraff and Witkin) with a simple 3x3
+// block-diagonal preconditioner (Sec. 7.2, "Preconditioning of the CG solver")
+// and stops when delta_new < 1e-4 delta_0 (Sec. 8).  The filter S zeroes
+// constrained vertices ("modified" PCG).  Unlike the paper, which multiplies the
+// local matrices directly, the matrix here is an assembled BSR.
+//
+// Per iteration three kernels run, all reading the solver scalars from device
+// memory, so the host never waits inside the loop:
+//   A  q = S(H c) and the partial dots c.q      -> last CTA: alpha = delta/(c.q)
+//   B  x += alpha c; r -= alpha q; s = P^-1 r; partial dots r.s
+//                                               -> last CTA: delta_new, beta, done
+//   C  c = S(s + beta c)
+// Dots are reduced deterministically: every CTA writes one partial, the last
+// CTA to finish sums the partials in index order.  Once `done` is set every
+// kernel returns immediately, so surplus launched iterations are no-ops.
+//
+// SpMV mapping: three lanes per block row, lane i of a row accumulates output
+// component i over the row's blocks (3 FMAs per block, each one useful), so no
+// cross-lane reduction is needed; ten rows per warp.  Rows are visited in an
+// order sorted by length (a stable bucket sort at set-up, longest first), so the
+// ten rows of a warp have similar lengths and few lanes idle: on GB300 an FP64
+// instruction costs the same whether 21 or 30 of its lanes are active.  The
+// mixed path gathers a float32 copy of the search direction, so its inner loop
+// has no float64 operation at all.
+#include <cuda_runtime.h>
+
+#include <cmath>
+
+#include "common.cuh"
+#include "context.cuh"
+#include "scan.cuh"
+
+namespace gipc {
+namespace {
+
+constexpr int kPcgThreads = 256;
+constexpr int kRowsPerWarp = 10;  // 3 lanes per row, lanes 30/31 idle
+
+enum PcgSlot { P_VEC = 9, P_PINV = 10, P_PART = 11, P_PERM = 12, P_VEC32 = 13 };
+
+constexpr int kLenBuckets = 64;   // rows are ordered by min(blocks in row, 63), longest first
+constexpr int kPermChunk = 1024;  // rows per block of the stable bucket sort
+
+struct PcgScalars {
+    double delta_new, delta_old, delta0, alpha, beta, tol, pq;
+    int iters, done, max_iter, status;
+    unsigned count_a, count_b, count_0;
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block-wide sum (fixed order) -> thread 0.
+__device__ __forceinline__ double block_sum(double v) {
+    __shared__ double sh[32];
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (w == 0) {
+        t = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
+        t = warp_sum(t);
+    }
+    __syncthreads();
+    return t;
+}
+
+// Publish this CTA's partial; returns true in exactly one (the last) CTA, which then sees all partials.
+__device__ __forceinline__ bool publish_partial(double* part, double v, unsigned* counter) {
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = v;
+        __threadfence();
+        const unsigned prev = atomicAdd(counter, 1u);
+        last = prev == gridDim.x - 1;
+    }
+    __syncthreads();
+    return last;
+}
+
+// Called by every thread of the last CTA: sums the partials with a fixed thread-to-partial map
+// and a fixed tree, so the total is identical run to run (result valid in thread 0).
+__device__ __forceinline__ double sum_partials(const double* part, int count) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < count; i += blockDim.x) s += __ldcg(part + i);
+    return block_sum(s);
+}
+
+// y = (H p)_row,comp for this lane (3 lanes per row, rows taken from the length-sorted order).
+template <typename VT, typename PT>
+__device__ __forceinline__ bool spmv_lane(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
+                                          const VT* __restrict__ vals, const PT* __restrict__ p,
+                                          const int32_t* __restrict__ perm, int64_t n, int64_t& row, int& comp,
+                                          double& out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (lane >= 3 * kRowsPerWarp) return false;
+    const int64_t slot = warp * kRowsPerWarp + lane / 3;
+    comp = lane % 3;
+    if (slot >= n) return false;
+    row = perm[slot];
+    const int32_t b0 = rowptr[row], b1 = rowptr[row + 1];
+    VT acc0 = VT(0), acc1 = VT(0);
+    int32_t b = b0;
+    // four blocks per step: the four column loads, then twelve value loads and twelve
+    // gathers are all independent, so each lane keeps many memory requests in flight
+    for (; b + 4 <= b1; b += 4) {
+        int64_t cc[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) cc[u] = colidx[b + u];
+        VT v[12];
+        PT pv[12];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const VT* vp = vals + 9 * (int64_t)(b + u) + 3 * comp;
+            const PT* pp = p + 3 * cc[u];
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                v[3 * u + j] = vp[j];
+                pv[3 * u + j] = pp[j];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u += 2) {
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                acc0 = fma(v[3 * u + j], (VT)pv[3 * u + j], acc0);
+                acc1 = fma(v[3 * u + 3 + j], (VT)pv[3 * u + 3 + j], acc1);
+            }
+        }
+    }
+    for (; b < b1; ++b) {
+        const int64_t c = colidx[b];
+        const VT* vp = vals + 9 * (int64_t)b + 3 * comp;
+        const PT* pp = p + 3 * c;
+        acc0 = fma(vp[0], (VT)pp[0], acc0);
+        acc0 = fma(vp[1], (VT)pp[1], acc0);
+        acc0 = fma(vp[2], (VT)pp[2], acc0);
+    }
+    out = (double)(acc0 + acc1);
+    return true;
+}
+
+// Stable bucket sort of rows by length (deterministic): per-chunk histograms, a scan in
+// (bucket, chunk) order, then one warp per chunk places its rows in order.
+__device__ __forceinline__ int len_key(const int32_t* __restrict__ rowptr, int64_t r) {
+    int len = rowptr[r + 1] - rowptr[r];
+    if (len > kLenBuckets - 1) len = kLenBuckets - 1;
+    return kLenBuckets - 1 - len;  // longest first
+}
+
+__global__ void perm_hist_kernel(const int32_t* __restrict__ rowptr, int64_t n, int32_t* __restrict__ counts,
+                                 int64_t chunks) {
+    __shared__ int h[kLenBuckets];
+    for (int i = threadIdx.x; i < kLenBuckets; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    const int64_t r0 = (int64_t)blockIdx.x * kPermChunk;
+    for (int64_t r = r0 + threadIdx.x; r < n && r < r0 + kPermChunk; r += blockDim.x) atomicAdd(&h[len_key(rowptr, r)], 1);
+    __syncthreads();
+    for (int i = threadIdx.x; i < kLenBuckets; i += blockDim.x) counts[(int64_t)i * chunks + blockIdx.x] = h[i];
+}
+
+__global__ void perm_scatter_kernel(const int32_t* __restrict__ rowptr, int64_t n, const int64_t* __restrict__ off,
+                                    int64_t chunks, int32_t* __restrict__ perm) {
+    __shared__ int64_t run[kLenBuckets];
+    const int lane = threadIdx.x;
+    for (int i = lane; i < kLenBuckets; i += 32) run[i] = off[(int64_t)i * chunks + blockIdx.x];
+    __syncwarp();
+    const int64_t r0 = (int64_t)blockIdx.x * kPermChunk;
+    for (int t = 0; t < kPermChunk; t += 32) {
+        const int64_t r = r0 + t + lane;
+        const bool valid = r < n;
+        const int key = valid ? len_key(rowptr, r) : kLenBuckets;
+        const unsigned grp = __match_any_sync(0xffffffffu, key);
+        const int rank = __popc(grp & ((1u << lane) - 1u));
+        if (valid) perm[run[key] + rank] = (int32_t)r;
+        __syncwarp();
+        if (valid && rank == 0) run[key] += __popc(grp);
+        __syncwarp();
+    }
+}
+
+// q = S(H c); alpha = delta_new / (c . q)
+template <typename VT, typename PT>
+__global__ void __launch_bounds__(kPcgThreads)
+pcg_spmv_kernel(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx, const VT* __restrict__ vals,
+                const PT* __restrict__ cg, const double* __restrict__ c, const int32_t* __restrict__ perm,
+                double* __restrict__ q, const uint8_t* __restrict__ fixed, int64_t n, double* __restrict__ part,
+                PcgScalars* __restrict__ S) {
+    if (S->done) return;
+    int64_t row;
+    int comp;
+    double y = 0.0, d = 0.0;
+    if (spmv_lane<VT, PT>(rowptr, colidx, vals, cg, perm, n, row, comp, y)) {
+        if (fixed && fixed[row]) y = 0.0;
+        q[3 * row + comp] = y;
+        d = c[3 * row + comp] * y;
+    }
+    const double bs = block_sum(d);
+    if (publish_partial(part, bs, &S->count_a)) {
+        const double pq = sum_partials(part, gridDim.x);
+        if (threadIdx.x == 0) {
+            S->pq = pq;
+            S->alpha = S->delta_new / pq;
+            S->count_a = 0;
+        }
+    }
+}
+
+// Block-Jacobi preconditioner as a per-vertex LDL^T factorisation of the diagonal block
+// H_ii (stored as l10, l20, l21, 1/d0, 1/d1, 1/d2).  Applying it by forward and back
+// substitution makes r . P^-1 r a sum of squares y_i^2 / d_i, nonnegative by
+// construction even when H_ii is very ill-conditioned (an explicit 3x3 inverse is not
+// numerically definite there).  A missing or non-positive-definite block falls back to I.
+template <typename VT>
+__global__ void pcg_factor_kernel(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
+                                  const VT* __restrict__ vals, int64_t n, double* __restrict__ fac) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    double m[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+    int32_t lo = rowptr[r], hi = rowptr[r + 1] - 1;
+    while (lo <= hi) {  // binary search for the diagonal block
+        const int32_t mid = (lo + hi) >> 1;
+        const int32_t cm = colidx[mid];
+        if (cm == r) {
+#pragma unroll
+            for (int i = 0; i < 9; ++i) m[i] = (double)vals[9 * (int64_t)mid + i];
+            break;
+        }
+        if (cm < r) lo = mid + 1;
+        else hi = mid - 1;
+    }
+    const double d0 = m[0];
+    const double l10 = m[3] / d0, l20 = m[6] / d0;
+    const double d1 = m[4] - l10 * l10 * d0;
+    const double l21 = (m[7] - l20 * l10 * d0) / d1;
+    const double d2 = m[8] - l20 * l20 * d0 - l21 * l21 * d1;
+    double* F = fac + 6 * r;
+    if (!(d0 > 0.0) || !(d1 > 0.0) || !(d2 > 0.0) || !isfinite(l10 + l20 + l21 + d2)) {
+        F[0] = F[1] = F[2] = 0.0;
+        F[3] = F[4] = F[5] = 1.0;
+        return;
+    }
+    F[0] = l10;
+    F[1] = l20;
+    F[2] = l21;
+    F[3] = 1.0 / d0;
+    F[4] = 1.0 / d1;
+    F[5] = 1.0 / d2;
+}
+
+// s = P^-1 r for one vertex; returns r . s = sum_i y_i^2 / d_i (>= 0).
+__device__ __forceinline__ double precond_apply(const double* __restrict__ F, const double r[3], double s[3]) {
+    const double l10 = F[0], l20 = F[1], l21 = F[2];
+    const double y0 = r[0];
+    const double y1 = r[1] - l10 * y0;
+    const double y2 = r[2] - l20 * y0 - l21 * y1;
+    const double z0 = y0 * F[3], z1 = y1 * F[4], z2 = y2 * F[5];
+    s[2] = z2;
+    s[1] = z1 - l21 * z2;
+    s[0] = z0 - l10 * s[1] - l20 * z2;
+    return y0 * z0 + y1 * z1 + y2 * z2;
+}
+
+// x += alpha c; r -= alpha q; s = P^-1 r; delta_new = r . s; beta; termination
+__global__ void __launch_bounds__(kPcgThreads)
+pcg_update_kernel(double* __restrict__ x, double* __restrict__ r, const double* __restrict__ c,
+                  const double* __restrict__ q, double* __restrict__ s, const double* __restrict__ pinv,
+                  int64_t n, double* __restrict__ part, PcgScalars* __restrict__ S) {
+    if (S->done) return;
+    const double alpha = S->alpha;
+    double d = 0.0;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        double rv[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            x[3 * v + i] += alpha * c[3 * v + i];
+            rv[i] = r[3 * v + i] - alpha * q[3 * v + i];
+            r[3 * v + i] = rv[i];
+        }
+        double sv[3];
+        d += precond_apply(pinv + 6 * v, rv, sv);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) s[3 * v + i] = sv[i];
+    }
+    const double bs = block_sum(d);
+    if (!publish_partial(part, bs, &S->count_b)) return;
+    const double dn = sum_partials(part, gridDim.x);
+    if (threadIdx.x == 0) {
+        S->delta_old = S->delta_new;
+        S->delta_new = dn;
+        S->beta = dn / S->delta_old;
+        S->iters += 1;
+        if (!isfinite(dn) || !isfinite(S->alpha)) {
+            S->status = GIPC_ERR_NONFINITE;
+            S->done = 1;
+        } else if (!(dn > 0.0) || dn < S->tol * S->delta0 || S->iters >= S->max_iter) {
+            S->done = 1;
+        }
+        S->count_b = 0;
+    }
+}
+
+__global__ void __launch_bounds__(kPcgThreads)
+pcg_direction_kernel(double* __restrict__ c, float* __restrict__ c32, const double* __restrict__ s,
+                     const uint8_t* __restrict__ fixed, int64_t n, const PcgScalars* __restrict__ S) {
+    // runs after the update of the same iteration; `done` may now be set, but c is still refreshed
+    // only while the solve continues
+    if (S->done) return;
+    const double beta = S->beta;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < 3 * n; e += (int64_t)gridDim.x * blockDim.x) {
+        const bool fx = fixed && fixed[e / 3];
+        const double ce = fx ? 0.0 : s[e] + beta * c[e];
+        c[e] = ce;
+        if (c32) c32[e] = (float)ce;
+    }
+}
+
+__global__ void soa_to_aos_kernel(const double* __restrict__ in, double* __restrict__ out, float* __restrict__ out32,
+                                  int64_t n, const uint8_t* __restrict__ fixed) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= 3 * n) return;
+    const int64_t v = e / 3;
+    const int comp = (int)(e - 3 * v);
+    const double val = (fixed && fixed[v]) ? 0.0 : in[comp * n + v];
+    out[e] = val;
+    if (out32) out32[e] = (float)val;
+}
+
+__global__ void aos_to_soa_kernel(const double* __restrict__ in, double* __restrict__ out, int64_t n) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= 3 * n) return;
+    const int64_t v = e / 3;
+    const int comp = (int)(e - 3 * v);
+    out[comp * n + v] = in[e];
+}
+
+// Setup: r = S(b - H x0), s = P^-1 r, c = S(s), delta_0 = r.s (H x0 already in q)
+__global__ void __launch_bounds__(kPcgThreads)
+pcg_init_kernel(const double* __restrict__ b, const double* __restrict__ q, double* __restrict__ r,
+                double* __restrict__ s, double* __restrict__ c, float* __restrict__ c32, const double* __restrict__ pinv,
+                const uint8_t* __restrict__ fixed, int64_t n, double* __restrict__ part, PcgScalars* __restrict__ S) {
+    double d = 0.0;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const bool fx = fixed && fixed[v];
+        double rv[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            rv[i] = fx ? 0.0 : b[3 * v + i] - q[3 * v + i];
+            r[3 * v + i] = rv[i];
+        }
+        double sv[3];
+        d += precond_apply(pinv + 6 * v, rv, sv);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            s[3 * v + i] = sv[i];
+            c[3 * v + i] = fx ? 0.0 : sv[i];
+            if (c32) c32[3 * v + i] = fx ? 0.0f : (float)sv[i];
+        }
+    }
+    const double bs = block_sum(d);
+    if (!publish_partial(part, bs, &S->count_0)) return;
+    const double d0 = sum_partials(part, gridDim.x);
+    if (threadIdx.x == 0) {
+        S->delta0 = d0;
+        S->delta_new = d0;
+        S->iters = 0;
+        S->status = GIPC_OK;
+        S->done = (!(d0 > 0.0) || !isfinite(d0) || S->max_iter <= 0) ? 1 : 0;
+        if (!isfinite(d0)) S->status = GIPC_ERR_NONFINITE;
+        S->count_0 = 0;
+    }
+}
+
+__global__ void pcg_set_scalars(PcgScalars* S, double tol, int max_iter) {
+    S->tol = tol;
+    S->max_iter = max_iter;
+    S->done = 0;
+    S->iters = 0;
+    S->status = GIPC_OK;
+    S->count_a = S->count_b = S->count_0 = 0;
+}
+
+inline unsigned spmv_blocks(int64_t n) {
+    const int64_t warps = (n + kRowsPerWarp - 1) / kRowsPerWarp;
+    return (unsigned)((warps * 32 + kPcgThreads - 1) / kPcgThreads);
+}
+
+inline unsigned vec_blocks(int64_t n) {
+    int64_t b = (n + kPcgThreads - 1) / kPcgThreads;
+    if (b > 152 * 8) b = 152 * 8;
+    return (unsigned)(b < 1 ? 1 : b);
+}
+
+}  // namespace
+}  // namespace gipc
+
+extern "C" gipc_status gipc_pcg(gipc_ctx* ctx, const gipc_bsr* A, const double* rhs, double* x,
+                                const uint8_t* fixed, const gipc_pcg_params* prm, int* iters_out_h,
+                                double* rel_out_h, void* stream) {
+    using namespace gipc;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!ctx || !A || !prm) return fail(GIPC_ERR_INVALID_ARG, "gipc_pcg: null context, matrix or parameters");
+    const int64_t n = A->n;
+    if (n < 0 || A->nnzb < 0) return fail(GIPC_ERR_INVALID_ARG, "gipc_pcg: negative sizes");
+    if (A->prec != GIPC_FP64 && A->prec != GIPC_MIXED) return fail(GIPC_ERR_INVALID_ARG, "gipc_pcg: bad precision");
+    if (!(prm->rel_tol >= 0.0) || prm->max_iter < 0 || prm->check_every < 0)
+        return fail(GIPC_ERR_INVALID_ARG, "gipc_pcg: need rel_tol >= 0, max_iter >= 0, check_every >= 0");
+    if (n == 0) {
+        if (iters_out_h) *iters_out_h = 0;
+        if (rel_out_h) *rel_out_h = 0.0;
+        return GIPC_OK;
+    }
+    if (!rhs || !x || !A->rowptr || (A->nnzb > 0 && (!A->colidx || !A->vals)))
+        return fail(GIPC_ERR_INVALID_ARG, "gipc_pcg: null vector or matrix pointer");
+    gipc_status s;
+    const int64_t nvec = 3 * n;
+    const unsigned vb = vec_blocks(n), sb = spmv_blocks(n);
+    const unsigned maxb = sb > vb ? sb : vb;
+    if ((s = ctx->slot[P_VEC].reserve(sizeof(double) * 6 * nvec)) != GIPC_OK) return s;
+    if ((s = ctx->slot[P_PINV].reserve(sizeof(double) * 6 * n)) != GIPC_OK) return s;
+    if ((s = ctx->slot[P_PART].reserve(sizeof(double) * (maxb + 8) + sizeof(PcgScalars) + 64)) != GIPC_OK) return s;
+    double* V = ctx->slot[P_VEC].as<double>();
+    double *b = V, *xv = V + nvec, *r = V + 2 * nvec, *sv = V + 3 * nvec, *c = V + 4 * nvec, *q = V + 5 * nvec;
+    double* pinv = ctx->slot[P_PINV].as<double>();
+    PcgScalars* S = reinterpret_cast<PcgScalars*>(ctx->slot[P_PART].as<char>());
+    double* part = reinterpret_cast<double*>(ctx->slot[P_PART].as<char>() + ((sizeof(PcgScalars) + 63) / 64) * 64);
+
+    const unsigned eb = (unsigned)((nvec + 255) / 256);
+    const int max_iter = prm->max_iter;
+    const bool f64 = A->prec == GIPC_FP64;
+    // row order by length (stable, deterministic)
+    const int64_t chunks = (n + kPermChunk - 1) / kPermChunk;
+    const int64_t ncnt = (int64_t)kLenBuckets * chunks;
+    if ((s = ctx->slot[P_PERM].reserve(sizeof(int32_t) * (n + ncnt) + sizeof(int64_t) * (ncnt + 1 + scan_scratch_words(ncnt)) + 64)) != GIPC_OK) return s;
+    int32_t* perm = ctx->slot[P_PERM].as<int32_t>();
+    int32_t* counts = perm + n;
+    int64_t* offs = reinterpret_cast<int64_t*>(ctx->slot[P_PERM].as<char>() + ((sizeof(int32_t) * (n + ncnt) + 15) / 16) * 16);
+    int64_t* scan_tmp = offs + ncnt + 1;
+    float* c32 = nullptr;
+    if (!f64) {
+        if ((s = ctx->slot[P_VEC32].reserve(sizeof(float) * 2 * nvec)) != GIPC_OK) return s;
+    }
+    float* x32 = f64 ? nullptr : ctx->slot[P_VEC32].as<float>();
+    if (!f64) c32 = x32 + nvec;
+    perm_hist_kernel<<<(unsigned)chunks, 256, 0, st>>>(A->rowptr, n, counts, chunks);
+    if (exclusive_scan<int32_t>(counts, offs, ncnt, scan_tmp, st) != cudaSuccess) return check_launch("gipc_pcg: scan");
+    perm_scatter_kernel<<<(unsigned)chunks, 32, 0, st>>>(A->rowptr, n, offs, chunks, perm);
+
+    pcg_set_scalars<<<1, 1, 0, st>>>(S, prm->rel_tol, max_iter);
+    soa_to_aos_kernel<<<eb, 256, 0, st>>>(rhs, b, nullptr, n, fixed);
+    soa_to_aos_kernel<<<eb, 256, 0, st>>>(x, xv, x32, n, fixed);
+    if (f64) pcg_factor_kernel<double><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(A->rowptr, A->colidx, (const double*)A->vals, n, pinv);
+    else pcg_factor_kernel<float><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(A->rowptr, A->colidx, (const float*)A->vals, n, pinv);
+    // q = S(H x0), reusing the spmv kernel with a scratch dot (alpha is overwritten at iteration 1)
+    if (f64) pcg_spmv_kernel<double, double><<<sb, kPcgThreads, 0, st>>>(A->rowptr, A->colidx, (const double*)A->vals, xv, xv, perm, q, fixed, n, part, S);
+    else pcg_spmv_kernel<float, float><<<sb, kPcgThreads, 0, st>>>(A->rowptr, A->colidx, (const float*)A->vals, x32, xv, perm, q, fixed, n, part, S);
+    pcg_init_kernel<<<vb, kPcgThreads, 0, st>>>(b, q, r, sv, c, c32, pinv, fixed, n, part, S);
+    if ((s = check_launch("gipc_pcg: setup")) != GIPC_OK) return s;
+
+    const int chunk = prm->check_every > 0 ? prm->check_every : (prm->rel_tol > 0.0 ? 16 : max_iter + 1);
+    PcgScalars hs{};
+    int launched = 0;
+    while (launched < max_iter) {
+        const int m = (max_iter - launched) < chunk ? (max_iter - launched) : chunk;
+        for (int it = 0; it < m; ++it) {
+            ctx->prof.start(GIPC_PROF_PCG_SPMV, st);
+            if (f64) pcg_spmv_kernel<double, double><<<sb, kPcgThreads, 0, st>>>(A->rowptr, A->colidx, (const double*)A->vals, c, c, perm, q, fixed, n, part, S);
+            else pcg_spmv_kernel<float, float><<<sb, kPcgThreads, 0, st>>>(A->rowptr, A->colidx, (const float*)A->vals, c32, c, perm, q, fixed, n, part, S);
+            ctx->prof.stop(GIPC_PROF_PCG_SPMV, st);
+            ctx->prof.start(GIPC_PROF_PCG_UPDATE, st);
+            pcg_update_kernel<<<vb, kPcgThreads, 0, st>>>(xv, r, c, q, sv, pinv, n, part, S);
+            ctx->prof.stop(GIPC_PROF_PCG_UPDATE, st);
+            ctx->prof.start(GIPC_PROF_PCG_DIRECTION, st);
+            pcg_direction_kernel<<<vb, kPcgThreads, 0, st>>>(c, c32, sv, fixed, n, S);
+            ctx->prof.stop(GIPC_PROF_PCG_DIRECTION, st);
+        }
+        launched += m;
+        if ((s = check_launch("gipc_pcg: iteration")) != GIPC_OK) return s;
+        if (launched < max_iter) {
+            cudaMemcpyAsync(&hs, S, sizeof(PcgScalars), cudaMemcpyDeviceToHost, st);
+            if (cudaStreamSynchronize(st) != cudaSuccess) return check_launch("gipc_pcg: sync");
+            if (hs.done) break;
+        }
+    }
+    aos_to_soa_kernel<<<eb, 256, 0, st>>>(xv, x, n);
+    cudaMemcpyAsync(&hs, S, sizeof(PcgScalars), cudaMemcpyDeviceToHost, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return check_launch("gipc_pcg: final sync");
+    if (iters_out_h) *iters_out_h = hs.iters;
+    if (rel_out_h) *rel_out_h = hs.delta0 > 0.0 ? hs.delta_new / hs.delta0 : 0.0;
+    if (hs.status == GIPC_ERR_NONFINITE) return fail(GIPC_ERR_NONFINITE, "gipc_pcg: non-finite residual");
+    if (prm->rel_tol > 0.0 && hs.delta0 > 0.0 && hs.delta_new >= prm->rel_tol * hs.delta0 && hs.delta_new > 0.0)
+        return fail(GIPC_ERR_NOT_CONVERGED, "gipc_pcg: %d iterations without reaching the tolerance", hs.iters);
+    return GIPC_OK;
+}
