@@ -242,6 +242,35 @@ gipc_status gipc_pcg(gipc_ctx* ctx, const gipc_bsr* A_h, const double* rhs, doub
                      const uint8_t* fixed, const gipc_pcg_params* prm_h, int* iters_out_h,
                      double* rel_out_h, void* stream);
 
+/* Largest system (block rows) gipc_pcg_noalloc accepts. */
+#define GIPC_PCG_NOALLOC_MAX_N 32768
+
+/* gipc_pcg without a context and without any device allocation.  (The paper
+ * has no counterpart: this entry point exists for callers, not for the method.)
+ *
+ * For callers that may not allocate device memory -- for example a host
+ * framework that owns all device memory through its own pool and forbids
+ * cudaMalloc, or a latency-critical loop in which cudaMalloc/cudaFree (which
+ * can synchronise the device) would stall work on other streams.  It runs the
+ * same solver as gipc_pcg with the same arguments and results, but keeps its
+ * working vectors in one fixed array of about 7.2 MB in device global memory
+ * that the library defines: every GPU that loads the library holds that array
+ * until the process exits.  The caller still passes the matrix, rhs and x.
+ *
+ *  - Limit: A->n <= GIPC_PCG_NOALLOC_MAX_N; larger systems are rejected with
+ *    GIPC_ERR_INVALID_ARG and a message naming the limit (nothing is enqueued).
+ *  - The first call on a device looks up the array's device address (once per
+ *    device, with that device current); make that first call before any
+ *    stream capture.
+ *  - All calls share the one array, which keeps the last call's contents; each
+ *    call clears what must start at zero (the solver's counters and flags).
+ *    Calls that overlap on the GPU (e.g. issued on two streams at once, or from
+ *    two host threads) race on the array and give wrong results: serialise them.
+ * Errors and outputs as gipc_pcg. */
+gipc_status gipc_pcg_noalloc(const gipc_bsr* A_h, const double* rhs, double* x, const uint8_t* fixed,
+                             const gipc_pcg_params* prm_h, int* iters_out_h, double* rel_out_h,
+                             void* stream);
+
 /* ------------------------------------------------------------------ profiling */
 
 /* Kernels that a context can time with CUDA events on the stream they are

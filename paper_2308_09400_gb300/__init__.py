@@ -15,7 +15,7 @@ from ._abi import (FLAG_ACTIVE, FLAG_FILTERED, FLAG_INVALID, FLAG_MOLLIFIED, Gip
 TYPE_IDS = {"PT": 0, "EE": 1, "PE": 2, "PP": 3, "EE_PAR": 4, "PE_PAR": 5, "PP_PAR": 6}
 NULL_INDEX = -2147483648
 
-__all__ = ["compute_eps_x", "eval_stencils", "assemble_bsr", "pcg", "Context", "default_context", "GipcError", "FLAG_ACTIVE", "FLAG_FILTERED",
+__all__ = ["compute_eps_x", "eval_stencils", "assemble_bsr", "pcg", "pcg_noalloc", "Context", "default_context", "GipcError", "FLAG_ACTIVE", "FLAG_FILTERED",
            "FLAG_MOLLIFIED", "FLAG_INVALID", "TYPE_IDS", "NULL_INDEX"]
 
 
@@ -221,4 +221,31 @@ def pcg(A, rhs, x0=None, fixed=None, rel_tol=1e-4, max_iter=1000, check_every=0,
                           ctypes.byref(prm), ctypes.byref(iters), ctypes.byref(rel), _stream(stream))
     if st != _abi.GIPC_OK and not (st == _abi.GIPC_ERR_NOT_CONVERGED and not raise_on_nonconvergence):
         raise GipcError("gipc_pcg", st)
+    return x, iters.value, rel.value
+
+
+PCG_NOALLOC_MAX_N = 32768
+
+
+def pcg_noalloc(A, rhs, x0=None, fixed=None, rel_tol=1e-4, max_iter=1000, check_every=0,
+                raise_on_nonconvergence=False, stream=None):
+    """``pcg`` without a context or any device allocation by the library (gipc_pcg_noalloc).
+
+    For callers that may not allocate device memory; the solver's working vectors live in a
+    fixed array of the library (systems of at most PCG_NOALLOC_MAX_N block rows).  Calls that
+    overlap on the GPU share that array and race: serialise them.
+    """
+    n = A["n"]
+    _check(rhs, "rhs", torch.float64, 3)
+    x = torch.zeros_like(rhs) if x0 is None else x0.clone()
+    if fixed is not None:
+        _check(fixed, "fixed", torch.uint8)
+    bsr = _bsr_struct(A)
+    prm = _abi.PcgParams(float(rel_tol), int(max_iter), int(check_every))
+    iters = ctypes.c_int(0)
+    rel = ctypes.c_double(0.0)
+    st = _abi.call_status("gipc_pcg_noalloc", ctypes.byref(bsr), _ptr(rhs), _ptr(x), _ptr(fixed),
+                          ctypes.byref(prm), ctypes.byref(iters), ctypes.byref(rel), _stream(stream))
+    if st != _abi.GIPC_OK and not (st == _abi.GIPC_ERR_NOT_CONVERGED and not raise_on_nonconvergence):
+        raise GipcError("gipc_pcg_noalloc", st)
     return x, iters.value, rel.value

@@ -61,6 +61,8 @@ SIGNATURES = {
                                  ctypes.POINTER(Bsr), _P, _P]),
     "gipc_pcg": (_INT, [_P, ctypes.POINTER(Bsr), _P, _P, _P, ctypes.POINTER(PcgParams),
                         ctypes.POINTER(_INT), ctypes.POINTER(_D), _P]),
+    "gipc_pcg_noalloc": (_INT, [ctypes.POINTER(Bsr), _P, _P, _P, ctypes.POINTER(PcgParams),
+                                ctypes.POINTER(_INT), ctypes.POINTER(_D), _P]),
     "gipc_profile_begin": (_INT, [_P]),
     "gipc_profile_read": (_INT, [_P, _INT, ctypes.POINTER(KernelTime)]),
     "gipc_profile_stop": (_INT, [_P]),

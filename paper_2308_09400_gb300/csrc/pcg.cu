@@ -500,3 +500,161 @@ extern "C" gipc_status gipc_pcg(gipc_ctx* ctx, const gipc_bsr* A, const double* 
         return fail(GIPC_ERR_NOT_CONVERGED, "gipc_pcg: %d iterations without reaching the tolerance", hs.iters);
     return GIPC_OK;
 }
+
+// ------------------------------------------------------------------------------------------
+// Allocation-free variant of the solver (gipc_pcg_noalloc).
+//
+// Some callers may not allocate device memory: a host framework that owns every byte of
+// device memory through its own pool and forbids cudaMalloc, or a latency-critical loop in
+// which a cudaMalloc / cudaFree (which can synchronise the device) would stall work queued on
+// other streams.  This variant runs the same kernels as gipc_pcg, but its working vectors live
+// in one fixed-size array in device global memory defined below, so it needs neither a
+// context nor any allocation.  The caller still passes the matrix, right-hand side and
+// solution buffers.
+#include <mutex>
+
+namespace gipc {
+namespace {
+
+constexpr int64_t kNoAllocMaxN = GIPC_PCG_NOALLOC_MAX_N;
+constexpr size_t na_align(size_t b) { return (b + 255) / 256 * 256; }
+constexpr int64_t kNaChunks = (kNoAllocMaxN + kPermChunk - 1) / kPermChunk;
+constexpr int64_t kNaCounts = (int64_t)kLenBuckets * kNaChunks;
+constexpr int kNaMaxBlocks = 152 * 8 + 16;  // >= spmv and vector grids for n <= kNoAllocMaxN
+// region sizes (bytes), each 256-byte aligned
+constexpr size_t kNaVec = na_align(sizeof(double) * 18 * kNoAllocMaxN);        // b, x, r, s, c, q
+constexpr size_t kNaFac = na_align(sizeof(double) * 6 * kNoAllocMaxN);         // LDL^T factors
+constexpr size_t kNaVec32 = na_align(sizeof(float) * 6 * kNoAllocMaxN);        // float32 x0 and c
+constexpr size_t kNaPerm = na_align(sizeof(int32_t) * (kNoAllocMaxN + kNaCounts));
+constexpr size_t kNaOffs = na_align(sizeof(int64_t) * (kNaCounts + 1 + 64));   // offsets + scan scratch
+constexpr size_t kNaPart = na_align(256 + sizeof(double) * kNaMaxBlocks);      // scalars + partials
+constexpr size_t kNoAllocBytes = kNaVec + kNaFac + kNaVec32 + kNaPerm + kNaOffs + kNaPart;
+static_assert(kNaCounts <= kScanTile, "row-length histogram must fit one scan tile");
+static_assert(sizeof(PcgScalars) <= 256, "solver scalars must fit their slot");
+
+}  // namespace
+}  // namespace gipc
+
+// The fixed scratch: every GPU that loads this library holds it until the process exits.
+static __device__ __align__(256) unsigned char g_pcg_noalloc_scratch[gipc::kNoAllocBytes];
+
+namespace gipc {
+namespace {
+
+std::mutex g_na_mutex;
+constexpr int kNaMaxDevices = 256;
+void* g_na_addr[kNaMaxDevices] = {};
+
+// Device address of the fixed scratch on the current device.  In host code the array's name
+// is only a host-side stand-in, so the address comes from cudaGetSymbolAddress, once per
+// device, with that device current.
+gipc_status noalloc_scratch(unsigned char** out) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNaMaxDevices)
+        return fail(GIPC_ERR_CUDA, "gipc_pcg_noalloc: no usable current device");
+    std::lock_guard<std::mutex> lock(g_na_mutex);
+    if (!g_na_addr[dev]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_pcg_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(GIPC_ERR_CUDA, "gipc_pcg_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+        g_na_addr[dev] = p;
+    }
+    *out = static_cast<unsigned char*>(g_na_addr[dev]);
+    return GIPC_OK;
+}
+
+}  // namespace
+}  // namespace gipc
+
+extern "C" gipc_status gipc_pcg_noalloc(const gipc_bsr* A, const double* rhs, double* x, const uint8_t* fixed,
+                                        const gipc_pcg_params* prm, int* iters_out_h, double* rel_out_h,
+                                        void* stream) {
+    using namespace gipc;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!A || !prm) return fail(GIPC_ERR_INVALID_ARG, "gipc_pcg_noalloc: null matrix or parameters");
+    const int64_t n = A->n;
+    if (n < 0 || A->nnzb < 0) return fail(GIPC_ERR_INVALID_ARG, "gipc_pcg_noalloc: negative sizes");
+    if (n > kNoAllocMaxN)
+        return fail(GIPC_ERR_INVALID_ARG, "gipc_pcg_noalloc: n = %lld exceeds the fixed scratch limit of %lld vertices",
+                    (long long)n, (long long)kNoAllocMaxN);
+    if (A->prec != GIPC_FP64 && A->prec != GIPC_MIXED)
+        return fail(GIPC_ERR_INVALID_ARG, "gipc_pcg_noalloc: bad precision");
+    if (!(prm->rel_tol >= 0.0) || prm->max_iter < 0 || prm->check_every < 0)
+        return fail(GIPC_ERR_INVALID_ARG, "gipc_pcg_noalloc: need rel_tol >= 0, max_iter >= 0, check_every >= 0");
+    if (n == 0) {
+        if (iters_out_h) *iters_out_h = 0;
+        if (rel_out_h) *rel_out_h = 0.0;
+        return GIPC_OK;
+    }
+    if (!rhs || !x || !A->rowptr || (A->nnzb > 0 && (!A->colidx || !A->vals)))
+        return fail(GIPC_ERR_INVALID_ARG, "gipc_pcg_noalloc: null vector or matrix pointer");
+    unsigned char* base = nullptr;
+    gipc_status s = noalloc_scratch(&base);
+    if (s != GIPC_OK) return s;
+
+    const int64_t nvec = 3 * n;
+    const unsigned vb = vec_blocks(n), sb = spmv_blocks(n);
+    double* V = reinterpret_cast<double*>(base);
+    double *b = V, *xv = V + nvec, *r = V + 2 * nvec, *sv = V + 3 * nvec, *c = V + 4 * nvec, *q = V + 5 * nvec;
+    double* pinv = reinterpret_cast<double*>(base + kNaVec);
+    const bool f64 = A->prec == GIPC_FP64;
+    float* x32 = f64 ? nullptr : reinterpret_cast<float*>(base + kNaVec + kNaFac);
+    float* c32 = f64 ? nullptr : x32 + nvec;
+    int32_t* perm = reinterpret_cast<int32_t*>(base + kNaVec + kNaFac + kNaVec32);
+    const int64_t chunks = (n + kPermChunk - 1) / kPermChunk;
+    const int64_t ncnt = (int64_t)kLenBuckets * chunks;
+    int32_t* counts = perm + n;
+    int64_t* offs = reinterpret_cast<int64_t*>(base + kNaVec + kNaFac + kNaVec32 + kNaPerm);
+    int64_t* scan_tmp = offs + ncnt + 1;
+    unsigned char* pbase = base + kNaVec + kNaFac + kNaVec32 + kNaPerm + kNaOffs;
+    PcgScalars* S = reinterpret_cast<PcgScalars*>(pbase);
+    double* part = reinterpret_cast<double*>(pbase + 256);
+
+    const unsigned eb = (unsigned)((nvec + 255) / 256);
+    const int max_iter = prm->max_iter;
+    perm_hist_kernel<<<(unsigned)chunks, 256, 0, st>>>(A->rowptr, n, counts, chunks);
+    if (exclusive_scan<int32_t>(counts, offs, ncnt, scan_tmp, st) != cudaSuccess)
+        return check_launch("gipc_pcg_noalloc: scan");
+    perm_scatter_kernel<<<(unsigned)chunks, 32, 0, st>>>(A->rowptr, n, offs, chunks, perm);
+    // the solver scalars (iteration count, done flag, reduction counters) start from zero on
+    // every call: pcg_set_scalars clears them; all other scratch is written before it is read
+    pcg_set_scalars<<<1, 1, 0, st>>>(S, prm->rel_tol, max_iter);
+    soa_to_aos_kernel<<<eb, 256, 0, st>>>(rhs, b, nullptr, n, fixed);
+    soa_to_aos_kernel<<<eb, 256, 0, st>>>(x, xv, x32, n, fixed);
+    if (f64) pcg_factor_kernel<double><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(A->rowptr, A->colidx, (const double*)A->vals, n, pinv);
+    else pcg_factor_kernel<float><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(A->rowptr, A->colidx, (const float*)A->vals, n, pinv);
+    if (f64) pcg_spmv_kernel<double, double><<<sb, kPcgThreads, 0, st>>>(A->rowptr, A->colidx, (const double*)A->vals, xv, xv, perm, q, fixed, n, part, S);
+    else pcg_spmv_kernel<float, float><<<sb, kPcgThreads, 0, st>>>(A->rowptr, A->colidx, (const float*)A->vals, x32, xv, perm, q, fixed, n, part, S);
+    pcg_init_kernel<<<vb, kPcgThreads, 0, st>>>(b, q, r, sv, c, c32, pinv, fixed, n, part, S);
+    if ((s = check_launch("gipc_pcg_noalloc: setup")) != GIPC_OK) return s;
+
+    const int chunk = prm->check_every > 0 ? prm->check_every : (prm->rel_tol > 0.0 ? 16 : max_iter + 1);
+    PcgScalars hs{};
+    int launched = 0;
+    while (launched < max_iter) {
+        const int m = (max_iter - launched) < chunk ? (max_iter - launched) : chunk;
+        for (int it = 0; it < m; ++it) {
+            if (f64) pcg_spmv_kernel<double, double><<<sb, kPcgThreads, 0, st>>>(A->rowptr, A->colidx, (const double*)A->vals, c, c, perm, q, fixed, n, part, S);
+            else pcg_spmv_kernel<float, float><<<sb, kPcgThreads, 0, st>>>(A->rowptr, A->colidx, (const float*)A->vals, c32, c, perm, q, fixed, n, part, S);
+            pcg_update_kernel<<<vb, kPcgThreads, 0, st>>>(xv, r, c, q, sv, pinv, n, part, S);
+            pcg_direction_kernel<<<vb, kPcgThreads, 0, st>>>(c, c32, sv, fixed, n, S);
+        }
+        launched += m;
+        if ((s = check_launch("gipc_pcg_noalloc: iteration")) != GIPC_OK) return s;
+        if (launched < max_iter) {
+            cudaMemcpyAsync(&hs, S, sizeof(PcgScalars), cudaMemcpyDeviceToHost, st);
+            if (cudaStreamSynchronize(st) != cudaSuccess) return check_launch("gipc_pcg_noalloc: sync");
+            if (hs.done) break;
+        }
+    }
+    aos_to_soa_kernel<<<eb, 256, 0, st>>>(xv, x, n);
+    cudaMemcpyAsync(&hs, S, sizeof(PcgScalars), cudaMemcpyDeviceToHost, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return check_launch("gipc_pcg_noalloc: final sync");
+    if (iters_out_h) *iters_out_h = hs.iters;
+    if (rel_out_h) *rel_out_h = hs.delta0 > 0.0 ? hs.delta_new / hs.delta0 : 0.0;
+    if (hs.status == GIPC_ERR_NONFINITE) return fail(GIPC_ERR_NONFINITE, "gipc_pcg_noalloc: non-finite residual");
+    if (prm->rel_tol > 0.0 && hs.delta0 > 0.0 && hs.delta_new >= prm->rel_tol * hs.delta0 && hs.delta_new > 0.0)
+        return fail(GIPC_ERR_NOT_CONVERGED, "gipc_pcg_noalloc: %d iterations without reaching the tolerance", hs.iters);
+    return GIPC_OK;
+}
