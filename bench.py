@@ -150,7 +150,9 @@ def launches_per_step(n):
     assembly = 11 + 2 * scan      # init, count, init_cursor, fill, 2 sorts, rowptr32, emit, seg_end, grad_init, values
     nck = 64 * ((n + 1023) // 1024)
     perm = 2 + (1 if nck <= 4096 else (3 if (nck + 4095) // 4096 <= 4096 else 5))  # row-length sort
-    pcg = perm + 6 + 3 * PCG_ITERS + 1  # set, 2 conversions, factor, spmv(x0), init, 3/iteration, back-conversion
+    nsl = (n + 9) // 10
+    sell = 2 + (1 if nsl <= 4096 else (3 if (nsl + 4095) // 4096 <= 4096 else 5))       # sliced layout
+    pcg = perm + sell + 6 + 3 * PCG_ITERS + 1  # set, 2 conversions, factor, spmv(x0), init, 3/iteration, back
     return 2 + assembly + pcg
 
 

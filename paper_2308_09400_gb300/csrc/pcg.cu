@@ -22,7 +22,9 @@
 // cross-lane reduction is needed; ten rows per warp.  Rows are visited in an
 // order sorted by length (a stable bucket sort at set-up, longest first), so the
 // ten rows of a warp have similar lengths and few lanes idle: on GB300 an FP64
-// instruction costs the same whether 21 or 30 of its lanes are active.  The
+// instruction costs the same whether 21 or 30 of its lanes are active.  gipc_pcg
+// copies the matrix once per solve into a sliced layout (ten rows per slice,
+// block j of the ten rows side by side) so every warp load is contiguous.  The
 // mixed path gathers a float32 copy of the search direction, so its inner loop
 // has no float64 operation at all.
 #include <cuda_runtime.h>
@@ -39,7 +41,7 @@ namespace {
 constexpr int kPcgThreads = 256;
 constexpr int kRowsPerWarp = 10;  // 3 lanes per row, lanes 30/31 idle
 
-enum PcgSlot { P_VEC = 9, P_PINV = 10, P_PART = 11, P_PERM = 12, P_VEC32 = 13 };
+enum PcgSlot { P_VEC = 9, P_PINV = 10, P_PART = 11, P_PERM = 12, P_VEC32 = 13, P_SELL = 14, P_SLICE = 15 };
 
 constexpr int kLenBuckets = 64;   // rows are ordered by min(blocks in row, 63), longest first
 constexpr int kPermChunk = 1024;  // rows per block of the stable bucket sort
@@ -184,6 +186,154 @@ __global__ void perm_scatter_kernel(const int32_t* __restrict__ rowptr, int64_t 
         __syncwarp();
         if (valid && rank == 0) run[key] += __popc(grp);
         __syncwarp();
+    }
+}
+
+// ---- sliced layout of the matrix for the solver (built once per solve) --------------------
+// Rows are taken ten at a time in the length-sorted order (one slice per warp).  Slice s
+// holds L_s steps (its longest row); step j stores block j of each of its ten rows side by
+// side: column indices at sell_col[(off_s + j)*10 + i] and the 9 values at
+// sell_vals[((off_s + j)*10 + i)*9 ...].  A warp step then reads 10 contiguous column indices
+// and 90 contiguous values.  Shorter rows are padded with zero blocks (column 0).
+
+__global__ void sell_len_kernel(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ perm, int64_t n,
+                                int64_t nsl, int32_t* __restrict__ slice_len) {
+    const int64_t sl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (sl >= nsl) return;
+    int32_t L = 0;
+    for (int i = 0; i < kRowsPerWarp; ++i) {
+        const int64_t slot = sl * kRowsPerWarp + i;
+        if (slot < n) {
+            const int32_t r = perm[slot];
+            const int32_t len = rowptr[r + 1] - rowptr[r];
+            L = len > L ? len : L;
+        }
+    }
+    slice_len[sl] = L;
+}
+
+template <typename VT>
+__global__ void sell_fill_kernel(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
+                                 const VT* __restrict__ vals, const int32_t* __restrict__ perm, int64_t n, int64_t nsl,
+                                 const int64_t* __restrict__ slice_off, int32_t* __restrict__ sell_col,
+                                 VT* __restrict__ sell_vals) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nsl * kRowsPerWarp) return;
+    const int64_t sl = t / kRowsPerWarp;
+    const int i = (int)(t - sl * kRowsPerWarp);
+    const int64_t off = slice_off[sl], L = slice_off[sl + 1] - off;
+    int32_t b0 = 0, len = 0;
+    if (t < n) {
+        const int32_t r = perm[t];
+        b0 = rowptr[r];
+        len = rowptr[r + 1] - b0;
+    }
+    for (int64_t j = 0; j < L; ++j) {
+        const int64_t p = (off + j) * kRowsPerWarp + i;
+        if (j < len) {
+            sell_col[p] = colidx[b0 + j];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) sell_vals[9 * p + k] = vals[9 * (int64_t)(b0 + j) + k];
+        } else {
+            sell_col[p] = 0;
+#pragma unroll
+            for (int k = 0; k < 9; ++k) sell_vals[9 * p + k] = VT(0);
+        }
+    }
+}
+
+// q = S(H c) over the sliced layout; alpha = delta_new / (c . q)
+// Persistent grid: warps stride over the slices.  Each lane issues all loads of an
+// eight-block group (columns, then values and gathered direction entries) before the group's
+// first FMA, so every warp keeps ~25 independent requests in flight; the kernel is bound by
+// memory latency, not by bytes.
+template <typename VT, typename PT>
+__global__ void __launch_bounds__(kPcgThreads)
+pcg_spmv_sell_kernel(const int32_t* __restrict__ rowptr, const int64_t* __restrict__ slice_off,
+                     const int32_t* __restrict__ sell_col,
+                     const VT* __restrict__ sell_vals, const PT* __restrict__ cg, const double* __restrict__ c,
+                     const int32_t* __restrict__ perm, double* __restrict__ q, const uint8_t* __restrict__ fixed,
+                     int64_t n, int64_t nsl, double* __restrict__ part, PcgScalars* __restrict__ S) {
+    if (S->done) return;
+    constexpr int U = 8;
+    const int lane = threadIdx.x & 31;
+    const int i = lane / 3, comp = lane - 3 * (lane / 3);
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    double d = 0.0;
+    for (int64_t sl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < nsl; sl += warps) {
+        const int64_t slot = sl * kRowsPerWarp + i;
+        if (lane >= 3 * kRowsPerWarp || slot >= n) continue;
+        // each lane walks its own row's blocks (never the padding), grouped so that block j
+        // goes to accumulator (j / 4) % 2 ... exactly as the row-ordered kernel, which keeps
+        // both layouts' rounding identical
+        const int64_t row = perm[slot];
+        const int64_t off = slice_off[sl];
+        const int64_t L = rowptr[row + 1] - rowptr[row];
+        VT acc0 = VT(0), acc1 = VT(0);
+        int64_t j = 0;
+        for (; j + U <= L; j += U) {
+            int64_t cc[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) cc[u] = sell_col[(off + j + u) * kRowsPerWarp + i];
+            VT v[3 * U];
+            PT pv[3 * U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const VT* vp = sell_vals + 9 * ((off + j + u) * kRowsPerWarp + i) + 3 * comp;
+                const PT* pp = cg + 3 * cc[u];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    v[3 * u + k] = __ldcs(vp + k);
+                    pv[3 * u + k] = __ldg(pp + k);
+                }
+            }
+#pragma unroll
+            for (int h = 0; h < U; h += 4) {
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    acc0 = fma(v[3 * h + k], (VT)pv[3 * h + k], acc0);
+                    acc1 = fma(v[3 * h + 3 + k], (VT)pv[3 * h + 3 + k], acc1);
+                }
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    acc0 = fma(v[3 * h + 6 + k], (VT)pv[3 * h + 6 + k], acc0);
+                    acc1 = fma(v[3 * h + 9 + k], (VT)pv[3 * h + 9 + k], acc1);
+                }
+            }
+        }
+        for (; j + 4 <= L; j += 4) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t p = (off + j + u) * kRowsPerWarp + i;
+                const VT* vp = sell_vals + 9 * p + 3 * comp;
+                const PT* pp = cg + 3 * (int64_t)sell_col[p];
+                VT& acc = (u & 1) ? acc1 : acc0;
+                acc = fma(vp[0], (VT)pp[0], acc);
+                acc = fma(vp[1], (VT)pp[1], acc);
+                acc = fma(vp[2], (VT)pp[2], acc);
+            }
+        }
+        for (; j < L; ++j) {
+            const int64_t p = (off + j) * kRowsPerWarp + i;
+            const VT* vp = sell_vals + 9 * p + 3 * comp;
+            const PT* pp = cg + 3 * (int64_t)sell_col[p];
+            acc0 = fma(vp[0], (VT)pp[0], acc0);
+            acc0 = fma(vp[1], (VT)pp[1], acc0);
+            acc0 = fma(vp[2], (VT)pp[2], acc0);
+        }
+        double y = (double)(acc0 + acc1);
+        if (fixed && fixed[row]) y = 0.0;
+        q[3 * row + comp] = y;
+        d += c[3 * row + comp] * y;
+    }
+    const double bs = block_sum(d);
+    if (publish_partial(part, bs, &S->count_a)) {
+        const double pq = sum_partials(part, gridDim.x);
+        if (threadIdx.x == 0) {
+            S->pq = pq;
+            S->alpha = S->delta_new / pq;
+            S->count_a = 0;
+        }
     }
 }
 
@@ -453,6 +603,27 @@ extern "C" gipc_status gipc_pcg(gipc_ctx* ctx, const gipc_bsr* A, const double* 
     perm_hist_kernel<<<(unsigned)chunks, 256, 0, st>>>(A->rowptr, n, counts, chunks);
     if (exclusive_scan<int32_t>(counts, offs, ncnt, scan_tmp, st) != cudaSuccess) return check_launch("gipc_pcg: scan");
     perm_scatter_kernel<<<(unsigned)chunks, 32, 0, st>>>(A->rowptr, n, offs, chunks, perm);
+    // sliced layout: slice lengths, their offsets, then the copy
+    const int64_t nsl = (n + kRowsPerWarp - 1) / kRowsPerWarp;
+    if ((s = ctx->slot[P_SLICE].reserve(sizeof(int32_t) * (nsl + 1) + sizeof(int64_t) * (nsl + 2 + scan_scratch_words(nsl)) + 64)) != GIPC_OK) return s;
+    int32_t* slice_len = ctx->slot[P_SLICE].as<int32_t>();
+    int64_t* slice_off = reinterpret_cast<int64_t*>(ctx->slot[P_SLICE].as<char>() + ((sizeof(int32_t) * (nsl + 1) + 15) / 16) * 16);
+    int64_t* slice_scan = slice_off + nsl + 2;
+    sell_len_kernel<<<(unsigned)((nsl + 255) / 256), 256, 0, st>>>(A->rowptr, perm, n, nsl, slice_len);
+    if (exclusive_scan<int32_t>(slice_len, slice_off, nsl, slice_scan, st) != cudaSuccess) return check_launch("gipc_pcg: scan");
+    int64_t steps = 0;
+    cudaMemcpyAsync(&steps, slice_off + nsl, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return check_launch("gipc_pcg: slice sync");
+    const size_t vsz = f64 ? sizeof(double) : sizeof(float);
+    const int64_t cells = steps * kRowsPerWarp;
+    if ((s = ctx->slot[P_SELL].reserve(sizeof(int32_t) * cells + 256 + vsz * 9 * cells)) != GIPC_OK) return s;
+    int32_t* sell_col = ctx->slot[P_SELL].as<int32_t>();
+    void* sell_vals = ctx->slot[P_SELL].as<char>() + ((sizeof(int32_t) * cells + 255) / 256) * 256;
+    const unsigned fb = (unsigned)((nsl * kRowsPerWarp + 255) / 256);
+    if (f64) sell_fill_kernel<double><<<fb, 256, 0, st>>>(A->rowptr, A->colidx, (const double*)A->vals, perm, n, nsl, slice_off, sell_col, (double*)sell_vals);
+    else sell_fill_kernel<float><<<fb, 256, 0, st>>>(A->rowptr, A->colidx, (const float*)A->vals, perm, n, nsl, slice_off, sell_col, (float*)sell_vals);
+    unsigned slb = (unsigned)((nsl * 32 + kPcgThreads - 1) / kPcgThreads);
+    if (slb > 152 * 8) slb = 152 * 8;  // persistent: one wave of 8 CTAs per SM
 
     pcg_set_scalars<<<1, 1, 0, st>>>(S, prm->rel_tol, max_iter);
     soa_to_aos_kernel<<<eb, 256, 0, st>>>(rhs, b, nullptr, n, fixed);
@@ -472,8 +643,8 @@ extern "C" gipc_status gipc_pcg(gipc_ctx* ctx, const gipc_bsr* A, const double* 
         const int m = (max_iter - launched) < chunk ? (max_iter - launched) : chunk;
         for (int it = 0; it < m; ++it) {
             ctx->prof.start(GIPC_PROF_PCG_SPMV, st);
-            if (f64) pcg_spmv_kernel<double, double><<<sb, kPcgThreads, 0, st>>>(A->rowptr, A->colidx, (const double*)A->vals, c, c, perm, q, fixed, n, part, S);
-            else pcg_spmv_kernel<float, float><<<sb, kPcgThreads, 0, st>>>(A->rowptr, A->colidx, (const float*)A->vals, c32, c, perm, q, fixed, n, part, S);
+            if (f64) pcg_spmv_sell_kernel<double, double><<<slb, kPcgThreads, 0, st>>>(A->rowptr, slice_off, sell_col, (const double*)sell_vals, c, c, perm, q, fixed, n, nsl, part, S);
+            else pcg_spmv_sell_kernel<float, float><<<slb, kPcgThreads, 0, st>>>(A->rowptr, slice_off, sell_col, (const float*)sell_vals, c32, c, perm, q, fixed, n, nsl, part, S);
             ctx->prof.stop(GIPC_PROF_PCG_SPMV, st);
             ctx->prof.start(GIPC_PROF_PCG_UPDATE, st);
             pcg_update_kernel<<<vb, kPcgThreads, 0, st>>>(xv, r, c, q, sv, pinv, n, part, S);
