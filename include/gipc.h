@@ -154,6 +154,45 @@ gipc_status gipc_eval_stencils(const double* x, int64_t n, const int32_t* stenci
                                int prec, int mode, double* energy, double* grad, void* hess,
                                double* lam, uint8_t* flags, void* stream);
 
+/* ------------------------------------------------------------------ tetrahedra */
+
+/* Stable neo-Hookean parameters: Psi = mu/2 (I2 - 3) + lambda/2 (J - alpha)^2
+ * - mu/2 log(I2 + 1), alpha = 1 + mu/lambda - mu/(4 lambda) (paper Sec. 8: the
+ * deformables use the Stable neo-Hookean energy). */
+typedef struct {
+    double mu, lambda;   /* energy parameters (from gipc_snh_params)                     */
+    double scale;        /* multiplies energy, gradient and Hessian (dt^2 in the step)    */
+} gipc_elastic_params;
+
+/* (mu, lambda) of the energy above from Young's modulus and Poisson's ratio:
+ * mu = 4/3 mu_L, lambda = lambda_L + 5/6 mu_L with the Lame parameters of (E, nu),
+ * so small strains behave as linear elasticity with (mu_L, lambda_L).  Host only. */
+gipc_status gipc_snh_params(double young, double poisson, double* mu_h, double* lambda_h);
+
+/* Rest state of tetrahedra from rest positions (float64 [3][n]):
+ *   Dm_inv  float64 [9][T]: inverse of Dm = [xbar1-xbar0, xbar2-xbar0, xbar3-xbar0], row-major
+ *   vol     float64 [T]:    |det Dm| / 6
+ *   mass    float64 [n] or NULL: lumped masses density * sum(vol)/4 over incident tetrahedra,
+ *           summed in ascending tetrahedron index (reproducible bit for bit)
+ * tets: int32 [4][T] vertex ids.  Synchronises the stream once (to report degenerate
+ * elements).  Errors: GIPC_ERR_INVALID_ARG (sizes, pointers, a zero-volume or
+ * out-of-range tetrahedron), GIPC_ERR_OOM, GIPC_ERR_CUDA. */
+gipc_status gipc_tet_rest(gipc_ctx* ctx, const double* rest_x, int64_t n, const int32_t* tets, int64_t T,
+                          double density, double* Dm_inv, double* vol, double* mass, void* stream);
+
+/* Energy scale*vol*Psi(F), gradient and PSD-projected Hessian of every tetrahedron,
+ * F = Ds Dm^-1.  The projection uses the closed-form eigensystem of the isotropic energy
+ * (twist, flip and scaling modes from a rotation-variant SVD of F), keeping the modes
+ * with positive eigenvalues.
+ *   energy float64 [T] or NULL; grad float64 [12][T] or NULL;
+ *   hess   [144][T] (row-major 12x12, vertex-major x,y,z), float64 (GIPC_FP64) or
+ *          float32 (GIPC_MIXED; computed in float64, stored in float32), or NULL
+ * A tetrahedron with a vertex id outside [0, n) gets energy 0 and no other output.
+ * Errors: GIPC_ERR_INVALID_ARG, GIPC_ERR_CUDA. */
+gipc_status gipc_eval_tets(const double* x, int64_t n, const int32_t* tets, int64_t T, const double* Dm_inv,
+                           const double* vol, const gipc_elastic_params* prm_h, int prec, double* energy,
+                           double* grad, void* hess, void* stream);
+
 /* ------------------------------------------------------------------ assembly */
 
 /* A square 3x3-block sparse matrix (BSR) over n block rows.  Block p of row r

@@ -15,7 +15,7 @@ from ._abi import (FLAG_ACTIVE, FLAG_FILTERED, FLAG_INVALID, FLAG_MOLLIFIED, Gip
 TYPE_IDS = {"PT": 0, "EE": 1, "PE": 2, "PP": 3, "EE_PAR": 4, "PE_PAR": 5, "PP_PAR": 6}
 NULL_INDEX = -2147483648
 
-__all__ = ["compute_eps_x", "eval_stencils", "assemble_bsr", "pcg", "pcg_noalloc", "Context", "default_context", "GipcError", "FLAG_ACTIVE", "FLAG_FILTERED",
+__all__ = ["compute_eps_x", "eval_stencils", "assemble_bsr", "pcg", "pcg_noalloc", "snh_params", "tet_rest", "eval_tets", "Context", "default_context", "GipcError", "FLAG_ACTIVE", "FLAG_FILTERED",
            "FLAG_MOLLIFIED", "FLAG_INVALID", "TYPE_IDS", "NULL_INDEX"]
 
 
@@ -249,3 +249,44 @@ def pcg_noalloc(A, rhs, x0=None, fixed=None, rel_tol=1e-4, max_iter=1000, check_
     if st != _abi.GIPC_OK and not (st == _abi.GIPC_ERR_NOT_CONVERGED and not raise_on_nonconvergence):
         raise GipcError("gipc_pcg_noalloc", st)
     return x, iters.value, rel.value
+
+
+def snh_params(young, poisson):
+    """(mu, lambda) of the Stable neo-Hookean energy for (E, nu) (gipc_snh_params)."""
+    mu, lam = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _abi.call("gipc_snh_params", float(young), float(poisson), ctypes.byref(mu), ctypes.byref(lam))
+    return mu.value, lam.value
+
+
+def tet_rest(rest_x, tets, density=None, ctx=None, stream=None):
+    """Dm^-1 [9, T], volumes [T] and (if density) lumped masses [n] (gipc_tet_rest)."""
+    ctx = ctx or default_context()
+    _check(rest_x, "rest_x", torch.float64, 3)
+    _check(tets, "tets", torch.int32, 4)
+    n, T = rest_x.shape[1], tets.shape[1]
+    dev = rest_x.device
+    Dmi = torch.empty((9, T), dtype=torch.float64, device=dev)
+    vol = torch.empty(T, dtype=torch.float64, device=dev)
+    mass = torch.empty(n, dtype=torch.float64, device=dev) if density is not None else None
+    _abi.call("gipc_tet_rest", ctx.handle, _ptr(rest_x), n, _ptr(tets), T, float(density or 0.0), _ptr(Dmi),
+              _ptr(vol), _ptr(mass), _stream(stream))
+    return Dmi, vol, mass
+
+
+def eval_tets(x, tets, Dm_inv, vol, mu, lam, scale, precision="fp64", want=("energy", "grad", "hess"),
+              out=None, stream=None):
+    """Stable neo-Hookean energy / gradient / projected Hessian per tetrahedron (gipc_eval_tets)."""
+    _check(x, "x", torch.float64, 3)
+    _check(tets, "tets", torch.int32, 4)
+    n, T = x.shape[1], tets.shape[1]
+    prec = {"fp64": _abi.GIPC_FP64, "mixed": _abi.GIPC_MIXED}[precision]
+    hdt = torch.float64 if prec == _abi.GIPC_FP64 else torch.float32
+    out = dict(out or {})
+    shapes = {"energy": ((T,), torch.float64), "grad": ((12, T), torch.float64), "hess": ((144, T), hdt)}
+    for key in set(want) | set(out):
+        if key not in out:
+            out[key] = torch.zeros(shapes[key][0], dtype=shapes[key][1], device=x.device)
+    prm = _abi.ElasticParams(float(mu), float(lam), float(scale))
+    _abi.call("gipc_eval_tets", _ptr(x), n, _ptr(tets), T, _ptr(Dm_inv), _ptr(vol), ctypes.byref(prm), prec,
+              _ptr(out.get("energy")), _ptr(out.get("grad")), _ptr(out.get("hess")), _stream(stream))
+    return out

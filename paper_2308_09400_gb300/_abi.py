@@ -34,6 +34,10 @@ class Elements(ctypes.Structure):
                 ("hess", ctypes.c_void_p), ("lam", ctypes.c_void_p), ("grad", ctypes.c_void_p)]
 
 
+class ElasticParams(ctypes.Structure):
+    _fields_ = [("mu", ctypes.c_double), ("lam", ctypes.c_double), ("scale", ctypes.c_double)]
+
+
 class PcgParams(ctypes.Structure):
     _fields_ = [("rel_tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("check_every", ctypes.c_int)]
 
@@ -57,6 +61,9 @@ SIGNATURES = {
     "gipc_compute_eps_x": (_INT, [_P, _I64, _P, _I64, _P, _P]),
     "gipc_eval_stencils": (_INT, [_P, _I64, _P, _I64, _P, ctypes.POINTER(BarrierParams), _INT, _INT,
                                   _P, _P, _P, _P, _P, _P]),
+    "gipc_snh_params": (_INT, [_D, _D, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
+    "gipc_tet_rest": (_INT, [_P, _P, _I64, _P, _I64, _D, _P, _P, _P, _P]),
+    "gipc_eval_tets": (_INT, [_P, _I64, _P, _I64, _P, _P, ctypes.POINTER(ElasticParams), _INT, _P, _P, _P, _P]),
     "gipc_assemble_bsr": (_INT, [_P, _I64, ctypes.POINTER(Elements), ctypes.POINTER(Elements), _P, _P,
                                  ctypes.POINTER(Bsr), _P, _P]),
     "gipc_pcg": (_INT, [_P, ctypes.POINTER(Bsr), _P, _P, _P, ctypes.POINTER(PcgParams),

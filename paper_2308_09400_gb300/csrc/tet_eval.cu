@@ -1,0 +1,477 @@
+// Stable neo-Hookean tetrahedra: energy, gradient and the analytically projected Hessian.
+//
+// The paper's deformables use the Stable neo-Hookean energy (Sec. 8) with the analytic
+// eigensystems of isotropic distortion energies it cites (Sec. 2, "Eigen Analysis"):
+//   Psi = mu/2 (I2 - 3) + lam/2 (J - alpha)^2 - mu/2 log(I2 + 1),
+//   I2 = ||F||^2, J = det F, alpha = 1 + mu/lam - mu/(4 lam).
+// Per element (one thread): F = Ds Dm^-1, a rotation-variant SVD F = U diag(s) V^T
+// (cyclic Jacobi on F^T F, then Gram-Schmidt on F V; s2 may be negative for an inverted
+// element), and the nine eigenpairs of d2Psi/dF2 in closed form:
+//   twist (i,j; k the third index):  mu(1 - 1/(I2+1)) + lam (J - alpha) s_k,  U (e_i e_j^T - e_j e_i^T) V^T / sqrt2
+//   flip  (i,j):                     mu(1 - 1/(I2+1)) - lam (J - alpha) s_k,  U (e_i e_j^T + e_j e_i^T) V^T / sqrt2
+//   scaling: eigenpairs (l, a) of the 3x3 matrix d2Psi/ds_i ds_j,            U diag(a) V^T
+// The projected block is scale * vol * sum over modes with l > 0 of l w w^T, w = dF/dx^T vec(Q),
+// where dF/dx^T maps a 3x3 G to forces (G Dm^-T columns on vertices 1..3, minus their sum on 0).
+#include <cmath>
+#include <type_traits>
+
+#include "common.cuh"
+#include "context.cuh"
+#include "scan.cuh"
+
+namespace gipc {
+namespace {
+
+struct ElasticConst {
+    double mu, lam, alpha, scale;
+};
+
+// One Jacobi rotation zeroing a[p][q] of a symmetric 3x3 matrix, accumulating into v.
+template <int P, int Q>
+__device__ __forceinline__ void jacobi_rot(double (&a)[3][3], double (&v)[3][3]) {
+    constexpr int R = 3 - P - Q;
+    const double apq = a[P][Q];
+    if (apq == 0.0) return;
+    const double theta = (a[Q][Q] - a[P][P]) / (2.0 * apq);
+    const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+    const double c = rsqrt(t * t + 1.0);
+    const double s = t * c;
+    a[P][P] -= t * apq;
+    a[Q][Q] += t * apq;
+    a[P][Q] = a[Q][P] = 0.0;
+    const double arp = a[R][P], arq = a[R][Q];
+    a[R][P] = a[P][R] = c * arp - s * arq;
+    a[R][Q] = a[Q][R] = s * arp + c * arq;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        const double vp = v[r][P], vq = v[r][Q];
+        v[r][P] = c * vp - s * vq;
+        v[r][Q] = s * vp + c * vq;
+    }
+}
+
+// Eigen-decomposition of a symmetric 3x3 matrix by cyclic Jacobi; eigenvalues on the
+// diagonal of a, eigenvectors in the columns of v.
+__device__ __forceinline__ void jacobi3(double (&a)[3][3], double (&v)[3][3]) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) v[r][c] = r == c ? 1.0 : 0.0;
+    for (int sweep = 0; sweep < 12; ++sweep) {
+        const double off = a[0][1] * a[0][1] + a[0][2] * a[0][2] + a[1][2] * a[1][2];
+        const double dia = a[0][0] * a[0][0] + a[1][1] * a[1][1] + a[2][2] * a[2][2];
+        if (!(off > 1e-34 * dia)) break;
+        jacobi_rot<0, 1>(a, v);
+        jacobi_rot<0, 2>(a, v);
+        jacobi_rot<1, 2>(a, v);
+    }
+}
+
+__device__ __forceinline__ void cross(const double* a, const double* b, double* o) {
+    o[0] = a[1] * b[2] - a[2] * b[1];
+    o[1] = a[2] * b[0] - a[0] * b[2];
+    o[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+// Rotation-variant SVD: F = U diag(s) V^T with det U = det V = 1, s0 >= s1 >= |s2|.
+__device__ void svd3(const double (&F)[3][3], double (&U)[3][3], double (&s)[3], double (&V)[3][3]) {
+    double S[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) S[i][j] = F[0][i] * F[0][j] + F[1][i] * F[1][j] + F[2][i] * F[2][j];
+    double W[3][3];
+    jacobi3(S, W);
+    double ev[3] = {S[0][0], S[1][1], S[2][2]};
+    int o[3] = {0, 1, 2};
+    // sort descending
+    if (ev[o[0]] < ev[o[1]]) { int t = o[0]; o[0] = o[1]; o[1] = t; }
+    if (ev[o[1]] < ev[o[2]]) { int t = o[1]; o[1] = o[2]; o[2] = t; }
+    if (ev[o[0]] < ev[o[1]]) { int t = o[0]; o[0] = o[1]; o[1] = t; }
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) V[r][c] = o[c] == 0 ? W[r][0] : (o[c] == 1 ? W[r][1] : W[r][2]);
+    double v0[3] = {V[0][0], V[1][0], V[2][0]}, v1[3] = {V[0][1], V[1][1], V[2][1]}, v2[3];
+    cross(v0, v1, v2);  // third column = v0 x v1 makes V a rotation
+#pragma unroll
+    for (int r = 0; r < 3; ++r) V[r][2] = v2[r];
+    // B = F V
+    double B[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) B[i][j] = F[i][0] * V[0][j] + F[i][1] * V[1][j] + F[i][2] * V[2][j];
+    double u0[3] = {B[0][0], B[1][0], B[2][0]};
+    double n0 = sqrt(u0[0] * u0[0] + u0[1] * u0[1] + u0[2] * u0[2]);
+    if (n0 > 0.0) {
+#pragma unroll
+        for (int r = 0; r < 3; ++r) u0[r] /= n0;
+    } else {
+        u0[0] = 1.0; u0[1] = 0.0; u0[2] = 0.0;
+    }
+    double b1[3] = {B[0][1], B[1][1], B[2][1]};
+    const double p = u0[0] * b1[0] + u0[1] * b1[1] + u0[2] * b1[2];
+    double u1[3] = {b1[0] - p * u0[0], b1[1] - p * u0[1], b1[2] - p * u0[2]};
+    double n1 = sqrt(u1[0] * u1[0] + u1[1] * u1[1] + u1[2] * u1[2]);
+    if (n1 > 1e-300 && n1 > 1e-14 * n0) {
+#pragma unroll
+        for (int r = 0; r < 3; ++r) u1[r] /= n1;
+    } else {  // any unit vector orthogonal to u0
+        const double ax = fabs(u0[0]), ay = fabs(u0[1]), az = fabs(u0[2]);
+        double e[3] = {0.0, 0.0, 0.0};
+        if (ax <= ay && ax <= az) e[0] = 1.0;
+        else if (ay <= az) e[1] = 1.0;
+        else e[2] = 1.0;
+        cross(u0, e, u1);
+        const double m = sqrt(u1[0] * u1[0] + u1[1] * u1[1] + u1[2] * u1[2]);
+#pragma unroll
+        for (int r = 0; r < 3; ++r) u1[r] /= m;
+        n1 = u1[0] * b1[0] + u1[1] * b1[1] + u1[2] * b1[2];
+    }
+    double u2[3];
+    cross(u0, u1, u2);
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        U[r][0] = u0[r];
+        U[r][1] = u1[r];
+        U[r][2] = u2[r];
+    }
+    s[0] = n0;
+    s[1] = n1;
+    s[2] = u2[0] * B[0][2] + u2[1] * B[1][2] + u2[2] * B[2][2];
+}
+
+// G (3x3) -> w (12): forces G Dm^-T on vertices 1..3, minus their sum on vertex 0.
+__device__ __forceinline__ void map_to_x(const double (&G)[3][3], const double (&Dmi)[3][3], double (&w)[12]) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        double s = 0.0;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            // (G Dm^-T)[r][a] = sum_c G[r][c] Dmi[a][c]
+            const double h = G[r][0] * Dmi[a][0] + G[r][1] * Dmi[a][1] + G[r][2] * Dmi[a][2];
+            w[3 * (a + 1) + r] = h;
+            s += h;
+        }
+        w[r] = -s;
+    }
+}
+
+template <typename HT>
+__device__ __forceinline__ void add_mode(double lam, const double (&Q)[3][3], const double (&Dmi)[3][3],
+                                         double (&H)[78]) {
+    if (!(lam > 0.0)) return;
+    double w[12];
+    map_to_x(Q, Dmi, w);
+    int idx = 0;
+#pragma unroll
+    for (int a = 0; a < 12; ++a) {
+        const double la = lam * w[a];
+#pragma unroll
+        for (int b = 0; b <= a; ++b) H[idx++] += la * w[b];
+    }
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(128)
+eval_tets_kernel(const double* __restrict__ x, int64_t n, const int32_t* __restrict__ tets, int64_t T,
+                 const double* __restrict__ Dm_inv, const double* __restrict__ vol, const ElasticConst K,
+                 double* __restrict__ energy, double* __restrict__ grad, void* __restrict__ hess_v) {
+    using HT = typename std::conditional<PREC == GIPC_FP64, double, float>::type;
+    HT* __restrict__ hess = static_cast<HT*>(hess_v);
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= T) return;
+    int32_t vid[4];
+    bool ok = true;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        vid[a] = __ldg(tets + a * T + t);
+        if (vid[a] < 0 || vid[a] >= n) ok = false;
+    }
+    if (!ok) {
+        if (energy) energy[t] = 0.0;
+        return;
+    }
+    double X[4][3];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int r = 0; r < 3; ++r) X[a][r] = __ldg(x + r * n + vid[a]);
+    double Dmi[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) Dmi[i][j] = __ldg(Dm_inv + (3 * i + j) * T + t);
+    const double k = K.scale * __ldg(vol + t);
+    // F = Ds Dm^-1
+    double F[3][3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        const double d0 = X[1][r] - X[0][r], d1 = X[2][r] - X[0][r], d2 = X[3][r] - X[0][r];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) F[r][c] = d0 * Dmi[0][c] + d1 * Dmi[1][c] + d2 * Dmi[2][c];
+    }
+    double I2 = 0.0;
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) I2 += F[r][c] * F[r][c];
+    double cof[3][3];  // cofactor matrix dJ/dF
+    {
+        double c0[3] = {F[0][0], F[1][0], F[2][0]}, c1[3] = {F[0][1], F[1][1], F[2][1]},
+               c2[3] = {F[0][2], F[1][2], F[2][2]}, t0[3], t1[3], t2[3];
+        cross(c1, c2, t0);
+        cross(c2, c0, t1);
+        cross(c0, c1, t2);
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            cof[r][0] = t0[r];
+            cof[r][1] = t1[r];
+            cof[r][2] = t2[r];
+        }
+    }
+    const double J = F[0][0] * cof[0][0] + F[1][0] * cof[1][0] + F[2][0] * cof[2][0];
+    const double ip1 = 1.0 / (I2 + 1.0);
+    const double Jm = J - K.alpha;
+    const double psi = 0.5 * K.mu * (I2 - 3.0) + 0.5 * K.lam * Jm * Jm - 0.5 * K.mu * log(I2 + 1.0);
+    const double m1 = K.mu * (1.0 - ip1);
+    // P = m1 F + lam (J - alpha) cof
+    double Pm[3][3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) Pm[r][c] = m1 * F[r][c] + K.lam * Jm * cof[r][c];
+    double g[12];
+    map_to_x(Pm, Dmi, g);
+    if (energy) energy[t] = k * psi;
+    if (grad) {
+#pragma unroll
+        for (int j = 0; j < 12; ++j) grad[j * T + t] = k * g[j];
+    }
+    if (!hess) return;
+
+    double U[3][3], s[3], V[3][3];
+    svd3(F, U, s, V);
+    double H[78];
+#pragma unroll
+    for (int q = 0; q < 78; ++q) H[q] = 0.0;
+    const double r2 = 0.70710678118654752440;
+    // twist / flip modes for the pairs (1,2), (0,2), (0,1)
+#pragma unroll
+    for (int kk = 0; kk < 3; ++kk) {
+        const int i = kk == 0 ? 1 : 0, j = kk == 2 ? 1 : 2;
+        const double lt = m1 + K.lam * Jm * s[kk];
+        const double lf = m1 - K.lam * Jm * s[kk];
+        double Qt[3][3], Qf[3][3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const double a = U[r][i] * V[c][j], b = U[r][j] * V[c][i];
+                Qt[r][c] = r2 * (a - b);
+                Qf[r][c] = r2 * (a + b);
+            }
+        add_mode<HT>(lt, Qt, Dmi, H);
+        add_mode<HT>(lf, Qf, Dmi, H);
+    }
+    // scaling modes: eigenpairs of A = d2 Psi / ds ds
+    {
+        double A[3][3];
+        const double ip2 = ip1 * ip1;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const int j = (i + 1) % 3, l = (i + 2) % 3;
+            A[i][i] = m1 + 2.0 * K.mu * s[i] * s[i] * ip2 + K.lam * (s[j] * s[l]) * (s[j] * s[l]);
+        }
+        const double sj = s[0] * s[1] * s[2];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = i + 1; j < 3; ++j) {
+                const int l = 3 - i - j;
+                A[i][j] = A[j][i] = 2.0 * K.mu * s[i] * s[j] * ip2 + K.lam * s[l] * (2.0 * sj - K.alpha);
+            }
+        double Avec[3][3];
+        jacobi3(A, Avec);
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+            double Q[3][3];
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    Q[r][c] = U[r][0] * Avec[0][m] * V[c][0] + U[r][1] * Avec[1][m] * V[c][1] + U[r][2] * Avec[2][m] * V[c][2];
+            add_mode<HT>(A[m][m], Q, Dmi, H);
+        }
+    }
+    int idx = 0;
+#pragma unroll
+    for (int a = 0; a < 12; ++a)
+#pragma unroll
+        for (int b = 0; b <= a; ++b) {
+            const HT h = (HT)(k * H[idx++]);
+            hess[(int64_t)(a * 12 + b) * T + t] = h;
+            if (a != b) hess[(int64_t)(b * 12 + a) * T + t] = h;
+        }
+}
+
+// Rest state: Dm^-1 (row-major, entry-major [9][T]) and volume |det Dm| / 6.
+__global__ void tet_rest_kernel(const double* __restrict__ x, int64_t n, const int32_t* __restrict__ tets,
+                                int64_t T, double* __restrict__ Dm_inv, double* __restrict__ vol,
+                                int32_t* __restrict__ bad) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= T) return;
+    int32_t v[4];
+    bool ok = true;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        v[a] = tets[a * T + t];
+        if (v[a] < 0 || v[a] >= n) ok = false;
+    }
+    double m[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+    if (ok) {
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) m[r][c] = x[r * n + v[c + 1]] - x[r * n + v[0]];
+    }
+    const double A = m[1][1] * m[2][2] - m[1][2] * m[2][1];
+    const double B = m[1][2] * m[2][0] - m[1][0] * m[2][2];
+    const double C = m[1][0] * m[2][1] - m[1][1] * m[2][0];
+    const double det = m[0][0] * A + m[0][1] * B + m[0][2] * C;
+    if (!ok || det == 0.0 || !isfinite(det)) {
+        atomicAdd(bad, 1);
+#pragma unroll
+        for (int q = 0; q < 9; ++q) Dm_inv[q * T + t] = 0.0;
+        vol[t] = 0.0;
+        return;
+    }
+    const double id = 1.0 / det;
+    const double inv[9] = {A * id, (m[0][2] * m[2][1] - m[0][1] * m[2][2]) * id, (m[0][1] * m[1][2] - m[0][2] * m[1][1]) * id,
+                           B * id, (m[0][0] * m[2][2] - m[0][2] * m[2][0]) * id, (m[0][2] * m[1][0] - m[0][0] * m[1][2]) * id,
+                           C * id, (m[0][1] * m[2][0] - m[0][0] * m[2][1]) * id, (m[0][0] * m[1][1] - m[0][1] * m[1][0]) * id};
+#pragma unroll
+    for (int q = 0; q < 9; ++q) Dm_inv[q * T + t] = inv[q];
+    vol[t] = fabs(det) / 6.0;
+}
+
+// Lumped mass, deterministic: incident tetrahedra of each vertex are collected, sorted by
+// index and summed in that order (density * vol / 4 each).
+__global__ void mass_count_kernel(const int32_t* __restrict__ tets, int64_t T, int64_t n, int32_t* __restrict__ cnt) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= T) return;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int32_t v = tets[a * T + t];
+        if (v >= 0 && v < n) atomicAdd(cnt + v, 1);
+    }
+}
+
+__global__ void mass_fill_kernel(const int32_t* __restrict__ tets, int64_t T, int64_t n, const int64_t* __restrict__ start,
+                                 unsigned long long* __restrict__ cursor, int32_t* __restrict__ list) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= T) return;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int32_t v = tets[a * T + t];
+        if (v >= 0 && v < n) list[start[v] + (int64_t)atomicAdd(cursor + v, 1ull)] = (int32_t)t;
+    }
+}
+
+__global__ void mass_sum_kernel(const int64_t* __restrict__ start, int32_t* __restrict__ list, const double* __restrict__ vol,
+                                double density, int64_t n, double* __restrict__ mass) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    const int64_t s0 = start[v], s1 = start[v + 1];
+    for (int64_t i = s0 + 1; i < s1; ++i) {  // insertion sort of the (short) incidence list
+        const int32_t key = list[i];
+        int64_t j = i - 1;
+        while (j >= s0 && list[j] > key) {
+            list[j + 1] = list[j];
+            --j;
+        }
+        list[j + 1] = key;
+    }
+    double m = 0.0;
+    for (int64_t i = s0; i < s1; ++i) m = __dadd_rn(m, __ddiv_rn(__dmul_rn(density, vol[list[i]]), 4.0));
+    mass[v] = m;
+}
+
+__global__ void zero_cursor_kernel(unsigned long long* __restrict__ c, int32_t* __restrict__ cnt, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        c[i] = 0ull;
+        cnt[i] = 0;
+    }
+}
+
+inline unsigned nb(int64_t w, int t) { return (unsigned)((w + t - 1) / t); }
+
+}  // namespace
+}  // namespace gipc
+
+extern "C" gipc_status gipc_snh_params(double young, double poisson, double* mu_h, double* lambda_h) {
+    if (!mu_h || !lambda_h || !(young > 0.0) || !(poisson > -1.0 && poisson < 0.5))
+        return gipc::fail(GIPC_ERR_INVALID_ARG, "gipc_snh_params: need E > 0, -1 < nu < 0.5 and outputs");
+    const double mu_l = young / (2.0 * (1.0 + poisson));
+    const double lam_l = young * poisson / ((1.0 + poisson) * (1.0 - 2.0 * poisson));
+    *mu_h = 4.0 / 3.0 * mu_l;
+    *lambda_h = lam_l + 5.0 / 6.0 * mu_l;
+    return GIPC_OK;
+}
+
+extern "C" gipc_status gipc_tet_rest(gipc_ctx* ctx, const double* rest_x, int64_t n, const int32_t* tets, int64_t T,
+                                     double density, double* Dm_inv, double* vol, double* mass, void* stream) {
+    using namespace gipc;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (n < 0 || T < 0) return fail(GIPC_ERR_INVALID_ARG, "gipc_tet_rest: negative size");
+    if (mass && (!ctx || !(density > 0.0))) return fail(GIPC_ERR_INVALID_ARG, "gipc_tet_rest: mass needs a context and density > 0");
+    if (T > 0 && (!rest_x || !tets || !Dm_inv || !vol)) return fail(GIPC_ERR_INVALID_ARG, "gipc_tet_rest: null pointer");
+    gipc_status s;
+    if (!ctx && T > 0) return fail(GIPC_ERR_INVALID_ARG, "gipc_tet_rest: null context");
+    if (T > 0) {
+        if ((s = ctx->slot[0].reserve(sizeof(int32_t) * 4)) != GIPC_OK) return s;
+        int32_t* bad = ctx->slot[0].as<int32_t>();
+        cudaMemsetAsync(bad, 0, sizeof(int32_t), st);
+        tet_rest_kernel<<<nb(T, 128), 128, 0, st>>>(rest_x, n, tets, T, Dm_inv, vol, bad);
+        int32_t hbad = 0;
+        cudaMemcpyAsync(&hbad, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+        if (cudaStreamSynchronize(st) != cudaSuccess) return check_launch("gipc_tet_rest");
+        if (hbad) return fail(GIPC_ERR_INVALID_ARG, "gipc_tet_rest: %d degenerate or out-of-range tetrahedra", hbad);
+    }
+    if (mass && n > 0) {
+        const int64_t links = 4 * T;
+        if ((s = ctx->slot[1].reserve(sizeof(int32_t) * (n + 1) + 16)) != GIPC_OK) return s;
+        if ((s = ctx->slot[2].reserve(sizeof(int64_t) * (n + 2 + scan_scratch_words(n + 1)) + sizeof(unsigned long long) * n)) != GIPC_OK) return s;
+        if ((s = ctx->slot[3].reserve(sizeof(int32_t) * (links + 1))) != GIPC_OK) return s;
+        int32_t* cnt = ctx->slot[1].as<int32_t>();
+        int64_t* start = ctx->slot[2].as<int64_t>();
+        int64_t* scan_tmp = start + n + 2;
+        unsigned long long* cursor = reinterpret_cast<unsigned long long*>(scan_tmp + scan_scratch_words(n + 1));
+        int32_t* list = ctx->slot[3].as<int32_t>();
+        zero_cursor_kernel<<<nb(n, 256), 256, 0, st>>>(cursor, cnt, n);
+        if (T > 0) mass_count_kernel<<<nb(T, 256), 256, 0, st>>>(tets, T, n, cnt);
+        if (exclusive_scan<int32_t>(cnt, start, n, scan_tmp, st) != cudaSuccess) return check_launch("gipc_tet_rest: scan");
+        if (T > 0) mass_fill_kernel<<<nb(T, 256), 256, 0, st>>>(tets, T, n, start, cursor, list);
+        mass_sum_kernel<<<nb(n, 256), 256, 0, st>>>(start, list, vol, density, n, mass);
+    }
+    return check_launch("gipc_tet_rest");
+}
+
+extern "C" gipc_status gipc_eval_tets(const double* x, int64_t n, const int32_t* tets, int64_t T, const double* Dm_inv,
+                                      const double* vol, const gipc_elastic_params* prm, int prec, double* energy,
+                                      double* grad, void* hess, void* stream) {
+    using namespace gipc;
+    if (n < 0 || T < 0) return fail(GIPC_ERR_INVALID_ARG, "gipc_eval_tets: negative size");
+    if (!prm || !(prm->mu > 0.0) || !(prm->lambda > 0.0) || !(prm->scale >= 0.0))
+        return fail(GIPC_ERR_INVALID_ARG, "gipc_eval_tets: need mu > 0, lambda > 0, scale >= 0");
+    if (prec != GIPC_FP64 && prec != GIPC_MIXED) return fail(GIPC_ERR_INVALID_ARG, "gipc_eval_tets: bad precision");
+    if (T == 0) return GIPC_OK;
+    if (!x || !tets || !Dm_inv || !vol) return fail(GIPC_ERR_INVALID_ARG, "gipc_eval_tets: null input");
+    ElasticConst K{prm->mu, prm->lambda, 1.0 + prm->mu / prm->lambda - prm->mu / (4.0 * prm->lambda), prm->scale};
+    cudaStream_t st = (cudaStream_t)stream;
+    if (prec == GIPC_FP64) eval_tets_kernel<GIPC_FP64><<<nb(T, 128), 128, 0, st>>>(x, n, tets, T, Dm_inv, vol, K, energy, grad, hess);
+    else eval_tets_kernel<GIPC_MIXED><<<nb(T, 128), 128, 0, st>>>(x, n, tets, T, Dm_inv, vol, K, energy, grad, hess);
+    return check_launch("gipc_eval_tets");
+}

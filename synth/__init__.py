@@ -431,3 +431,49 @@ def random_elements(n, k, T, seed=7, mix=DEFAULT_MIX, hub=None, hub_count=0):
         "tet_grad": rng.normal(size=(12, T)), "mass": rng.uniform(0.5, 1.5, n),
         "grad_base": rng.normal(size=(3, n)),
     }
+
+
+# ----------------------------------------------------------------------------- tetrahedral meshes
+_KUHN = [(0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)]
+
+
+def tet_box(nx, ny, nz, spacing=1.0, origin=(0.0, 0.0, 0.0)):
+    """Vertex grid nx x ny x nz split into 6 tetrahedra per cell (Freudenthal/Kuhn split along
+    the cell diagonal), every tetrahedron positively oriented.
+
+    Returns (x (3, n) float64, tets (4, T) int32); vertex (i, j, k) has id (i*ny + j)*nz + k."""
+    I, Jg, K = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij")
+    x = np.stack([I.ravel() * spacing + origin[0], Jg.ravel() * spacing + origin[1],
+                  K.ravel() * spacing + origin[2]]).astype(np.float64)
+    vid = lambda i, j, k: (i * ny + j) * nz + k
+    ci, cj, ck = np.meshgrid(np.arange(nx - 1), np.arange(ny - 1), np.arange(nz - 1), indexing="ij")
+    ci, cj, ck = ci.ravel(), cj.ravel(), ck.ravel()
+    tets = []
+    for perm in _KUHN:
+        p = [np.array([ci, cj, ck])]
+        cur = p[0].copy()
+        for ax in perm:
+            cur = cur.copy()
+            cur[ax] += 1
+            p.append(cur)
+        v = [vid(q[0], q[1], q[2]) for q in p]
+        odd = sum(1 for a in range(3) for b in range(a + 1, 3) if perm[a] > perm[b]) % 2
+        if odd:
+            v[1], v[2] = v[2], v[1]
+        tets.append(np.stack(v))
+    T = np.concatenate(tets, axis=1).astype(np.int32)
+    # make every element positively oriented
+    P = [x[:, T[a]] for a in range(4)]
+    det = np.einsum("ij,ij->j", P[1] - P[0], np.cross((P[2] - P[0]).T, (P[3] - P[0]).T).T)
+    flip = det < 0
+    T[1, flip], T[2, flip] = T[2, flip].copy(), T[1, flip].copy()
+    return x, np.ascontiguousarray(T)
+
+
+def deform(x, seed, amplitude=0.05, jitter=0.01):
+    """Smooth random deformation plus jitter (for elasticity tests); same shape as x."""
+    rng = np.random.default_rng(seed)
+    A = np.eye(3) + amplitude * rng.normal(size=(3, 3))
+    k = rng.normal(size=(3, 3)) * 2.0
+    y = A @ x + amplitude * np.sin(k @ x) + jitter * rng.normal(size=x.shape) * (np.ptp(x) / 50 + 1e-12)
+    return np.ascontiguousarray(y)
