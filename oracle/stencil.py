@@ -134,7 +134,9 @@ def eval_stencil(typ, pts, eps_x, dhat, kappa, d_thr_ratio=0.1):
               + lam8p * np.outer(_vec(Q8p), _vec(Q8p)))         # Eq. 36
         dbdJ = bt_gam * 2.0 * J @ N_gam + bt_g * 2.0 * J @ N_g  # Eq. 30 with Eq. 14
         dJdx = np.zeros((3, 3, n))
-        dJdx[1, 1, :] = dc / (2.0 * sc)                        # d sqrt(c)/dx
+        # d sqrt(c)/dx; at exactly parallel edges (c = 0) sqrt(c) is not differentiable and the
+        # mollified energy, its gradient and Hessian all vanish (e(0) = 0): take it as 0 (reading)
+        dJdx[1, 1, :] = dc / (2.0 * sc) if sc > 0.0 else 0.0
         dJdx[2, 2, :] = grad_f
         grad, hess, D = _project(dJdx, dbdJ, HJ)
         lam, w = lam8p, D.T @ _vec(Q8p)

@@ -477,3 +477,95 @@ def deform(x, seed, amplitude=0.05, jitter=0.01):
     k = rng.normal(size=(3, 3)) * 2.0
     y = A @ x + amplitude * np.sin(k @ x) + jitter * rng.normal(size=x.shape) * (np.ptp(x) / 50 + 1e-12)
     return np.ascontiguousarray(y)
+
+
+# ----------------------------------------------------------------------------- scenes
+def surface_lists(x, tets):
+    """Boundary of a tetrahedral mesh: triangles (3, m) oriented outward, edges (2, e) with a < b,
+    and boundary vertices (v,); all int32, sorted canonically (triangles by their sorted vertex
+    triple, edges lexicographically, vertices ascending)."""
+    T = tets.shape[1]
+    tt = tets.T.astype(np.int64)
+    opp_idx = [(1, 2, 3, 0), (0, 2, 3, 1), (0, 1, 3, 2), (0, 1, 2, 3)]   # face vertices + opposite
+    F = np.concatenate([tt[:, list(o[:3])] for o in opp_idx])             # (4T, 3)
+    O = np.concatenate([tt[:, o[3]] for o in opp_idx])                    # opposite vertex
+    key = np.sort(F, axis=1)
+    _, inv, cnt = np.unique(key, axis=0, return_inverse=True, return_counts=True)
+    b = cnt[inv.ravel()] == 1
+    F, O, key = F[b], O[b], key[b]
+    nrm = np.cross(x[:, F[:, 1]].T - x[:, F[:, 0]].T, x[:, F[:, 2]].T - x[:, F[:, 0]].T)
+    inward = np.einsum("ij,ij->i", nrm, x[:, O].T - x[:, F[:, 0]].T) > 0
+    F[inward, 1], F[inward, 2] = F[inward, 2].copy(), F[inward, 1].copy()
+    order = np.lexsort((key[:, 2], key[:, 1], key[:, 0]))
+    tris = F[order].T
+    E = np.concatenate([tris[[0, 1]], tris[[1, 2]], tris[[2, 0]]], axis=1)
+    E = np.unique(np.sort(E, axis=0), axis=1)
+    verts = np.unique(tris.ravel())
+    return (np.ascontiguousarray(tris.astype(np.int32)), np.ascontiguousarray(E.astype(np.int32)),
+            np.ascontiguousarray(verts.astype(np.int32)))
+
+
+def _merge(parts):
+    xs, ts, off = [], [], 0
+    for x, t in parts:
+        xs.append(x)
+        ts.append(t + off)
+        off += x.shape[1]
+    return np.ascontiguousarray(np.concatenate(xs, axis=1)), np.ascontiguousarray(np.concatenate(ts, axis=1).astype(np.int32))
+
+
+def two_cubes(gap=0.5, velocity=-2.0):
+    """Two unit cubes, 5x5x5 vertices (125 verts, 384 tets) each; the top one `gap` above the
+    bottom one moving at `velocity` in z; the bottom face z = 0 is fixed.
+    Returns dict(x, v, tets, fixed, tris, edges, verts, l)."""
+    xa, ta = tet_box(5, 5, 5, spacing=0.25)
+    xb, tb = tet_box(5, 5, 5, spacing=0.25, origin=(0.0, 0.0, 1.0 + gap))
+    x, tets = _merge([(xa, ta), (xb, tb)])
+    n = x.shape[1]
+    v = np.zeros((3, n))
+    v[2, 125:] = velocity
+    fixed = np.zeros(n, np.uint8)
+    fixed[:125][xa[2] == 0.0] = 1
+    tris, edges, verts = surface_lists(x, tets)
+    l = float(np.linalg.norm(x.max(axis=1) - x.min(axis=1)))
+    return {"x": x, "v": v, "tets": tets, "fixed": fixed, "tris": tris, "edges": edges, "verts": verts, "l": l}
+
+
+def ball(radius=0.1, cells=14, center=(0.0, 0.0, 0.0)):
+    """Voxel ball: the Freudenthal grid of the bounding cube with `cells` cells per side, keeping
+    the tetrahedra whose centroid lies inside the sphere; unused vertices dropped."""
+    h = 2.0 * radius / cells
+    x, t = tet_box(cells + 1, cells + 1, cells + 1, spacing=h, origin=tuple(c - radius for c in center))
+    cen = (x[:, t[0]] + x[:, t[1]] + x[:, t[2]] + x[:, t[3]]) / 4.0
+    keep = np.linalg.norm(cen - np.asarray(center)[:, None], axis=0) <= radius
+    t = t[:, keep]
+    used = np.unique(t)
+    remap = -np.ones(x.shape[1], np.int64)
+    remap[used] = np.arange(len(used))
+    return np.ascontiguousarray(x[:, used]), np.ascontiguousarray(remap[t].astype(np.int32))
+
+
+def sphere_grid(nx=8, ny=8, radius=0.1, cells=14, gap=1e-3):
+    """nx x ny balls of `radius` on a floor (z = 0, two fixed triangles spanning the grid), neighbours
+    and floor `gap` apart.  The floor is a fixed thin tetrahedral slab so every primitive comes from
+    a tetrahedral mesh.  Returns the same dict as two_cubes."""
+    parts = []
+    pitch = 2 * radius + gap
+    for i in range(nx):
+        for j in range(ny):
+            parts.append(ball(radius, cells, center=(i * pitch, j * pitch, radius + gap)))
+    lo, hi = -radius - 0.05, (max(nx, ny) - 1) * pitch + radius + 0.05
+    slab_x, slab_t = tet_box(2, 2, 2, spacing=1.0)
+    slab_x = slab_x.copy()
+    slab_x[0] = lo + slab_x[0] * (hi - lo)
+    slab_x[1] = lo + slab_x[1] * (hi - lo)
+    slab_x[2] = -0.05 + slab_x[2] * 0.05
+    parts.append((slab_x, slab_t))
+    x, tets = _merge(parts)
+    n = x.shape[1]
+    fixed = np.zeros(n, np.uint8)
+    fixed[n - slab_x.shape[1]:] = 1
+    tris, edges, verts = surface_lists(x, tets)
+    l = float(np.linalg.norm(x.max(axis=1) - x.min(axis=1)))
+    return {"x": x, "v": np.zeros((3, n)), "tets": tets, "fixed": fixed, "tris": tris, "edges": edges,
+            "verts": verts, "l": l}
