@@ -310,6 +310,116 @@ gipc_status gipc_pcg_noalloc(const gipc_bsr* A_h, const double* rhs, double* x, 
                              const gipc_pcg_params* prm_h, int* iters_out_h, double* rel_out_h,
                              void* stream);
 
+/* ------------------------------------------------------------------ contacts */
+
+/* The collision surface: device arrays of vertex ids. */
+typedef struct {
+    const int32_t* tris;   /* int32 [3][ntri] surface triangles                        */
+    int64_t ntri;
+    const int32_t* edges;  /* int32 [2][nedge] surface edges                            */
+    int64_t nedge;
+    const int32_t* verts;  /* int32 [nvert] surface vertices                            */
+    int64_t nvert;
+} gipc_surface;
+
+/* The contact stencils of the barrier at positions x (paper Eq. 3 over the
+ * point-triangle pairs of Eq. 4 and the edge-edge pairs of Eq. 5).
+ *
+ * A pair is a surface vertex and a surface triangle not containing it, or two
+ * surface edges i < j without a shared vertex.  Every pair whose distance is
+ * below dhat yields one stencil, typed by the closest features of its
+ * constrained minimum (interior, point-edge or point-point; Sec. 3.1) and
+ * encoded as in Sec. 7.2.  Edge-edge pairs whose parallel measure
+ * c = |(a1-a0) x (b1-b0)|^2 is below eps_x (Sec. 6.1, computed from rest_x)
+ * take the nearly-parallel types.  Pairs are screened by bounding boxes padded
+ * by dhat (1 + 1e-9); the distance test and classification are float64 IEEE
+ * operations in a fixed order without contraction.
+ *
+ *   x, rest_x  float64 [3][n]
+ *   stencils   int32 [4][capacity] out: the first *count_h columns
+ *   eps_x      float64 [capacity] out: 0 for point-triangle pairs,
+ *              1e-3 |a1-a0|^2 |b1-b0|^2 at rest for edge-edge pairs
+ *   count_h    host out: number of contacts
+ * Order: point-triangle pairs by (surface-vertex position in verts, triangle),
+ * then edge-edge pairs by (i, j); identical on every run.  Synchronises the
+ * stream once (to read the count).  Errors: GIPC_ERR_INVALID_ARG;
+ * GIPC_ERR_CAPACITY when *count_h > capacity (nothing is written; *count_h
+ * holds the required size); GIPC_ERR_OOM; GIPC_ERR_CUDA. */
+gipc_status gipc_find_contacts(gipc_ctx* ctx, const double* x, const double* rest_x, int64_t n,
+                               const gipc_surface* srf_h, double dhat, int32_t* stencils, double* eps_x,
+                               int64_t capacity, int64_t* count_h, void* stream);
+
+/* Largest feasible step along d (paper Alg. 1, "maxFeasibleStepSize"):
+ * alpha = min(1, min over pairs of the additive-CCD time of the motion x -> x + d).
+ * Every point-triangle and edge-edge pair (as in gipc_find_contacts) whose swept
+ * bounding boxes overlap is advanced conservatively with its common translation
+ * removed: first step (1 - slack) d0 / l_p, then 0.9 d / l_p, stopping once the
+ * distance falls below slack * d0 (d0 the initial distance, l_p the bound on
+ * the relative motion).  Result in [0, 1] on the host.  Synchronises the stream.
+ *   x, d   float64 [3][n];  slack in (0, 1) (0.1 is the usual value)
+ * Errors: GIPC_ERR_INVALID_ARG; GIPC_ERR_OOM; GIPC_ERR_CUDA. */
+gipc_status gipc_ccd_max_step(gipc_ctx* ctx, const double* x, const double* d, int64_t n,
+                              const gipc_surface* srf_h, double slack, double* alpha_h, void* stream);
+
+/* ------------------------------------------------------------------ time step */
+
+/* A simulated scene: tetrahedral meshes, their surface and the fixed vertices.
+ * All arrays are device arrays the caller keeps alive during a step. */
+typedef struct {
+    int64_t n;                /* vertices                                               */
+    const double* rest_x;     /* float64 [3][n] rest positions (eps_x of edge pairs)    */
+    const int32_t* tets;      /* int32 [4][T]                                           */
+    int64_t T;
+    const double* Dm_inv;     /* float64 [9][T] from gipc_tet_rest                      */
+    const double* vol;        /* float64 [T]                                            */
+    const double* mass;       /* float64 [n] lumped masses                              */
+    const uint8_t* fixed;     /* uint8 [n] (nonzero: prescribed, kept in place) or NULL */
+    gipc_surface surface;
+    double l;                 /* length of the scene's bounding-box diagonal            */
+} gipc_scene;
+
+typedef struct {
+    double dt;               /* time step                                                    */
+    double gravity[3];       /* body acceleration                                            */
+    gipc_elastic_params elastic;  /* scale is ignored (dt^2 is used)                         */
+    gipc_barrier_params barrier;
+    double eps_d;            /* stop when max|d| / (l dt) <= eps_d                           */
+    double pcg_tol;          /* gipc_pcg_params.rel_tol of each Newton solve                 */
+    int max_pcg;             /* PCG iteration cap per Newton iteration                       */
+    int max_newton;          /* Newton iteration cap                                         */
+    int max_ls;              /* line-search trials per Newton iteration                      */
+    int prec;                /* GIPC_FP64 or GIPC_MIXED (Hessian storage and SpMV)           */
+    int hess_mode;           /* GIPC_HESS_DENSE or GIPC_HESS_RANK1 for the contact stencils  */
+} gipc_step_params;
+
+typedef struct {
+    int newton_iters;        /* Newton iterations taken                                     */
+    int pcg_iters;           /* PCG iterations summed over the Newton iterations            */
+    int ls_trials;           /* line-search energy evaluations summed                       */
+    int converged;           /* 1 if the eps_d test ended the loop                          */
+    int64_t contacts;        /* contact stencils at the final positions                     */
+    double energy;           /* incremental potential at the final positions                */
+    double last_alpha;       /* step length of the last Newton iteration                    */
+} gipc_step_stats;
+
+/* One implicit time step by projected Newton (paper Alg. 1) on the incremental
+ * potential (Sec. 3.1, Eq. 1-2):
+ *   I(x) = 1/2 (x - xt)^T M (x - xt) + dt^2 sum_T vol Psi(F) + kappa sum_k b_k(x),
+ *   xt = x^t + dt v^t + dt^2 gravity (fixed vertices: xt = x^t).
+ * Each iteration: contacts at x; g and H = M + PSD-projected Hessians assembled
+ * into a BSR matrix; d from the modified PCG (fixed vertices filtered; a solve
+ * that reaches max_pcg is used as it is); alpha = gipc_ccd_max_step(x, d, 0.1);
+ * backtracking alpha /= 2 until I(x + alpha d) <= I(x), contacts re-detected at
+ * each trial (after max_ls trials the last one is kept); stop when
+ * max|d| / (l dt) <= eps_d or after max_newton iterations.
+ *   x  float64 [3][n]: x^t in, x^{t+1} out
+ *   v  float64 [3][n]: v^t in, (x^{t+1} - x^t) / dt out
+ * Synchronises the stream several times per iteration.  Scratch is owned by ctx.
+ * Errors: GIPC_ERR_INVALID_ARG; GIPC_ERR_NONFINITE; GIPC_ERR_OOM; GIPC_ERR_CUDA;
+ * GIPC_ERR_CAPACITY (a matrix row with more than 8192 contributions). */
+gipc_status gipc_newton_step(gipc_ctx* ctx, const gipc_scene* sc_h, double* x, double* v,
+                             const gipc_step_params* prm_h, gipc_step_stats* stats_h, void* stream);
+
 /* ------------------------------------------------------------------ profiling */
 
 /* Kernels that a context can time with CUDA events on the stream they are

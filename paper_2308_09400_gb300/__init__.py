@@ -15,7 +15,8 @@ from ._abi import (FLAG_ACTIVE, FLAG_FILTERED, FLAG_INVALID, FLAG_MOLLIFIED, Gip
 TYPE_IDS = {"PT": 0, "EE": 1, "PE": 2, "PP": 3, "EE_PAR": 4, "PE_PAR": 5, "PP_PAR": 6}
 NULL_INDEX = -2147483648
 
-__all__ = ["compute_eps_x", "eval_stencils", "assemble_bsr", "pcg", "pcg_noalloc", "snh_params", "tet_rest", "eval_tets", "Context", "default_context", "GipcError", "FLAG_ACTIVE", "FLAG_FILTERED",
+__all__ = ["compute_eps_x", "eval_stencils", "assemble_bsr", "pcg", "pcg_noalloc", "snh_params", "tet_rest", "eval_tets",
+           "Surface", "find_contacts", "ccd_max_step", "Scene", "newton_step", "Context", "default_context", "GipcError", "FLAG_ACTIVE", "FLAG_FILTERED",
            "FLAG_MOLLIFIED", "FLAG_INVALID", "TYPE_IDS", "NULL_INDEX"]
 
 
@@ -290,3 +291,103 @@ def eval_tets(x, tets, Dm_inv, vol, mu, lam, scale, precision="fp64", want=("ene
     _abi.call("gipc_eval_tets", _ptr(x), n, _ptr(tets), T, _ptr(Dm_inv), _ptr(vol), ctypes.byref(prm), prec,
               _ptr(out.get("energy")), _ptr(out.get("grad")), _ptr(out.get("hess")), _stream(stream))
     return out
+
+
+# ------------------------------------------------------------------------- contacts and time step
+class Surface:
+    """Collision surface: tris int32 [3, m], edges int32 [2, e], verts int32 [v] (CUDA tensors)."""
+
+    def __init__(self, tris, edges, verts):
+        _check(tris, "tris", torch.int32, 3)
+        _check(edges, "edges", torch.int32, 2)
+        _check(verts, "verts", torch.int32)
+        self.tris, self.edges, self.verts = tris, edges, verts
+
+    def struct(self):
+        return _abi.Surface(self.tris.data_ptr(), self.tris.shape[1], self.edges.data_ptr(), self.edges.shape[1],
+                            self.verts.data_ptr(), self.verts.shape[0])
+
+
+def find_contacts(x, rest_x, surface, dhat, capacity=None, ctx=None, stream=None):
+    """Contact stencils int32 [4, k] and eps_x [k] at positions x (gipc_find_contacts)."""
+    ctx = ctx or default_context()
+    _check(x, "x", torch.float64, 3)
+    _check(rest_x, "rest_x", torch.float64, 3)
+    n = x.shape[1]
+    srf = surface.struct()
+    cap = 4096 if capacity is None else int(capacity)
+    for _ in range(2):
+        st = torch.empty((4, max(cap, 1)), dtype=torch.int32, device=x.device)
+        eps = torch.empty(max(cap, 1), dtype=torch.float64, device=x.device)
+        cnt = ctypes.c_int64(0)
+        s = _abi.call_status("gipc_find_contacts", ctx.handle, _ptr(x), _ptr(rest_x), n, ctypes.byref(srf),
+                             float(dhat), _ptr(st), _ptr(eps), cap, ctypes.byref(cnt), _stream(stream))
+        if s == _abi.GIPC_OK:
+            k = cnt.value
+            return st[:, :k].contiguous(), eps[:k].clone()
+        if s != _abi.GIPC_ERR_CAPACITY or capacity is not None:
+            raise GipcError("gipc_find_contacts", s)
+        cap = cnt.value
+    raise GipcError("gipc_find_contacts", s)
+
+
+def ccd_max_step(x, d, surface, slack=0.1, ctx=None, stream=None):
+    """Largest feasible step in [0, 1] along d by additive CCD (gipc_ccd_max_step)."""
+    ctx = ctx or default_context()
+    _check(x, "x", torch.float64, 3)
+    _check(d, "d", torch.float64, 3)
+    a = ctypes.c_double(0.0)
+    srf = surface.struct()
+    _abi.call("gipc_ccd_max_step", ctx.handle, _ptr(x), _ptr(d), x.shape[1], ctypes.byref(srf), float(slack),
+              ctypes.byref(a), _stream(stream))
+    return a.value
+
+
+class Scene:
+    """Device-resident scene of tetrahedral meshes for newton_step.
+
+    ``x`` float64 [3, n] rest (= initial) positions, ``tets`` int32 [4, T], ``surface`` a Surface,
+    ``fixed`` bool/uint8 [n] or None, ``l`` the bounding-box diagonal (computed if None)."""
+
+    def __init__(self, rest_x, tets, surface, density, fixed=None, l=None, ctx=None):
+        _check(rest_x, "rest_x", torch.float64, 3)
+        self.rest_x = rest_x
+        self.tets = tets
+        self.surface = surface
+        self.Dm_inv, self.vol, self.mass = tet_rest(rest_x, tets, density, ctx=ctx)
+        n = rest_x.shape[1]
+        self.fixed = (fixed.to(device=rest_x.device, dtype=torch.uint8).contiguous() if fixed is not None
+                      else None)
+        if l is None:
+            ext = rest_x.max(dim=1).values - rest_x.min(dim=1).values
+            l = float(torch.linalg.norm(ext))
+        self.l = float(l)
+        self.n = n
+
+    def struct(self):
+        return _abi.Scene(self.n, self.rest_x.data_ptr(), self.tets.data_ptr(), self.tets.shape[1],
+                          self.Dm_inv.data_ptr(), self.vol.data_ptr(), self.mass.data_ptr(),
+                          self.fixed.data_ptr() if self.fixed is not None else None, self.surface.struct(), self.l)
+
+
+def newton_step(scene, x, v, dt, mu, lam, dhat, kappa, gravity=(0.0, 0.0, -9.81), d_thr_ratio=0.1, eps_d=1e-2,
+                pcg_tol=1e-4, max_pcg=500, max_newton=50, max_ls=30, precision="fp64", hess_mode="dense",
+                ctx=None, stream=None):
+    """One implicit time step; updates x and v in place and returns a stats dict (gipc_newton_step)."""
+    ctx = ctx or default_context()
+    _check(x, "x", torch.float64, 3)
+    _check(v, "v", torch.float64, 3)
+    prm = _abi.StepParams()
+    prm.dt = float(dt)
+    prm.gravity[:] = [float(g) for g in gravity]
+    prm.elastic = _abi.ElasticParams(float(mu), float(lam), 0.0)
+    prm.barrier = _abi.BarrierParams(float(dhat), float(kappa), float(d_thr_ratio))
+    prm.eps_d, prm.pcg_tol = float(eps_d), float(pcg_tol)
+    prm.max_pcg, prm.max_newton, prm.max_ls = int(max_pcg), int(max_newton), int(max_ls)
+    prm.prec = {"fp64": _abi.GIPC_FP64, "mixed": _abi.GIPC_MIXED}[precision]
+    prm.hess_mode = {"dense": _abi.GIPC_HESS_DENSE, "rank1": _abi.GIPC_HESS_RANK1}[hess_mode]
+    stats = _abi.StepStats()
+    sc = scene.struct()
+    _abi.call("gipc_newton_step", ctx.handle, ctypes.byref(sc), _ptr(x), _ptr(v), ctypes.byref(prm),
+              ctypes.byref(stats), _stream(stream))
+    return {f: getattr(stats, f) for f, _ in _abi.StepStats._fields_}

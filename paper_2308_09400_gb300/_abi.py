@@ -42,6 +42,31 @@ class PcgParams(ctypes.Structure):
     _fields_ = [("rel_tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("check_every", ctypes.c_int)]
 
 
+class Surface(ctypes.Structure):
+    _fields_ = [("tris", ctypes.c_void_p), ("ntri", ctypes.c_int64), ("edges", ctypes.c_void_p),
+                ("nedge", ctypes.c_int64), ("verts", ctypes.c_void_p), ("nvert", ctypes.c_int64)]
+
+
+class Scene(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("rest_x", ctypes.c_void_p), ("tets", ctypes.c_void_p),
+                ("T", ctypes.c_int64), ("Dm_inv", ctypes.c_void_p), ("vol", ctypes.c_void_p),
+                ("mass", ctypes.c_void_p), ("fixed", ctypes.c_void_p), ("surface", Surface),
+                ("l", ctypes.c_double)]
+
+
+class StepParams(ctypes.Structure):
+    _fields_ = [("dt", ctypes.c_double), ("gravity", ctypes.c_double * 3), ("elastic", ElasticParams),
+                ("barrier", BarrierParams), ("eps_d", ctypes.c_double), ("pcg_tol", ctypes.c_double),
+                ("max_pcg", ctypes.c_int), ("max_newton", ctypes.c_int), ("max_ls", ctypes.c_int),
+                ("prec", ctypes.c_int), ("hess_mode", ctypes.c_int)]
+
+
+class StepStats(ctypes.Structure):
+    _fields_ = [("newton_iters", ctypes.c_int), ("pcg_iters", ctypes.c_int), ("ls_trials", ctypes.c_int),
+                ("converged", ctypes.c_int), ("contacts", ctypes.c_int64), ("energy", ctypes.c_double),
+                ("last_alpha", ctypes.c_double)]
+
+
 class KernelTime(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
 
@@ -70,6 +95,11 @@ SIGNATURES = {
                         ctypes.POINTER(_INT), ctypes.POINTER(_D), _P]),
     "gipc_pcg_noalloc": (_INT, [ctypes.POINTER(Bsr), _P, _P, _P, ctypes.POINTER(PcgParams),
                                 ctypes.POINTER(_INT), ctypes.POINTER(_D), _P]),
+    "gipc_find_contacts": (_INT, [_P, _P, _P, _I64, ctypes.POINTER(Surface), _D, _P, _P, _I64,
+                                  ctypes.POINTER(_I64), _P]),
+    "gipc_ccd_max_step": (_INT, [_P, _P, _P, _I64, ctypes.POINTER(Surface), _D, ctypes.POINTER(_D), _P]),
+    "gipc_newton_step": (_INT, [_P, ctypes.POINTER(Scene), _P, _P, ctypes.POINTER(StepParams),
+                                ctypes.POINTER(StepStats), _P]),
     "gipc_profile_begin": (_INT, [_P]),
     "gipc_profile_read": (_INT, [_P, _INT, ctypes.POINTER(KernelTime)]),
     "gipc_profile_stop": (_INT, [_P]),

@@ -16,7 +16,7 @@ OBJDIR = os.path.join(os.path.dirname(HERE), "_build", "obj")
 LIB = os.path.join(LIBDIR, "libgipc.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2", "-Xcompiler", "-ffp-contract=off",
          "--expt-relaxed-constexpr"]
 
 

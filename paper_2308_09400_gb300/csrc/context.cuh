@@ -69,7 +69,7 @@ struct gipc_profiler {
 
 struct gipc_ctx {
     int device = 0;
-    static constexpr int kSlots = 16;
+    static constexpr int kSlots = 40;   // assembly 0-8, pcg 9-15, contacts 16-19 and 30-32, time step 20-29
     gipc_scratch slot[kSlots];
     gipc_profiler prof;
     void release_all() {

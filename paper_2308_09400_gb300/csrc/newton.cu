@@ -1,0 +1,347 @@
+// One implicit time step by projected Newton with CCD-filtered backtracking line search
+// (Alg. 1 on the incremental potential of Sec. 3.1, Eq. 1-2).
+//
+// The host drives the loop; every arithmetic step runs in the library's kernels: contact
+// detection and CCD (contact.cu), tetrahedron and stencil evaluation, BSR assembly, the
+// modified PCG, and the small vector kernels and deterministic reductions below.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "common.cuh"
+#include "context.cuh"
+
+namespace gipc {
+
+gipc_status find_contacts_impl(gipc_ctx* ctx, const double* x, const double* rest_x, int64_t n, const gipc_surface& srf,
+                               double dhat, int32_t* stencils, double* eps_x, int64_t cap, int64_t* count,
+                               bool compact, cudaStream_t st);
+gipc_status ccd_impl(gipc_ctx* ctx, const double* x, const double* d, int64_t n, const gipc_surface& srf, double slack,
+                     double* alpha, cudaStream_t st);
+
+namespace {
+
+enum NewtonSlot { N_VEC = 20, N_ST0 = 21, N_ST1 = 22, N_SEVAL = 23, N_TEVAL = 24, N_ENER = 25, N_ROW = 26,
+                  N_COL = 27, N_VAL = 28, N_RED = 29 };
+constexpr int kRedThreads = 256;
+constexpr int kRedBlocks = 512;   // partial sums per reduction (fixed: results do not depend on the device)
+
+inline unsigned nb(int64_t w, int t) { return (unsigned)std::max<int64_t>(1, (w + t - 1) / t); }
+
+// xt = x0 + dt v0 + dt^2 g on free vertices, x0 on fixed ones
+__global__ void inertia_target_kernel(const double* __restrict__ x0, const double* __restrict__ v0,
+                                      const uint8_t* __restrict__ fixed, int64_t n, double dt, double dt2g0,
+                                      double dt2g1, double dt2g2, double* __restrict__ xt) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const bool fx = fixed && fixed[i];
+    const double g[3] = {dt2g0, dt2g1, dt2g2};
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const double p = x0[q * n + i];
+        xt[q * n + i] = fx ? p : __dadd_rn(__dadd_rn(p, __dmul_rn(dt, v0[q * n + i])), g[q]);
+    }
+}
+
+// gbase = m (x - xt);  rhs is set to zero for the solver's initial guess elsewhere
+__global__ void grad_base_kernel(const double* __restrict__ x, const double* __restrict__ xt,
+                                 const double* __restrict__ m, int64_t n, double* __restrict__ gb) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= 3 * n) return;
+    gb[j] = __dmul_rn(m[j % n], __dsub_rn(x[j], xt[j]));
+}
+
+__global__ void negate_kernel(const double* __restrict__ a, int64_t m, double* __restrict__ b) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < m) b[j] = -a[j];
+}
+
+// x = xp + alpha d
+__global__ void axpy_kernel(const double* __restrict__ xp, const double* __restrict__ d, double alpha, int64_t m,
+                            double* __restrict__ x) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < m) x[j] = __dadd_rn(xp[j], __dmul_rn(alpha, d[j]));
+}
+
+// v = (x - x0) / dt
+__global__ void velocity_kernel(const double* __restrict__ x, const double* __restrict__ x0, double dt, int64_t m,
+                                double* __restrict__ v) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < m) v[j] = __ddiv_rn(__dsub_rn(x[j], x0[j]), dt);
+}
+
+__device__ __forceinline__ double block_reduce(double v, bool is_max) {
+    __shared__ double sh[kRedThreads / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double u = __shfl_xor_sync(0xffffffffu, v, o);
+        v = is_max ? fmax(v, u) : __dadd_rn(v, u);
+    }
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        v = threadIdx.x < kRedThreads / 32 ? sh[threadIdx.x] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double u = __shfl_xor_sync(0xffffffffu, v, o);
+            v = is_max ? fmax(v, u) : __dadd_rn(v, u);
+        }
+    }
+    return v;
+}
+
+// term kinds of the reductions
+enum RedKind { R_ARRAY = 0, R_INERTIA = 1, R_MAXABS = 2 };
+
+// Partial sums over fixed chunks: block b reduces [b*chunk, (b+1)*chunk) in a fixed pattern.
+__global__ void __launch_bounds__(kRedThreads)
+partial_reduce_kernel(int kind, const double* __restrict__ a, const double* __restrict__ b,
+                      const double* __restrict__ m, int64_t n, int64_t count, int64_t chunk,
+                      double* __restrict__ partial) {
+    const int64_t lo = (int64_t)blockIdx.x * chunk;
+    const int64_t hi = std::min(count, lo + chunk);
+    double acc = 0.0;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += kRedThreads) {
+        double t;
+        if (kind == R_ARRAY) {
+            t = a[i];
+            acc = __dadd_rn(acc, t);
+        } else if (kind == R_INERTIA) {
+            const double dx = __dsub_rn(a[i], b[i]), dy = __dsub_rn(a[n + i], b[n + i]),
+                         dz = __dsub_rn(a[2 * n + i], b[2 * n + i]);
+            t = __dmul_rn(m[i], __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)));
+            acc = __dadd_rn(acc, t);
+        } else {
+            acc = fmax(acc, fabs(a[i]));
+        }
+    }
+    acc = block_reduce(acc, kind == R_MAXABS);
+    if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+}
+
+__global__ void __launch_bounds__(kRedThreads)
+final_reduce_kernel(const double* __restrict__ partial, int np, bool is_max, double* __restrict__ out) {
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < np; i += kRedThreads) acc = is_max ? fmax(acc, partial[i]) : __dadd_rn(acc, partial[i]);
+    acc = block_reduce(acc, is_max);
+    if (threadIdx.x == 0) *out = acc;
+}
+
+// Enqueue a reduction of `count` terms into *out (device).
+void reduce(int kind, const double* a, const double* b, const double* m, int64_t n, int64_t count, double* partial,
+            double* out, cudaStream_t st) {
+    if (count <= 0) {
+        cudaMemsetAsync(out, 0, sizeof(double), st);
+        return;
+    }
+    const int64_t chunk = std::max<int64_t>(kRedThreads, (count + kRedBlocks - 1) / kRedBlocks);
+    const int np = (int)((count + chunk - 1) / chunk);
+    partial_reduce_kernel<<<np, kRedThreads, 0, st>>>(kind, a, b, m, n, count, chunk, partial);
+    final_reduce_kernel<<<1, kRedThreads, 0, st>>>(partial, np, kind == R_MAXABS, out);
+}
+
+struct ContactSet {
+    int slot;
+    int64_t cap = 0, k = 0;
+    int32_t* st = nullptr;
+    double* eps = nullptr;
+};
+
+struct Step {
+    gipc_ctx* ctx;
+    const gipc_scene& sc;
+    const gipc_step_params& prm;
+    cudaStream_t st;
+    int64_t n;
+    double *x0, *xt, *xp, *d, *g, *rhs, *gb;
+    double *partial, *res;
+    ContactSet set[2];
+
+    Step(gipc_ctx* c, const gipc_scene& s, const gipc_step_params& p, cudaStream_t q)
+        : ctx(c), sc(s), prm(p), st(q), n(s.n) {
+        set[0].slot = N_ST0;
+        set[1].slot = N_ST1;
+    }
+
+    gipc_status contacts(const double* x, ContactSet& cs) {
+        for (int attempt = 0; attempt < 2; ++attempt) {
+            int64_t cnt = 0;
+            const gipc_status s = find_contacts_impl(ctx, x, sc.rest_x, n, sc.surface, prm.barrier.dhat, cs.st, cs.eps,
+                                                     cs.cap, &cnt, true, st);
+            if (s == GIPC_OK) {
+                cs.k = cnt;
+                return GIPC_OK;
+            }
+            if (s != GIPC_ERR_CAPACITY) return s;
+            const int64_t cap = cnt + cnt / 4 + 1024;
+            const gipc_status r = ctx->slot[cs.slot].reserve((size_t)cap * (4 * sizeof(int32_t) + sizeof(double)));
+            if (r != GIPC_OK) return r;
+            cs.cap = cap;
+            cs.eps = ctx->slot[cs.slot].as<double>();
+            cs.st = reinterpret_cast<int32_t*>(cs.eps + cap);
+        }
+        return fail(GIPC_ERR_CUDA, "gipc_newton_step: contact count changed between passes");
+    }
+
+    // I(x) and the contacts at x
+    gipc_status potential(const double* x, ContactSet& cs, double* I) {
+        gipc_status s;
+        if ((s = contacts(x, cs)) != GIPC_OK) return s;
+        const int64_t T = sc.T, k = cs.k;
+        if ((s = ctx->slot[N_ENER].reserve(sizeof(double) * (T + k + 2))) != GIPC_OK) return s;
+        double* te = ctx->slot[N_ENER].as<double>();
+        double* se = te + T;
+        gipc_elastic_params ep = prm.elastic;
+        ep.scale = prm.dt * prm.dt;
+        if ((s = gipc_eval_tets(x, n, sc.tets, T, sc.Dm_inv, sc.vol, &ep, GIPC_FP64, te, nullptr, nullptr, st)) != GIPC_OK)
+            return s;
+        if (k > 0 && (s = gipc_eval_stencils(x, n, cs.st, k, cs.eps, &prm.barrier, GIPC_FP64, GIPC_HESS_DENSE, se, nullptr,
+                                             nullptr, nullptr, nullptr, st)) != GIPC_OK)
+            return s;
+        reduce(R_INERTIA, x, xt, sc.mass, n, n, partial, res + 0, st);
+        reduce(R_ARRAY, te, nullptr, nullptr, 0, T, partial + kRedBlocks, res + 1, st);
+        reduce(R_ARRAY, se, nullptr, nullptr, 0, k, partial + 2 * kRedBlocks, res + 2, st);
+        double h[3];
+        cudaMemcpyAsync(h, res, 3 * sizeof(double), cudaMemcpyDeviceToHost, st);
+        if (cudaStreamSynchronize(st) != cudaSuccess) return check_launch("gipc_newton_step: energy");
+        *I = (0.5 * h[0] + h[1]) + h[2];
+        if (!std::isfinite(*I)) return fail(GIPC_ERR_NONFINITE, "gipc_newton_step: non-finite energy");
+        return GIPC_OK;
+    }
+
+    gipc_status run(double* x, double* v, gipc_step_stats* stats) {
+        const int64_t m3 = 3 * n;
+        gipc_status s;
+        if ((s = ctx->slot[N_VEC].reserve(sizeof(double) * 7 * m3)) != GIPC_OK) return s;
+        if ((s = ctx->slot[N_RED].reserve(sizeof(double) * (4 * kRedBlocks + 8))) != GIPC_OK) return s;
+        x0 = ctx->slot[N_VEC].as<double>();
+        xt = x0 + m3;
+        xp = xt + m3;
+        d = xp + m3;
+        g = d + m3;
+        rhs = g + m3;
+        gb = rhs + m3;
+        partial = ctx->slot[N_RED].as<double>();
+        res = partial + 4 * kRedBlocks;
+        for (auto& cs : set) {
+            cs.cap = (int64_t)(ctx->slot[cs.slot].bytes / (4 * sizeof(int32_t) + sizeof(double)));
+            cs.eps = ctx->slot[cs.slot].as<double>();
+            cs.st = reinterpret_cast<int32_t*>(cs.eps + cs.cap);
+        }
+        const double dt = prm.dt;
+        cudaMemcpyAsync(x0, x, sizeof(double) * m3, cudaMemcpyDeviceToDevice, st);
+        inertia_target_kernel<<<nb(n, 256), 256, 0, st>>>(x0, v, sc.fixed, n, dt, (dt * dt) * prm.gravity[0],
+                                                           (dt * dt) * prm.gravity[1], (dt * dt) * prm.gravity[2], xt);
+        int cur = 0;
+        double I_prev = 0.0;
+        if ((s = potential(x, set[cur], &I_prev)) != GIPC_OK) return s;
+        gipc_step_stats S{};
+        const int T = (int)sc.T;
+        const bool mixed = prm.prec == GIPC_MIXED;
+        const size_t hb = mixed ? sizeof(float) : sizeof(double);
+        for (int it = 0; it < prm.max_newton; ++it) {
+            ContactSet& A = set[cur];
+            const int64_t k = A.k;
+            // element gradients and projected Hessians
+            if ((s = ctx->slot[N_TEVAL].reserve(sizeof(double) * 12 * T + hb * 144 * T + 16)) != GIPC_OK) return s;
+            double* tg = ctx->slot[N_TEVAL].as<double>();
+            void* th = tg + 12 * (int64_t)T;
+            gipc_elastic_params ep = prm.elastic;
+            ep.scale = dt * dt;
+            if ((s = gipc_eval_tets(x, n, sc.tets, T, sc.Dm_inv, sc.vol, &ep, prm.prec, nullptr, tg, th, st)) != GIPC_OK)
+                return s;
+            const bool rank1 = prm.hess_mode == GIPC_HESS_RANK1;
+            const int64_t hper = rank1 ? 12 : 144;
+            if ((s = ctx->slot[N_SEVAL].reserve(sizeof(double) * 13 * std::max<int64_t>(k, 1) + hb * hper * k + 16)) != GIPC_OK)
+                return s;
+            double* sg = ctx->slot[N_SEVAL].as<double>();
+            double* sl = sg + 12 * k;
+            void* sh = sl + std::max<int64_t>(k, 1);
+            if (k > 0 &&
+                (s = gipc_eval_stencils(x, n, A.st, k, A.eps, &prm.barrier, prm.prec, prm.hess_mode, nullptr, sg, sh,
+                                        rank1 ? sl : nullptr, nullptr, st)) != GIPC_OK)
+                return s;
+            grad_base_kernel<<<nb(m3, 256), 256, 0, st>>>(x, xt, sc.mass, n, gb);
+            // H = M + sum P^T H_e P, g = M(x - xt) + sum P^T g_e
+            gipc_elements te{sc.tets, T, GIPC_HESS_DENSE, th, nullptr, tg};
+            gipc_elements se{A.st, k, prm.hess_mode, sh, rank1 ? sl : nullptr, sg};
+            if ((s = ctx->slot[N_ROW].reserve(sizeof(int32_t) * (n + 1))) != GIPC_OK) return s;
+            gipc_bsr H{};
+            H.prec = prm.prec;
+            H.rowptr = ctx->slot[N_ROW].as<int32_t>();
+            for (int attempt = 0; attempt < 2; ++attempt) {
+                H.capacity = std::min<int64_t>((int64_t)(ctx->slot[N_COL].bytes / sizeof(int32_t)),
+                                               (int64_t)(ctx->slot[N_VAL].bytes / (9 * hb)));
+                H.colidx = ctx->slot[N_COL].as<int32_t>();
+                H.vals = ctx->slot[N_VAL].ptr;
+                s = gipc_assemble_bsr(ctx, n, k > 0 ? &se : nullptr, &te, sc.mass, gb, &H, g, st);
+                if (s != GIPC_ERR_CAPACITY || H.nnzb <= H.capacity) break;
+                const int64_t cap = H.nnzb + H.nnzb / 8 + 1024;
+                if ((s = ctx->slot[N_COL].reserve(sizeof(int32_t) * cap)) != GIPC_OK) return s;
+                if ((s = ctx->slot[N_VAL].reserve(9 * hb * cap)) != GIPC_OK) return s;
+                s = GIPC_ERR_CAPACITY;
+            }
+            if (s != GIPC_OK) return s;
+            // d = argmin of the quadratic model (modified PCG, fixed vertices filtered)
+            negate_kernel<<<nb(m3, 256), 256, 0, st>>>(g, m3, rhs);
+            cudaMemsetAsync(d, 0, sizeof(double) * m3, st);
+            gipc_pcg_params pp{prm.pcg_tol, prm.max_pcg, 0};
+            int pit = 0;
+            s = gipc_pcg(ctx, &H, rhs, d, sc.fixed, &pp, &pit, nullptr, st);
+            if (s != GIPC_OK && s != GIPC_ERR_NOT_CONVERGED) return s;
+            S.pcg_iters += pit;
+            // step filter and backtracking
+            double alpha = 1.0;
+            if ((s = ccd_impl(ctx, x, d, n, sc.surface, 0.1, &alpha, st)) != GIPC_OK) return s;
+            cudaMemcpyAsync(xp, x, sizeof(double) * m3, cudaMemcpyDeviceToDevice, st);
+            const int nxt = 1 - cur;
+            double I_new = I_prev;
+            for (int ls = 0; ls < std::max(prm.max_ls, 1); ++ls) {
+                axpy_kernel<<<nb(m3, 256), 256, 0, st>>>(xp, d, alpha, m3, x);
+                if ((s = potential(x, set[nxt], &I_new)) != GIPC_OK) return s;
+                ++S.ls_trials;
+                if (I_new <= I_prev) break;
+                alpha *= 0.5;
+            }
+            cur = nxt;
+            I_prev = I_new;
+            ++S.newton_iters;
+            S.last_alpha = alpha;
+            reduce(R_MAXABS, d, nullptr, nullptr, 0, m3, partial + 3 * kRedBlocks, res + 3, st);
+            double dmax = 0.0;
+            cudaMemcpyAsync(&dmax, res + 3, sizeof(double), cudaMemcpyDeviceToHost, st);
+            if (cudaStreamSynchronize(st) != cudaSuccess) return check_launch("gipc_newton_step: step norm");
+            if (dmax / (sc.l * dt) <= prm.eps_d) {
+                S.converged = 1;
+                break;
+            }
+        }
+        velocity_kernel<<<nb(m3, 256), 256, 0, st>>>(x, x0, dt, m3, v);
+        S.contacts = set[cur].k;
+        S.energy = I_prev;
+        if (stats) *stats = S;
+        return check_launch("gipc_newton_step");
+    }
+};
+
+}  // namespace
+}  // namespace gipc
+
+extern "C" gipc_status gipc_newton_step(gipc_ctx* ctx, const gipc_scene* sc, double* x, double* v,
+                                        const gipc_step_params* prm, gipc_step_stats* stats, void* stream) {
+    using namespace gipc;
+    if (!ctx || !sc || !prm || !x || !v) return fail(GIPC_ERR_INVALID_ARG, "gipc_newton_step: null argument");
+    if (sc->n <= 0 || sc->T < 0 || !sc->rest_x || !sc->mass || (sc->T > 0 && (!sc->tets || !sc->Dm_inv || !sc->vol)))
+        return fail(GIPC_ERR_INVALID_ARG, "gipc_newton_step: incomplete scene");
+    if (sc->T > 0x7fffffff) return fail(GIPC_ERR_INVALID_ARG, "gipc_newton_step: too many tetrahedra");
+    if (!(prm->dt > 0.0) || !(sc->l > 0.0) || !(prm->eps_d >= 0.0) || prm->max_newton < 0 || prm->max_pcg < 0 ||
+        (prm->prec != GIPC_FP64 && prm->prec != GIPC_MIXED) ||
+        (prm->hess_mode != GIPC_HESS_DENSE && prm->hess_mode != GIPC_HESS_RANK1))
+        return fail(GIPC_ERR_INVALID_ARG, "gipc_newton_step: bad step parameters");
+    const gipc_barrier_params& b = prm->barrier;
+    if (!(b.dhat > 0.0) || !(b.kappa >= 0.0) || !(b.d_thr_ratio > 0.0 && b.d_thr_ratio < 1.0))
+        return fail(GIPC_ERR_INVALID_ARG, "gipc_newton_step: bad barrier parameters");
+    Step step(ctx, *sc, *prm, (cudaStream_t)stream);
+    return step.run(x, v, stats);
+}

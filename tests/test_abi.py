@@ -55,3 +55,33 @@ def test_host_side_argument_checks_need_no_gpu(libpath):
     assert L.gipc_eval_stencils(None, 10, None, 3, None, ctypes.byref(prm), 7, 0, None, None, None,
                                 None, None, None) == -1
     assert L.gipc_compute_eps_x(None, 3, None, -2, None, None) == -1
+
+
+def test_ctypes_struct_layouts_match_the_header(tmp_path):
+    """Field offsets and sizes of every ctypes struct equal the C compiler's for include/gipc.h."""
+    from paper_2308_09400_gb300 import _abi
+    structs = {"gipc_barrier_params": _abi.BarrierParams, "gipc_bsr": _abi.Bsr, "gipc_elements": _abi.Elements,
+               "gipc_elastic_params": _abi.ElasticParams, "gipc_pcg_params": _abi.PcgParams,
+               "gipc_kernel_time": _abi.KernelTime, "gipc_surface": _abi.Surface, "gipc_scene": _abi.Scene,
+               "gipc_step_params": _abi.StepParams, "gipc_step_stats": _abi.StepStats}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{os.path.join(ROOT, "include", "gipc.h")}"',
+             'int main(void) {']
+    for cname, py in structs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            cf = {"lam": "lambda"}.get(f, f) if cname == "gipc_elastic_params" else f
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {cf}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    import subprocess
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines():
+        c, f, v = line.split()
+        got[(c, f)] = int(v)
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)

@@ -1,0 +1,182 @@
+"""GPU parity of gipc_find_contacts, gipc_ccd_max_step and gipc_newton_step against the oracle.
+
+Contact lists (stencil tuples and eps_x) are compared bit for bit: both sides take every decision
+(box test, distance below dhat, closest feature, parallel test) with the same float64 operations.
+The CCD step is compared exactly as well (same per-pair arithmetic, order-independent minimum).
+The Newton step is compared on its iteration path (iterations, contacts) and its positions, which
+differ only by the rounding of the PCG's reductions.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+import synth  # noqa: E402
+from oracle import contact as C  # noqa: E402
+from oracle import geometry as G  # noqa: E402
+from oracle import newton as N  # noqa: E402
+from oracle import tet as TT  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def gipc():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2308_09400_gb300 as g
+    return g
+
+
+def _dev(a):
+    return torch.tensor(np.ascontiguousarray(a), device="cuda")
+
+
+def _rotz(x, idx, th, c):
+    X = x[:, idx] - np.asarray(c, float)[:, None]
+    R = np.array([[np.cos(th), -np.sin(th), 0.0], [np.sin(th), np.cos(th), 0.0], [0.0, 0.0, 1.0]])
+    x[:, idx] = R @ X + np.asarray(c, float)[:, None]
+
+
+def _variant(kind):
+    """Two unit cubes with the top one placed 0.5 dhat above the bottom one."""
+    sc = synth.two_cubes(gap=0.0)
+    x = sc["x"].copy()
+    dh = 1e-3 * sc["l"]
+    top = np.arange(125, 250)
+    if kind == "generic":            # shifted and jittered: interior point-triangle / edge-edge
+        rng = np.random.default_rng(3)
+        x[:, 125:] += np.array([0.031, 0.017, 0.0])[:, None]
+        x += 1e-4 * rng.normal(size=x.shape)
+    elif kind == "shifted":          # half a cell over and turned by 2e-3 rad: nearly parallel edges
+        x[0, 125:] += 0.125
+        _rotz(x, top, 2e-3, (0.625, 0.5, 0.0))
+    elif kind == "rot45":            # turned by 45 degrees: crossing edges, corners over faces
+        _rotz(x, top, np.pi / 4, (0.5, 0.5, 0.0))
+    x[2, 125:] += 0.5 * dh           # "aligned": only this offset
+    return sc, x, dh
+
+
+def _surface(g, sc):
+    return g.Surface(_dev(sc["tris"]), _dev(sc["edges"]), _dev(sc["verts"]))
+
+
+KINDS = ("generic", "aligned", "shifted", "rot45")
+
+
+def test_variants_cover_every_stencil_type():
+    seen = set()
+    for kind in KINDS:
+        sc, x, dh = _variant(kind)
+        st, _ = C.find_contacts(x, sc["x"], sc["tris"], sc["edges"], sc["verts"], dh)
+        seen |= {G.decode(st[:, i])[0] for i in range(st.shape[1])}
+    assert seen == set(range(7))
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_find_contacts_bit_exact(gipc, kind):
+    sc, x, dh = _variant(kind)
+    ref_st, ref_eps = C.find_contacts(x, sc["x"], sc["tris"], sc["edges"], sc["verts"], dh)
+    st, eps = gipc.find_contacts(_dev(x), _dev(sc["x"]), _surface(gipc, sc), dh)
+    assert st.shape == ref_st.shape
+    assert np.array_equal(st.cpu().numpy(), ref_st)
+    assert np.array_equal(eps.cpu().numpy(), ref_eps)
+
+
+def test_find_contacts_ball_grid_and_capacity(gipc):
+    """Thousands of surface primitives (several tiles, ragged tails) and the capacity protocol."""
+    sc = synth.sphere_grid(2, 2, radius=0.05, cells=8, gap=1e-3)
+    x = sc["x"].copy()
+    rng = np.random.default_rng(11)
+    x += 2e-4 * rng.normal(size=x.shape)
+    dh = 2e-3
+    ref_st, ref_eps = C.find_contacts(x, sc["x"], sc["tris"], sc["edges"], sc["verts"], dh)
+    assert ref_st.shape[1] > 100
+    srf = _surface(gipc, sc)
+    st, eps = gipc.find_contacts(_dev(x), _dev(sc["x"]), srf, dh, capacity=None)
+    assert np.array_equal(st.cpu().numpy(), ref_st)
+    assert np.array_equal(eps.cpu().numpy(), ref_eps)
+    with pytest.raises(gipc.GipcError, match="CAPACITY"):
+        gipc.find_contacts(_dev(x), _dev(sc["x"]), srf, dh, capacity=ref_st.shape[1] - 1)
+    st2, _ = gipc.find_contacts(_dev(x), _dev(sc["x"]), srf, dh, capacity=ref_st.shape[1])
+    assert np.array_equal(st2.cpu().numpy(), ref_st)
+
+
+def test_find_contacts_empty_inputs(gipc):
+    sc, x, dh = _variant("aligned")
+    empty3 = torch.zeros((3, 0), dtype=torch.int32, device="cuda")
+    empty2 = torch.zeros((2, 0), dtype=torch.int32, device="cuda")
+    empty1 = torch.zeros(0, dtype=torch.int32, device="cuda")
+    st, eps = gipc.find_contacts(_dev(x), _dev(sc["x"]), gipc.Surface(empty3, empty2, empty1), dh)
+    assert st.shape == (4, 0) and eps.shape == (0,)
+    # far apart: no contacts
+    x[2, 125:] += 1.0
+    st, _ = gipc.find_contacts(_dev(x), _dev(sc["x"]), _surface(gipc, sc), dh)
+    assert st.shape[1] == 0
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_ccd_step_exact(gipc, kind):
+    sc, x, dh = _variant(kind)
+    rng = np.random.default_rng(5)
+    d = np.zeros_like(x)
+    d[2, 125:] = -4 * dh                         # would pass through the bottom cube's top face
+    d[:, 125:] += 0.5 * dh * rng.normal(size=(3, 125))
+    ref = C.max_step(x, d, sc["tris"], sc["edges"], sc["verts"])
+    got = gipc.ccd_max_step(_dev(x), _dev(d), _surface(gipc, sc))
+    assert 0.0 < ref < 1.0
+    assert got == ref
+    # moving apart: the full step is feasible
+    d2 = np.zeros_like(x)
+    d2[2, 125:] = 3 * dh
+    assert gipc.ccd_max_step(_dev(x), _dev(d2), _surface(gipc, sc)) == 1.0 == \
+        C.max_step(x, d2, sc["tris"], sc["edges"], sc["verts"])
+
+
+def _newton_case():
+    sc0, x0, dh = _variant("generic")
+    mu, lam = TT.snh_params(1e5, 0.4)
+    prm = dict(dhat=dh, kappa=1e3, dt=0.01, mu=mu, lam=lam, gravity=(0.0, 0.0, -9.81), eps_d=1e-2,
+               pcg_tol=1e-4, max_pcg=500, max_newton=8, max_ls=30)
+    return sc0, x0, prm
+
+
+def test_newton_step_matches_oracle(gipc):
+    sc0, x0, prm = _newton_case()
+    osc = N.build_scene(dict(sc0, x=x0), prm, 1000.0)
+    xo, vo, so = N.newton_step(osc, x0, sc0["v"], prm)
+    scene = gipc.Scene(_dev(x0), _dev(sc0["tets"]), _surface(gipc, sc0), 1000.0,
+                       fixed=_dev(sc0["fixed"]), l=osc["l"])
+    x, v = _dev(x0), _dev(sc0["v"])
+    st = gipc.newton_step(scene, x, v, dt=prm["dt"], mu=prm["mu"], lam=prm["lam"], dhat=prm["dhat"],
+                          kappa=prm["kappa"], gravity=prm["gravity"], eps_d=prm["eps_d"], pcg_tol=prm["pcg_tol"],
+                          max_pcg=prm["max_pcg"], max_newton=prm["max_newton"], max_ls=prm["max_ls"])
+    xg, vg = x.cpu().numpy(), v.cpu().numpy()
+    assert st["newton_iters"] == so["newton"]
+    assert st["contacts"] == so["contacts"][-1]
+    assert st["last_alpha"] == pytest.approx(so["alpha"][-1], rel=1e-8)
+    assert abs(st["pcg_iters"] - sum(so["pcg"])) <= 2
+    scale = np.abs(xo - x0).max()
+    err = np.abs(xg - xo).max() / scale
+    assert err <= 1e-6, f"position error {err:.3e} of the step"
+    assert np.abs(vg - vo).max() <= 1e-6 * np.abs(vo).max()
+    assert st["energy"] == pytest.approx(so["energy"], rel=1e-9)
+    assert C.count_intersections(xg, sc0["tris"], sc0["edges"]) == 0
+
+
+def test_newton_step_mixed_and_rank1_converge_to_the_same_positions(gipc):
+    """float32 Hessian storage / SpMV and the rank-1 stencil form change the search directions,
+    not the minimiser (the gradient stays float64): run to a tight Newton tolerance, both land
+    within 1e-6 l (l the bounding-box diagonal) of each other."""
+    sc0, x0, prm = _newton_case()
+    scene = gipc.Scene(_dev(x0), _dev(sc0["tets"]), _surface(gipc, sc0), 1000.0, fixed=_dev(sc0["fixed"]))
+    out = {}
+    for prec, hm in (("fp64", "dense"), ("mixed", "rank1")):
+        x, v = _dev(x0), _dev(sc0["v"])
+        st = gipc.newton_step(scene, x, v, dt=prm["dt"], mu=prm["mu"], lam=prm["lam"], dhat=prm["dhat"],
+                              kappa=prm["kappa"], eps_d=1e-7, pcg_tol=1e-8, max_pcg=2000, max_newton=200,
+                              precision=prec, hess_mode=hm)
+        assert st["converged"] == 1, (prec, st)
+        out[prec] = x.cpu().numpy()
+        assert C.count_intersections(out[prec], sc0["tris"], sc0["edges"]) == 0
+    err = np.abs(out["mixed"] - out["fp64"]).max()
+    assert err <= 1e-6 * scene.l, f"converged-position difference {err:.3e}"
