@@ -239,8 +239,8 @@ typedef struct {
  * Blocks until the pattern size is known (one stream synchronisation), then
  * enqueues the value pass.  Scratch is owned by ctx and reused across calls.
  * Errors: GIPC_ERR_INVALID_ARG; GIPC_ERR_CAPACITY when nnzb > bsr->capacity
- * (bsr->nnzb then holds the required count and rowptr is valid) or when a row
- * receives more than 8192 contributions; GIPC_ERR_OOM; GIPC_ERR_CUDA. */
+ * (bsr->nnzb then holds the required count and rowptr is valid) or nnzb does
+ * not fit int32; GIPC_ERR_OOM; GIPC_ERR_CUDA. */
 gipc_status gipc_assemble_bsr(gipc_ctx* ctx, int64_t n, const gipc_elements* stencils_h,
                               const gipc_elements* tets_h, const double* mass, const double* grad_base,
                               gipc_bsr* bsr_h, double* grad_out, void* stream);
@@ -312,7 +312,8 @@ gipc_status gipc_pcg_noalloc(const gipc_bsr* A_h, const double* rhs, double* x, 
 
 /* ------------------------------------------------------------------ contacts */
 
-/* The collision surface: device arrays of vertex ids. */
+/* The collision surface: device arrays of vertex ids, each in [0, n) (not
+ * checked on the device). */
 typedef struct {
     const int32_t* tris;   /* int32 [3][ntri] surface triangles                        */
     int64_t ntri;
@@ -416,7 +417,7 @@ typedef struct {
  *   v  float64 [3][n]: v^t in, (x^{t+1} - x^t) / dt out
  * Synchronises the stream several times per iteration.  Scratch is owned by ctx.
  * Errors: GIPC_ERR_INVALID_ARG; GIPC_ERR_NONFINITE; GIPC_ERR_OOM; GIPC_ERR_CUDA;
- * GIPC_ERR_CAPACITY (a matrix row with more than 8192 contributions). */
+ * GIPC_ERR_CAPACITY (more than 2^31 matrix blocks). */
 gipc_status gipc_newton_step(gipc_ctx* ctx, const gipc_scene* sc_h, double* x, double* v,
                              const gipc_step_params* prm_h, gipc_step_stats* stats_h, void* stream);
 
@@ -430,7 +431,11 @@ typedef enum {
     GIPC_PROF_PCG_DIRECTION = 2, /* c = S(s + beta c)                             */
     GIPC_PROF_ASM_PATTERN = 3,   /* assembly: count .. rowptr (one span per call) */
     GIPC_PROF_ASM_VALUES = 4,    /* assembly: emit + value / gradient sums        */
-    GIPC_PROF_KINDS = 5
+    GIPC_PROF_CONTACTS = 5,      /* contact detection (broad phase + classify)    */
+    GIPC_PROF_CCD = 6,           /* CCD step filter                               */
+    GIPC_PROF_ELEMENTS = 7,      /* time step: element gradients + Hessians       */
+    GIPC_PROF_ENERGY = 8,        /* time step: energies and their reductions      */
+    GIPC_PROF_KINDS = 9
 } gipc_prof_kind;
 
 typedef struct {

@@ -12,7 +12,8 @@
 //              into its row bucket (order within a bucket is arbitrary);
 //              cid = element_id << 4 | a << 2 | b, the mass key is (i << 32 | 0)
 //   4. sort    each row bucket by key: warp-wide bitonic sort in shared memory
-//              for rows up to 512 contributions, block-wide up to 8192
+//              for rows up to 512 contributions, block-wide up to 8192, and one
+//              block sorting in global memory beyond that (rare hub vertices)
 //   5. unique  distinct columns per row -> row_nnzb -> rowptr (scan)
 //   6. emit    colidx and the first contribution of every block
 // Values (deterministic): one thread per block sums its contributions in key
@@ -173,11 +174,13 @@ sort_rows_warp_kernel(const int64_t* __restrict__ row_start, uint64_t* __restric
     }
 }
 
-// Rows longer than kWarpRowMax: one block per row (grid-stride over the queue).
+// Rows longer than kWarpRowMax: one block per row (grid-stride over the queue); rows longer
+// than kBlockRowMax are queued again (huge_rows) for the global-memory sort.
 __global__ void __launch_bounds__(1024)
 sort_rows_block_kernel(const int64_t* __restrict__ row_start, uint64_t* __restrict__ keys,
                        int32_t* __restrict__ row_nnzb, const int32_t* __restrict__ long_rows,
-                       const int32_t* __restrict__ n_long, int32_t* __restrict__ err) {
+                       const int32_t* __restrict__ n_long, int32_t* __restrict__ huge_rows,
+                       int32_t* __restrict__ n_huge) {
     extern __shared__ uint64_t buf[];
     __shared__ int heads_sh;
     const int cnt = *n_long;
@@ -186,10 +189,7 @@ sort_rows_block_kernel(const int64_t* __restrict__ row_start, uint64_t* __restri
         const int64_t st = row_start[r];
         const int L = (int)(row_start[r + 1] - st);
         if (L > kBlockRowMax) {
-            if (threadIdx.x == 0) {
-                atomicMax(err, L);
-                row_nnzb[r] = 0;
-            }
+            if (threadIdx.x == 0) huge_rows[atomicAdd(n_huge, 1)] = (int32_t)r;
             continue;
         }
         const int P = next_pow2(L);
@@ -203,6 +203,57 @@ sort_rows_block_kernel(const int64_t* __restrict__ row_start, uint64_t* __restri
             keys[st + t] = k;
             heads += (t == 0 || key_col(buf[t - 1]) != key_col(k)) ? 1 : 0;
         }
+        atomicAdd(&heads_sh, heads);
+        __syncthreads();
+        if (threadIdx.x == 0) row_nnzb[r] = heads_sh;
+        __syncthreads();
+    }
+}
+
+// Rows longer than kBlockRowMax: one block sorts the row in place in global memory with an
+// ascending-only bitonic network (each merge starts with a "flip" compare), which sorts any
+// length L: positions >= L act as +infinity and never take part in a swap.
+__global__ void __launch_bounds__(1024)
+sort_rows_global_kernel(const int64_t* __restrict__ row_start, uint64_t* __restrict__ keys,
+                        int32_t* __restrict__ row_nnzb, const int32_t* __restrict__ huge_rows,
+                        const int32_t* __restrict__ n_huge) {
+    __shared__ int heads_sh;
+    const int cnt = *n_huge;
+    for (int q = blockIdx.x; q < cnt; q += gridDim.x) {
+        const int64_t r = huge_rows[q];
+        uint64_t* K = keys + row_start[r];
+        const int64_t L = row_start[r + 1] - row_start[r];
+        int64_t P = 1;
+        while (P < L) P <<= 1;
+        for (int64_t k = 2; k <= P; k <<= 1) {
+            const int64_t h = k >> 1;
+            for (int64_t i = threadIdx.x; i < P / 2; i += blockDim.x) {
+                const int64_t blk = (i / h) * k, o = i % h;
+                const int64_t a = blk + o, b = blk + k - 1 - o;
+                if (b < L && K[a] > K[b]) {
+                    const uint64_t t = K[a];
+                    K[a] = K[b];
+                    K[b] = t;
+                }
+            }
+            __syncthreads();
+            for (int64_t j = k >> 2; j > 0; j >>= 1) {
+                for (int64_t i = threadIdx.x; i < P / 2; i += blockDim.x) {
+                    const int64_t a = (i / j) * 2 * j + (i % j), b = a + j;
+                    if (b < L && K[a] > K[b]) {
+                        const uint64_t t = K[a];
+                        K[a] = K[b];
+                        K[b] = t;
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        if (threadIdx.x == 0) heads_sh = 0;
+        __syncthreads();
+        int heads = 0;
+        for (int64_t t = threadIdx.x; t < L; t += blockDim.x)
+            heads += (t == 0 || key_col(K[t - 1]) != key_col(K[t])) ? 1 : 0;
         atomicAdd(&heads_sh, heads);
         __syncthreads();
         if (threadIdx.x == 0) row_nnzb[r] = heads_sh;
@@ -387,7 +438,7 @@ extern "C" gipc_status gipc_assemble_bsr(gipc_ctx* ctx, int64_t n, const gipc_el
     if ((st = ctx->slot[S_KEYS].reserve(sizeof(uint64_t) * cbound)) != GIPC_OK) return st;
     if ((st = ctx->slot[S_NNZB].reserve(sizeof(int32_t) * (n + 1))) != GIPC_OK) return st;
     if ((st = ctx->slot[S_ELEMN3].reserve(ne + 1)) != GIPC_OK) return st;
-    if ((st = ctx->slot[S_MISC].reserve(sizeof(uint64_t) * n + sizeof(int32_t) * (n + 4))) != GIPC_OK) return st;
+    if ((st = ctx->slot[S_MISC].reserve(sizeof(uint64_t) * n + sizeof(int32_t) * (2 * n + 4))) != GIPC_OK) return st;
     if ((st = ctx->slot[S_SCAN].reserve(sizeof(int64_t) * scan_scratch_words(n + 1))) != GIPC_OK) return st;
     if ((st = ctx->slot[S_ROWPTR64].reserve(sizeof(int64_t) * (n + 1))) != GIPC_OK) return st;
     int32_t* row_cnt = ctx->slot[S_ROWCNT].as<int32_t>();
@@ -398,7 +449,8 @@ extern "C" gipc_status gipc_assemble_bsr(gipc_ctx* ctx, int64_t n, const gipc_el
     unsigned long long* cursor = ctx->slot[S_MISC].as<unsigned long long>();
     int32_t* long_rows = reinterpret_cast<int32_t*>(cursor + n);
     int32_t* n_long = long_rows + n;
-    int32_t* err = n_long + 1;
+    int32_t* n_huge = n_long + 1;
+    int32_t* huge_rows = n_huge + 1;
     int64_t* scan_tmp = ctx->slot[S_SCAN].as<int64_t>();
     int64_t* rowptr64 = ctx->slot[S_ROWPTR64].as<int64_t>();
 
@@ -420,21 +472,17 @@ extern "C" gipc_status gipc_assemble_bsr(gipc_ctx* ctx, int64_t n, const gipc_el
         attr_set = true;
     }
     sort_rows_block_kernel<<<152, 1024, kBlockRowMax * sizeof(uint64_t), s>>>(row_start, keys, row_nnzb, long_rows,
-                                                                          n_long, err);
+                                                                          n_long, huge_rows, n_huge);
+    sort_rows_global_kernel<<<152, 1024, 0, s>>>(row_start, keys, row_nnzb, huge_rows, n_huge);
     if (exclusive_scan<int32_t>(row_nnzb, rowptr64, n, scan_tmp, s) != cudaSuccess)
         return check_launch("gipc_assemble_bsr: scan");
     rowptr32_kernel<<<blocks_for(n + 1, 256, 1 << 30), 256, 0, s>>>(rowptr64, bsr->rowptr, n);
     ctx->prof.stop(GIPC_PROF_ASM_PATTERN, s);
     if ((st = check_launch("gipc_assemble_bsr: pattern")) != GIPC_OK) return st;
     int64_t host_vals[2] = {0, 0};
-    int32_t host_err = 0;
     cudaMemcpyAsync(&host_vals[0], rowptr64 + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
-    cudaMemcpyAsync(&host_err, err, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
     if (cudaStreamSynchronize(s) != cudaSuccess) return check_launch("gipc_assemble_bsr: sync");
     const int64_t nnzb = host_vals[0];
-    if (host_err > 0)
-        return fail(GIPC_ERR_CAPACITY, "gipc_assemble_bsr: a row has %d contributions (limit %d)", host_err,
-                    kBlockRowMax);
     if (nnzb >= INT32_MAX) return fail(GIPC_ERR_CAPACITY, "gipc_assemble_bsr: nnzb exceeds int32");
     bsr->nnzb = nnzb;
     if (nnzb > bsr->capacity)

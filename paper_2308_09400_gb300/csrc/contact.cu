@@ -8,16 +8,18 @@
 //
 // Broad phase: a uniform grid stored as a spatial hash.  Every target primitive (triangle or
 // edge) is inserted into each cell its float64 box (padded by dhat for detection, swept for CCD)
-// overlaps; every query (a surface vertex, or an edge i looking for edges j > i) visits the cells
-// of its own box.  A pair is taken only in the cell holding the low corner of the intersection of
-// the two boxes, so each overlapping pair is met exactly once, whatever the cell size or hash
-// collisions.  The cell size is the mean target-box extent, doubled until no box spans more than
-// a few hundred cells.  The grid only proposes candidates: the float64 box test and the
-// classification decide, written as a fixed sequence of IEEE operations without contraction
-// (__d*_rn), so they take exactly the decisions of any implementation of the same formulas.
-// Two passes (count, then write at scanned offsets) and a per-query sort by target index give
-// a deterministic list: point-triangle pairs ordered by (surface vertex, triangle), then
-// edge-edge pairs by (edge i, edge j > i).
+// overlaps (at most once per hash bucket), as a 32-byte entry holding its id and its box rounded
+// outward to float32.  One warp serves one query (a surface vertex, or an edge i looking for edges
+// j > i): it walks the cells of the query box and scans each bucket 32 entries at a time with
+// coalesced loads, testing the float32 boxes first (conservative), then the float64 boxes.  A pair
+// is taken only in the cell holding the low corner of the intersection of the two boxes, so each
+// overlapping pair is met exactly once, whatever the cell size or hash collisions.  The cell size
+// is the mean target-box extent, doubled until no box spans more than a few hundred cells.  The
+// grid only proposes candidates: the float64 box test and the classification decide, written as a
+// fixed sequence of IEEE operations without contraction (__d*_rn), so they take exactly the
+// decisions of any implementation of the same formulas.  Two passes (count, then write at scanned
+// offsets) and a per-query sort by target index give a deterministic list: point-triangle pairs
+// ordered by (surface vertex, triangle), then edge-edge pairs by (edge i, edge j > i).
 //
 // Step filter (Alg. 1 "maxFeasibleStepSize"): additive CCD (conservative advancement with
 // the common displacement removed) for every pair whose swept float64 boxes overlap; the step
@@ -36,9 +38,16 @@ namespace {
 
 constexpr int kThreads = 128;
 constexpr int64_t kMaxCellsPerBox = 512;   // cell-size doubling threshold
-// context scratch slots: query counts / sort keys, query offsets, target boxes, scalars, hash
-// tables, per-target cell counts, their offsets
-enum ContactSlot { C_CNT = 16, C_QOFF = 17, C_BOX = 18, C_MISC = 19, C_GRID = 30, C_TCNT = 31, C_TOFF = 32 };
+constexpr int kWarps = kThreads / 32;
+// context scratch slots: query counts (then cursors), query offsets, scalars, sort keys, candidate
+// pairs, pair codes; per grid (triangles,
+// edges): float64 target boxes, hash tables, per-target cell counts and their offsets
+enum ContactSlot { C_CNT = 16, C_QOFF = 17, C_MISC = 19, C_KEY = 37, C_PAIRS = 38, C_CODE = 39 };
+constexpr int kGridSlots[2][4] = {{18, 30, 31, 32}, {33, 34, 35, 36}};
+// scalars in C_MISC: per grid g at 4g: extent sum, 1 / cell size, largest cell count; CCD minimum
+// at 8, pair counter at 9
+constexpr int kMiscAmin = 8;
+constexpr int kMiscPairs = 9;
 
 struct V3 {
     double x, y, z;
@@ -161,14 +170,21 @@ struct Surf {
 };
 
 // ------------------------------------------------------------------------------ grid
+// Bucket entry: target id and its box rounded outward to float32 (two 16-byte halves).
+struct __align__(16) Entry {
+    float lx, ly, lz;
+    int32_t id;
+    float hx, hy, hz, pad;
+};
+
 struct Grid {
-    const double* lo;        // [3][m] target box low corners
+    const double* lo;        // [3][m] target box low corners (float64)
     const double* hi;        // [3][m]
     int64_t m;
     const double* inv_h;     // device scalar: 1 / cell size
     uint64_t mask;           // buckets - 1 (power of two)
     const int64_t* boff;     // [buckets + 1] bucket offsets into ent
-    const int32_t* ent;      // target ids grouped by bucket
+    const Entry* ent;        // entries grouped by bucket
 };
 
 __device__ __forceinline__ int64_t cell_of(double v, double inv_h) { return (int64_t)floor(__dmul_rn(v, inv_h)); }
@@ -211,7 +227,7 @@ __global__ void target_boxes_kernel(const double* __restrict__ x, const double* 
             ext = fmax(ext, __dsub_rn(h, l));
         }
     }
-    // block sum of the extents, one atomic per block (the cell size only steers the search)
+    // warp sums of the extents, one atomic per warp (the cell size only steers the search)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) ext += __shfl_xor_sync(0xffffffffu, ext, o);
     if ((threadIdx.x & 31) == 0 && ext > 0.0) atomicAdd(ext_sum, ext);
@@ -234,7 +250,7 @@ __device__ __forceinline__ int64_t box_cells(double lx, double ly, double lz, do
     return a * b * c;
 }
 
-// Cells per target (int32, saturated) and the largest count over targets and query boxes.
+// Cells per target (int32, saturated) and the largest count over the targets.
 __global__ void cells_count_kernel(const double* __restrict__ lo, const double* __restrict__ hi, int64_t m,
                                    const double* __restrict__ inv_h, int32_t* __restrict__ cnt,
                                    unsigned long long* __restrict__ max_cells) {
@@ -270,129 +286,215 @@ __global__ void point_cells_kernel(const double* __restrict__ x, const double* _
 template <bool FILL>
 __global__ void bucket_kernel(const double* __restrict__ lo, const double* __restrict__ hi, int64_t m,
                               const double* __restrict__ inv_h, uint64_t mask, int32_t* __restrict__ bcnt,
-                              const int64_t* __restrict__ boff, int32_t* __restrict__ ent) {
+                              const int64_t* __restrict__ boff, Entry* __restrict__ ent) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= m) return;
+    const double l[3] = {lo[t], lo[m + t], lo[2 * m + t]}, h[3] = {hi[t], hi[m + t], hi[2 * m + t]};
     int64_t c0[3], c1[3];
-    const int64_t nc = box_cells(lo[t], lo[m + t], lo[2 * m + t], hi[t], hi[m + t], hi[2 * m + t], *inv_h, c0, c1);
+    const int64_t nc = box_cells(l[0], l[1], l[2], h[0], h[1], h[2], *inv_h, c0, c1);
     if (nc > kMaxCellsPerBox) return;
     const int64_t nx = c1[0] - c0[0] + 1, ny = c1[1] - c0[1] + 1;
     auto bucket_at = [&](int64_t li) {
         return bucket_of(c0[0] + li % nx, c0[1] + (li / nx) % ny, c0[2] + li / (nx * ny), mask);
     };
+    Entry E;
+    if (FILL) {
+        E.lx = __double2float_rd(l[0]); E.ly = __double2float_rd(l[1]); E.lz = __double2float_rd(l[2]);
+        E.hx = __double2float_ru(h[0]); E.hy = __double2float_ru(h[1]); E.hz = __double2float_ru(h[2]);
+        E.id = (int32_t)t;
+        E.pad = 0.f;
+    }
     for (int64_t li = 0; li < nc; ++li) {
         const uint64_t b = bucket_at(li);
         bool seen = false;
         for (int64_t lj = 0; lj < li && !seen; ++lj) seen = bucket_at(lj) == b;
         if (seen) continue;
         const int32_t slot = atomicAdd(&bcnt[b], 1);
-        if (FILL) ent[boff[b] + slot] = (int32_t)t;
+        if (FILL) ent[boff[b] + slot] = E;
     }
 }
 
-// Visit every candidate target of the query box [ql, qh] exactly once per overlapping pair:
-// f(t) is called for targets whose box overlaps the query box in the float64 test of the
-// caller (`overlap`), in the reference cell of the pair.
-template <class F>
-__device__ __forceinline__ void for_each_candidate(const Grid& G, const double ql[3], const double qh[3], double ih,
-                                                   F&& f) {
-    int64_t c0[3], c1[3];
-    if (box_cells(ql[0], ql[1], ql[2], qh[0], qh[1], qh[2], ih, c0, c1) > kMaxCellsPerBox) return;
-    for (int64_t cz = c0[2]; cz <= c1[2]; ++cz)
-        for (int64_t cy = c0[1]; cy <= c1[1]; ++cy)
-            for (int64_t cx = c0[0]; cx <= c1[0]; ++cx) {
-                const uint64_t b = bucket_of(cx, cy, cz, G.mask);
-                for (int64_t e = G.boff[b], e1 = G.boff[b + 1]; e < e1; ++e) {
-                    const int32_t t = G.ent[e];
-                    const double tl[3] = {G.lo[t], G.lo[G.m + t], G.lo[2 * G.m + t]};
-                    const double th[3] = {G.hi[t], G.hi[G.m + t], G.hi[2 * G.m + t]};
-                    if (!(ql[0] <= th[0] && qh[0] >= tl[0] && ql[1] <= th[1] && qh[1] >= tl[1] && ql[2] <= th[2] &&
-                          qh[2] >= tl[2]))
-                        continue;
-                    // reference cell: the low corner of the intersection
-                    if (cell_of(fmax(ql[0], tl[0]), ih) != cx || cell_of(fmax(ql[1], tl[1]), ih) != cy ||
-                        cell_of(fmax(ql[2], tl[2]), ih) != cz)
-                        continue;
-                    f(t);
-                }
+// Candidate pairs.  Each warp takes queries q = warp, warp + nw, ... and walks the cells of the
+// query box (the same box in every lane); each round every lane tests one bucket entry: the
+// float32 boxes, the float64 boxes, whether this cell is the pair's reference cell (the low
+// corner of the intersection of the two boxes) and the kind's index filters.  Survivors are
+// queued in shared memory (64 per warp) and appended to the global pair list 32 at a time with
+// one atomic.  The list order is arbitrary; the pair SET is fixed by the float64 tests.
+enum PairKind { K_PT = 0, K_EE = 1, K_PT_SWEPT = 2 };
+
+struct PairList {
+    int32_t* q;                  // [cap] query index (surface-vertex position, or edge id)
+    int32_t* t;                  // [cap] target index (triangle or edge id)
+    int64_t cap;
+    unsigned long long* count;   // device counter (may exceed cap: the caller grows and retries)
+};
+
+template <int KIND>
+__global__ void __launch_bounds__(kThreads)
+scan_pairs_kernel(const double* __restrict__ x, const double* __restrict__ dx, int64_t n, Surf S, Grid G,
+                  PairList L) {
+    __shared__ int32_t qq_sh[kWarps][64], qt_sh[kWarps][64];
+    int32_t* qq = qq_sh[threadIdx.x >> 5];
+    int32_t* qt = qt_sh[threadIdx.x >> 5];
+    const int lane = threadIdx.x & 31;
+    const int64_t nq = KIND == K_EE ? S.nedge : S.nvert;
+    const int64_t nw = (int64_t)gridDim.x * kWarps;
+    const double ih = *G.inv_h;
+    const float4* ent4 = reinterpret_cast<const float4*>(G.ent);
+    auto flush = [&](int cnt) {   // append the first cnt queued pairs (cnt <= 32)
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(L.count, (unsigned long long)cnt);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (lane < cnt && (int64_t)(base + lane) < L.cap) {
+            L.q[base + lane] = qq[lane];
+            L.t[base + lane] = qt[lane];
+        }
+    };
+    int queued = 0;   // same value in every lane
+    for (int64_t q = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5); q < nq; q += nw) {
+        double ql[3], qh[3];
+        int32_t p = 0, ia = 0, ib = 0;
+        if (KIND == K_EE) {
+            ia = S.edges[q];
+            ib = S.edges[S.nedge + q];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                ql[c] = G.lo[c * G.m + q];
+                qh[c] = G.hi[c * G.m + q];
             }
+        } else {
+            p = S.verts[q];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const double a = x[c * n + p];
+                const double b = KIND == K_PT_SWEPT ? __dadd_rn(a, dx[c * n + p]) : a;
+                ql[c] = fmin(a, b);
+                qh[c] = fmax(a, b);
+            }
+        }
+        int64_t c0[3], c1[3];
+        if (box_cells(ql[0], ql[1], ql[2], qh[0], qh[1], qh[2], ih, c0, c1) > kMaxCellsPerBox) continue;
+        const float fl[3] = {__double2float_rd(ql[0]), __double2float_rd(ql[1]), __double2float_rd(ql[2])};
+        const float fh[3] = {__double2float_ru(qh[0]), __double2float_ru(qh[1]), __double2float_ru(qh[2])};
+        for (int64_t cz = c0[2]; cz <= c1[2]; ++cz)
+            for (int64_t cy = c0[1]; cy <= c1[1]; ++cy)
+                for (int64_t cx = c0[0]; cx <= c1[0]; ++cx) {
+                    const uint64_t b = bucket_of(cx, cy, cz, G.mask);
+                    const int64_t e0 = G.boff[b], e1 = G.boff[b + 1];
+                    for (int64_t base = e0; base < e1; base += 32) {
+                        const int64_t e = base + lane;
+                        bool ok = false;
+                        int32_t t = 0;
+                        if (e < e1) {
+                            const float4 A = __ldg(ent4 + 2 * e), B = __ldg(ent4 + 2 * e + 1);
+                            t = __float_as_int(A.w);
+                            ok = fl[0] <= B.x && fh[0] >= A.x && fl[1] <= B.y && fh[1] >= A.y && fl[2] <= B.z &&
+                                 fh[2] >= A.z && (KIND != K_EE || t > q);
+                            if (ok) {
+                                const double tl[3] = {G.lo[t], G.lo[G.m + t], G.lo[2 * G.m + t]};
+                                const double th[3] = {G.hi[t], G.hi[G.m + t], G.hi[2 * G.m + t]};
+                                ok = ql[0] <= th[0] && qh[0] >= tl[0] && ql[1] <= th[1] && qh[1] >= tl[1] &&
+                                     ql[2] <= th[2] && qh[2] >= tl[2] && cell_of(fmax(ql[0], tl[0]), ih) == cx &&
+                                     cell_of(fmax(ql[1], tl[1]), ih) == cy && cell_of(fmax(ql[2], tl[2]), ih) == cz;
+                            }
+                            if (ok) {   // no shared vertex
+                                if (KIND == K_EE) {
+                                    const int32_t j0 = S.edges[t], j1 = S.edges[S.nedge + t];
+                                    ok = j0 != ia && j0 != ib && j1 != ia && j1 != ib;
+                                } else {
+                                    ok = p != S.tris[t] && p != S.tris[S.ntri + t] && p != S.tris[2 * S.ntri + t];
+                                }
+                            }
+                        }
+                        const unsigned m = __ballot_sync(0xffffffffu, ok);
+                        if (ok) {
+                            const int at = queued + __popc(m & ((1u << lane) - 1u));
+                            qq[at] = (int32_t)q;
+                            qt[at] = t;
+                        }
+                        queued += __popc(m);
+                        __syncwarp();
+                        if (queued >= 32) {
+                            flush(32);
+                            const int rest = queued - 32;
+                            const int32_t mq = lane < rest ? qq[32 + lane] : 0, mt = lane < rest ? qt[32 + lane] : 0;
+                            __syncwarp();
+                            if (lane < rest) {
+                                qq[lane] = mq;
+                                qt[lane] = mt;
+                            }
+                            queued = rest;
+                            __syncwarp();
+                        }
+                    }
+                }
+    }
+    if (queued > 0) flush(queued);
 }
 
 // ------------------------------------------------------------------------------ detection
-// Point-triangle queries: PASS 0 counts, PASS 1 writes (unsorted within a query) at off[k].
-template <int PASS>
-__global__ void __launch_bounds__(kThreads)
-pt_query_kernel(const double* __restrict__ x, int64_t n, Surf S, Grid G, double dh2, int32_t* __restrict__ cnt,
-                const int64_t* __restrict__ off, int32_t* __restrict__ st, double* __restrict__ eps,
-                int32_t* __restrict__ key, int64_t stride) {
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= S.nvert) return;
-    const int32_t p = S.verts[k];
-    const V3 xp = ld3(x, n, p);
-    const double q[3] = {xp.x, xp.y, xp.z};
-    int32_t c = 0;
-    int64_t w = PASS == 1 ? off[k] : 0;
-    for_each_candidate(G, q, q, *G.inv_h, [&](int32_t t) {
-        const int32_t a = S.tris[t], b = S.tris[S.ntri + t], cc = S.tris[2 * S.ntri + t];
-        if (p == a || p == b || p == cc) return;
-        double d2;
-        int ci = 0, cj = 0;
-        const int type = classify_pt(xp, ld3(x, n, a), ld3(x, n, b), ld3(x, n, cc), d2, ci, cj);
-        if (!(d2 < dh2)) return;
-        if (PASS == 0) {
-            ++c;
-            return;
-        }
-        const int32_t T[3] = {a, b, cc};
-        int32_t s1, s2, s3;
-        if (type == 0) { s1 = a; s2 = b; s3 = cc; }
-        else if (type == 1) { s1 = T[ci]; s2 = T[cj]; s3 = GIPC_NULL_INDEX; }
-        else { s1 = T[ci]; s2 = GIPC_NULL_INDEX; s3 = GIPC_NULL_INDEX; }
-        st[w] = neg(p);
-        st[stride + w] = s1;
-        st[2 * stride + w] = s2;
-        st[3 * stride + w] = s3;
-        eps[w] = 0.0;
-        key[w] = t;
-        ++w;
-    });
-    if (PASS == 0) cnt[k] = c;
+// Classify every candidate pair once: code = type | i << 2 | j << 4 (closest features) for a pair
+// closer than dhat, -1 otherwise; hits are counted per query (combined query index: surface
+// vertices first, then edges).
+__global__ void classify_pairs_kernel(const double* __restrict__ x, int64_t n, Surf S, const int32_t* __restrict__ pq,
+                                      const int32_t* __restrict__ pt, int64_t npt, int64_t np, double dh2,
+                                      int32_t* __restrict__ code, int32_t* __restrict__ cnt) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= np) return;
+    const int32_t q = pq[r], t = pt[r];
+    double d2;
+    int type, i = 0, j = 0;
+    int64_t qc;
+    if (r < npt) {
+        const int32_t p = S.verts[q];
+        type = classify_pt(ld3(x, n, p), ld3(x, n, S.tris[t]), ld3(x, n, S.tris[S.ntri + t]),
+                           ld3(x, n, S.tris[2 * S.ntri + t]), d2, i, j);
+        qc = q;
+    } else {
+        type = classify_ee(ld3(x, n, S.edges[q]), ld3(x, n, S.edges[S.nedge + q]), ld3(x, n, S.edges[t]),
+                           ld3(x, n, S.edges[S.nedge + t]), d2, i, j);
+        qc = S.nvert + q;
+    }
+    const bool hit = d2 < dh2;
+    code[r] = hit ? (type | i << 2 | j << 4) : -1;
+    if (hit) atomicAdd(&cnt[qc], 1);
 }
 
-template <int PASS>
-__global__ void __launch_bounds__(kThreads)
-ee_query_kernel(const double* __restrict__ x, const double* __restrict__ rx, int64_t n, Surf S, Grid G, double dh2,
-                int32_t* __restrict__ cnt, const int64_t* __restrict__ off, int32_t* __restrict__ st,
-                double* __restrict__ eps, int32_t* __restrict__ key, int64_t stride) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= S.nedge) return;
-    const int32_t ia = S.edges[i], ib = S.edges[S.nedge + i];
-    const V3 A0 = ld3(x, n, ia), A1 = ld3(x, n, ib);
-    const double ql[3] = {G.lo[i], G.lo[G.m + i], G.lo[2 * G.m + i]};
-    const double qh[3] = {G.hi[i], G.hi[G.m + i], G.hi[2 * G.m + i]};
-    int32_t c = 0;
-    int64_t w = PASS == 1 ? off[i] : 0;
-    for_each_candidate(G, ql, qh, *G.inv_h, [&](int32_t j) {
-        if (j <= i) return;
-        const int32_t jb0 = S.edges[j], jb1 = S.edges[S.nedge + j];
-        if (jb0 == ia || jb0 == ib || jb1 == ia || jb1 == ib) return;
-        const V3 B0 = ld3(x, n, jb0), B1 = ld3(x, n, jb1);
-        double d2;
-        int P = 0, Q = 0;
-        const int type = classify_ee(A0, A1, B0, B1, d2, P, Q);
-        if (!(d2 < dh2)) return;
-        if (PASS == 0) {
-            ++c;
-            return;
-        }
+// Write the stencil of every hit at off[query] + a per-query cursor (the order within a query is
+// fixed afterwards by sorting on the target index).
+__global__ void write_pairs_kernel(const double* __restrict__ x, const double* __restrict__ rx, int64_t n, Surf S,
+                                   const int32_t* __restrict__ pq, const int32_t* __restrict__ ptg,
+                                   const int32_t* __restrict__ code, int64_t npt, int64_t np,
+                                   const int64_t* __restrict__ off, int32_t* __restrict__ cur, int32_t* __restrict__ st,
+                                   double* __restrict__ eps, int32_t* __restrict__ key, int64_t stride) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= np) return;
+    const int32_t c = code[r];
+    if (c < 0) return;
+    const int32_t q = pq[r], t = ptg[r];
+    const int type = c & 3, i = (c >> 2) & 3, j = (c >> 4) & 3;
+    int32_t s0, s1, s2, s3;
+    double ex = 0.0;
+    int64_t at;
+    if (r < npt) {
+        at = off[q] + atomicAdd(&cur[q], 1);
+        const int32_t p = S.verts[q];
+        const int32_t T[3] = {S.tris[t], S.tris[S.ntri + t], S.tris[2 * S.ntri + t]};
+        s0 = neg(p);
+        if (type == 0) { s1 = T[0]; s2 = T[1]; s3 = T[2]; }
+        else if (type == 1) { s1 = T[i]; s2 = T[j]; s3 = GIPC_NULL_INDEX; }
+        else { s1 = T[i]; s2 = GIPC_NULL_INDEX; s3 = GIPC_NULL_INDEX; }
+    } else {
+        const int64_t qc = S.nvert + q;
+        at = off[qc] + atomicAdd(&cur[qc], 1);
+        const int32_t V[4] = {S.edges[q], S.edges[S.nedge + q], S.edges[t], S.edges[S.nedge + t]};
         // eps_x from rest positions, then the parallel test at the current positions
-        const V3 ra = vsub(ld3(rx, n, ib), ld3(rx, n, ia)), rb = vsub(ld3(rx, n, jb1), ld3(rx, n, jb0));
-        const double ex = __dmul_rn(__dmul_rn(1e-3, vdot(ra, ra)), vdot(rb, rb));
-        const V3 cr = vcross(vsub(A1, A0), vsub(B1, B0));
+        const V3 ra = vsub(ld3(rx, n, V[1]), ld3(rx, n, V[0])), rb = vsub(ld3(rx, n, V[3]), ld3(rx, n, V[2]));
+        ex = __dmul_rn(__dmul_rn(1e-3, vdot(ra, ra)), vdot(rb, rb));
+        const V3 cr = vcross(vsub(ld3(x, n, V[1]), ld3(x, n, V[0])), vsub(ld3(x, n, V[3]), ld3(x, n, V[2])));
         const bool par = vdot(cr, cr) < ex;
-        const int32_t V[4] = {ia, ib, jb0, jb1};
         const int mate[4] = {1, 0, 3, 2};
-        int32_t s0, s1, s2, s3;
+        const int P = i, Q = j;
         if (type == 0) {
             s0 = V[0]; s1 = par ? neg(V[1]) : V[1]; s2 = V[2]; s3 = V[3];
         } else if (type == 1) {
@@ -403,15 +505,13 @@ ee_query_kernel(const double* __restrict__ x, const double* __restrict__ rx, int
             if (par) { s0 = neg(V[P]); s1 = neg(V[mate[P]]); s2 = neg(V[Q]); s3 = neg(V[mate[Q]]); }
             else { s0 = neg(V[P]); s1 = V[Q]; s2 = GIPC_NULL_INDEX; s3 = GIPC_NULL_INDEX; }
         }
-        st[w] = s0;
-        st[stride + w] = s1;
-        st[2 * stride + w] = s2;
-        st[3 * stride + w] = s3;
-        eps[w] = ex;
-        key[w] = j;
-        ++w;
-    });
-    if (PASS == 0) cnt[i] = c;
+    }
+    st[at] = s0;
+    st[stride + at] = s1;
+    st[2 * stride + at] = s2;
+    st[3 * stride + at] = s3;
+    eps[at] = ex;
+    key[at] = t;
 }
 
 // Sort each query's outputs by target index (insertion sort: a query meets few targets).
@@ -471,6 +571,8 @@ __device__ double accd(V3 (&X)[4], const V3 (&P)[4], bool pt, double s, int max_
     const double g = __dmul_rn(s, d);
     double t = 0.0;
     double tl = __ddiv_rn(__dmul_rn(__dsub_rn(1.0, s), d), lp);
+    // the first step already passes t = 1: the distance at the advanced point would go unused
+    if (tl > 1.0) return 1.0;
     for (int it = 0; it < max_iter; ++it) {
 #pragma unroll
         for (int i = 0; i < 4; ++i)
@@ -490,111 +592,132 @@ __device__ __forceinline__ void atomic_min_pos(unsigned long long* addr, double 
     atomicMin(addr, (unsigned long long)__double_as_longlong(v));
 }
 
-__global__ void __launch_bounds__(kThreads)
-pt_ccd_kernel(const double* __restrict__ x, const double* __restrict__ dx, int64_t n, Surf S, Grid G, double s,
-              int max_iter, unsigned long long* __restrict__ amin) {
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= S.nvert) return;
-    const int32_t p = S.verts[k];
-    double ql[3], qh[3];
+__device__ __forceinline__ double warp_min(double v) {
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
-        const double a = x[q * n + p], b = __dadd_rn(a, dx[q * n + p]);
-        ql[q] = fmin(a, b);
-        qh[q] = fmax(a, b);
-    }
-    double best = 1.0;
-    for_each_candidate(G, ql, qh, *G.inv_h, [&](int32_t t) {
-        const int32_t ids[4] = {p, S.tris[t], S.tris[S.ntri + t], S.tris[2 * S.ntri + t]};
-        if (p == ids[1] || p == ids[2] || p == ids[3]) return;
-        V3 X[4], P[4];
-#pragma unroll
-        for (int a = 0; a < 4; ++a) {
-            X[a] = ld3(x, n, ids[a]);
-            P[a] = ld3(dx, n, ids[a]);
-        }
-        best = fmin(best, accd(X, P, true, s, max_iter));
-    });
-    if (best < 1.0) atomic_min_pos(amin, best);
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
 }
 
-__global__ void __launch_bounds__(kThreads)
-ee_ccd_kernel(const double* __restrict__ x, const double* __restrict__ dx, int64_t n, Surf S, Grid G, double s,
-              int max_iter, unsigned long long* __restrict__ amin) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= S.nedge) return;
-    const int32_t ia = S.edges[i], ib = S.edges[S.nedge + i];
-    const double ql[3] = {G.lo[i], G.lo[G.m + i], G.lo[2 * G.m + i]};
-    const double qh[3] = {G.hi[i], G.hi[G.m + i], G.hi[2 * G.m + i]};
+// ACCD of every candidate pair (point-triangle pairs first); the step is the minimum over pairs.
+__global__ void ccd_pairs_kernel(const double* __restrict__ x, const double* __restrict__ dx, int64_t n, Surf S,
+                                 const int32_t* __restrict__ pq, const int32_t* __restrict__ ptg, int64_t npt,
+                                 int64_t np, double s, int max_iter, unsigned long long* __restrict__ amin) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double best = 1.0;
-    for_each_candidate(G, ql, qh, *G.inv_h, [&](int32_t j) {
-        if (j <= i) return;
-        const int32_t ids[4] = {ia, ib, S.edges[j], S.edges[S.nedge + j]};
-        if (ids[2] == ia || ids[2] == ib || ids[3] == ia || ids[3] == ib) return;
+    if (r < np) {
+        const int32_t q = pq[r], t = ptg[r];
+        int32_t ids[4];
+        if (r < npt) {
+            ids[0] = S.verts[q]; ids[1] = S.tris[t]; ids[2] = S.tris[S.ntri + t]; ids[3] = S.tris[2 * S.ntri + t];
+        } else {
+            ids[0] = S.edges[q]; ids[1] = S.edges[S.nedge + q]; ids[2] = S.edges[t]; ids[3] = S.edges[S.nedge + t];
+        }
         V3 X[4], P[4];
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
             X[a] = ld3(x, n, ids[a]);
             P[a] = ld3(dx, n, ids[a]);
         }
-        best = fmin(best, accd(X, P, false, s, max_iter));
-    });
-    if (best < 1.0) atomic_min_pos(amin, best);
+        best = accd(X, P, r < npt, s, max_iter);
+    }
+    best = warp_min(best);
+    if ((threadIdx.x & 31) == 0 && best < 1.0) atomic_min_pos(amin, best);
 }
 
 inline unsigned nblk(int64_t w, int t) { return (unsigned)std::max<int64_t>(1, (w + t - 1) / t); }
+// persistent warp-per-query grids: at most 16 blocks of kWarps warps per SM
+inline unsigned wblk(int64_t queries) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>((queries + kWarps - 1) / kWarps, 152 * 16)); }
 
-// Insert the m primitives (nv vertices each) into a hashed grid over their boxes (x, swept by
-// d if given, padded by pad).  Synchronises once per cell-size attempt.
-gipc_status build_grid(gipc_ctx* ctx, const double* x, const double* d, int64_t n, const int32_t* prim, int nv,
+// Insert the m primitives (nv vertices each) into hashed grid g over their boxes (x, swept by
+// d if given, padded by pad).  Synchronises once per cell-size attempt.  `pts`: surface
+// vertices whose swept boxes also bound the cell size (CCD).
+gipc_status build_grid(gipc_ctx* ctx, int g, const double* x, const double* d, int64_t n, const int32_t* prim, int nv,
                        int64_t m, double pad, const gipc_surface* pts, Grid& G, cudaStream_t st) {
     gipc_status s;
-    // layout of C_MISC: [0] ext_sum, [1] inv_h, [2] max_cells, [3] amin (CCD)
-    if ((s = ctx->slot[C_MISC].reserve(64)) != GIPC_OK) return s;
-    double* misc = ctx->slot[C_MISC].as<double>();
+    gipc_scratch* slot = ctx->slot;
+    const int* gs = kGridSlots[g];
+    if ((s = slot[C_MISC].reserve(16 * sizeof(double))) != GIPC_OK) return s;
+    double* misc = slot[C_MISC].as<double>() + 4 * g;
     unsigned long long* max_cells = reinterpret_cast<unsigned long long*>(misc + 2);
-    if ((s = ctx->slot[C_BOX].reserve(sizeof(double) * 6 * (m + 1))) != GIPC_OK) return s;
-    double* lo = ctx->slot[C_BOX].as<double>();
+    if ((s = slot[gs[0]].reserve(sizeof(double) * 6 * (m + 1))) != GIPC_OK) return s;
+    double* lo = slot[gs[0]].as<double>();
     double* hi = lo + 3 * m;
-    if ((s = ctx->slot[C_TCNT].reserve(sizeof(int32_t) * (m + 1))) != GIPC_OK) return s;
-    int32_t* cnt = ctx->slot[C_TCNT].as<int32_t>();
-    if ((s = ctx->slot[C_TOFF].reserve(sizeof(int64_t) * (m + 2 + scan_scratch_words(m + 1)))) != GIPC_OK) return s;
-    int64_t* off = ctx->slot[C_TOFF].as<int64_t>();
+    if ((s = slot[gs[2]].reserve(sizeof(int32_t) * (m + 1))) != GIPC_OK) return s;
+    int32_t* cnt = slot[gs[2]].as<int32_t>();
+    if ((s = slot[gs[3]].reserve(sizeof(int64_t) * (m + 2 + scan_scratch_words(m + 1)))) != GIPC_OK) return s;
+    int64_t* off = slot[gs[3]].as<int64_t>();
     cudaMemsetAsync(misc, 0, sizeof(double), st);
-    if (m > 0) target_boxes_kernel<<<nblk(m, 256), 256, 0, st>>>(x, d, n, prim, nv, m, pad, lo, hi, misc);
+    target_boxes_kernel<<<nblk(m, 256), 256, 0, st>>>(x, d, n, prim, nv, m, pad, lo, hi, misc);
     int64_t total = 0;
     unsigned long long mc = 0;
     for (double scale = 1.0;; scale *= 2.0) {
         cell_size_kernel<<<1, 1, 0, st>>>(misc, m, scale, misc + 1);
         cudaMemsetAsync(max_cells, 0, sizeof(unsigned long long), st);
-        if (m > 0) cells_count_kernel<<<nblk(m, 256), 256, 0, st>>>(lo, hi, m, misc + 1, cnt, max_cells);
+        cells_count_kernel<<<nblk(m, 256), 256, 0, st>>>(lo, hi, m, misc + 1, cnt, max_cells);
         if (pts && pts->nvert > 0)
             point_cells_kernel<<<nblk(pts->nvert, 256), 256, 0, st>>>(x, d, n, pts->verts, pts->nvert, misc + 1, max_cells);
-        if (m > 0 && exclusive_scan<int32_t>(cnt, off, m, off + m + 2, st) != cudaSuccess)
+        if (exclusive_scan<int32_t>(cnt, off, m, off + m + 2, st) != cudaSuccess)
             return check_launch("contact grid: scan");
         cudaMemcpyAsync(&mc, max_cells, sizeof(mc), cudaMemcpyDeviceToHost, st);
-        if (m > 0) cudaMemcpyAsync(&total, off + m, sizeof(total), cudaMemcpyDeviceToHost, st);
+        cudaMemcpyAsync(&total, off + m, sizeof(total), cudaMemcpyDeviceToHost, st);
         if (cudaStreamSynchronize(st) != cudaSuccess) return check_launch("contact grid: sync");
         if ((int64_t)mc <= kMaxCellsPerBox) break;
         if (scale > 1e12) return fail(GIPC_ERR_NONFINITE, "contact grid: non-finite or unbounded positions");
     }
     uint64_t buckets = 1024;
     while ((int64_t)buckets < 2 * total) buckets <<= 1;
-    const size_t grid_bytes = sizeof(int64_t) * (buckets + 2 + scan_scratch_words(buckets + 1)) +
-                              sizeof(int32_t) * (buckets + total + 1);
-    if ((s = ctx->slot[C_GRID].reserve(grid_bytes)) != GIPC_OK) return s;
-    int64_t* boff = ctx->slot[C_GRID].as<int64_t>();
+    const int64_t head = buckets + 2 + scan_scratch_words(buckets + 1);   // int64 words before the counts
+    const int64_t cnt_words = (buckets + 1) / 2 + 1;                       // int32 counts, in int64 words
+    const size_t grid_bytes = sizeof(int64_t) * (head + cnt_words) + sizeof(Entry) * (total + 1) + 16;
+    if ((s = slot[gs[1]].reserve(grid_bytes)) != GIPC_OK) return s;
+    int64_t* boff = slot[gs[1]].as<int64_t>();
     int64_t* btmp = boff + buckets + 2;
-    int32_t* bcnt = reinterpret_cast<int32_t*>(btmp + scan_scratch_words(buckets + 1));
-    int32_t* ent = bcnt + buckets;
+    int32_t* bcnt = reinterpret_cast<int32_t*>(boff + head);
+    // entries start on a 16-byte boundary after the counts
+    uintptr_t ep = reinterpret_cast<uintptr_t>(boff + head + cnt_words);
+    ep = (ep + 15) & ~uintptr_t(15);
+    Entry* ent = reinterpret_cast<Entry*>(ep);
     cudaMemsetAsync(bcnt, 0, sizeof(int32_t) * buckets, st);
-    if (m > 0) bucket_kernel<false><<<nblk(m, 256), 256, 0, st>>>(lo, hi, m, misc + 1, buckets - 1, bcnt, nullptr, nullptr);
+    bucket_kernel<false><<<nblk(m, 256), 256, 0, st>>>(lo, hi, m, misc + 1, buckets - 1, bcnt, nullptr, nullptr);
     if (exclusive_scan<int32_t>(bcnt, boff, (int64_t)buckets, btmp, st) != cudaSuccess)
         return check_launch("contact grid: bucket scan");
     cudaMemsetAsync(bcnt, 0, sizeof(int32_t) * buckets, st);
-    if (m > 0) bucket_kernel<true><<<nblk(m, 256), 256, 0, st>>>(lo, hi, m, misc + 1, buckets - 1, bcnt, boff, ent);
+    bucket_kernel<true><<<nblk(m, 256), 256, 0, st>>>(lo, hi, m, misc + 1, buckets - 1, bcnt, boff, ent);
     G = Grid{lo, hi, m, misc + 1, buckets - 1, boff, ent};
     return check_launch("contact grid");
+}
+
+// Candidate pairs of the point-triangle grid Gt (if any) followed by those of the edge grid Ge
+// (if any) into the context's pair list; *npt / *np: point-triangle pairs / all pairs.
+// Synchronises once per attempt (the list grows when the count exceeds its capacity).
+gipc_status collect_pairs(gipc_ctx* ctx, const double* x, const double* d, int64_t n, const Surf& S, const Grid* Gt,
+                          const Grid* Ge, bool swept, int64_t* npt, int64_t* np, PairList& L, cudaStream_t st) {
+    gipc_status s;
+    unsigned long long* counter = reinterpret_cast<unsigned long long*>(ctx->slot[C_MISC].as<double>() + kMiscPairs);
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        L.cap = (int64_t)(ctx->slot[C_PAIRS].bytes / (2 * sizeof(int32_t)));
+        L.q = ctx->slot[C_PAIRS].as<int32_t>();
+        L.t = L.q + L.cap;
+        L.count = counter;
+        unsigned long long c[2] = {0, 0};
+        cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st);
+        if (Gt) {
+            if (swept) scan_pairs_kernel<K_PT_SWEPT><<<wblk(S.nvert), kThreads, 0, st>>>(x, d, n, S, *Gt, L);
+            else scan_pairs_kernel<K_PT><<<wblk(S.nvert), kThreads, 0, st>>>(x, d, n, S, *Gt, L);
+        }
+        cudaMemcpyAsync(&c[0], counter, sizeof(c[0]), cudaMemcpyDeviceToHost, st);
+        if (Ge) scan_pairs_kernel<K_EE><<<wblk(S.nedge), kThreads, 0, st>>>(x, d, n, S, *Ge, L);
+        cudaMemcpyAsync(&c[1], counter, sizeof(c[1]), cudaMemcpyDeviceToHost, st);
+        if (cudaStreamSynchronize(st) != cudaSuccess) return check_launch("contact pairs: sync");
+        if ((int64_t)c[1] <= L.cap) {
+            *npt = (int64_t)c[0];
+            *np = (int64_t)c[1];
+            return check_launch("contact pairs");
+        }
+        const int64_t want = (int64_t)c[1] + (int64_t)c[1] / 4 + 4096;
+        if ((s = ctx->slot[C_PAIRS].reserve(sizeof(int32_t) * 2 * want)) != GIPC_OK) return s;
+    }
+    return fail(GIPC_ERR_CUDA, "contact pairs: candidate count changed between passes");
 }
 
 }  // namespace
@@ -603,6 +726,7 @@ gipc_status build_grid(gipc_ctx* ctx, const double* x, const double* d, int64_t 
 gipc_status find_contacts_impl(gipc_ctx* ctx, const double* x, const double* rest_x, int64_t n, const gipc_surface& srf,
                                double dhat, int32_t* stencils, double* eps_x, int64_t cap, int64_t* count,
                                bool compact, cudaStream_t st) {
+    gipc_prof_span span(ctx->prof, GIPC_PROF_CONTACTS, st);
     Surf S{srf.tris, srf.ntri, srf.edges, srf.nedge, srf.verts, srf.nvert};
     const double pad = dhat * (1.0 + 1e-9);
     const double dh2 = dhat * dhat;
@@ -610,29 +734,30 @@ gipc_status find_contacts_impl(gipc_ctx* ctx, const double* x, const double* res
     *count = 0;
     if (nq == 0) return GIPC_OK;
     gipc_status s;
-    if ((s = ctx->slot[C_CNT].reserve(sizeof(int32_t) * (nq + 1))) != GIPC_OK) return s;
-    int32_t* cnt = ctx->slot[C_CNT].as<int32_t>();
-    // Count pass: triangle grid + point queries, then edge grid + edge queries.  One scratch set
-    // holds one grid at a time, so the triangle grid is built again for its write pass.
-    int64_t total = 0;
+    if ((s = ctx->slot[C_MISC].reserve(16 * sizeof(double))) != GIPC_OK) return s;
+    const bool pt = S.nvert > 0 && S.ntri > 0;
     Grid Gt{}, Ge{};
-    if (S.nvert > 0 && S.ntri > 0) {
-        if ((s = build_grid(ctx, x, nullptr, n, S.tris, 3, S.ntri, pad, nullptr, Gt, st)) != GIPC_OK) return s;
-        pt_query_kernel<0><<<nblk(S.nvert, kThreads), kThreads, 0, st>>>(x, n, S, Gt, dh2, cnt, nullptr, nullptr, nullptr,
-                                                                          nullptr, 0);
-    } else if (S.nvert > 0) {
-        cudaMemsetAsync(cnt, 0, sizeof(int32_t) * S.nvert, st);
-    }
-    if (S.nedge > 0) {
-        if ((s = build_grid(ctx, x, nullptr, n, S.edges, 2, S.nedge, pad, nullptr, Ge, st)) != GIPC_OK) return s;
-        ee_query_kernel<0><<<nblk(S.nedge, kThreads), kThreads, 0, st>>>(x, rest_x, n, S, Ge, dh2, cnt + S.nvert, nullptr,
-                                                                          nullptr, nullptr, nullptr, 0);
-    }
+    if (pt && (s = build_grid(ctx, 0, x, nullptr, n, S.tris, 3, S.ntri, pad, nullptr, Gt, st)) != GIPC_OK) return s;
+    if (S.nedge > 0 && (s = build_grid(ctx, 1, x, nullptr, n, S.edges, 2, S.nedge, pad, nullptr, Ge, st)) != GIPC_OK)
+        return s;
+    PairList L{};
+    int64_t npt = 0, np = 0;
+    if ((s = collect_pairs(ctx, x, nullptr, n, S, pt ? &Gt : nullptr, S.nedge > 0 ? &Ge : nullptr, false, &npt, &np, L,
+                           st)) != GIPC_OK)
+        return s;
+    // classify once, count per query
+    if ((s = ctx->slot[C_CNT].reserve(sizeof(int32_t) * (nq + 1))) != GIPC_OK) return s;
+    if ((s = ctx->slot[C_CODE].reserve(sizeof(int32_t) * (np + 1))) != GIPC_OK) return s;
+    int32_t* cnt = ctx->slot[C_CNT].as<int32_t>();
+    int32_t* code = ctx->slot[C_CODE].as<int32_t>();
+    cudaMemsetAsync(cnt, 0, sizeof(int32_t) * nq, st);
+    if (np > 0) classify_pairs_kernel<<<nblk(np, 128), 128, 0, st>>>(x, n, S, L.q, L.t, npt, np, dh2, code, cnt);
     // offsets over both kinds (point-triangle pairs first)
     if ((s = ctx->slot[C_QOFF].reserve(sizeof(int64_t) * (nq + 2 + scan_scratch_words(nq + 1)))) != GIPC_OK) return s;
     int64_t* off = ctx->slot[C_QOFF].as<int64_t>();
     if (exclusive_scan<int32_t>(cnt, off, nq, off + nq + 2, st) != cudaSuccess)
         return check_launch("gipc_find_contacts: scan");
+    int64_t total = 0;
     cudaMemcpyAsync(&total, off + nq, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
     if (cudaStreamSynchronize(st) != cudaSuccess) return check_launch("gipc_find_contacts: sync");
     *count = total;
@@ -640,40 +765,36 @@ gipc_status find_contacts_impl(gipc_ctx* ctx, const double* x, const double* res
     if (total == 0) return GIPC_OK;
     // rows of the output are `stride` apart: the caller's capacity, or the count itself (compact)
     const int64_t stride = compact ? total : cap;
-    // the counts are consumed: their slot now holds the sort keys
-    if ((s = ctx->slot[C_CNT].reserve(sizeof(int32_t) * (total + 1))) != GIPC_OK) return s;
-    int32_t* key = ctx->slot[C_CNT].as<int32_t>();
-    // write passes: the edge grid is the one currently built; then rebuild the triangle grid
-    if (S.nedge > 0)
-        ee_query_kernel<1><<<nblk(S.nedge, kThreads), kThreads, 0, st>>>(x, rest_x, n, S, Ge, dh2, nullptr, off + S.nvert,
-                                                                          stencils, eps_x, key, stride);
-    if (S.nvert > 0 && S.ntri > 0) {
-        if ((s = build_grid(ctx, x, nullptr, n, S.tris, 3, S.ntri, pad, nullptr, Gt, st)) != GIPC_OK) return s;
-        pt_query_kernel<1><<<nblk(S.nvert, kThreads), kThreads, 0, st>>>(x, n, S, Gt, dh2, nullptr, off, stencils, eps_x,
-                                                                          key, stride);
-    }
+    if ((s = ctx->slot[C_KEY].reserve(sizeof(int32_t) * (total + 1))) != GIPC_OK) return s;
+    int32_t* key = ctx->slot[C_KEY].as<int32_t>();
+    cudaMemsetAsync(cnt, 0, sizeof(int32_t) * nq, st);   // the counts become per-query cursors
+    write_pairs_kernel<<<nblk(np, 256), 256, 0, st>>>(x, rest_x, n, S, L.q, L.t, code, npt, np, off, cnt, stencils, eps_x,
+                                                       key, stride);
     segment_sort_kernel<<<nblk(nq, 256), 256, 0, st>>>(off, nq, key, stencils, eps_x, stride);
     return check_launch("gipc_find_contacts");
 }
 
 gipc_status ccd_impl(gipc_ctx* ctx, const double* x, const double* d, int64_t n, const gipc_surface& srf, double slack,
                      double* alpha, cudaStream_t st) {
+    gipc_prof_span span(ctx->prof, GIPC_PROF_CCD, st);
     Surf S{srf.tris, srf.ntri, srf.edges, srf.nedge, srf.verts, srf.nvert};
     const int max_iter = 100000;
     gipc_status s;
-    if ((s = ctx->slot[C_MISC].reserve(64)) != GIPC_OK) return s;
-    unsigned long long* amin = reinterpret_cast<unsigned long long*>(ctx->slot[C_MISC].as<double>() + 3);
+    if ((s = ctx->slot[C_MISC].reserve(16 * sizeof(double))) != GIPC_OK) return s;
+    unsigned long long* amin = reinterpret_cast<unsigned long long*>(ctx->slot[C_MISC].as<double>() + kMiscAmin);
     const double one = 1.0;
     cudaMemcpyAsync(amin, &one, sizeof(double), cudaMemcpyHostToDevice, st);
-    Grid G{};
-    if (S.nvert > 0 && S.ntri > 0) {
-        if ((s = build_grid(ctx, x, d, n, S.tris, 3, S.ntri, 0.0, &srf, G, st)) != GIPC_OK) return s;
-        pt_ccd_kernel<<<nblk(S.nvert, kThreads), kThreads, 0, st>>>(x, d, n, S, G, slack, max_iter, amin);
-    }
-    if (S.nedge > 0) {
-        if ((s = build_grid(ctx, x, d, n, S.edges, 2, S.nedge, 0.0, nullptr, G, st)) != GIPC_OK) return s;
-        ee_ccd_kernel<<<nblk(S.nedge, kThreads), kThreads, 0, st>>>(x, d, n, S, G, slack, max_iter, amin);
-    }
+    Grid Gt{}, Ge{};
+    const bool pt = S.nvert > 0 && S.ntri > 0;
+    if (pt && (s = build_grid(ctx, 0, x, d, n, S.tris, 3, S.ntri, 0.0, &srf, Gt, st)) != GIPC_OK) return s;
+    if (S.nedge > 0 && (s = build_grid(ctx, 1, x, d, n, S.edges, 2, S.nedge, 0.0, nullptr, Ge, st)) != GIPC_OK)
+        return s;
+    PairList L{};
+    int64_t npt = 0, np = 0;
+    if ((s = collect_pairs(ctx, x, d, n, S, pt ? &Gt : nullptr, S.nedge > 0 ? &Ge : nullptr, true, &npt, &np, L, st)) !=
+        GIPC_OK)
+        return s;
+    if (np > 0) ccd_pairs_kernel<<<nblk(np, 128), 128, 0, st>>>(x, d, n, S, L.q, L.t, npt, np, slack, max_iter, amin);
     double a = 1.0;
     cudaMemcpyAsync(&a, amin, sizeof(double), cudaMemcpyDeviceToHost, st);
     if (cudaStreamSynchronize(st) != cudaSuccess) return check_launch("gipc_ccd_max_step: sync");

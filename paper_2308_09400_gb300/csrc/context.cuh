@@ -67,9 +67,18 @@ struct gipc_profiler {
     }
 };
 
+// Records one span of `kind` around a scope (no-op while profiling is off).
+struct gipc_prof_span {
+    gipc_profiler& p;
+    int kind;
+    cudaStream_t s;
+    gipc_prof_span(gipc_profiler& p_, int k, cudaStream_t s_) : p(p_), kind(k), s(s_) { p.start(kind, s); }
+    ~gipc_prof_span() { p.stop(kind, s); }
+};
+
 struct gipc_ctx {
     int device = 0;
-    static constexpr int kSlots = 40;   // assembly 0-8, pcg 9-15, contacts 16-19 and 30-32, time step 20-29
+    static constexpr int kSlots = 40;   // assembly 0-8, pcg 9-15, contacts 16-19 and 30-39, time step 20-29
     gipc_scratch slot[kSlots];
     gipc_profiler prof;
     void release_all() {

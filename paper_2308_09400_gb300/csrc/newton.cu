@@ -189,6 +189,7 @@ struct Step {
         gipc_status s;
         if ((s = contacts(x, cs)) != GIPC_OK) return s;
         const int64_t T = sc.T, k = cs.k;
+        gipc_prof_span span(ctx->prof, GIPC_PROF_ENERGY, st);
         if ((s = ctx->slot[N_ENER].reserve(sizeof(double) * (T + k + 2))) != GIPC_OK) return s;
         double* te = ctx->slot[N_ENER].as<double>();
         double* se = te + T;
@@ -244,6 +245,7 @@ struct Step {
             ContactSet& A = set[cur];
             const int64_t k = A.k;
             // element gradients and projected Hessians
+            ctx->prof.start(GIPC_PROF_ELEMENTS, st);
             if ((s = ctx->slot[N_TEVAL].reserve(sizeof(double) * 12 * T + hb * 144 * T + 16)) != GIPC_OK) return s;
             double* tg = ctx->slot[N_TEVAL].as<double>();
             void* th = tg + 12 * (int64_t)T;
@@ -262,6 +264,7 @@ struct Step {
                 (s = gipc_eval_stencils(x, n, A.st, k, A.eps, &prm.barrier, prm.prec, prm.hess_mode, nullptr, sg, sh,
                                         rank1 ? sl : nullptr, nullptr, st)) != GIPC_OK)
                 return s;
+            ctx->prof.stop(GIPC_PROF_ELEMENTS, st);
             grad_base_kernel<<<nb(m3, 256), 256, 0, st>>>(x, xt, sc.mass, n, gb);
             // H = M + sum P^T H_e P, g = M(x - xt) + sum P^T g_e
             gipc_elements te{sc.tets, T, GIPC_HESS_DENSE, th, nullptr, tg};

@@ -545,20 +545,21 @@ def ball(radius=0.1, cells=14, center=(0.0, 0.0, 0.0)):
     return np.ascontiguousarray(x[:, used]), np.ascontiguousarray(remap[t].astype(np.int32))
 
 
-def sphere_grid(nx=8, ny=8, radius=0.1, cells=14, gap=1e-3):
-    """nx x ny balls of `radius` on a floor (z = 0, two fixed triangles spanning the grid), neighbours
-    and floor `gap` apart.  The floor is a fixed thin tetrahedral slab so every primitive comes from
-    a tetrahedral mesh.  Returns the same dict as two_cubes."""
+def sphere_grid(nx=8, ny=8, radius=0.1, cells=14, gap=1e-3, floor_cells=64):
+    """nx x ny balls of `radius` on a floor (top face z = 0), neighbours and floor `gap` apart.
+    The floor is a fixed thin tetrahedral slab of floor_cells x floor_cells x 1 grid cells, so every
+    primitive comes from a tetrahedral mesh and no floor vertex is shared by a large share of the
+    contacts.  Returns the same dict as two_cubes."""
     parts = []
     pitch = 2 * radius + gap
     for i in range(nx):
         for j in range(ny):
             parts.append(ball(radius, cells, center=(i * pitch, j * pitch, radius + gap)))
     lo, hi = -radius - 0.05, (max(nx, ny) - 1) * pitch + radius + 0.05
-    slab_x, slab_t = tet_box(2, 2, 2, spacing=1.0)
+    slab_x, slab_t = tet_box(floor_cells + 1, floor_cells + 1, 2, spacing=1.0)
     slab_x = slab_x.copy()
-    slab_x[0] = lo + slab_x[0] * (hi - lo)
-    slab_x[1] = lo + slab_x[1] * (hi - lo)
+    slab_x[0] = lo + slab_x[0] / floor_cells * (hi - lo)
+    slab_x[1] = lo + slab_x[1] / floor_cells * (hi - lo)
     slab_x[2] = -0.05 + slab_x[2] * 0.05
     parts.append((slab_x, slab_t))
     x, tets = _merge(parts)

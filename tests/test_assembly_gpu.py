@@ -110,11 +110,20 @@ def test_long_rows_use_the_block_sort(gipc):
     assert got["rowptr"][8] - got["rowptr"][7] > 512
 
 
-def test_row_beyond_limit_is_reported(gipc):
+def test_rows_beyond_the_block_sort_use_the_global_sort(gipc):
+    """A hub vertex in 2100 point-triangle stencils gets 8401 contributions (> 8192 per block)."""
     n = 12000
     d = synth.random_elements(n, 2500, 0, seed=15, mix=(("PT", 1.0),), hub=3, hub_count=2100)
-    with pytest.raises(gipc.GipcError, match="contributions"):
-        _gpu_assemble(gipc, n, d, "rank1", with_tets=False)
+    got = _gpu_assemble(gipc, n, d, "rank1", with_tets=False)
+    rows = [3, 4, 500]
+    ref = _oracle(n, d, "rank1", with_tets=False, rows=rows)
+    for q, r in enumerate(rows):
+        a0, a1 = got["rowptr"][r], got["rowptr"][r + 1]
+        b0, b1 = ref["rowptr"][q], ref["rowptr"][q + 1]
+        np.testing.assert_array_equal(got["colidx"][a0:a1], ref["colidx"][b0:b1])
+        assert np.array_equal(got["vals"][a0:a1], ref["vals"][b0:b1])
+    assert np.array_equal(got["grad"][:, rows], ref["grad"][:, rows])
+    assert got["rowptr"][4] - got["rowptr"][3] > 2000
 
 
 def test_capacity_retry(gipc):

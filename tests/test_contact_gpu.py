@@ -84,7 +84,7 @@ def test_find_contacts_bit_exact(gipc, kind):
 
 def test_find_contacts_ball_grid_and_capacity(gipc):
     """Thousands of surface primitives (several tiles, ragged tails) and the capacity protocol."""
-    sc = synth.sphere_grid(2, 2, radius=0.05, cells=8, gap=1e-3)
+    sc = synth.sphere_grid(2, 2, radius=0.05, cells=8, gap=1e-3, floor_cells=6)
     x = sc["x"].copy()
     rng = np.random.default_rng(11)
     x += 2e-4 * rng.normal(size=x.shape)
