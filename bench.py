@@ -45,6 +45,10 @@ def parse():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--hess-mode", default="dense", choices=["dense", "rank1"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--newton-steps", type=int, default=4,
+                    help="implicit time steps of the sphere-grid scene per precision (0: skip)")
+    ap.add_argument("--c2-steps", type=int, default=3,
+                    help="time steps of the per-step FP64 / mixed converged-position comparison (0: skip)")
     return ap.parse_args()
 
 
@@ -243,6 +247,7 @@ def run_gpu(args):
     d2h = out_h.numel() * out_h.element_size()
     Wd = dict(W)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ctx.profile_begin()   # same per-kernel event spans as the timed region
     barrier()
     e0.record()
     for _ in range(args.steps):
@@ -252,6 +257,7 @@ def run_gpu(args):
         out_h.copy_(dd, non_blocking=True)
     e1.record()
     barrier()
+    ctx.profile_stop()
     e2e_ms = e0.elapsed_time(e1) / args.steps
     if world > 1:
         t = torch.tensor([e2e_ms], device=dev)
@@ -270,12 +276,12 @@ def run_gpu(args):
         ach_fl = flops_l / avg / 1e9
         if args.precision == "fp64" and ach_fl / FP64_PEAK > ach_bw / hbm:
             roof = {"bound": "alu", "achieved": ach_fl / 1e3, "peak": FP64_PEAK / 1e3, "unit": "TFLOP/s",
-                    "frac": ach_fl / FP64_PEAK, "kernel": "pcg_spmv_kernel<double>",
+                    "frac": ach_fl / FP64_PEAK, "kernel": "pcg_spmv_sell_kernel<double>",
                     "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2070 MHz (probe measured 1.26 TFLOP/s)",
                     "hbm_frac": ach_bw / hbm}
         else:
             roof = {"bound": "hbm", "achieved": ach_bw, "peak": hbm, "unit": "GB/s", "frac": ach_bw / hbm,
-                    "kernel": f"pcg_spmv_kernel<{'double' if args.precision == 'fp64' else 'float'}>",
+                    "kernel": f"pcg_spmv_sell_kernel<{'double' if args.precision == 'fp64' else 'float'}>",
                     "peak_source": f"{hbm_src} (MEASURED_PEAKS.json hbm_gbs)" if hbm_src == "measured" else hbm_src,
                     "fp64_frac": ach_fl / FP64_PEAK if args.precision == "fp64" else None}
         roof["algorithmic_bytes_per_launch"] = bytes_l
@@ -302,11 +308,98 @@ def run_gpu(args):
             "gpu_launches": launches_per_step(n) * args.steps,
             "clocks": clk,
         }
+        if args.newton_steps > 0:
+            line["newton"] = run_newton(g, dev, ctx, args.newton_steps, args.c2_steps)
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args, Wh, sample=16000)
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------- Newton iterations/s
+NEWTON_FORMS = (("fp64", "dense"), ("mixed", "rank1"))
+
+
+def newton_scene():
+    """8 x 8 tet-meshed spheres (radius 0.1, 14 cells per diameter) 1e-3 above a tessellated
+    floor slab and 1e-3 apart; E = 1e5 Pa, nu = 0.4, rho = 1000, dt = 0.01, dhat = 1e-3 l,
+    kappa = 1e3, gravity -9.81 z."""
+    import synth
+    return synth.sphere_grid(8, 8)
+
+
+def run_c2(g, scene, sc, prm, dev, steps):
+    """Converged-position error of the mixed rank-one form against FP64 dense.  After one FP64
+    settling step (the initially compressed lattice has several nearby minima, so that first step
+    lands on a path-dependent one in any precision), each step starts from the FP64 state and is
+    solved by both forms to eps_d = 1e-5 (PCG tolerance 1e-7); the FP64 result carries the
+    trajectory on.  Reported per step as max |x_mixed - x_fp64| / l."""
+    import numpy as np
+    import torch
+    T = lambda a: torch.tensor(np.ascontiguousarray(a), device=dev)
+    tight = dict(prm, eps_d=1e-5, pcg_tol=1e-7, max_pcg=5000, max_newton=200)
+    x, v = T(sc["x"]), T(sc["v"])
+    g.newton_step(scene, x, v, precision="fp64", hess_mode="dense", **tight)
+    errs, conv, iters = [], [], []
+    for _ in range(steps):
+        out = {}
+        for prec, hm in NEWTON_FORMS:
+            xx, vv = x.clone(), v.clone()
+            st = g.newton_step(scene, xx, vv, precision=prec, hess_mode=hm, **tight)
+            out[prec] = (xx, vv, st)
+        errs.append((out["mixed"][0] - out["fp64"][0]).abs().max().item() / sc["l"])
+        conv.append([out["fp64"][2]["converged"], out["mixed"][2]["converged"]])
+        iters.append([out["fp64"][2]["newton_iters"], out["mixed"][2]["newton_iters"]])
+        x, v = out["fp64"][0], out["fp64"][1]
+    return {"definition": "after one FP64 settling step; per step, from the FP64 state: "
+                          "max|x_mixed - x_fp64| / l, both solved to eps_d 1e-5, PCG tol 1e-7",
+            "max_err_over_l": max(errs), "per_step_err_over_l": errs, "converged_fp64_mixed": conv,
+            "newton_iters_fp64_mixed": iters, "target": 1e-6}
+
+
+def run_newton(g, dev, ctx, steps, c2_steps=0):
+    """Implicit time steps of the sphere-grid scene through gipc_newton_step, FP64 dense and mixed
+    rank-one forms from the same initial state; Newton iterations per second and per-phase times."""
+    import numpy as np
+    import torch
+
+    sc = newton_scene()
+    T = lambda a: torch.tensor(np.ascontiguousarray(a), device=dev)
+    srf = g.Surface(T(sc["tris"]), T(sc["edges"]), T(sc["verts"]))
+    scene = g.Scene(T(sc["x"]), T(sc["tets"]), srf, 1000.0, fixed=T(sc["fixed"]), l=sc["l"])
+    mu, lam = g.snh_params(1e5, 0.4)
+    prm = dict(dt=0.01, mu=mu, lam=lam, dhat=1e-3 * sc["l"], kappa=KAPPA, eps_d=1e-2, pcg_tol=1e-4,
+               max_pcg=1000, max_newton=50)
+    out = {"scene": {"workload": "sphere grid 8x8 (radius 0.1) on a tessellated floor slab",
+                     "vertices": int(sc["x"].shape[1]), "tets": int(sc["tets"].shape[1]),
+                     "surface_tris": int(sc["tris"].shape[1]), "surface_edges": int(sc["edges"].shape[1]),
+                     "dt": 0.01, "dhat": prm["dhat"], "kappa": KAPPA, "eps_d": 1e-2, "pcg_tol": 1e-4,
+                     "E": 1e5, "nu": 0.4, "rho": 1000.0}}
+    for prec, hm in NEWTON_FORMS:
+        x, v = T(sc["x"]), T(sc["v"])
+        g.newton_step(scene, x, v, precision=prec, hess_mode=hm, **prm)   # warm-up step (sizes scratch)
+        torch.cuda.synchronize()
+        ctx.profile_begin()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        iters = pcg = 0
+        e0.record()
+        for _ in range(steps):
+            st = g.newton_step(scene, x, v, precision=prec, hess_mode=hm, **prm)
+            iters += st["newton_iters"]
+            pcg += st["pcg_iters"]
+        e1.record()
+        torch.cuda.synchronize()
+        prof = ctx.profile_read()
+        ctx.profile_stop()
+        ms = e0.elapsed_time(e1)
+        phase = {k: v[1] / max(iters, 1) for k, v in prof.items()}
+        out[f"{prec}_{hm}"] = {"newton_iters_per_s": iters / (ms * 1e-3), "ms_per_newton_iter": ms / max(iters, 1),
+                               "time_steps": steps, "newton_iters": iters, "pcg_iters": pcg,
+                               "contacts_final": st["contacts"], "phase_ms_per_newton_iter": phase}
+    if c2_steps > 0:
+        out["converged_position_error"] = run_c2(g, scene, sc, prm, dev, c2_steps)
+    return out
 
 
 # ----------------------------------------------------------------------------- oracle (CPU) arm

@@ -545,16 +545,21 @@ def ball(radius=0.1, cells=14, center=(0.0, 0.0, 0.0)):
     return np.ascontiguousarray(x[:, used]), np.ascontiguousarray(remap[t].astype(np.int32))
 
 
-def sphere_grid(nx=8, ny=8, radius=0.1, cells=14, gap=1e-3, floor_cells=64):
+def sphere_grid(nx=8, ny=8, radius=0.1, cells=14, gap=1e-3, floor_cells=64, jitter=0.25, seed=20230812):
     """nx x ny balls of `radius` on a floor (top face z = 0), neighbours and floor `gap` apart.
-    The floor is a fixed thin tetrahedral slab of floor_cells x floor_cells x 1 grid cells, so every
-    primitive comes from a tetrahedral mesh and no floor vertex is shared by a large share of the
-    contacts.  Returns the same dict as two_cubes."""
+    Each ball centre is moved by a seeded offset uniform in [-jitter*gap/2, jitter*gap/2]^3 (z only
+    upward), so the lattice has no exact symmetry.  The floor is a fixed thin tetrahedral slab of
+    floor_cells x floor_cells x 1 grid cells, so every primitive comes from a tetrahedral mesh and
+    no floor vertex is shared by a large share of the contacts.  Returns the same dict as
+    two_cubes."""
     parts = []
     pitch = 2 * radius + gap
+    rng = np.random.default_rng(seed)
     for i in range(nx):
         for j in range(ny):
-            parts.append(ball(radius, cells, center=(i * pitch, j * pitch, radius + gap)))
+            o = 0.5 * jitter * gap * rng.uniform(-1.0, 1.0, 3)
+            o[2] = abs(o[2])
+            parts.append(ball(radius, cells, center=(i * pitch + o[0], j * pitch + o[1], radius + gap + o[2])))
     lo, hi = -radius - 0.05, (max(nx, ny) - 1) * pitch + radius + 0.05
     slab_x, slab_t = tet_box(floor_cells + 1, floor_cells + 1, 2, spacing=1.0)
     slab_x = slab_x.copy()
