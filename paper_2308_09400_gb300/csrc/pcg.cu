@@ -39,7 +39,9 @@ namespace gipc {
 namespace {
 
 constexpr int kPcgThreads = 256;
-constexpr int kRowsPerWarp = 10;  // 3 lanes per row, lanes 30/31 idle
+constexpr int kRowsPerWarp = 10;  // row-ordered kernel: 3 lanes per row, lanes 30/31 idle
+constexpr int kSellC = 32;        // sliced kernel: rows per slice (one lane per row)
+constexpr int kVpt = 4;           // vertices per thread (pipelined) in the update / direction kernels
 
 enum PcgSlot { P_VEC = 9, P_PINV = 10, P_PART = 11, P_PERM = 12, P_VEC32 = 13, P_SELL = 14, P_SLICE = 15 };
 
@@ -190,19 +192,20 @@ __global__ void perm_scatter_kernel(const int32_t* __restrict__ rowptr, int64_t 
 }
 
 // ---- sliced layout of the matrix for the solver (built once per solve) --------------------
-// Rows are taken ten at a time in the length-sorted order (one slice per warp).  Slice s
-// holds L_s steps (its longest row); step j stores block j of each of its ten rows side by
-// side: column indices at sell_col[(off_s + j)*10 + i] and the 9 values at
-// sell_vals[((off_s + j)*10 + i)*9 ...].  A warp step then reads 10 contiguous column indices
-// and 90 contiguous values.  Shorter rows are padded with zero blocks (column 0).
+// SELL-32: rows are taken 32 at a time in the length-sorted order (one slice per warp, one lane
+// per row).  Slice s holds L_s steps (its longest row); step j stores block j of each of its 32
+// rows side by side, entry-major: column indices at sell_col[(off_s + j)*32 + i] and entry k of
+// the 3x3 block at sell_vals[((off_s + j)*9 + k)*32 + i].  Every value load of a warp then reads
+// 32 consecutive words.  Shorter rows are padded with zero blocks (column 0); the kernel never
+// reads the padding (each lane walks its own row length).
 
 __global__ void sell_len_kernel(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ perm, int64_t n,
                                 int64_t nsl, int32_t* __restrict__ slice_len) {
     const int64_t sl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (sl >= nsl) return;
     int32_t L = 0;
-    for (int i = 0; i < kRowsPerWarp; ++i) {
-        const int64_t slot = sl * kRowsPerWarp + i;
+    for (int i = 0; i < kSellC; ++i) {
+        const int64_t slot = sl * kSellC + i;
         if (slot < n) {
             const int32_t r = perm[slot];
             const int32_t len = rowptr[r + 1] - rowptr[r];
@@ -218,9 +221,9 @@ __global__ void sell_fill_kernel(const int32_t* __restrict__ rowptr, const int32
                                  const int64_t* __restrict__ slice_off, int32_t* __restrict__ sell_col,
                                  VT* __restrict__ sell_vals) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= nsl * kRowsPerWarp) return;
-    const int64_t sl = t / kRowsPerWarp;
-    const int i = (int)(t - sl * kRowsPerWarp);
+    if (t >= nsl * kSellC) return;
+    const int64_t sl = t / kSellC;
+    const int i = (int)(t - sl * kSellC);
     const int64_t off = slice_off[sl], L = slice_off[sl + 1] - off;
     int32_t b0 = 0, len = 0;
     if (t < n) {
@@ -229,25 +232,22 @@ __global__ void sell_fill_kernel(const int32_t* __restrict__ rowptr, const int32
         len = rowptr[r + 1] - b0;
     }
     for (int64_t j = 0; j < L; ++j) {
-        const int64_t p = (off + j) * kRowsPerWarp + i;
-        if (j < len) {
-            sell_col[p] = colidx[b0 + j];
+        const int64_t p = (off + j) * kSellC + i;
+        const bool real = j < len;
+        sell_col[p] = real ? colidx[b0 + j] : 0;
 #pragma unroll
-            for (int k = 0; k < 9; ++k) sell_vals[9 * p + k] = vals[9 * (int64_t)(b0 + j) + k];
-        } else {
-            sell_col[p] = 0;
-#pragma unroll
-            for (int k = 0; k < 9; ++k) sell_vals[9 * p + k] = VT(0);
-        }
+        for (int k = 0; k < 9; ++k)
+            sell_vals[((off + j) * 9 + k) * kSellC + i] = real ? vals[9 * (int64_t)(b0 + j) + k] : VT(0);
     }
 }
 
-// q = S(H c) over the sliced layout; alpha = delta_new / (c . q)
-// Persistent grid: warps stride over the slices.  Each lane issues all loads of an
-// eight-block group (columns, then values and gathered direction entries) before the group's
-// first FMA, so every warp keeps ~25 independent requests in flight; the kernel is bound by
-// memory latency, not by bytes.
-template <typename VT, typename PT>
+// q = S(H c) over the SELL-32 layout; alpha = delta_new / (c . q)
+// Persistent grid: warps stride over the slices, lane i computes the three entries of row i of
+// its slice.  Per group of U blocks a lane issues its column and value loads, then the gathers
+// of the direction, then the FMAs.  Block j of a row goes to accumulator j % 2 for
+// j < 4 floor(L / 4) and to accumulator 0 after that, each block adding its three products per
+// entry in column order -- the order of the row-ordered kernel, so both give the same bits.
+template <typename VT, typename PT, int U>
 __global__ void __launch_bounds__(kPcgThreads)
 pcg_spmv_sell_kernel(const int32_t* __restrict__ rowptr, const int64_t* __restrict__ slice_off,
                      const int32_t* __restrict__ sell_col,
@@ -255,76 +255,62 @@ pcg_spmv_sell_kernel(const int32_t* __restrict__ rowptr, const int64_t* __restri
                      const int32_t* __restrict__ perm, double* __restrict__ q, const uint8_t* __restrict__ fixed,
                      int64_t n, int64_t nsl, double* __restrict__ part, PcgScalars* __restrict__ S) {
     if (S->done) return;
-    constexpr int U = 8;
     const int lane = threadIdx.x & 31;
-    const int i = lane / 3, comp = lane - 3 * (lane / 3);
     const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     double d = 0.0;
     for (int64_t sl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < nsl; sl += warps) {
-        const int64_t slot = sl * kRowsPerWarp + i;
-        if (lane >= 3 * kRowsPerWarp || slot >= n) continue;
-        // each lane walks its own row's blocks (never the padding), grouped so that block j
-        // goes to accumulator (j / 4) % 2 ... exactly as the row-ordered kernel, which keeps
-        // both layouts' rounding identical
+        const int64_t slot = sl * kSellC + lane;
+        if (slot >= n) continue;
         const int64_t row = perm[slot];
         const int64_t off = slice_off[sl];
         const int64_t L = rowptr[row + 1] - rowptr[row];
-        VT acc0 = VT(0), acc1 = VT(0);
+        const int64_t L4 = L & ~int64_t(3);
+        VT a0[3] = {VT(0), VT(0), VT(0)}, a1[3] = {VT(0), VT(0), VT(0)};
         int64_t j = 0;
-        for (; j + U <= L; j += U) {
-            int64_t cc[U];
+        for (; j + U <= L4; j += U) {
+            int32_t cc[U];
+            VT v[U][9];
+            PT pv[U][3];
 #pragma unroll
-            for (int u = 0; u < U; ++u) cc[u] = sell_col[(off + j + u) * kRowsPerWarp + i];
-            VT v[3 * U];
-            PT pv[3 * U];
+            for (int u = 0; u < U; ++u) cc[u] = __ldcs(sell_col + (off + j + u) * kSellC + lane);
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+#pragma unroll
+                for (int k = 0; k < 9; ++k) v[u][k] = __ldcs(sell_vals + ((off + j + u) * 9 + k) * kSellC + lane);
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+#pragma unroll
+                for (int k = 0; k < 3; ++k) pv[u][k] = __ldg(cg + 3 * (int64_t)cc[u] + k);
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                const VT* vp = sell_vals + 9 * ((off + j + u) * kRowsPerWarp + i) + 3 * comp;
-                const PT* pp = cg + 3 * cc[u];
+                VT* a = (u & 1) ? a1 : a0;
 #pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    v[3 * u + k] = __ldcs(vp + k);
-                    pv[3 * u + k] = __ldg(pp + k);
-                }
-            }
+                for (int e = 0; e < 3; ++e)
 #pragma unroll
-            for (int h = 0; h < U; h += 4) {
-#pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    acc0 = fma(v[3 * h + k], (VT)pv[3 * h + k], acc0);
-                    acc1 = fma(v[3 * h + 3 + k], (VT)pv[3 * h + 3 + k], acc1);
-                }
-#pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    acc0 = fma(v[3 * h + 6 + k], (VT)pv[3 * h + 6 + k], acc0);
-                    acc1 = fma(v[3 * h + 9 + k], (VT)pv[3 * h + 9 + k], acc1);
-                }
-            }
-        }
-        for (; j + 4 <= L; j += 4) {
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int64_t p = (off + j + u) * kRowsPerWarp + i;
-                const VT* vp = sell_vals + 9 * p + 3 * comp;
-                const PT* pp = cg + 3 * (int64_t)sell_col[p];
-                VT& acc = (u & 1) ? acc1 : acc0;
-                acc = fma(vp[0], (VT)pp[0], acc);
-                acc = fma(vp[1], (VT)pp[1], acc);
-                acc = fma(vp[2], (VT)pp[2], acc);
+                    for (int k = 0; k < 3; ++k) a[e] = fma(v[u][3 * e + k], (VT)pv[u][k], a[e]);
             }
         }
         for (; j < L; ++j) {
-            const int64_t p = (off + j) * kRowsPerWarp + i;
-            const VT* vp = sell_vals + 9 * p + 3 * comp;
-            const PT* pp = cg + 3 * (int64_t)sell_col[p];
-            acc0 = fma(vp[0], (VT)pp[0], acc0);
-            acc0 = fma(vp[1], (VT)pp[1], acc0);
-            acc0 = fma(vp[2], (VT)pp[2], acc0);
+            const int32_t cj = __ldcs(sell_col + (off + j) * kSellC + lane);
+            VT v[9];
+            PT pv[3];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) v[k] = __ldcs(sell_vals + ((off + j) * 9 + k) * kSellC + lane);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) pv[k] = __ldg(cg + 3 * (int64_t)cj + k);
+            VT* a = (j < L4 && (j & 1)) ? a1 : a0;
+#pragma unroll
+            for (int e = 0; e < 3; ++e)
+#pragma unroll
+                for (int k = 0; k < 3; ++k) a[e] = fma(v[3 * e + k], (VT)pv[k], a[e]);
         }
-        double y = (double)(acc0 + acc1);
-        if (fixed && fixed[row]) y = 0.0;
-        q[3 * row + comp] = y;
-        d += c[3 * row + comp] * y;
+        const bool fx = fixed && fixed[row];
+#pragma unroll
+        for (int e = 0; e < 3; ++e) {
+            const double y = fx ? 0.0 : (double)(a0[e] + a1[e]);
+            q[3 * row + e] = y;
+            d += c[3 * row + e] * y;
+        }
     }
     const double bs = block_sum(d);
     if (publish_partial(part, bs, &S->count_a)) {
@@ -420,6 +406,9 @@ __device__ __forceinline__ double precond_apply(const double* __restrict__ F, co
 }
 
 // x += alpha c; r -= alpha q; s = P^-1 r; delta_new = r . s; beta; termination
+// Persistent grid; each thread walks its vertices (stride apart, so loads stay coalesced) with a
+// one-deep software pipeline: the next vertex's 18 loads are in flight while the FP64 work of the
+// current one runs.  The per-thread sum runs over its vertices in index order.
 __global__ void __launch_bounds__(kPcgThreads)
 pcg_update_kernel(double* __restrict__ x, double* __restrict__ r, const double* __restrict__ c,
                   const double* __restrict__ q, double* __restrict__ s, const double* __restrict__ pinv,
@@ -427,18 +416,47 @@ pcg_update_kernel(double* __restrict__ x, double* __restrict__ r, const double* 
     if (S->done) return;
     const double alpha = S->alpha;
     double d = 0.0;
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
-        double rv[3];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double xv[3], cv[3], rv[3], qv[3], F[6];
+    auto load = [&](int64_t w, double* X, double* C, double* R, double* Q, double* P) {
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
-            x[3 * v + i] += alpha * c[3 * v + i];
-            rv[i] = r[3 * v + i] - alpha * q[3 * v + i];
+            X[i] = x[3 * w + i];
+            C[i] = c[3 * w + i];
+            R[i] = r[3 * w + i];
+            Q[i] = q[3 * w + i];
+        }
+#pragma unroll
+        for (int i = 0; i < 6; ++i) P[i] = pinv[6 * w + i];
+    };
+    if (v < n) load(v, xv, cv, rv, qv, F);
+    while (v < n) {
+        const int64_t vn = v + stride;
+        double xn[3], cn[3], rn[3], qn[3], Fn[6];
+        if (vn < n) load(vn, xn, cn, rn, qn, Fn);
+        double sv[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            x[3 * v + i] = xv[i] + alpha * cv[i];
+            rv[i] = rv[i] - alpha * qv[i];
             r[3 * v + i] = rv[i];
         }
-        double sv[3];
-        d += precond_apply(pinv + 6 * v, rv, sv);
+        d += precond_apply(F, rv, sv);
 #pragma unroll
         for (int i = 0; i < 3; ++i) s[3 * v + i] = sv[i];
+        if (vn < n) {
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                xv[i] = xn[i];
+                cv[i] = cn[i];
+                rv[i] = rn[i];
+                qv[i] = qn[i];
+            }
+#pragma unroll
+            for (int i = 0; i < 6; ++i) F[i] = Fn[i];
+        }
+        v = vn;
     }
     const double bs = block_sum(d);
     if (!publish_partial(part, bs, &S->count_b)) return;
@@ -465,11 +483,45 @@ pcg_direction_kernel(double* __restrict__ c, float* __restrict__ c32, const doub
     // only while the solve continues
     if (S->done) return;
     const double beta = S->beta;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < 3 * n; e += (int64_t)gridDim.x * blockDim.x) {
-        const bool fx = fixed && fixed[e / 3];
-        const double ce = fx ? 0.0 : s[e] + beta * c[e];
-        c[e] = ce;
-        if (c32) c32[e] = (float)ce;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double sv[3], cv[3];
+    bool fx = false;
+    if (v < n) {
+        fx = fixed && fixed[v];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            sv[i] = s[3 * v + i];
+            cv[i] = c[3 * v + i];
+        }
+    }
+    while (v < n) {   // one-deep software pipeline, as in the update
+        const int64_t vn = v + stride;
+        double sn[3], cn[3];
+        bool fn = false;
+        if (vn < n) {
+            fn = fixed && fixed[vn];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                sn[i] = s[3 * vn + i];
+                cn[i] = c[3 * vn + i];
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const double ce = fx ? 0.0 : sv[i] + beta * cv[i];
+            c[3 * v + i] = ce;
+            if (c32) c32[3 * v + i] = (float)ce;
+        }
+        if (vn < n) {
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                sv[i] = sn[i];
+                cv[i] = cn[i];
+            }
+            fx = fn;
+        }
+        v = vn;
     }
 }
 
@@ -544,7 +596,7 @@ inline unsigned spmv_blocks(int64_t n) {
 }
 
 inline unsigned vec_blocks(int64_t n) {
-    int64_t b = (n + kPcgThreads - 1) / kPcgThreads;
+    int64_t b = (n + (int64_t)kPcgThreads * kVpt - 1) / ((int64_t)kPcgThreads * kVpt);
     if (b > 152 * 8) b = 152 * 8;
     return (unsigned)(b < 1 ? 1 : b);
 }
@@ -604,7 +656,7 @@ extern "C" gipc_status gipc_pcg(gipc_ctx* ctx, const gipc_bsr* A, const double* 
     if (exclusive_scan<int32_t>(counts, offs, ncnt, scan_tmp, st) != cudaSuccess) return check_launch("gipc_pcg: scan");
     perm_scatter_kernel<<<(unsigned)chunks, 32, 0, st>>>(A->rowptr, n, offs, chunks, perm);
     // sliced layout: slice lengths, their offsets, then the copy
-    const int64_t nsl = (n + kRowsPerWarp - 1) / kRowsPerWarp;
+    const int64_t nsl = (n + kSellC - 1) / kSellC;
     if ((s = ctx->slot[P_SLICE].reserve(sizeof(int32_t) * (nsl + 1) + sizeof(int64_t) * (nsl + 2 + scan_scratch_words(nsl)) + 64)) != GIPC_OK) return s;
     int32_t* slice_len = ctx->slot[P_SLICE].as<int32_t>();
     int64_t* slice_off = reinterpret_cast<int64_t*>(ctx->slot[P_SLICE].as<char>() + ((sizeof(int32_t) * (nsl + 1) + 15) / 16) * 16);
@@ -615,11 +667,11 @@ extern "C" gipc_status gipc_pcg(gipc_ctx* ctx, const gipc_bsr* A, const double* 
     cudaMemcpyAsync(&steps, slice_off + nsl, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
     if (cudaStreamSynchronize(st) != cudaSuccess) return check_launch("gipc_pcg: slice sync");
     const size_t vsz = f64 ? sizeof(double) : sizeof(float);
-    const int64_t cells = steps * kRowsPerWarp;
+    const int64_t cells = steps * kSellC;
     if ((s = ctx->slot[P_SELL].reserve(sizeof(int32_t) * cells + 256 + vsz * 9 * cells)) != GIPC_OK) return s;
     int32_t* sell_col = ctx->slot[P_SELL].as<int32_t>();
     void* sell_vals = ctx->slot[P_SELL].as<char>() + ((sizeof(int32_t) * cells + 255) / 256) * 256;
-    const unsigned fb = (unsigned)((nsl * kRowsPerWarp + 255) / 256);
+    const unsigned fb = (unsigned)((nsl * kSellC + 255) / 256);
     if (f64) sell_fill_kernel<double><<<fb, 256, 0, st>>>(A->rowptr, A->colidx, (const double*)A->vals, perm, n, nsl, slice_off, sell_col, (double*)sell_vals);
     else sell_fill_kernel<float><<<fb, 256, 0, st>>>(A->rowptr, A->colidx, (const float*)A->vals, perm, n, nsl, slice_off, sell_col, (float*)sell_vals);
     unsigned slb = (unsigned)((nsl * 32 + kPcgThreads - 1) / kPcgThreads);
@@ -643,8 +695,8 @@ extern "C" gipc_status gipc_pcg(gipc_ctx* ctx, const gipc_bsr* A, const double* 
         const int m = (max_iter - launched) < chunk ? (max_iter - launched) : chunk;
         for (int it = 0; it < m; ++it) {
             ctx->prof.start(GIPC_PROF_PCG_SPMV, st);
-            if (f64) pcg_spmv_sell_kernel<double, double><<<slb, kPcgThreads, 0, st>>>(A->rowptr, slice_off, sell_col, (const double*)sell_vals, c, c, perm, q, fixed, n, nsl, part, S);
-            else pcg_spmv_sell_kernel<float, float><<<slb, kPcgThreads, 0, st>>>(A->rowptr, slice_off, sell_col, (const float*)sell_vals, c32, c, perm, q, fixed, n, nsl, part, S);
+            if (f64) pcg_spmv_sell_kernel<double, double, 2><<<slb, kPcgThreads, 0, st>>>(A->rowptr, slice_off, sell_col, (const double*)sell_vals, c, c, perm, q, fixed, n, nsl, part, S);
+            else pcg_spmv_sell_kernel<float, float, 4><<<slb, kPcgThreads, 0, st>>>(A->rowptr, slice_off, sell_col, (const float*)sell_vals, c32, c, perm, q, fixed, n, nsl, part, S);
             ctx->prof.stop(GIPC_PROF_PCG_SPMV, st);
             ctx->prof.start(GIPC_PROF_PCG_UPDATE, st);
             pcg_update_kernel<<<vb, kPcgThreads, 0, st>>>(xv, r, c, q, sv, pinv, n, part, S);
