@@ -29,6 +29,7 @@
 // has no float64 operation at all.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 
 #include "common.cuh"
@@ -241,75 +242,188 @@ __global__ void sell_fill_kernel(const int32_t* __restrict__ rowptr, const int32
     }
 }
 
-// q = S(H c) over the SELL-32 layout; alpha = delta_new / (c . q)
-// Persistent grid: warps stride over the slices, lane i computes the three entries of row i of
-// its slice.  Per group of U blocks a lane issues its column and value loads, then the gathers
-// of the direction, then the FMAs.  Block j of a row goes to accumulator j % 2 for
-// j < 4 floor(L / 4) and to accumulator 0 after that, each block adding its three products per
-// entry in column order -- the order of the row-ordered kernel, so both give the same bits.
-template <typename VT, typename PT, int U>
-__global__ void __launch_bounds__(kPcgThreads)
-pcg_spmv_sell_kernel(const int32_t* __restrict__ rowptr, const int64_t* __restrict__ slice_off,
-                     const int32_t* __restrict__ sell_col,
-                     const VT* __restrict__ sell_vals, const PT* __restrict__ cg, const double* __restrict__ c,
-                     const int32_t* __restrict__ perm, double* __restrict__ q, const uint8_t* __restrict__ fixed,
-                     int64_t n, int64_t nsl, double* __restrict__ part, PcgScalars* __restrict__ S) {
+// ---- q = S(H c) over the SELL-32 layout, slices streamed into shared memory by bulk async copies ----
+// Each warp owns NS staging buffers of U steps (U*9*32 values + U*32 column indices, both
+// contiguous in the SELL-32 layout) and one mbarrier per buffer.  Lane 0 issues the bulk copies
+// of the next groups (cp.async.bulk, completion counted on the buffer's mbarrier) before the warp
+// waits for the current one, so HBM streams while the warp gathers the direction and multiplies.  The
+// arithmetic order is that of the row-ordered kernel: block j of a row goes to accumulator j % 2
+// for j < 4 floor(L / 4) and to accumulator 0 after that, each block adding its three products
+// per entry in column order.  Waits are bounded: a wait that runs out records GIPC_ERR_TIMEOUT and
+// the solve stops.
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void async_proxy_fence() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Wait for `parity` of `bar` for at most ~1 s of SM clock; false on timeout.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > 2000000000ll) return false;
+    return true;
+}
+
+// Staging geometry: U steps per group, W warps per CTA, NS buffers per warp.
+template <typename VT, int U, int W, int NS>
+struct StageLayout {
+    static constexpr unsigned kValBytes = U * 9 * kSellC * sizeof(VT);
+    static constexpr unsigned kColBytes = U * kSellC * sizeof(int32_t);
+    static constexpr unsigned kBuf = kValBytes + kColBytes;   // per buffer (multiple of 128)
+    static constexpr unsigned kWarpBytes = NS * kBuf;
+    static constexpr unsigned kBlockBytes = W * kWarpBytes + W * NS * 8;
+};
+
+// Pipeline per warp over the groups g of a slice: the copies of the next NS-1 groups are in
+// flight while group g is multiplied; with NS >= 3 the direction entries of group g+1 are also
+// gathered before group g is multiplied.
+template <typename VT, typename PT, int U, int W, int NS>
+__global__ void __launch_bounds__(W * 32)
+pcg_spmv_tma_kernel(const int32_t* __restrict__ rowptr, const int64_t* __restrict__ slice_off,
+                    const int32_t* __restrict__ sell_col, const VT* __restrict__ sell_vals, const PT* __restrict__ cg,
+                    const double* __restrict__ c, const int32_t* __restrict__ perm, double* __restrict__ q,
+                    const uint8_t* __restrict__ fixed, int64_t n, int64_t nsl, double* __restrict__ part,
+                    PcgScalars* __restrict__ S) {
+    using Lay = StageLayout<VT, U, W, NS>;
+    constexpr bool kPrefetchGather = NS >= 3;
     if (S->done) return;
-    const int lane = threadIdx.x & 31;
+    extern __shared__ __align__(128) unsigned char stage[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    unsigned char* wbuf = stage + w * Lay::kWarpBytes;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(stage + W * Lay::kWarpBytes) + NS * w;
+    if (lane == 0) {
+        for (int b = 0; b < NS; ++b) mbar_init(bars + b, 1);
+        mbar_init_fence();
+    }
+    __syncwarp();
+    unsigned parity = 0;   // bit b: phase parity to wait for on buffer b
+    unsigned base = 0;     // buffer ring position of the current slice's group 0
+    bool timed_out = false;
+    // lane 0: stage group g of the slice (steps [g*U, min((g+1)*U, Ls))) into buffer b
+    auto issue = [&](unsigned b, int64_t off, int64_t Ls, int64_t g) {
+        const int64_t j0 = g * U;
+        const int64_t steps = (Ls - j0) < U ? (Ls - j0) : U;
+        const unsigned vb = (unsigned)(steps * 9 * kSellC * sizeof(VT)), cb = (unsigned)(steps * kSellC * sizeof(int32_t));
+        unsigned char* dst = wbuf + b * Lay::kBuf;
+        async_proxy_fence();
+        mbar_expect_tx(bars + b, vb + cb);
+        bulk_load(dst, sell_vals + (off + j0) * 9 * kSellC, vb, bars + b);
+        bulk_load(dst + Lay::kValBytes, sell_col + (off + j0) * kSellC, cb, bars + b);
+    };
+    auto wait = [&](unsigned b) {   // warp-uniform outcome
+        const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(bars + b, (parity >> b) & 1));
+        parity ^= 1u << b;
+        return ok;
+    };
     const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     double d = 0.0;
-    for (int64_t sl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < nsl; sl += warps) {
+    for (int64_t sl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < nsl && !timed_out; sl += warps) {
+        const int64_t off = slice_off[sl], Ls = slice_off[sl + 1] - off;
+        const int64_t G = (Ls + U - 1) / U;
         const int64_t slot = sl * kSellC + lane;
-        if (slot >= n) continue;
-        const int64_t row = perm[slot];
-        const int64_t off = slice_off[sl];
-        const int64_t L = rowptr[row + 1] - rowptr[row];
+        const bool real = slot < n;
+        const int64_t row = real ? perm[slot] : 0;
+        const int64_t L = real ? rowptr[row + 1] - rowptr[row] : 0;
         const int64_t L4 = L & ~int64_t(3);
         VT a0[3] = {VT(0), VT(0), VT(0)}, a1[3] = {VT(0), VT(0), VT(0)};
-        int64_t j = 0;
-        for (; j + U <= L4; j += U) {
-            int32_t cc[U];
-            VT v[U][9];
-            PT pv[U][3];
-#pragma unroll
-            for (int u = 0; u < U; ++u) cc[u] = __ldcs(sell_col + (off + j + u) * kSellC + lane);
+        PT pc[U][3], pn[U][3];   // gathered direction of the current / next group
+        auto gather = [&](unsigned b, int64_t g, PT (&pv)[U][3]) {
+            const int32_t* sc = reinterpret_cast<const int32_t*>(wbuf + b * Lay::kBuf + Lay::kValBytes);
 #pragma unroll
             for (int u = 0; u < U; ++u)
+                if (g * U + u < L) {
+                    const int64_t cj = sc[u * kSellC + lane];
 #pragma unroll
-                for (int k = 0; k < 9; ++k) v[u][k] = __ldcs(sell_vals + ((off + j + u) * 9 + k) * kSellC + lane);
-#pragma unroll
-            for (int u = 0; u < U; ++u)
-#pragma unroll
-                for (int k = 0; k < 3; ++k) pv[u][k] = __ldg(cg + 3 * (int64_t)cc[u] + k);
+                    for (int k = 0; k < 3; ++k) pv[u][k] = __ldg(cg + 3 * cj + k);
+                }
+        };
+        if (lane == 0)
+            for (int64_t g = 0; g < NS - 1 && g < G; ++g) issue((base + (unsigned)g) % NS, off, Ls, g);
+        if (kPrefetchGather && G > 0) {
+            if (!wait(base % NS)) timed_out = true;
+            else gather(base % NS, 0, pc);
+        }
+        for (int64_t g = 0; g < G && !timed_out; ++g) {
+            const unsigned b = (base + (unsigned)g) % NS;
+            // group g+NS-1 goes to the buffer group g-1 used (released at the end of iteration g-1)
+            if (g + NS - 1 < G && lane == 0) issue((base + (unsigned)(g + NS - 1)) % NS, off, Ls, g + NS - 1);
+            if (kPrefetchGather) {
+                if (g + 1 < G) {
+                    const unsigned bn = (base + (unsigned)g + 1) % NS;
+                    if (!wait(bn)) {
+                        timed_out = true;
+                        break;
+                    }
+                    gather(bn, g + 1, pn);
+                }
+            } else {
+                if (!wait(b)) {
+                    timed_out = true;
+                    break;
+                }
+                gather(b, g, pc);
+            }
+            const VT* sv = reinterpret_cast<const VT*>(wbuf + b * Lay::kBuf);
+            const int64_t j0 = g * U;
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                VT* a = (u & 1) ? a1 : a0;
+                const int64_t jj = j0 + u;
+                if (jj < L) {
+                    VT* a = (jj < L4 && (jj & 1)) ? a1 : a0;
 #pragma unroll
-                for (int e = 0; e < 3; ++e)
+                    for (int e = 0; e < 3; ++e)
 #pragma unroll
-                    for (int k = 0; k < 3; ++k) a[e] = fma(v[u][3 * e + k], (VT)pv[u][k], a[e]);
+                        for (int k = 0; k < 3; ++k)
+                            a[e] = fma(sv[(u * 9 + 3 * e + k) * kSellC + lane], (VT)pc[u][k], a[e]);
+                }
+            }
+            if (kPrefetchGather) {
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) pc[u][k] = pn[u][k];
+            }
+            __syncwarp();   // every lane is done with buffer b before it is refilled
+        }
+        base = (base + (unsigned)G) % NS;
+        if (timed_out) break;
+        if (real) {
+            const bool fx = fixed && fixed[row];
+#pragma unroll
+            for (int e = 0; e < 3; ++e) {
+                const double y = fx ? 0.0 : (double)(a0[e] + a1[e]);
+                q[3 * row + e] = y;
+                d += c[3 * row + e] * y;
             }
         }
-        for (; j < L; ++j) {
-            const int32_t cj = __ldcs(sell_col + (off + j) * kSellC + lane);
-            VT v[9];
-            PT pv[3];
-#pragma unroll
-            for (int k = 0; k < 9; ++k) v[k] = __ldcs(sell_vals + ((off + j) * 9 + k) * kSellC + lane);
-#pragma unroll
-            for (int k = 0; k < 3; ++k) pv[k] = __ldg(cg + 3 * (int64_t)cj + k);
-            VT* a = (j < L4 && (j & 1)) ? a1 : a0;
-#pragma unroll
-            for (int e = 0; e < 3; ++e)
-#pragma unroll
-                for (int k = 0; k < 3; ++k) a[e] = fma(v[3 * e + k], (VT)pv[k], a[e]);
-        }
-        const bool fx = fixed && fixed[row];
-#pragma unroll
-        for (int e = 0; e < 3; ++e) {
-            const double y = fx ? 0.0 : (double)(a0[e] + a1[e]);
-            q[3 * row + e] = y;
-            d += c[3 * row + e] * y;
+    }
+    if (timed_out) {
+        // let copies still in flight land before the CTA can exit, then stop the solve
+        for (int b = 0; b < NS; ++b) mbar_wait_bounded(bars + b, (parity >> b) & 1);
+        if (lane == 0) {
+            S->status = GIPC_ERR_TIMEOUT;
+            S->done = 1;
         }
     }
     const double bs = block_sum(d);
@@ -321,6 +435,30 @@ pcg_spmv_sell_kernel(const int32_t* __restrict__ rowptr, const int64_t* __restri
             S->count_a = 0;
         }
     }
+}
+
+// Staging configurations (U, W, NS) of the FP64 and mixed products, from a sweep on the 4.1M-block
+// C1 system (FP64: 84 us vs 86-110 us for the others tried; mixed: 42 us vs 43-56 us).
+constexpr int kU64 = 1, kW64 = 16, kNS64 = 2;
+constexpr int kU32 = 2, kW32 = 16, kNS32 = 2;
+
+template <typename VT, typename PT, int U, int W, int NS>
+void launch_spmv_tma(const int32_t* rowptr, const int64_t* slice_off, const int32_t* sell_col, const VT* sell_vals,
+                     const PT* cg, const double* c, const int32_t* perm, double* q, const uint8_t* fixed, int64_t n,
+                     int64_t nsl, double* part, PcgScalars* S, cudaStream_t st) {
+    using Lay = StageLayout<VT, U, W, NS>;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(pcg_spmv_tma_kernel<VT, PT, U, W, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)Lay::kBlockBytes);
+        attr = true;
+    }
+    // persistent: as many CTAs as fit in one wave (shared memory bound), at most one per W slices
+    const int per_sm = std::max(1, std::min(16, (int)((220u * 1024u) / Lay::kBlockBytes)));
+    const int64_t want = (nsl + W - 1) / W;
+    const unsigned blocks = (unsigned)std::min<int64_t>(std::max<int64_t>(want, 1), 152 * per_sm);
+    pcg_spmv_tma_kernel<VT, PT, U, W, NS><<<blocks, W * 32, Lay::kBlockBytes, st>>>(
+        rowptr, slice_off, sell_col, sell_vals, cg, c, perm, q, fixed, n, nsl, part, S);
 }
 
 // q = S(H c); alpha = delta_new / (c . q)
@@ -674,9 +812,6 @@ extern "C" gipc_status gipc_pcg(gipc_ctx* ctx, const gipc_bsr* A, const double* 
     const unsigned fb = (unsigned)((nsl * kSellC + 255) / 256);
     if (f64) sell_fill_kernel<double><<<fb, 256, 0, st>>>(A->rowptr, A->colidx, (const double*)A->vals, perm, n, nsl, slice_off, sell_col, (double*)sell_vals);
     else sell_fill_kernel<float><<<fb, 256, 0, st>>>(A->rowptr, A->colidx, (const float*)A->vals, perm, n, nsl, slice_off, sell_col, (float*)sell_vals);
-    unsigned slb = (unsigned)((nsl * 32 + kPcgThreads - 1) / kPcgThreads);
-    if (slb > 152 * 8) slb = 152 * 8;  // persistent: one wave of 8 CTAs per SM
-
     pcg_set_scalars<<<1, 1, 0, st>>>(S, prm->rel_tol, max_iter);
     soa_to_aos_kernel<<<eb, 256, 0, st>>>(rhs, b, nullptr, n, fixed);
     soa_to_aos_kernel<<<eb, 256, 0, st>>>(x, xv, x32, n, fixed);
@@ -695,8 +830,12 @@ extern "C" gipc_status gipc_pcg(gipc_ctx* ctx, const gipc_bsr* A, const double* 
         const int m = (max_iter - launched) < chunk ? (max_iter - launched) : chunk;
         for (int it = 0; it < m; ++it) {
             ctx->prof.start(GIPC_PROF_PCG_SPMV, st);
-            if (f64) pcg_spmv_sell_kernel<double, double, 2><<<slb, kPcgThreads, 0, st>>>(A->rowptr, slice_off, sell_col, (const double*)sell_vals, c, c, perm, q, fixed, n, nsl, part, S);
-            else pcg_spmv_sell_kernel<float, float, 4><<<slb, kPcgThreads, 0, st>>>(A->rowptr, slice_off, sell_col, (const float*)sell_vals, c32, c, perm, q, fixed, n, nsl, part, S);
+            if (f64)
+                launch_spmv_tma<double, double, kU64, kW64, kNS64>(A->rowptr, slice_off, sell_col, (const double*)sell_vals,
+                                                                   c, c, perm, q, fixed, n, nsl, part, S, st);
+            else
+                launch_spmv_tma<float, float, kU32, kW32, kNS32>(A->rowptr, slice_off, sell_col, (const float*)sell_vals,
+                                                                 c32, c, perm, q, fixed, n, nsl, part, S, st);
             ctx->prof.stop(GIPC_PROF_PCG_SPMV, st);
             ctx->prof.start(GIPC_PROF_PCG_UPDATE, st);
             pcg_update_kernel<<<vb, kPcgThreads, 0, st>>>(xv, r, c, q, sv, pinv, n, part, S);
