@@ -421,6 +421,33 @@ typedef struct {
 gipc_status gipc_newton_step(gipc_ctx* ctx, const gipc_scene* sc_h, double* x, double* v,
                              const gipc_step_params* prm_h, gipc_step_stats* stats_h, void* stream);
 
+/* Many independent scenes advanced together (batched time step).  The paper has no batched
+ * form; this is the batching extension of the hot path.
+ *
+ * `all` is the concatenation of the scenes: scene k owns the vertices
+ * [vert_off_h[k], vert_off_h[k+1]); every tetrahedron, surface triangle, edge and vertex lies in
+ * one scene, and the tetrahedra and the three surface lists are ordered by scene.  all.l is not
+ * used (l_h gives each scene's bounding-box diagonal for its stopping test). */
+typedef struct {
+    gipc_scene all;
+    int32_t nscenes;
+    const int64_t* vert_off_h;   /* [nscenes+1] host, from 0 to all.n, strictly increasing */
+    const double* l_h;           /* [nscenes] host */
+} gipc_scene_batch;
+
+/* One implicit time step of every scene (the Newton loop of gipc_newton_step per scene), all
+ * scenes in one set of launches per phase: contacts are never formed across scenes (the broad
+ * phase keys its cells by scene), the system matrix is block diagonal, the PCG keeps each
+ * scene's own alpha, beta, residual and stopping test, and the CCD step, line-search step,
+ * incremental potential and Newton stopping test are per scene.  A scene whose test is met stops
+ * moving while the others continue.
+ *   x, v      as gipc_newton_step, over all vertices
+ *   stats_h   [nscenes] per-scene statistics (host), or NULL
+ * Errors: as gipc_newton_step; GIPC_ERR_INVALID_ARG also when an element spans two scenes or a
+ * list is not ordered by scene (checked on the device, one synchronisation). */
+gipc_status gipc_newton_step_batch(gipc_ctx* ctx, const gipc_scene_batch* batch_h, double* x, double* v,
+                                   const gipc_step_params* prm_h, gipc_step_stats* stats_h, void* stream);
+
 /* ------------------------------------------------------------------ profiling */
 
 /* Kernels that a context can time with CUDA events on the stream they are

@@ -16,7 +16,8 @@ TYPE_IDS = {"PT": 0, "EE": 1, "PE": 2, "PP": 3, "EE_PAR": 4, "PE_PAR": 5, "PP_PA
 NULL_INDEX = -2147483648
 
 __all__ = ["compute_eps_x", "eval_stencils", "assemble_bsr", "pcg", "pcg_noalloc", "snh_params", "tet_rest", "eval_tets",
-           "Surface", "find_contacts", "ccd_max_step", "Scene", "newton_step", "Context", "default_context", "GipcError", "FLAG_ACTIVE", "FLAG_FILTERED",
+           "Surface", "find_contacts", "ccd_max_step", "Scene", "newton_step", "SceneBatch", "newton_step_batch",
+           "Context", "default_context", "GipcError", "FLAG_ACTIVE", "FLAG_FILTERED",
            "FLAG_MOLLIFIED", "FLAG_INVALID", "TYPE_IDS", "NULL_INDEX"]
 
 
@@ -391,3 +392,73 @@ def newton_step(scene, x, v, dt, mu, lam, dhat, kappa, gravity=(0.0, 0.0, -9.81)
     _abi.call("gipc_newton_step", ctx.handle, ctypes.byref(sc), _ptr(x), _ptr(v), ctypes.byref(prm),
               ctypes.byref(stats), _stream(stream))
     return {f: getattr(stats, f) for f, _ in _abi.StepStats._fields_}
+
+
+class SceneBatch:
+    """Independent scenes concatenated for newton_step_batch.
+
+    ``scenes``: list of dicts with numpy arrays x (3, n_k), tets (4, T_k), tris (3, m_k),
+    edges (2, e_k), verts (v_k,) in the scene's own vertex ids, optional fixed (n_k,) and l
+    (bounding-box diagonal; computed if absent).  Vertex ids are offset so scene k owns
+    [vert_off[k], vert_off[k+1]); all lists stay ordered by scene."""
+
+    def __init__(self, scenes, density, device="cuda", ctx=None):
+        import numpy as np
+        off = [0]
+        for sc in scenes:
+            off.append(off[-1] + sc["x"].shape[1])
+        self.vert_off = np.array(off, dtype=np.int64)
+
+        def cat(key, rows):
+            parts = [np.asarray(sc[key], dtype=np.int64) + o for sc, o in zip(scenes, off)]
+            a = np.concatenate(parts, axis=-1) if parts else np.zeros((rows, 0), np.int64)
+            return torch.tensor(np.ascontiguousarray(a.astype(np.int32)), device=device)
+
+        x = np.concatenate([np.asarray(sc["x"], dtype=np.float64) for sc in scenes], axis=1)
+        fixed = np.concatenate([np.asarray(sc.get("fixed", np.zeros(sc["x"].shape[1])), dtype=np.uint8)
+                                for sc in scenes])
+        ls = []
+        for sc in scenes:
+            if sc.get("l") is not None:
+                ls.append(float(sc["l"]))
+            else:
+                ext = sc["x"].max(axis=1) - sc["x"].min(axis=1)
+                ls.append(float(np.linalg.norm(ext)))
+        self.l = np.array(ls, dtype=np.float64)
+        tets = cat("tets", 4)
+        surface = Surface(cat("tris", 3), cat("edges", 2), cat("verts", 1).reshape(-1).contiguous())
+        self.scene = Scene(torch.tensor(x, device=device), tets, surface, density,
+                           fixed=torch.tensor(fixed, device=device), l=float(self.l.max()), ctx=ctx)
+        self.nscenes = len(scenes)
+
+    def split(self, a):
+        """Per-scene views of a [3, n] array."""
+        return [a[:, self.vert_off[k]:self.vert_off[k + 1]] for k in range(self.nscenes)]
+
+    def struct(self):
+        self._keep = (self.vert_off.copy(), self.l.copy())
+        return _abi.SceneBatch(self.scene.struct(), self.nscenes, self._keep[0].ctypes.data, self._keep[1].ctypes.data)
+
+
+def newton_step_batch(batch, x, v, dt, mu, lam, dhat, kappa, gravity=(0.0, 0.0, -9.81), d_thr_ratio=0.1, eps_d=1e-2,
+                      pcg_tol=1e-4, max_pcg=500, max_newton=50, max_ls=30, precision="fp64", hess_mode="dense",
+                      ctx=None, stream=None):
+    """One implicit time step of every scene of a SceneBatch; updates x and v in place and returns a
+    list of per-scene stats dicts (gipc_newton_step_batch)."""
+    ctx = ctx or default_context()
+    _check(x, "x", torch.float64, 3)
+    _check(v, "v", torch.float64, 3)
+    prm = _abi.StepParams()
+    prm.dt = float(dt)
+    prm.gravity[:] = [float(g) for g in gravity]
+    prm.elastic = _abi.ElasticParams(float(mu), float(lam), 0.0)
+    prm.barrier = _abi.BarrierParams(float(dhat), float(kappa), float(d_thr_ratio))
+    prm.eps_d, prm.pcg_tol = float(eps_d), float(pcg_tol)
+    prm.max_pcg, prm.max_newton, prm.max_ls = int(max_pcg), int(max_newton), int(max_ls)
+    prm.prec = {"fp64": _abi.GIPC_FP64, "mixed": _abi.GIPC_MIXED}[precision]
+    prm.hess_mode = {"dense": _abi.GIPC_HESS_DENSE, "rank1": _abi.GIPC_HESS_RANK1}[hess_mode]
+    stats = (_abi.StepStats * batch.nscenes)()
+    b = batch.struct()
+    _abi.call("gipc_newton_step_batch", ctx.handle, ctypes.byref(b), _ptr(x), _ptr(v), ctypes.byref(prm), stats,
+              _stream(stream))
+    return [{f: getattr(s, f) for f, _ in _abi.StepStats._fields_} for s in stats]

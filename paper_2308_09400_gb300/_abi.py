@@ -54,6 +54,10 @@ class Scene(ctypes.Structure):
                 ("l", ctypes.c_double)]
 
 
+class SceneBatch(ctypes.Structure):
+    _fields_ = [("all", Scene), ("nscenes", ctypes.c_int32), ("vert_off_h", ctypes.c_void_p), ("l_h", ctypes.c_void_p)]
+
+
 class StepParams(ctypes.Structure):
     _fields_ = [("dt", ctypes.c_double), ("gravity", ctypes.c_double * 3), ("elastic", ElasticParams),
                 ("barrier", BarrierParams), ("eps_d", ctypes.c_double), ("pcg_tol", ctypes.c_double),
@@ -101,6 +105,7 @@ SIGNATURES = {
     "gipc_ccd_max_step": (_INT, [_P, _P, _P, _I64, ctypes.POINTER(Surface), _D, ctypes.POINTER(_D), _P]),
     "gipc_newton_step": (_INT, [_P, ctypes.POINTER(Scene), _P, _P, ctypes.POINTER(StepParams),
                                 ctypes.POINTER(StepStats), _P]),
+    "gipc_newton_step_batch": (_INT, [_P, ctypes.POINTER(SceneBatch), _P, _P, ctypes.POINTER(StepParams), _P, _P]),
     "gipc_profile_begin": (_INT, [_P]),
     "gipc_profile_read": (_INT, [_P, _INT, ctypes.POINTER(KernelTime)]),
     "gipc_profile_stop": (_INT, [_P]),

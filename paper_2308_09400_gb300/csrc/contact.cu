@@ -174,7 +174,8 @@ struct Surf {
 struct __align__(16) Entry {
     float lx, ly, lz;
     int32_t id;
-    float hx, hy, hz, pad;
+    float hx, hy, hz;
+    int32_t scene;   // scene of the target (batched scenes never pair across scenes)
 };
 
 struct Grid {
@@ -189,9 +190,11 @@ struct Grid {
 
 __device__ __forceinline__ int64_t cell_of(double v, double inv_h) { return (int64_t)floor(__dmul_rn(v, inv_h)); }
 
-__device__ __forceinline__ uint64_t bucket_of(int64_t cx, int64_t cy, int64_t cz, uint64_t mask) {
-    // Teschner et al. (2003) spatial hash of the three cell coordinates, then a splitmix64 finaliser
-    uint64_t h = ((uint64_t)cx * 73856093ull) ^ ((uint64_t)cy * 19349663ull) ^ ((uint64_t)cz * 83492791ull);
+__device__ __forceinline__ uint64_t bucket_of(int64_t cx, int64_t cy, int64_t cz, int32_t scene, uint64_t mask) {
+    // Teschner et al. (2003) spatial hash of the three cell coordinates and the scene, then a
+    // splitmix64 finaliser
+    uint64_t h = ((uint64_t)cx * 73856093ull) ^ ((uint64_t)cy * 19349663ull) ^ ((uint64_t)cz * 83492791ull) ^
+                 ((uint64_t)(uint32_t)scene * 2654435761ull);
     h ^= h >> 31;
     h *= 0xbf58476d1ce4e5b9ull;
     h ^= h >> 29;
@@ -285,24 +288,26 @@ __global__ void point_cells_kernel(const double* __restrict__ x, const double* _
 // pair is then met exactly once.
 template <bool FILL>
 __global__ void bucket_kernel(const double* __restrict__ lo, const double* __restrict__ hi, int64_t m,
+                              const int32_t* __restrict__ prim, const int32_t* __restrict__ vscene,
                               const double* __restrict__ inv_h, uint64_t mask, int32_t* __restrict__ bcnt,
                               const int64_t* __restrict__ boff, Entry* __restrict__ ent) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= m) return;
+    const int32_t scene = vscene ? vscene[prim[t]] : 0;
     const double l[3] = {lo[t], lo[m + t], lo[2 * m + t]}, h[3] = {hi[t], hi[m + t], hi[2 * m + t]};
     int64_t c0[3], c1[3];
     const int64_t nc = box_cells(l[0], l[1], l[2], h[0], h[1], h[2], *inv_h, c0, c1);
     if (nc > kMaxCellsPerBox) return;
     const int64_t nx = c1[0] - c0[0] + 1, ny = c1[1] - c0[1] + 1;
     auto bucket_at = [&](int64_t li) {
-        return bucket_of(c0[0] + li % nx, c0[1] + (li / nx) % ny, c0[2] + li / (nx * ny), mask);
+        return bucket_of(c0[0] + li % nx, c0[1] + (li / nx) % ny, c0[2] + li / (nx * ny), scene, mask);
     };
     Entry E;
     if (FILL) {
         E.lx = __double2float_rd(l[0]); E.ly = __double2float_rd(l[1]); E.lz = __double2float_rd(l[2]);
         E.hx = __double2float_ru(h[0]); E.hy = __double2float_ru(h[1]); E.hz = __double2float_ru(h[2]);
         E.id = (int32_t)t;
-        E.pad = 0.f;
+        E.scene = scene;
     }
     for (int64_t li = 0; li < nc; ++li) {
         const uint64_t b = bucket_at(li);
@@ -332,7 +337,7 @@ struct PairList {
 template <int KIND>
 __global__ void __launch_bounds__(kThreads)
 scan_pairs_kernel(const double* __restrict__ x, const double* __restrict__ dx, int64_t n, Surf S, Grid G,
-                  PairList L) {
+                  const int32_t* __restrict__ vscene, PairList L) {
     __shared__ int32_t qq_sh[kWarps][64], qt_sh[kWarps][64];
     int32_t* qq = qq_sh[threadIdx.x >> 5];
     int32_t* qt = qt_sh[threadIdx.x >> 5];
@@ -372,6 +377,7 @@ scan_pairs_kernel(const double* __restrict__ x, const double* __restrict__ dx, i
                 qh[c] = fmax(a, b);
             }
         }
+        const int32_t qs = vscene ? vscene[KIND == K_EE ? ia : p] : 0;   // the query's scene
         int64_t c0[3], c1[3];
         if (box_cells(ql[0], ql[1], ql[2], qh[0], qh[1], qh[2], ih, c0, c1) > kMaxCellsPerBox) continue;
         const float fl[3] = {__double2float_rd(ql[0]), __double2float_rd(ql[1]), __double2float_rd(ql[2])};
@@ -379,7 +385,7 @@ scan_pairs_kernel(const double* __restrict__ x, const double* __restrict__ dx, i
         for (int64_t cz = c0[2]; cz <= c1[2]; ++cz)
             for (int64_t cy = c0[1]; cy <= c1[1]; ++cy)
                 for (int64_t cx = c0[0]; cx <= c1[0]; ++cx) {
-                    const uint64_t b = bucket_of(cx, cy, cz, G.mask);
+                    const uint64_t b = bucket_of(cx, cy, cz, qs, G.mask);
                     const int64_t e0 = G.boff[b], e1 = G.boff[b + 1];
                     for (int64_t base = e0; base < e1; base += 32) {
                         const int64_t e = base + lane;
@@ -388,8 +394,8 @@ scan_pairs_kernel(const double* __restrict__ x, const double* __restrict__ dx, i
                         if (e < e1) {
                             const float4 A = __ldg(ent4 + 2 * e), B = __ldg(ent4 + 2 * e + 1);
                             t = __float_as_int(A.w);
-                            ok = fl[0] <= B.x && fh[0] >= A.x && fl[1] <= B.y && fh[1] >= A.y && fl[2] <= B.z &&
-                                 fh[2] >= A.z && (KIND != K_EE || t > q);
+                            ok = __float_as_int(B.w) == qs && fl[0] <= B.x && fh[0] >= A.x && fl[1] <= B.y &&
+                                 fh[1] >= A.y && fl[2] <= B.z && fh[2] >= A.z && (KIND != K_EE || t > q);
                             if (ok) {
                                 const double tl[3] = {G.lo[t], G.lo[G.m + t], G.lo[2 * G.m + t]};
                                 const double th[3] = {G.hi[t], G.hi[G.m + t], G.hi[2 * G.m + t]};
@@ -601,9 +607,11 @@ __device__ __forceinline__ double warp_min(double v) {
 // ACCD of every candidate pair (point-triangle pairs first); the step is the minimum over pairs.
 __global__ void ccd_pairs_kernel(const double* __restrict__ x, const double* __restrict__ dx, int64_t n, Surf S,
                                  const int32_t* __restrict__ pq, const int32_t* __restrict__ ptg, int64_t npt,
-                                 int64_t np, double s, int max_iter, unsigned long long* __restrict__ amin) {
+                                 int64_t np, double s, int max_iter, const int32_t* __restrict__ vscene,
+                                 unsigned long long* __restrict__ amin) {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double best = 1.0;
+    int32_t scene = 0;
     if (r < np) {
         const int32_t q = pq[r], t = ptg[r];
         int32_t ids[4];
@@ -619,12 +627,22 @@ __global__ void ccd_pairs_kernel(const double* __restrict__ x, const double* __r
             P[a] = ld3(dx, n, ids[a]);
         }
         best = accd(X, P, r < npt, s, max_iter);
+        if (vscene) scene = vscene[ids[0]];
     }
-    best = warp_min(best);
-    if ((threadIdx.x & 31) == 0 && best < 1.0) atomic_min_pos(amin, best);
+    if (!vscene) {   // one scene: one atomic per warp
+        best = warp_min(best);
+        if ((threadIdx.x & 31) == 0 && best < 1.0) atomic_min_pos(amin, best);
+    } else if (best < 1.0) {
+        atomic_min_pos(amin + scene, best);
+    }
 }
 
 inline unsigned nblk(int64_t w, int t) { return (unsigned)std::max<int64_t>(1, (w + t - 1) / t); }
+
+__global__ void fill_kernel(double* __restrict__ a, int64_t m, double v) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) a[i] = v;
+}
 // persistent warp-per-query grids: at most 16 blocks of kWarps warps per SM
 inline unsigned wblk(int64_t queries) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>((queries + kWarps - 1) / kWarps, 152 * 16)); }
 
@@ -632,7 +650,8 @@ inline unsigned wblk(int64_t queries) { return (unsigned)std::max<int64_t>(1, st
 // d if given, padded by pad).  Synchronises once per cell-size attempt.  `pts`: surface
 // vertices whose swept boxes also bound the cell size (CCD).
 gipc_status build_grid(gipc_ctx* ctx, int g, const double* x, const double* d, int64_t n, const int32_t* prim, int nv,
-                       int64_t m, double pad, const gipc_surface* pts, Grid& G, cudaStream_t st) {
+                       int64_t m, double pad, const gipc_surface* pts, const int32_t* vscene, Grid& G,
+                       cudaStream_t st) {
     gipc_status s;
     gipc_scratch* slot = ctx->slot;
     const int* gs = kGridSlots[g];
@@ -678,11 +697,12 @@ gipc_status build_grid(gipc_ctx* ctx, int g, const double* x, const double* d, i
     ep = (ep + 15) & ~uintptr_t(15);
     Entry* ent = reinterpret_cast<Entry*>(ep);
     cudaMemsetAsync(bcnt, 0, sizeof(int32_t) * buckets, st);
-    bucket_kernel<false><<<nblk(m, 256), 256, 0, st>>>(lo, hi, m, misc + 1, buckets - 1, bcnt, nullptr, nullptr);
+    bucket_kernel<false><<<nblk(m, 256), 256, 0, st>>>(lo, hi, m, prim, vscene, misc + 1, buckets - 1, bcnt, nullptr,
+                                                        nullptr);
     if (exclusive_scan<int32_t>(bcnt, boff, (int64_t)buckets, btmp, st) != cudaSuccess)
         return check_launch("contact grid: bucket scan");
     cudaMemsetAsync(bcnt, 0, sizeof(int32_t) * buckets, st);
-    bucket_kernel<true><<<nblk(m, 256), 256, 0, st>>>(lo, hi, m, misc + 1, buckets - 1, bcnt, boff, ent);
+    bucket_kernel<true><<<nblk(m, 256), 256, 0, st>>>(lo, hi, m, prim, vscene, misc + 1, buckets - 1, bcnt, boff, ent);
     G = Grid{lo, hi, m, misc + 1, buckets - 1, boff, ent};
     return check_launch("contact grid");
 }
@@ -691,7 +711,8 @@ gipc_status build_grid(gipc_ctx* ctx, int g, const double* x, const double* d, i
 // (if any) into the context's pair list; *npt / *np: point-triangle pairs / all pairs.
 // Synchronises once per attempt (the list grows when the count exceeds its capacity).
 gipc_status collect_pairs(gipc_ctx* ctx, const double* x, const double* d, int64_t n, const Surf& S, const Grid* Gt,
-                          const Grid* Ge, bool swept, int64_t* npt, int64_t* np, PairList& L, cudaStream_t st) {
+                          const Grid* Ge, bool swept, const int32_t* vscene, int64_t* npt, int64_t* np, PairList& L,
+                          cudaStream_t st) {
     gipc_status s;
     unsigned long long* counter = reinterpret_cast<unsigned long long*>(ctx->slot[C_MISC].as<double>() + kMiscPairs);
     for (int attempt = 0; attempt < 2; ++attempt) {
@@ -702,11 +723,11 @@ gipc_status collect_pairs(gipc_ctx* ctx, const double* x, const double* d, int64
         unsigned long long c[2] = {0, 0};
         cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st);
         if (Gt) {
-            if (swept) scan_pairs_kernel<K_PT_SWEPT><<<wblk(S.nvert), kThreads, 0, st>>>(x, d, n, S, *Gt, L);
-            else scan_pairs_kernel<K_PT><<<wblk(S.nvert), kThreads, 0, st>>>(x, d, n, S, *Gt, L);
+            if (swept) scan_pairs_kernel<K_PT_SWEPT><<<wblk(S.nvert), kThreads, 0, st>>>(x, d, n, S, *Gt, vscene, L);
+            else scan_pairs_kernel<K_PT><<<wblk(S.nvert), kThreads, 0, st>>>(x, d, n, S, *Gt, vscene, L);
         }
         cudaMemcpyAsync(&c[0], counter, sizeof(c[0]), cudaMemcpyDeviceToHost, st);
-        if (Ge) scan_pairs_kernel<K_EE><<<wblk(S.nedge), kThreads, 0, st>>>(x, d, n, S, *Ge, L);
+        if (Ge) scan_pairs_kernel<K_EE><<<wblk(S.nedge), kThreads, 0, st>>>(x, d, n, S, *Ge, vscene, L);
         cudaMemcpyAsync(&c[1], counter, sizeof(c[1]), cudaMemcpyDeviceToHost, st);
         if (cudaStreamSynchronize(st) != cudaSuccess) return check_launch("contact pairs: sync");
         if ((int64_t)c[1] <= L.cap) {
@@ -725,7 +746,7 @@ gipc_status collect_pairs(gipc_ctx* ctx, const double* x, const double* d, int64
 // Internal entry points shared with the time-step driver (newton.cu).
 gipc_status find_contacts_impl(gipc_ctx* ctx, const double* x, const double* rest_x, int64_t n, const gipc_surface& srf,
                                double dhat, int32_t* stencils, double* eps_x, int64_t cap, int64_t* count,
-                               bool compact, cudaStream_t st) {
+                               bool compact, const int32_t* vscene, int64_t* npt_out, cudaStream_t st) {
     gipc_prof_span span(ctx->prof, GIPC_PROF_CONTACTS, st);
     Surf S{srf.tris, srf.ntri, srf.edges, srf.nedge, srf.verts, srf.nvert};
     const double pad = dhat * (1.0 + 1e-9);
@@ -737,13 +758,15 @@ gipc_status find_contacts_impl(gipc_ctx* ctx, const double* x, const double* res
     if ((s = ctx->slot[C_MISC].reserve(16 * sizeof(double))) != GIPC_OK) return s;
     const bool pt = S.nvert > 0 && S.ntri > 0;
     Grid Gt{}, Ge{};
-    if (pt && (s = build_grid(ctx, 0, x, nullptr, n, S.tris, 3, S.ntri, pad, nullptr, Gt, st)) != GIPC_OK) return s;
-    if (S.nedge > 0 && (s = build_grid(ctx, 1, x, nullptr, n, S.edges, 2, S.nedge, pad, nullptr, Ge, st)) != GIPC_OK)
+    if (pt && (s = build_grid(ctx, 0, x, nullptr, n, S.tris, 3, S.ntri, pad, nullptr, vscene, Gt, st)) != GIPC_OK)
+        return s;
+    if (S.nedge > 0 &&
+        (s = build_grid(ctx, 1, x, nullptr, n, S.edges, 2, S.nedge, pad, nullptr, vscene, Ge, st)) != GIPC_OK)
         return s;
     PairList L{};
     int64_t npt = 0, np = 0;
-    if ((s = collect_pairs(ctx, x, nullptr, n, S, pt ? &Gt : nullptr, S.nedge > 0 ? &Ge : nullptr, false, &npt, &np, L,
-                           st)) != GIPC_OK)
+    if ((s = collect_pairs(ctx, x, nullptr, n, S, pt ? &Gt : nullptr, S.nedge > 0 ? &Ge : nullptr, false, vscene, &npt,
+                           &np, L, st)) != GIPC_OK)
         return s;
     // classify once, count per query
     if ((s = ctx->slot[C_CNT].reserve(sizeof(int32_t) * (nq + 1))) != GIPC_OK) return s;
@@ -757,10 +780,12 @@ gipc_status find_contacts_impl(gipc_ctx* ctx, const double* x, const double* res
     int64_t* off = ctx->slot[C_QOFF].as<int64_t>();
     if (exclusive_scan<int32_t>(cnt, off, nq, off + nq + 2, st) != cudaSuccess)
         return check_launch("gipc_find_contacts: scan");
-    int64_t total = 0;
+    int64_t total = 0, npt_contacts = 0;
     cudaMemcpyAsync(&total, off + nq, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(&npt_contacts, off + S.nvert, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
     if (cudaStreamSynchronize(st) != cudaSuccess) return check_launch("gipc_find_contacts: sync");
     *count = total;
+    if (npt_out) *npt_out = npt_contacts;
     if (total > cap) return fail(GIPC_ERR_CAPACITY, "gipc_find_contacts: %lld contacts, capacity %lld", (long long)total, (long long)cap);
     if (total == 0) return GIPC_OK;
     // rows of the output are `stride` apart: the caller's capacity, or the count itself (compact)
@@ -774,31 +799,33 @@ gipc_status find_contacts_impl(gipc_ctx* ctx, const double* x, const double* res
     return check_launch("gipc_find_contacts");
 }
 
+// alpha_h: host [nscenes] step per scene (nscenes = 1 and vscene = NULL for one scene);
+// amin_dev: device [nscenes] scratch for the per-scene minima when vscene is given.
 gipc_status ccd_impl(gipc_ctx* ctx, const double* x, const double* d, int64_t n, const gipc_surface& srf, double slack,
-                     double* alpha, cudaStream_t st) {
+                     double* alpha_h, cudaStream_t st, const int32_t* vscene, int nscenes, double* amin_dev) {
     gipc_prof_span span(ctx->prof, GIPC_PROF_CCD, st);
     Surf S{srf.tris, srf.ntri, srf.edges, srf.nedge, srf.verts, srf.nvert};
     const int max_iter = 100000;
     gipc_status s;
     if ((s = ctx->slot[C_MISC].reserve(16 * sizeof(double))) != GIPC_OK) return s;
-    unsigned long long* amin = reinterpret_cast<unsigned long long*>(ctx->slot[C_MISC].as<double>() + kMiscAmin);
-    const double one = 1.0;
-    cudaMemcpyAsync(amin, &one, sizeof(double), cudaMemcpyHostToDevice, st);
+    double* amin_d = vscene ? amin_dev : ctx->slot[C_MISC].as<double>() + kMiscAmin;
+    const int ns = vscene ? nscenes : 1;
+    fill_kernel<<<nblk(ns, 256), 256, 0, st>>>(amin_d, ns, 1.0);
+    unsigned long long* amin = reinterpret_cast<unsigned long long*>(amin_d);
     Grid Gt{}, Ge{};
     const bool pt = S.nvert > 0 && S.ntri > 0;
-    if (pt && (s = build_grid(ctx, 0, x, d, n, S.tris, 3, S.ntri, 0.0, &srf, Gt, st)) != GIPC_OK) return s;
-    if (S.nedge > 0 && (s = build_grid(ctx, 1, x, d, n, S.edges, 2, S.nedge, 0.0, nullptr, Ge, st)) != GIPC_OK)
+    if (pt && (s = build_grid(ctx, 0, x, d, n, S.tris, 3, S.ntri, 0.0, &srf, vscene, Gt, st)) != GIPC_OK) return s;
+    if (S.nedge > 0 && (s = build_grid(ctx, 1, x, d, n, S.edges, 2, S.nedge, 0.0, nullptr, vscene, Ge, st)) != GIPC_OK)
         return s;
     PairList L{};
     int64_t npt = 0, np = 0;
-    if ((s = collect_pairs(ctx, x, d, n, S, pt ? &Gt : nullptr, S.nedge > 0 ? &Ge : nullptr, true, &npt, &np, L, st)) !=
-        GIPC_OK)
+    if ((s = collect_pairs(ctx, x, d, n, S, pt ? &Gt : nullptr, S.nedge > 0 ? &Ge : nullptr, true, vscene, &npt, &np, L,
+                           st)) != GIPC_OK)
         return s;
-    if (np > 0) ccd_pairs_kernel<<<nblk(np, 128), 128, 0, st>>>(x, d, n, S, L.q, L.t, npt, np, slack, max_iter, amin);
-    double a = 1.0;
-    cudaMemcpyAsync(&a, amin, sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (np > 0)
+        ccd_pairs_kernel<<<nblk(np, 128), 128, 0, st>>>(x, d, n, S, L.q, L.t, npt, np, slack, max_iter, vscene, amin);
+    cudaMemcpyAsync(alpha_h, amin_d, sizeof(double) * ns, cudaMemcpyDeviceToHost, st);
     if (cudaStreamSynchronize(st) != cudaSuccess) return check_launch("gipc_ccd_max_step: sync");
-    *alpha = a;
     return check_launch("gipc_ccd_max_step");
 }
 
@@ -814,8 +841,8 @@ extern "C" gipc_status gipc_find_contacts(gipc_ctx* ctx, const double* x, const 
     if (!x || !rest_x || (srf->ntri && !srf->tris) || (srf->nedge && !srf->edges) || (srf->nvert && !srf->verts) ||
         (capacity > 0 && (!stencils || !eps_x)))
         return fail(GIPC_ERR_INVALID_ARG, "gipc_find_contacts: null pointer");
-    return find_contacts_impl(ctx, x, rest_x, n, *srf, dhat, stencils, eps_x, capacity, count_h, false,
-                              (cudaStream_t)stream);
+    return find_contacts_impl(ctx, x, rest_x, n, *srf, dhat, stencils, eps_x, capacity, count_h, false, nullptr,
+                              nullptr, (cudaStream_t)stream);
 }
 
 extern "C" gipc_status gipc_ccd_max_step(gipc_ctx* ctx, const double* x, const double* d, int64_t n,
@@ -823,5 +850,5 @@ extern "C" gipc_status gipc_ccd_max_step(gipc_ctx* ctx, const double* x, const d
     using namespace gipc;
     if (!ctx || !srf || !alpha_h || !x || !d) return fail(GIPC_ERR_INVALID_ARG, "gipc_ccd_max_step: null pointer");
     if (n < 0 || !(slack > 0.0 && slack < 1.0)) return fail(GIPC_ERR_INVALID_ARG, "gipc_ccd_max_step: need 0 < slack < 1");
-    return ccd_impl(ctx, x, d, n, *srf, slack, alpha_h, (cudaStream_t)stream);
+    return ccd_impl(ctx, x, d, n, *srf, slack, alpha_h, (cudaStream_t)stream, nullptr, 1, nullptr);
 }

@@ -78,7 +78,7 @@ struct gipc_prof_span {
 
 struct gipc_ctx {
     int device = 0;
-    static constexpr int kSlots = 40;   // assembly 0-8, pcg 9-15, contacts 16-19 and 30-39, time step 20-29
+    static constexpr int kSlots = 48;   // assembly 0-8, pcg 9-15 and 40, contacts 16-19 and 30-39, time step 20-29 and 41-47
     gipc_scratch slot[kSlots];
     gipc_profiler prof;
     void release_all() {

@@ -8,6 +8,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <vector>
 
 #include "common.cuh"
 #include "context.cuh"
@@ -16,9 +17,12 @@ namespace gipc {
 
 gipc_status find_contacts_impl(gipc_ctx* ctx, const double* x, const double* rest_x, int64_t n, const gipc_surface& srf,
                                double dhat, int32_t* stencils, double* eps_x, int64_t cap, int64_t* count,
-                               bool compact, cudaStream_t st);
+                               bool compact, const int32_t* vscene, int64_t* npt_out, cudaStream_t st);
 gipc_status ccd_impl(gipc_ctx* ctx, const double* x, const double* d, int64_t n, const gipc_surface& srf, double slack,
-                     double* alpha, cudaStream_t st);
+                     double* alpha_h, cudaStream_t st, const int32_t* vscene, int nscenes, double* amin_dev);
+gipc_status pcg_impl(gipc_ctx* ctx, const gipc_bsr* A, const double* rhs, double* x, const uint8_t* fixed,
+                     const gipc_pcg_params* prm, int* iters_out_h, double* rel_out_h, cudaStream_t st,
+                     const int64_t* voff, int nscenes, int* scene_iters_h, int* scene_status_h);
 
 namespace {
 
@@ -168,7 +172,7 @@ struct Step {
         for (int attempt = 0; attempt < 2; ++attempt) {
             int64_t cnt = 0;
             const gipc_status s = find_contacts_impl(ctx, x, sc.rest_x, n, sc.surface, prm.barrier.dhat, cs.st, cs.eps,
-                                                     cs.cap, &cnt, true, st);
+                                                     cs.cap, &cnt, true, nullptr, nullptr, st);
             if (s == GIPC_OK) {
                 cs.k = cnt;
                 return GIPC_OK;
@@ -296,7 +300,7 @@ struct Step {
             S.pcg_iters += pit;
             // step filter and backtracking
             double alpha = 1.0;
-            if ((s = ccd_impl(ctx, x, d, n, sc.surface, 0.1, &alpha, st)) != GIPC_OK) return s;
+            if ((s = ccd_impl(ctx, x, d, n, sc.surface, 0.1, &alpha, st, nullptr, 1, nullptr)) != GIPC_OK) return s;
             cudaMemcpyAsync(xp, x, sizeof(double) * m3, cudaMemcpyDeviceToDevice, st);
             const int nxt = 1 - cur;
             double I_new = I_prev;
@@ -328,6 +332,402 @@ struct Step {
     }
 };
 
+
+// ============================================================================ batched scenes
+// Many independent scenes in one set of launches per phase: the scenes are concatenated (vertex
+// ranges voff), contacts never pair across scenes (the broad phase hashes the scene into its
+// cells), the matrix is block diagonal, the PCG keeps per-scene scalars, and every scalar of the
+// Newton loop (energies, CCD step, line-search step, stopping test) is per scene.
+
+enum BatchSlot { B_VS = 41, B_OFF = 42, B_SCAL = 43, B_MASK = 44 };
+
+// scene of vertex v for every v (scene k owns [voff[k], voff[k+1]))
+__global__ void vertex_scene_kernel(const int64_t* __restrict__ voff, int nscenes, int64_t n, int32_t* __restrict__ vs) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    int lo = 0, hi = nscenes - 1;
+    while (lo < hi) {   // last k with voff[k] <= v
+        const int mid = (lo + hi + 1) >> 1;
+        if (voff[mid] <= v) lo = mid;
+        else hi = mid - 1;
+    }
+    vs[v] = lo;
+}
+
+// Layout check: every element inside one scene; element lists non-decreasing in scene.
+__global__ void batch_layout_kernel(const int32_t* __restrict__ ids, int nv, int64_t m, int64_t n,
+                                    const int32_t* __restrict__ vs, int32_t* __restrict__ bad) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= m) return;
+    int32_t s0 = -1;
+    for (int a = 0; a < nv; ++a) {
+        const int32_t v = ids[a * m + t];
+        if (v < 0 || v >= n) {
+            atomicOr(bad, 1);
+            return;
+        }
+        if (s0 < 0) s0 = vs[v];
+        else if (vs[v] != s0) atomicOr(bad, 2);
+    }
+    if (t + 1 < m) {
+        const int32_t v1 = ids[t + 1];
+        if (v1 >= 0 && v1 < n && vs[v1] < s0) atomicOr(bad, 4);
+    }
+}
+
+// Range [lo, hi) of scene sc in a list of m items whose scene (of the first vertex) is
+// non-decreasing; stencils decode a sign-encoded first slot.
+template <bool STENCIL>
+__device__ __forceinline__ void scene_range(const int32_t* __restrict__ first, int64_t lo0, int64_t hi0,
+                                            const int32_t* __restrict__ vs, int sc, int64_t& lo, int64_t& hi) {
+    auto key = [&](int64_t i) {
+        const int32_t v = first[i];
+        return vs[STENCIL ? (v >= 0 ? v : ~v) : v];
+    };
+    int64_t a = lo0, b = hi0;   // first index with key >= sc
+    while (a < b) {
+        const int64_t m = (a + b) >> 1;
+        if (key(m) < sc) a = m + 1;
+        else b = m;
+    }
+    lo = a;
+    b = hi0;                    // first index with key > sc
+    while (a < b) {
+        const int64_t m = (a + b) >> 1;
+        if (key(m) <= sc) a = m + 1;
+        else b = m;
+    }
+    hi = a;
+}
+
+__device__ __forceinline__ double bsum_all(double v) {   // fixed-order block sum, broadcast
+    __shared__ double sh[32];
+    __shared__ double total;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        double t = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) total = t;
+    }
+    __syncthreads();
+    const double r = total;
+    __syncthreads();
+    return r;
+}
+
+// Per-scene incremental potential: 1/2 sum m |x - xt|^2 over the scene's vertices + its tets'
+// energies + its stencils' energies (point-triangle block [0, npt), then edge-edge block).
+// One CTA per scene, each sum in a fixed order.
+__global__ void __launch_bounds__(256)
+scene_energy_kernel(const double* __restrict__ x, const double* __restrict__ xt, const double* __restrict__ mass,
+                    int64_t n, const int64_t* __restrict__ voff, const int32_t* __restrict__ tets, int64_t T,
+                    const double* __restrict__ te, const int32_t* __restrict__ st, int64_t k, int64_t npt,
+                    const double* __restrict__ se, const int32_t* __restrict__ vs, double* __restrict__ I,
+                    int64_t* __restrict__ contacts) {
+    const int sc = blockIdx.x;
+    double a = 0.0;
+    for (int64_t i = voff[sc] + threadIdx.x; i < voff[sc + 1]; i += blockDim.x) {
+        const double dx = __dsub_rn(x[i], xt[i]), dy = __dsub_rn(x[n + i], xt[n + i]), dz = __dsub_rn(x[2 * n + i], xt[2 * n + i]);
+        a = __dadd_rn(a, __dmul_rn(mass[i], __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz))));
+    }
+    const double inertia = bsum_all(a);
+    int64_t lo, hi;
+    scene_range<false>(tets, 0, T, vs, sc, lo, hi);
+    a = 0.0;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) a = __dadd_rn(a, te[i]);
+    const double elastic = bsum_all(a);
+    int64_t l1, h1, l2, h2;
+    scene_range<true>(st, 0, npt, vs, sc, l1, h1);
+    scene_range<true>(st, npt, k, vs, sc, l2, h2);
+    a = 0.0;
+    for (int64_t i = l1 + threadIdx.x; i < h1; i += blockDim.x) a = __dadd_rn(a, se[i]);
+    for (int64_t i = l2 + threadIdx.x; i < h2; i += blockDim.x) a = __dadd_rn(a, se[i]);
+    const double barrier = bsum_all(a);
+    if (threadIdx.x == 0) {
+        I[sc] = __dadd_rn(__dadd_rn(__dmul_rn(0.5, inertia), elastic), barrier);
+        if (contacts) contacts[sc] = (h1 - l1) + (h2 - l2);
+    }
+}
+
+// Per-scene max |d| over the scene's vertices.
+__global__ void __launch_bounds__(256)
+scene_maxabs_kernel(const double* __restrict__ d, int64_t n, const int64_t* __restrict__ voff, double* __restrict__ out) {
+    const int sc = blockIdx.x;
+    double a = 0.0;
+    for (int64_t i = voff[sc] + threadIdx.x; i < voff[sc + 1]; i += blockDim.x)
+        a = fmax(a, fmax(fabs(d[i]), fmax(fabs(d[n + i]), fabs(d[2 * n + i]))));
+    __shared__ double sh[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a = fmax(a, __shfl_xor_sync(0xffffffffu, a, o));
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = a;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, sh[w]);
+        out[sc] = m;
+    }
+}
+
+// x = xp + alpha[scene] d
+__global__ void axpy_scene_kernel(const double* __restrict__ xp, const double* __restrict__ d,
+                                  const double* __restrict__ alpha, const int32_t* __restrict__ vs, int64_t n,
+                                  double* __restrict__ x) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= 3 * n) return;
+    x[j] = __dadd_rn(xp[j], __dmul_rn(alpha[vs[j % n]], d[j]));
+}
+
+// solver filter: fixed vertices and every vertex of a scene that has stopped
+__global__ void scene_mask_kernel(const uint8_t* __restrict__ fixed, const int32_t* __restrict__ vs,
+                                  const int32_t* __restrict__ active, int64_t n, uint8_t* __restrict__ mask) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    mask[v] = (fixed && fixed[v]) || !active[vs[v]] ? 1 : 0;
+}
+
+struct BatchStep : Step {
+    int ns;
+    const int64_t* voff_h;
+    const double* l_h;
+    int64_t* voff = nullptr;    // device [ns+1]
+    int32_t* vs = nullptr;      // device [n]
+    double* sI = nullptr;       // device per-scene scalars
+    double* sA = nullptr;
+    double* sD = nullptr;
+    int64_t* sC = nullptr;
+    int32_t* sAct = nullptr;
+    uint8_t* mask = nullptr;
+    std::vector<double> I_h, Inew_h, alpha_h, dmax_h;
+    std::vector<int64_t> cont_h;
+    std::vector<int32_t> active_h;
+    int64_t npt_cur = 0, npt_nxt = 0;
+
+    BatchStep(gipc_ctx* c, const gipc_scene& s, const gipc_step_params& p, cudaStream_t q, int nsc,
+              const int64_t* vo, const double* l)
+        : Step(c, s, p, q), ns(nsc), voff_h(vo), l_h(l) {}
+
+    gipc_status contacts_b(const double* x, ContactSet& cs, int64_t* npt) {
+        for (int attempt = 0; attempt < 2; ++attempt) {
+            int64_t cnt = 0;
+            const gipc_status s = find_contacts_impl(ctx, x, sc.rest_x, n, sc.surface, prm.barrier.dhat, cs.st, cs.eps,
+                                                     cs.cap, &cnt, true, vs, npt, st);
+            if (s == GIPC_OK) {
+                cs.k = cnt;
+                return GIPC_OK;
+            }
+            if (s != GIPC_ERR_CAPACITY) return s;
+            const int64_t cap = cnt + cnt / 4 + 1024;
+            const gipc_status r = ctx->slot[cs.slot].reserve((size_t)cap * (4 * sizeof(int32_t) + sizeof(double)));
+            if (r != GIPC_OK) return r;
+            cs.cap = cap;
+            cs.eps = ctx->slot[cs.slot].as<double>();
+            cs.st = reinterpret_cast<int32_t*>(cs.eps + cap);
+        }
+        return fail(GIPC_ERR_CUDA, "gipc_newton_step_batch: contact count changed between passes");
+    }
+
+    // per-scene I(x) into I_out (host) and the contacts at x
+    gipc_status potential_b(const double* x, ContactSet& cs, int64_t* npt, std::vector<double>& I_out) {
+        gipc_status s;
+        if ((s = contacts_b(x, cs, npt)) != GIPC_OK) return s;
+        const int64_t T = sc.T, k = cs.k;
+        gipc_prof_span span(ctx->prof, GIPC_PROF_ENERGY, st);
+        if ((s = ctx->slot[N_ENER].reserve(sizeof(double) * (T + k + 2))) != GIPC_OK) return s;
+        double* te = ctx->slot[N_ENER].as<double>();
+        double* se = te + T;
+        gipc_elastic_params ep = prm.elastic;
+        ep.scale = prm.dt * prm.dt;
+        if ((s = gipc_eval_tets(x, n, sc.tets, T, sc.Dm_inv, sc.vol, &ep, GIPC_FP64, te, nullptr, nullptr, st)) != GIPC_OK)
+            return s;
+        if (k > 0 && (s = gipc_eval_stencils(x, n, cs.st, k, cs.eps, &prm.barrier, GIPC_FP64, GIPC_HESS_DENSE, se, nullptr,
+                                             nullptr, nullptr, nullptr, st)) != GIPC_OK)
+            return s;
+        scene_energy_kernel<<<ns, 256, 0, st>>>(x, xt, sc.mass, n, voff, sc.tets, T, te, cs.st, k, *npt, se, vs, sI, sC);
+        cudaMemcpyAsync(I_out.data(), sI, sizeof(double) * ns, cudaMemcpyDeviceToHost, st);
+        cudaMemcpyAsync(cont_h.data(), sC, sizeof(int64_t) * ns, cudaMemcpyDeviceToHost, st);
+        if (cudaStreamSynchronize(st) != cudaSuccess) return check_launch("gipc_newton_step_batch: energy");
+        for (int k2 = 0; k2 < ns; ++k2)
+            if (!std::isfinite(I_out[k2])) return fail(GIPC_ERR_NONFINITE, "gipc_newton_step_batch: non-finite energy in scene %d", k2);
+        return GIPC_OK;
+    }
+
+    gipc_status run_batch(double* x, double* v, gipc_step_stats* stats) {
+        const int64_t m3 = 3 * n;
+        gipc_status s;
+        if ((s = ctx->slot[N_VEC].reserve(sizeof(double) * 7 * m3)) != GIPC_OK) return s;
+        if ((s = ctx->slot[N_RED].reserve(sizeof(double) * (4 * kRedBlocks + 8))) != GIPC_OK) return s;
+        if ((s = ctx->slot[B_VS].reserve(sizeof(int32_t) * (n + 1))) != GIPC_OK) return s;
+        if ((s = ctx->slot[B_OFF].reserve(sizeof(int64_t) * (ns + 1))) != GIPC_OK) return s;
+        if ((s = ctx->slot[B_SCAL].reserve(sizeof(double) * 3 * ns + sizeof(int64_t) * ns + sizeof(int32_t) * (ns + 4))) !=
+            GIPC_OK)
+            return s;
+        if ((s = ctx->slot[B_MASK].reserve(n + 16)) != GIPC_OK) return s;
+        x0 = ctx->slot[N_VEC].as<double>();
+        xt = x0 + m3;
+        xp = xt + m3;
+        d = xp + m3;
+        g = d + m3;
+        rhs = g + m3;
+        gb = rhs + m3;
+        partial = ctx->slot[N_RED].as<double>();
+        res = partial + 4 * kRedBlocks;
+        vs = ctx->slot[B_VS].as<int32_t>();
+        voff = ctx->slot[B_OFF].as<int64_t>();
+        sI = ctx->slot[B_SCAL].as<double>();
+        sA = sI + ns;
+        sD = sA + ns;
+        sC = reinterpret_cast<int64_t*>(sD + ns);
+        sAct = reinterpret_cast<int32_t*>(sC + ns);
+        int32_t* bad = sAct + ns;
+        mask = ctx->slot[B_MASK].as<uint8_t>();
+        for (auto& cs : set) {
+            cs.cap = (int64_t)(ctx->slot[cs.slot].bytes / (4 * sizeof(int32_t) + sizeof(double)));
+            cs.eps = ctx->slot[cs.slot].as<double>();
+            cs.st = reinterpret_cast<int32_t*>(cs.eps + cs.cap);
+        }
+        I_h.assign(ns, 0.0);
+        Inew_h.assign(ns, 0.0);
+        alpha_h.assign(ns, 1.0);
+        dmax_h.assign(ns, 0.0);
+        cont_h.assign(ns, 0);
+        active_h.assign(ns, 1);
+        // scene of every vertex, and the layout the per-scene sums rely on
+        cudaMemcpyAsync(voff, voff_h, sizeof(int64_t) * (ns + 1), cudaMemcpyHostToDevice, st);
+        vertex_scene_kernel<<<nb(n, 256), 256, 0, st>>>(voff, ns, n, vs);
+        cudaMemsetAsync(bad, 0, sizeof(int32_t), st);
+        if (sc.T > 0) batch_layout_kernel<<<nb(sc.T, 256), 256, 0, st>>>(sc.tets, 4, sc.T, n, vs, bad);
+        const gipc_surface& sf = sc.surface;
+        if (sf.ntri > 0) batch_layout_kernel<<<nb(sf.ntri, 256), 256, 0, st>>>(sf.tris, 3, sf.ntri, n, vs, bad);
+        if (sf.nedge > 0) batch_layout_kernel<<<nb(sf.nedge, 256), 256, 0, st>>>(sf.edges, 2, sf.nedge, n, vs, bad);
+        if (sf.nvert > 0) batch_layout_kernel<<<nb(sf.nvert, 256), 256, 0, st>>>(sf.verts, 1, sf.nvert, n, vs, bad);
+        int32_t bad_h = 0;
+        cudaMemcpyAsync(&bad_h, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+        if (cudaStreamSynchronize(st) != cudaSuccess) return check_launch("gipc_newton_step_batch: layout");
+        if (bad_h)
+            return fail(GIPC_ERR_INVALID_ARG,
+                        "gipc_newton_step_batch: an element spans two scenes, an id is out of range, or a list is not "
+                        "ordered by scene (code %d)",
+                        bad_h);
+        const double dt = prm.dt;
+        cudaMemcpyAsync(x0, x, sizeof(double) * m3, cudaMemcpyDeviceToDevice, st);
+        inertia_target_kernel<<<nb(n, 256), 256, 0, st>>>(x0, v, sc.fixed, n, dt, (dt * dt) * prm.gravity[0],
+                                                           (dt * dt) * prm.gravity[1], (dt * dt) * prm.gravity[2], xt);
+        int cur = 0;
+        if ((s = potential_b(x, set[cur], &npt_cur, I_h)) != GIPC_OK) return s;
+        std::vector<gipc_step_stats> S((size_t)ns);
+        std::vector<int> piters(ns, 0), pstat(ns, 0);
+        std::vector<int32_t> accepted(ns, 0);
+        const int T = (int)sc.T;
+        const bool mixed = prm.prec == GIPC_MIXED;
+        const size_t hb = mixed ? sizeof(float) : sizeof(double);
+        for (int it = 0; it < prm.max_newton; ++it) {
+            bool any = false;
+            for (int k = 0; k < ns; ++k) any |= active_h[k] != 0;
+            if (!any) break;
+            ContactSet& A = set[cur];
+            const int64_t k = A.k;
+            ctx->prof.start(GIPC_PROF_ELEMENTS, st);
+            if ((s = ctx->slot[N_TEVAL].reserve(sizeof(double) * 12 * T + hb * 144 * T + 16)) != GIPC_OK) return s;
+            double* tg = ctx->slot[N_TEVAL].as<double>();
+            void* th = tg + 12 * (int64_t)T;
+            gipc_elastic_params ep = prm.elastic;
+            ep.scale = dt * dt;
+            if ((s = gipc_eval_tets(x, n, sc.tets, T, sc.Dm_inv, sc.vol, &ep, prm.prec, nullptr, tg, th, st)) != GIPC_OK)
+                return s;
+            const bool rank1 = prm.hess_mode == GIPC_HESS_RANK1;
+            const int64_t hper = rank1 ? 12 : 144;
+            if ((s = ctx->slot[N_SEVAL].reserve(sizeof(double) * 13 * std::max<int64_t>(k, 1) + hb * hper * k + 16)) != GIPC_OK)
+                return s;
+            double* sg = ctx->slot[N_SEVAL].as<double>();
+            double* sl = sg + 12 * k;
+            void* sh = sl + std::max<int64_t>(k, 1);
+            if (k > 0 &&
+                (s = gipc_eval_stencils(x, n, A.st, k, A.eps, &prm.barrier, prm.prec, prm.hess_mode, nullptr, sg, sh,
+                                        rank1 ? sl : nullptr, nullptr, st)) != GIPC_OK)
+                return s;
+            ctx->prof.stop(GIPC_PROF_ELEMENTS, st);
+            grad_base_kernel<<<nb(m3, 256), 256, 0, st>>>(x, xt, sc.mass, n, gb);
+            gipc_elements te{sc.tets, T, GIPC_HESS_DENSE, th, nullptr, tg};
+            gipc_elements se{A.st, k, prm.hess_mode, sh, rank1 ? sl : nullptr, sg};
+            if ((s = ctx->slot[N_ROW].reserve(sizeof(int32_t) * (n + 1))) != GIPC_OK) return s;
+            gipc_bsr H{};
+            H.prec = prm.prec;
+            H.rowptr = ctx->slot[N_ROW].as<int32_t>();
+            for (int attempt = 0; attempt < 2; ++attempt) {
+                H.capacity = std::min<int64_t>((int64_t)(ctx->slot[N_COL].bytes / sizeof(int32_t)),
+                                               (int64_t)(ctx->slot[N_VAL].bytes / (9 * hb)));
+                H.colidx = ctx->slot[N_COL].as<int32_t>();
+                H.vals = ctx->slot[N_VAL].ptr;
+                s = gipc_assemble_bsr(ctx, n, k > 0 ? &se : nullptr, &te, sc.mass, gb, &H, g, st);
+                if (s != GIPC_ERR_CAPACITY || H.nnzb <= H.capacity) break;
+                const int64_t cap = H.nnzb + H.nnzb / 8 + 1024;
+                if ((s = ctx->slot[N_COL].reserve(sizeof(int32_t) * cap)) != GIPC_OK) return s;
+                if ((s = ctx->slot[N_VAL].reserve(9 * hb * cap)) != GIPC_OK) return s;
+                s = GIPC_ERR_CAPACITY;
+            }
+            if (s != GIPC_OK) return s;
+            // directions of the scenes still iterating; stopped scenes are filtered out (d = 0)
+            cudaMemcpyAsync(sAct, active_h.data(), sizeof(int32_t) * ns, cudaMemcpyHostToDevice, st);
+            scene_mask_kernel<<<nb(n, 256), 256, 0, st>>>(sc.fixed, vs, sAct, n, mask);
+            negate_kernel<<<nb(m3, 256), 256, 0, st>>>(g, m3, rhs);
+            cudaMemsetAsync(d, 0, sizeof(double) * m3, st);
+            gipc_pcg_params pp{prm.pcg_tol, prm.max_pcg, 0};
+            s = pcg_impl(ctx, &H, rhs, d, mask, &pp, nullptr, nullptr, st, voff, ns, piters.data(), pstat.data());
+            if (s != GIPC_OK && s != GIPC_ERR_NOT_CONVERGED) return s;
+            // per-scene step filter, then backtracking per scene
+            if ((s = ccd_impl(ctx, x, d, n, sc.surface, 0.1, alpha_h.data(), st, vs, ns, sA)) != GIPC_OK) return s;
+            for (int q = 0; q < ns; ++q) {
+                accepted[q] = active_h[q] ? 0 : 1;
+                if (active_h[q]) S[q].pcg_iters += piters[q];
+            }
+            cudaMemcpyAsync(xp, x, sizeof(double) * m3, cudaMemcpyDeviceToDevice, st);
+            const int nxt = 1 - cur;
+            for (int ls = 0; ls < std::max(prm.max_ls, 1); ++ls) {
+                cudaMemcpyAsync(sA, alpha_h.data(), sizeof(double) * ns, cudaMemcpyHostToDevice, st);
+                axpy_scene_kernel<<<nb(m3, 256), 256, 0, st>>>(xp, d, sA, vs, n, x);
+                if ((s = potential_b(x, set[nxt], &npt_nxt, Inew_h)) != GIPC_OK) return s;
+                bool all = true;
+                for (int q = 0; q < ns; ++q) {
+                    if (accepted[q]) continue;
+                    ++S[q].ls_trials;
+                    if (Inew_h[q] <= I_h[q]) accepted[q] = 1;
+                    else {
+                        alpha_h[q] *= 0.5;
+                        all = false;
+                    }
+                }
+                if (all) break;
+            }
+            cur = nxt;
+            npt_cur = npt_nxt;
+            scene_maxabs_kernel<<<ns, 256, 0, st>>>(d, n, voff, sD);
+            cudaMemcpyAsync(dmax_h.data(), sD, sizeof(double) * ns, cudaMemcpyDeviceToHost, st);
+            if (cudaStreamSynchronize(st) != cudaSuccess) return check_launch("gipc_newton_step_batch: step norm");
+            for (int q = 0; q < ns; ++q) {
+                if (!active_h[q]) continue;
+                I_h[q] = Inew_h[q];
+                ++S[q].newton_iters;
+                S[q].last_alpha = alpha_h[q];
+                if (dmax_h[q] / (l_h[q] * dt) <= prm.eps_d) {
+                    S[q].converged = 1;
+                    active_h[q] = 0;
+                }
+            }
+        }
+        velocity_kernel<<<nb(m3, 256), 256, 0, st>>>(x, x0, dt, m3, v);
+        for (int q = 0; q < ns; ++q) {
+            S[q].contacts = cont_h[q];
+            S[q].energy = I_h[q];
+            if (stats) stats[q] = S[q];
+        }
+        return check_launch("gipc_newton_step_batch");
+    }
+};
 }  // namespace
 }  // namespace gipc
 
@@ -347,4 +747,30 @@ extern "C" gipc_status gipc_newton_step(gipc_ctx* ctx, const gipc_scene* sc, dou
         return fail(GIPC_ERR_INVALID_ARG, "gipc_newton_step: bad barrier parameters");
     Step step(ctx, *sc, *prm, (cudaStream_t)stream);
     return step.run(x, v, stats);
+}
+
+extern "C" gipc_status gipc_newton_step_batch(gipc_ctx* ctx, const gipc_scene_batch* b, double* x, double* v,
+                                              const gipc_step_params* prm, gipc_step_stats* stats, void* stream) {
+    using namespace gipc;
+    if (!ctx || !b || !prm || !x || !v) return fail(GIPC_ERR_INVALID_ARG, "gipc_newton_step_batch: null argument");
+    const gipc_scene* sc = &b->all;
+    if (b->nscenes <= 0 || !b->vert_off_h || !b->l_h) return fail(GIPC_ERR_INVALID_ARG, "gipc_newton_step_batch: no scenes");
+    if (sc->n <= 0 || sc->T < 0 || !sc->rest_x || !sc->mass || (sc->T > 0 && (!sc->tets || !sc->Dm_inv || !sc->vol)))
+        return fail(GIPC_ERR_INVALID_ARG, "gipc_newton_step_batch: incomplete scene");
+    if (sc->T > 0x7fffffff) return fail(GIPC_ERR_INVALID_ARG, "gipc_newton_step_batch: too many tetrahedra");
+    if (b->vert_off_h[0] != 0 || b->vert_off_h[b->nscenes] != sc->n)
+        return fail(GIPC_ERR_INVALID_ARG, "gipc_newton_step_batch: vertex ranges must start at 0 and end at n");
+    for (int k = 0; k < b->nscenes; ++k) {
+        if (b->vert_off_h[k + 1] <= b->vert_off_h[k]) return fail(GIPC_ERR_INVALID_ARG, "gipc_newton_step_batch: empty or decreasing vertex range %d", k);
+        if (!(b->l_h[k] > 0.0)) return fail(GIPC_ERR_INVALID_ARG, "gipc_newton_step_batch: l of scene %d must be > 0", k);
+    }
+    if (!(prm->dt > 0.0) || !(prm->eps_d >= 0.0) || prm->max_newton < 0 || prm->max_pcg < 0 ||
+        (prm->prec != GIPC_FP64 && prm->prec != GIPC_MIXED) ||
+        (prm->hess_mode != GIPC_HESS_DENSE && prm->hess_mode != GIPC_HESS_RANK1))
+        return fail(GIPC_ERR_INVALID_ARG, "gipc_newton_step_batch: bad step parameters");
+    const gipc_barrier_params& bp = prm->barrier;
+    if (!(bp.dhat > 0.0) || !(bp.kappa >= 0.0) || !(bp.d_thr_ratio > 0.0 && bp.d_thr_ratio < 1.0))
+        return fail(GIPC_ERR_INVALID_ARG, "gipc_newton_step_batch: bad barrier parameters");
+    BatchStep step(ctx, *sc, *prm, (cudaStream_t)stream, b->nscenes, b->vert_off_h, b->l_h);
+    return step.run_batch(x, v, stats);
 }

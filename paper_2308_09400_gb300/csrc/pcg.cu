@@ -30,6 +30,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <vector>
 #include <cmath>
 
 #include "common.cuh"
@@ -44,7 +45,7 @@ constexpr int kRowsPerWarp = 10;  // row-ordered kernel: 3 lanes per row, lanes 
 constexpr int kSellC = 32;        // sliced kernel: rows per slice (one lane per row)
 constexpr int kVpt = 4;           // vertices per thread (pipelined) in the update / direction kernels
 
-enum PcgSlot { P_VEC = 9, P_PINV = 10, P_PART = 11, P_PERM = 12, P_VEC32 = 13, P_SELL = 14, P_SLICE = 15 };
+enum PcgSlot { P_VEC = 9, P_PINV = 10, P_PART = 11, P_PERM = 12, P_VEC32 = 13, P_SELL = 14, P_SLICE = 15, P_SCENE = 40 };
 
 constexpr int kLenBuckets = 64;   // rows are ordered by min(blocks in row, 63), longest first
 constexpr int kPermChunk = 1024;  // rows per block of the stable bucket sort
@@ -53,6 +54,13 @@ struct PcgScalars {
     double delta_new, delta_old, delta0, alpha, beta, tol, pq;
     int iters, done, max_iter, status;
     unsigned count_a, count_b, count_0;
+    unsigned scenes_done;   // batched solves: scenes that have stopped
+};
+
+// Per-scene state of a batched solve (independent systems on disjoint vertex ranges).
+struct SceneScalars {
+    double delta0, delta;
+    int iters, done, status, pad;
 };
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -726,6 +734,120 @@ __global__ void pcg_set_scalars(PcgScalars* S, double tol, int max_iter) {
     S->iters = 0;
     S->status = GIPC_OK;
     S->count_a = S->count_b = S->count_0 = 0;
+    S->scenes_done = 0;
+}
+
+// ---- batched solves: one CTA per scene for everything but the product ---------------------
+// Each scene is an independent system on the vertex range [voff[s], voff[s+1]) (the matrix has
+// no blocks across ranges).  The product q = S(H c) runs over all rows at once; everything that
+// needs a reduction (c.q, r.s) and the updates run with one CTA per scene, so each scene keeps
+// its own alpha, beta, delta and stopping test, in the order of the single-system iteration.
+
+__device__ __forceinline__ double block_sum_all(double v) {   // block sum broadcast to every thread
+    __shared__ double total;
+    const double t = block_sum(v);
+    if (threadIdx.x == 0) total = t;
+    __syncthreads();
+    const double r = total;
+    __syncthreads();
+    return r;
+}
+
+__device__ __forceinline__ void scene_stop(SceneScalars* SS, PcgScalars* S, int nscenes) {
+    SS->done = 1;
+    if (atomicAdd(&S->scenes_done, 1u) + 1u == (unsigned)nscenes) S->done = 1;
+}
+
+__global__ void __launch_bounds__(kPcgThreads)
+pcg_scene_init_kernel(const double* __restrict__ b, const double* __restrict__ q, double* __restrict__ r,
+                      double* __restrict__ s, double* __restrict__ c, float* __restrict__ c32,
+                      const double* __restrict__ pinv, const uint8_t* __restrict__ fixed, const int64_t* __restrict__ voff,
+                      int nscenes, SceneScalars* __restrict__ SS, PcgScalars* __restrict__ S) {
+    const int sc = blockIdx.x;
+    const int64_t v0 = voff[sc], v1 = voff[sc + 1];
+    double d = 0.0;
+    for (int64_t v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
+        const bool fx = fixed && fixed[v];
+        double rv[3], sv[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            rv[i] = fx ? 0.0 : b[3 * v + i] - q[3 * v + i];
+            r[3 * v + i] = rv[i];
+        }
+        d += precond_apply(pinv + 6 * v, rv, sv);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            s[3 * v + i] = sv[i];
+            c[3 * v + i] = fx ? 0.0 : sv[i];
+            if (c32) c32[3 * v + i] = fx ? 0.0f : (float)sv[i];
+        }
+    }
+    const double d0 = block_sum_all(d);
+    if (threadIdx.x == 0) {
+        SceneScalars& Z = SS[sc];
+        Z.delta0 = Z.delta = d0;
+        Z.iters = 0;
+        Z.done = 0;
+        Z.status = isfinite(d0) ? GIPC_OK : GIPC_ERR_NONFINITE;
+        if (!(d0 > 0.0) || !isfinite(d0) || S->max_iter <= 0) scene_stop(&Z, S, nscenes);
+    }
+}
+
+// alpha = delta / (c.q); x += alpha c; r -= alpha q; s = P^-1 r; delta' = r.s; beta; stop test;
+// c = S(s + beta c) while the scene continues.
+__global__ void __launch_bounds__(kPcgThreads)
+pcg_scene_step_kernel(double* __restrict__ x, double* __restrict__ r, double* __restrict__ c, float* __restrict__ c32,
+                      const double* __restrict__ q, double* __restrict__ s, const double* __restrict__ pinv,
+                      const uint8_t* __restrict__ fixed, const int64_t* __restrict__ voff, int nscenes,
+                      SceneScalars* __restrict__ SS, PcgScalars* __restrict__ S) {
+    const int sc = blockIdx.x;
+    if (SS[sc].done) return;
+    const int64_t v0 = voff[sc], v1 = voff[sc + 1];
+    double pq = 0.0;
+    for (int64_t e = 3 * v0 + threadIdx.x; e < 3 * v1; e += blockDim.x) pq += c[e] * q[e];
+    pq = block_sum_all(pq);
+    const double delta = SS[sc].delta;
+    const double alpha = delta / pq;
+    double d = 0.0;
+    for (int64_t v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
+        double rv[3], sv[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            x[3 * v + i] += alpha * c[3 * v + i];
+            rv[i] = r[3 * v + i] - alpha * q[3 * v + i];
+            r[3 * v + i] = rv[i];
+        }
+        d += precond_apply(pinv + 6 * v, rv, sv);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) s[3 * v + i] = sv[i];
+    }
+    const double dn = block_sum_all(d);
+    __shared__ int stop;
+    if (threadIdx.x == 0) {
+        SceneScalars& Z = SS[sc];
+        Z.delta = dn;
+        Z.iters += 1;
+        stop = 0;
+        if (!isfinite(dn) || !isfinite(alpha)) {
+            Z.status = GIPC_ERR_NONFINITE;
+            stop = 1;
+        } else if (!(dn > 0.0) || dn < S->tol * Z.delta0 || Z.iters >= S->max_iter) {
+            stop = 1;
+        }
+        if (stop) scene_stop(&Z, S, nscenes);
+    }
+    __syncthreads();
+    if (stop) return;
+    const double beta = dn / delta;
+    for (int64_t v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
+        const bool fx = fixed && fixed[v];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const double ce = fx ? 0.0 : s[3 * v + i] + beta * c[3 * v + i];
+            c[3 * v + i] = ce;
+            if (c32) c32[3 * v + i] = (float)ce;
+        }
+    }
 }
 
 inline unsigned spmv_blocks(int64_t n) {
@@ -742,11 +864,13 @@ inline unsigned vec_blocks(int64_t n) {
 }  // namespace
 }  // namespace gipc
 
-extern "C" gipc_status gipc_pcg(gipc_ctx* ctx, const gipc_bsr* A, const double* rhs, double* x,
-                                const uint8_t* fixed, const gipc_pcg_params* prm, int* iters_out_h,
-                                double* rel_out_h, void* stream) {
-    using namespace gipc;
-    cudaStream_t st = (cudaStream_t)stream;
+namespace gipc {
+// One solve, or (voff != NULL) nscenes independent solves on the vertex ranges voff (device,
+// [nscenes+1]) with per-scene scalars; scene_iters_h / scene_status_h (host, [nscenes]) report
+// each scene's iterations and status.
+gipc_status pcg_impl(gipc_ctx* ctx, const gipc_bsr* A, const double* rhs, double* x, const uint8_t* fixed,
+                     const gipc_pcg_params* prm, int* iters_out_h, double* rel_out_h, cudaStream_t st,
+                     const int64_t* voff, int nscenes, int* scene_iters_h, int* scene_status_h) {
     if (!ctx || !A || !prm) return fail(GIPC_ERR_INVALID_ARG, "gipc_pcg: null context, matrix or parameters");
     const int64_t n = A->n;
     if (n < 0 || A->nnzb < 0) return fail(GIPC_ERR_INVALID_ARG, "gipc_pcg: negative sizes");
@@ -820,7 +944,14 @@ extern "C" gipc_status gipc_pcg(gipc_ctx* ctx, const gipc_bsr* A, const double* 
     // q = S(H x0), reusing the spmv kernel with a scratch dot (alpha is overwritten at iteration 1)
     if (f64) pcg_spmv_kernel<double, double><<<sb, kPcgThreads, 0, st>>>(A->rowptr, A->colidx, (const double*)A->vals, xv, xv, perm, q, fixed, n, part, S);
     else pcg_spmv_kernel<float, float><<<sb, kPcgThreads, 0, st>>>(A->rowptr, A->colidx, (const float*)A->vals, x32, xv, perm, q, fixed, n, part, S);
-    pcg_init_kernel<<<vb, kPcgThreads, 0, st>>>(b, q, r, sv, c, c32, pinv, fixed, n, part, S);
+    SceneScalars* SS = nullptr;
+    if (voff) {
+        if ((s = ctx->slot[P_SCENE].reserve(sizeof(SceneScalars) * (nscenes + 1))) != GIPC_OK) return s;
+        SS = ctx->slot[P_SCENE].as<SceneScalars>();
+        pcg_scene_init_kernel<<<nscenes, kPcgThreads, 0, st>>>(b, q, r, sv, c, c32, pinv, fixed, voff, nscenes, SS, S);
+    } else {
+        pcg_init_kernel<<<vb, kPcgThreads, 0, st>>>(b, q, r, sv, c, c32, pinv, fixed, n, part, S);
+    }
     if ((s = check_launch("gipc_pcg: setup")) != GIPC_OK) return s;
 
     const int chunk = prm->check_every > 0 ? prm->check_every : (prm->rel_tol > 0.0 ? 16 : max_iter + 1);
@@ -837,6 +968,13 @@ extern "C" gipc_status gipc_pcg(gipc_ctx* ctx, const gipc_bsr* A, const double* 
                 launch_spmv_tma<float, float, kU32, kW32, kNS32>(A->rowptr, slice_off, sell_col, (const float*)sell_vals,
                                                                  c32, c, perm, q, fixed, n, nsl, part, S, st);
             ctx->prof.stop(GIPC_PROF_PCG_SPMV, st);
+            if (voff) {
+                ctx->prof.start(GIPC_PROF_PCG_UPDATE, st);
+                pcg_scene_step_kernel<<<nscenes, kPcgThreads, 0, st>>>(xv, r, c, c32, q, sv, pinv, fixed, voff, nscenes,
+                                                                       SS, S);
+                ctx->prof.stop(GIPC_PROF_PCG_UPDATE, st);
+                continue;
+            }
             ctx->prof.start(GIPC_PROF_PCG_UPDATE, st);
             pcg_update_kernel<<<vb, kPcgThreads, 0, st>>>(xv, r, c, q, sv, pinv, n, part, S);
             ctx->prof.stop(GIPC_PROF_PCG_UPDATE, st);
@@ -854,6 +992,28 @@ extern "C" gipc_status gipc_pcg(gipc_ctx* ctx, const gipc_bsr* A, const double* 
     }
     aos_to_soa_kernel<<<eb, 256, 0, st>>>(xv, x, n);
     cudaMemcpyAsync(&hs, S, sizeof(PcgScalars), cudaMemcpyDeviceToHost, st);
+    if (voff) {
+        std::vector<SceneScalars> hz((size_t)nscenes);
+        cudaMemcpyAsync(hz.data(), SS, sizeof(SceneScalars) * nscenes, cudaMemcpyDeviceToHost, st);
+        if (cudaStreamSynchronize(st) != cudaSuccess) return check_launch("gipc_pcg: final sync");
+        int most = 0;
+        bool nonfinite = false, short_of_tol = false;
+        for (int k = 0; k < nscenes; ++k) {
+            if (scene_iters_h) scene_iters_h[k] = hz[k].iters;
+            most = std::max(most, hz[k].iters);
+            const bool nf = hz[k].status == GIPC_ERR_NONFINITE;
+            const bool nc = prm->rel_tol > 0.0 && hz[k].delta0 > 0.0 && hz[k].delta >= prm->rel_tol * hz[k].delta0 &&
+                            hz[k].delta > 0.0;
+            if (scene_status_h) scene_status_h[k] = nf ? GIPC_ERR_NONFINITE : (nc ? GIPC_ERR_NOT_CONVERGED : GIPC_OK);
+            nonfinite |= nf;
+            short_of_tol |= nc;
+        }
+        if (iters_out_h) *iters_out_h = most;
+        if (rel_out_h) *rel_out_h = 0.0;
+        if (nonfinite) return fail(GIPC_ERR_NONFINITE, "gipc_pcg: non-finite residual in a scene");
+        if (short_of_tol) return fail(GIPC_ERR_NOT_CONVERGED, "gipc_pcg: a scene did not reach the tolerance");
+        return GIPC_OK;
+    }
     if (cudaStreamSynchronize(st) != cudaSuccess) return check_launch("gipc_pcg: final sync");
     if (iters_out_h) *iters_out_h = hs.iters;
     if (rel_out_h) *rel_out_h = hs.delta0 > 0.0 ? hs.delta_new / hs.delta0 : 0.0;
@@ -861,6 +1021,14 @@ extern "C" gipc_status gipc_pcg(gipc_ctx* ctx, const gipc_bsr* A, const double* 
     if (prm->rel_tol > 0.0 && hs.delta0 > 0.0 && hs.delta_new >= prm->rel_tol * hs.delta0 && hs.delta_new > 0.0)
         return fail(GIPC_ERR_NOT_CONVERGED, "gipc_pcg: %d iterations without reaching the tolerance", hs.iters);
     return GIPC_OK;
+}
+}  // namespace gipc
+
+extern "C" gipc_status gipc_pcg(gipc_ctx* ctx, const gipc_bsr* A, const double* rhs, double* x,
+                                const uint8_t* fixed, const gipc_pcg_params* prm, int* iters_out_h,
+                                double* rel_out_h, void* stream) {
+    return gipc::pcg_impl(ctx, A, rhs, x, fixed, prm, iters_out_h, rel_out_h, (cudaStream_t)stream, nullptr, 1, nullptr,
+                          nullptr);
 }
 
 // ------------------------------------------------------------------------------------------

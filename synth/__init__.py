@@ -575,3 +575,49 @@ def sphere_grid(nx=8, ny=8, radius=0.1, cells=14, gap=1e-3, floor_cells=64, jitt
     l = float(np.linalg.norm(x.max(axis=1) - x.min(axis=1)))
     return {"x": x, "v": np.zeros((3, n)), "tets": tets, "fixed": fixed, "tris": tris, "edges": edges,
             "verts": verts, "l": l}
+
+
+def stack_scene(rng, n_bodies, target_verts, dhat, size=0.2):
+    """One scene of `n_bodies` tet-meshed cubes or balls (about target_verts vertices in all)
+    stacked along z, each gap uniform in [0, 2 dhat] (below dhat the bodies start in contact),
+    with small seeded lateral offsets and turns; the lowest layer of the bottom body is fixed."""
+    per = max(target_verts / n_bodies, 27.0)
+    parts, z = [], 0.0
+    for b in range(n_bodies):
+        if rng.random() < 0.5:
+            m = max(3, int(round(per ** (1.0 / 3.0))))
+            xb, tb = tet_box(m, m, m, spacing=size / (m - 1))
+        else:
+            cells = max(4, int(round((per / 0.52) ** (1.0 / 3.0))) - 1)
+            xb, tb = ball(size / 2, cells, center=(size / 2, size / 2, size / 2))
+        xb = xb.copy()
+        th = rng.uniform(-0.3, 0.3)
+        c, s_ = np.cos(th), np.sin(th)
+        cx = xb[0] - size / 2
+        cy = xb[1] - size / 2
+        xb[0] = c * cx - s_ * cy + size / 2 + rng.uniform(-0.2, 0.2) * size
+        xb[1] = s_ * cx + c * cy + size / 2 + rng.uniform(-0.2, 0.2) * size
+        xb[2] = xb[2] - xb[2].min() + z
+        parts.append((xb, tb))
+        z = xb[2].max() + rng.uniform(0.0, 2.0) * dhat
+    x, tets = _merge(parts)
+    n = x.shape[1]
+    fixed = np.zeros(n, np.uint8)
+    n0 = parts[0][0].shape[1]
+    fixed[:n0][parts[0][0][2] <= parts[0][0][2].min() + 1e-12] = 1
+    tris, edges, verts = surface_lists(x, tets)
+    l = float(np.linalg.norm(x.max(axis=1) - x.min(axis=1)))
+    return {"x": x, "v": np.zeros((3, n)), "tets": tets, "fixed": fixed, "tris": tris, "edges": edges,
+            "verts": verts, "l": l}
+
+
+def batch_scenes(n_scenes=256, seed=20230813, vmin=200, vmax=5000, dhat=5e-4):
+    """Independent scenes of 2 to 6 stacked cubes / balls each, vertex counts log-uniform in
+    [vmin, vmax] per scene; one dhat for the batch.  Returns (list of scene dicts, dhat)."""
+    rng = np.random.default_rng(seed)
+    scenes = []
+    for _ in range(n_scenes):
+        nb = int(rng.integers(2, 7))
+        tv = float(np.exp(rng.uniform(np.log(vmin), np.log(vmax))))
+        scenes.append(stack_scene(rng, nb, tv, dhat))
+    return scenes, dhat

@@ -1,0 +1,108 @@
+"""Batched time step (gipc_newton_step_batch) against running every scene alone through
+gipc_newton_step (itself checked against the oracle).
+
+The scenes are independent: each keeps its own PCG scalars, CCD step, line search and stopping
+test.  Per scene the batched step must reproduce the single-scene step's Newton iteration count
+and contact count, and its positions to within the rounding of the solver's reductions (the
+batched PCG sums each scene with one CTA, the single one over the whole grid)."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+import synth  # noqa: E402
+from oracle import contact as C  # noqa: E402
+
+DT, E, NU, RHO, KAPPA = 0.01, 1e5, 0.4, 1000.0, 1e3
+
+
+@pytest.fixture(scope="module")
+def gipc():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2308_09400_gb300 as g
+    return g
+
+
+def _dev(a):
+    return torch.tensor(np.ascontiguousarray(a), device="cuda")
+
+
+def _single(g, sc, dhat, **kw):
+    srf = g.Surface(_dev(sc["tris"]), _dev(sc["edges"]), _dev(sc["verts"]))
+    scene = g.Scene(_dev(sc["x"]), _dev(sc["tets"]), srf, RHO, fixed=_dev(sc["fixed"]), l=sc["l"])
+    mu, lam = g.snh_params(E, NU)
+    x, v = _dev(sc["x"]), _dev(sc["v"])
+    st = g.newton_step(scene, x, v, dt=DT, mu=mu, lam=lam, dhat=dhat, kappa=KAPPA, **kw)
+    return x.cpu().numpy(), v.cpu().numpy(), st
+
+
+def _batch(g, scenes, dhat, **kw):
+    b = g.SceneBatch(scenes, RHO)
+    mu, lam = g.snh_params(E, NU)
+    x = b.scene.rest_x.clone()
+    v = _dev(np.concatenate([s["v"] for s in scenes], axis=1))
+    stats = g.newton_step_batch(b, x, v, dt=DT, mu=mu, lam=lam, dhat=dhat, kappa=KAPPA, **kw)
+    return b, x.cpu().numpy(), v.cpu().numpy(), stats
+
+
+def _scenes(n=5, seed=7, vmax=900):
+    scenes, dhat = synth.batch_scenes(n, seed=seed, vmin=150, vmax=vmax, dhat=5e-4)
+    for s in scenes:   # move them so every scene starts with some motion
+        s["v"][2] = -0.5
+    return scenes, dhat
+
+
+@pytest.mark.parametrize("precision,hess_mode", [("fp64", "dense"), ("mixed", "rank1")])
+def test_batch_matches_each_scene_alone(gipc, precision, hess_mode):
+    scenes, dhat = _scenes()
+    kw = dict(precision=precision, hess_mode=hess_mode, max_newton=12)
+    b, xb, vb, stats = _batch(gipc, scenes, dhat, **kw)
+    assert len(stats) == len(scenes)
+    assert sum(s["contacts"] for s in stats) > 0
+    for k, sc in enumerate(scenes):
+        xs, vs, st = _single(gipc, sc, dhat, **kw)
+        lo, hi = b.vert_off[k], b.vert_off[k + 1]
+        assert stats[k]["newton_iters"] == st["newton_iters"], (k, stats[k], st)
+        assert stats[k]["contacts"] == st["contacts"], (k, stats[k], st)
+        assert stats[k]["converged"] == st["converged"]
+        step = np.abs(xs - sc["x"]).max()
+        err = np.abs(xb[:, lo:hi] - xs).max()
+        # FP64: the reductions' order alone; mixed: the float32 copy of the direction rounds the
+        # last-bit differences of alpha and beta up to float32 precision
+        rtol = 1e-7 if precision == "fp64" else 1e-5
+        assert err <= rtol * step + 1e-15, f"scene {k}: {err:.3e} of a {step:.3e} step"
+        assert stats[k]["energy"] == pytest.approx(st["energy"], rel=1e-9)
+        assert C.count_intersections(xb[:, lo:hi], sc["tris"], sc["edges"]) == 0
+
+
+def test_scenes_never_touch_each_other(gipc):
+    """Two copies of a stack at the same place in space: run together they must behave exactly
+    like each alone (no contact across scenes)."""
+    scenes, dhat = _scenes(n=1, seed=11)
+    twin = [scenes[0], {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in scenes[0].items()}]
+    b, xb, _, stats = _batch(gipc, twin, dhat, max_newton=8)
+    xs, _, st = _single(gipc, scenes[0], dhat, max_newton=8)
+    n = scenes[0]["x"].shape[1]
+    for k in range(2):
+        assert stats[k]["contacts"] == st["contacts"]
+        assert stats[k]["newton_iters"] == st["newton_iters"]
+        step = np.abs(xs - scenes[0]["x"]).max()
+        assert np.abs(xb[:, k * n:(k + 1) * n] - xs).max() <= 1e-7 * step + 1e-15
+    # the two copies are bit-identical to each other (same arithmetic, scene by scene)
+    assert np.array_equal(xb[:, :n], xb[:, n:])
+
+
+def test_unordered_lists_are_rejected(gipc):
+    scenes, dhat = _scenes(n=3, seed=5)
+    b = gipc.SceneBatch(scenes, RHO)
+    perm = torch.randperm(b.scene.tets.shape[1], device="cuda", generator=torch.Generator(device="cuda").manual_seed(1))
+    b.scene.tets = b.scene.tets[:, perm].contiguous()
+    b.scene.Dm_inv = b.scene.Dm_inv[:, perm].contiguous()
+    b.scene.vol = b.scene.vol[perm].contiguous()
+    mu, lam = gipc.snh_params(E, NU)
+    x = b.scene.rest_x.clone()
+    v = torch.zeros_like(x)
+    with pytest.raises(gipc.GipcError, match="ordered by scene"):
+        gipc.newton_step_batch(b, x, v, dt=DT, mu=mu, lam=lam, dhat=dhat, kappa=KAPPA)
