@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--newton-steps", type=int, default=4,
                     help="implicit time steps of the sphere-grid scene per precision (0: skip)")
+    ap.add_argument("--batch-steps", type=int, default=3,
+                    help="time steps of the 256-scene batch, batched and one scene at a time (0: skip)")
     ap.add_argument("--c2-steps", type=int, default=3,
                     help="time steps of the per-step FP64 / mixed converged-position comparison (0: skip)")
     return ap.parse_args()
@@ -310,6 +312,8 @@ def run_gpu(args):
         }
         if args.newton_steps > 0:
             line["newton"] = run_newton(g, dev, ctx, args.newton_steps, args.c2_steps)
+        if args.batch_steps > 0:
+            line["batched"] = run_batch_bench(g, dev, ctx, args.batch_steps)
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args, Wh, sample=16000)
         print(json.dumps(line))
@@ -399,6 +403,68 @@ def run_newton(g, dev, ctx, steps, c2_steps=0):
                                "contacts_final": st["contacts"], "phase_ms_per_newton_iter": phase}
     if c2_steps > 0:
         out["converged_position_error"] = run_c2(g, scene, sc, prm, dev, c2_steps)
+    return out
+
+
+# ----------------------------------------------------------------------------- batched scenes
+def run_batch_bench(g, dev, ctx, steps):
+    """256 independent scenes (2-6 stacked cubes / balls each, 200-5000 vertices log-uniform, gaps
+    uniform in [0, 2 dhat]): `steps` implicit steps from rest through gipc_newton_step_batch, and the
+    same steps of every scene alone through gipc_newton_step; scene Newton iterations per second."""
+    import numpy as np
+    import torch
+    import synth
+
+    scenes, dhat = synth.batch_scenes(256)
+    T = lambda a: torch.tensor(np.ascontiguousarray(a), device=dev)
+    mu, lam = g.snh_params(1e5, 0.4)
+    prm = dict(dt=0.01, mu=mu, lam=lam, dhat=dhat, kappa=KAPPA, eps_d=1e-2, pcg_tol=1e-4, max_pcg=1000,
+               max_newton=50)
+    b = g.SceneBatch(scenes, 1000.0)
+    v_init = np.concatenate([sc["v"] for sc in scenes], axis=1)
+    singles = []
+    for sc in scenes:
+        srf = g.Surface(T(sc["tris"]), T(sc["edges"]), T(sc["verts"]))
+        singles.append(g.Scene(T(sc["x"]), T(sc["tets"]), srf, 1000.0, fixed=T(sc["fixed"]), l=sc["l"]))
+    out = {"workload": "256 scenes of 2-6 stacked tet cubes / balls, 200-5000 vertices each (log-uniform), "
+                       "gaps uniform in [0, 2 dhat]",
+           "vertices": int(sum(sc["x"].shape[1] for sc in scenes)), "tets": int(sum(sc["tets"].shape[1] for sc in scenes)),
+           "dhat": dhat, "time_steps": steps}
+    for prec, hm in NEWTON_FORMS:
+        # warm-up (scratch sizing) on a throw-away copy
+        xw, vw = b.scene.rest_x.clone(), T(v_init)
+        g.newton_step_batch(b, xw, vw, precision=prec, hess_mode=hm, **prm)
+        x, v = b.scene.rest_x.clone(), T(v_init)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        its = 0
+        per_step = []
+        for _ in range(steps):
+            st = g.newton_step_batch(b, x, v, precision=prec, hess_mode=hm, **prm)
+            per_step.append(sum(s["newton_iters"] for s in st))
+        e1.record()
+        torch.cuda.synchronize()
+        ms_b = e0.elapsed_time(e1)
+        its = sum(per_step)
+        # the same steps, every scene alone
+        xs = [T(sc["x"]) for sc in scenes]
+        vs = [T(sc["v"]) for sc in scenes]
+        g.newton_step(singles[0], xs[0].clone(), vs[0].clone(), precision=prec, hess_mode=hm, **prm)
+        torch.cuda.synchronize()
+        e0.record()
+        its1 = 0
+        for _ in range(steps):
+            for k in range(len(scenes)):
+                its1 += g.newton_step(singles[k], xs[k], vs[k], precision=prec, hess_mode=hm, **prm)["newton_iters"]
+        e1.record()
+        torch.cuda.synchronize()
+        ms_p = e0.elapsed_time(e1)
+        out[f"{prec}_{hm}"] = {"batched_ms_per_step": ms_b / steps, "batched_scene_iters_per_s": its / (ms_b * 1e-3),
+                               "one_at_a_time_ms_per_step": ms_p / steps,
+                               "one_at_a_time_scene_iters_per_s": its1 / (ms_p * 1e-3),
+                               "scene_newton_iters": its, "scene_newton_iters_one_at_a_time": its1,
+                               "scene_newton_iters_per_step": per_step, "speedup": ms_p / ms_b}
     return out
 
 

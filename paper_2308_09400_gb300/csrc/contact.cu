@@ -37,15 +37,15 @@ namespace gipc {
 namespace {
 
 constexpr int kThreads = 128;
-constexpr int64_t kMaxCellsPerBox = 512;   // cell-size doubling threshold
+constexpr int64_t kMaxCellsPerBox = 64;    // cell-size doubling threshold (cells per box)
 constexpr int kWarps = kThreads / 32;
 // context scratch slots: query counts (then cursors), query offsets, scalars, sort keys, candidate
 // pairs, pair codes; per grid (triangles,
 // edges): float64 target boxes, hash tables, per-target cell counts and their offsets
 enum ContactSlot { C_CNT = 16, C_QOFF = 17, C_MISC = 19, C_KEY = 37, C_PAIRS = 38, C_CODE = 39 };
-constexpr int kGridSlots[2][4] = {{18, 30, 31, 32}, {33, 34, 35, 36}};
-// scalars in C_MISC: per grid g at 4g: extent sum, 1 / cell size, largest cell count; CCD minimum
-// at 8, pair counter at 9
+constexpr int kGridSlots[2][5] = {{18, 30, 31, 32, 45}, {33, 34, 35, 36, 46}};
+// scalars in C_MISC: per grid g the largest cell count at 4g + 2; CCD minimum at 8, pair counter
+// at 9.  Per-scene extent sums, counts and inverse cell sizes live in the grid's last slot.
 constexpr int kMiscAmin = 8;
 constexpr int kMiscPairs = 9;
 
@@ -182,7 +182,7 @@ struct Grid {
     const double* lo;        // [3][m] target box low corners (float64)
     const double* hi;        // [3][m]
     int64_t m;
-    const double* inv_h;     // device scalar: 1 / cell size
+    const double* inv_h;     // device [scenes]: 1 / cell size of each scene
     uint64_t mask;           // buckets - 1 (power of two)
     const int64_t* boff;     // [buckets + 1] bucket offsets into ent
     const Entry* ent;        // entries grouped by bucket
@@ -205,7 +205,8 @@ __device__ __forceinline__ uint64_t bucket_of(int64_t cx, int64_t cy, int64_t cz
 // padded by pad -- the same values as the reference formulas (min and max are exact).
 __global__ void target_boxes_kernel(const double* __restrict__ x, const double* __restrict__ d, int64_t n,
                                     const int32_t* __restrict__ prim, int nv, int64_t m, double pad,
-                                    double* __restrict__ lo, double* __restrict__ hi, double* __restrict__ ext_sum) {
+                                    const int32_t* __restrict__ vscene, double* __restrict__ lo, double* __restrict__ hi,
+                                    double* __restrict__ ext_sum, double* __restrict__ ext_cnt) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double ext = 0.0;
     if (t < m) {
@@ -230,16 +231,36 @@ __global__ void target_boxes_kernel(const double* __restrict__ x, const double* 
             ext = fmax(ext, __dsub_rn(h, l));
         }
     }
-    // warp sums of the extents, one atomic per warp (the cell size only steers the search)
+    // extent sums per scene (the cell size only steers the search): one scene -> one atomic per
+    // warp; batched scenes -> one per target
+    if (vscene) {
+        if (t < m) {
+            const int32_t sc = vscene[prim[t]];
+            atomicAdd(ext_sum + sc, ext);
+            atomicAdd(ext_cnt + sc, 1.0);
+        }
+        return;
+    }
+    double c = t < m ? 1.0 : 0.0;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) ext += __shfl_xor_sync(0xffffffffu, ext, o);
-    if ((threadIdx.x & 31) == 0 && ext > 0.0) atomicAdd(ext_sum, ext);
+    for (int o = 16; o > 0; o >>= 1) {
+        ext += __shfl_xor_sync(0xffffffffu, ext, o);
+        c += __shfl_xor_sync(0xffffffffu, c, o);
+    }
+    if ((threadIdx.x & 31) == 0 && c > 0.0) {
+        atomicAdd(ext_sum, ext);
+        atomicAdd(ext_cnt, c);
+    }
 }
 
-__global__ void cell_size_kernel(const double* __restrict__ ext_sum, int64_t m, double scale, double* __restrict__ inv_h) {
-    double h = m > 0 ? *ext_sum / (double)m : 1.0;
+// Cell size of each scene: the mean extent of its target boxes, times `scale`.
+__global__ void cell_size_kernel(const double* __restrict__ ext_sum, const double* __restrict__ ext_cnt, int ns,
+                                 double scale, double* __restrict__ inv_h) {
+    const int sc = blockIdx.x * blockDim.x + threadIdx.x;
+    if (sc >= ns) return;
+    double h = ext_cnt[sc] > 0.0 ? ext_sum[sc] / ext_cnt[sc] : 1.0;
     if (!(h > 0.0) || !isfinite(h)) h = 1.0;
-    *inv_h = 1.0 / (h * scale);
+    inv_h[sc] = 1.0 / (h * scale);
 }
 
 __device__ __forceinline__ int64_t box_cells(double lx, double ly, double lz, double hx, double hy, double hz,
@@ -255,20 +276,22 @@ __device__ __forceinline__ int64_t box_cells(double lx, double ly, double lz, do
 
 // Cells per target (int32, saturated) and the largest count over the targets.
 __global__ void cells_count_kernel(const double* __restrict__ lo, const double* __restrict__ hi, int64_t m,
+                                   const int32_t* __restrict__ prim, const int32_t* __restrict__ vscene,
                                    const double* __restrict__ inv_h, int32_t* __restrict__ cnt,
                                    unsigned long long* __restrict__ max_cells) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= m) return;
     int64_t c0[3], c1[3];
-    const int64_t c = box_cells(lo[t], lo[m + t], lo[2 * m + t], hi[t], hi[m + t], hi[2 * m + t], *inv_h, c0, c1);
+    const double ih = inv_h[vscene ? vscene[prim[t]] : 0];
+    const int64_t c = box_cells(lo[t], lo[m + t], lo[2 * m + t], hi[t], hi[m + t], hi[2 * m + t], ih, c0, c1);
     cnt[t] = (int32_t)std::min<int64_t>(c, kMaxCellsPerBox + 1);
     atomicMax(max_cells, (unsigned long long)c);
 }
 
 // Swept point boxes of the surface vertices (CCD queries) only report their cell counts.
 __global__ void point_cells_kernel(const double* __restrict__ x, const double* __restrict__ d, int64_t n,
-                                   const int32_t* __restrict__ verts, int64_t nv, const double* __restrict__ inv_h,
-                                   unsigned long long* __restrict__ max_cells) {
+                                   const int32_t* __restrict__ verts, int64_t nv, const int32_t* __restrict__ vscene,
+                                   const double* __restrict__ inv_h, unsigned long long* __restrict__ max_cells) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nv) return;
     const int32_t p = verts[k];
@@ -280,7 +303,8 @@ __global__ void point_cells_kernel(const double* __restrict__ x, const double* _
         h[q] = fmax(a, b);
     }
     int64_t c0[3], c1[3];
-    atomicMax(max_cells, (unsigned long long)box_cells(l[0], l[1], l[2], h[0], h[1], h[2], *inv_h, c0, c1));
+    const double ih = inv_h[vscene ? vscene[p] : 0];
+    atomicMax(max_cells, (unsigned long long)box_cells(l[0], l[1], l[2], h[0], h[1], h[2], ih, c0, c1));
 }
 
 // Insert target t into the bucket of each cell its box overlaps, at most once per bucket (two
@@ -296,7 +320,7 @@ __global__ void bucket_kernel(const double* __restrict__ lo, const double* __res
     const int32_t scene = vscene ? vscene[prim[t]] : 0;
     const double l[3] = {lo[t], lo[m + t], lo[2 * m + t]}, h[3] = {hi[t], hi[m + t], hi[2 * m + t]};
     int64_t c0[3], c1[3];
-    const int64_t nc = box_cells(l[0], l[1], l[2], h[0], h[1], h[2], *inv_h, c0, c1);
+    const int64_t nc = box_cells(l[0], l[1], l[2], h[0], h[1], h[2], inv_h[scene], c0, c1);
     if (nc > kMaxCellsPerBox) return;
     const int64_t nx = c1[0] - c0[0] + 1, ny = c1[1] - c0[1] + 1;
     auto bucket_at = [&](int64_t li) {
@@ -344,7 +368,6 @@ scan_pairs_kernel(const double* __restrict__ x, const double* __restrict__ dx, i
     const int lane = threadIdx.x & 31;
     const int64_t nq = KIND == K_EE ? S.nedge : S.nvert;
     const int64_t nw = (int64_t)gridDim.x * kWarps;
-    const double ih = *G.inv_h;
     const float4* ent4 = reinterpret_cast<const float4*>(G.ent);
     auto flush = [&](int cnt) {   // append the first cnt queued pairs (cnt <= 32)
         unsigned long long base = 0;
@@ -378,6 +401,7 @@ scan_pairs_kernel(const double* __restrict__ x, const double* __restrict__ dx, i
             }
         }
         const int32_t qs = vscene ? vscene[KIND == K_EE ? ia : p] : 0;   // the query's scene
+        const double ih = G.inv_h[qs];
         int64_t c0[3], c1[3];
         if (box_cells(ql[0], ql[1], ql[2], qh[0], qh[1], qh[2], ih, c0, c1) > kMaxCellsPerBox) continue;
         const float fl[3] = {__double2float_rd(ql[0]), __double2float_rd(ql[1]), __double2float_rd(ql[2])};
@@ -650,7 +674,7 @@ inline unsigned wblk(int64_t queries) { return (unsigned)std::max<int64_t>(1, st
 // d if given, padded by pad).  Synchronises once per cell-size attempt.  `pts`: surface
 // vertices whose swept boxes also bound the cell size (CCD).
 gipc_status build_grid(gipc_ctx* ctx, int g, const double* x, const double* d, int64_t n, const int32_t* prim, int nv,
-                       int64_t m, double pad, const gipc_surface* pts, const int32_t* vscene, Grid& G,
+                       int64_t m, double pad, const gipc_surface* pts, const int32_t* vscene, int nscenes, Grid& G,
                        cudaStream_t st) {
     gipc_status s;
     gipc_scratch* slot = ctx->slot;
@@ -665,16 +689,23 @@ gipc_status build_grid(gipc_ctx* ctx, int g, const double* x, const double* d, i
     int32_t* cnt = slot[gs[2]].as<int32_t>();
     if ((s = slot[gs[3]].reserve(sizeof(int64_t) * (m + 2 + scan_scratch_words(m + 1)))) != GIPC_OK) return s;
     int64_t* off = slot[gs[3]].as<int64_t>();
-    cudaMemsetAsync(misc, 0, sizeof(double), st);
-    target_boxes_kernel<<<nblk(m, 256), 256, 0, st>>>(x, d, n, prim, nv, m, pad, lo, hi, misc);
+    // per-scene extent sums and counts, then 1 / cell size per scene
+    const int ns = vscene ? nscenes : 1;
+    if ((s = slot[gs[4]].reserve(sizeof(double) * 3 * ns)) != GIPC_OK) return s;
+    double* ext_sum = slot[gs[4]].as<double>();
+    double* ext_cnt = ext_sum + ns;
+    double* inv_h = ext_cnt + ns;
+    cudaMemsetAsync(ext_sum, 0, sizeof(double) * 2 * ns, st);
+    target_boxes_kernel<<<nblk(m, 256), 256, 0, st>>>(x, d, n, prim, nv, m, pad, vscene, lo, hi, ext_sum, ext_cnt);
     int64_t total = 0;
     unsigned long long mc = 0;
     for (double scale = 1.0;; scale *= 2.0) {
-        cell_size_kernel<<<1, 1, 0, st>>>(misc, m, scale, misc + 1);
+        cell_size_kernel<<<nblk(ns, 256), 256, 0, st>>>(ext_sum, ext_cnt, ns, scale, inv_h);
         cudaMemsetAsync(max_cells, 0, sizeof(unsigned long long), st);
-        cells_count_kernel<<<nblk(m, 256), 256, 0, st>>>(lo, hi, m, misc + 1, cnt, max_cells);
+        cells_count_kernel<<<nblk(m, 256), 256, 0, st>>>(lo, hi, m, prim, vscene, inv_h, cnt, max_cells);
         if (pts && pts->nvert > 0)
-            point_cells_kernel<<<nblk(pts->nvert, 256), 256, 0, st>>>(x, d, n, pts->verts, pts->nvert, misc + 1, max_cells);
+            point_cells_kernel<<<nblk(pts->nvert, 256), 256, 0, st>>>(x, d, n, pts->verts, pts->nvert, vscene, inv_h,
+                                                                       max_cells);
         if (exclusive_scan<int32_t>(cnt, off, m, off + m + 2, st) != cudaSuccess)
             return check_launch("contact grid: scan");
         cudaMemcpyAsync(&mc, max_cells, sizeof(mc), cudaMemcpyDeviceToHost, st);
@@ -697,13 +728,13 @@ gipc_status build_grid(gipc_ctx* ctx, int g, const double* x, const double* d, i
     ep = (ep + 15) & ~uintptr_t(15);
     Entry* ent = reinterpret_cast<Entry*>(ep);
     cudaMemsetAsync(bcnt, 0, sizeof(int32_t) * buckets, st);
-    bucket_kernel<false><<<nblk(m, 256), 256, 0, st>>>(lo, hi, m, prim, vscene, misc + 1, buckets - 1, bcnt, nullptr,
+    bucket_kernel<false><<<nblk(m, 256), 256, 0, st>>>(lo, hi, m, prim, vscene, inv_h, buckets - 1, bcnt, nullptr,
                                                         nullptr);
     if (exclusive_scan<int32_t>(bcnt, boff, (int64_t)buckets, btmp, st) != cudaSuccess)
         return check_launch("contact grid: bucket scan");
     cudaMemsetAsync(bcnt, 0, sizeof(int32_t) * buckets, st);
-    bucket_kernel<true><<<nblk(m, 256), 256, 0, st>>>(lo, hi, m, prim, vscene, misc + 1, buckets - 1, bcnt, boff, ent);
-    G = Grid{lo, hi, m, misc + 1, buckets - 1, boff, ent};
+    bucket_kernel<true><<<nblk(m, 256), 256, 0, st>>>(lo, hi, m, prim, vscene, inv_h, buckets - 1, bcnt, boff, ent);
+    G = Grid{lo, hi, m, inv_h, buckets - 1, boff, ent};
     return check_launch("contact grid");
 }
 
@@ -746,7 +777,7 @@ gipc_status collect_pairs(gipc_ctx* ctx, const double* x, const double* d, int64
 // Internal entry points shared with the time-step driver (newton.cu).
 gipc_status find_contacts_impl(gipc_ctx* ctx, const double* x, const double* rest_x, int64_t n, const gipc_surface& srf,
                                double dhat, int32_t* stencils, double* eps_x, int64_t cap, int64_t* count,
-                               bool compact, const int32_t* vscene, int64_t* npt_out, cudaStream_t st) {
+                               bool compact, const int32_t* vscene, int64_t* npt_out, cudaStream_t st, int nscenes) {
     gipc_prof_span span(ctx->prof, GIPC_PROF_CONTACTS, st);
     Surf S{srf.tris, srf.ntri, srf.edges, srf.nedge, srf.verts, srf.nvert};
     const double pad = dhat * (1.0 + 1e-9);
@@ -758,10 +789,10 @@ gipc_status find_contacts_impl(gipc_ctx* ctx, const double* x, const double* res
     if ((s = ctx->slot[C_MISC].reserve(16 * sizeof(double))) != GIPC_OK) return s;
     const bool pt = S.nvert > 0 && S.ntri > 0;
     Grid Gt{}, Ge{};
-    if (pt && (s = build_grid(ctx, 0, x, nullptr, n, S.tris, 3, S.ntri, pad, nullptr, vscene, Gt, st)) != GIPC_OK)
+    if (pt && (s = build_grid(ctx, 0, x, nullptr, n, S.tris, 3, S.ntri, pad, nullptr, vscene, nscenes, Gt, st)) != GIPC_OK)
         return s;
     if (S.nedge > 0 &&
-        (s = build_grid(ctx, 1, x, nullptr, n, S.edges, 2, S.nedge, pad, nullptr, vscene, Ge, st)) != GIPC_OK)
+        (s = build_grid(ctx, 1, x, nullptr, n, S.edges, 2, S.nedge, pad, nullptr, vscene, nscenes, Ge, st)) != GIPC_OK)
         return s;
     PairList L{};
     int64_t npt = 0, np = 0;
@@ -814,8 +845,8 @@ gipc_status ccd_impl(gipc_ctx* ctx, const double* x, const double* d, int64_t n,
     unsigned long long* amin = reinterpret_cast<unsigned long long*>(amin_d);
     Grid Gt{}, Ge{};
     const bool pt = S.nvert > 0 && S.ntri > 0;
-    if (pt && (s = build_grid(ctx, 0, x, d, n, S.tris, 3, S.ntri, 0.0, &srf, vscene, Gt, st)) != GIPC_OK) return s;
-    if (S.nedge > 0 && (s = build_grid(ctx, 1, x, d, n, S.edges, 2, S.nedge, 0.0, nullptr, vscene, Ge, st)) != GIPC_OK)
+    if (pt && (s = build_grid(ctx, 0, x, d, n, S.tris, 3, S.ntri, 0.0, &srf, vscene, nscenes, Gt, st)) != GIPC_OK) return s;
+    if (S.nedge > 0 && (s = build_grid(ctx, 1, x, d, n, S.edges, 2, S.nedge, 0.0, nullptr, vscene, nscenes, Ge, st)) != GIPC_OK)
         return s;
     PairList L{};
     int64_t npt = 0, np = 0;
@@ -842,7 +873,7 @@ extern "C" gipc_status gipc_find_contacts(gipc_ctx* ctx, const double* x, const 
         (capacity > 0 && (!stencils || !eps_x)))
         return fail(GIPC_ERR_INVALID_ARG, "gipc_find_contacts: null pointer");
     return find_contacts_impl(ctx, x, rest_x, n, *srf, dhat, stencils, eps_x, capacity, count_h, false, nullptr,
-                              nullptr, (cudaStream_t)stream);
+                              nullptr, (cudaStream_t)stream, 1);
 }
 
 extern "C" gipc_status gipc_ccd_max_step(gipc_ctx* ctx, const double* x, const double* d, int64_t n,

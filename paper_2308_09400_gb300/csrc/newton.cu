@@ -17,7 +17,7 @@ namespace gipc {
 
 gipc_status find_contacts_impl(gipc_ctx* ctx, const double* x, const double* rest_x, int64_t n, const gipc_surface& srf,
                                double dhat, int32_t* stencils, double* eps_x, int64_t cap, int64_t* count,
-                               bool compact, const int32_t* vscene, int64_t* npt_out, cudaStream_t st);
+                               bool compact, const int32_t* vscene, int64_t* npt_out, cudaStream_t st, int nscenes);
 gipc_status ccd_impl(gipc_ctx* ctx, const double* x, const double* d, int64_t n, const gipc_surface& srf, double slack,
                      double* alpha_h, cudaStream_t st, const int32_t* vscene, int nscenes, double* amin_dev);
 gipc_status pcg_impl(gipc_ctx* ctx, const gipc_bsr* A, const double* rhs, double* x, const uint8_t* fixed,
@@ -172,7 +172,7 @@ struct Step {
         for (int attempt = 0; attempt < 2; ++attempt) {
             int64_t cnt = 0;
             const gipc_status s = find_contacts_impl(ctx, x, sc.rest_x, n, sc.surface, prm.barrier.dhat, cs.st, cs.eps,
-                                                     cs.cap, &cnt, true, nullptr, nullptr, st);
+                                                     cs.cap, &cnt, true, nullptr, nullptr, st, 1);
             if (s == GIPC_OK) {
                 cs.k = cnt;
                 return GIPC_OK;
@@ -339,7 +339,7 @@ struct Step {
 // cells), the matrix is block diagonal, the PCG keeps per-scene scalars, and every scalar of the
 // Newton loop (energies, CCD step, line-search step, stopping test) is per scene.
 
-enum BatchSlot { B_VS = 41, B_OFF = 42, B_SCAL = 43, B_MASK = 44 };
+enum BatchSlot { B_VS = 48 };
 
 // scene of vertex v for every v (scene k owns [voff[k], voff[k+1]))
 __global__ void vertex_scene_kernel(const int64_t* __restrict__ voff, int nscenes, int64_t n, int32_t* __restrict__ vs) {
@@ -490,32 +490,148 @@ __global__ void scene_mask_kernel(const uint8_t* __restrict__ fixed, const int32
     mask[v] = (fixed && fixed[v]) || !active[vs[v]] ? 1 : 0;
 }
 
-struct BatchStep : Step {
-    int ns;
-    const int64_t* voff_h;
-    const double* l_h;
-    int64_t* voff = nullptr;    // device [ns+1]
-    int32_t* vs = nullptr;      // device [n]
-    double* sI = nullptr;       // device per-scene scalars
-    double* sA = nullptr;
-    double* sD = nullptr;
+// ---- packing: the batch is rebuilt (gathered) to hold only the scenes still iterating ------
+// Element ranges of every scene in a list ordered by scene (one thread per scene).
+__global__ void scene_elem_ranges_kernel(const int32_t* __restrict__ first, int64_t m, const int32_t* __restrict__ vs,
+                                         int ns, int64_t* __restrict__ lo, int64_t* __restrict__ hi) {
+    const int sc = blockIdx.x * blockDim.x + threadIdx.x;
+    if (sc >= ns) return;
+    int64_t l, h;
+    scene_range<false>(first, 0, m, vs, sc, l, h);
+    lo[sc] = l;
+    hi[sc] = h;
+}
+
+__device__ __forceinline__ int packed_scene(const int64_t* __restrict__ off, int nsp, int64_t i) {
+    int lo = 0, hi = nsp - 1;   // last k with off[k] <= i
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= i) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Packed vertex v' of packed scene s' comes from original vertex src[s'] + (v' - pvoff[s']).
+__global__ void pack_vertices_kernel(int64_t np, const int64_t* __restrict__ pvoff, int nsp,
+                                     const int64_t* __restrict__ src, int64_t n, const double* __restrict__ x,
+                                     const double* __restrict__ xt, const double* __restrict__ rest,
+                                     const double* __restrict__ mass, const uint8_t* __restrict__ fixed,
+                                     double* __restrict__ xw, double* __restrict__ xtw, double* __restrict__ restw,
+                                     double* __restrict__ massw, uint8_t* __restrict__ fixedw, int64_t* __restrict__ orig,
+                                     int32_t* __restrict__ vsw) {
+    const int64_t vp = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (vp >= np) return;
+    const int sp = packed_scene(pvoff, nsp, vp);
+    const int64_t v = src[sp] + (vp - pvoff[sp]);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        xw[c * np + vp] = x[c * n + v];
+        xtw[c * np + vp] = xt[c * n + v];
+        restw[c * np + vp] = rest[c * n + v];
+    }
+    massw[vp] = mass[v];
+    fixedw[vp] = fixed ? fixed[v] : 0;
+    orig[vp] = v;
+    vsw[vp] = sp;
+}
+
+// Packed element e' of packed scene s' is original element esrc[s'] + (e' - peoff[s']); its
+// vertex ids shift by vshift[s'].  Optional per-element payload: Dm^-1 (9) and volume.
+__global__ void pack_elements_kernel(int64_t mp, const int64_t* __restrict__ peoff, int nsp,
+                                     const int64_t* __restrict__ esrc, const int64_t* __restrict__ vshift, int nv,
+                                     const int32_t* __restrict__ ids, int64_t m, int32_t* __restrict__ idsw,
+                                     const double* __restrict__ dm, const double* __restrict__ vol,
+                                     double* __restrict__ dmw, double* __restrict__ volw) {
+    const int64_t ep = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (ep >= mp) return;
+    const int sp = packed_scene(peoff, nsp, ep);
+    const int64_t e = esrc[sp] + (ep - peoff[sp]);
+    for (int a = 0; a < nv; ++a) idsw[a * mp + ep] = (int32_t)(ids[a * m + e] + vshift[sp]);
+    if (dm) {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) dmw[k * mp + ep] = dm[k * m + e];
+        volw[ep] = vol[e];
+    }
+}
+
+__global__ void unpack_x_kernel(int64_t np, const int64_t* __restrict__ orig, const double* __restrict__ xw, int64_t n,
+                                double* __restrict__ x) {
+    const int64_t vp = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (vp >= np) return;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) x[c * n + orig[vp]] = xw[c * np + vp];
+}
+
+enum PackSlot { W_V = 41, W_E = 42, W_S = 43, W_I = 44, W_M = 47 };
+
+struct BatchStep {
+    gipc_ctx* ctx;
+    const gipc_scene& full;          // the caller's batch
+    const gipc_step_params& prm;
+    cudaStream_t st;
+    const int ns_full;
+    const int64_t* voff_full_h;
+    const double* l_full_h;
+    // current (possibly packed) batch
+    gipc_scene sc{};
+    int64_t n = 0;
+    int ns = 0;
+    std::vector<int> map;            // packed scene -> original scene
+    std::vector<int64_t> voff_h;
+    std::vector<double> l_h;
+    int64_t* voff = nullptr;         // device [ns+1]
+    int32_t* vs = nullptr;           // device [n]
+    const int64_t* orig = nullptr;   // device [n] original vertex id, NULL when not packed
+    double *x = nullptr, *xt = nullptr;
+    // full-size vectors
+    double *x0 = nullptr, *xt_full = nullptr, *xp = nullptr, *d = nullptr, *g = nullptr, *rhs = nullptr, *gb = nullptr;
+    double *sI = nullptr, *sA = nullptr, *sD = nullptr;
     int64_t* sC = nullptr;
     int32_t* sAct = nullptr;
     uint8_t* mask = nullptr;
+    ContactSet set[2];
+    // element ranges of every original scene (host) for packing
+    std::vector<int64_t> tlo, thi, rlo, rhi, elo, ehi, plo, phi;
     std::vector<double> I_h, Inew_h, alpha_h, dmax_h;
     std::vector<int64_t> cont_h;
     std::vector<int32_t> active_h;
     int64_t npt_cur = 0, npt_nxt = 0;
 
-    BatchStep(gipc_ctx* c, const gipc_scene& s, const gipc_step_params& p, cudaStream_t q, int nsc,
-              const int64_t* vo, const double* l)
-        : Step(c, s, p, q), ns(nsc), voff_h(vo), l_h(l) {}
+    BatchStep(gipc_ctx* c, const gipc_scene& s, const gipc_step_params& p, cudaStream_t q, int nsc, const int64_t* vo,
+              const double* l)
+        : ctx(c), full(s), prm(p), st(q), ns_full(nsc), voff_full_h(vo), l_full_h(l) {
+        set[0].slot = N_ST0;
+        set[1].slot = N_ST1;
+    }
 
-    gipc_status contacts_b(const double* x, ContactSet& cs, int64_t* npt) {
+    void sizes_per_scene() {
+        I_h.assign(ns, 0.0);
+        Inew_h.assign(ns, 0.0);
+        alpha_h.assign(ns, 1.0);
+        dmax_h.assign(ns, 0.0);
+        cont_h.assign(ns, 0);
+    }
+
+    gipc_status scene_scalars() {
+        gipc_status s;
+        if ((s = ctx->slot[W_S].reserve(sizeof(double) * 3 * ns + sizeof(int64_t) * (2 * ns + 2) + sizeof(int32_t) * (ns + 4) +
+                                        64)) != GIPC_OK)
+            return s;
+        sI = ctx->slot[W_S].as<double>();
+        sA = sI + ns;
+        sD = sA + ns;
+        sC = reinterpret_cast<int64_t*>(sD + ns);
+        voff = sC + ns;
+        sAct = reinterpret_cast<int32_t*>(voff + ns + 2);
+        return GIPC_OK;
+    }
+
+    gipc_status contacts_b(const double* xc, ContactSet& cs, int64_t* npt) {
         for (int attempt = 0; attempt < 2; ++attempt) {
             int64_t cnt = 0;
-            const gipc_status s = find_contacts_impl(ctx, x, sc.rest_x, n, sc.surface, prm.barrier.dhat, cs.st, cs.eps,
-                                                     cs.cap, &cnt, true, vs, npt, st);
+            const gipc_status s = find_contacts_impl(ctx, xc, sc.rest_x, n, sc.surface, prm.barrier.dhat, cs.st, cs.eps,
+                                                     cs.cap, &cnt, true, vs, npt, st, ns);
             if (s == GIPC_OK) {
                 cs.k = cnt;
                 return GIPC_OK;
@@ -532,9 +648,9 @@ struct BatchStep : Step {
     }
 
     // per-scene I(x) into I_out (host) and the contacts at x
-    gipc_status potential_b(const double* x, ContactSet& cs, int64_t* npt, std::vector<double>& I_out) {
+    gipc_status potential_b(const double* xc, ContactSet& cs, int64_t* npt, std::vector<double>& I_out) {
         gipc_status s;
-        if ((s = contacts_b(x, cs, npt)) != GIPC_OK) return s;
+        if ((s = contacts_b(xc, cs, npt)) != GIPC_OK) return s;
         const int64_t T = sc.T, k = cs.k;
         gipc_prof_span span(ctx->prof, GIPC_PROF_ENERGY, st);
         if ((s = ctx->slot[N_ENER].reserve(sizeof(double) * (T + k + 2))) != GIPC_OK) return s;
@@ -542,63 +658,199 @@ struct BatchStep : Step {
         double* se = te + T;
         gipc_elastic_params ep = prm.elastic;
         ep.scale = prm.dt * prm.dt;
-        if ((s = gipc_eval_tets(x, n, sc.tets, T, sc.Dm_inv, sc.vol, &ep, GIPC_FP64, te, nullptr, nullptr, st)) != GIPC_OK)
+        if ((s = gipc_eval_tets(xc, n, sc.tets, T, sc.Dm_inv, sc.vol, &ep, GIPC_FP64, te, nullptr, nullptr, st)) != GIPC_OK)
             return s;
-        if (k > 0 && (s = gipc_eval_stencils(x, n, cs.st, k, cs.eps, &prm.barrier, GIPC_FP64, GIPC_HESS_DENSE, se, nullptr,
+        if (k > 0 && (s = gipc_eval_stencils(xc, n, cs.st, k, cs.eps, &prm.barrier, GIPC_FP64, GIPC_HESS_DENSE, se, nullptr,
                                              nullptr, nullptr, nullptr, st)) != GIPC_OK)
             return s;
-        scene_energy_kernel<<<ns, 256, 0, st>>>(x, xt, sc.mass, n, voff, sc.tets, T, te, cs.st, k, *npt, se, vs, sI, sC);
+        scene_energy_kernel<<<ns, 256, 0, st>>>(xc, xt, sc.mass, n, voff, sc.tets, T, te, cs.st, k, *npt, se, vs, sI, sC);
         cudaMemcpyAsync(I_out.data(), sI, sizeof(double) * ns, cudaMemcpyDeviceToHost, st);
         cudaMemcpyAsync(cont_h.data(), sC, sizeof(int64_t) * ns, cudaMemcpyDeviceToHost, st);
         if (cudaStreamSynchronize(st) != cudaSuccess) return check_launch("gipc_newton_step_batch: energy");
         for (int k2 = 0; k2 < ns; ++k2)
-            if (!std::isfinite(I_out[k2])) return fail(GIPC_ERR_NONFINITE, "gipc_newton_step_batch: non-finite energy in scene %d", k2);
+            if (!std::isfinite(I_out[k2]))
+                return fail(GIPC_ERR_NONFINITE, "gipc_newton_step_batch: non-finite energy in scene %d", map[k2]);
         return GIPC_OK;
     }
 
-    gipc_status run_batch(double* x, double* v, gipc_step_stats* stats) {
-        const int64_t m3 = 3 * n;
+    // element ranges of every original scene in the four lists (one synchronisation)
+    gipc_status full_ranges(const int32_t* vs_full) {
         gipc_status s;
-        if ((s = ctx->slot[N_VEC].reserve(sizeof(double) * 7 * m3)) != GIPC_OK) return s;
-        if ((s = ctx->slot[N_RED].reserve(sizeof(double) * (4 * kRedBlocks + 8))) != GIPC_OK) return s;
-        if ((s = ctx->slot[B_VS].reserve(sizeof(int32_t) * (n + 1))) != GIPC_OK) return s;
-        if ((s = ctx->slot[B_OFF].reserve(sizeof(int64_t) * (ns + 1))) != GIPC_OK) return s;
-        if ((s = ctx->slot[B_SCAL].reserve(sizeof(double) * 3 * ns + sizeof(int64_t) * ns + sizeof(int32_t) * (ns + 4))) !=
-            GIPC_OK)
-            return s;
-        if ((s = ctx->slot[B_MASK].reserve(n + 16)) != GIPC_OK) return s;
+        if ((s = ctx->slot[W_I].reserve(sizeof(int64_t) * 8 * (ns_full + 1))) != GIPC_OK) return s;
+        int64_t* R = ctx->slot[W_I].as<int64_t>();
+        const int32_t* lists[4] = {full.tets, full.surface.tris, full.surface.edges, full.surface.verts};
+        const int64_t counts[4] = {full.T, full.surface.ntri, full.surface.nedge, full.surface.nvert};
+        for (int q = 0; q < 4; ++q)
+            scene_elem_ranges_kernel<<<nb(ns_full, 128), 128, 0, st>>>(lists[q], counts[q], vs_full, ns_full,
+                                                                       R + 2 * q * ns_full, R + (2 * q + 1) * ns_full);
+        std::vector<int64_t> h(8 * (size_t)ns_full);
+        cudaMemcpyAsync(h.data(), R, sizeof(int64_t) * 8 * ns_full, cudaMemcpyDeviceToHost, st);
+        if (cudaStreamSynchronize(st) != cudaSuccess) return check_launch("gipc_newton_step_batch: ranges");
+        auto cp = [&](std::vector<int64_t>& o, int k) { o.assign(h.begin() + k * ns_full, h.begin() + (k + 1) * ns_full); };
+        cp(tlo, 0);
+        cp(thi, 1);
+        cp(rlo, 2);
+        cp(rhi, 3);
+        cp(elo, 4);
+        cp(ehi, 5);
+        cp(plo, 6);
+        cp(phi, 7);
+        return GIPC_OK;
+    }
+
+    // Rebuild the working batch from the caller's arrays with the original scenes `keep`.
+    gipc_status pack(const std::vector<int>& keep, double* x_full) {
+        gipc_status s;
+        const int nsp = (int)keep.size();
+        std::vector<int64_t> pvoff(nsp + 1, 0), src(nsp), vshift(nsp);
+        std::vector<int64_t> poff[4], psrc[4];
+        const std::vector<int64_t>* los[4] = {&tlo, &rlo, &elo, &plo};
+        const std::vector<int64_t>* his[4] = {&thi, &rhi, &ehi, &phi};
+        for (int q = 0; q < 4; ++q) {
+            poff[q].assign(nsp + 1, 0);
+            psrc[q].assign(nsp, 0);
+        }
+        for (int k = 0; k < nsp; ++k) {
+            const int o = keep[k];
+            src[k] = voff_full_h[o];
+            pvoff[k + 1] = pvoff[k] + (voff_full_h[o + 1] - voff_full_h[o]);
+            vshift[k] = pvoff[k] - voff_full_h[o];
+            for (int q = 0; q < 4; ++q) {
+                psrc[q][k] = (*los[q])[o];
+                poff[q][k + 1] = poff[q][k] + ((*his[q])[o] - (*los[q])[o]);
+            }
+        }
+        const int64_t np = pvoff[nsp];
+        const int64_t mT = poff[0][nsp], mR = poff[1][nsp], mE = poff[2][nsp], mP = poff[3][nsp];
+        // small index arrays: pvoff, src, vshift, then (poff, psrc) for the four lists
+        const size_t idx_words = (size_t)(nsp + 1) + 2 * nsp + 4 * (2 * nsp + 1);
+        if ((s = ctx->slot[W_M].reserve(sizeof(int64_t) * (idx_words + 8))) != GIPC_OK) return s;
+        int64_t* M = ctx->slot[W_M].as<int64_t>();
+        std::vector<int64_t> hm;
+        hm.reserve(idx_words);
+        hm.insert(hm.end(), pvoff.begin(), pvoff.end());
+        hm.insert(hm.end(), src.begin(), src.end());
+        hm.insert(hm.end(), vshift.begin(), vshift.end());
+        for (int q = 0; q < 4; ++q) {
+            hm.insert(hm.end(), poff[q].begin(), poff[q].end());
+            hm.insert(hm.end(), psrc[q].begin(), psrc[q].end());
+        }
+        cudaMemcpyAsync(M, hm.data(), sizeof(int64_t) * hm.size(), cudaMemcpyHostToDevice, st);
+        const int64_t* d_pvoff = M;
+        const int64_t* d_src = M + nsp + 1;
+        const int64_t* d_vshift = d_src + nsp;
+        const int64_t* d_poff[4];
+        const int64_t* d_psrc[4];
+        const int64_t* cur = d_vshift + nsp;
+        for (int q = 0; q < 4; ++q) {
+            d_poff[q] = cur;
+            d_psrc[q] = cur + nsp + 1;
+            cur += 2 * nsp + 1;
+        }
+        // vertex data: x, xt, rest (3 each), mass, original id, scene id, fixed, solver mask
+        const size_t vbytes = sizeof(double) * 10 * np + sizeof(int64_t) * np + sizeof(int32_t) * np + 2 * np + 64;
+        if ((s = ctx->slot[W_V].reserve(vbytes)) != GIPC_OK) return s;
+        double* V = ctx->slot[W_V].as<double>();
+        double* xw = V;
+        double* xtw = V + 3 * np;
+        double* restw = V + 6 * np;
+        double* massw = V + 9 * np;
+        int64_t* origw = reinterpret_cast<int64_t*>(V + 10 * np);
+        int32_t* vsw = reinterpret_cast<int32_t*>(origw + np);
+        uint8_t* fixedw = reinterpret_cast<uint8_t*>(vsw + np);
+        uint8_t* maskw = fixedw + np;
+        pack_vertices_kernel<<<nb(np, 256), 256, 0, st>>>(np, d_pvoff, nsp, d_src, full.n, x_full, xt_full, full.rest_x,
+                                                          full.mass, full.fixed, xw, xtw, restw, massw, fixedw, origw, vsw);
+        // elements: tets (+ Dm^-1, volume), triangles, edges, surface vertices
+        const size_t ebytes = sizeof(int32_t) * (4 * mT + 3 * mR + 2 * mE + mP) + sizeof(double) * 10 * mT + 256;
+        if ((s = ctx->slot[W_E].reserve(ebytes)) != GIPC_OK) return s;
+        double* E = ctx->slot[W_E].as<double>();
+        double* dmw = E;
+        double* volw = E + 9 * mT;
+        int32_t* tw = reinterpret_cast<int32_t*>(volw + mT);
+        int32_t* rw = tw + 4 * mT;
+        int32_t* ew = rw + 3 * mR;
+        int32_t* pw = ew + 2 * mE;
+        const int32_t* lists[4] = {full.tets, full.surface.tris, full.surface.edges, full.surface.verts};
+        const int64_t counts[4] = {full.T, full.surface.ntri, full.surface.nedge, full.surface.nvert};
+        int32_t* outs[4] = {tw, rw, ew, pw};
+        const int64_t pm[4] = {mT, mR, mE, mP};
+        const int nvs[4] = {4, 3, 2, 1};
+        for (int q = 0; q < 4; ++q)
+            if (pm[q] > 0)
+                pack_elements_kernel<<<nb(pm[q], 256), 256, 0, st>>>(
+                    pm[q], d_poff[q], nsp, d_psrc[q], d_vshift, nvs[q], lists[q], counts[q], outs[q],
+                    q == 0 ? full.Dm_inv : nullptr, q == 0 ? full.vol : nullptr, q == 0 ? dmw : nullptr,
+                    q == 0 ? volw : nullptr);
+        // the working batch
+        ns = nsp;
+        n = np;
+        map = keep;
+        voff_h = pvoff;
+        l_h.assign(nsp, 0.0);
+        for (int k = 0; k < nsp; ++k) l_h[k] = l_full_h[keep[k]];
+        sc = full;
+        sc.n = np;
+        sc.rest_x = restw;
+        sc.tets = tw;
+        sc.T = mT;
+        sc.Dm_inv = dmw;
+        sc.vol = volw;
+        sc.mass = massw;
+        sc.fixed = fixedw;
+        sc.surface = gipc_surface{rw, mR, ew, mE, pw, mP};
+        x = xw;
+        xt = xtw;
+        orig = origw;
+        vs = vsw;
+        mask = maskw;
+        if ((s = scene_scalars()) != GIPC_OK) return s;
+        cudaMemcpyAsync(voff, voff_h.data(), sizeof(int64_t) * (ns + 1), cudaMemcpyHostToDevice, st);
+        sizes_per_scene();
+        return check_launch("gipc_newton_step_batch: pack");
+    }
+
+    void unpack(double* x_full) {
+        if (orig) unpack_x_kernel<<<nb(n, 256), 256, 0, st>>>(n, orig, x, full.n, x_full);
+    }
+
+    gipc_status run_batch(double* x_full, double* v, gipc_step_stats* stats) {
+        const int64_t nf = full.n, m3f = 3 * nf;
+        gipc_status s;
+        if ((s = ctx->slot[N_VEC].reserve(sizeof(double) * 7 * m3f)) != GIPC_OK) return s;
+        if ((s = ctx->slot[B_VS].reserve(sizeof(int32_t) * (nf + 1) + nf + 64)) != GIPC_OK) return s;
         x0 = ctx->slot[N_VEC].as<double>();
-        xt = x0 + m3;
-        xp = xt + m3;
-        d = xp + m3;
-        g = d + m3;
-        rhs = g + m3;
-        gb = rhs + m3;
-        partial = ctx->slot[N_RED].as<double>();
-        res = partial + 4 * kRedBlocks;
-        vs = ctx->slot[B_VS].as<int32_t>();
-        voff = ctx->slot[B_OFF].as<int64_t>();
-        sI = ctx->slot[B_SCAL].as<double>();
-        sA = sI + ns;
-        sD = sA + ns;
-        sC = reinterpret_cast<int64_t*>(sD + ns);
-        sAct = reinterpret_cast<int32_t*>(sC + ns);
-        int32_t* bad = sAct + ns;
-        mask = ctx->slot[B_MASK].as<uint8_t>();
+        xt_full = x0 + m3f;
+        xp = xt_full + m3f;
+        d = xp + m3f;
+        g = d + m3f;
+        rhs = g + m3f;
+        gb = rhs + m3f;
         for (auto& cs : set) {
             cs.cap = (int64_t)(ctx->slot[cs.slot].bytes / (4 * sizeof(int32_t) + sizeof(double)));
             cs.eps = ctx->slot[cs.slot].as<double>();
             cs.st = reinterpret_cast<int32_t*>(cs.eps + cs.cap);
         }
-        I_h.assign(ns, 0.0);
-        Inew_h.assign(ns, 0.0);
-        alpha_h.assign(ns, 1.0);
-        dmax_h.assign(ns, 0.0);
-        cont_h.assign(ns, 0);
-        active_h.assign(ns, 1);
+        // the unpacked working batch is the caller's
+        ns = ns_full;
+        n = nf;
+        sc = full;
+        map.resize(ns);
+        for (int k = 0; k < ns; ++k) map[k] = k;
+        voff_h.assign(voff_full_h, voff_full_h + ns + 1);
+        l_h.assign(l_full_h, l_full_h + ns);
+        vs = ctx->slot[B_VS].as<int32_t>();
+        mask = reinterpret_cast<uint8_t*>(vs + nf + 1);
+        orig = nullptr;
+        x = x_full;
+        xt = xt_full;
+        if ((s = scene_scalars()) != GIPC_OK) return s;
+        sizes_per_scene();
+        std::vector<int32_t> act_full(ns_full, 1);
         // scene of every vertex, and the layout the per-scene sums rely on
-        cudaMemcpyAsync(voff, voff_h, sizeof(int64_t) * (ns + 1), cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(voff, voff_h.data(), sizeof(int64_t) * (ns + 1), cudaMemcpyHostToDevice, st);
         vertex_scene_kernel<<<nb(n, 256), 256, 0, st>>>(voff, ns, n, vs);
+        int32_t* bad = sAct + ns;
         cudaMemsetAsync(bad, 0, sizeof(int32_t), st);
         if (sc.T > 0) batch_layout_kernel<<<nb(sc.T, 256), 256, 0, st>>>(sc.tets, 4, sc.T, n, vs, bad);
         const gipc_surface& sf = sc.surface;
@@ -613,24 +865,43 @@ struct BatchStep : Step {
                         "gipc_newton_step_batch: an element spans two scenes, an id is out of range, or a list is not "
                         "ordered by scene (code %d)",
                         bad_h);
+        if ((s = full_ranges(vs)) != GIPC_OK) return s;
         const double dt = prm.dt;
-        cudaMemcpyAsync(x0, x, sizeof(double) * m3, cudaMemcpyDeviceToDevice, st);
-        inertia_target_kernel<<<nb(n, 256), 256, 0, st>>>(x0, v, sc.fixed, n, dt, (dt * dt) * prm.gravity[0],
-                                                           (dt * dt) * prm.gravity[1], (dt * dt) * prm.gravity[2], xt);
+        cudaMemcpyAsync(x0, x_full, sizeof(double) * m3f, cudaMemcpyDeviceToDevice, st);
+        inertia_target_kernel<<<nb(nf, 256), 256, 0, st>>>(x0, v, full.fixed, nf, dt, (dt * dt) * prm.gravity[0],
+                                                            (dt * dt) * prm.gravity[1], (dt * dt) * prm.gravity[2], xt_full);
         int cur = 0;
         if ((s = potential_b(x, set[cur], &npt_cur, I_h)) != GIPC_OK) return s;
-        std::vector<gipc_step_stats> S((size_t)ns);
-        std::vector<int> piters(ns, 0), pstat(ns, 0);
-        std::vector<int32_t> accepted(ns, 0);
-        const int T = (int)sc.T;
+        std::vector<gipc_step_stats> S((size_t)ns_full);
+        std::vector<double> I_full(ns_full, 0.0);
+        std::vector<int64_t> cont_full(ns_full, 0);
+        std::vector<int> piters(ns_full, 0), pstat(ns_full, 0);
+        std::vector<int32_t> accepted(ns_full, 0);
+        active_h.assign(ns, 1);
         const bool mixed = prm.prec == GIPC_MIXED;
         const size_t hb = mixed ? sizeof(float) : sizeof(double);
         for (int it = 0; it < prm.max_newton; ++it) {
-            bool any = false;
-            for (int k = 0; k < ns; ++k) any |= active_h[k] != 0;
-            if (!any) break;
+            int n_active = 0;
+            for (int k = 0; k < ns; ++k) n_active += active_h[k] != 0;
+            if (n_active == 0) break;
+            if (2 * n_active <= ns) {
+                // half the packed scenes have stopped: keep their results, repack the others
+                for (int k = 0; k < ns; ++k) {
+                    I_full[map[k]] = I_h[k];
+                    cont_full[map[k]] = cont_h[k];
+                }
+                unpack(x_full);
+                std::vector<int> keep;
+                for (int k = 0; k < ns; ++k)
+                    if (active_h[k]) keep.push_back(map[k]);
+                if ((s = pack(keep, x_full)) != GIPC_OK) return s;
+                active_h.assign(ns, 1);
+                if ((s = potential_b(x, set[cur], &npt_cur, I_h)) != GIPC_OK) return s;
+            }
             ContactSet& A = set[cur];
             const int64_t k = A.k;
+            const int64_t m3 = 3 * n;
+            const int T = (int)sc.T;
             ctx->prof.start(GIPC_PROF_ELEMENTS, st);
             if ((s = ctx->slot[N_TEVAL].reserve(sizeof(double) * 12 * T + hb * 144 * T + 16)) != GIPC_OK) return s;
             double* tg = ctx->slot[N_TEVAL].as<double>();
@@ -683,7 +954,7 @@ struct BatchStep : Step {
             if ((s = ccd_impl(ctx, x, d, n, sc.surface, 0.1, alpha_h.data(), st, vs, ns, sA)) != GIPC_OK) return s;
             for (int q = 0; q < ns; ++q) {
                 accepted[q] = active_h[q] ? 0 : 1;
-                if (active_h[q]) S[q].pcg_iters += piters[q];
+                if (active_h[q]) S[map[q]].pcg_iters += piters[q];
             }
             cudaMemcpyAsync(xp, x, sizeof(double) * m3, cudaMemcpyDeviceToDevice, st);
             const int nxt = 1 - cur;
@@ -694,7 +965,7 @@ struct BatchStep : Step {
                 bool all = true;
                 for (int q = 0; q < ns; ++q) {
                     if (accepted[q]) continue;
-                    ++S[q].ls_trials;
+                    ++S[map[q]].ls_trials;
                     if (Inew_h[q] <= I_h[q]) accepted[q] = 1;
                     else {
                         alpha_h[q] *= 0.5;
@@ -711,18 +982,24 @@ struct BatchStep : Step {
             for (int q = 0; q < ns; ++q) {
                 if (!active_h[q]) continue;
                 I_h[q] = Inew_h[q];
-                ++S[q].newton_iters;
-                S[q].last_alpha = alpha_h[q];
+                gipc_step_stats& Z = S[map[q]];
+                ++Z.newton_iters;
+                Z.last_alpha = alpha_h[q];
                 if (dmax_h[q] / (l_h[q] * dt) <= prm.eps_d) {
-                    S[q].converged = 1;
+                    Z.converged = 1;
                     active_h[q] = 0;
                 }
             }
         }
-        velocity_kernel<<<nb(m3, 256), 256, 0, st>>>(x, x0, dt, m3, v);
-        for (int q = 0; q < ns; ++q) {
-            S[q].contacts = cont_h[q];
-            S[q].energy = I_h[q];
+        for (int k = 0; k < ns; ++k) {
+            I_full[map[k]] = I_h[k];
+            cont_full[map[k]] = cont_h[k];
+        }
+        unpack(x_full);
+        velocity_kernel<<<nb(m3f, 256), 256, 0, st>>>(x_full, x0, dt, m3f, v);
+        for (int q = 0; q < ns_full; ++q) {
+            S[q].contacts = cont_full[q];
+            S[q].energy = I_full[q];
             if (stats) stats[q] = S[q];
         }
         return check_launch("gipc_newton_step_batch");
