@@ -448,6 +448,58 @@ typedef struct {
 gipc_status gipc_newton_step_batch(gipc_ctx* ctx, const gipc_scene_batch* batch_h, double* x, double* v,
                                    const gipc_step_params* prm_h, gipc_step_stats* stats_h, void* stream);
 
+/* ------------------------------------------------------------------ differentiation */
+/* The paper has no derivatives with respect to the simulation inputs; this section is the
+ * differentiation extension of the hot path.  Everything here is EXACT (no PSD projection):
+ * element energies are evaluated with hyper-dual numbers, so gradients, Hessian-vector products
+ * and Hessian blocks carry no truncation error. */
+
+/* out = base + sum_e P_e^T v_e: element vectors v_e (the `grad` field of each list, [12][count]
+ * slot-major as gipc_eval_* write them) summed per vertex in ascending element order (tetrahedra
+ * first), the order of the assembled gradient.  `hess`, `lam` and `hess_mode` are ignored.
+ *   base  float64 [3][n] or NULL;  out  float64 [3][n]
+ * Never synchronises.  Errors: GIPC_ERR_INVALID_ARG, GIPC_ERR_OOM, GIPC_ERR_CUDA. */
+gipc_status gipc_scatter_elements(gipc_ctx* ctx, int64_t n, const gipc_elements* stencils_h,
+                                  const gipc_elements* tets_h, const double* base, double* out, void* stream);
+
+/* The incremental potential at x for a given contact list (stencils [4][k], eps_x [k]):
+ *   I(x) = 1/2 (x - xt)^T M (x - xt) + ep.scale sum_T vol Psi(F) + sum_k kappa btilde_k(x)
+ * (Sec. 3.1, Eq. 1-2, Eq. 24-25; Psi as gipc_eval_tets, btilde as gipc_eval_stencils' energy) and
+ * its exact derivatives:
+ *   energy_h  host scalar or NULL (synchronises when given)
+ *   grad      float64 [3][n] or NULL:  dI/dx
+ *   Hu        float64 [3][n] or NULL:  (d2I/dx2) u for u float64 [3][n] (matrix free)
+ * xt may be NULL (no inertia term in energy / grad; Hu still includes M u).
+ * Errors: GIPC_ERR_INVALID_ARG, GIPC_ERR_OOM, GIPC_ERR_CUDA. */
+gipc_status gipc_potential_derivs(gipc_ctx* ctx, const gipc_scene* sc_h, const double* x, const double* xt,
+                                  const int32_t* stencils, const double* eps_x, int64_t k,
+                                  const gipc_barrier_params* bp_h, const gipc_elastic_params* ep_h,
+                                  const double* u, double* energy_h, double* grad, double* Hu, void* stream);
+
+/* The exact Hessian M + sum_e P_e^T (d2 E_e / dx_e^2) P_e of the same potential assembled into
+ * `bsr_h` (float64; capacity protocol of gipc_assemble_bsr).  It may be indefinite.
+ * Synchronises once (pattern size).  Errors as gipc_assemble_bsr. */
+gipc_status gipc_potential_hessian(gipc_ctx* ctx, const gipc_scene* sc_h, const double* x, const int32_t* stencils,
+                                   const double* eps_x, int64_t k, const gipc_barrier_params* bp_h,
+                                   const gipc_elastic_params* ep_h, gipc_bsr* bsr_h, void* stream);
+
+/* Adjoint of one converged implicit step (x_old, v_old) -> (x_new, v_new = (x_new - x_old)/dt),
+ * by implicit differentiation of grad I(x_new) = 0: with a = adj_x_new + adj_v_new / dt on free
+ * vertices, solve H lambda = a (H the exact Hessian at x_new with the contacts at x_new, fixed
+ * vertices filtered; modified PCG to prm_h->pcg_tol * 1e-4 relative, at most 20 prm_h->max_pcg
+ * iterations), then
+ *   adj_v_old = dt M lambda                      (0 on fixed vertices)
+ *   adj_x_old = M lambda - adj_v_new / dt         (adj_x_new - H lambda on fixed vertices)
+ *   *adj_logE_h += -lambda . dI_elastic/dx        (= E dL/dE: Psi is linear in E at fixed nu)
+ * adj_x_new / adj_v_new may be NULL (zero); adj_x_old / adj_v_old may be NULL (not written).
+ * x_new must be a converged step of gipc_newton_step with the same parameters.  Synchronises.
+ * Errors: GIPC_ERR_INVALID_ARG, GIPC_ERR_NOT_CONVERGED (the adjoint solve), GIPC_ERR_OOM,
+ * GIPC_ERR_CUDA. */
+gipc_status gipc_adjoint_step(gipc_ctx* ctx, const gipc_scene* sc_h, const double* x_new, const double* x_old,
+                              const double* v_old, const gipc_step_params* prm_h, const double* adj_x_new,
+                              const double* adj_v_new, double* adj_x_old, double* adj_v_old, double* adj_logE_h,
+                              int* pcg_iters_h, void* stream);
+
 /* ------------------------------------------------------------------ profiling */
 
 /* Kernels that a context can time with CUDA events on the stream they are

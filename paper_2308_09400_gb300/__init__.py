@@ -17,7 +17,8 @@ NULL_INDEX = -2147483648
 
 __all__ = ["compute_eps_x", "eval_stencils", "assemble_bsr", "pcg", "pcg_noalloc", "snh_params", "tet_rest", "eval_tets",
            "Surface", "find_contacts", "ccd_max_step", "Scene", "newton_step", "SceneBatch", "newton_step_batch",
-           "Context", "default_context", "GipcError", "FLAG_ACTIVE", "FLAG_FILTERED",
+           "scatter_elements", "potential_derivs", "potential_hessian", "adjoint_step", "incremental_potential",
+           "IncrementalPotential", "simulate", "adjoint", "Context", "default_context", "GipcError", "FLAG_ACTIVE", "FLAG_FILTERED",
            "FLAG_MOLLIFIED", "FLAG_INVALID", "TYPE_IDS", "NULL_INDEX"]
 
 
@@ -462,3 +463,176 @@ def newton_step_batch(batch, x, v, dt, mu, lam, dhat, kappa, gravity=(0.0, 0.0, 
     _abi.call("gipc_newton_step_batch", ctx.handle, ctypes.byref(b), _ptr(x), _ptr(v), ctypes.byref(prm), stats,
               _stream(stream))
     return [{f: getattr(s, f) for f, _ in _abi.StepStats._fields_} for s in stats]
+
+
+# ------------------------------------------------------------------------- differentiation
+def _step_params(dt, mu, lam, dhat, kappa, gravity=(0.0, 0.0, -9.81), d_thr_ratio=0.1, eps_d=1e-2, pcg_tol=1e-4,
+                 max_pcg=500, max_newton=50, max_ls=30, precision="fp64", hess_mode="dense"):
+    prm = _abi.StepParams()
+    prm.dt = float(dt)
+    prm.gravity[:] = [float(g) for g in gravity]
+    prm.elastic = _abi.ElasticParams(float(mu), float(lam), 0.0)
+    prm.barrier = _abi.BarrierParams(float(dhat), float(kappa), float(d_thr_ratio))
+    prm.eps_d, prm.pcg_tol = float(eps_d), float(pcg_tol)
+    prm.max_pcg, prm.max_newton, prm.max_ls = int(max_pcg), int(max_newton), int(max_ls)
+    prm.prec = {"fp64": _abi.GIPC_FP64, "mixed": _abi.GIPC_MIXED}[precision]
+    prm.hess_mode = {"dense": _abi.GIPC_HESS_DENSE, "rank1": _abi.GIPC_HESS_RANK1}[hess_mode]
+    return prm
+
+
+def scatter_elements(n, stencils=None, stencil_vec=None, tets=None, tet_vec=None, base=None, ctx=None, stream=None):
+    """out [3, n] = base + per-vertex sums of element vectors [12, count] (gipc_scatter_elements)."""
+    ctx = ctx or default_context()
+    dev = (stencils if stencils is not None else tets).device
+    out = torch.empty((3, n), dtype=torch.float64, device=dev)
+    se = _abi.Elements(stencils.data_ptr(), stencils.shape[1], 0, None, None, stencil_vec.data_ptr()) \
+        if stencils is not None else None
+    te = _abi.Elements(tets.data_ptr(), tets.shape[1], 0, None, None, tet_vec.data_ptr()) if tets is not None else None
+    _abi.call("gipc_scatter_elements", ctx.handle, n, ctypes.byref(se) if se else None,
+              ctypes.byref(te) if te else None, _ptr(base), _ptr(out), _stream(stream))
+    return out
+
+
+def potential_derivs(scene, x, stencils, eps_x, dhat, kappa, mu, lam, scale, xt=None, u=None, want=("energy", "grad"),
+                     ctx=None, stream=None):
+    """Exact I(x), dI/dx and (d2I/dx2) u of the incremental potential for a contact list
+    (gipc_potential_derivs).  Returns a dict with the requested keys (energy, grad, Hu)."""
+    ctx = ctx or default_context()
+    _check(x, "x", torch.float64, 3)
+    n = x.shape[1]
+    k = stencils.shape[1] if stencils is not None else 0
+    bp = _abi.BarrierParams(float(dhat), float(kappa), 0.1)
+    ep = _abi.ElasticParams(float(mu), float(lam), float(scale))
+    e = ctypes.c_double(0.0)
+    out = {}
+    grad = torch.empty((3, n), dtype=torch.float64, device=x.device) if "grad" in want else None
+    Hu = torch.empty((3, n), dtype=torch.float64, device=x.device) if u is not None else None
+    sc = scene.struct()
+    _abi.call("gipc_potential_derivs", ctx.handle, ctypes.byref(sc), _ptr(x), _ptr(xt),
+              _ptr(stencils) if k else None, _ptr(eps_x) if k else None, k, ctypes.byref(bp), ctypes.byref(ep),
+              _ptr(u), ctypes.byref(e) if "energy" in want else None, _ptr(grad), _ptr(Hu), _stream(stream))
+    if "energy" in want:
+        out["energy"] = e.value
+    if grad is not None:
+        out["grad"] = grad
+    if Hu is not None:
+        out["Hu"] = Hu
+    return out
+
+
+def potential_hessian(scene, x, stencils, eps_x, dhat, kappa, mu, lam, scale, ctx=None, stream=None):
+    """The exact Hessian (mass + element Hessians) as a BSR dict (gipc_potential_hessian)."""
+    ctx = ctx or default_context()
+    n = x.shape[1]
+    k = stencils.shape[1] if stencils is not None else 0
+    bp = _abi.BarrierParams(float(dhat), float(kappa), 0.1)
+    ep = _abi.ElasticParams(float(mu), float(lam), float(scale))
+    rowptr = torch.empty(n + 1, dtype=torch.int32, device=x.device)
+    cap = 64 * n + 1024
+    sc = scene.struct()
+    for _ in range(2):
+        colidx = torch.empty(cap, dtype=torch.int32, device=x.device)
+        vals = torch.empty(cap * 9, dtype=torch.float64, device=x.device)
+        b = _abi.Bsr(n, 0, cap, rowptr.data_ptr(), colidx.data_ptr(), vals.data_ptr(), _abi.GIPC_FP64)
+        s = _abi.call_status("gipc_potential_hessian", ctx.handle, ctypes.byref(sc), _ptr(x),
+                             _ptr(stencils) if k else None, _ptr(eps_x) if k else None, k, ctypes.byref(bp),
+                             ctypes.byref(ep), ctypes.byref(b), _stream(stream))
+        if s == _abi.GIPC_OK:
+            return {"n": n, "nnzb": b.nnzb, "rowptr": rowptr, "colidx": colidx[:b.nnzb],
+                    "vals": vals[:9 * b.nnzb].reshape(-1, 3, 3), "prec": "fp64"}
+        if s != _abi.GIPC_ERR_CAPACITY:
+            raise GipcError("gipc_potential_hessian", s)
+        cap = b.nnzb + 16
+    raise GipcError("gipc_potential_hessian", s)
+
+
+def adjoint_step(scene, x_new, x_old, v_old, adj_x_new, adj_v_new, dt, mu, lam, dhat, kappa, pcg_tol=1e-4,
+                 max_pcg=500, ctx=None, stream=None):
+    """Adjoint of one converged implicit step (gipc_adjoint_step): returns
+    (dL/dx_old, dL/dv_old, E dL/dE of this step, adjoint PCG iterations)."""
+    ctx = ctx or default_context()
+    prm = _step_params(dt, mu, lam, dhat, kappa, pcg_tol=pcg_tol, max_pcg=max_pcg)
+    ax = torch.empty_like(x_new)
+    av = torch.empty_like(x_new)
+    le = ctypes.c_double(0.0)
+    it = ctypes.c_int(0)
+    sc = scene.struct()
+    st = _abi.call_status("gipc_adjoint_step", ctx.handle, ctypes.byref(sc), _ptr(x_new), _ptr(x_old), _ptr(v_old),
+                          ctypes.byref(prm), _ptr(adj_x_new), _ptr(adj_v_new), _ptr(ax), _ptr(av), ctypes.byref(le),
+                          ctypes.byref(it), _stream(stream))
+    if st not in (_abi.GIPC_OK, _abi.GIPC_ERR_NOT_CONVERGED):
+        raise GipcError("gipc_adjoint_step", st)
+    return ax, av, le.value, it.value
+
+
+class _PotentialGrad(torch.autograd.Function):
+    """x -> dI/dx; its backward is the exact Hessian-vector product (matrix free)."""
+
+    @staticmethod
+    def forward(ctx_, x, args):
+        ctx_.save_for_backward(x)
+        ctx_.args = args
+        return potential_derivs(args["scene"], x.detach().contiguous(), args["stencils"], args["eps_x"], args["dhat"],
+                                args["kappa"], args["mu"], args["lam"], args["scale"], xt=args["xt"],
+                                want=("grad",))["grad"]
+
+    @staticmethod
+    def backward(ctx_, gout):
+        (x,) = ctx_.saved_tensors
+        a = ctx_.args
+        Hu = potential_derivs(a["scene"], x.detach().contiguous(), a["stencils"], a["eps_x"], a["dhat"], a["kappa"],
+                              a["mu"], a["lam"], a["scale"], xt=a["xt"], u=gout.contiguous(), want=())["Hu"]
+        return Hu, None
+
+
+class IncrementalPotential(torch.autograd.Function):
+    """I(x) of one implicit step for a fixed contact list: backward is the exact gradient kernel,
+    double backward the exact Hessian-vector kernel (use torch.autograd.grad(..., create_graph=True))."""
+
+    @staticmethod
+    def forward(ctx_, x, args):
+        ctx_.save_for_backward(x)
+        ctx_.args = args
+        e = potential_derivs(args["scene"], x.detach().contiguous(), args["stencils"], args["eps_x"], args["dhat"],
+                             args["kappa"], args["mu"], args["lam"], args["scale"], xt=args["xt"],
+                             want=("energy",))["energy"]
+        return torch.tensor(e, dtype=torch.float64, device=x.device)
+
+    @staticmethod
+    def backward(ctx_, gout):
+        (x,) = ctx_.saved_tensors
+        g = _PotentialGrad.apply(x, ctx_.args)
+        return gout * g, None
+
+
+def incremental_potential(x, scene, xt, stencils, eps_x, dhat, kappa, mu, lam, scale):
+    """Differentiable I(x) (see IncrementalPotential)."""
+    args = dict(scene=scene, xt=xt, stencils=stencils, eps_x=eps_x, dhat=dhat, kappa=kappa, mu=mu, lam=lam,
+                scale=scale)
+    return IncrementalPotential.apply(x, args)
+
+
+def simulate(scene, x0, v0, steps, dt, mu, lam, dhat, kappa, **kw):
+    """Implicit steps with the state checkpointed before each step: returns (x, v, checkpoints),
+    checkpoints = [(x_t, v_t)] for t = 0 .. steps (the last one is the result)."""
+    x, v = x0.clone(), v0.clone()
+    cps = [(x.clone(), v.clone())]
+    for _ in range(steps):
+        newton_step(scene, x, v, dt=dt, mu=mu, lam=lam, dhat=dhat, kappa=kappa, **kw)
+        cps.append((x.clone(), v.clone()))
+    return x, v, cps
+
+
+def adjoint(scene, checkpoints, dL_dx_final, dL_dv_final, dt, mu, lam, dhat, kappa, **kw):
+    """Implicit adjoint through the checkpointed steps (newest first): returns
+    (dL/dx0, dL/dv0, dL/dE * E, adjoint PCG iterations per step)."""
+    ax, av = dL_dx_final, dL_dv_final
+    logE = 0.0
+    its = []
+    for t in range(len(checkpoints) - 1, 0, -1):
+        x_new = checkpoints[t][0]
+        x_old, v_old = checkpoints[t - 1]
+        ax, av, le, it = adjoint_step(scene, x_new, x_old, v_old, ax, av, dt, mu, lam, dhat, kappa, **kw)
+        logE += le
+        its.append(it)
+    return ax, av, logE, its

@@ -106,6 +106,13 @@ SIGNATURES = {
     "gipc_newton_step": (_INT, [_P, ctypes.POINTER(Scene), _P, _P, ctypes.POINTER(StepParams),
                                 ctypes.POINTER(StepStats), _P]),
     "gipc_newton_step_batch": (_INT, [_P, ctypes.POINTER(SceneBatch), _P, _P, ctypes.POINTER(StepParams), _P, _P]),
+    "gipc_scatter_elements": (_INT, [_P, _I64, ctypes.POINTER(Elements), ctypes.POINTER(Elements), _P, _P, _P]),
+    "gipc_potential_derivs": (_INT, [_P, ctypes.POINTER(Scene), _P, _P, _P, _P, _I64, ctypes.POINTER(BarrierParams),
+                                     ctypes.POINTER(ElasticParams), _P, ctypes.POINTER(_D), _P, _P, _P]),
+    "gipc_potential_hessian": (_INT, [_P, ctypes.POINTER(Scene), _P, _P, _P, _I64, ctypes.POINTER(BarrierParams),
+                                      ctypes.POINTER(ElasticParams), ctypes.POINTER(Bsr), _P]),
+    "gipc_adjoint_step": (_INT, [_P, ctypes.POINTER(Scene), _P, _P, _P, ctypes.POINTER(StepParams), _P, _P, _P, _P,
+                                 ctypes.POINTER(_D), ctypes.POINTER(_INT), _P]),
     "gipc_profile_begin": (_INT, [_P]),
     "gipc_profile_read": (_INT, [_P, _INT, ctypes.POINTER(KernelTime)]),
     "gipc_profile_stop": (_INT, [_P]),

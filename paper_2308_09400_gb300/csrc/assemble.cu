@@ -387,6 +387,40 @@ __global__ void values_kernel(const uint64_t* __restrict__ keys, const int64_t* 
     }
 }
 
+// out[r] = base[r] + the slot vectors of the elements containing vertex r, in ascending element
+// id (tetrahedra first) -- the order the assembled gradient uses.  The row's keys are sorted by
+// (column, contribution id), so the contributions of vertex r to itself form one run.
+__global__ void scatter_rows_kernel(const uint64_t* __restrict__ keys, const int64_t* __restrict__ row_start, int64_t n,
+                                    ElemList tets, ElemList sts, const double* __restrict__ base,
+                                    double* __restrict__ out) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    int64_t lo = row_start[r], hi = row_start[r + 1];
+    while (lo < hi) {   // first key of column r
+        const int64_t m = (lo + hi) >> 1;
+        if (key_col(keys[m]) < (uint32_t)r) lo = m + 1;
+        else hi = m;
+    }
+    double acc[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) acc[i] = base ? base[(int64_t)i * n + r] : 0.0;
+    for (int64_t p = lo; p < row_start[r + 1] && key_col(keys[p]) == (uint32_t)r; ++p) {
+        const uint32_t cid1 = (uint32_t)keys[p];
+        if (cid1 == 0u) continue;
+        const uint32_t cid = cid1 - 1u;
+        const int64_t e = cid >> 4;
+        const int a = (cid >> 2) & 3;
+        const bool is_tet = e < tets.count;
+        const ElemList& Lst = is_tet ? tets : sts;
+        const int64_t el = is_tet ? e : e - tets.count;
+        if (!Lst.grad) continue;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) acc[i] = __dadd_rn(acc[i], Lst.grad[(int64_t)(3 * a + i) * Lst.count + el]);
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) out[(int64_t)i * n + r] = acc[i];
+}
+
 inline unsigned blocks_for(int64_t work, int threads, int64_t cap = 152 * 32) {
     int64_t b = (work + threads - 1) / threads;
     if (b < 1) b = 1;
@@ -505,4 +539,60 @@ extern "C" gipc_status gipc_assemble_bsr(gipc_ctx* ctx, int64_t n, const gipc_el
     }
     ctx->prof.stop(GIPC_PROF_ASM_VALUES, s);
     return check_launch("gipc_assemble_bsr: values");
+}
+
+extern "C" gipc_status gipc_scatter_elements(gipc_ctx* ctx, int64_t n, const gipc_elements* stencils_h,
+                                             const gipc_elements* tets_h, const double* base, double* out,
+                                             void* stream) {
+    using namespace gipc;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!ctx || !out) return fail(GIPC_ERR_INVALID_ARG, "gipc_scatter_elements: null context or output");
+    if (n <= 0 || n >= INT32_MAX) return fail(GIPC_ERR_INVALID_ARG, "gipc_scatter_elements: n out of range");
+    ElemList L[2] = {};
+    const gipc_elements* in[2] = {tets_h, stencils_h};
+    for (int q = 0; q < 2; ++q) {
+        if (!in[q] || in[q]->count == 0) continue;
+        const gipc_elements& E = *in[q];
+        if (E.count < 0 || !E.idx) return fail(GIPC_ERR_INVALID_ARG, "gipc_scatter_elements: bad element list");
+        L[q] = {E.idx, E.count, GIPC_HESS_DENSE, nullptr, nullptr, E.grad};
+    }
+    const int64_t ne = L[0].count + L[1].count;
+    if (ne >= (int64_t)(1 << 28) - 1) return fail(GIPC_ERR_INVALID_ARG, "gipc_scatter_elements: too many elements");
+    const int64_t cbound = 16 * ne + n;
+    gipc_status st;
+    if ((st = ctx->slot[S_ROWCNT].reserve(sizeof(int32_t) * (n + 1))) != GIPC_OK) return st;
+    if ((st = ctx->slot[S_ROWSTART].reserve(sizeof(int64_t) * (n + 1))) != GIPC_OK) return st;
+    if ((st = ctx->slot[S_KEYS].reserve(sizeof(uint64_t) * cbound)) != GIPC_OK) return st;
+    if ((st = ctx->slot[S_NNZB].reserve(sizeof(int32_t) * (n + 1))) != GIPC_OK) return st;
+    if ((st = ctx->slot[S_ELEMN3].reserve(ne + 1)) != GIPC_OK) return st;
+    if ((st = ctx->slot[S_MISC].reserve(sizeof(uint64_t) * n + sizeof(int32_t) * (2 * n + 4))) != GIPC_OK) return st;
+    if ((st = ctx->slot[S_SCAN].reserve(sizeof(int64_t) * scan_scratch_words(n + 1))) != GIPC_OK) return st;
+    int32_t* row_cnt = ctx->slot[S_ROWCNT].as<int32_t>();
+    int64_t* row_start = ctx->slot[S_ROWSTART].as<int64_t>();
+    uint64_t* keys = ctx->slot[S_KEYS].as<uint64_t>();
+    int32_t* row_nnzb = ctx->slot[S_NNZB].as<int32_t>();
+    uint8_t* elem_n3 = ctx->slot[S_ELEMN3].as<uint8_t>();
+    unsigned long long* cursor = ctx->slot[S_MISC].as<unsigned long long>();
+    int32_t* long_rows = reinterpret_cast<int32_t*>(cursor + n);
+    int32_t* n_long = long_rows + n;
+    int32_t* n_huge = n_long + 1;
+    int32_t* huge_rows = n_huge + 1;
+    int64_t* scan_tmp = ctx->slot[S_SCAN].as<int64_t>();
+    init_rows_kernel<<<blocks_for(n, 256, 1 << 30), 256, 0, s>>>(row_cnt, n, 0);
+    if (ne > 0) count_kernel<<<blocks_for(ne, 256), 256, 0, s>>>(L[0], L[1], n, row_cnt, elem_n3);
+    if (exclusive_scan<int32_t>(row_cnt, row_start, n, scan_tmp, s) != cudaSuccess)
+        return check_launch("gipc_scatter_elements: scan");
+    init_cursor_kernel<<<blocks_for(n, 256, 1 << 30), 256, 0, s>>>(row_start, cursor, keys, n, 0);
+    if (ne > 0) fill_kernel<<<blocks_for(ne, 256), 256, 0, s>>>(L[0], L[1], n, elem_n3, cursor, keys);
+    if (cudaMemsetAsync(n_long, 0, 2 * sizeof(int32_t), s) != cudaSuccess)
+        return fail(GIPC_ERR_CUDA, "gipc_scatter_elements: memset failed");
+    sort_rows_warp_kernel<<<blocks_for(n, kSortWarps, 152 * 64), 32 * kSortWarps, 0, s>>>(row_start, keys, n, row_nnzb,
+                                                                                       long_rows, n_long);
+    cudaFuncSetAttribute(sort_rows_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(kBlockRowMax * sizeof(uint64_t)));
+    sort_rows_block_kernel<<<152, 1024, kBlockRowMax * sizeof(uint64_t), s>>>(row_start, keys, row_nnzb, long_rows,
+                                                                          n_long, huge_rows, n_huge);
+    sort_rows_global_kernel<<<152, 1024, 0, s>>>(row_start, keys, row_nnzb, huge_rows, n_huge);
+    scatter_rows_kernel<<<blocks_for(n, 256, 1 << 30), 256, 0, s>>>(keys, row_start, n, L[0], L[1], base, out);
+    return check_launch("gipc_scatter_elements");
 }

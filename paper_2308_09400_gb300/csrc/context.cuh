@@ -78,7 +78,7 @@ struct gipc_prof_span {
 
 struct gipc_ctx {
     int device = 0;
-    static constexpr int kSlots = 56;   // assembly 0-8, pcg 9-15 and 40, contacts 16-19, 30-39 and 45-46, time step 20-29, 41-44 and 47-48
+    static constexpr int kSlots = 64;   // assembly 0-8, pcg 9-15 and 40, contacts 16-19, 30-39 and 45-46, time step 20-29, 41-44 and 47-48, derivatives 49-57
     gipc_scratch slot[kSlots];
     gipc_profiler prof;
     void release_all() {

@@ -514,18 +514,19 @@ def _merge(parts):
     return np.ascontiguousarray(np.concatenate(xs, axis=1)), np.ascontiguousarray(np.concatenate(ts, axis=1).astype(np.int32))
 
 
-def two_cubes(gap=0.5, velocity=-2.0):
-    """Two unit cubes, 5x5x5 vertices (125 verts, 384 tets) each; the top one `gap` above the
-    bottom one moving at `velocity` in z; the bottom face z = 0 is fixed.
+def two_cubes(gap=0.5, velocity=-2.0, m=5):
+    """Two unit cubes of m x m x m vertices each (m = 5: 125 verts, 384 tets); the top one `gap`
+    above the bottom one moving at `velocity` in z; the bottom face z = 0 is fixed.
     Returns dict(x, v, tets, fixed, tris, edges, verts, l)."""
-    xa, ta = tet_box(5, 5, 5, spacing=0.25)
-    xb, tb = tet_box(5, 5, 5, spacing=0.25, origin=(0.0, 0.0, 1.0 + gap))
+    xa, ta = tet_box(m, m, m, spacing=1.0 / (m - 1))
+    xb, tb = tet_box(m, m, m, spacing=1.0 / (m - 1), origin=(0.0, 0.0, 1.0 + gap))
     x, tets = _merge([(xa, ta), (xb, tb)])
     n = x.shape[1]
+    na = xa.shape[1]
     v = np.zeros((3, n))
-    v[2, 125:] = velocity
+    v[2, na:] = velocity
     fixed = np.zeros(n, np.uint8)
-    fixed[:125][xa[2] == 0.0] = 1
+    fixed[:na][xa[2] == 0.0] = 1
     tris, edges, verts = surface_lists(x, tets)
     l = float(np.linalg.norm(x.max(axis=1) - x.min(axis=1)))
     return {"x": x, "v": v, "tets": tets, "fixed": fixed, "tris": tris, "edges": edges, "verts": verts, "l": l}
