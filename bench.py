@@ -34,6 +34,7 @@ KAPPA = 1e3
 HBM_PEAK_FALLBACK = 6800.0        # GB/s, recipe fallback
 FP64_PEAK = 152 * 4 * 2.070       # GFLOP/s: 152 SMs x 2 FP64 FMA/clk x 2070 MHz (nominal 1.25 TFLOP/s)
 FP32_PEAK = 152 * 256 * 2.070     # GFLOP/s: 152 SMs x 128 FP32 FMA/clk x 2070 MHz
+PROF_EVERY = 8                     # per-iteration solver kernels: one CUDA-event span per 8 launches
 
 
 def parse():
@@ -49,6 +50,8 @@ def parse():
                     help="implicit time steps of the sphere-grid scene per precision (0: skip)")
     ap.add_argument("--batch-steps", type=int, default=3,
                     help="time steps of the 256-scene batch, batched and one scene at a time (0: skip)")
+    ap.add_argument("--diff-steps", type=int, default=10,
+                    help="checkpointed steps of the beam-on-plate scene differentiated by the adjoint (0: skip)")
     ap.add_argument("--c2-steps", type=int, default=3,
                     help="time steps of the per-step FP64 / mixed converged-position comparison (0: skip)")
     return ap.parse_args()
@@ -74,7 +77,7 @@ def workload(seed_offset=0):
 def workload_desc(args):
     return (f"C1 batch: {K_STENCILS} stencils (own-vertex geometry, 3.7M vertex slots) -> "
             f"{args.hess_mode} {'FP64' if args.precision == 'fp64' else 'FP32'} Hessian blocks -> BSR over "
-            f"2x388x388 two-sheet index space -> {PCG_ITERS} PCG iterations")
+            f"2x388x388 two-sheet index space (stencils of each type in cell order) -> {PCG_ITERS} PCG iterations")
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -197,6 +200,8 @@ def run_gpu(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     ctx = g.default_context()
+    for kind in ("pcg_spmv", "pcg_update", "pcg_direction"):   # spans on 1 of every PROF_EVERY iterations
+        ctx.profile_sampling(kind, PROF_EVERY)
 
     Wh = workload(seed_offset=rank)
     W = {"x": torch.tensor(Wh["x"], device=dev), "st_own": torch.tensor(Wh["st_own"], device=dev),
@@ -278,12 +283,13 @@ def run_gpu(args):
         ach_fl = flops_l / avg / 1e9
         if args.precision == "fp64" and ach_fl / FP64_PEAK > ach_bw / hbm:
             roof = {"bound": "alu", "achieved": ach_fl / 1e3, "peak": FP64_PEAK / 1e3, "unit": "TFLOP/s",
-                    "frac": ach_fl / FP64_PEAK, "kernel": "pcg_spmv_sell_kernel<double>",
+                    "frac": ach_fl / FP64_PEAK, "kernel": "pcg_spmv_tma_kernel<double, double, 1, 16, 2>",
                     "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2070 MHz (probe measured 1.26 TFLOP/s)",
                     "hbm_frac": ach_bw / hbm}
         else:
             roof = {"bound": "hbm", "achieved": ach_bw, "peak": hbm, "unit": "GB/s", "frac": ach_bw / hbm,
-                    "kernel": f"pcg_spmv_sell_kernel<{'double' if args.precision == 'fp64' else 'float'}>",
+                    "kernel": ("pcg_spmv_tma_kernel<double, double, 1, 16, 2>" if args.precision == "fp64"
+                               else "pcg_spmv_tma_kernel<float, float, 2, 16, 2>"),
                     "peak_source": f"{hbm_src} (MEASURED_PEAKS.json hbm_gbs)" if hbm_src == "measured" else hbm_src,
                     "fp64_frac": ach_fl / FP64_PEAK if args.precision == "fp64" else None}
         roof["algorithmic_bytes_per_launch"] = bytes_l
@@ -300,7 +306,9 @@ def run_gpu(args):
             "config": {"workload": workload_desc(args), "stencils_per_gpu": K_STENCILS, "vertices": n,
                        "nnzb": nnzb, "pcg_iterations": PCG_ITERS, "precision": args.precision,
                        "hess_mode": args.hess_mode, "parallelism": f"replicas{world}",
-                       "l2": "inputs larger than L2 (>1.3 GB touched per step; no flush needed)"},
+                       "l2": "inputs larger than L2 (>1.3 GB touched per step; no flush needed)",
+                       "kernel_timing": f"CUDA-event spans in the timed region; PCG kernels on 1 of every {PROF_EVERY} "
+                                        "iterations"},
             "phases_ms": {"eval": phase[0], "assemble": phase[1], "pcg": phase[2]},
             "kernel_ms": {k: (v[1] / max(v[0], 1)) for k, v in prof.items()},
             "linearize_solve_per_s": 1000.0 / ms,
@@ -314,6 +322,8 @@ def run_gpu(args):
             line["newton"] = run_newton(g, dev, ctx, args.newton_steps, args.c2_steps)
         if args.batch_steps > 0:
             line["batched"] = run_batch_bench(g, dev, ctx, args.batch_steps)
+        if args.diff_steps > 0:
+            line["differentiation"] = run_diff_bench(g, dev, ctx, args.diff_steps)
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args, Wh, sample=16000)
         print(json.dumps(line))
@@ -466,6 +476,119 @@ def run_batch_bench(g, dev, ctx, steps):
                                "scene_newton_iters": its, "scene_newton_iters_one_at_a_time": its1,
                                "scene_newton_iters_per_step": per_step, "speedup": ms_p / ms_b}
     return out
+
+
+# ----------------------------------------------------------------------------- differentiation
+DIFF_SEED = 20230814
+
+
+def run_diff_bench(g, dev, ctx, steps, fd_h=1e-6, eps_d=1e-5, eps_polish=1e-12):
+    """Tet beam (41 x 11 x 11 vertices, 1.0 x 0.25 x 0.25) turned 0.3 rad about z and resting on a
+    tet plate (65 x 65 x 4 vertices, 2 x 2, bottom layer fixed), the beam moving at (0.05, 0, -0.1)
+    m/s; FP64 dense steps (dt 0.01, E 1e5, nu 0.4, rho 1000, dhat 1e-3 l, kappa 1e3).
+    Each step: projected Newton to eps_d, then exact-Hessian Newton refinement to eps_polish.
+    L = w . x_T for seeded w: `steps` checkpointed steps, the implicit adjoint back through them
+    (dL/dv0, E dL/dE), the exact derivative kernels at x_T (gradient + Hessian-vector product per
+    element and through autograd), and central differences with step fd_h of L along a seeded
+    direction of v0 and in log E."""
+    import numpy as np
+    import torch
+    import synth
+
+    sc = synth.beam_on_plate()
+    T = lambda a: torch.tensor(np.ascontiguousarray(a), device=dev)
+    srf = g.Surface(T(sc["tris"]), T(sc["edges"]), T(sc["verts"]))
+    scene = g.Scene(T(sc["x"]), T(sc["tets"]), srf, 1000.0, fixed=T(sc["fixed"]), l=sc["l"])
+    mu, lam = g.snh_params(1e5, 0.4)
+    dt, dhat = 0.01, sc["dhat"]
+    prm = dict(dt=dt, mu=mu, lam=lam, dhat=dhat, kappa=KAPPA, eps_d=eps_d, pcg_tol=1e-10, max_pcg=5000,
+               max_newton=100)
+    pol = dict(eps_polish=eps_polish, max_iters=10, pcg_tol=1e-24, max_pcg=20000)
+    adj_tol = 1e-22     # r.P^-1 r relative to its start: an 1e-11 smaller residual
+    x0, v0 = T(sc["x"]), T(sc["v"])
+    g.newton_step(scene, x0.clone(), v0.clone(), **prm)      # warm-up (scratch sizing)
+    torch.cuda.synchronize()
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    e0, e1 = ev(), ev()
+    stats = []
+    e0.record()
+    xT, vT, cps = g.simulate(scene, x0, v0, steps, stats=stats, polish=pol, **prm)
+    e1.record()
+    torch.cuda.synchronize()
+    fwd_ms = e0.elapsed_time(e1)
+    rng = np.random.default_rng(DIFF_SEED)
+    w = T(rng.normal(size=sc["x"].shape))
+    zero = torch.zeros_like(w)
+    g.adjoint_step(scene, cps[1][0], cps[0][0], cps[0][1], w, zero, dt, mu, lam, dhat, KAPPA, pcg_tol=adj_tol,
+                   max_pcg=20000)
+    torch.cuda.synchronize()
+    e0.record()
+    ax0, av0, logE, its = g.adjoint(scene, cps, w, zero, dt, mu, lam, dhat, KAPPA, pcg_tol=adj_tol, max_pcg=20000)
+    e1.record()
+    torch.cuda.synchronize()
+    adj_ms = e0.elapsed_time(e1)
+
+    # derivative kernels at x_T with the contacts there
+    stn, eps = g.find_contacts(xT, scene.rest_x, scene.surface, dhat)
+    k = int(stn.shape[1])
+    ntet = int(sc["tets"].shape[1])
+    xt = cps[-2][0] + dt * cps[-2][1]
+    u = T(rng.normal(size=sc["x"].shape))
+    args = (scene, xT, stn, eps, dhat, KAPPA, mu, lam, dt * dt)
+    reps = 20
+    for _ in range(3):
+        g.potential_derivs(*args, xt=xt, u=u, want=("grad",))
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        g.potential_derivs(*args, xt=xt, u=u, want=("grad",))
+    e1.record()
+    torch.cuda.synchronize()
+    derivs_ms = e0.elapsed_time(e1) / reps
+    X = xT.clone().requires_grad_(True)
+    for r in range(reps + 3):
+        if r == 3:
+            torch.cuda.synchronize()
+            e0.record()
+        I = g.incremental_potential(X, scene, xt, stn, eps, dhat, KAPPA, mu, lam, dt * dt)
+        (gX,) = torch.autograd.grad(I, X, create_graph=True)
+        (Hu,) = torch.autograd.grad((gX * u).sum(), X)
+    e1.record()
+    torch.cuda.synchronize()
+    autograd_ms = e0.elapsed_time(e1) / reps
+
+    # central differences of the GPU forward
+    def L(v, mu_=mu, lam_=lam):
+        xx, _, _ = g.simulate(scene, x0, v, steps, polish=pol, **dict(prm, mu=mu_, lam=lam_))
+        return float((w * xx).sum())
+
+    dirv = rng.normal(size=sc["x"].shape)
+    dirv[:, np.asarray(sc["fixed"], bool)] = 0.0
+    dv = T(dirv)
+    fd_v = (L(v0 + fd_h * dv) - L(v0 - fd_h * dv)) / (2 * fd_h)
+    ad_v = float((av0 * dv).sum())
+    mp, lp = g.snh_params(1e5 * (1 + fd_h), 0.4)
+    mm, lm = g.snh_params(1e5 * (1 - fd_h), 0.4)
+    fd_E = (L(v0, mp, lp) - L(v0, mm, lm)) / (np.log1p(fd_h) - np.log1p(-fd_h))
+    newton_its = sum(s["newton_iters"] for s in stats)
+    return {"workload": "tet beam 41x11x11 (turned 0.3 rad) resting on a tet plate 65x65x4, beam at "
+                        "(0.05, 0, -0.1) m/s; L = w . x_T, w seeded normal",
+            "vertices": int(sc["x"].shape[1]), "tets": ntet, "surface_tris": int(sc["tris"].shape[1]),
+            "surface_edges": int(sc["edges"].shape[1]), "dhat": dhat, "eps_d": eps_d, "eps_polish": eps_polish,
+            "time_steps": steps, "polish_iters": [s["polish_iters"] for s in stats],
+            "polish_final_step": max(s["polish_step"] for s in stats),
+            "contacts_per_step": [s["contacts"] for s in stats], "newton_iters": newton_its,
+            "converged_steps": int(sum(s["converged"] for s in stats)),
+            "forward_ms": fwd_ms,
+            "forward_iters_per_s": (newton_its + sum(s["polish_iters"] for s in stats)) / (fwd_ms * 1e-3),
+            "adjoint_ms": adj_ms, "adjoint_ms_per_step": adj_ms / steps, "adjoint_pcg_iters": its,
+            "adjoint_pcg_tol": adj_tol,
+            "derivative_kernels": {"contacts": k, "tets": ntet, "grad_and_hvp_ms": derivs_ms,
+                                   "elements_per_s": (k + ntet) / (derivs_ms * 1e-3),
+                                   "autograd_grad_and_double_backward_ms": autograd_ms},
+            "fd_check": {"h": fd_h, "dL_dv0_dir": {"adjoint": ad_v, "fd": fd_v,
+                                                   "rel_err": abs(ad_v - fd_v) / abs(fd_v)},
+                         "E_dL_dE": {"adjoint": logE, "fd": fd_E, "rel_err": abs(logE - fd_E) / abs(fd_E)}}}
 
 
 # ----------------------------------------------------------------------------- oracle (CPU) arm

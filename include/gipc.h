@@ -486,8 +486,10 @@ gipc_status gipc_potential_hessian(gipc_ctx* ctx, const gipc_scene* sc_h, const 
 /* Adjoint of one converged implicit step (x_old, v_old) -> (x_new, v_new = (x_new - x_old)/dt),
  * by implicit differentiation of grad I(x_new) = 0: with a = adj_x_new + adj_v_new / dt on free
  * vertices, solve H lambda = a (H the exact Hessian at x_new with the contacts at x_new, fixed
- * vertices filtered; modified PCG to prm_h->pcg_tol * 1e-4 relative, at most 20 prm_h->max_pcg
- * iterations), then
+ * vertices filtered; modified PCG stopped as gipc_pcg does, once r.P^-1 r < prm_h->pcg_tol times
+ * its start -- a ratio of squared norms, so 1e-20 asks for a 1e-10 smaller residual -- or after
+ * prm_h->max_pcg iterations; at a converged step H is the Hessian at a minimiser, so it is positive
+ * semidefinite on the free coordinates and PCG applies), then
  *   adj_v_old = dt M lambda                      (0 on fixed vertices)
  *   adj_x_old = M lambda - adj_v_new / dt         (adj_x_new - H lambda on fixed vertices)
  *   *adj_logE_h += -lambda . dI_elastic/dx        (= E dL/dE: Psi is linear in E at fixed nu)
@@ -499,6 +501,26 @@ gipc_status gipc_adjoint_step(gipc_ctx* ctx, const gipc_scene* sc_h, const doubl
                               const double* v_old, const gipc_step_params* prm_h, const double* adj_x_new,
                               const double* adj_v_new, double* adj_x_old, double* adj_v_old, double* adj_logE_h,
                               int* pcg_iters_h, void* stream);
+
+/* Refinement of a step of gipc_newton_step for differentiation: Newton iterations on the same
+ * incremental potential (inertia target xt = x_old + dt v_old + dt^2 g, x_old on fixed vertices)
+ * with the exact Hessian instead of the projected one.  At a minimiser that Hessian is positive
+ * semidefinite and Newton converges quadratically, so a step the projected method (linear
+ * convergence, an energy line search that cannot resolve decreases below the rounding of I)
+ * leaves at eps_d ~ 1e-6 reaches eps_polish ~ 1e-13 in a few iterations.  Each iteration:
+ * contacts at x, exact gradient and Hessian (modified PCG to prm_h->pcg_tol, at most
+ * prm_h->max_pcg iterations), the CCD step along d capped at 1 (slackness 0.1), x += alpha d.
+ *   x      float64 [3][n], in / out;  v  float64 [3][n] or NULL: out, (x - x_old) / dt
+ *   eps_polish  stop once alpha = 1 and max|d| / (l dt) <= eps_polish
+ *   max_iters   at most this many iterations;  iters_h, step_h (host, may be NULL): iterations
+ *               run and the last max|d| / (l dt)
+ * A direction that does not descend (the exact Hessian not positive definite there) ends the
+ * refinement without moving x.  Synchronises every iteration.
+ * Errors: GIPC_ERR_INVALID_ARG, GIPC_ERR_NOT_CONVERGED (eps_polish not reached; x and v hold the
+ * last iterate), GIPC_ERR_CAPACITY, GIPC_ERR_OOM, GIPC_ERR_CUDA. */
+gipc_status gipc_newton_polish(gipc_ctx* ctx, const gipc_scene* sc_h, double* x, double* v, const double* x_old,
+                               const double* v_old, const gipc_step_params* prm_h, double eps_polish, int max_iters,
+                               int* iters_h, double* step_h, void* stream);
 
 /* ------------------------------------------------------------------ profiling */
 
@@ -528,6 +550,12 @@ gipc_status gipc_profile_begin(gipc_ctx* ctx);
  * recording continues until gipc_profile_stop. */
 gipc_status gipc_profile_read(gipc_ctx* ctx, int kind, gipc_kernel_time* out_h);
 gipc_status gipc_profile_stop(gipc_ctx* ctx);
+/* Record only one launch in `every` of `kind` (0 or 1: every launch; kept across
+ * gipc_profile_begin).  Each recorded span is an event pair on the launching stream around the
+ * launch, and the pair delays the next launch by a few microseconds, so the per-iteration solver
+ * kernels are best sampled.  `launches` of gipc_profile_read then counts the recorded spans.
+ * Errors: GIPC_ERR_INVALID_ARG. */
+gipc_status gipc_profile_sampling(gipc_ctx* ctx, int kind, int every);
 
 #ifdef __cplusplus
 }

@@ -17,7 +17,8 @@ NULL_INDEX = -2147483648
 
 __all__ = ["compute_eps_x", "eval_stencils", "assemble_bsr", "pcg", "pcg_noalloc", "snh_params", "tet_rest", "eval_tets",
            "Surface", "find_contacts", "ccd_max_step", "Scene", "newton_step", "SceneBatch", "newton_step_batch",
-           "scatter_elements", "potential_derivs", "potential_hessian", "adjoint_step", "incremental_potential",
+           "scatter_elements", "potential_derivs", "potential_hessian", "adjoint_step", "newton_polish",
+           "incremental_potential",
            "IncrementalPotential", "simulate", "adjoint", "Context", "default_context", "GipcError", "FLAG_ACTIVE", "FLAG_FILTERED",
            "FLAG_MOLLIFIED", "FLAG_INVALID", "TYPE_IDS", "NULL_INDEX"]
 
@@ -117,6 +118,10 @@ class Context:
 
     def profile_stop(self):
         _abi.call("gipc_profile_stop", self._h)
+
+    def profile_sampling(self, kind, every):
+        """Record one launch in `every` of the named kind (gipc_profile_sampling)."""
+        _abi.call("gipc_profile_sampling", self._h, _abi.PROF_KINDS[kind], int(every))
 
     def close(self):
         if self._h:
@@ -546,10 +551,12 @@ def potential_hessian(scene, x, stencils, eps_x, dhat, kappa, mu, lam, scale, ct
     raise GipcError("gipc_potential_hessian", s)
 
 
-def adjoint_step(scene, x_new, x_old, v_old, adj_x_new, adj_v_new, dt, mu, lam, dhat, kappa, pcg_tol=1e-4,
-                 max_pcg=500, ctx=None, stream=None):
+def adjoint_step(scene, x_new, x_old, v_old, adj_x_new, adj_v_new, dt, mu, lam, dhat, kappa, pcg_tol=1e-20,
+                 max_pcg=20000, ctx=None, stream=None):
     """Adjoint of one converged implicit step (gipc_adjoint_step): returns
-    (dL/dx_old, dL/dv_old, E dL/dE of this step, adjoint PCG iterations)."""
+    (dL/dx_old, dL/dv_old, E dL/dE of this step, adjoint PCG iterations).  The adjoint solve stops
+    once r.P^-1 r < pcg_tol times its start (squared norms: 1e-20 is a 1e-10 smaller residual) or
+    after max_pcg iterations; GipcError if it does not reach pcg_tol."""
     ctx = ctx or default_context()
     prm = _step_params(dt, mu, lam, dhat, kappa, pcg_tol=pcg_tol, max_pcg=max_pcg)
     ax = torch.empty_like(x_new)
@@ -560,7 +567,7 @@ def adjoint_step(scene, x_new, x_old, v_old, adj_x_new, adj_v_new, dt, mu, lam, 
     st = _abi.call_status("gipc_adjoint_step", ctx.handle, ctypes.byref(sc), _ptr(x_new), _ptr(x_old), _ptr(v_old),
                           ctypes.byref(prm), _ptr(adj_x_new), _ptr(adj_v_new), _ptr(ax), _ptr(av), ctypes.byref(le),
                           ctypes.byref(it), _stream(stream))
-    if st not in (_abi.GIPC_OK, _abi.GIPC_ERR_NOT_CONVERGED):
+    if st != _abi.GIPC_OK:
         raise GipcError("gipc_adjoint_step", st)
     return ax, av, le.value, it.value
 
@@ -612,13 +619,45 @@ def incremental_potential(x, scene, xt, stencils, eps_x, dhat, kappa, mu, lam, s
     return IncrementalPotential.apply(x, args)
 
 
-def simulate(scene, x0, v0, steps, dt, mu, lam, dhat, kappa, **kw):
+def newton_polish(scene, x, v, x_old, v_old, dt, mu, lam, dhat, kappa, eps_polish=1e-13, max_iters=8,
+                  gravity=(0.0, 0.0, -9.81), d_thr_ratio=0.1, pcg_tol=1e-24, max_pcg=20000, ctx=None, stream=None):
+    """Exact-Hessian Newton refinement of a step of newton_step (gipc_newton_polish): updates x and
+    v in place; returns (iterations, last max|d| / (l dt)).  GipcError if eps_polish is not met."""
+    ctx = ctx or default_context()
+    for t, nm in ((x, "x"), (v, "v"), (x_old, "x_old"), (v_old, "v_old")):
+        _check(t, nm, torch.float64, 3)
+    prm = _step_params(dt, mu, lam, dhat, kappa, gravity=gravity, d_thr_ratio=d_thr_ratio, pcg_tol=pcg_tol,
+                       max_pcg=max_pcg)
+    it = ctypes.c_int(0)
+    step = ctypes.c_double(0.0)
+    sc = scene.struct()
+    _abi.call("gipc_newton_polish", ctx.handle, ctypes.byref(sc), _ptr(x), _ptr(v), _ptr(x_old), _ptr(v_old),
+              ctypes.byref(prm), float(eps_polish), int(max_iters), ctypes.byref(it), ctypes.byref(step),
+              _stream(stream))
+    return it.value, step.value
+
+
+_POLISH_KEYS = ("gravity", "d_thr_ratio")
+
+
+def simulate(scene, x0, v0, steps, dt, mu, lam, dhat, kappa, stats=None, polish=None, **kw):
     """Implicit steps with the state checkpointed before each step: returns (x, v, checkpoints),
-    checkpoints = [(x_t, v_t)] for t = 0 .. steps (the last one is the result)."""
+    checkpoints = [(x_t, v_t)] for t = 0 .. steps (the last one is the result).  Each step's
+    statistics are appended to `stats` when it is a list.  With `polish` (a dict of newton_polish
+    keyword arguments) every step is refined by newton_polish after newton_step, so the adjoint's
+    condition grad I(x_{t+1}) = 0 holds to that tolerance; the refinement's iteration count and
+    final step are added to the step's statistics."""
     x, v = x0.clone(), v0.clone()
     cps = [(x.clone(), v.clone())]
     for _ in range(steps):
-        newton_step(scene, x, v, dt=dt, mu=mu, lam=lam, dhat=dhat, kappa=kappa, **kw)
+        st = newton_step(scene, x, v, dt=dt, mu=mu, lam=lam, dhat=dhat, kappa=kappa, **kw)
+        if polish is not None:
+            pk = {k: kw[k] for k in _POLISH_KEYS if k in kw}
+            pk.update(polish)
+            st["polish_iters"], st["polish_step"] = newton_polish(scene, x, v, cps[-1][0], cps[-1][1], dt, mu, lam, dhat,
+                                                                  kappa, **pk)
+        if stats is not None:
+            stats.append(st)
         cps.append((x.clone(), v.clone()))
     return x, v, cps
 

@@ -113,7 +113,10 @@ SIGNATURES = {
                                       ctypes.POINTER(ElasticParams), ctypes.POINTER(Bsr), _P]),
     "gipc_adjoint_step": (_INT, [_P, ctypes.POINTER(Scene), _P, _P, _P, ctypes.POINTER(StepParams), _P, _P, _P, _P,
                                  ctypes.POINTER(_D), ctypes.POINTER(_INT), _P]),
+    "gipc_newton_polish": (_INT, [_P, ctypes.POINTER(Scene), _P, _P, _P, _P, ctypes.POINTER(StepParams), ctypes.c_double,
+                                  ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), _P]),
     "gipc_profile_begin": (_INT, [_P]),
+    "gipc_profile_sampling": (_INT, [_P, _INT, _INT]),
     "gipc_profile_read": (_INT, [_P, _INT, ctypes.POINTER(KernelTime)]),
     "gipc_profile_stop": (_INT, [_P]),
 }

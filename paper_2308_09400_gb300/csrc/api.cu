@@ -55,6 +55,13 @@ extern "C" gipc_status gipc_profile_begin(gipc_ctx* ctx) {
     return GIPC_OK;
 }
 
+extern "C" gipc_status gipc_profile_sampling(gipc_ctx* ctx, int kind, int every) {
+    if (!ctx || kind < 0 || kind >= GIPC_PROF_KINDS || every < 0)
+        return gipc::fail(GIPC_ERR_INVALID_ARG, "gipc_profile_sampling: bad arguments");
+    ctx->prof.every[kind] = every;
+    return GIPC_OK;
+}
+
 extern "C" gipc_status gipc_profile_stop(gipc_ctx* ctx) {
     if (!ctx) return gipc::fail(GIPC_ERR_INVALID_ARG, "gipc_profile_stop: null context");
     ctx->prof.on = false;

@@ -40,6 +40,9 @@ struct gipc_profiler {
     bool on = false;
     std::vector<cudaEvent_t> pool[kKinds];
     int used[kKinds] = {};
+    int every[kKinds] = {};       // record one launch in `every` (0 or 1: all)
+    unsigned seen[kKinds] = {};   // launches of the kind since profiling began
+    bool open[kKinds] = {};       // the current launch is being recorded
     cudaEvent_t take(int kind) {
         if (used[kind] == (int)pool[kind].size()) {
             cudaEvent_t e;
@@ -48,16 +51,27 @@ struct gipc_profiler {
         }
         return pool[kind][used[kind]++];
     }
-    // record a start / stop pair around one launch of `kind`
+    // record a start / stop pair around one launch of `kind` (a sampled subset, if so set)
     void start(int kind, cudaStream_t s) {
-        if (on) {
-            cudaEvent_t e = take(kind);
-            if (e) cudaEventRecord(e, s);
-        }
+        if (!on) return;
+        open[kind] = every[kind] <= 1 || seen[kind] % (unsigned)every[kind] == 0;
+        ++seen[kind];
+        if (open[kind]) record(kind, s);
     }
-    void stop(int kind, cudaStream_t s) { start(kind, s); }
+    void stop(int kind, cudaStream_t s) {
+        if (on && open[kind]) record(kind, s);
+        open[kind] = false;
+    }
+    void record(int kind, cudaStream_t s) {
+        cudaEvent_t e = take(kind);
+        if (e) cudaEventRecord(e, s);
+    }
     void reset() {
-        for (int k = 0; k < kKinds; ++k) used[k] = 0;
+        for (int k = 0; k < kKinds; ++k) {
+            used[k] = 0;
+            seen[k] = 0;
+            open[k] = false;
+        }
     }
     void release() {
         for (auto& v : pool)
@@ -78,7 +92,7 @@ struct gipc_prof_span {
 
 struct gipc_ctx {
     int device = 0;
-    static constexpr int kSlots = 64;   // assembly 0-8, pcg 9-15 and 40, contacts 16-19, 30-39 and 45-46, time step 20-29, 41-44 and 47-48, derivatives 49-57
+    static constexpr int kSlots = 64;   // assembly 0-8, pcg 9-15 and 40, contacts 16-19, 30-39 and 45-46, time step 20-29, 41-44 and 47-48, derivatives 49-58
     gipc_scratch slot[kSlots];
     gipc_profiler prof;
     void release_all() {

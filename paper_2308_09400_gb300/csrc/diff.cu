@@ -32,10 +32,13 @@ gipc_status find_contacts_impl(gipc_ctx* ctx, const double* x, const double* res
 gipc_status pcg_impl(gipc_ctx* ctx, const gipc_bsr* A, const double* rhs, double* x, const uint8_t* fixed,
                      const gipc_pcg_params* prm, int* iters_out_h, double* rel_out_h, cudaStream_t st,
                      const int64_t* voff, int nscenes, int* scene_iters_h, int* scene_status_h);
+gipc_status ccd_impl(gipc_ctx* ctx, const double* x, const double* d, int64_t n, const gipc_surface& srf, double slack,
+                     double* alpha_h, cudaStream_t st, const int32_t* vscene, int nscenes, double* amin_dev);
 
 namespace {
 
-enum DiffSlot { D_ELEM = 49, D_VEC = 50, D_RED = 51, D_CON = 52, D_HES = 53, D_ADJ = 54, D_ROW = 55, D_COL = 56, D_VAL = 57 };
+enum DiffSlot { D_ELEM = 49, D_VEC = 50, D_RED = 51, D_CON = 52, D_HES = 53, D_ADJ = 54, D_ROW = 55, D_COL = 56, D_VAL = 57,
+                D_POL = 58 };
 
 // ------------------------------------------------------------------ hyper-dual numbers
 struct HD {
@@ -341,6 +344,58 @@ __global__ void __launch_bounds__(1024) dot_kernel(const double* __restrict__ a,
     }
 }
 
+// xt = x0 + dt v0 + dt^2 g on free vertices, x0 on fixed ones (the inertia target of the step)
+__global__ void step_target_kernel(const double* __restrict__ x0, const double* __restrict__ v0,
+                                   const uint8_t* __restrict__ fixed, int64_t n, double dt, double g0, double g1,
+                                   double g2, double* __restrict__ xt) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const bool fx = fixed && fixed[i];
+    const double g[3] = {g0, g1, g2};
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const double p = x0[q * n + i];
+        xt[q * n + i] = fx ? p : __dadd_rn(__dadd_rn(p, __dmul_rn(dt, v0[q * n + i])), g[q]);
+    }
+}
+
+// rhs = -g on free vertices, 0 on fixed ones
+__global__ void neg_free_kernel(const double* __restrict__ g, const uint8_t* __restrict__ fixed, int64_t n,
+                                double* __restrict__ rhs) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= 3 * n) return;
+    rhs[j] = (fixed && fixed[j % n]) ? 0.0 : -g[j];
+}
+
+// x += alpha d;  v = (x - x0) / dt when v is given
+__global__ void step_apply_kernel(double* __restrict__ x, const double* __restrict__ d, double alpha, int64_t m) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < m) x[j] += alpha * d[j];
+}
+
+__global__ void step_velocity_kernel(const double* __restrict__ x, const double* __restrict__ x0, double dt, int64_t m,
+                                     double* __restrict__ v) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < m) v[j] = (x[j] - x0[j]) / dt;
+}
+
+// max |a[i]| into *out (one CTA)
+__global__ void __launch_bounds__(1024) maxabs_kernel(const double* __restrict__ a, int64_t m, double* __restrict__ out) {
+    __shared__ double sh[32];
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < m; i += blockDim.x) s = fmax(s, fabs(a[i]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_xor_sync(0xffffffffu, s, o));
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        s = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_xor_sync(0xffffffffu, s, o));
+        if (threadIdx.x == 0) *out = s;
+    }
+}
+
 inline unsigned nbk(int64_t w, int t) { return (unsigned)std::max<int64_t>(1, (w + t - 1) / t); }
 
 TetConst tet_const(const gipc_elastic_params& ep) {
@@ -443,6 +498,50 @@ gipc_status check_scene(const gipc_scene* sc, const char* who) {
         return fail(GIPC_ERR_INVALID_ARG, "%s: incomplete scene", who);
     return GIPC_OK;
 }
+
+// The contact list at x (compact, in the D_CON slot, grown once if it was short).
+gipc_status contacts_at(gipc_ctx* ctx, const gipc_scene& sc, const double* x, double dhat, cudaStream_t st,
+                        int32_t** sti, double** eps, int64_t* k) {
+    using namespace gipc;
+    gipc_status s;
+    if ((s = ctx->slot[D_CON].reserve(sizeof(double) * 4096 * 3)) != GIPC_OK) return s;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        const int64_t cap = (int64_t)(ctx->slot[D_CON].bytes / (4 * sizeof(int32_t) + sizeof(double)));
+        *eps = ctx->slot[D_CON].as<double>();
+        *sti = reinterpret_cast<int32_t*>(*eps + cap);
+        s = find_contacts_impl(ctx, x, sc.rest_x, sc.n, sc.surface, dhat, *sti, *eps, cap, k, true, nullptr, nullptr, st,
+                               1);
+        if (s != GIPC_ERR_CAPACITY) return s;
+        if ((s = ctx->slot[D_CON].reserve((size_t)(*k + *k / 4 + 1024) * (4 * sizeof(int32_t) + sizeof(double)))) !=
+            GIPC_OK)
+            return s;
+    }
+    return fail(GIPC_ERR_CAPACITY, "contact list still short after growing it");
+}
+
+// The exact Hessian at x into the D_ROW / D_COL / D_VAL slots (grown once if they were short).
+gipc_status exact_hessian(gipc_ctx* ctx, const gipc_scene& sc, const double* x, const int32_t* sti, const double* eps,
+                          int64_t k, const gipc_barrier_params& bp, const gipc_elastic_params& ep, gipc_bsr* H,
+                          cudaStream_t st) {
+    using namespace gipc;
+    gipc_status s;
+    *H = gipc_bsr{};
+    H->prec = GIPC_FP64;
+    if ((s = ctx->slot[D_ROW].reserve(sizeof(int32_t) * (sc.n + 1))) != GIPC_OK) return s;
+    H->rowptr = ctx->slot[D_ROW].as<int32_t>();
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        H->capacity = std::min<int64_t>((int64_t)(ctx->slot[D_COL].bytes / sizeof(int32_t)),
+                                        (int64_t)(ctx->slot[D_VAL].bytes / (9 * sizeof(double))));
+        H->colidx = ctx->slot[D_COL].as<int32_t>();
+        H->vals = ctx->slot[D_VAL].ptr;
+        s = potential_hessian_impl(ctx, sc, x, sti, eps, k, bp, ep, H, st);
+        if (s != GIPC_ERR_CAPACITY || H->nnzb <= H->capacity) return s;
+        const int64_t c2 = H->nnzb + H->nnzb / 8 + 1024;
+        if ((s = ctx->slot[D_COL].reserve(sizeof(int32_t) * c2)) != GIPC_OK) return s;
+        if ((s = ctx->slot[D_VAL].reserve(sizeof(double) * 9 * c2)) != GIPC_OK) return s;
+    }
+    return fail(GIPC_ERR_CAPACITY, "exact Hessian still short after growing it");
+}
 }  // namespace
 
 extern "C" gipc_status gipc_potential_derivs(gipc_ctx* ctx, const gipc_scene* sc, const double* x, const double* xt,
@@ -486,44 +585,15 @@ extern "C" gipc_status gipc_adjoint_step(gipc_ctx* ctx, const gipc_scene* sc, co
     (void)x_old;
     (void)v_old;
     const int64_t n = sc->n, m3 = 3 * n;
-    // contacts at x_new
-    if ((s = ctx->slot[D_CON].reserve(sizeof(double) * 4096 * 3)) != GIPC_OK) return s;
+    // contacts and the exact Hessian at x_new
+    int32_t* sti = nullptr;
+    double* eps = nullptr;
     int64_t k = 0;
-    for (int attempt = 0; attempt < 2; ++attempt) {
-        const int64_t cap = (int64_t)(ctx->slot[D_CON].bytes / (4 * sizeof(int32_t) + sizeof(double)));
-        double* eps = ctx->slot[D_CON].as<double>();
-        int32_t* sti = reinterpret_cast<int32_t*>(eps + cap);
-        s = find_contacts_impl(ctx, x_new, sc->rest_x, n, sc->surface, prm->barrier.dhat, sti, eps, cap, &k, true, nullptr,
-                               nullptr, st, 1);
-        if (s == GIPC_OK) break;
-        if (s != GIPC_ERR_CAPACITY) return s;
-        if ((s = ctx->slot[D_CON].reserve((size_t)(k + k / 4 + 1024) * (4 * sizeof(int32_t) + sizeof(double)))) != GIPC_OK)
-            return s;
-    }
-    if (s != GIPC_OK) return s;
-    const int64_t cap = (int64_t)(ctx->slot[D_CON].bytes / (4 * sizeof(int32_t) + sizeof(double)));
-    double* eps = ctx->slot[D_CON].as<double>();
-    int32_t* sti = reinterpret_cast<int32_t*>(eps + cap);
+    if ((s = contacts_at(ctx, *sc, x_new, prm->barrier.dhat, st, &sti, &eps, &k)) != GIPC_OK) return s;
     gipc_elastic_params ep = prm->elastic;
     ep.scale = prm->dt * prm->dt;
-    // exact Hessian at x_new
     gipc_bsr H{};
-    H.prec = GIPC_FP64;
-    if ((s = ctx->slot[D_ROW].reserve(sizeof(int32_t) * (n + 1))) != GIPC_OK) return s;
-    H.rowptr = ctx->slot[D_ROW].as<int32_t>();
-    for (int attempt = 0; attempt < 2; ++attempt) {
-        H.capacity = std::min<int64_t>((int64_t)(ctx->slot[D_COL].bytes / sizeof(int32_t)),
-                                       (int64_t)(ctx->slot[D_VAL].bytes / (9 * sizeof(double))));
-        H.colidx = ctx->slot[D_COL].as<int32_t>();
-        H.vals = ctx->slot[D_VAL].ptr;
-        s = potential_hessian_impl(ctx, *sc, x_new, sti, eps, k, prm->barrier, ep, &H, st);
-        if (s != GIPC_ERR_CAPACITY || H.nnzb <= H.capacity) break;
-        const int64_t c2 = H.nnzb + H.nnzb / 8 + 1024;
-        if ((s = ctx->slot[D_COL].reserve(sizeof(int32_t) * c2)) != GIPC_OK) return s;
-        if ((s = ctx->slot[D_VAL].reserve(sizeof(double) * 9 * c2)) != GIPC_OK) return s;
-        s = GIPC_ERR_CAPACITY;
-    }
-    if (s != GIPC_OK) return s;
+    if ((s = exact_hessian(ctx, *sc, x_new, sti, eps, k, prm->barrier, ep, &H, st)) != GIPC_OK) return s;
     // H lambda = a
     if ((s = ctx->slot[D_ADJ].reserve(sizeof(double) * (4 * m3 + 8))) != GIPC_OK) return s;
     double* a = ctx->slot[D_ADJ].as<double>();
@@ -533,7 +603,7 @@ extern "C" gipc_status gipc_adjoint_step(gipc_ctx* ctx, const gipc_scene* sc, co
     double* red = gel + m3;
     adjoint_rhs_kernel<<<nbk(m3, 256), 256, 0, st>>>(adj_x_new, adj_v_new, sc->fixed, n, prm->dt, a);
     cudaMemsetAsync(lam, 0, sizeof(double) * m3, st);
-    gipc_pcg_params pp{prm->pcg_tol * 1e-4, 20 * std::max(prm->max_pcg, 1), 0};
+    gipc_pcg_params pp{prm->pcg_tol, std::max(prm->max_pcg, 1), 0};
     int pit = 0;
     const gipc_status ps = pcg_impl(ctx, &H, a, lam, sc->fixed, &pp, &pit, nullptr, st, nullptr, 1, nullptr, nullptr);
     if (pcg_iters_h) *pcg_iters_h = pit;
@@ -558,4 +628,70 @@ extern "C" gipc_status gipc_adjoint_step(gipc_ctx* ctx, const gipc_scene* sc, co
     }
     if (ps == GIPC_ERR_NOT_CONVERGED) return fail(GIPC_ERR_NOT_CONVERGED, "gipc_adjoint_step: the adjoint solve did not converge");
     return check_launch("gipc_adjoint_step");
+}
+
+extern "C" gipc_status gipc_newton_polish(gipc_ctx* ctx, const gipc_scene* sc, double* x, double* v, const double* x_old,
+                                          const double* v_old, const gipc_step_params* prm, double eps_polish,
+                                          int max_iters, int* iters_h, double* step_h, void* stream) {
+    using namespace gipc;
+    cudaStream_t st = (cudaStream_t)stream;
+    gipc_status s;
+    if (!ctx || !x || !x_old || !v_old || !prm) return fail(GIPC_ERR_INVALID_ARG, "gipc_newton_polish: null argument");
+    if ((s = check_scene(sc, "gipc_newton_polish")) != GIPC_OK) return s;
+    if (!(prm->dt > 0.0) || !(prm->barrier.dhat > 0.0) || !(sc->l > 0.0) || !(eps_polish >= 0.0) || max_iters < 0)
+        return fail(GIPC_ERR_INVALID_ARG, "gipc_newton_polish: bad parameters");
+    const int64_t n = sc->n, m3 = 3 * n;
+    const double dt = prm->dt;
+    if ((s = ctx->slot[D_POL].reserve(sizeof(double) * (4 * m3 + 8))) != GIPC_OK) return s;
+    double* xt = ctx->slot[D_POL].as<double>();
+    double* g = xt + m3;
+    double* rhs = g + m3;
+    double* d = rhs + m3;
+    double* red = d + m3;
+    step_target_kernel<<<nbk(n, 256), 256, 0, st>>>(x_old, v_old, sc->fixed, n, dt, dt * dt * prm->gravity[0],
+                                                    dt * dt * prm->gravity[1], dt * dt * prm->gravity[2], xt);
+    gipc_elastic_params ep = prm->elastic;
+    ep.scale = dt * dt;
+    int it = 0;
+    double step = INFINITY;
+    bool converged = false;
+    for (; it < max_iters && !converged; ++it) {
+        int32_t* sti = nullptr;
+        double* eps = nullptr;
+        int64_t k = 0;
+        if ((s = contacts_at(ctx, *sc, x, prm->barrier.dhat, st, &sti, &eps, &k)) != GIPC_OK) return s;
+        if ((s = potential_derivs_impl(ctx, *sc, x, xt, sti, eps, k, prm->barrier, ep, nullptr, nullptr, g, nullptr, false,
+                                       st)) != GIPC_OK)
+            return s;
+        gipc_bsr H{};
+        if ((s = exact_hessian(ctx, *sc, x, sti, eps, k, prm->barrier, ep, &H, st)) != GIPC_OK) return s;
+        neg_free_kernel<<<nbk(m3, 256), 256, 0, st>>>(g, sc->fixed, n, rhs);
+        cudaMemsetAsync(d, 0, sizeof(double) * m3, st);
+        gipc_pcg_params pp{prm->pcg_tol, std::max(prm->max_pcg, 1), 0};
+        const gipc_status ps = pcg_impl(ctx, &H, rhs, d, sc->fixed, &pp, nullptr, nullptr, st, nullptr, 1, nullptr, nullptr);
+        if (ps != GIPC_OK && ps != GIPC_ERR_NOT_CONVERGED) return ps;
+        // a Newton direction of the exact Hessian descends only where that Hessian is positive
+        // definite: stop (leaving x as it is) when it does not
+        dot_kernel<<<1, 1024, 0, st>>>(g, d, m3, red);
+        maxabs_kernel<<<1, 1024, 0, st>>>(d, m3, red + 1);
+        double h[2] = {0.0, 0.0};
+        cudaMemcpyAsync(h, red, 2 * sizeof(double), cudaMemcpyDeviceToHost, st);
+        if (cudaStreamSynchronize(st) != cudaSuccess) return check_launch("gipc_newton_polish: direction");
+        if (!(h[0] < 0.0) && h[1] > 0.0) break;
+        step = h[1] / (sc->l * dt);
+        if (!(h[1] > 0.0)) {
+            converged = true;
+            break;
+        }
+        double alpha = 1.0;
+        if ((s = ccd_impl(ctx, x, d, n, sc->surface, 0.1, &alpha, st, nullptr, 1, nullptr)) != GIPC_OK) return s;
+        step_apply_kernel<<<nbk(m3, 256), 256, 0, st>>>(x, d, std::min(alpha, 1.0), m3);
+        converged = alpha >= 1.0 && step <= eps_polish;
+    }
+    if (v) step_velocity_kernel<<<nbk(m3, 256), 256, 0, st>>>(x, x_old, dt, m3, v);
+    if (iters_h) *iters_h = it;
+    if (step_h) *step_h = step;
+    if ((s = check_launch("gipc_newton_polish")) != GIPC_OK) return s;
+    if (!converged) return fail(GIPC_ERR_NOT_CONVERGED, "gipc_newton_polish: step %.3e of l dt after %d iterations", step, it);
+    return GIPC_OK;
 }

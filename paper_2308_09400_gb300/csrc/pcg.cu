@@ -43,7 +43,11 @@ namespace {
 constexpr int kPcgThreads = 256;
 constexpr int kRowsPerWarp = 10;  // row-ordered kernel: 3 lanes per row, lanes 30/31 idle
 constexpr int kSellC = 32;        // sliced kernel: rows per slice (one lane per row)
-constexpr int kVpt = 4;           // vertices per thread (pipelined) in the update / direction kernels
+constexpr int kVpt = 4;           // vertices per thread in the setup kernel
+constexpr int kUpdT = 256;        // update kernel: vertices (= threads) per tile
+constexpr int kUpdPerSm = 2;      // update kernel: resident CTAs per SM (persistent grid)
+constexpr int kFuseMaxTiles = 8;  // fused update / direction: tiles per CTA kept in shared memory
+constexpr int kDirEpt = 4;        // direction kernel: vector entries per thread
 
 enum PcgSlot { P_VEC = 9, P_PINV = 10, P_PART = 11, P_PERM = 12, P_VEC32 = 13, P_SELL = 14, P_SLICE = 15, P_SCENE = 40 };
 
@@ -55,6 +59,7 @@ struct PcgScalars {
     int iters, done, max_iter, status;
     unsigned count_a, count_b, count_0;
     unsigned scenes_done;   // batched solves: scenes that have stopped
+    unsigned bar_count, bar_gen;   // grid barrier of the fused update / direction kernel
 };
 
 // Per-scene state of a batched solve (independent systems on disjoint vertex ranges).
@@ -345,8 +350,14 @@ pcg_spmv_tma_kernel(const int32_t* __restrict__ rowptr, const int64_t* __restric
         return ok;
     };
     const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     double d = 0.0;
-    for (int64_t sl = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < nsl && !timed_out; sl += warps) {
+    // slices are longest first; a warp takes one per round, in alternating directions (round r:
+    // r * warps + wid, then r * warps + warps - 1 - wid), so long and short slices pair up and the
+    // warps finish together; every thread's set of slices is fixed, so its partial sum is too
+    for (int64_t rnd = 0; rnd * warps < nsl && !timed_out; ++rnd) {
+        const int64_t sl = rnd * warps + ((rnd & 1) ? warps - 1 - wid : wid);
+        if (sl >= nsl) continue;
         const int64_t off = slice_off[sl], Ls = slice_off[sl + 1] - off;
         const int64_t G = (Ls + U - 1) / U;
         const int64_t slot = sl * kSellC + lane;
@@ -497,7 +508,7 @@ pcg_spmv_kernel(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ 
 }
 
 // Block-Jacobi preconditioner as a per-vertex LDL^T factorisation of the diagonal block
-// H_ii (stored as l10, l20, l21, 1/d0, 1/d1, 1/d2).  Applying it by forward and back
+// H_ii, stored [6][n] (l10, l20, l21, 1/d0, 1/d1, 1/d2 of vertex v at k * n + v).  Applying it by forward and back
 // substitution makes r . P^-1 r a sum of squares y_i^2 / d_i, nonnegative by
 // construction even when H_ii is very ill-conditioned (an explicit 3x3 inverse is not
 // numerically definite there).  A missing or non-positive-definite block falls back to I.
@@ -524,18 +535,23 @@ __global__ void pcg_factor_kernel(const int32_t* __restrict__ rowptr, const int3
     const double d1 = m[4] - l10 * l10 * d0;
     const double l21 = (m[7] - l20 * l10 * d0) / d1;
     const double d2 = m[8] - l20 * l20 * d0 - l21 * l21 * d1;
-    double* F = fac + 6 * r;
+    double* F = fac + r;
     if (!(d0 > 0.0) || !(d1 > 0.0) || !(d2 > 0.0) || !isfinite(l10 + l20 + l21 + d2)) {
-        F[0] = F[1] = F[2] = 0.0;
-        F[3] = F[4] = F[5] = 1.0;
+        F[0] = F[n] = F[2 * n] = 0.0;
+        F[3 * n] = F[4 * n] = F[5 * n] = 1.0;
         return;
     }
     F[0] = l10;
-    F[1] = l20;
-    F[2] = l21;
-    F[3] = 1.0 / d0;
-    F[4] = 1.0 / d1;
-    F[5] = 1.0 / d2;
+    F[n] = l20;
+    F[2 * n] = l21;
+    F[3 * n] = 1.0 / d0;
+    F[4 * n] = 1.0 / d1;
+    F[5 * n] = 1.0 / d2;
+}
+
+__device__ __forceinline__ void load_factor(const double* __restrict__ fac, int64_t n, int64_t v, double F[6]) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) F[k] = fac[k * n + v];
 }
 
 // s = P^-1 r for one vertex; returns r . s = sum_i y_i^2 / d_i (>= 0).
@@ -551,58 +567,81 @@ __device__ __forceinline__ double precond_apply(const double* __restrict__ F, co
     return y0 * z0 + y1 * z1 + y2 * z2;
 }
 
-// x += alpha c; r -= alpha q; s = P^-1 r; delta_new = r . s; beta; termination
-// Persistent grid; each thread walks its vertices (stride apart, so loads stay coalesced) with a
-// one-deep software pipeline: the next vertex's 18 loads are in flight while the FP64 work of the
-// current one runs.  The per-thread sum runs over its vertices in index order.
-__global__ void __launch_bounds__(kPcgThreads)
+// x += alpha c; r -= alpha q; s = P^-1 r; delta_new = r . s; beta; termination.
+// Persistent CTAs walk tiles of kUpdT vertices.  A tile's 3 kUpdT entries of x, c, r, q and s are
+// read and written as flat coalesced runs and handed between the flat (axpy) and the per-vertex
+// (preconditioner) layouts through shared memory; the factors are [6][n].  The next tile's 18
+// loads per thread are issued before the current tile's FP64 work, so the FP64 pipe and HBM
+// overlap.  Each thread sums its vertices (one per tile, tiles in order) into its partial.
+__global__ void __launch_bounds__(kUpdT, kUpdPerSm)
 pcg_update_kernel(double* __restrict__ x, double* __restrict__ r, const double* __restrict__ c,
-                  const double* __restrict__ q, double* __restrict__ s, const double* __restrict__ pinv,
+                  const double* __restrict__ q, double* __restrict__ s, const double* __restrict__ fac,
                   int64_t n, double* __restrict__ part, PcgScalars* __restrict__ S) {
     if (S->done) return;
+    __shared__ double rt[3 * kUpdT], st[3 * kUpdT];
     const double alpha = S->alpha;
-    double d = 0.0;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = threadIdx.x;
+    const int64_t ntiles = (n + kUpdT - 1) / kUpdT, ne = 3 * n;
     double xv[3], cv[3], rv[3], qv[3], F[6];
-    auto load = [&](int64_t w, double* X, double* C, double* R, double* Q, double* P) {
+    auto load = [&](int64_t tl, double* X, double* C, double* R, double* Q, double* Fv) {
+        const int64_t e0 = 3 * kUpdT * tl + t;
 #pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            X[i] = x[3 * w + i];
-            C[i] = c[3 * w + i];
-            R[i] = r[3 * w + i];
-            Q[i] = q[3 * w + i];
+        for (int j = 0; j < 3; ++j) {
+            const int64_t e = e0 + j * kUpdT;
+            if (e < ne) {
+                X[j] = x[e];
+                C[j] = c[e];
+                R[j] = r[e];
+                Q[j] = q[e];
+            }
         }
-#pragma unroll
-        for (int i = 0; i < 6; ++i) P[i] = pinv[6 * w + i];
+        const int64_t v = kUpdT * tl + t;
+        if (v < n) load_factor(fac, n, v, Fv);
     };
-    if (v < n) load(v, xv, cv, rv, qv, F);
-    while (v < n) {
-        const int64_t vn = v + stride;
+    double d = 0.0;
+    int64_t tl = blockIdx.x;
+    if (tl < ntiles) load(tl, xv, cv, rv, qv, F);
+    while (tl < ntiles) {   // uniform across the CTA
+        const int64_t tn = tl + gridDim.x;
         double xn[3], cn[3], rn[3], qn[3], Fn[6];
-        if (vn < n) load(vn, xn, cn, rn, qn, Fn);
-        double sv[3];
+        if (tn < ntiles) load(tn, xn, cn, rn, qn, Fn);
+        const int64_t e0 = 3 * kUpdT * tl + t, v = kUpdT * tl + t;
 #pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            x[3 * v + i] = xv[i] + alpha * cv[i];
-            rv[i] = rv[i] - alpha * qv[i];
-            r[3 * v + i] = rv[i];
+        for (int j = 0; j < 3; ++j) {
+            const int64_t e = e0 + j * kUpdT;
+            if (e < ne) {
+                x[e] = xv[j] + alpha * cv[j];
+                const double re = rv[j] - alpha * qv[j];
+                r[e] = re;
+                rt[t + j * kUpdT] = re;
+            }
         }
-        d += precond_apply(F, rv, sv);
+        __syncthreads();
+        if (v < n) {
+            const double r3[3] = {rt[3 * t], rt[3 * t + 1], rt[3 * t + 2]};
+            double s3[3];
+            d += precond_apply(F, r3, s3);
 #pragma unroll
-        for (int i = 0; i < 3; ++i) s[3 * v + i] = sv[i];
-        if (vn < n) {
+            for (int i = 0; i < 3; ++i) st[3 * t + i] = s3[i];
+        }
+        __syncthreads();
 #pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                xv[i] = xn[i];
-                cv[i] = cn[i];
-                rv[i] = rn[i];
-                qv[i] = qn[i];
+        for (int j = 0; j < 3; ++j) {
+            const int64_t e = e0 + j * kUpdT;
+            if (e < ne) s[e] = st[t + j * kUpdT];
+        }
+        if (tn < ntiles) {
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                xv[j] = xn[j];
+                cv[j] = cn[j];
+                rv[j] = rn[j];
+                qv[j] = qn[j];
             }
 #pragma unroll
-            for (int i = 0; i < 6; ++i) F[i] = Fn[i];
+            for (int k = 0; k < 6; ++k) F[k] = Fn[k];
         }
-        v = vn;
+        tl = tn;
     }
     const double bs = block_sum(d);
     if (!publish_partial(part, bs, &S->count_b)) return;
@@ -622,6 +661,172 @@ pcg_update_kernel(double* __restrict__ x, double* __restrict__ r, const double* 
     }
 }
 
+// Fused update and direction of one solve (one launch per iteration instead of two).
+// Phase 1, per tile this CTA owns: x += alpha c; r -= alpha q; s = P^-1 r and this thread's part
+// of r.s, as in pcg_update_kernel, but s and c stay in shared memory.  A grid barrier (the grid
+// is launched cooperatively, so every CTA is resident) then lets every CTA sum the partials in
+// the same fixed order -- identical totals everywhere -- and form beta and the stopping test;
+// phase 2 writes c = S(s + beta c) (and its float32 copy) for the same tiles while the solve
+// continues.  CTA 0 records the scalars.  The arithmetic is that of the two separate kernels.
+// The barrier wait is bounded: past kBarrierCycles it sets GIPC_ERR_TIMEOUT and stops the solve.
+constexpr long long kBarrierCycles = 4000000000LL;   // ~2 s at 2 GHz
+
+__device__ __forceinline__ bool grid_barrier(PcgScalars* S) {
+    __shared__ int ok;
+    if (threadIdx.x == 0) {
+        volatile unsigned* gen = &S->bar_gen;
+        const unsigned g0 = *gen;
+        __threadfence();
+        const unsigned prev = atomicAdd(&S->bar_count, 1u);
+        ok = 1;
+        if (prev == gridDim.x - 1) {
+            S->bar_count = 0;
+            __threadfence();
+            atomicExch(&S->bar_gen, g0 + 1u);
+        } else {
+            const long long t0 = clock64();
+            while (*gen == g0) {
+                if (clock64() - t0 > kBarrierCycles) {
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+__global__ void __launch_bounds__(kUpdT, kUpdPerSm)
+pcg_update_direction_kernel(double* __restrict__ x, double* __restrict__ r, double* __restrict__ c,
+                            float* __restrict__ c32, const double* __restrict__ q, const double* __restrict__ fac,
+                            const uint8_t* __restrict__ fixed, int64_t n, double* __restrict__ part,
+                            PcgScalars* __restrict__ S) {
+    if (S->done) return;
+    extern __shared__ double keep[];   // per owned tile: s then c, flat order, 3 kUpdT each
+    __shared__ double rt[3 * kUpdT], st[3 * kUpdT];
+    // every scalar this launch reads is read here, before the barrier: CTA 0 rewrites them after it
+    const double alpha = S->alpha, delta_old = S->delta_new, tol = S->tol, delta0 = S->delta0;
+    const int iters = S->iters + 1, max_iter = S->max_iter;
+    const int t = threadIdx.x;
+    const int64_t ntiles = (n + kUpdT - 1) / kUpdT, ne = 3 * n;
+    double xv[3], cv[3], rv[3], qv[3], F[6];
+    auto load = [&](int64_t tl, double* X, double* C, double* R, double* Q, double* Fv) {
+        const int64_t e0 = 3 * kUpdT * tl + t;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const int64_t e = e0 + j * kUpdT;
+            if (e < ne) {
+                X[j] = x[e];
+                C[j] = c[e];
+                R[j] = r[e];
+                Q[j] = q[e];
+            }
+        }
+        const int64_t v = kUpdT * tl + t;
+        if (v < n) load_factor(fac, n, v, Fv);
+    };
+    double d = 0.0;
+    int64_t tl = blockIdx.x;
+    int slot = 0;
+    if (tl < ntiles) load(tl, xv, cv, rv, qv, F);
+    while (tl < ntiles) {
+        const int64_t tn = tl + gridDim.x;
+        double xn[3], cn[3], rn[3], qn[3], Fn[6];
+        if (tn < ntiles) load(tn, xn, cn, rn, qn, Fn);
+        double* ks = keep + (int64_t)slot * 6 * kUpdT;
+        const int64_t e0 = 3 * kUpdT * tl + t, v = kUpdT * tl + t;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const int64_t e = e0 + j * kUpdT;
+            if (e < ne) {
+                x[e] = xv[j] + alpha * cv[j];
+                const double re = rv[j] - alpha * qv[j];
+                r[e] = re;
+                rt[t + j * kUpdT] = re;
+                ks[3 * kUpdT + t + j * kUpdT] = cv[j];
+            }
+        }
+        __syncthreads();
+        if (v < n) {
+            const double r3[3] = {rt[3 * t], rt[3 * t + 1], rt[3 * t + 2]};
+            double s3[3];
+            d += precond_apply(F, r3, s3);
+#pragma unroll
+            for (int i = 0; i < 3; ++i) st[3 * t + i] = s3[i];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < 3; ++j) ks[t + j * kUpdT] = st[t + j * kUpdT];
+        if (tn < ntiles) {
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                xv[j] = xn[j];
+                cv[j] = cn[j];
+                rv[j] = rn[j];
+                qv[j] = qn[j];
+            }
+#pragma unroll
+            for (int k = 0; k < 6; ++k) F[k] = Fn[k];
+        }
+        tl = tn;
+        ++slot;
+    }
+    const double bs = block_sum(d);
+    if (t == 0) part[blockIdx.x] = bs;
+    if (!grid_barrier(S)) {
+        if (t == 0) {
+            S->status = GIPC_ERR_TIMEOUT;
+            S->done = 1;
+        }
+        return;
+    }
+    __shared__ double dn_sh;
+    const double tot = sum_partials(part, gridDim.x);
+    if (t == 0) dn_sh = tot;
+    __syncthreads();
+    const double dn = dn_sh;
+    const double beta = dn / delta_old;
+    int status = GIPC_OK, done = 0;
+    if (!isfinite(dn) || !isfinite(alpha)) {
+        status = GIPC_ERR_NONFINITE;
+        done = 1;
+    } else if (!(dn > 0.0) || dn < tol * delta0 || iters >= max_iter) {
+        done = 1;
+    }
+    if (!done) {
+        slot = 0;
+        for (int64_t tl2 = blockIdx.x; tl2 < ntiles; tl2 += gridDim.x, ++slot) {
+            const double* ks = keep + (int64_t)slot * 6 * kUpdT;
+            const int64_t e0 = 3 * kUpdT * tl2 + t;
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                const int64_t e = e0 + j * kUpdT;
+                if (e < ne) {
+                    const bool fx = fixed && fixed[e / 3];
+                    const double ce = fx ? 0.0 : ks[t + j * kUpdT] + beta * ks[3 * kUpdT + t + j * kUpdT];
+                    c[e] = ce;
+                    if (c32) c32[e] = (float)ce;
+                }
+            }
+        }
+    }
+    if (blockIdx.x == 0 && t == 0) {
+        S->delta_old = delta_old;
+        S->delta_new = dn;
+        S->beta = beta;
+        S->iters = iters;
+        if (S->status != GIPC_ERR_TIMEOUT) {
+            S->status = status;
+            S->done = done;
+        }
+    }
+}
+
+// c = S(s + beta c) and its float32 copy, over the flat [3n] vectors with kDirEpt coalesced
+// entries per thread.
 __global__ void __launch_bounds__(kPcgThreads)
 pcg_direction_kernel(double* __restrict__ c, float* __restrict__ c32, const double* __restrict__ s,
                      const uint8_t* __restrict__ fixed, int64_t n, const PcgScalars* __restrict__ S) {
@@ -629,45 +834,28 @@ pcg_direction_kernel(double* __restrict__ c, float* __restrict__ c32, const doub
     // only while the solve continues
     if (S->done) return;
     const double beta = S->beta;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    double sv[3], cv[3];
-    bool fx = false;
-    if (v < n) {
-        fx = fixed && fixed[v];
+    const int64_t ne = 3 * n;
+    const int64_t e0 = (int64_t)blockIdx.x * (kPcgThreads * kDirEpt) + threadIdx.x;
+    double sv[kDirEpt], cv[kDirEpt];
+    bool fx[kDirEpt];
 #pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            sv[i] = s[3 * v + i];
-            cv[i] = c[3 * v + i];
+    for (int j = 0; j < kDirEpt; ++j) {
+        const int64_t e = e0 + j * kPcgThreads;
+        fx[j] = false;
+        if (e < ne) {
+            sv[j] = s[e];
+            cv[j] = c[e];
+            fx[j] = fixed && fixed[e / 3];
         }
     }
-    while (v < n) {   // one-deep software pipeline, as in the update
-        const int64_t vn = v + stride;
-        double sn[3], cn[3];
-        bool fn = false;
-        if (vn < n) {
-            fn = fixed && fixed[vn];
 #pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                sn[i] = s[3 * vn + i];
-                cn[i] = c[3 * vn + i];
-            }
+    for (int j = 0; j < kDirEpt; ++j) {
+        const int64_t e = e0 + j * kPcgThreads;
+        if (e < ne) {
+            const double ce = fx[j] ? 0.0 : sv[j] + beta * cv[j];
+            c[e] = ce;
+            if (c32) c32[e] = (float)ce;
         }
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            const double ce = fx ? 0.0 : sv[i] + beta * cv[i];
-            c[3 * v + i] = ce;
-            if (c32) c32[3 * v + i] = (float)ce;
-        }
-        if (vn < n) {
-#pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                sv[i] = sn[i];
-                cv[i] = cn[i];
-            }
-            fx = fn;
-        }
-        v = vn;
     }
 }
 
@@ -695,6 +883,7 @@ __global__ void __launch_bounds__(kPcgThreads)
 pcg_init_kernel(const double* __restrict__ b, const double* __restrict__ q, double* __restrict__ r,
                 double* __restrict__ s, double* __restrict__ c, float* __restrict__ c32, const double* __restrict__ pinv,
                 const uint8_t* __restrict__ fixed, int64_t n, double* __restrict__ part, PcgScalars* __restrict__ S) {
+    const int64_t ldf = n;
     double d = 0.0;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
         const bool fx = fixed && fixed[v];
@@ -705,7 +894,9 @@ pcg_init_kernel(const double* __restrict__ b, const double* __restrict__ q, doub
             r[3 * v + i] = rv[i];
         }
         double sv[3];
-        d += precond_apply(pinv + 6 * v, rv, sv);
+        double F[6];
+        load_factor(pinv, ldf, v, F);
+        d += precond_apply(F, rv, sv);
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
             s[3 * v + i] = sv[i];
@@ -735,6 +926,7 @@ __global__ void pcg_set_scalars(PcgScalars* S, double tol, int max_iter) {
     S->status = GIPC_OK;
     S->count_a = S->count_b = S->count_0 = 0;
     S->scenes_done = 0;
+    S->bar_count = S->bar_gen = 0;
 }
 
 // ---- batched solves: one CTA per scene for everything but the product ---------------------
@@ -761,8 +953,9 @@ __device__ __forceinline__ void scene_stop(SceneScalars* SS, PcgScalars* S, int 
 __global__ void __launch_bounds__(kPcgThreads)
 pcg_scene_init_kernel(const double* __restrict__ b, const double* __restrict__ q, double* __restrict__ r,
                       double* __restrict__ s, double* __restrict__ c, float* __restrict__ c32,
-                      const double* __restrict__ pinv, const uint8_t* __restrict__ fixed, const int64_t* __restrict__ voff,
-                      int nscenes, SceneScalars* __restrict__ SS, PcgScalars* __restrict__ S) {
+                      const double* __restrict__ pinv, int64_t ldf, const uint8_t* __restrict__ fixed,
+                      const int64_t* __restrict__ voff, int nscenes, SceneScalars* __restrict__ SS,
+                      PcgScalars* __restrict__ S) {
     const int sc = blockIdx.x;
     const int64_t v0 = voff[sc], v1 = voff[sc + 1];
     double d = 0.0;
@@ -774,7 +967,9 @@ pcg_scene_init_kernel(const double* __restrict__ b, const double* __restrict__ q
             rv[i] = fx ? 0.0 : b[3 * v + i] - q[3 * v + i];
             r[3 * v + i] = rv[i];
         }
-        d += precond_apply(pinv + 6 * v, rv, sv);
+        double F[6];
+        load_factor(pinv, ldf, v, F);
+        d += precond_apply(F, rv, sv);
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
             s[3 * v + i] = sv[i];
@@ -798,7 +993,7 @@ pcg_scene_init_kernel(const double* __restrict__ b, const double* __restrict__ q
 __global__ void __launch_bounds__(kPcgThreads)
 pcg_scene_step_kernel(double* __restrict__ x, double* __restrict__ r, double* __restrict__ c, float* __restrict__ c32,
                       const double* __restrict__ q, double* __restrict__ s, const double* __restrict__ pinv,
-                      const uint8_t* __restrict__ fixed, const int64_t* __restrict__ voff, int nscenes,
+                      int64_t ldf, const uint8_t* __restrict__ fixed, const int64_t* __restrict__ voff, int nscenes,
                       SceneScalars* __restrict__ SS, PcgScalars* __restrict__ S) {
     const int sc = blockIdx.x;
     if (SS[sc].done) return;
@@ -817,7 +1012,9 @@ pcg_scene_step_kernel(double* __restrict__ x, double* __restrict__ r, double* __
             rv[i] = r[3 * v + i] - alpha * q[3 * v + i];
             r[3 * v + i] = rv[i];
         }
-        d += precond_apply(pinv + 6 * v, rv, sv);
+        double F[6];
+        load_factor(pinv, ldf, v, F);
+        d += precond_apply(F, rv, sv);
 #pragma unroll
         for (int i = 0; i < 3; ++i) s[3 * v + i] = sv[i];
     }
@@ -855,6 +1052,53 @@ inline unsigned spmv_blocks(int64_t n) {
     return (unsigned)((warps * 32 + kPcgThreads - 1) / kPcgThreads);
 }
 
+inline unsigned upd_blocks(int64_t n) {
+    const int64_t tiles = (n + kUpdT - 1) / kUpdT;
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(tiles, 152 * kUpdPerSm));
+}
+
+inline unsigned dir_blocks(int64_t n) {
+    const int64_t per = (int64_t)kPcgThreads * kDirEpt;
+    return (unsigned)(n > 0 ? (3 * n + per - 1) / per : 1);
+}
+
+// Launch shape of the fused update / direction kernel, or ok = false when it does not apply (the
+// owned tiles would not fit in shared memory, or the grid would not be resident all at once).
+struct FusePlan {
+    bool ok = false;
+    unsigned grid = 0;
+    size_t smem = 0;
+};
+
+inline FusePlan plan_fused(int64_t n) {
+    FusePlan p;
+    int dev = 0, sms = 0, coop = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return p;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return p;
+    if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return p;
+    const int64_t ntiles = (n + kUpdT - 1) / kUpdT;
+    if (ntiles < 1) return p;
+    const int64_t grid = std::min<int64_t>(ntiles, (int64_t)sms * kUpdPerSm);
+    const int64_t tpc = (ntiles + grid - 1) / grid;
+    if (tpc > kFuseMaxTiles) return p;
+    const size_t smem = (size_t)tpc * 6 * kUpdT * sizeof(double);
+    static bool attr_set = false;
+    if (!attr_set) {
+        if (cudaFuncSetAttribute(pcg_update_direction_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(kFuseMaxTiles * 6 * kUpdT * sizeof(double))) != cudaSuccess)
+            return p;
+        attr_set = true;
+    }
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pcg_update_direction_kernel, kUpdT, smem) != cudaSuccess)
+        return p;
+    if ((int64_t)per_sm * sms < grid) return p;
+    p.ok = true;
+    p.grid = (unsigned)grid;
+    p.smem = smem;
+    return p;
+}
+
 inline unsigned vec_blocks(int64_t n) {
     int64_t b = (n + (int64_t)kPcgThreads * kVpt - 1) / ((int64_t)kPcgThreads * kVpt);
     if (b > 152 * 8) b = 152 * 8;
@@ -886,8 +1130,9 @@ gipc_status pcg_impl(gipc_ctx* ctx, const gipc_bsr* A, const double* rhs, double
         return fail(GIPC_ERR_INVALID_ARG, "gipc_pcg: null vector or matrix pointer");
     gipc_status s;
     const int64_t nvec = 3 * n;
-    const unsigned vb = vec_blocks(n), sb = spmv_blocks(n);
-    const unsigned maxb = sb > vb ? sb : vb;
+    const unsigned vb = vec_blocks(n), sb = spmv_blocks(n), ub = upd_blocks(n), db = dir_blocks(n);
+    const FusePlan fuse = voff ? FusePlan{} : plan_fused(n);
+    const unsigned maxb = std::max(std::max(std::max(sb, vb), ub), fuse.grid);
     if ((s = ctx->slot[P_VEC].reserve(sizeof(double) * 6 * nvec)) != GIPC_OK) return s;
     if ((s = ctx->slot[P_PINV].reserve(sizeof(double) * 6 * n)) != GIPC_OK) return s;
     if ((s = ctx->slot[P_PART].reserve(sizeof(double) * (maxb + 8) + sizeof(PcgScalars) + 64)) != GIPC_OK) return s;
@@ -948,7 +1193,7 @@ gipc_status pcg_impl(gipc_ctx* ctx, const gipc_bsr* A, const double* rhs, double
     if (voff) {
         if ((s = ctx->slot[P_SCENE].reserve(sizeof(SceneScalars) * (nscenes + 1))) != GIPC_OK) return s;
         SS = ctx->slot[P_SCENE].as<SceneScalars>();
-        pcg_scene_init_kernel<<<nscenes, kPcgThreads, 0, st>>>(b, q, r, sv, c, c32, pinv, fixed, voff, nscenes, SS, S);
+        pcg_scene_init_kernel<<<nscenes, kPcgThreads, 0, st>>>(b, q, r, sv, c, c32, pinv, n, fixed, voff, nscenes, SS, S);
     } else {
         pcg_init_kernel<<<vb, kPcgThreads, 0, st>>>(b, q, r, sv, c, c32, pinv, fixed, n, part, S);
     }
@@ -970,16 +1215,26 @@ gipc_status pcg_impl(gipc_ctx* ctx, const gipc_bsr* A, const double* rhs, double
             ctx->prof.stop(GIPC_PROF_PCG_SPMV, st);
             if (voff) {
                 ctx->prof.start(GIPC_PROF_PCG_UPDATE, st);
-                pcg_scene_step_kernel<<<nscenes, kPcgThreads, 0, st>>>(xv, r, c, c32, q, sv, pinv, fixed, voff, nscenes,
-                                                                       SS, S);
+                pcg_scene_step_kernel<<<nscenes, kPcgThreads, 0, st>>>(xv, r, c, c32, q, sv, pinv, n, fixed, voff,
+                                                                       nscenes, SS, S);
                 ctx->prof.stop(GIPC_PROF_PCG_UPDATE, st);
                 continue;
             }
             ctx->prof.start(GIPC_PROF_PCG_UPDATE, st);
-            pcg_update_kernel<<<vb, kPcgThreads, 0, st>>>(xv, r, c, q, sv, pinv, n, part, S);
+            if (fuse.ok) {
+                int64_t n_arg = n;
+                const uint8_t* fixed_arg = fixed;
+                void* args[] = {&xv, &r, &c, &c32, &q, &pinv, &fixed_arg, &n_arg, &part, &S};
+                if (cudaLaunchCooperativeKernel((const void*)pcg_update_direction_kernel, dim3(fuse.grid), dim3(kUpdT), args,
+                                                fuse.smem, st) != cudaSuccess)
+                    return check_launch("gipc_pcg: fused update");
+                ctx->prof.stop(GIPC_PROF_PCG_UPDATE, st);
+                continue;
+            }
+            pcg_update_kernel<<<ub, kUpdT, 0, st>>>(xv, r, c, q, sv, pinv, n, part, S);
             ctx->prof.stop(GIPC_PROF_PCG_UPDATE, st);
             ctx->prof.start(GIPC_PROF_PCG_DIRECTION, st);
-            pcg_direction_kernel<<<vb, kPcgThreads, 0, st>>>(c, c32, sv, fixed, n, S);
+            pcg_direction_kernel<<<db, kPcgThreads, 0, st>>>(c, c32, sv, fixed, n, S);
             ctx->prof.stop(GIPC_PROF_PCG_DIRECTION, st);
         }
         launched += m;
@@ -1050,7 +1305,8 @@ constexpr int64_t kNoAllocMaxN = GIPC_PCG_NOALLOC_MAX_N;
 constexpr size_t na_align(size_t b) { return (b + 255) / 256 * 256; }
 constexpr int64_t kNaChunks = (kNoAllocMaxN + kPermChunk - 1) / kPermChunk;
 constexpr int64_t kNaCounts = (int64_t)kLenBuckets * kNaChunks;
-constexpr int kNaMaxBlocks = 152 * 8 + 16;  // >= spmv and vector grids for n <= kNoAllocMaxN
+constexpr int kNaMaxBlocks = 152 * 8 + 16;  // >= spmv, vector and update grids for n <= kNoAllocMaxN
+static_assert((kNoAllocMaxN + kUpdT - 1) / kUpdT <= kNaMaxBlocks, "update grid must fit the partials");
 // region sizes (bytes), each 256-byte aligned
 constexpr size_t kNaVec = na_align(sizeof(double) * 18 * kNoAllocMaxN);        // b, x, r, s, c, q
 constexpr size_t kNaFac = na_align(sizeof(double) * 6 * kNoAllocMaxN);         // LDL^T factors
@@ -1124,7 +1380,7 @@ extern "C" gipc_status gipc_pcg_noalloc(const gipc_bsr* A, const double* rhs, do
     if (s != GIPC_OK) return s;
 
     const int64_t nvec = 3 * n;
-    const unsigned vb = vec_blocks(n), sb = spmv_blocks(n);
+    const unsigned vb = vec_blocks(n), sb = spmv_blocks(n), ub = upd_blocks(n), db = dir_blocks(n);
     double* V = reinterpret_cast<double*>(base);
     double *b = V, *xv = V + nvec, *r = V + 2 * nvec, *sv = V + 3 * nvec, *c = V + 4 * nvec, *q = V + 5 * nvec;
     double* pinv = reinterpret_cast<double*>(base + kNaVec);
@@ -1167,8 +1423,8 @@ extern "C" gipc_status gipc_pcg_noalloc(const gipc_bsr* A, const double* rhs, do
         for (int it = 0; it < m; ++it) {
             if (f64) pcg_spmv_kernel<double, double><<<sb, kPcgThreads, 0, st>>>(A->rowptr, A->colidx, (const double*)A->vals, c, c, perm, q, fixed, n, part, S);
             else pcg_spmv_kernel<float, float><<<sb, kPcgThreads, 0, st>>>(A->rowptr, A->colidx, (const float*)A->vals, c32, c, perm, q, fixed, n, part, S);
-            pcg_update_kernel<<<vb, kPcgThreads, 0, st>>>(xv, r, c, q, sv, pinv, n, part, S);
-            pcg_direction_kernel<<<vb, kPcgThreads, 0, st>>>(c, c32, sv, fixed, n, S);
+            pcg_update_kernel<<<ub, kUpdT, 0, st>>>(xv, r, c, q, sv, pinv, n, part, S);
+            pcg_direction_kernel<<<db, kPcgThreads, 0, st>>>(c, c32, sv, fixed, n, S);
         }
         launched += m;
         if ((s = check_launch("gipc_pcg_noalloc: iteration")) != GIPC_OK) return s;

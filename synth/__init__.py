@@ -323,7 +323,7 @@ def batch_stencils(k, seed=20230810, mix=DEFAULT_MIX, dhat=UNIT_DHAT):
 
 
 # ----------------------------------------------------------------------------- two-sheet index space
-def sheet_index_space(k, seed=20230811, side=388, radius=0, mix=DEFAULT_MIX):
+def sheet_index_space(k, seed=20230811, side=388, radius=0, mix=DEFAULT_MIX, ordered=True):
     """Stencil tuples over two triangulated side x side vertex grids (ids [0, 2 side^2)).
 
     Each stencil couples a primitive of one sheet with a primitive of the other
@@ -331,6 +331,9 @@ def sheet_index_space(k, seed=20230811, side=388, radius=0, mix=DEFAULT_MIX):
     triangle as its type needs), so the index pattern is that of two sheets in
     contact.  Used for assembly and SpMV workloads; the block values come from
     the own-vertex geometry of ``batch_stencils`` with the same type counts.
+    With ``ordered`` the stencils of each type follow their cells in row-major
+    order, the order in which a broad phase that walks the primitives emits them;
+    otherwise they are in random order.
     Returns (4, k) int32 tuples (same type order as ``type_counts``) and n.
     """
     rng = np.random.default_rng(seed)
@@ -371,6 +374,9 @@ def sheet_index_space(k, seed=20230811, side=388, radius=0, mix=DEFAULT_MIX):
         if cnt == 0:
             continue
         i, j = cells(cnt)
+        if ordered:
+            o = np.lexsort((j, i))
+            i, j = i[o], j[o]
         pi, pj = partner(i, j)
         sa = rng.integers(0, 2, cnt)
         sb = 1 - sa
@@ -576,6 +582,41 @@ def sphere_grid(nx=8, ny=8, radius=0.1, cells=14, gap=1e-3, floor_cells=64, jitt
     l = float(np.linalg.norm(x.max(axis=1) - x.min(axis=1)))
     return {"x": x, "v": np.zeros((3, n)), "tets": tets, "fixed": fixed, "tris": tris, "edges": edges,
             "verts": verts, "l": l}
+
+
+def beam_on_plate(beam=(41, 11, 11), plate=(65, 65, 4), beam_cell=0.025, plate_side=2.0, turn=0.3,
+                  gap_frac=0.5, velocity=(0.05, 0.0, -0.1)):
+    """A tet-meshed beam (vertex grid `beam`, cell `beam_cell`: 41 x 11 x 11 is 1.0 x 0.25 x 0.25)
+    turned by `turn` rad about z and lying `gap_frac` dhat above a tet-meshed plate (vertex grid
+    `plate` over a square of side `plate_side`, same cell height as width) whose bottom layer is
+    fixed; dhat = 1e-3 l.  The turn keeps the two grids out of alignment.  The beam moves at
+    `velocity`.  Returns the same dict as two_cubes plus "dhat"."""
+    px, pt = tet_box(*plate, spacing=1.0)
+    px = px.copy()
+    hp = plate_side / (plate[0] - 1)
+    px[0] = -plate_side / 2 + px[0] * hp
+    px[1] = -plate_side / 2 + px[1] * (plate_side / (plate[1] - 1))
+    px[2] = -(plate[2] - 1) * hp + px[2] * hp
+    bx, bt = tet_box(*beam, spacing=beam_cell)
+    bx = bx.copy()
+    bx -= ((np.array(beam) - 1) * beam_cell / 2.0)[:, None]
+    c, s_ = np.cos(turn), np.sin(turn)
+    bx[0], bx[1] = c * bx[0] - s_ * bx[1], s_ * bx[0] + c * bx[1]
+    bx[2] -= bx[2].min()
+    lo = np.minimum(px.min(axis=1), bx.min(axis=1))
+    hi = np.maximum(px.max(axis=1), bx.max(axis=1))
+    dhat = 1e-3 * float(np.linalg.norm(hi - lo))
+    bx[2] += gap_frac * dhat
+    x, tets = _merge([(bx, bt), (px, pt)])
+    n, nb = x.shape[1], bx.shape[1]
+    v = np.zeros((3, n))
+    v[:, :nb] = np.asarray(velocity, float)[:, None]
+    fixed = np.zeros(n, np.uint8)
+    fixed[nb:][px[2] <= px[2].min() + 1e-12] = 1
+    tris, edges, verts = surface_lists(x, tets)
+    l = float(np.linalg.norm(x.max(axis=1) - x.min(axis=1)))
+    return {"x": x, "v": v, "tets": tets, "fixed": fixed, "tris": tris, "edges": edges, "verts": verts, "l": l,
+            "dhat": 1e-3 * l}
 
 
 def stack_scene(rng, n_bodies, target_verts, dhat, size=0.2):
