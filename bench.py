@@ -40,12 +40,14 @@ PROF_EVERY = 8                     # per-iteration solver kernels: one CUDA-even
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gipc", choices=["gipc", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--hess-mode", default="dense", choices=["dense", "rank1"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--product", default="native", choices=["native", "float_pair"],
+                    help="arithmetic of the solver's H c for FP64 matrices (the headline uses native)")
     ap.add_argument("--newton-steps", type=int, default=4,
                     help="implicit time steps of the sphere-grid scene per precision (0: skip)")
     ap.add_argument("--batch-steps", type=int, default=3,
@@ -94,7 +96,7 @@ class ClockSampler:
                  "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                  "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
-                                          "-lms", "200", "-f", self.path],
+                                          "-lms", "100", "-f", self.path],
                                          stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -148,7 +150,8 @@ def gpu_step(g, dev, W, args, bufs, ctx):
     bufs["bsr"] = {"rowptr": A["rowptr"], "colidx": A["colidx"], "vals": A["vals"], "grad": A["grad"]}
     marks[2].record()
     torch.neg(A["grad"], out=bufs["rhs"])
-    d, k, rel = g.pcg(A, bufs["rhs"], rel_tol=0.0, max_iter=PCG_ITERS, ctx=ctx)
+    d, k, rel = g.pcg(A, bufs["rhs"], rel_tol=0.0, max_iter=PCG_ITERS, ctx=ctx,
+                      product=getattr(args, "product", "native"))
     marks[3].record()
     return d, A, marks
 
@@ -318,6 +321,8 @@ def run_gpu(args):
             "gpu_launches": launches_per_step(n) * args.steps,
             "clocks": clk,
         }
+        if args.precision == "fp64" and args.hess_mode == "dense" and args.product == "native":
+            line["float_pair_product"] = run_float_pair(g, dev, W, args, bufs, ctx, d, bytes_l, hbm)
         if args.newton_steps > 0:
             line["newton"] = run_newton(g, dev, ctx, args.newton_steps, args.c2_steps)
         if args.batch_steps > 0:
@@ -329,6 +334,37 @@ def run_gpu(args):
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_float_pair(g, dev, W, args, bufs, ctx, d_native, bytes_l, hbm):
+    """The same C1 step with the solver's H c in double-float arithmetic (gipc_product
+    GIPC_PRODUCT_FLOAT_PAIR): time per step, the SpMV against the HBM roof (same bytes as FP64),
+    and the Newton direction's deviation from the native FP64 result after the same iterations."""
+    import argparse
+    import torch
+    a2 = argparse.Namespace(**dict(vars(args), product="float_pair"))
+    for _ in range(2):
+        d2, _, _ = gpu_step(g, dev, W, a2, bufs, ctx)
+    torch.cuda.synchronize()
+    ctx.profile_begin()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        d2, _, _ = gpu_step(g, dev, W, a2, bufs, ctx)
+    e1.record()
+    torch.cuda.synchronize()
+    prof = ctx.profile_read()
+    ctx.profile_stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    spmv_n, spmv_ms = prof["pcg_spmv"]
+    avg = spmv_ms / max(spmv_n, 1) * 1e-3
+    dev_rel = ((d2 - d_native).abs().max() / d_native.abs().max()).item()
+    return {"ms_per_step": ms, "stencils_per_s": K_STENCILS / (ms * 1e-3),
+            "spmv_us": avg * 1e6, "spmv_hbm_frac": bytes_l / avg / 1e9 / hbm,
+            "kernel": "pcg_spmv_tma_kernel<fpair, fpair, 2, 16, 2>",
+            "direction_max_rel_dev_from_native": dev_rel,
+            "note": "FP64 matrix and vectors; H c products and sums as float32 pairs (about 2^-44 relative "
+                    "per row); not the headline"}
 
 
 # ----------------------------------------------------------------------------- Newton iterations/s

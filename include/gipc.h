@@ -247,10 +247,24 @@ gipc_status gipc_assemble_bsr(gipc_ctx* ctx, int64_t n, const gipc_elements* ste
 
 /* ------------------------------------------------------------------ solver */
 
+/* Arithmetic of the matrix-vector product H c inside the solver (FP64 matrices; ignored for
+ * GIPC_MIXED matrices, batched solves and gipc_pcg_noalloc, which use the native form). */
+typedef enum {
+    GIPC_PRODUCT_NATIVE = 0,      /* FP64 products and sums                                          */
+    GIPC_PRODUCT_FLOAT_PAIR = 1   /* each FP64 value of H and c split once into two float32 (x = hi +
+                                   * lo), products and sums in double-float arithmetic (Dekker's exact
+                                   * product, Knuth's TwoSum) on the FP32 pipe, the row result rounded to
+                                   * FP64: about 2^-44 relative per row instead of 2^-52, the same bytes,
+                                   * a fraction of the FP64 instructions.  Values below ~1e-30 in
+                                   * magnitude lose their low part (float32 range).                    */
+} gipc_product;
+
 typedef struct {
     double rel_tol;    /* stop when delta_new < rel_tol * delta_0 (paper Sec. 8: 1e-4); 0 runs max_iter */
     int max_iter;      /* iteration cap (>= 0)                                                        */
     int check_every;   /* host checks for convergence every this many iterations; 0 = automatic       */
+    int product;       /* gipc_product of H c (0: native)                                              */
+    int reserved;      /* 0                                                                            */
 } gipc_pcg_params;
 
 /* Solve H x = rhs by modified PCG with a 3x3 block-Jacobi preconditioner

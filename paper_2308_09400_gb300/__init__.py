@@ -208,12 +208,13 @@ def _bsr_struct(A):
 
 
 def pcg(A, rhs, x0=None, fixed=None, rel_tol=1e-4, max_iter=1000, check_every=0, raise_on_nonconvergence=False,
-        ctx=None, stream=None):
+        product="native", ctx=None, stream=None):
     """Modified block-Jacobi PCG on an assembled BSR (gipc_pcg).
 
     ``A`` is the dict returned by ``assemble_bsr``; ``rhs`` float64 [3, n].  Returns
     (x [3, n], iterations, delta_new / delta_0).  A capped solve with rel_tol > 0
-    returns its last iterate unless ``raise_on_nonconvergence``.
+    returns its last iterate unless ``raise_on_nonconvergence``.  ``product`` selects the
+    arithmetic of H c for FP64 matrices: "native" or "float_pair" (gipc_product).
     """
     ctx = ctx or default_context()
     n = A["n"]
@@ -222,7 +223,8 @@ def pcg(A, rhs, x0=None, fixed=None, rel_tol=1e-4, max_iter=1000, check_every=0,
     if fixed is not None:
         _check(fixed, "fixed", torch.uint8)
     bsr = _bsr_struct(A)
-    prm = _abi.PcgParams(float(rel_tol), int(max_iter), int(check_every))
+    prm = _abi.PcgParams(float(rel_tol), int(max_iter), int(check_every),
+                         {"native": _abi.GIPC_PRODUCT_NATIVE, "float_pair": _abi.GIPC_PRODUCT_FLOAT_PAIR}[product])
     iters = ctypes.c_int(0)
     rel = ctypes.c_double(0.0)
     st = _abi.call_status("gipc_pcg", ctx.handle, ctypes.byref(bsr), _ptr(rhs), _ptr(x), _ptr(fixed),

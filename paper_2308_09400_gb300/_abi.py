@@ -15,6 +15,7 @@ STATUS_NAMES = {0: "GIPC_OK", -1: "GIPC_ERR_INVALID_ARG", -2: "GIPC_ERR_CUDA", -
 
 GIPC_FP64, GIPC_MIXED = 0, 1
 GIPC_HESS_DENSE, GIPC_HESS_RANK1 = 0, 1
+GIPC_PRODUCT_NATIVE, GIPC_PRODUCT_FLOAT_PAIR = 0, 1
 
 FLAG_ACTIVE, FLAG_FILTERED, FLAG_MOLLIFIED, FLAG_INVALID = 0x01, 0x02, 0x04, 0x80
 
@@ -39,7 +40,8 @@ class ElasticParams(ctypes.Structure):
 
 
 class PcgParams(ctypes.Structure):
-    _fields_ = [("rel_tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("check_every", ctypes.c_int)]
+    _fields_ = [("rel_tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("check_every", ctypes.c_int),
+                ("product", ctypes.c_int), ("reserved", ctypes.c_int)]
 
 
 class Surface(ctypes.Structure):

@@ -111,6 +111,60 @@ __device__ __forceinline__ double sum_partials(const double* part, int count) {
     return block_sum(s);
 }
 
+// Double-float numbers for the float-pair product: x = hi + lo with two float32 (|lo| <= half an
+// ulp of hi).  Products use Dekker's exact float product (the FMA gives the rounding error of
+// hi * hi), sums Knuth's TwoSum; every operation is an explicitly rounded float32 intrinsic, so
+// the compiler cannot contract or reorder it.
+struct __align__(8) fpair {
+    float hi, lo;
+    __device__ fpair(float h = 0.0f, float l = 0.0f) : hi(h), lo(l) {}
+    __device__ explicit operator double() const { return (double)hi + (double)lo; }
+};
+
+__device__ __forceinline__ fpair two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return fpair(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb)));
+}
+
+__device__ __forceinline__ fpair fast_two_sum(float a, float b) {   // |a| >= |b| or a == 0
+    const float s = __fadd_rn(a, b);
+    return fpair(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+
+__device__ __forceinline__ fpair operator+(fpair a, fpair b) {
+    const fpair s = two_sum(a.hi, b.hi);
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+
+__device__ __forceinline__ fpair split_double(double x) {
+    const float h = __double2float_rn(x);
+    return fpair(h, __double2float_rn(x - (double)h));
+}
+
+// c + a b in each arithmetic (the generic product code calls these)
+__device__ __forceinline__ double mac(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float mac(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ fpair mac(fpair a, fpair b, fpair c) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    const float e = __fmaf_rn(a.hi, b.hi, -p);                                 // a.hi b.hi = p + e exactly
+    const float t = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e));            // a.lo b.lo (~2^-48) dropped
+    const fpair s = two_sum(c.hi, p);
+    return fast_two_sum(s.hi, __fadd_rn(c.lo, __fadd_rn(s.lo, t)));
+}
+
+__device__ __forceinline__ double ldg_(const double* p) { return __ldg(p); }
+__device__ __forceinline__ float ldg_(const float* p) { return __ldg(p); }
+__device__ __forceinline__ fpair ldg_(const fpair* p) {
+    const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+    return fpair(v.x, v.y);
+}
+
+// matrix values as the product stores them
+__device__ __forceinline__ void store_val(double* d, double v) { *d = v; }
+__device__ __forceinline__ void store_val(float* d, float v) { *d = v; }
+__device__ __forceinline__ void store_val(fpair* d, double v) { *d = split_double(v); }
+
 // y = (H p)_row,comp for this lane (3 lanes per row, rows taken from the length-sorted order).
 template <typename VT, typename PT>
 __device__ __forceinline__ bool spmv_lane(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
@@ -229,11 +283,11 @@ __global__ void sell_len_kernel(const int32_t* __restrict__ rowptr, const int32_
     slice_len[sl] = L;
 }
 
-template <typename VT>
+template <typename VT, typename VD>
 __global__ void sell_fill_kernel(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
                                  const VT* __restrict__ vals, const int32_t* __restrict__ perm, int64_t n, int64_t nsl,
                                  const int64_t* __restrict__ slice_off, int32_t* __restrict__ sell_col,
-                                 VT* __restrict__ sell_vals) {
+                                 VD* __restrict__ sell_vals) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nsl * kSellC) return;
     const int64_t sl = t / kSellC;
@@ -251,7 +305,7 @@ __global__ void sell_fill_kernel(const int32_t* __restrict__ rowptr, const int32
         sell_col[p] = real ? colidx[b0 + j] : 0;
 #pragma unroll
         for (int k = 0; k < 9; ++k)
-            sell_vals[((off + j) * 9 + k) * kSellC + i] = real ? vals[9 * (int64_t)(b0 + j) + k] : VT(0);
+            store_val(sell_vals + ((off + j) * 9 + k) * kSellC + i, real ? vals[9 * (int64_t)(b0 + j) + k] : VT(0));
     }
 }
 
@@ -374,7 +428,7 @@ pcg_spmv_tma_kernel(const int32_t* __restrict__ rowptr, const int64_t* __restric
                 if (g * U + u < L) {
                     const int64_t cj = sc[u * kSellC + lane];
 #pragma unroll
-                    for (int k = 0; k < 3; ++k) pv[u][k] = __ldg(cg + 3 * cj + k);
+                    for (int k = 0; k < 3; ++k) pv[u][k] = ldg_(cg + 3 * cj + k);
                 }
         };
         if (lane == 0)
@@ -414,7 +468,7 @@ pcg_spmv_tma_kernel(const int32_t* __restrict__ rowptr, const int64_t* __restric
                     for (int e = 0; e < 3; ++e)
 #pragma unroll
                         for (int k = 0; k < 3; ++k)
-                            a[e] = fma(sv[(u * 9 + 3 * e + k) * kSellC + lane], (VT)pc[u][k], a[e]);
+                            a[e] = mac(sv[(u * 9 + 3 * e + k) * kSellC + lane], (VT)pc[u][k], a[e]);
                 }
             }
             if (kPrefetchGather) {
@@ -460,6 +514,7 @@ pcg_spmv_tma_kernel(const int32_t* __restrict__ rowptr, const int64_t* __restric
 // C1 system (FP64: 84 us vs 86-110 us for the others tried; mixed: 42 us vs 43-56 us).
 constexpr int kU64 = 1, kW64 = 16, kNS64 = 2;
 constexpr int kU32 = 2, kW32 = 16, kNS32 = 2;
+constexpr int kUfp = 2, kWfp = 16, kNSfp = 2;   // float-pair product (8-byte values, FP32-pipe arithmetic)
 
 template <typename VT, typename PT, int U, int W, int NS>
 void launch_spmv_tma(const int32_t* rowptr, const int64_t* slice_off, const int32_t* sell_col, const VT* sell_vals,
@@ -467,15 +522,20 @@ void launch_spmv_tma(const int32_t* rowptr, const int64_t* slice_off, const int3
                      int64_t nsl, double* part, PcgScalars* S, cudaStream_t st) {
     using Lay = StageLayout<VT, U, W, NS>;
     static bool attr = false;
+    static int per_sm = 1, sms = 152;
     if (!attr) {
         cudaFuncSetAttribute(pcg_spmv_tma_kernel<VT, PT, U, W, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)Lay::kBlockBytes);
+        // persistent: as many CTAs as are resident at once (shared memory and registers)
+        int dev = 0, occ = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pcg_spmv_tma_kernel<VT, PT, U, W, NS>, W * 32,
+                                                          Lay::kBlockBytes) == cudaSuccess)
+            per_sm = std::max(1, std::min(16, occ));
         attr = true;
     }
-    // persistent: as many CTAs as fit in one wave (shared memory bound), at most one per W slices
-    const int per_sm = std::max(1, std::min(16, (int)((220u * 1024u) / Lay::kBlockBytes)));
-    const int64_t want = (nsl + W - 1) / W;
-    const unsigned blocks = (unsigned)std::min<int64_t>(std::max<int64_t>(want, 1), 152 * per_sm);
+    const int64_t want = (nsl + W - 1) / W;   // at most one CTA per W slices
+    const unsigned blocks = (unsigned)std::min<int64_t>(std::max<int64_t>(want, 1), (int64_t)sms * per_sm);
     pcg_spmv_tma_kernel<VT, PT, U, W, NS><<<blocks, W * 32, Lay::kBlockBytes, st>>>(
         rowptr, slice_off, sell_col, sell_vals, cg, c, perm, q, fixed, n, nsl, part, S);
 }
@@ -701,7 +761,8 @@ __device__ __forceinline__ bool grid_barrier(PcgScalars* S) {
 
 __global__ void __launch_bounds__(kUpdT, kUpdPerSm)
 pcg_update_direction_kernel(double* __restrict__ x, double* __restrict__ r, double* __restrict__ c,
-                            float* __restrict__ c32, const double* __restrict__ q, const double* __restrict__ fac,
+                            float* __restrict__ c32, fpair* __restrict__ c2, const double* __restrict__ q,
+                            const double* __restrict__ fac,
                             const uint8_t* __restrict__ fixed, int64_t n, double* __restrict__ part,
                             PcgScalars* __restrict__ S) {
     if (S->done) return;
@@ -809,6 +870,7 @@ pcg_update_direction_kernel(double* __restrict__ x, double* __restrict__ r, doub
                     const double ce = fx ? 0.0 : ks[t + j * kUpdT] + beta * ks[3 * kUpdT + t + j * kUpdT];
                     c[e] = ce;
                     if (c32) c32[e] = (float)ce;
+                    if (c2) c2[e] = split_double(ce);
                 }
             }
         }
@@ -828,7 +890,8 @@ pcg_update_direction_kernel(double* __restrict__ x, double* __restrict__ r, doub
 // c = S(s + beta c) and its float32 copy, over the flat [3n] vectors with kDirEpt coalesced
 // entries per thread.
 __global__ void __launch_bounds__(kPcgThreads)
-pcg_direction_kernel(double* __restrict__ c, float* __restrict__ c32, const double* __restrict__ s,
+pcg_direction_kernel(double* __restrict__ c, float* __restrict__ c32, fpair* __restrict__ c2,
+                     const double* __restrict__ s,
                      const uint8_t* __restrict__ fixed, int64_t n, const PcgScalars* __restrict__ S) {
     // runs after the update of the same iteration; `done` may now be set, but c is still refreshed
     // only while the solve continues
@@ -855,6 +918,7 @@ pcg_direction_kernel(double* __restrict__ c, float* __restrict__ c32, const doub
             const double ce = fx[j] ? 0.0 : sv[j] + beta * cv[j];
             c[e] = ce;
             if (c32) c32[e] = (float)ce;
+            if (c2) c2[e] = split_double(ce);
         }
     }
 }
@@ -881,7 +945,8 @@ __global__ void aos_to_soa_kernel(const double* __restrict__ in, double* __restr
 // Setup: r = S(b - H x0), s = P^-1 r, c = S(s), delta_0 = r.s (H x0 already in q)
 __global__ void __launch_bounds__(kPcgThreads)
 pcg_init_kernel(const double* __restrict__ b, const double* __restrict__ q, double* __restrict__ r,
-                double* __restrict__ s, double* __restrict__ c, float* __restrict__ c32, const double* __restrict__ pinv,
+                double* __restrict__ s, double* __restrict__ c, float* __restrict__ c32, fpair* __restrict__ c2,
+                const double* __restrict__ pinv,
                 const uint8_t* __restrict__ fixed, int64_t n, double* __restrict__ part, PcgScalars* __restrict__ S) {
     const int64_t ldf = n;
     double d = 0.0;
@@ -902,6 +967,7 @@ pcg_init_kernel(const double* __restrict__ b, const double* __restrict__ q, doub
             s[3 * v + i] = sv[i];
             c[3 * v + i] = fx ? 0.0 : sv[i];
             if (c32) c32[3 * v + i] = fx ? 0.0f : (float)sv[i];
+            if (c2) c2[3 * v + i] = split_double(fx ? 0.0 : sv[i]);
         }
     }
     const double bs = block_sum(d);
@@ -1121,6 +1187,8 @@ gipc_status pcg_impl(gipc_ctx* ctx, const gipc_bsr* A, const double* rhs, double
     if (A->prec != GIPC_FP64 && A->prec != GIPC_MIXED) return fail(GIPC_ERR_INVALID_ARG, "gipc_pcg: bad precision");
     if (!(prm->rel_tol >= 0.0) || prm->max_iter < 0 || prm->check_every < 0)
         return fail(GIPC_ERR_INVALID_ARG, "gipc_pcg: need rel_tol >= 0, max_iter >= 0, check_every >= 0");
+    if (prm->product != GIPC_PRODUCT_NATIVE && prm->product != GIPC_PRODUCT_FLOAT_PAIR)
+        return fail(GIPC_ERR_INVALID_ARG, "gipc_pcg: unknown product arithmetic %d", prm->product);
     if (n == 0) {
         if (iters_out_h) *iters_out_h = 0;
         if (rel_out_h) *rel_out_h = 0.0;
@@ -1154,8 +1222,13 @@ gipc_status pcg_impl(gipc_ctx* ctx, const gipc_bsr* A, const double* rhs, double
     int64_t* offs = reinterpret_cast<int64_t*>(ctx->slot[P_PERM].as<char>() + ((sizeof(int32_t) * (n + ncnt) + 15) / 16) * 16);
     int64_t* scan_tmp = offs + ncnt + 1;
     float* c32 = nullptr;
+    fpair* c2 = nullptr;   // float-pair copy of the direction (float-pair product)
+    const bool fp = f64 && !voff && prm->product == GIPC_PRODUCT_FLOAT_PAIR;
     if (!f64) {
         if ((s = ctx->slot[P_VEC32].reserve(sizeof(float) * 2 * nvec)) != GIPC_OK) return s;
+    } else if (fp) {
+        if ((s = ctx->slot[P_VEC32].reserve(sizeof(fpair) * nvec)) != GIPC_OK) return s;
+        c2 = ctx->slot[P_VEC32].as<fpair>();
     }
     float* x32 = f64 ? nullptr : ctx->slot[P_VEC32].as<float>();
     if (!f64) c32 = x32 + nvec;
@@ -1179,8 +1252,9 @@ gipc_status pcg_impl(gipc_ctx* ctx, const gipc_bsr* A, const double* rhs, double
     int32_t* sell_col = ctx->slot[P_SELL].as<int32_t>();
     void* sell_vals = ctx->slot[P_SELL].as<char>() + ((sizeof(int32_t) * cells + 255) / 256) * 256;
     const unsigned fb = (unsigned)((nsl * kSellC + 255) / 256);
-    if (f64) sell_fill_kernel<double><<<fb, 256, 0, st>>>(A->rowptr, A->colidx, (const double*)A->vals, perm, n, nsl, slice_off, sell_col, (double*)sell_vals);
-    else sell_fill_kernel<float><<<fb, 256, 0, st>>>(A->rowptr, A->colidx, (const float*)A->vals, perm, n, nsl, slice_off, sell_col, (float*)sell_vals);
+    if (fp) sell_fill_kernel<double, fpair><<<fb, 256, 0, st>>>(A->rowptr, A->colidx, (const double*)A->vals, perm, n, nsl, slice_off, sell_col, (fpair*)sell_vals);
+    else if (f64) sell_fill_kernel<double, double><<<fb, 256, 0, st>>>(A->rowptr, A->colidx, (const double*)A->vals, perm, n, nsl, slice_off, sell_col, (double*)sell_vals);
+    else sell_fill_kernel<float, float><<<fb, 256, 0, st>>>(A->rowptr, A->colidx, (const float*)A->vals, perm, n, nsl, slice_off, sell_col, (float*)sell_vals);
     pcg_set_scalars<<<1, 1, 0, st>>>(S, prm->rel_tol, max_iter);
     soa_to_aos_kernel<<<eb, 256, 0, st>>>(rhs, b, nullptr, n, fixed);
     soa_to_aos_kernel<<<eb, 256, 0, st>>>(x, xv, x32, n, fixed);
@@ -1195,7 +1269,7 @@ gipc_status pcg_impl(gipc_ctx* ctx, const gipc_bsr* A, const double* rhs, double
         SS = ctx->slot[P_SCENE].as<SceneScalars>();
         pcg_scene_init_kernel<<<nscenes, kPcgThreads, 0, st>>>(b, q, r, sv, c, c32, pinv, n, fixed, voff, nscenes, SS, S);
     } else {
-        pcg_init_kernel<<<vb, kPcgThreads, 0, st>>>(b, q, r, sv, c, c32, pinv, fixed, n, part, S);
+        pcg_init_kernel<<<vb, kPcgThreads, 0, st>>>(b, q, r, sv, c, c32, c2, pinv, fixed, n, part, S);
     }
     if ((s = check_launch("gipc_pcg: setup")) != GIPC_OK) return s;
 
@@ -1206,7 +1280,10 @@ gipc_status pcg_impl(gipc_ctx* ctx, const gipc_bsr* A, const double* rhs, double
         const int m = (max_iter - launched) < chunk ? (max_iter - launched) : chunk;
         for (int it = 0; it < m; ++it) {
             ctx->prof.start(GIPC_PROF_PCG_SPMV, st);
-            if (f64)
+            if (fp)
+                launch_spmv_tma<fpair, fpair, kUfp, kWfp, kNSfp>(A->rowptr, slice_off, sell_col, (const fpair*)sell_vals,
+                                                                 c2, c, perm, q, fixed, n, nsl, part, S, st);
+            else if (f64)
                 launch_spmv_tma<double, double, kU64, kW64, kNS64>(A->rowptr, slice_off, sell_col, (const double*)sell_vals,
                                                                    c, c, perm, q, fixed, n, nsl, part, S, st);
             else
@@ -1224,7 +1301,7 @@ gipc_status pcg_impl(gipc_ctx* ctx, const gipc_bsr* A, const double* rhs, double
             if (fuse.ok) {
                 int64_t n_arg = n;
                 const uint8_t* fixed_arg = fixed;
-                void* args[] = {&xv, &r, &c, &c32, &q, &pinv, &fixed_arg, &n_arg, &part, &S};
+                void* args[] = {&xv, &r, &c, &c32, &c2, &q, &pinv, &fixed_arg, &n_arg, &part, &S};
                 if (cudaLaunchCooperativeKernel((const void*)pcg_update_direction_kernel, dim3(fuse.grid), dim3(kUpdT), args,
                                                 fuse.smem, st) != cudaSuccess)
                     return check_launch("gipc_pcg: fused update");
@@ -1234,7 +1311,7 @@ gipc_status pcg_impl(gipc_ctx* ctx, const gipc_bsr* A, const double* rhs, double
             pcg_update_kernel<<<ub, kUpdT, 0, st>>>(xv, r, c, q, sv, pinv, n, part, S);
             ctx->prof.stop(GIPC_PROF_PCG_UPDATE, st);
             ctx->prof.start(GIPC_PROF_PCG_DIRECTION, st);
-            pcg_direction_kernel<<<db, kPcgThreads, 0, st>>>(c, c32, sv, fixed, n, S);
+            pcg_direction_kernel<<<db, kPcgThreads, 0, st>>>(c, c32, c2, sv, fixed, n, S);
             ctx->prof.stop(GIPC_PROF_PCG_DIRECTION, st);
         }
         launched += m;
@@ -1412,7 +1489,7 @@ extern "C" gipc_status gipc_pcg_noalloc(const gipc_bsr* A, const double* rhs, do
     else pcg_factor_kernel<float><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(A->rowptr, A->colidx, (const float*)A->vals, n, pinv);
     if (f64) pcg_spmv_kernel<double, double><<<sb, kPcgThreads, 0, st>>>(A->rowptr, A->colidx, (const double*)A->vals, xv, xv, perm, q, fixed, n, part, S);
     else pcg_spmv_kernel<float, float><<<sb, kPcgThreads, 0, st>>>(A->rowptr, A->colidx, (const float*)A->vals, x32, xv, perm, q, fixed, n, part, S);
-    pcg_init_kernel<<<vb, kPcgThreads, 0, st>>>(b, q, r, sv, c, c32, pinv, fixed, n, part, S);
+    pcg_init_kernel<<<vb, kPcgThreads, 0, st>>>(b, q, r, sv, c, c32, nullptr, pinv, fixed, n, part, S);
     if ((s = check_launch("gipc_pcg_noalloc: setup")) != GIPC_OK) return s;
 
     const int chunk = prm->check_every > 0 ? prm->check_every : (prm->rel_tol > 0.0 ? 16 : max_iter + 1);
@@ -1424,7 +1501,7 @@ extern "C" gipc_status gipc_pcg_noalloc(const gipc_bsr* A, const double* rhs, do
             if (f64) pcg_spmv_kernel<double, double><<<sb, kPcgThreads, 0, st>>>(A->rowptr, A->colidx, (const double*)A->vals, c, c, perm, q, fixed, n, part, S);
             else pcg_spmv_kernel<float, float><<<sb, kPcgThreads, 0, st>>>(A->rowptr, A->colidx, (const float*)A->vals, c32, c, perm, q, fixed, n, part, S);
             pcg_update_kernel<<<ub, kUpdT, 0, st>>>(xv, r, c, q, sv, pinv, n, part, S);
-            pcg_direction_kernel<<<db, kPcgThreads, 0, st>>>(c, c32, sv, fixed, n, S);
+            pcg_direction_kernel<<<db, kPcgThreads, 0, st>>>(c, c32, nullptr, sv, fixed, n, S);
         }
         launched += m;
         if ((s = check_launch("gipc_pcg_noalloc: iteration")) != GIPC_OK) return s;
