@@ -74,6 +74,13 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
+// Programmatic dependent launch: a kernel launched with programmatic stream serialization may
+// start while the previous kernel of the stream finishes; it must wait here before it touches
+// anything that kernel writes (a no-op when the launch was an ordinary one).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// Lets the next kernel of the stream start launching (its CTAs still wait as above).
+__device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // Block-wide sum (fixed order) -> thread 0.
 __device__ __forceinline__ double block_sum(double v) {
     __shared__ double sh[32];
@@ -374,7 +381,6 @@ pcg_spmv_tma_kernel(const int32_t* __restrict__ rowptr, const int64_t* __restric
                     PcgScalars* __restrict__ S) {
     using Lay = StageLayout<VT, U, W, NS>;
     constexpr bool kPrefetchGather = NS >= 3;
-    if (S->done) return;
     extern __shared__ __align__(128) unsigned char stage[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     unsigned char* wbuf = stage + w * Lay::kWarpBytes;
@@ -405,6 +411,22 @@ pcg_spmv_tma_kernel(const int32_t* __restrict__ rowptr, const int64_t* __restric
     };
     const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    // The matrix does not depend on the previous kernel: the first slice's leading groups are put
+    // in flight before waiting for it (under a programmatic dependent launch they overlap its tail).
+    const int64_t pre_sl = wid < nsl ? wid : -1;
+    int64_t pre_groups = 0;
+    if (pre_sl >= 0) {
+        const int64_t off = slice_off[pre_sl], Ls = slice_off[pre_sl + 1] - off;
+        pre_groups = std::min<int64_t>(NS - 1, (Ls + U - 1) / U);
+        if (lane == 0)
+            for (int64_t g = 0; g < pre_groups; ++g) issue((unsigned)g, off, Ls, g);
+    }
+    pdl_wait();
+    if (S->done) {   // uniform: the solve has stopped; let the staged copies land, then leave
+        for (int64_t g = 0; g < pre_groups; ++g) mbar_wait_bounded(bars + g, 0);
+        __syncwarp();
+        return;
+    }
     double d = 0.0;
     // slices are longest first; a warp takes one per round, in alternating directions (round r:
     // r * warps + wid, then r * warps + warps - 1 - wid), so long and short slices pair up and the
@@ -431,7 +453,7 @@ pcg_spmv_tma_kernel(const int32_t* __restrict__ rowptr, const int64_t* __restric
                     for (int k = 0; k < 3; ++k) pv[u][k] = ldg_(cg + 3 * cj + k);
                 }
         };
-        if (lane == 0)
+        if (lane == 0 && sl != pre_sl)   // (the first slice's leading groups are already in flight)
             for (int64_t g = 0; g < NS - 1 && g < G; ++g) issue((base + (unsigned)g) % NS, off, Ls, g);
         if (kPrefetchGather && G > 0) {
             if (!wait(base % NS)) timed_out = true;
@@ -536,8 +558,20 @@ void launch_spmv_tma(const int32_t* rowptr, const int64_t* slice_off, const int3
     }
     const int64_t want = (nsl + W - 1) / W;   // at most one CTA per W slices
     const unsigned blocks = (unsigned)std::min<int64_t>(std::max<int64_t>(want, 1), (int64_t)sms * per_sm);
-    pcg_spmv_tma_kernel<VT, PT, U, W, NS><<<blocks, W * 32, Lay::kBlockBytes, st>>>(
-        rowptr, slice_off, sell_col, sell_vals, cg, c, perm, q, fixed, n, nsl, part, S);
+    // programmatic dependent launch: the CTAs may start (and stage matrix slices) while the previous
+    // kernel finishes; the kernel waits for it before reading the direction or the scalars
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(blocks);
+    cfg.blockDim = dim3(W * 32);
+    cfg.dynamicSmemBytes = Lay::kBlockBytes;
+    cfg.stream = st;
+    cudaLaunchAttribute attr_pdl[1];
+    attr_pdl[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr_pdl[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr_pdl;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, pcg_spmv_tma_kernel<VT, PT, U, W, NS>, rowptr, slice_off, sell_col, sell_vals, cg, c, perm,
+                       q, fixed, n, nsl, part, S);
 }
 
 // q = S(H c); alpha = delta_new / (c . q)
@@ -765,6 +799,7 @@ pcg_update_direction_kernel(double* __restrict__ x, double* __restrict__ r, doub
                             const double* __restrict__ fac,
                             const uint8_t* __restrict__ fixed, int64_t n, double* __restrict__ part,
                             PcgScalars* __restrict__ S) {
+    pdl_release();   // the next product may begin staging its matrix slices as SMs free up
     if (S->done) return;
     extern __shared__ double keep[];   // per owned tile: s then c, flat order, 3 kUpdT each
     __shared__ double rt[3 * kUpdT], st[3 * kUpdT];
