@@ -12,6 +12,8 @@
 //   scaling: eigenpairs (l, a) of the 3x3 matrix d2Psi/ds_i ds_j,            U diag(a) V^T
 // The projected block is scale * vol * sum over modes with l > 0 of l w w^T, w = dF/dx^T vec(Q),
 // where dF/dx^T maps a 3x3 G to forces (G Dm^-T columns on vertices 1..3, minus their sum on 0).
+// Energy and gradient are computed in float64 for both precisions; the projected Hessian in the
+// precision it is stored in (float64, or float32 for the mixed form, whose blocks are float32).
 #include <cmath>
 #include <type_traits>
 
@@ -26,25 +28,41 @@ struct ElasticConst {
     double mu, lam, alpha, scale;
 };
 
+// Arithmetic-type constants of the Hessian projection.
+template <typename CT>
+struct Num;
+template <>
+struct Num<double> {
+    static constexpr double jacobi_tol = 1e-34;   // off-diagonal^2 / diagonal^2 that ends the sweeps
+    static constexpr double tiny = 1e-300;
+    static constexpr double rel = 1e-14;
+};
+template <>
+struct Num<float> {
+    static constexpr float jacobi_tol = 1e-14f;
+    static constexpr float tiny = 1e-35f;
+    static constexpr float rel = 1e-6f;
+};
+
 // One Jacobi rotation zeroing a[p][q] of a symmetric 3x3 matrix, accumulating into v.
-template <int P, int Q>
-__device__ __forceinline__ void jacobi_rot(double (&a)[3][3], double (&v)[3][3]) {
+template <int P, int Q, typename CT>
+__device__ __forceinline__ void jacobi_rot(CT (&a)[3][3], CT (&v)[3][3]) {
     constexpr int R = 3 - P - Q;
-    const double apq = a[P][Q];
-    if (apq == 0.0) return;
-    const double theta = (a[Q][Q] - a[P][P]) / (2.0 * apq);
-    const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-    const double c = rsqrt(t * t + 1.0);
-    const double s = t * c;
+    const CT apq = a[P][Q];
+    if (apq == CT(0)) return;
+    const CT theta = (a[Q][Q] - a[P][P]) / (CT(2) * apq);
+    const CT t = (theta >= CT(0) ? CT(1) : CT(-1)) / (fabs(theta) + sqrt(theta * theta + CT(1)));
+    const CT c = rsqrt(t * t + CT(1));
+    const CT s = t * c;
     a[P][P] -= t * apq;
     a[Q][Q] += t * apq;
-    a[P][Q] = a[Q][P] = 0.0;
-    const double arp = a[R][P], arq = a[R][Q];
+    a[P][Q] = a[Q][P] = CT(0);
+    const CT arp = a[R][P], arq = a[R][Q];
     a[R][P] = a[P][R] = c * arp - s * arq;
     a[R][Q] = a[Q][R] = s * arp + c * arq;
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
-        const double vp = v[r][P], vq = v[r][Q];
+        const CT vp = v[r][P], vq = v[r][Q];
         v[r][P] = c * vp - s * vq;
         v[r][Q] = s * vp + c * vq;
     }
@@ -52,37 +70,40 @@ __device__ __forceinline__ void jacobi_rot(double (&a)[3][3], double (&v)[3][3])
 
 // Eigen-decomposition of a symmetric 3x3 matrix by cyclic Jacobi; eigenvalues on the
 // diagonal of a, eigenvectors in the columns of v.
-__device__ __forceinline__ void jacobi3(double (&a)[3][3], double (&v)[3][3]) {
+template <typename CT>
+__device__ __forceinline__ void jacobi3(CT (&a)[3][3], CT (&v)[3][3]) {
 #pragma unroll
     for (int r = 0; r < 3; ++r)
 #pragma unroll
-        for (int c = 0; c < 3; ++c) v[r][c] = r == c ? 1.0 : 0.0;
+        for (int c = 0; c < 3; ++c) v[r][c] = r == c ? CT(1) : CT(0);
     for (int sweep = 0; sweep < 12; ++sweep) {
-        const double off = a[0][1] * a[0][1] + a[0][2] * a[0][2] + a[1][2] * a[1][2];
-        const double dia = a[0][0] * a[0][0] + a[1][1] * a[1][1] + a[2][2] * a[2][2];
-        if (!(off > 1e-34 * dia)) break;
+        const CT off = a[0][1] * a[0][1] + a[0][2] * a[0][2] + a[1][2] * a[1][2];
+        const CT dia = a[0][0] * a[0][0] + a[1][1] * a[1][1] + a[2][2] * a[2][2];
+        if (!(off > Num<CT>::jacobi_tol * dia)) break;
         jacobi_rot<0, 1>(a, v);
         jacobi_rot<0, 2>(a, v);
         jacobi_rot<1, 2>(a, v);
     }
 }
 
-__device__ __forceinline__ void cross(const double* a, const double* b, double* o) {
+template <typename CT>
+__device__ __forceinline__ void cross(const CT* a, const CT* b, CT* o) {
     o[0] = a[1] * b[2] - a[2] * b[1];
     o[1] = a[2] * b[0] - a[0] * b[2];
     o[2] = a[0] * b[1] - a[1] * b[0];
 }
 
 // Rotation-variant SVD: F = U diag(s) V^T with det U = det V = 1, s0 >= s1 >= |s2|.
-__device__ void svd3(const double (&F)[3][3], double (&U)[3][3], double (&s)[3], double (&V)[3][3]) {
-    double S[3][3];
+template <typename CT>
+__device__ void svd3(const CT (&F)[3][3], CT (&U)[3][3], CT (&s)[3], CT (&V)[3][3]) {
+    CT S[3][3];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int j = 0; j < 3; ++j) S[i][j] = F[0][i] * F[0][j] + F[1][i] * F[1][j] + F[2][i] * F[2][j];
-    double W[3][3];
+    CT W[3][3];
     jacobi3(S, W);
-    double ev[3] = {S[0][0], S[1][1], S[2][2]};
+    CT ev[3] = {S[0][0], S[1][1], S[2][2]};
     int o[3] = {0, 1, 2};
     // sort descending
     if (ev[o[0]] < ev[o[1]]) { int t = o[0]; o[0] = o[1]; o[1] = t; }
@@ -92,44 +113,44 @@ __device__ void svd3(const double (&F)[3][3], double (&U)[3][3], double (&s)[3],
     for (int r = 0; r < 3; ++r)
 #pragma unroll
         for (int c = 0; c < 3; ++c) V[r][c] = o[c] == 0 ? W[r][0] : (o[c] == 1 ? W[r][1] : W[r][2]);
-    double v0[3] = {V[0][0], V[1][0], V[2][0]}, v1[3] = {V[0][1], V[1][1], V[2][1]}, v2[3];
+    CT v0[3] = {V[0][0], V[1][0], V[2][0]}, v1[3] = {V[0][1], V[1][1], V[2][1]}, v2[3];
     cross(v0, v1, v2);  // third column = v0 x v1 makes V a rotation
 #pragma unroll
     for (int r = 0; r < 3; ++r) V[r][2] = v2[r];
     // B = F V
-    double B[3][3];
+    CT B[3][3];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int j = 0; j < 3; ++j) B[i][j] = F[i][0] * V[0][j] + F[i][1] * V[1][j] + F[i][2] * V[2][j];
-    double u0[3] = {B[0][0], B[1][0], B[2][0]};
-    double n0 = sqrt(u0[0] * u0[0] + u0[1] * u0[1] + u0[2] * u0[2]);
-    if (n0 > 0.0) {
+    CT u0[3] = {B[0][0], B[1][0], B[2][0]};
+    CT n0 = sqrt(u0[0] * u0[0] + u0[1] * u0[1] + u0[2] * u0[2]);
+    if (n0 > CT(0)) {
 #pragma unroll
         for (int r = 0; r < 3; ++r) u0[r] /= n0;
     } else {
-        u0[0] = 1.0; u0[1] = 0.0; u0[2] = 0.0;
+        u0[0] = CT(1); u0[1] = CT(0); u0[2] = CT(0);
     }
-    double b1[3] = {B[0][1], B[1][1], B[2][1]};
-    const double p = u0[0] * b1[0] + u0[1] * b1[1] + u0[2] * b1[2];
-    double u1[3] = {b1[0] - p * u0[0], b1[1] - p * u0[1], b1[2] - p * u0[2]};
-    double n1 = sqrt(u1[0] * u1[0] + u1[1] * u1[1] + u1[2] * u1[2]);
-    if (n1 > 1e-300 && n1 > 1e-14 * n0) {
+    CT b1[3] = {B[0][1], B[1][1], B[2][1]};
+    const CT p = u0[0] * b1[0] + u0[1] * b1[1] + u0[2] * b1[2];
+    CT u1[3] = {b1[0] - p * u0[0], b1[1] - p * u0[1], b1[2] - p * u0[2]};
+    CT n1 = sqrt(u1[0] * u1[0] + u1[1] * u1[1] + u1[2] * u1[2]);
+    if (n1 > Num<CT>::tiny && n1 > Num<CT>::rel * n0) {
 #pragma unroll
         for (int r = 0; r < 3; ++r) u1[r] /= n1;
     } else {  // any unit vector orthogonal to u0
-        const double ax = fabs(u0[0]), ay = fabs(u0[1]), az = fabs(u0[2]);
-        double e[3] = {0.0, 0.0, 0.0};
-        if (ax <= ay && ax <= az) e[0] = 1.0;
-        else if (ay <= az) e[1] = 1.0;
-        else e[2] = 1.0;
+        const CT ax = fabs(u0[0]), ay = fabs(u0[1]), az = fabs(u0[2]);
+        CT e[3] = {CT(0), CT(0), CT(0)};
+        if (ax <= ay && ax <= az) e[0] = CT(1);
+        else if (ay <= az) e[1] = CT(1);
+        else e[2] = CT(1);
         cross(u0, e, u1);
-        const double m = sqrt(u1[0] * u1[0] + u1[1] * u1[1] + u1[2] * u1[2]);
+        const CT m = sqrt(u1[0] * u1[0] + u1[1] * u1[1] + u1[2] * u1[2]);
 #pragma unroll
         for (int r = 0; r < 3; ++r) u1[r] /= m;
         n1 = u1[0] * b1[0] + u1[1] * b1[1] + u1[2] * b1[2];
     }
-    double u2[3];
+    CT u2[3];
     cross(u0, u1, u2);
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
@@ -143,14 +164,15 @@ __device__ void svd3(const double (&F)[3][3], double (&U)[3][3], double (&s)[3],
 }
 
 // G (3x3) -> w (12): forces G Dm^-T on vertices 1..3, minus their sum on vertex 0.
-__device__ __forceinline__ void map_to_x(const double (&G)[3][3], const double (&Dmi)[3][3], double (&w)[12]) {
+template <typename CT>
+__device__ __forceinline__ void map_to_x(const CT (&G)[3][3], const CT (&Dmi)[3][3], CT (&w)[12]) {
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
-        double s = 0.0;
+        CT s = CT(0);
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             // (G Dm^-T)[r][a] = sum_c G[r][c] Dmi[a][c]
-            const double h = G[r][0] * Dmi[a][0] + G[r][1] * Dmi[a][1] + G[r][2] * Dmi[a][2];
+            const CT h = G[r][0] * Dmi[a][0] + G[r][1] * Dmi[a][1] + G[r][2] * Dmi[a][2];
             w[3 * (a + 1) + r] = h;
             s += h;
         }
@@ -158,16 +180,15 @@ __device__ __forceinline__ void map_to_x(const double (&G)[3][3], const double (
     }
 }
 
-template <typename HT>
-__device__ __forceinline__ void add_mode(double lam, const double (&Q)[3][3], const double (&Dmi)[3][3],
-                                         double (&H)[78]) {
-    if (!(lam > 0.0)) return;
-    double w[12];
+template <typename CT>
+__device__ __forceinline__ void add_mode(CT lam, const CT (&Q)[3][3], const CT (&Dmi)[3][3], CT (&H)[78]) {
+    if (!(lam > CT(0))) return;
+    CT w[12];
     map_to_x(Q, Dmi, w);
     int idx = 0;
 #pragma unroll
     for (int a = 0; a < 12; ++a) {
-        const double la = lam * w[a];
+        const CT la = lam * w[a];
 #pragma unroll
         for (int b = 0; b <= a; ++b) H[idx++] += la * w[b];
     }
@@ -251,66 +272,78 @@ eval_tets_kernel(const double* __restrict__ x, int64_t n, const int32_t* __restr
     }
     if (!hess) return;
 
-    double U[3][3], s[3], V[3][3];
-    svd3(F, U, s, V);
-    double H[78];
+    // the projected Hessian in the stored precision (the same operations as float64 when it is)
+    using CT = HT;
+    CT Fc[3][3], Dc[3][3];
 #pragma unroll
-    for (int q = 0; q < 78; ++q) H[q] = 0.0;
-    const double r2 = 0.70710678118654752440;
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            Fc[i][j] = (CT)F[i][j];
+            Dc[i][j] = (CT)Dmi[i][j];
+        }
+    const CT m1c = (CT)m1, lJ = (CT)(K.lam * Jm), muc = (CT)K.mu, lamc = (CT)K.lam, alc = (CT)K.alpha;
+    CT U[3][3], sv[3], V[3][3];
+    svd3(Fc, U, sv, V);
+    CT H[78];
+#pragma unroll
+    for (int q = 0; q < 78; ++q) H[q] = CT(0);
+    const CT r2 = (CT)0.70710678118654752440;
     // twist / flip modes for the pairs (1,2), (0,2), (0,1)
 #pragma unroll
     for (int kk = 0; kk < 3; ++kk) {
         const int i = kk == 0 ? 1 : 0, j = kk == 2 ? 1 : 2;
-        const double lt = m1 + K.lam * Jm * s[kk];
-        const double lf = m1 - K.lam * Jm * s[kk];
-        double Qt[3][3], Qf[3][3];
+        const CT lt = m1c + lJ * sv[kk];
+        const CT lf = m1c - lJ * sv[kk];
+        CT Qt[3][3], Qf[3][3];
 #pragma unroll
         for (int r = 0; r < 3; ++r)
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                const double a = U[r][i] * V[c][j], b = U[r][j] * V[c][i];
+                const CT a = U[r][i] * V[c][j], b = U[r][j] * V[c][i];
                 Qt[r][c] = r2 * (a - b);
                 Qf[r][c] = r2 * (a + b);
             }
-        add_mode<HT>(lt, Qt, Dmi, H);
-        add_mode<HT>(lf, Qf, Dmi, H);
+        add_mode(lt, Qt, Dc, H);
+        add_mode(lf, Qf, Dc, H);
     }
     // scaling modes: eigenpairs of A = d2 Psi / ds ds
     {
-        double A[3][3];
-        const double ip2 = ip1 * ip1;
+        CT A[3][3];
+        const CT ip2 = (CT)(ip1 * ip1);
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
             const int j = (i + 1) % 3, l = (i + 2) % 3;
-            A[i][i] = m1 + 2.0 * K.mu * s[i] * s[i] * ip2 + K.lam * (s[j] * s[l]) * (s[j] * s[l]);
+            A[i][i] = m1c + CT(2) * muc * sv[i] * sv[i] * ip2 + lamc * (sv[j] * sv[l]) * (sv[j] * sv[l]);
         }
-        const double sj = s[0] * s[1] * s[2];
+        const CT sj = sv[0] * sv[1] * sv[2];
 #pragma unroll
         for (int i = 0; i < 3; ++i)
 #pragma unroll
             for (int j = i + 1; j < 3; ++j) {
                 const int l = 3 - i - j;
-                A[i][j] = A[j][i] = 2.0 * K.mu * s[i] * s[j] * ip2 + K.lam * s[l] * (2.0 * sj - K.alpha);
+                A[i][j] = A[j][i] = CT(2) * muc * sv[i] * sv[j] * ip2 + lamc * sv[l] * (CT(2) * sj - alc);
             }
-        double Avec[3][3];
+        CT Avec[3][3];
         jacobi3(A, Avec);
 #pragma unroll
         for (int m = 0; m < 3; ++m) {
-            double Q[3][3];
+            CT Q[3][3];
 #pragma unroll
             for (int r = 0; r < 3; ++r)
 #pragma unroll
                 for (int c = 0; c < 3; ++c)
                     Q[r][c] = U[r][0] * Avec[0][m] * V[c][0] + U[r][1] * Avec[1][m] * V[c][1] + U[r][2] * Avec[2][m] * V[c][2];
-            add_mode<HT>(A[m][m], Q, Dmi, H);
+            add_mode(A[m][m], Q, Dc, H);
         }
     }
+    const CT kc = (CT)k;
     int idx = 0;
 #pragma unroll
     for (int a = 0; a < 12; ++a)
 #pragma unroll
         for (int b = 0; b <= a; ++b) {
-            const HT h = (HT)(k * H[idx++]);
+            const HT h = kc * H[idx++];
             hess[(int64_t)(a * 12 + b) * T + t] = h;
             if (a != b) hess[(int64_t)(b * 12 + a) * T + t] = h;
         }
