@@ -445,7 +445,9 @@ def run_newton(g, dev, ctx, steps, c2_steps=0):
         prof = ctx.profile_read()
         ctx.profile_stop()
         ms = e0.elapsed_time(e1)
-        phase = {k: v[1] / max(iters, 1) for k, v in prof.items()}
+        # the solver kernels' spans are sampled: mean span x launches (one per PCG iteration)
+        phase = {k: (v[1] / max(v[0], 1) * pcg if k in ("pcg_spmv", "pcg_update") else v[1]) / max(iters, 1)
+                 for k, v in prof.items() if k != "pcg_direction"}
         out[f"{prec}_{hm}"] = {"newton_iters_per_s": iters / (ms * 1e-3), "ms_per_newton_iter": ms / max(iters, 1),
                                "time_steps": steps, "newton_iters": iters, "pcg_iters": pcg,
                                "contacts_final": st["contacts"], "phase_ms_per_newton_iter": phase}
