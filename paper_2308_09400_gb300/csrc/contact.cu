@@ -27,6 +27,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstring>
 #include <cmath>
 
 #include "common.cuh"
@@ -42,12 +43,13 @@ constexpr int kWarps = kThreads / 32;
 // context scratch slots: query counts (then cursors), query offsets, scalars, sort keys, candidate
 // pairs, pair codes; per grid (triangles,
 // edges): float64 target boxes, hash tables, per-target cell counts and their offsets
-enum ContactSlot { C_CNT = 16, C_QOFF = 17, C_MISC = 19, C_KEY = 37, C_PAIRS = 38, C_CODE = 39 };
+enum ContactSlot { C_CNT = 16, C_QOFF = 17, C_MISC = 19, C_KEY = 37, C_PAIRS = 38, C_CODE = 39, C_CPAIRS = 59, C_CX = 60 };
 constexpr int kGridSlots[2][5] = {{18, 30, 31, 32, 45}, {33, 34, 35, 36, 46}};
 // scalars in C_MISC: per grid g the largest cell count at 4g + 2; CCD minimum at 8, pair counter
 // at 9.  Per-scene extent sums, counts and inverse cell sizes live in the grid's last slot.
 constexpr int kMiscAmin = 8;
 constexpr int kMiscPairs = 9;
+constexpr int kMiscDisp = 10;   // cached candidates: max |x - x_b| at 10, max |d| at 11 (bit patterns)
 
 struct V3 {
     double x, y, z;
@@ -629,10 +631,31 @@ __device__ __forceinline__ double warp_min(double v) {
 }
 
 // ACCD of every candidate pair (point-triangle pairs first); the step is the minimum over pairs.
+// Swept box (x and x + d) of the vertices ids[a0..a1), as the grid builds it (unpadded).
+__device__ __forceinline__ void swept_box(const V3* X, const V3* P, int a0, int a1, double (&lo)[3], double (&hi)[3]) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        lo[c] = INFINITY;
+        hi[c] = -INFINITY;
+    }
+    for (int a = a0; a < a1; ++a) {
+        const double p[3] = {X[a].x, X[a].y, X[a].z}, d[3] = {P[a].x, P[a].y, P[a].z};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const double y = __dadd_rn(p[c], d[c]);
+            lo[c] = fmin(lo[c], fmin(p[c], y));
+            hi[c] = fmax(hi[c], fmax(p[c], y));
+        }
+    }
+}
+
+// ACCD of every candidate pair (point-triangle pairs first); the step is the minimum over pairs.
+// With box_filter the pairs come from a superset (the time step's cached candidates) and only
+// those whose swept boxes overlap -- the pairs the swept grid would propose -- are tested.
 __global__ void ccd_pairs_kernel(const double* __restrict__ x, const double* __restrict__ dx, int64_t n, Surf S,
                                  const int32_t* __restrict__ pq, const int32_t* __restrict__ ptg, int64_t npt,
                                  int64_t np, double s, int max_iter, const int32_t* __restrict__ vscene,
-                                 unsigned long long* __restrict__ amin) {
+                                 unsigned long long* __restrict__ amin, bool box_filter) {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double best = 1.0;
     int32_t scene = 0;
@@ -650,7 +673,16 @@ __global__ void ccd_pairs_kernel(const double* __restrict__ x, const double* __r
             X[a] = ld3(x, n, ids[a]);
             P[a] = ld3(dx, n, ids[a]);
         }
-        best = accd(X, P, r < npt, s, max_iter);
+        bool test = true;
+        if (box_filter) {
+            const int split = r < npt ? 1 : 2;   // query vertices: the point, or the first edge
+            double ql[3], qh[3], tl[3], th[3];
+            swept_box(X, P, 0, split, ql, qh);
+            swept_box(X, P, split, 4, tl, th);
+            test = ql[0] <= th[0] && qh[0] >= tl[0] && ql[1] <= th[1] && qh[1] >= tl[1] && ql[2] <= th[2] &&
+                   qh[2] >= tl[2];
+        }
+        if (test) best = accd(X, P, r < npt, s, max_iter);
         if (vscene) scene = vscene[ids[0]];
     }
     if (!vscene) {   // one scene: one atomic per warp
@@ -667,6 +699,31 @@ __global__ void fill_kernel(double* __restrict__ a, int64_t m, double v) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < m) a[i] = v;
 }
+// out[0] = max over surface vertices and axes of |x - xb|, out[1] = of |d| (when d), as the bit
+// patterns of nonnegative doubles (which order like the values).
+__global__ void disp_kernel(const double* __restrict__ x, const double* __restrict__ xb, const double* __restrict__ d,
+                            int64_t n, const int32_t* __restrict__ verts, int64_t nvert,
+                            unsigned long long* __restrict__ out) {
+    double a = 0.0, b = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nvert; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = verts[i];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            a = fmax(a, fabs(x[c * n + v] - xb[c * n + v]));
+            if (d) b = fmax(b, fabs(d[c * n + v]));
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a = fmax(a, __shfl_xor_sync(0xffffffffu, a, o));
+        b = fmax(b, __shfl_xor_sync(0xffffffffu, b, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(out, (unsigned long long)__double_as_longlong(a));
+        atomicMax(out + 1, (unsigned long long)__double_as_longlong(b));
+    }
+}
+
 // persistent warp-per-query grids: at most 16 blocks of kWarps warps per SM
 inline unsigned wblk(int64_t queries) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>((queries + kWarps - 1) / kWarps, 152 * 16)); }
 
@@ -772,12 +829,36 @@ gipc_status collect_pairs(gipc_ctx* ctx, const double* x, const double* d, int64
     return fail(GIPC_ERR_CUDA, "contact pairs: candidate count changed between passes");
 }
 
+bool cache_matches(const gipc_ctx* ctx, int64_t n, const gipc_surface& srf, double dhat) {
+    const gipc_contact_cache& C = ctx->ccache;
+    return C.valid && C.n == n && C.dhat == dhat && C.tris == srf.tris && C.edges == srf.edges &&
+           C.verts == srf.verts && C.ntri == srf.ntri && C.nedge == srf.nedge && C.nvert == srf.nvert;
+}
+
+// Largest per-axis move of a surface vertex since the cached candidates were built, and the
+// largest per-axis entry of d over the surface vertices.  Synchronises once.
+gipc_status cache_disp(gipc_ctx* ctx, const double* x, const double* d, int64_t n, const gipc_surface& srf,
+                       double* delta, double* dmax, cudaStream_t st) {
+    unsigned long long* out = reinterpret_cast<unsigned long long*>(ctx->slot[C_MISC].as<double>() + kMiscDisp);
+    cudaMemsetAsync(out, 0, 2 * sizeof(unsigned long long), st);
+    const unsigned blocks = std::min(nblk(srf.nvert, 256), 152u * 4u);
+    disp_kernel<<<blocks, 256, 0, st>>>(x, ctx->slot[C_CX].as<double>(), d, n, srf.verts, srf.nvert, out);
+    unsigned long long h[2] = {0, 0};
+    cudaMemcpyAsync(h, out, sizeof(h), cudaMemcpyDeviceToHost, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return check_launch("contact cache: sync");
+    std::memcpy(delta, &h[0], sizeof(double));
+    std::memcpy(dmax, &h[1], sizeof(double));
+    return check_launch("contact cache");
+}
+
 }  // namespace
 
 // Internal entry points shared with the time-step driver (newton.cu).
+// cached: use and refill the context's candidate cache (one scene; the time step's detections).
 gipc_status find_contacts_impl(gipc_ctx* ctx, const double* x, const double* rest_x, int64_t n, const gipc_surface& srf,
                                double dhat, int32_t* stencils, double* eps_x, int64_t cap, int64_t* count,
-                               bool compact, const int32_t* vscene, int64_t* npt_out, cudaStream_t st, int nscenes) {
+                               bool compact, const int32_t* vscene, int64_t* npt_out, cudaStream_t st, int nscenes,
+                               bool cached) {
     gipc_prof_span span(ctx->prof, GIPC_PROF_CONTACTS, st);
     Surf S{srf.tris, srf.ntri, srf.edges, srf.nedge, srf.verts, srf.nvert};
     const double pad = dhat * (1.0 + 1e-9);
@@ -788,17 +869,62 @@ gipc_status find_contacts_impl(gipc_ctx* ctx, const double* x, const double* res
     gipc_status s;
     if ((s = ctx->slot[C_MISC].reserve(16 * sizeof(double))) != GIPC_OK) return s;
     const bool pt = S.nvert > 0 && S.ntri > 0;
-    Grid Gt{}, Ge{};
-    if (pt && (s = build_grid(ctx, 0, x, nullptr, n, S.tris, 3, S.ntri, pad, nullptr, vscene, nscenes, Gt, st)) != GIPC_OK)
-        return s;
-    if (S.nedge > 0 &&
-        (s = build_grid(ctx, 1, x, nullptr, n, S.edges, 2, S.nedge, pad, nullptr, vscene, nscenes, Ge, st)) != GIPC_OK)
-        return s;
+    // cached candidates: valid while no surface vertex has moved more than the margin since they
+    // were collected (boxes padded by dhat + 2 margin); the classification below decides exactly
+    const bool use_cache = cached && !vscene;
+    const double margin = 0.5 * dhat;
+    bool hit = false;
+    if (use_cache && cache_matches(ctx, n, srf, dhat)) {
+        double delta = 0.0, dm = 0.0;
+        if ((s = cache_disp(ctx, x, nullptr, n, srf, &delta, &dm, st)) != GIPC_OK) return s;
+        hit = delta * (1.0 + 1e-9) <= ctx->ccache.margin;
+    }
     PairList L{};
     int64_t npt = 0, np = 0;
-    if ((s = collect_pairs(ctx, x, nullptr, n, S, pt ? &Gt : nullptr, S.nedge > 0 ? &Ge : nullptr, false, vscene, &npt,
-                           &np, L, st)) != GIPC_OK)
-        return s;
+    if (hit) {
+        np = ctx->ccache.np;
+        npt = ctx->ccache.npt;
+        L.q = ctx->slot[C_CPAIRS].as<int32_t>();
+        L.t = L.q + np;
+    } else {
+        const double pad_b = use_cache ? (dhat + 2.0 * margin) * (1.0 + 1e-9) : pad;
+        Grid Gt{}, Ge{};
+        if (pt && (s = build_grid(ctx, 0, x, nullptr, n, S.tris, 3, S.ntri, pad_b, nullptr, vscene, nscenes, Gt, st)) !=
+                      GIPC_OK)
+            return s;
+        if (S.nedge > 0 &&
+            (s = build_grid(ctx, 1, x, nullptr, n, S.edges, 2, S.nedge, pad_b, nullptr, vscene, nscenes, Ge, st)) !=
+                GIPC_OK)
+            return s;
+        if ((s = collect_pairs(ctx, x, nullptr, n, S, pt ? &Gt : nullptr, S.nedge > 0 ? &Ge : nullptr, false, vscene,
+                               &npt, &np, L, st)) != GIPC_OK)
+            return s;
+        if (use_cache) {   // keep the candidates and the positions they were collected at
+            ctx->ccache.valid = false;
+            if ((s = ctx->slot[C_CPAIRS].reserve(sizeof(int32_t) * 2 * (np + 1))) != GIPC_OK) return s;
+            if ((s = ctx->slot[C_CX].reserve(sizeof(double) * 3 * n)) != GIPC_OK) return s;
+            int32_t* cq = ctx->slot[C_CPAIRS].as<int32_t>();
+            cudaMemcpyAsync(cq, L.q, sizeof(int32_t) * np, cudaMemcpyDeviceToDevice, st);
+            cudaMemcpyAsync(cq + np, L.t, sizeof(int32_t) * np, cudaMemcpyDeviceToDevice, st);
+            cudaMemcpyAsync(ctx->slot[C_CX].as<double>(), x, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, st);
+            gipc_contact_cache& C = ctx->ccache;
+            C.n = n;
+            C.npt = npt;
+            C.np = np;
+            C.tris = srf.tris;
+            C.edges = srf.edges;
+            C.verts = srf.verts;
+            C.ntri = srf.ntri;
+            C.nedge = srf.nedge;
+            C.nvert = srf.nvert;
+            C.dhat = dhat;
+            C.margin = margin;
+            C.pad = pad_b;
+            C.valid = true;
+            L.q = cq;
+            L.t = cq + np;
+        }
+    }
     // classify once, count per query
     if ((s = ctx->slot[C_CNT].reserve(sizeof(int32_t) * (nq + 1))) != GIPC_OK) return s;
     if ((s = ctx->slot[C_CODE].reserve(sizeof(int32_t) * (np + 1))) != GIPC_OK) return s;
@@ -832,8 +958,12 @@ gipc_status find_contacts_impl(gipc_ctx* ctx, const double* x, const double* res
 
 // alpha_h: host [nscenes] step per scene (nscenes = 1 and vscene = NULL for one scene);
 // amin_dev: device [nscenes] scratch for the per-scene minima when vscene is given.
+// cached: when the context's candidate cache covers every pair the swept grid would propose
+// (2 (max |x - x_b| + max |d|) <= its padding), test its pairs through the same swept-box
+// overlap instead of building the swept grid; the step is the same.
 gipc_status ccd_impl(gipc_ctx* ctx, const double* x, const double* d, int64_t n, const gipc_surface& srf, double slack,
-                     double* alpha_h, cudaStream_t st, const int32_t* vscene, int nscenes, double* amin_dev) {
+                     double* alpha_h, cudaStream_t st, const int32_t* vscene, int nscenes, double* amin_dev,
+                     bool cached) {
     gipc_prof_span span(ctx->prof, GIPC_PROF_CCD, st);
     Surf S{srf.tris, srf.ntri, srf.edges, srf.nedge, srf.verts, srf.nvert};
     const int max_iter = 100000;
@@ -843,6 +973,20 @@ gipc_status ccd_impl(gipc_ctx* ctx, const double* x, const double* d, int64_t n,
     const int ns = vscene ? nscenes : 1;
     fill_kernel<<<nblk(ns, 256), 256, 0, st>>>(amin_d, ns, 1.0);
     unsigned long long* amin = reinterpret_cast<unsigned long long*>(amin_d);
+    if (cached && !vscene && cache_matches(ctx, n, srf, ctx->ccache.dhat)) {
+        double delta = 0.0, dm = 0.0;
+        if ((s = cache_disp(ctx, x, d, n, srf, &delta, &dm, st)) != GIPC_OK) return s;
+        if (2.0 * (delta + dm) * (1.0 + 1e-9) <= ctx->ccache.pad) {
+            const int64_t np = ctx->ccache.np;
+            const int32_t* cq = ctx->slot[C_CPAIRS].as<int32_t>();
+            if (np > 0)
+                ccd_pairs_kernel<<<nblk(np, 128), 128, 0, st>>>(x, d, n, S, cq, cq + np, ctx->ccache.npt, np, slack,
+                                                                 max_iter, nullptr, amin, true);
+            cudaMemcpyAsync(alpha_h, amin_d, sizeof(double), cudaMemcpyDeviceToHost, st);
+            if (cudaStreamSynchronize(st) != cudaSuccess) return check_launch("gipc_ccd_max_step: sync");
+            return check_launch("gipc_ccd_max_step");
+        }
+    }
     Grid Gt{}, Ge{};
     const bool pt = S.nvert > 0 && S.ntri > 0;
     if (pt && (s = build_grid(ctx, 0, x, d, n, S.tris, 3, S.ntri, 0.0, &srf, vscene, nscenes, Gt, st)) != GIPC_OK) return s;
@@ -854,7 +998,8 @@ gipc_status ccd_impl(gipc_ctx* ctx, const double* x, const double* d, int64_t n,
                            st)) != GIPC_OK)
         return s;
     if (np > 0)
-        ccd_pairs_kernel<<<nblk(np, 128), 128, 0, st>>>(x, d, n, S, L.q, L.t, npt, np, slack, max_iter, vscene, amin);
+        ccd_pairs_kernel<<<nblk(np, 128), 128, 0, st>>>(x, d, n, S, L.q, L.t, npt, np, slack, max_iter, vscene, amin,
+                                                         false);
     cudaMemcpyAsync(alpha_h, amin_d, sizeof(double) * ns, cudaMemcpyDeviceToHost, st);
     if (cudaStreamSynchronize(st) != cudaSuccess) return check_launch("gipc_ccd_max_step: sync");
     return check_launch("gipc_ccd_max_step");
@@ -873,7 +1018,7 @@ extern "C" gipc_status gipc_find_contacts(gipc_ctx* ctx, const double* x, const 
         (capacity > 0 && (!stencils || !eps_x)))
         return fail(GIPC_ERR_INVALID_ARG, "gipc_find_contacts: null pointer");
     return find_contacts_impl(ctx, x, rest_x, n, *srf, dhat, stencils, eps_x, capacity, count_h, false, nullptr,
-                              nullptr, (cudaStream_t)stream, 1);
+                              nullptr, (cudaStream_t)stream, 1, false);
 }
 
 extern "C" gipc_status gipc_ccd_max_step(gipc_ctx* ctx, const double* x, const double* d, int64_t n,
@@ -881,5 +1026,5 @@ extern "C" gipc_status gipc_ccd_max_step(gipc_ctx* ctx, const double* x, const d
     using namespace gipc;
     if (!ctx || !srf || !alpha_h || !x || !d) return fail(GIPC_ERR_INVALID_ARG, "gipc_ccd_max_step: null pointer");
     if (n < 0 || !(slack > 0.0 && slack < 1.0)) return fail(GIPC_ERR_INVALID_ARG, "gipc_ccd_max_step: need 0 < slack < 1");
-    return ccd_impl(ctx, x, d, n, *srf, slack, alpha_h, (cudaStream_t)stream, nullptr, 1, nullptr);
+    return ccd_impl(ctx, x, d, n, *srf, slack, alpha_h, (cudaStream_t)stream, nullptr, 1, nullptr, false);
 }

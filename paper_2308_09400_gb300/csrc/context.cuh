@@ -90,13 +90,27 @@ struct gipc_prof_span {
     ~gipc_prof_span() { p.stop(kind, s); }
 };
 
+// Candidate pairs of the contact broad phase kept between the detections of one time step: built
+// with boxes padded by dhat + 2 margin around the positions x_b, they contain every pair closer
+// than dhat at any x with max |x - x_b| <= margin (per axis), and every pair whose swept boxes
+// overlap for a step d with 2 (max |x - x_b| + max |d|) <= dhat + 2 margin.
+struct gipc_contact_cache {
+    bool valid = false;
+    int64_t n = 0, npt = 0, np = 0;          // vertex count, point-triangle pairs, all pairs
+    const int32_t *tris = nullptr, *edges = nullptr, *verts = nullptr;
+    int64_t ntri = 0, nedge = 0, nvert = 0;
+    double dhat = 0.0, margin = 0.0, pad = 0.0;
+};
+
 struct gipc_ctx {
     int device = 0;
-    static constexpr int kSlots = 64;   // assembly 0-8, pcg 9-15 and 40, contacts 16-19, 30-39 and 45-46, time step 20-29, 41-44 and 47-48, derivatives 49-58
+    static constexpr int kSlots = 64;   // assembly 0-8, pcg 9-15 and 40, contacts 16-19, 30-39, 45-46 and 59-60, time step 20-29, 41-44 and 47-48, derivatives 49-58
     gipc_scratch slot[kSlots];
     gipc_profiler prof;
+    gipc_contact_cache ccache;   // filled and used by the time step only
     void release_all() {
         for (auto& s : slot) s.release();
         prof.release();
+        ccache.valid = false;
     }
 };

@@ -28,12 +28,14 @@ namespace gipc {
 
 gipc_status find_contacts_impl(gipc_ctx* ctx, const double* x, const double* rest_x, int64_t n, const gipc_surface& srf,
                                double dhat, int32_t* stencils, double* eps_x, int64_t cap, int64_t* count,
-                               bool compact, const int32_t* vscene, int64_t* npt_out, cudaStream_t st, int nscenes);
+                               bool compact, const int32_t* vscene, int64_t* npt_out, cudaStream_t st, int nscenes,
+                               bool cached);
 gipc_status pcg_impl(gipc_ctx* ctx, const gipc_bsr* A, const double* rhs, double* x, const uint8_t* fixed,
                      const gipc_pcg_params* prm, int* iters_out_h, double* rel_out_h, cudaStream_t st,
                      const int64_t* voff, int nscenes, int* scene_iters_h, int* scene_status_h);
 gipc_status ccd_impl(gipc_ctx* ctx, const double* x, const double* d, int64_t n, const gipc_surface& srf, double slack,
-                     double* alpha_h, cudaStream_t st, const int32_t* vscene, int nscenes, double* amin_dev);
+                     double* alpha_h, cudaStream_t st, const int32_t* vscene, int nscenes, double* amin_dev,
+                     bool cached);
 
 namespace {
 
@@ -510,7 +512,7 @@ gipc_status contacts_at(gipc_ctx* ctx, const gipc_scene& sc, const double* x, do
         *eps = ctx->slot[D_CON].as<double>();
         *sti = reinterpret_cast<int32_t*>(*eps + cap);
         s = find_contacts_impl(ctx, x, sc.rest_x, sc.n, sc.surface, dhat, *sti, *eps, cap, k, true, nullptr, nullptr, st,
-                               1);
+                               1, false);
         if (s != GIPC_ERR_CAPACITY) return s;
         if ((s = ctx->slot[D_CON].reserve((size_t)(*k + *k / 4 + 1024) * (4 * sizeof(int32_t) + sizeof(double)))) !=
             GIPC_OK)
@@ -684,7 +686,7 @@ extern "C" gipc_status gipc_newton_polish(gipc_ctx* ctx, const gipc_scene* sc, d
             break;
         }
         double alpha = 1.0;
-        if ((s = ccd_impl(ctx, x, d, n, sc->surface, 0.1, &alpha, st, nullptr, 1, nullptr)) != GIPC_OK) return s;
+        if ((s = ccd_impl(ctx, x, d, n, sc->surface, 0.1, &alpha, st, nullptr, 1, nullptr, false)) != GIPC_OK) return s;
         step_apply_kernel<<<nbk(m3, 256), 256, 0, st>>>(x, d, std::min(alpha, 1.0), m3);
         converged = alpha >= 1.0 && step <= eps_polish;
     }

@@ -17,9 +17,11 @@ namespace gipc {
 
 gipc_status find_contacts_impl(gipc_ctx* ctx, const double* x, const double* rest_x, int64_t n, const gipc_surface& srf,
                                double dhat, int32_t* stencils, double* eps_x, int64_t cap, int64_t* count,
-                               bool compact, const int32_t* vscene, int64_t* npt_out, cudaStream_t st, int nscenes);
+                               bool compact, const int32_t* vscene, int64_t* npt_out, cudaStream_t st, int nscenes,
+                               bool cached);
 gipc_status ccd_impl(gipc_ctx* ctx, const double* x, const double* d, int64_t n, const gipc_surface& srf, double slack,
-                     double* alpha_h, cudaStream_t st, const int32_t* vscene, int nscenes, double* amin_dev);
+                     double* alpha_h, cudaStream_t st, const int32_t* vscene, int nscenes, double* amin_dev,
+                     bool cached);
 gipc_status pcg_impl(gipc_ctx* ctx, const gipc_bsr* A, const double* rhs, double* x, const uint8_t* fixed,
                      const gipc_pcg_params* prm, int* iters_out_h, double* rel_out_h, cudaStream_t st,
                      const int64_t* voff, int nscenes, int* scene_iters_h, int* scene_status_h);
@@ -172,7 +174,7 @@ struct Step {
         for (int attempt = 0; attempt < 2; ++attempt) {
             int64_t cnt = 0;
             const gipc_status s = find_contacts_impl(ctx, x, sc.rest_x, n, sc.surface, prm.barrier.dhat, cs.st, cs.eps,
-                                                     cs.cap, &cnt, true, nullptr, nullptr, st, 1);
+                                                     cs.cap, &cnt, true, nullptr, nullptr, st, 1, true);
             if (s == GIPC_OK) {
                 cs.k = cnt;
                 return GIPC_OK;
@@ -218,6 +220,9 @@ struct Step {
     gipc_status run(double* x, double* v, gipc_step_stats* stats) {
         const int64_t m3 = 3 * n;
         gipc_status s;
+        // the broad-phase candidates are reused only within this step (the caller may change the
+        // scene between steps)
+        ctx->ccache.valid = false;
         if ((s = ctx->slot[N_VEC].reserve(sizeof(double) * 7 * m3)) != GIPC_OK) return s;
         if ((s = ctx->slot[N_RED].reserve(sizeof(double) * (4 * kRedBlocks + 8))) != GIPC_OK) return s;
         x0 = ctx->slot[N_VEC].as<double>();
@@ -300,7 +305,7 @@ struct Step {
             S.pcg_iters += pit;
             // step filter and backtracking
             double alpha = 1.0;
-            if ((s = ccd_impl(ctx, x, d, n, sc.surface, 0.1, &alpha, st, nullptr, 1, nullptr)) != GIPC_OK) return s;
+            if ((s = ccd_impl(ctx, x, d, n, sc.surface, 0.1, &alpha, st, nullptr, 1, nullptr, true)) != GIPC_OK) return s;
             cudaMemcpyAsync(xp, x, sizeof(double) * m3, cudaMemcpyDeviceToDevice, st);
             const int nxt = 1 - cur;
             double I_new = I_prev;
@@ -631,7 +636,7 @@ struct BatchStep {
         for (int attempt = 0; attempt < 2; ++attempt) {
             int64_t cnt = 0;
             const gipc_status s = find_contacts_impl(ctx, xc, sc.rest_x, n, sc.surface, prm.barrier.dhat, cs.st, cs.eps,
-                                                     cs.cap, &cnt, true, vs, npt, st, ns);
+                                                     cs.cap, &cnt, true, vs, npt, st, ns, false);
             if (s == GIPC_OK) {
                 cs.k = cnt;
                 return GIPC_OK;
@@ -951,7 +956,7 @@ struct BatchStep {
             s = pcg_impl(ctx, &H, rhs, d, mask, &pp, nullptr, nullptr, st, voff, ns, piters.data(), pstat.data());
             if (s != GIPC_OK && s != GIPC_ERR_NOT_CONVERGED) return s;
             // per-scene step filter, then backtracking per scene
-            if ((s = ccd_impl(ctx, x, d, n, sc.surface, 0.1, alpha_h.data(), st, vs, ns, sA)) != GIPC_OK) return s;
+            if ((s = ccd_impl(ctx, x, d, n, sc.surface, 0.1, alpha_h.data(), st, vs, ns, sA, false)) != GIPC_OK) return s;
             for (int q = 0; q < ns; ++q) {
                 accepted[q] = active_h[q] ? 0 : 1;
                 if (active_h[q]) S[map[q]].pcg_iters += piters[q];

@@ -180,3 +180,26 @@ def test_newton_step_mixed_and_rank1_converge_to_the_same_positions(gipc):
         assert C.count_intersections(out[prec], sc0["tris"], sc0["edges"]) == 0
     err = np.abs(out["mixed"] - out["fp64"]).max()
     assert err <= 1e-6 * scene.l, f"converged-position difference {err:.3e}"
+
+
+def test_newton_steps_on_a_ball_grid_keep_the_exact_contact_set(gipc):
+    """Several time steps of balls settling on a floor.  Within a step the time-step driver reuses
+    its broad-phase candidates while the surface stays within their margin.  After every step its
+    contact count must equal a fresh detection at the result, and the result must be free of
+    intersections."""
+    sc = synth.sphere_grid(2, 2, radius=0.05, cells=8, gap=1e-3, floor_cells=6)
+    srf = _surface(gipc, sc)
+    scene = gipc.Scene(_dev(sc["x"]), _dev(sc["tets"]), srf, 1000.0, fixed=_dev(sc["fixed"]), l=sc["l"])
+    mu, lam = gipc.snh_params(1e5, 0.4)
+    dh = 1e-3 * sc["l"]
+    x, v = _dev(sc["x"]), _dev(sc["v"])
+    total_iters = 0
+    for _ in range(4):
+        st = gipc.newton_step(scene, x, v, dt=0.01, mu=mu, lam=lam, dhat=dh, kappa=1e3, eps_d=1e-4, pcg_tol=1e-6,
+                              max_pcg=1000, max_newton=50)
+        total_iters += st["newton_iters"]
+        fresh, _ = gipc.find_contacts(x, scene.rest_x, srf, dh, capacity=None)
+        assert st["contacts"] == fresh.shape[1]
+        xs = x.cpu().numpy()
+        assert C.count_intersections(xs, sc["tris"], sc["edges"]) == 0
+    assert total_iters > 4 and st["contacts"] > 0
