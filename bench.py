@@ -68,6 +68,29 @@ def peaks():
         return HBM_PEAK_FALLBACK, "fallback"
 
 
+# ----------------------------------------------------------------------------- ranks
+def rank_env():
+    """(world, rank, local rank) from the torchrun environment (1, 0, 0 without it)."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def max_over_ranks(value, world, device):
+    """The largest of every rank's value (the job's time is that of its slowest rank)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, ms):
+    """Whole-job throughput: every rank processes its own batch of units_per_rank in (at most) ms."""
+    return units_per_rank * world / (ms * 1e-3)
+
+
 def workload(seed_offset=0):
     import synth
     d = synth.batch_stencils(K_STENCILS, seed=20230810 + seed_offset)
@@ -195,9 +218,7 @@ def run_gpu(args):
     import torch.distributed as dist
     import paper_2308_09400_gb300 as g
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = rank_env()
     if world > 1:
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
@@ -244,10 +265,7 @@ def run_gpu(args):
     for m in all_marks:
         phase += [m[0].elapsed_time(m[1]), m[1].elapsed_time(m[2]), m[2].elapsed_time(m[3])]
     phase /= args.steps
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world, dev)
 
     # e2e: host (pinned) inputs in, Newton direction out, through the public API
     host = {"x": torch.tensor(Wh["x"]).pin_memory(), "st_own": torch.tensor(Wh["st_own"]).pin_memory(),
@@ -269,10 +287,7 @@ def run_gpu(args):
     barrier()
     ctx.profile_stop()
     e2e_ms = e0.elapsed_time(e1) / args.steps
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(e2e_ms, world, dev)
 
     if rank == 0:
         hbm, hbm_src = peaks()
@@ -300,9 +315,8 @@ def run_gpu(args):
         roof["avg_launch_us"] = avg * 1e6
         roof["launches"] = spmv_n
         roof["traffic"] = measured_traffic("pcg_spmv", args.precision)
-        stencils = K_STENCILS * world
         line = {
-            "metric": METRIC, "value": stencils / (ms * 1e-3), "unit": "stencils/s", "n_gpus": world,
+            "metric": METRIC, "value": job_rate(K_STENCILS, world, ms), "unit": "stencils/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
@@ -316,7 +330,7 @@ def run_gpu(args):
             "kernel_ms": {k: (v[1] / max(v[0], 1)) for k, v in prof.items()},
             "linearize_solve_per_s": 1000.0 / ms,
             "roofline": roof,
-            "e2e": {"value": stencils / (e2e_ms * 1e-3), "unit": "stencils/s", "h2d_bytes_per_step": h2d,
+            "e2e": {"value": job_rate(K_STENCILS, world, e2e_ms), "unit": "stencils/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
             "gpu_launches": launches_per_step(n) * args.steps,
             "clocks": clk,
@@ -663,8 +677,7 @@ def cpu_baseline(args, Wh, sample):
 
 
 def run_reference(args):
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
+    world, rank, _ = rank_env()
     if rank != 0:
         return
     Wh = workload()
