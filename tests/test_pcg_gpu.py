@@ -113,6 +113,49 @@ def test_float_pair_product(gipc):
             raise gipc.GipcError("gipc_pcg", st)
 
 
+def _chain_system(n, seed):
+    """Block-tridiagonal SPD system built directly as BSR arrays: diagonal blocks B B^T + 3 I,
+    couplings E_i between vertices i and i+1 (and E_i^T back), |E| small (diagonally dominant)."""
+    rng = np.random.default_rng(seed)
+    B = 0.5 * rng.normal(size=(n, 3, 3))
+    D = B @ np.transpose(B, (0, 2, 1)) + 3.0 * np.eye(3)
+    E = 0.1 * rng.normal(size=(n - 1, 3, 3))
+    cnt = np.full(n, 3)
+    cnt[0] = cnt[-1] = 2
+    rowptr = np.zeros(n + 1, np.int64)
+    rowptr[1:] = np.cumsum(cnt)
+    colidx = np.zeros(rowptr[-1], np.int64)
+    vals = np.zeros((rowptr[-1], 3, 3))
+    i = np.arange(n)
+    pos = rowptr[:-1].copy()
+    lower = i > 0                                   # (i, i-1) = E_{i-1}^T
+    colidx[pos[lower]] = i[lower] - 1
+    vals[pos[lower]] = np.transpose(E, (0, 2, 1))
+    pos[lower] += 1
+    colidx[pos] = i                                 # (i, i)
+    vals[pos] = D
+    pos += 1
+    upper = i < n - 1                               # (i, i+1) = E_i
+    colidx[pos[upper]] = i[upper] + 1
+    vals[pos[upper]] = E
+    b = rng.normal(size=(3, n))
+    return {"rowptr": rowptr, "colidx": colidx, "vals": vals.reshape(-1, 9)}, b
+
+
+def test_large_system_takes_the_split_update_kernels(gipc):
+    """700k block rows: more 256-vertex tiles than the fused update / direction kernel keeps in
+    shared memory, so the solve runs the separate update and direction kernels; iterates after a
+    fixed number of iterations match the oracle's to 1e-10."""
+    n = 700_000
+    R, b = _chain_system(n, seed=45)
+    for iters in (1, 4):
+        ref = P.pcg(R, n, b, tol=0.0, max_iter=iters)
+        x, k, rel = gipc.pcg(_gpu_bsr(R, n), torch.tensor(b, device="cuda"), rel_tol=0.0, max_iter=iters)
+        assert k == iters == ref["iters"]
+        assert np.abs(x.cpu().numpy() - ref["x"]).max() <= 1e-10 * np.abs(ref["x"]).max()
+        assert rel == pytest.approx(ref["rel"], rel=1e-8)
+
+
 def test_nonconvergence_reported(gipc):
     n = 500
     R, b, _, _ = spd_system(n, 2000, 300, seed=44)
