@@ -101,7 +101,8 @@ def workload(seed_offset=0):
 
 def workload_desc(args):
     return (f"C1 batch: {K_STENCILS} stencils (own-vertex geometry, 3.7M vertex slots) -> "
-            f"{args.hess_mode} {'FP64' if args.precision == 'fp64' else 'FP32'} Hessian blocks -> BSR over "
+            f"{args.hess_mode} {'FP64' if args.precision == 'fp64' else 'FP32'} Hessian blocks"
+            f"{' (stored as element-major 3x3 sub-blocks)' if args.hess_mode == 'dense' else ''} -> BSR over "
             f"2x388x388 two-sheet index space (stencils of each type in cell order) -> {PCG_ITERS} PCG iterations")
 
 
@@ -162,12 +163,15 @@ def gpu_step(g, dev, W, args, bufs, ctx):
     marks = [ev(enable_timing=True) for _ in range(4)]
     marks[0].record()
     eps = g.compute_eps_x(W["x"], W["st_own"], out=bufs["eps"])
+    # dense blocks are written element-major as 3x3 sub-blocks (GIPC_HESS_BLOCKS): the same
+    # values, contiguous for the assembly's per-contribution reads
+    mode = "blocks" if args.hess_mode == "dense" else args.hess_mode
     e = g.eval_stencils(W["x"], W["st_own"], eps, W["dhat"], KAPPA, precision=args.precision,
-                        mode=args.hess_mode, want=("energy", "grad", "hess", "lam", "flags")
+                        mode=mode, want=("energy", "grad", "hess", "lam", "flags")
                         if args.hess_mode == "rank1" else ("energy", "grad", "hess", "flags"), out=bufs["eval"])
     bufs["eval"] = e
     marks[1].record()
-    A = g.assemble_bsr(W["n"], stencils=W["st_sheet"], stencil_hess=e["hess"], stencil_mode=args.hess_mode,
+    A = g.assemble_bsr(W["n"], stencils=W["st_sheet"], stencil_hess=e["hess"], stencil_mode=mode,
                        stencil_lam=e.get("lam"), stencil_grad=e["grad"], mass=W["mass"],
                        precision=args.precision, out=bufs["bsr"], ctx=ctx)
     bufs["bsr"] = {"rowptr": A["rowptr"], "colidx": A["colidx"], "vals": A["vals"], "grad": A["grad"]}
@@ -179,16 +183,24 @@ def gpu_step(g, dev, W, args, bufs, ctx):
     return d, A, marks
 
 
-def launches_per_step(n):
-    tiles = (n + 1 + 4095) // 4096
-    scan = 1 if n + 1 <= 4096 else (3 if tiles <= 4096 else 5)
-    assembly = 11 + 2 * scan      # init, count, init_cursor, fill, 2 sorts, rowptr32, emit, seg_end, grad_init, values
-    nck = 64 * ((n + 1023) // 1024)
-    perm = 2 + (1 if nck <= 4096 else (3 if (nck + 4095) // 4096 <= 4096 else 5))  # row-length sort
-    nsl = (n + 9) // 10
-    sell = 2 + (1 if nsl <= 4096 else (3 if (nsl + 4095) // 4096 <= 4096 else 5))       # sliced layout
-    pcg = perm + sell + 6 + 3 * PCG_ITERS + 1  # set, 2 conversions, factor, spmv(x0), init, 3/iteration, back
-    return 2 + assembly + pcg
+def _scan_launches(m):
+    """Kernels of one device-wide exclusive scan of m items (4096 per tile, recursive totals)."""
+    return 1 if m <= 4096 else 2 + _scan_launches((m + 4095) // 4096)
+
+
+def launches_per_step(n, sms=152):
+    """The library's kernel launches in one C1 step (the sequence a launch list shows).
+
+    eps_x + evaluation; assembly: row init, count, cursor init, fill, three row sorts, rowptr,
+    emit, segment end, gradient init, values, and two scans over the n rows; solver: row-length
+    histogram + scatter (+ scan of the 64 buckets x 1024-row chunks), slice lengths + fill (+ scan
+    of the SELL-32 slices), scalars, two layout conversions, factors, the first product, setup, the
+    final layout conversion, and per iteration the product plus the fused update / direction (the
+    separate update and direction when the fused kernel's tiles do not fit: 8 x 256 vertices per
+    CTA, 2 CTAs per SM)."""
+    scans = 2 * _scan_launches(n) + _scan_launches(64 * ((n + 1023) // 1024)) + _scan_launches((n + 31) // 32)
+    fused = (n + 255) // 256 <= 8 * 2 * sms
+    return 2 + 12 + 11 + scans + (2 if fused else 3) * PCG_ITERS
 
 
 def source_hash(*rel):
@@ -336,7 +348,7 @@ def run_gpu(args):
             "clocks": clk,
         }
         if args.precision == "fp64" and args.hess_mode == "dense" and args.product == "native":
-            line["float_pair_product"] = run_float_pair(g, dev, W, args, bufs, ctx, d, bytes_l, hbm)
+            line["float_pair_product"] = run_float_pair(g, dev, W, args, bufs, ctx, bytes_l, hbm)
         if args.newton_steps > 0:
             line["newton"] = run_newton(g, dev, ctx, args.newton_steps, args.c2_steps)
         if args.batch_steps > 0:
@@ -350,13 +362,15 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
-def run_float_pair(g, dev, W, args, bufs, ctx, d_native, bytes_l, hbm):
+def run_float_pair(g, dev, W, args, bufs, ctx, bytes_l, hbm):
     """The same C1 step with the solver's H c in double-float arithmetic (gipc_product
     GIPC_PRODUCT_FLOAT_PAIR): time per step, the SpMV against the HBM roof (same bytes as FP64),
     and the Newton direction's deviation from the native FP64 result after the same iterations."""
     import argparse
     import torch
     a2 = argparse.Namespace(**dict(vars(args), product="float_pair"))
+    d_native, _, _ = gpu_step(g, dev, W, args, bufs, ctx)   # the native solve of the same inputs
+    d_native = d_native.clone()
     for _ in range(2):
         d2, _, _ = gpu_step(g, dev, W, a2, bufs, ctx)
     torch.cuda.synchronize()
@@ -372,7 +386,6 @@ def run_float_pair(g, dev, W, args, bufs, ctx, d_native, bytes_l, hbm):
     ms = e0.elapsed_time(e1) / args.steps
     spmv_n, spmv_ms = prof["pcg_spmv"]
     avg = spmv_ms / max(spmv_n, 1) * 1e-3
-    d_native = d_native.clone()
     ok = bool(torch.isfinite(d_native).all().item()) and bool(torch.isfinite(d2).all().item())
     dev_rel = ((d2 - d_native).abs().max() / d_native.abs().max()).item() if ok else float("nan")
     return {"ms_per_step": ms, "stencils_per_s": K_STENCILS / (ms * 1e-3),

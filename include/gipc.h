@@ -40,7 +40,9 @@ typedef enum {
     GIPC_ERR_NOT_CONVERGED = -4, /* an iteration cap was reached                         */
     GIPC_ERR_NONFINITE = -5,     /* a NaN or Inf was detected in device data             */
     GIPC_ERR_TIMEOUT = -6,       /* a bounded device wait expired                        */
-    GIPC_ERR_CAPACITY = -7       /* an output buffer is smaller than the result          */
+    GIPC_ERR_CAPACITY = -7,      /* an output buffer is smaller than the result          */
+    GIPC_ERR_INDEFINITE = -8     /* the solver met c . H c <= 0: H is not positive definite
+                                  * on the free coordinates (the last iterate is returned) */
 } gipc_status;
 
 /* Contact stencil types.  The type is carried by the signs of the stencil's
@@ -75,7 +77,11 @@ typedef enum { GIPC_FP64 = 0, GIPC_MIXED = 1 } gipc_precision;
 
 typedef enum {
     GIPC_HESS_DENSE = 0,   /* the full 3s x 3s block per stencil                        */
-    GIPC_HESS_RANK1 = 1    /* (lambda, w) with block = lambda * w w^T                    */
+    GIPC_HESS_RANK1 = 1,   /* (lambda, w) with block = lambda * w w^T                    */
+    GIPC_HESS_BLOCKS = 2   /* the same dense values, element-major as 16 contiguous 3x3
+                            * sub-blocks: entry (3a+i, 3b+j) of element e at
+                            * [(e * 16 + 4a + b) * 9 + 3i + j] ([count][16][9]; the
+                            * sub-blocks of slots >= s are not written)                */
 } gipc_hess_mode;
 
 /* Parameters of the barrier (paper Sec. 5.3-5.4, 6.1).  Lengths are in the
@@ -136,10 +142,11 @@ gipc_status gipc_compute_eps_x(const double* rest_x, int64_t n, const int32_t* s
  *              holds no parallel types (then eps_x = 0: mollifier inactive)
  *   prm_h      barrier parameters (host)
  *   prec       GIPC_FP64, or GIPC_MIXED (Hessian blocks / w written as float32)
- *   mode       GIPC_HESS_DENSE or GIPC_HESS_RANK1
+ *   mode       GIPC_HESS_DENSE, GIPC_HESS_BLOCKS or GIPC_HESS_RANK1
  *   energy     float64 [k] or NULL
  *   grad       float64 [12][k] or NULL; entries j < 3s used (slot-major x,y,z)
  *   hess       DENSE: [144][k] entries a*3s+b for a, b < 3s (row-major block);
+ *              BLOCKS: [k][16][9], the same values as 3x3 sub-blocks (see the enum);
  *              RANK1: [12][k] holding w (entries j < 3s);
  *              float64 for GIPC_FP64, float32 for GIPC_MIXED; or NULL
  *   lam        float64 [k] (RANK1 only; kappa * lambda) or NULL
@@ -185,13 +192,15 @@ gipc_status gipc_tet_rest(gipc_ctx* ctx, const double* rest_x, int64_t n, const 
  * (twist, flip and scaling modes from a rotation-variant SVD of F), keeping the modes
  * with positive eigenvalues.
  *   energy float64 [T] or NULL; grad float64 [12][T] or NULL;
- *   hess   [144][T] (row-major 12x12, vertex-major x,y,z), float64 (GIPC_FP64) or
- *          float32 (GIPC_MIXED; computed in float64, stored in float32), or NULL
+ *   hess_mode  GIPC_HESS_DENSE: hess [144][T] (row-major 12x12, vertex-major x,y,z);
+ *              GIPC_HESS_BLOCKS: hess [T][16][9] (3x3 sub-blocks, see the enum)
+ *   hess   float64 (GIPC_FP64), or float32 (GIPC_MIXED: the projection computed in float32
+ *          arithmetic; energy and gradient stay float64), or NULL
  * A tetrahedron with a vertex id outside [0, n) gets energy 0 and no other output.
  * Errors: GIPC_ERR_INVALID_ARG, GIPC_ERR_CUDA. */
 gipc_status gipc_eval_tets(const double* x, int64_t n, const int32_t* tets, int64_t T, const double* Dm_inv,
-                           const double* vol, const gipc_elastic_params* prm_h, int prec, double* energy,
-                           double* grad, void* hess, void* stream);
+                           const double* vol, const gipc_elastic_params* prm_h, int prec, int hess_mode,
+                           double* energy, double* grad, void* hess, void* stream);
 
 /* ------------------------------------------------------------------ assembly */
 
@@ -213,7 +222,8 @@ typedef struct {
 typedef struct {
     const int32_t* idx;   /* stencils: int32 [4][count] sign-encoded; tets: int32 [4][count] vertex ids */
     int64_t count;
-    int hess_mode;        /* GIPC_HESS_DENSE ([144][count]) or, stencils only, GIPC_HESS_RANK1     */
+    int hess_mode;        /* GIPC_HESS_DENSE ([144][count]), GIPC_HESS_BLOCKS ([count][16][9]) or,
+                           * stencils only, GIPC_HESS_RANK1                                         */
     const void* hess;     /* dense blocks or w [12][count]; float64 / float32 as the BSR's prec     */
     const double* lam;    /* RANK1: lambda [count] (block = lam * w w^T)                              */
     const double* grad;   /* float64 [12][count] element gradients, or NULL                          */
@@ -264,8 +274,13 @@ typedef struct {
     int max_iter;      /* iteration cap (>= 0)                                                        */
     int check_every;   /* host checks for convergence every this many iterations; 0 = automatic       */
     int product;       /* gipc_product of H c (0: native)                                              */
-    int reserved;      /* 0                                                                            */
+    int flags;         /* 0, or GIPC_PCG_STOP_ON_INDEFINITE                                             */
 } gipc_pcg_params;
+
+/* gipc_pcg_params.flags: stop with GIPC_ERR_INDEFINITE when a search direction has c . H c <= 0
+ * (one system; ignored by batched solves).  Off by default: the paper's modified PCG continues,
+ * and near its rounding floor a float32 product can give c . H c <= 0 for a positive definite H. */
+#define GIPC_PCG_STOP_ON_INDEFINITE 1
 
 /* Solve H x = rhs by modified PCG with a 3x3 block-Jacobi preconditioner
  * (paper Sec. 7.2 "Parallel solver optimizations" and "Preconditioning of the
@@ -289,8 +304,10 @@ typedef struct {
  * results.  Synchronises the stream at the end (and every check_every
  * iterations when rel_tol > 0).
  * Errors: GIPC_ERR_INVALID_ARG; GIPC_ERR_NOT_CONVERGED (rel_tol > 0 and the cap
- * was reached; x holds the last iterate); GIPC_ERR_NONFINITE; GIPC_ERR_OOM;
- * GIPC_ERR_CUDA. */
+ * was reached; x holds the last iterate); GIPC_ERR_INDEFINITE (with
+ * GIPC_PCG_STOP_ON_INDEFINITE: c . H c <= 0 for a search direction, H is not positive
+ * definite on the free coordinates; x holds the last iterate); GIPC_ERR_NONFINITE;
+ * GIPC_ERR_OOM; GIPC_ERR_CUDA. */
 gipc_status gipc_pcg(gipc_ctx* ctx, const gipc_bsr* A_h, const double* rhs, double* x,
                      const uint8_t* fixed, const gipc_pcg_params* prm_h, int* iters_out_h,
                      double* rel_out_h, void* stream);
@@ -509,7 +526,9 @@ gipc_status gipc_potential_hessian(gipc_ctx* ctx, const gipc_scene* sc_h, const 
  *   *adj_logE_h += -lambda . dI_elastic/dx        (= E dL/dE: Psi is linear in E at fixed nu)
  * adj_x_new / adj_v_new may be NULL (zero); adj_x_old / adj_v_old may be NULL (not written).
  * x_new must be a converged step of gipc_newton_step with the same parameters.  Synchronises.
- * Errors: GIPC_ERR_INVALID_ARG, GIPC_ERR_NOT_CONVERGED (the adjoint solve), GIPC_ERR_OOM,
+ * Errors: GIPC_ERR_INVALID_ARG, GIPC_ERR_NOT_CONVERGED (the adjoint solve), GIPC_ERR_INDEFINITE
+ * (the exact Hessian at x_new is not positive definite: x_new is not a converged minimiser; refine
+ * it with gipc_newton_polish), GIPC_ERR_OOM,
  * GIPC_ERR_CUDA. */
 gipc_status gipc_adjoint_step(gipc_ctx* ctx, const gipc_scene* sc_h, const double* x_new, const double* x_old,
                               const double* v_old, const gipc_step_params* prm_h, const double* adj_x_new,

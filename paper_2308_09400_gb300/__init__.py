@@ -59,7 +59,8 @@ def eval_stencils(x, stencils, eps_x, dhat, kappa, d_thr_ratio=0.1, precision="f
     """Barrier energy / gradient / projected Hessian per stencil (gipc_eval_stencils).
 
     Returns a dict with the requested entries: energy [k] f64, grad [12, k] f64,
-    hess [144, k] (dense) or [12, k] (rank1: w), lam [k] (rank1), flags [k] u8.
+    hess [144, k] (dense), [k, 144] (blocks: each stencil's 3x3 sub-blocks contiguous) or [12, k]
+    (rank1: w), lam [k] (rank1), flags [k] u8.
     Hessian tensors are float64 for precision='fp64' and float32 for 'mixed'.
     ``out`` may supply preallocated tensors under the same keys.
     """
@@ -69,7 +70,7 @@ def eval_stencils(x, stencils, eps_x, dhat, kappa, d_thr_ratio=0.1, precision="f
     if eps_x is not None:
         _check(eps_x, "eps_x", torch.float64)
     prec = {"fp64": _abi.GIPC_FP64, "mixed": _abi.GIPC_MIXED}[precision]
-    md = {"dense": _abi.GIPC_HESS_DENSE, "rank1": _abi.GIPC_HESS_RANK1}[mode]
+    md = {"dense": _abi.GIPC_HESS_DENSE, "rank1": _abi.GIPC_HESS_RANK1, "blocks": _abi.GIPC_HESS_BLOCKS}[mode]
     hdt = torch.float64 if prec == _abi.GIPC_FP64 else torch.float32
     dev = x.device
     out = dict(out or {})
@@ -77,7 +78,8 @@ def eval_stencils(x, stencils, eps_x, dhat, kappa, d_thr_ratio=0.1, precision="f
     if md == _abi.GIPC_HESS_RANK1 and "hess" in want:
         want.add("lam")
     shapes = {"energy": ((k,), torch.float64), "grad": ((12, k), torch.float64),
-              "hess": (((144 if md == _abi.GIPC_HESS_DENSE else 12), k), hdt),
+              "hess": ({_abi.GIPC_HESS_DENSE: (144, k), _abi.GIPC_HESS_BLOCKS: (k, 144), _abi.GIPC_HESS_RANK1: (12, k)}[md],
+                       hdt),
               "lam": ((k,), torch.float64), "flags": ((k,), torch.uint8)}
     for key in want:
         if key not in out:
@@ -150,7 +152,7 @@ def _elements(idx, blocks, mode, lam, grad):
     if idx is None:
         return None
     _check(idx, "element indices", torch.int32, 4)
-    return _abi.Elements(idx.data_ptr(), idx.shape[1], {"dense": 0, "rank1": 1}[mode],
+    return _abi.Elements(idx.data_ptr(), idx.shape[1], {"dense": 0, "rank1": 1, "blocks": 2}[mode],
                          blocks.data_ptr() if blocks is not None else 0,
                          lam.data_ptr() if lam is not None else 0,
                          grad.data_ptr() if grad is not None else 0)
@@ -158,18 +160,20 @@ def _elements(idx, blocks, mode, lam, grad):
 
 def assemble_bsr(n, stencils=None, stencil_hess=None, stencil_mode="dense", stencil_lam=None,
                  stencil_grad=None, tets=None, tet_hess=None, tet_grad=None, mass=None, grad_base=None,
-                 precision="fp64", want_grad=True, capacity=None, ctx=None, stream=None, out=None):
+                 precision="fp64", want_grad=True, capacity=None, ctx=None, stream=None, out=None, tet_mode="dense"):
     """Assemble the BSR Hessian and the gradient (gipc_assemble_bsr).
 
     Returns dict(rowptr [n+1] i32, colidx [nnzb] i32, vals [nnzb, 9] f64/f32, grad [3, n] f64, nnzb).
     ``out`` may hold preallocated colidx/vals (capacity = their length) and rowptr/grad.
+    ``stencil_mode`` / ``tet_mode`` name the layout the blocks come in ("dense", "blocks", and for
+    stencils "rank1").
     """
     ctx = ctx or default_context()
     dev = torch.device("cuda", torch.cuda.current_device())
     prec = {"fp64": _abi.GIPC_FP64, "mixed": _abi.GIPC_MIXED}[precision]
     vdt = torch.float64 if prec == _abi.GIPC_FP64 else torch.float32
     se = _elements(stencils, stencil_hess, stencil_mode, stencil_lam, stencil_grad)
-    te = _elements(tets, tet_hess, "dense", None, tet_grad)
+    te = _elements(tets, tet_hess, tet_mode, None, tet_grad)
     ne = (0 if stencils is None else stencils.shape[1]) + (0 if tets is None else tets.shape[1])
     out = dict(out or {})
     rowptr = out.get("rowptr")
@@ -208,13 +212,14 @@ def _bsr_struct(A):
 
 
 def pcg(A, rhs, x0=None, fixed=None, rel_tol=1e-4, max_iter=1000, check_every=0, raise_on_nonconvergence=False,
-        product="native", ctx=None, stream=None):
+        product="native", stop_on_indefinite=False, ctx=None, stream=None):
     """Modified block-Jacobi PCG on an assembled BSR (gipc_pcg).
 
     ``A`` is the dict returned by ``assemble_bsr``; ``rhs`` float64 [3, n].  Returns
     (x [3, n], iterations, delta_new / delta_0).  A capped solve with rel_tol > 0
     returns its last iterate unless ``raise_on_nonconvergence``.  ``product`` selects the
-    arithmetic of H c for FP64 matrices: "native" or "float_pair" (gipc_product).
+    arithmetic of H c for FP64 matrices: "native" or "float_pair" (gipc_product).  With
+    ``stop_on_indefinite`` a direction with c.Hc <= 0 raises GipcError (GIPC_ERR_INDEFINITE).
     """
     ctx = ctx or default_context()
     n = A["n"]
@@ -224,7 +229,8 @@ def pcg(A, rhs, x0=None, fixed=None, rel_tol=1e-4, max_iter=1000, check_every=0,
         _check(fixed, "fixed", torch.uint8)
     bsr = _bsr_struct(A)
     prm = _abi.PcgParams(float(rel_tol), int(max_iter), int(check_every),
-                         {"native": _abi.GIPC_PRODUCT_NATIVE, "float_pair": _abi.GIPC_PRODUCT_FLOAT_PAIR}[product])
+                         {"native": _abi.GIPC_PRODUCT_NATIVE, "float_pair": _abi.GIPC_PRODUCT_FLOAT_PAIR}[product],
+                         _abi.GIPC_PCG_STOP_ON_INDEFINITE if stop_on_indefinite else 0)
     iters = ctypes.c_int(0)
     rel = ctypes.c_double(0.0)
     st = _abi.call_status("gipc_pcg", ctx.handle, ctypes.byref(bsr), _ptr(rhs), _ptr(x), _ptr(fixed),
@@ -284,20 +290,25 @@ def tet_rest(rest_x, tets, density=None, ctx=None, stream=None):
 
 
 def eval_tets(x, tets, Dm_inv, vol, mu, lam, scale, precision="fp64", want=("energy", "grad", "hess"),
-              out=None, stream=None):
-    """Stable neo-Hookean energy / gradient / projected Hessian per tetrahedron (gipc_eval_tets)."""
+              layout="dense", out=None, stream=None):
+    """Stable neo-Hookean energy / gradient / projected Hessian per tetrahedron (gipc_eval_tets).
+
+    ``layout`` "dense": hess [144, T] entry-major; "blocks": hess [T, 144] holding the 16 3x3
+    sub-blocks of each element contiguously (GIPC_HESS_BLOCKS)."""
     _check(x, "x", torch.float64, 3)
     _check(tets, "tets", torch.int32, 4)
     n, T = x.shape[1], tets.shape[1]
     prec = {"fp64": _abi.GIPC_FP64, "mixed": _abi.GIPC_MIXED}[precision]
     hdt = torch.float64 if prec == _abi.GIPC_FP64 else torch.float32
     out = dict(out or {})
-    shapes = {"energy": ((T,), torch.float64), "grad": ((12, T), torch.float64), "hess": ((144, T), hdt)}
+    hm = {"dense": _abi.GIPC_HESS_DENSE, "blocks": _abi.GIPC_HESS_BLOCKS}[layout]
+    shapes = {"energy": ((T,), torch.float64), "grad": ((12, T), torch.float64),
+              "hess": (((144, T) if hm == _abi.GIPC_HESS_DENSE else (T, 144)), hdt)}
     for key in set(want) | set(out):
         if key not in out:
             out[key] = torch.zeros(shapes[key][0], dtype=shapes[key][1], device=x.device)
     prm = _abi.ElasticParams(float(mu), float(lam), float(scale))
-    _abi.call("gipc_eval_tets", _ptr(x), n, _ptr(tets), T, _ptr(Dm_inv), _ptr(vol), ctypes.byref(prm), prec,
+    _abi.call("gipc_eval_tets", _ptr(x), n, _ptr(tets), T, _ptr(Dm_inv), _ptr(vol), ctypes.byref(prm), prec, hm,
               _ptr(out.get("energy")), _ptr(out.get("grad")), _ptr(out.get("hess")), _stream(stream))
     return out
 

@@ -11,11 +11,12 @@ from .build import LIB
 GIPC_OK = 0
 STATUS_NAMES = {0: "GIPC_OK", -1: "GIPC_ERR_INVALID_ARG", -2: "GIPC_ERR_CUDA", -3: "GIPC_ERR_OOM",
                 -4: "GIPC_ERR_NOT_CONVERGED", -5: "GIPC_ERR_NONFINITE", -6: "GIPC_ERR_TIMEOUT",
-                -7: "GIPC_ERR_CAPACITY"}
+                -7: "GIPC_ERR_CAPACITY", -8: "GIPC_ERR_INDEFINITE"}
 
 GIPC_FP64, GIPC_MIXED = 0, 1
-GIPC_HESS_DENSE, GIPC_HESS_RANK1 = 0, 1
+GIPC_HESS_DENSE, GIPC_HESS_RANK1, GIPC_HESS_BLOCKS = 0, 1, 2
 GIPC_PRODUCT_NATIVE, GIPC_PRODUCT_FLOAT_PAIR = 0, 1
+GIPC_PCG_STOP_ON_INDEFINITE = 1
 
 FLAG_ACTIVE, FLAG_FILTERED, FLAG_MOLLIFIED, FLAG_INVALID = 0x01, 0x02, 0x04, 0x80
 
@@ -41,7 +42,7 @@ class ElasticParams(ctypes.Structure):
 
 class PcgParams(ctypes.Structure):
     _fields_ = [("rel_tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("check_every", ctypes.c_int),
-                ("product", ctypes.c_int), ("reserved", ctypes.c_int)]
+                ("product", ctypes.c_int), ("flags", ctypes.c_int)]
 
 
 class Surface(ctypes.Structure):
@@ -95,7 +96,7 @@ SIGNATURES = {
                                   _P, _P, _P, _P, _P, _P]),
     "gipc_snh_params": (_INT, [_D, _D, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     "gipc_tet_rest": (_INT, [_P, _P, _I64, _P, _I64, _D, _P, _P, _P, _P]),
-    "gipc_eval_tets": (_INT, [_P, _I64, _P, _I64, _P, _P, ctypes.POINTER(ElasticParams), _INT, _P, _P, _P, _P]),
+    "gipc_eval_tets": (_INT, [_P, _I64, _P, _I64, _P, _P, ctypes.POINTER(ElasticParams), _INT, _INT, _P, _P, _P, _P]),
     "gipc_assemble_bsr": (_INT, [_P, _I64, ctypes.POINTER(Elements), ctypes.POINTER(Elements), _P, _P,
                                  ctypes.POINTER(Bsr), _P, _P]),
     "gipc_pcg": (_INT, [_P, ctypes.POINTER(Bsr), _P, _P, _P, ctypes.POINTER(PcgParams),
@@ -149,6 +150,7 @@ def lib():
 
 
 GIPC_ERR_CAPACITY = -7
+GIPC_ERR_INDEFINITE = -8
 GIPC_ERR_NOT_CONVERGED = -4
 
 

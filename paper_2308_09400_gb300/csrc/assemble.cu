@@ -351,14 +351,21 @@ __global__ void values_kernel(const uint64_t* __restrict__ keys, const int64_t* 
             const ElemList& Lst = is_tet ? tets : sts;
             const int64_t el = is_tet ? e : e - tets.count;
             const int64_t cnt = Lst.count;
-            const int n3 = elem_n3[e];
             if (Lst.mode == GIPC_HESS_DENSE) {
+                const int n3 = elem_n3[e];
                 const VT* H = static_cast<const VT*>(Lst.hess);
 #pragma unroll
                 for (int i = 0; i < 3; ++i)
 #pragma unroll
                     for (int j = 0; j < 3; ++j)
                         acc[3 * i + j] = add_rn(acc[3 * i + j], H[(int64_t)((3 * a + i) * n3 + 3 * bb + j) * cnt + el]);
+            } else if (Lst.mode == GIPC_HESS_BLOCKS) {   // the 9 values are contiguous
+                const VT* H = static_cast<const VT*>(Lst.hess) + (el * 16 + a * 4 + bb) * 9;
+                VT h[9];
+#pragma unroll
+                for (int q = 0; q < 9; ++q) h[q] = H[q];
+#pragma unroll
+                for (int q = 0; q < 9; ++q) acc[q] = add_rn(acc[q], h[q]);
             } else {
                 const VT* W = static_cast<const VT*>(Lst.hess);
                 const VT lam = (VT)Lst.lam[el];
@@ -448,9 +455,9 @@ extern "C" gipc_status gipc_assemble_bsr(gipc_ctx* ctx, int64_t n, const gipc_el
         const gipc_elements& E = *in[q];
         if (E.count < 0) return fail(GIPC_ERR_INVALID_ARG, "gipc_assemble_bsr: negative element count");
         if (!E.idx || !E.hess) return fail(GIPC_ERR_INVALID_ARG, "gipc_assemble_bsr: null element indices/blocks");
-        if (E.hess_mode != GIPC_HESS_DENSE && E.hess_mode != GIPC_HESS_RANK1)
+        if (E.hess_mode != GIPC_HESS_DENSE && E.hess_mode != GIPC_HESS_RANK1 && E.hess_mode != GIPC_HESS_BLOCKS)
             return fail(GIPC_ERR_INVALID_ARG, "gipc_assemble_bsr: unknown Hessian mode");
-        if (q == 0 && E.hess_mode != GIPC_HESS_DENSE)
+        if (q == 0 && E.hess_mode == GIPC_HESS_RANK1)
             return fail(GIPC_ERR_INVALID_ARG, "gipc_assemble_bsr: tetrahedra need dense blocks");
         if (E.hess_mode == GIPC_HESS_RANK1 && !E.lam)
             return fail(GIPC_ERR_INVALID_ARG, "gipc_assemble_bsr: rank-one blocks need lam");

@@ -605,7 +605,7 @@ extern "C" gipc_status gipc_adjoint_step(gipc_ctx* ctx, const gipc_scene* sc, co
     double* red = gel + m3;
     adjoint_rhs_kernel<<<nbk(m3, 256), 256, 0, st>>>(adj_x_new, adj_v_new, sc->fixed, n, prm->dt, a);
     cudaMemsetAsync(lam, 0, sizeof(double) * m3, st);
-    gipc_pcg_params pp{prm->pcg_tol, std::max(prm->max_pcg, 1), 0};
+    gipc_pcg_params pp{prm->pcg_tol, std::max(prm->max_pcg, 1), 0, GIPC_PRODUCT_NATIVE, GIPC_PCG_STOP_ON_INDEFINITE};
     int pit = 0;
     const gipc_status ps = pcg_impl(ctx, &H, a, lam, sc->fixed, &pp, &pit, nullptr, st, nullptr, 1, nullptr, nullptr);
     if (pcg_iters_h) *pcg_iters_h = pit;
@@ -669,11 +669,12 @@ extern "C" gipc_status gipc_newton_polish(gipc_ctx* ctx, const gipc_scene* sc, d
         if ((s = exact_hessian(ctx, *sc, x, sti, eps, k, prm->barrier, ep, &H, st)) != GIPC_OK) return s;
         neg_free_kernel<<<nbk(m3, 256), 256, 0, st>>>(g, sc->fixed, n, rhs);
         cudaMemsetAsync(d, 0, sizeof(double) * m3, st);
-        gipc_pcg_params pp{prm->pcg_tol, std::max(prm->max_pcg, 1), 0};
+        gipc_pcg_params pp{prm->pcg_tol, std::max(prm->max_pcg, 1), 0, GIPC_PRODUCT_NATIVE, GIPC_PCG_STOP_ON_INDEFINITE};
         const gipc_status ps = pcg_impl(ctx, &H, rhs, d, sc->fixed, &pp, nullptr, nullptr, st, nullptr, 1, nullptr, nullptr);
-        if (ps != GIPC_OK && ps != GIPC_ERR_NOT_CONVERGED) return ps;
+        if (ps != GIPC_OK && ps != GIPC_ERR_NOT_CONVERGED && ps != GIPC_ERR_INDEFINITE) return ps;
         // a Newton direction of the exact Hessian descends only where that Hessian is positive
-        // definite: stop (leaving x as it is) when it does not
+        // definite: stop (leaving x as it is) when it is not, or when the direction does not descend
+        if (ps == GIPC_ERR_INDEFINITE) break;
         dot_kernel<<<1, 1024, 0, st>>>(g, d, m3, red);
         maxabs_kernel<<<1, 1024, 0, st>>>(d, m3, red + 1);
         double h[2] = {0.0, 0.0};

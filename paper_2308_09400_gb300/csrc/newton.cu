@@ -201,7 +201,7 @@ struct Step {
         double* se = te + T;
         gipc_elastic_params ep = prm.elastic;
         ep.scale = prm.dt * prm.dt;
-        if ((s = gipc_eval_tets(x, n, sc.tets, T, sc.Dm_inv, sc.vol, &ep, GIPC_FP64, te, nullptr, nullptr, st)) != GIPC_OK)
+        if ((s = gipc_eval_tets(x, n, sc.tets, T, sc.Dm_inv, sc.vol, &ep, GIPC_FP64, GIPC_HESS_DENSE, te, nullptr, nullptr, st)) != GIPC_OK)
             return s;
         if (k > 0 && (s = gipc_eval_stencils(x, n, cs.st, k, cs.eps, &prm.barrier, GIPC_FP64, GIPC_HESS_DENSE, se, nullptr,
                                              nullptr, nullptr, nullptr, st)) != GIPC_OK)
@@ -260,7 +260,7 @@ struct Step {
             void* th = tg + 12 * (int64_t)T;
             gipc_elastic_params ep = prm.elastic;
             ep.scale = dt * dt;
-            if ((s = gipc_eval_tets(x, n, sc.tets, T, sc.Dm_inv, sc.vol, &ep, prm.prec, nullptr, tg, th, st)) != GIPC_OK)
+            if ((s = gipc_eval_tets(x, n, sc.tets, T, sc.Dm_inv, sc.vol, &ep, prm.prec, GIPC_HESS_DENSE, nullptr, tg, th, st)) != GIPC_OK)
                 return s;
             const bool rank1 = prm.hess_mode == GIPC_HESS_RANK1;
             const int64_t hper = rank1 ? 12 : 144;
@@ -663,7 +663,7 @@ struct BatchStep {
         double* se = te + T;
         gipc_elastic_params ep = prm.elastic;
         ep.scale = prm.dt * prm.dt;
-        if ((s = gipc_eval_tets(xc, n, sc.tets, T, sc.Dm_inv, sc.vol, &ep, GIPC_FP64, te, nullptr, nullptr, st)) != GIPC_OK)
+        if ((s = gipc_eval_tets(xc, n, sc.tets, T, sc.Dm_inv, sc.vol, &ep, GIPC_FP64, GIPC_HESS_DENSE, te, nullptr, nullptr, st)) != GIPC_OK)
             return s;
         if (k > 0 && (s = gipc_eval_stencils(xc, n, cs.st, k, cs.eps, &prm.barrier, GIPC_FP64, GIPC_HESS_DENSE, se, nullptr,
                                              nullptr, nullptr, nullptr, st)) != GIPC_OK)
@@ -913,7 +913,7 @@ struct BatchStep {
             void* th = tg + 12 * (int64_t)T;
             gipc_elastic_params ep = prm.elastic;
             ep.scale = dt * dt;
-            if ((s = gipc_eval_tets(x, n, sc.tets, T, sc.Dm_inv, sc.vol, &ep, prm.prec, nullptr, tg, th, st)) != GIPC_OK)
+            if ((s = gipc_eval_tets(x, n, sc.tets, T, sc.Dm_inv, sc.vol, &ep, prm.prec, GIPC_HESS_DENSE, nullptr, tg, th, st)) != GIPC_OK)
                 return s;
             const bool rank1 = prm.hess_mode == GIPC_HESS_RANK1;
             const int64_t hper = rank1 ? 12 : 144;

@@ -57,6 +57,7 @@ constexpr int kPermChunk = 1024;  // rows per block of the stable bucket sort
 struct PcgScalars {
     double delta_new, delta_old, delta0, alpha, beta, tol, pq;
     int iters, done, max_iter, status;
+    int stop_indefinite;   // stop with GIPC_ERR_INDEFINITE on c.q <= 0 (one system, on request)
     unsigned count_a, count_b, count_0;
     unsigned scenes_done;   // batched solves: scenes that have stopped
     unsigned bar_count, bar_gen;   // grid barrier of the fused update / direction kernel
@@ -528,6 +529,10 @@ pcg_spmv_tma_kernel(const int32_t* __restrict__ rowptr, const int64_t* __restric
             S->pq = pq;
             S->alpha = S->delta_new / pq;
             S->count_a = 0;
+            if (S->stop_indefinite && pq <= 0.0) {   // no descent along c: H not positive definite
+                S->status = GIPC_ERR_INDEFINITE;
+                S->done = 1;
+            }
         }
     }
 }
@@ -577,10 +582,12 @@ void launch_spmv_tma(const int32_t* rowptr, const int64_t* slice_off, const int3
 // q = S(H c); alpha = delta_new / (c . q)
 template <typename VT, typename PT>
 __global__ void __launch_bounds__(kPcgThreads)
+// direction: c is a search direction (a curvature c.q <= 0 stops the solve); false for the first
+// product H x0, whose x0 is any starting point.
 pcg_spmv_kernel(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx, const VT* __restrict__ vals,
                 const PT* __restrict__ cg, const double* __restrict__ c, const int32_t* __restrict__ perm,
                 double* __restrict__ q, const uint8_t* __restrict__ fixed, int64_t n, double* __restrict__ part,
-                PcgScalars* __restrict__ S) {
+                PcgScalars* __restrict__ S, bool direction) {
     if (S->done) return;
     int64_t row;
     int comp;
@@ -597,6 +604,10 @@ pcg_spmv_kernel(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ 
             S->pq = pq;
             S->alpha = S->delta_new / pq;
             S->count_a = 0;
+            if (direction && S->stop_indefinite && pq <= 0.0) {   // no descent along c
+                S->status = GIPC_ERR_INDEFINITE;
+                S->done = 1;
+            }
         }
     }
 }
@@ -1019,7 +1030,7 @@ pcg_init_kernel(const double* __restrict__ b, const double* __restrict__ q, doub
     }
 }
 
-__global__ void pcg_set_scalars(PcgScalars* S, double tol, int max_iter) {
+__global__ void pcg_set_scalars(PcgScalars* S, double tol, int max_iter, int stop_indefinite) {
     S->tol = tol;
     S->max_iter = max_iter;
     S->done = 0;
@@ -1028,6 +1039,7 @@ __global__ void pcg_set_scalars(PcgScalars* S, double tol, int max_iter) {
     S->count_a = S->count_b = S->count_0 = 0;
     S->scenes_done = 0;
     S->bar_count = S->bar_gen = 0;
+    S->stop_indefinite = stop_indefinite;
 }
 
 // ---- batched solves: one CTA per scene for everything but the product ---------------------
@@ -1290,14 +1302,15 @@ gipc_status pcg_impl(gipc_ctx* ctx, const gipc_bsr* A, const double* rhs, double
     if (fp) sell_fill_kernel<double, fpair><<<fb, 256, 0, st>>>(A->rowptr, A->colidx, (const double*)A->vals, perm, n, nsl, slice_off, sell_col, (fpair*)sell_vals);
     else if (f64) sell_fill_kernel<double, double><<<fb, 256, 0, st>>>(A->rowptr, A->colidx, (const double*)A->vals, perm, n, nsl, slice_off, sell_col, (double*)sell_vals);
     else sell_fill_kernel<float, float><<<fb, 256, 0, st>>>(A->rowptr, A->colidx, (const float*)A->vals, perm, n, nsl, slice_off, sell_col, (float*)sell_vals);
-    pcg_set_scalars<<<1, 1, 0, st>>>(S, prm->rel_tol, max_iter);
+    pcg_set_scalars<<<1, 1, 0, st>>>(S, prm->rel_tol, max_iter,
+                                     (!voff && (prm->flags & GIPC_PCG_STOP_ON_INDEFINITE)) ? 1 : 0);
     soa_to_aos_kernel<<<eb, 256, 0, st>>>(rhs, b, nullptr, n, fixed);
     soa_to_aos_kernel<<<eb, 256, 0, st>>>(x, xv, x32, n, fixed);
     if (f64) pcg_factor_kernel<double><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(A->rowptr, A->colidx, (const double*)A->vals, n, pinv);
     else pcg_factor_kernel<float><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(A->rowptr, A->colidx, (const float*)A->vals, n, pinv);
     // q = S(H x0), reusing the spmv kernel with a scratch dot (alpha is overwritten at iteration 1)
-    if (f64) pcg_spmv_kernel<double, double><<<sb, kPcgThreads, 0, st>>>(A->rowptr, A->colidx, (const double*)A->vals, xv, xv, perm, q, fixed, n, part, S);
-    else pcg_spmv_kernel<float, float><<<sb, kPcgThreads, 0, st>>>(A->rowptr, A->colidx, (const float*)A->vals, x32, xv, perm, q, fixed, n, part, S);
+    if (f64) pcg_spmv_kernel<double, double><<<sb, kPcgThreads, 0, st>>>(A->rowptr, A->colidx, (const double*)A->vals, xv, xv, perm, q, fixed, n, part, S, false);
+    else pcg_spmv_kernel<float, float><<<sb, kPcgThreads, 0, st>>>(A->rowptr, A->colidx, (const float*)A->vals, x32, xv, perm, q, fixed, n, part, S, false);
     SceneScalars* SS = nullptr;
     if (voff) {
         if ((s = ctx->slot[P_SCENE].reserve(sizeof(SceneScalars) * (nscenes + 1))) != GIPC_OK) return s;
@@ -1385,6 +1398,8 @@ gipc_status pcg_impl(gipc_ctx* ctx, const gipc_bsr* A, const double* rhs, double
     if (iters_out_h) *iters_out_h = hs.iters;
     if (rel_out_h) *rel_out_h = hs.delta0 > 0.0 ? hs.delta_new / hs.delta0 : 0.0;
     if (hs.status == GIPC_ERR_NONFINITE) return fail(GIPC_ERR_NONFINITE, "gipc_pcg: non-finite residual");
+    if (hs.status == GIPC_ERR_INDEFINITE)
+        return fail(GIPC_ERR_INDEFINITE, "gipc_pcg: c . H c <= 0 after %d iterations (H not positive definite)", hs.iters);
     if (prm->rel_tol > 0.0 && hs.delta0 > 0.0 && hs.delta_new >= prm->rel_tol * hs.delta0 && hs.delta_new > 0.0)
         return fail(GIPC_ERR_NOT_CONVERGED, "gipc_pcg: %d iterations without reaching the tolerance", hs.iters);
     return GIPC_OK;
@@ -1517,13 +1532,13 @@ extern "C" gipc_status gipc_pcg_noalloc(const gipc_bsr* A, const double* rhs, do
     perm_scatter_kernel<<<(unsigned)chunks, 32, 0, st>>>(A->rowptr, n, offs, chunks, perm);
     // the solver scalars (iteration count, done flag, reduction counters) start from zero on
     // every call: pcg_set_scalars clears them; all other scratch is written before it is read
-    pcg_set_scalars<<<1, 1, 0, st>>>(S, prm->rel_tol, max_iter);
+    pcg_set_scalars<<<1, 1, 0, st>>>(S, prm->rel_tol, max_iter, (prm->flags & GIPC_PCG_STOP_ON_INDEFINITE) ? 1 : 0);
     soa_to_aos_kernel<<<eb, 256, 0, st>>>(rhs, b, nullptr, n, fixed);
     soa_to_aos_kernel<<<eb, 256, 0, st>>>(x, xv, x32, n, fixed);
     if (f64) pcg_factor_kernel<double><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(A->rowptr, A->colidx, (const double*)A->vals, n, pinv);
     else pcg_factor_kernel<float><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(A->rowptr, A->colidx, (const float*)A->vals, n, pinv);
-    if (f64) pcg_spmv_kernel<double, double><<<sb, kPcgThreads, 0, st>>>(A->rowptr, A->colidx, (const double*)A->vals, xv, xv, perm, q, fixed, n, part, S);
-    else pcg_spmv_kernel<float, float><<<sb, kPcgThreads, 0, st>>>(A->rowptr, A->colidx, (const float*)A->vals, x32, xv, perm, q, fixed, n, part, S);
+    if (f64) pcg_spmv_kernel<double, double><<<sb, kPcgThreads, 0, st>>>(A->rowptr, A->colidx, (const double*)A->vals, xv, xv, perm, q, fixed, n, part, S, false);
+    else pcg_spmv_kernel<float, float><<<sb, kPcgThreads, 0, st>>>(A->rowptr, A->colidx, (const float*)A->vals, x32, xv, perm, q, fixed, n, part, S, false);
     pcg_init_kernel<<<vb, kPcgThreads, 0, st>>>(b, q, r, sv, c, c32, nullptr, pinv, fixed, n, part, S);
     if ((s = check_launch("gipc_pcg_noalloc: setup")) != GIPC_OK) return s;
 
@@ -1533,8 +1548,8 @@ extern "C" gipc_status gipc_pcg_noalloc(const gipc_bsr* A, const double* rhs, do
     while (launched < max_iter) {
         const int m = (max_iter - launched) < chunk ? (max_iter - launched) : chunk;
         for (int it = 0; it < m; ++it) {
-            if (f64) pcg_spmv_kernel<double, double><<<sb, kPcgThreads, 0, st>>>(A->rowptr, A->colidx, (const double*)A->vals, c, c, perm, q, fixed, n, part, S);
-            else pcg_spmv_kernel<float, float><<<sb, kPcgThreads, 0, st>>>(A->rowptr, A->colidx, (const float*)A->vals, c32, c, perm, q, fixed, n, part, S);
+            if (f64) pcg_spmv_kernel<double, double><<<sb, kPcgThreads, 0, st>>>(A->rowptr, A->colidx, (const double*)A->vals, c, c, perm, q, fixed, n, part, S, true);
+            else pcg_spmv_kernel<float, float><<<sb, kPcgThreads, 0, st>>>(A->rowptr, A->colidx, (const float*)A->vals, c32, c, perm, q, fixed, n, part, S, true);
             pcg_update_kernel<<<ub, kUpdT, 0, st>>>(xv, r, c, q, sv, pinv, n, part, S);
             pcg_direction_kernel<<<db, kPcgThreads, 0, st>>>(c, c32, nullptr, sv, fixed, n, S);
         }
@@ -1552,6 +1567,9 @@ extern "C" gipc_status gipc_pcg_noalloc(const gipc_bsr* A, const double* rhs, do
     if (iters_out_h) *iters_out_h = hs.iters;
     if (rel_out_h) *rel_out_h = hs.delta0 > 0.0 ? hs.delta_new / hs.delta0 : 0.0;
     if (hs.status == GIPC_ERR_NONFINITE) return fail(GIPC_ERR_NONFINITE, "gipc_pcg_noalloc: non-finite residual");
+    if (hs.status == GIPC_ERR_INDEFINITE)
+        return fail(GIPC_ERR_INDEFINITE, "gipc_pcg_noalloc: c . H c <= 0 after %d iterations (H not positive definite)",
+                    hs.iters);
     if (prm->rel_tol > 0.0 && hs.delta0 > 0.0 && hs.delta_new >= prm->rel_tol * hs.delta0 && hs.delta_new > 0.0)
         return fail(GIPC_ERR_NOT_CONVERGED, "gipc_pcg_noalloc: %d iterations without reaching the tolerance", hs.iters);
     return GIPC_OK;

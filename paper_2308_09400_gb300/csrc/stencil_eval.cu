@@ -268,6 +268,13 @@ __device__ __forceinline__ void st_out(T* p, int64_t idx, double v) {
     p[idx] = static_cast<T>(v);
 }
 
+// Position of dense entry (a, b) (a, b < 3s) of element e in the dense layouts.
+template <int MODE>
+__device__ __forceinline__ int64_t dense_at(int a, int b, int n3, int64_t k, int64_t e) {
+    if (MODE == GIPC_HESS_BLOCKS) return (e * 16 + (a / 3) * 4 + b / 3) * 9 + (a % 3) * 3 + b % 3;
+    return (int64_t)(a * n3 + b) * k + e;
+}
+
 template <int PREC, int MODE>
 __global__ void __launch_bounds__(128)
 eval_stencils_kernel(const double* __restrict__ x, int64_t n, const int32_t* __restrict__ st, int64_t k,
@@ -431,8 +438,8 @@ eval_stencils_kernel(const double* __restrict__ x, int64_t n, const int32_t* __r
 #pragma unroll
                     for (int bcol = 0; bcol <= a; ++bcol) {
                         const double h = ta * w[bcol];
-                        hess[(int64_t)(a * n3 + bcol) * k + i] = h;
-                        if (bcol != a) hess[(int64_t)(bcol * n3 + a) * k + i] = h;
+                        hess[dense_at<MODE>(a, bcol, n3, k, i)] = h;
+                        if (bcol != a) hess[dense_at<MODE>(bcol, a, n3, k, i)] = h;
                     }
                 }
             }
@@ -448,8 +455,8 @@ eval_stencils_kernel(const double* __restrict__ x, int64_t n, const int32_t* __r
 #pragma unroll
                     for (int bcol = 0; bcol <= a; ++bcol) {
                         const float h = ta * wf[bcol];
-                        hess[(int64_t)(a * n3 + bcol) * k + i] = h;
-                        if (bcol != a) hess[(int64_t)(bcol * n3 + a) * k + i] = h;
+                        hess[dense_at<MODE>(a, bcol, n3, k, i)] = h;
+                        if (bcol != a) hess[dense_at<MODE>(bcol, a, n3, k, i)] = h;
                     }
                 }
             }
@@ -515,7 +522,7 @@ extern "C" gipc_status gipc_eval_stencils(const double* x, int64_t n, const int3
         return fail(GIPC_ERR_INVALID_ARG, "gipc_eval_stencils: need dhat > 0, kappa >= 0, 0 < d_thr_ratio < 1");
     if (prec != GIPC_FP64 && prec != GIPC_MIXED)
         return fail(GIPC_ERR_INVALID_ARG, "gipc_eval_stencils: unknown precision %d", prec);
-    if (mode != GIPC_HESS_DENSE && mode != GIPC_HESS_RANK1)
+    if (mode != GIPC_HESS_DENSE && mode != GIPC_HESS_RANK1 && mode != GIPC_HESS_BLOCKS)
         return fail(GIPC_ERR_INVALID_ARG, "gipc_eval_stencils: unknown Hessian mode %d", mode);
     if (k == 0) return GIPC_OK;
     if (!x || !stencils) return fail(GIPC_ERR_INVALID_ARG, "gipc_eval_stencils: null x or stencils");
@@ -535,8 +542,10 @@ extern "C" gipc_status gipc_eval_stencils(const double* x, int64_t n, const int3
 #define GIPC_LAUNCH(P, M) \
     eval_stencils_kernel<P, M><<<blocks, 128, 0, s>>>(x, n, stencils, k, eps_x, K, energy, grad, hess, lam, flags)
     if (prec == GIPC_FP64 && mode == GIPC_HESS_DENSE) GIPC_LAUNCH(GIPC_FP64, GIPC_HESS_DENSE);
+    else if (prec == GIPC_FP64 && mode == GIPC_HESS_BLOCKS) GIPC_LAUNCH(GIPC_FP64, GIPC_HESS_BLOCKS);
     else if (prec == GIPC_FP64) GIPC_LAUNCH(GIPC_FP64, GIPC_HESS_RANK1);
     else if (mode == GIPC_HESS_DENSE) GIPC_LAUNCH(GIPC_MIXED, GIPC_HESS_DENSE);
+    else if (mode == GIPC_HESS_BLOCKS) GIPC_LAUNCH(GIPC_MIXED, GIPC_HESS_BLOCKS);
     else GIPC_LAUNCH(GIPC_MIXED, GIPC_HESS_RANK1);
 #undef GIPC_LAUNCH
     return check_launch("gipc_eval_stencils");

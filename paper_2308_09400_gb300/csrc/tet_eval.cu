@@ -194,7 +194,7 @@ __device__ __forceinline__ void add_mode(CT lam, const CT (&Q)[3][3], const CT (
     }
 }
 
-template <int PREC>
+template <int PREC, int MODE>
 __global__ void __launch_bounds__(128)
 eval_tets_kernel(const double* __restrict__ x, int64_t n, const int32_t* __restrict__ tets, int64_t T,
                  const double* __restrict__ Dm_inv, const double* __restrict__ vol, const ElasticConst K,
@@ -344,8 +344,13 @@ eval_tets_kernel(const double* __restrict__ x, int64_t n, const int32_t* __restr
 #pragma unroll
         for (int b = 0; b <= a; ++b) {
             const HT h = kc * H[idx++];
-            hess[(int64_t)(a * 12 + b) * T + t] = h;
-            if (a != b) hess[(int64_t)(b * 12 + a) * T + t] = h;
+            if (MODE == GIPC_HESS_BLOCKS) {   // element-major 3x3 sub-blocks
+                hess[(t * 16 + (a / 3) * 4 + b / 3) * 9 + (a % 3) * 3 + b % 3] = h;
+                if (a != b) hess[(t * 16 + (b / 3) * 4 + a / 3) * 9 + (b % 3) * 3 + a % 3] = h;
+            } else {
+                hess[(int64_t)(a * 12 + b) * T + t] = h;
+                if (a != b) hess[(int64_t)(b * 12 + a) * T + t] = h;
+            }
         }
 }
 
@@ -493,18 +498,27 @@ extern "C" gipc_status gipc_tet_rest(gipc_ctx* ctx, const double* rest_x, int64_
 }
 
 extern "C" gipc_status gipc_eval_tets(const double* x, int64_t n, const int32_t* tets, int64_t T, const double* Dm_inv,
-                                      const double* vol, const gipc_elastic_params* prm, int prec, double* energy,
-                                      double* grad, void* hess, void* stream) {
+                                      const double* vol, const gipc_elastic_params* prm, int prec, int hess_mode,
+                                      double* energy, double* grad, void* hess, void* stream) {
     using namespace gipc;
     if (n < 0 || T < 0) return fail(GIPC_ERR_INVALID_ARG, "gipc_eval_tets: negative size");
     if (!prm || !(prm->mu > 0.0) || !(prm->lambda > 0.0) || !(prm->scale >= 0.0))
         return fail(GIPC_ERR_INVALID_ARG, "gipc_eval_tets: need mu > 0, lambda > 0, scale >= 0");
     if (prec != GIPC_FP64 && prec != GIPC_MIXED) return fail(GIPC_ERR_INVALID_ARG, "gipc_eval_tets: bad precision");
+    if (hess_mode != GIPC_HESS_DENSE && hess_mode != GIPC_HESS_BLOCKS)
+        return fail(GIPC_ERR_INVALID_ARG, "gipc_eval_tets: hess_mode must be GIPC_HESS_DENSE or GIPC_HESS_BLOCKS");
     if (T == 0) return GIPC_OK;
     if (!x || !tets || !Dm_inv || !vol) return fail(GIPC_ERR_INVALID_ARG, "gipc_eval_tets: null input");
     ElasticConst K{prm->mu, prm->lambda, 1.0 + prm->mu / prm->lambda - prm->mu / (4.0 * prm->lambda), prm->scale};
     cudaStream_t st = (cudaStream_t)stream;
-    if (prec == GIPC_FP64) eval_tets_kernel<GIPC_FP64><<<nb(T, 128), 128, 0, st>>>(x, n, tets, T, Dm_inv, vol, K, energy, grad, hess);
-    else eval_tets_kernel<GIPC_MIXED><<<nb(T, 128), 128, 0, st>>>(x, n, tets, T, Dm_inv, vol, K, energy, grad, hess);
+    const bool blk = hess_mode == GIPC_HESS_BLOCKS;
+    if (prec == GIPC_FP64 && blk)
+        eval_tets_kernel<GIPC_FP64, GIPC_HESS_BLOCKS><<<nb(T, 128), 128, 0, st>>>(x, n, tets, T, Dm_inv, vol, K, energy, grad, hess);
+    else if (prec == GIPC_FP64)
+        eval_tets_kernel<GIPC_FP64, GIPC_HESS_DENSE><<<nb(T, 128), 128, 0, st>>>(x, n, tets, T, Dm_inv, vol, K, energy, grad, hess);
+    else if (blk)
+        eval_tets_kernel<GIPC_MIXED, GIPC_HESS_BLOCKS><<<nb(T, 128), 128, 0, st>>>(x, n, tets, T, Dm_inv, vol, K, energy, grad, hess);
+    else
+        eval_tets_kernel<GIPC_MIXED, GIPC_HESS_DENSE><<<nb(T, 128), 128, 0, st>>>(x, n, tets, T, Dm_inv, vol, K, energy, grad, hess);
     return check_launch("gipc_eval_tets");
 }

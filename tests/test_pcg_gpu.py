@@ -156,6 +156,23 @@ def test_large_system_takes_the_split_update_kernels(gipc):
         assert rel == pytest.approx(ref["rel"], rel=1e-8)
 
 
+def test_indefinite_matrix_reported(gipc):
+    """On request, a direction of negative curvature stops the solve with GIPC_ERR_INDEFINITE
+    (the last iterate kept) instead of continuing with a negative step length; by default the
+    iteration runs on, as the paper's modified PCG does."""
+    n = 300
+    R, b, _, _ = spd_system(n, 900, 200, seed=46)
+    vals = np.asarray(R["vals"]).reshape(-1, 3, 3).copy()
+    rows = np.repeat(np.arange(n), np.diff(R["rowptr"]))
+    diag = np.asarray(R["colidx"]) == rows
+    vals[diag] = -vals[diag]                        # negative definite diagonal dominates
+    Rn = dict(R, vals=vals.reshape(-1, 9))
+    with pytest.raises(gipc.GipcError, match="INDEFINITE"):
+        gipc.pcg(_gpu_bsr(Rn, n), torch.tensor(b, device="cuda"), rel_tol=1e-8, max_iter=50, stop_on_indefinite=True)
+    x, k, _ = gipc.pcg(_gpu_bsr(Rn, n), torch.tensor(b, device="cuda"), rel_tol=0.0, max_iter=5)
+    assert k == 5
+
+
 def test_nonconvergence_reported(gipc):
     n = 500
     R, b, _, _ = spd_system(n, 2000, 300, seed=44)

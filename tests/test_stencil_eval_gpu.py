@@ -88,6 +88,22 @@ def test_fp64_dense_parity_unit_set(gipc, unit):
     assert_parity(got, ref, d["stencils"])
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_blocks_layout_is_the_dense_layout_rearranged(gipc, unit, precision):
+    """GIPC_HESS_BLOCKS holds the dense values bit for bit, each 3x3 sub-block contiguous."""
+    d, eps, _ = unit
+    dense = _run(gipc, d, eps, precision=precision, mode="dense", want=("hess",))["hess"]   # [144, k]
+    blk = _run(gipc, d, eps, precision=precision, mode="blocks", want=("hess",))["hess"]    # [k, 144]
+    n3 = _n3(d["stencils"])
+    for s3 in (6, 9, 12):
+        idx = np.nonzero(n3 == s3)[0]
+        assert len(idx) > 0
+        for a in range(s3):
+            for b in range(s3):
+                at = ((a // 3) * 4 + b // 3) * 9 + (a % 3) * 3 + b % 3
+                assert np.array_equal(blk[idx, at], dense[a * s3 + b, idx])
+
+
 def test_fp64_rank1_parity_unit_set(gipc, unit):
     d, eps, ref = unit
     got = _run(gipc, d, eps, mode="rank1", want=("energy", "grad", "hess", "lam", "flags"))

@@ -143,3 +143,15 @@ def test_full_size_sampled(gipc):
     ref = O.eval_tets(x, sub, Dmi, vol, mu, lam, DT * DT)
     got = {k: v.cpu().numpy()[..., idx] for k, v in g.items()}
     _compare(got, ref, 1e-10)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_blocks_layout_is_the_dense_layout_rearranged(gipc, precision):
+    rest, x, tets = _mesh(7, invert=2)
+    mu, lam = O.snh_params(E, NU)
+    Dmi, vol, _ = O.rest_state(rest, tets, RHO)
+    args = (_dev(x), _dev(tets), _dev(Dmi), _dev(vol), mu, lam, DT * DT)
+    a = gipc.eval_tets(*args, precision=precision, want=("hess",))["hess"].cpu().numpy()                  # [144, T]
+    b = gipc.eval_tets(*args, precision=precision, want=("hess",), layout="blocks")["hess"].cpu().numpy()  # [T, 144]
+    at = [((r // 3) * 4 + c // 3) * 9 + (r % 3) * 3 + c % 3 for r in range(12) for c in range(12)]
+    assert np.array_equal(b[:, at], a.T)
