@@ -829,10 +829,12 @@ gipc_status collect_pairs(gipc_ctx* ctx, const double* x, const double* d, int64
     return fail(GIPC_ERR_CUDA, "contact pairs: candidate count changed between passes");
 }
 
-bool cache_matches(const gipc_ctx* ctx, int64_t n, const gipc_surface& srf, double dhat) {
+bool cache_matches(const gipc_ctx* ctx, int64_t n, const gipc_surface& srf, double dhat, const int32_t* vscene,
+                   int nscenes) {
     const gipc_contact_cache& C = ctx->ccache;
     return C.valid && C.n == n && C.dhat == dhat && C.tris == srf.tris && C.edges == srf.edges &&
-           C.verts == srf.verts && C.ntri == srf.ntri && C.nedge == srf.nedge && C.nvert == srf.nvert;
+           C.verts == srf.verts && C.ntri == srf.ntri && C.nedge == srf.nedge && C.nvert == srf.nvert &&
+           C.vscene == vscene && C.nscenes == (vscene ? nscenes : 1);
 }
 
 // Largest per-axis move of a surface vertex since the cached candidates were built, and the
@@ -871,10 +873,10 @@ gipc_status find_contacts_impl(gipc_ctx* ctx, const double* x, const double* res
     const bool pt = S.nvert > 0 && S.ntri > 0;
     // cached candidates: valid while no surface vertex has moved more than the margin since they
     // were collected (boxes padded by dhat + 2 margin); the classification below decides exactly
-    const bool use_cache = cached && !vscene;
+    const bool use_cache = cached;
     const double margin = 0.5 * dhat;
     bool hit = false;
-    if (use_cache && cache_matches(ctx, n, srf, dhat)) {
+    if (use_cache && cache_matches(ctx, n, srf, dhat, vscene, nscenes)) {
         double delta = 0.0, dm = 0.0;
         if ((s = cache_disp(ctx, x, nullptr, n, srf, &delta, &dm, st)) != GIPC_OK) return s;
         hit = delta * (1.0 + 1e-9) <= ctx->ccache.margin;
@@ -917,6 +919,8 @@ gipc_status find_contacts_impl(gipc_ctx* ctx, const double* x, const double* res
             C.ntri = srf.ntri;
             C.nedge = srf.nedge;
             C.nvert = srf.nvert;
+            C.vscene = vscene;
+            C.nscenes = vscene ? nscenes : 1;
             C.dhat = dhat;
             C.margin = margin;
             C.pad = pad_b;
@@ -973,7 +977,7 @@ gipc_status ccd_impl(gipc_ctx* ctx, const double* x, const double* d, int64_t n,
     const int ns = vscene ? nscenes : 1;
     fill_kernel<<<nblk(ns, 256), 256, 0, st>>>(amin_d, ns, 1.0);
     unsigned long long* amin = reinterpret_cast<unsigned long long*>(amin_d);
-    if (cached && !vscene && cache_matches(ctx, n, srf, ctx->ccache.dhat)) {
+    if (cached && cache_matches(ctx, n, srf, ctx->ccache.dhat, vscene, nscenes)) {
         double delta = 0.0, dm = 0.0;
         if ((s = cache_disp(ctx, x, d, n, srf, &delta, &dm, st)) != GIPC_OK) return s;
         if (2.0 * (delta + dm) * (1.0 + 1e-9) <= ctx->ccache.pad) {
@@ -981,8 +985,8 @@ gipc_status ccd_impl(gipc_ctx* ctx, const double* x, const double* d, int64_t n,
             const int32_t* cq = ctx->slot[C_CPAIRS].as<int32_t>();
             if (np > 0)
                 ccd_pairs_kernel<<<nblk(np, 128), 128, 0, st>>>(x, d, n, S, cq, cq + np, ctx->ccache.npt, np, slack,
-                                                                 max_iter, nullptr, amin, true);
-            cudaMemcpyAsync(alpha_h, amin_d, sizeof(double), cudaMemcpyDeviceToHost, st);
+                                                                 max_iter, vscene, amin, true);
+            cudaMemcpyAsync(alpha_h, amin_d, sizeof(double) * ns, cudaMemcpyDeviceToHost, st);
             if (cudaStreamSynchronize(st) != cudaSuccess) return check_launch("gipc_ccd_max_step: sync");
             return check_launch("gipc_ccd_max_step");
         }

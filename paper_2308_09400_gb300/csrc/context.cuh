@@ -99,12 +99,14 @@ struct gipc_contact_cache {
     int64_t n = 0, npt = 0, np = 0;          // vertex count, point-triangle pairs, all pairs
     const int32_t *tris = nullptr, *edges = nullptr, *verts = nullptr;
     int64_t ntri = 0, nedge = 0, nvert = 0;
+    const int32_t* vscene = nullptr;         // batched scenes: the vertex -> scene map, and their count
+    int nscenes = 1;
     double dhat = 0.0, margin = 0.0, pad = 0.0;
 };
 
 struct gipc_ctx {
     int device = 0;
-    static constexpr int kSlots = 64;   // assembly 0-8, pcg 9-15 and 40, contacts 16-19, 30-39, 45-46 and 59-60, time step 20-29, 41-44 and 47-48, derivatives 49-58
+    static constexpr int kSlots = 64;   // assembly 0-8 and 61, pcg 9-15 and 40, contacts 16-19, 30-39, 45-46 and 59-60, time step 20-29, 41-44 and 47-48, derivatives 49-58
     gipc_scratch slot[kSlots];
     gipc_profiler prof;
     gipc_contact_cache ccache;   // filled and used by the time step only

@@ -636,7 +636,7 @@ struct BatchStep {
         for (int attempt = 0; attempt < 2; ++attempt) {
             int64_t cnt = 0;
             const gipc_status s = find_contacts_impl(ctx, xc, sc.rest_x, n, sc.surface, prm.barrier.dhat, cs.st, cs.eps,
-                                                     cs.cap, &cnt, true, vs, npt, st, ns, false);
+                                                     cs.cap, &cnt, true, vs, npt, st, ns, true);
             if (s == GIPC_OK) {
                 cs.k = cnt;
                 return GIPC_OK;
@@ -706,6 +706,7 @@ struct BatchStep {
     // Rebuild the working batch from the caller's arrays with the original scenes `keep`.
     gipc_status pack(const std::vector<int>& keep, double* x_full) {
         gipc_status s;
+        ctx->ccache.valid = false;   // the packed lists reuse the same buffers with other scenes
         const int nsp = (int)keep.size();
         std::vector<int64_t> pvoff(nsp + 1, 0), src(nsp), vshift(nsp);
         std::vector<int64_t> poff[4], psrc[4];
@@ -822,6 +823,7 @@ struct BatchStep {
     gipc_status run_batch(double* x_full, double* v, gipc_step_stats* stats) {
         const int64_t nf = full.n, m3f = 3 * nf;
         gipc_status s;
+        ctx->ccache.valid = false;   // candidates are reused only within this step
         if ((s = ctx->slot[N_VEC].reserve(sizeof(double) * 7 * m3f)) != GIPC_OK) return s;
         if ((s = ctx->slot[B_VS].reserve(sizeof(int32_t) * (nf + 1) + nf + 64)) != GIPC_OK) return s;
         x0 = ctx->slot[N_VEC].as<double>();
@@ -956,7 +958,7 @@ struct BatchStep {
             s = pcg_impl(ctx, &H, rhs, d, mask, &pp, nullptr, nullptr, st, voff, ns, piters.data(), pstat.data());
             if (s != GIPC_OK && s != GIPC_ERR_NOT_CONVERGED) return s;
             // per-scene step filter, then backtracking per scene
-            if ((s = ccd_impl(ctx, x, d, n, sc.surface, 0.1, alpha_h.data(), st, vs, ns, sA, false)) != GIPC_OK) return s;
+            if ((s = ccd_impl(ctx, x, d, n, sc.surface, 0.1, alpha_h.data(), st, vs, ns, sA, true)) != GIPC_OK) return s;
             for (int q = 0; q < ns; ++q) {
                 accepted[q] = active_h[q] ? 0 : 1;
                 if (active_h[q]) S[map[q]].pcg_iters += piters[q];
