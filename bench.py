@@ -188,19 +188,21 @@ def _scan_launches(m):
     return 1 if m <= 4096 else 2 + _scan_launches((m + 4095) // 4096)
 
 
-def launches_per_step(n, sms=152):
+def launches_per_step(n, nnzb, sms=152):
     """The library's kernel launches in one C1 step (the sequence a launch list shows).
 
     eps_x + evaluation; assembly: row init, count, cursor init, fill, three row sorts, rowptr,
-    emit, segment end, gradient init, values, and two scans over the n rows; solver: row-length
+    emit, segment end, gradient init, the block-order histogram + scatter, values, two scans over
+    the n rows and one over the 32 count bins x 1024-block chunks; solver: row-length
     histogram + scatter (+ scan of the 64 buckets x 1024-row chunks), slice lengths + fill (+ scan
     of the SELL-32 slices), scalars, two layout conversions, factors, the first product, setup, the
     final layout conversion, and per iteration the product plus the fused update / direction (the
     separate update and direction when the fused kernel's tiles do not fit: 8 x 256 vertices per
     CTA, 2 CTAs per SM)."""
+    order = (2 + _scan_launches(32 * ((nnzb + 1023) // 1024))) if nnzb > 0 else 0
     scans = 2 * _scan_launches(n) + _scan_launches(64 * ((n + 1023) // 1024)) + _scan_launches((n + 31) // 32)
     fused = (n + 255) // 256 <= 8 * 2 * sms
-    return 2 + 12 + 11 + scans + (2 if fused else 3) * PCG_ITERS
+    return 2 + 12 + order + 11 + scans + (2 if fused else 3) * PCG_ITERS
 
 
 def source_hash(*rel):
@@ -344,7 +346,7 @@ def run_gpu(args):
             "roofline": roof,
             "e2e": {"value": job_rate(K_STENCILS, world, e2e_ms), "unit": "stencils/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
-            "gpu_launches": launches_per_step(n) * args.steps,
+            "gpu_launches": launches_per_step(n, nnzb) * args.steps,
             "clocks": clk,
         }
         if args.precision == "fp64" and args.hess_mode == "dense" and args.product == "native":

@@ -20,7 +20,14 @@
 // order, i.e. the mass first, then elements in ascending id (tetrahedra before
 // stencils), exactly the order of a sequential reference.  The diagonal block
 // of row r also sums the slot gradients of its contributors into g[r].
+// Threads take the blocks in falling order of contribution count (a stable
+// counting sort of the block ids), so a warp's lanes loop equally long: an
+// instruction costs its full issue slots however few lanes are active, which
+// matters most for float64 adds (1/64 of the float32 rate).  Each block is
+// still summed alone and in key order, so the values do not depend on it.
 #include <cuda_runtime.h>
+
+#include <algorithm>
 
 #include "common.cuh"
 #include "context.cuh"
@@ -33,7 +40,13 @@ constexpr int kWarpRowMax = 512;
 constexpr int kBlockRowMax = 8192;
 constexpr int kSortWarps = 4;
 
-enum Slot { S_ROWCNT = 0, S_ROWSTART, S_KEYS, S_NNZB, S_SEG, S_ELEMN3, S_MISC, S_SCAN, S_ROWPTR64 };
+enum Slot { S_ROWCNT = 0, S_ROWSTART, S_KEYS, S_NNZB, S_SEG, S_ELEMN3, S_MISC, S_SCAN, S_ROWPTR64, S_ORDER = 61 };
+
+// Blocks are evaluated in order of falling contribution count so that the lanes of a warp run
+// loops of equal length: counts are binned into kOrderBins (the last bin holds every count above),
+// and each warp of the ordering kernels takes kOrderChunk consecutive blocks.
+constexpr int kOrderBins = 32;
+constexpr int kOrderChunk = 1024;
 
 struct ElemList {
     const int32_t* idx;
@@ -313,13 +326,64 @@ __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(
 __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
 
 // One thread per block: in-order sum of its contributions (mass first, then elements by id).
+// Bin of block b: kOrderBins - 1 for the fewest contributions down to 0 for the most.
+__device__ __forceinline__ int order_bin(const int64_t* __restrict__ seg, int64_t b) {
+    const int64_t c = seg[b + 1] - seg[b];
+    return kOrderBins - 1 - (int)(c < kOrderBins - 1 ? c : kOrderBins - 1);
+}
+
+// hist[bin * nchunk + chunk] = blocks of the bin in the chunk (one warp per chunk of kOrderChunk).
+__global__ void order_hist_kernel(const int64_t* __restrict__ seg, int64_t nnzb, int64_t nchunk,
+                                  int32_t* __restrict__ hist) {
+    __shared__ int32_t cnt[8][kOrderBins];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t chunk = (int64_t)blockIdx.x * 8 + w;
+    if (chunk >= nchunk) return;
+    cnt[w][lane] = 0;
+    __syncwarp();
+    const int64_t b0 = chunk * kOrderChunk;
+    for (int r = 0; r < kOrderChunk / 32; ++r) {
+        const int64_t b = b0 + r * 32 + lane;
+        const int bin = b < nnzb ? order_bin(seg, b) : -1;
+        const unsigned same = __match_any_sync(0xffffffffu, bin);
+        if (bin >= 0 && (same & ((1u << lane) - 1u)) == 0u) cnt[w][bin] += __popc(same);
+        __syncwarp();
+    }
+    hist[(int64_t)lane * nchunk + chunk] = cnt[w][lane];
+}
+
+// order[off[bin * nchunk + chunk] + rank] = b: a stable counting sort of all blocks by bin, with
+// off the exclusive prefix of hist (bin-major, so every chunk's blocks of a bin follow the
+// previous chunk's).
+__global__ void order_scatter_kernel(const int64_t* __restrict__ seg, int64_t nnzb, int64_t nchunk,
+                                     const int64_t* __restrict__ off, int32_t* __restrict__ order) {
+    __shared__ int64_t pos[8][kOrderBins];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t chunk = (int64_t)blockIdx.x * 8 + w;
+    if (chunk >= nchunk) return;
+    pos[w][lane] = off[(int64_t)lane * nchunk + chunk];
+    __syncwarp();
+    const int64_t b0 = chunk * kOrderChunk;
+    for (int r = 0; r < kOrderChunk / 32; ++r) {
+        const int64_t b = b0 + r * 32 + lane;
+        const int bin = b < nnzb ? order_bin(seg, b) : -1;
+        const unsigned same = __match_any_sync(0xffffffffu, bin);
+        const unsigned below = same & ((1u << lane) - 1u);
+        if (bin >= 0) order[pos[w][bin] + __popc(below)] = (int32_t)b;
+        __syncwarp();
+        if (bin >= 0 && below == 0u) pos[w][bin] += __popc(same);
+        __syncwarp();
+    }
+}
+
 template <typename VT>
 __global__ void values_kernel(const uint64_t* __restrict__ keys, const int64_t* __restrict__ seg, int64_t nnzb,
-                              int64_t n, ElemList tets, ElemList sts, const uint8_t* __restrict__ elem_n3,
-                              const double* __restrict__ mass, VT* __restrict__ vals,
-                              const double* __restrict__ g0, double* __restrict__ gout) {
-    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nnzb;
-         b += (int64_t)gridDim.x * blockDim.x) {
+                              const int32_t* __restrict__ order, int64_t n, ElemList tets, ElemList sts,
+                              const uint8_t* __restrict__ elem_n3, const double* __restrict__ mass,
+                              VT* __restrict__ vals, const double* __restrict__ g0, double* __restrict__ gout) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nnzb;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = order ? (int64_t)order[t] : t;
         const int64_t s0 = seg[b], s1 = seg[b + 1];
         VT acc[9];
 #pragma unroll
@@ -532,17 +596,35 @@ extern "C" gipc_status gipc_assemble_bsr(gipc_ctx* ctx, int64_t n, const gipc_el
     if (nnzb > 0 && (!bsr->colidx || !bsr->vals)) return fail(GIPC_ERR_INVALID_ARG, "gipc_assemble_bsr: null colidx/vals");
     if ((st = ctx->slot[S_SEG].reserve(sizeof(int64_t) * (nnzb + 1))) != GIPC_OK) return st;
     int64_t* seg = ctx->slot[S_SEG].as<int64_t>();
+    // the block order of the values kernel: falling contribution count, stable
+    const int64_t nchunk = (nnzb + kOrderChunk - 1) / kOrderChunk;
+    const int64_t nbin = (int64_t)kOrderBins * nchunk;
+    if ((st = ctx->slot[S_ORDER].reserve(sizeof(int64_t) * (nbin + 1) + sizeof(int32_t) * (nbin + nnzb))) != GIPC_OK)
+        return st;
+    if ((st = ctx->slot[S_SCAN].reserve(sizeof(int64_t) * scan_scratch_words(std::max(n, nbin) + 1))) != GIPC_OK)
+        return st;
+    scan_tmp = ctx->slot[S_SCAN].as<int64_t>();
+    int64_t* bin_off = ctx->slot[S_ORDER].as<int64_t>();
+    int32_t* bin_hist = reinterpret_cast<int32_t*>(bin_off + nbin + 1);
+    int32_t* order = bin_hist + nbin;
     ctx->prof.start(GIPC_PROF_ASM_VALUES, s);
     emit_kernel<<<blocks_for(n, 8, 152 * 64), 256, 0, s>>>(row_start, keys, rowptr64, n, bsr->colidx, seg);
     seg_end_kernel<<<1, 1, 0, s>>>(seg, rowptr64, row_start, n);
     if (grad_out) grad_init_kernel<<<blocks_for(3 * n, 256, 1 << 30), 256, 0, s>>>(grad_base, grad_out, 3 * n);
     if (nnzb > 0) {
+        const unsigned ob = (unsigned)((nchunk + 7) / 8);
+        order_hist_kernel<<<ob, 256, 0, s>>>(seg, nnzb, nchunk, bin_hist);
+        if (exclusive_scan<int32_t>(bin_hist, bin_off, nbin, scan_tmp, s) != cudaSuccess)
+            return check_launch("gipc_assemble_bsr: scan");
+        order_scatter_kernel<<<ob, 256, 0, s>>>(seg, nnzb, nchunk, bin_off, order);
         if (bsr->prec == GIPC_FP64)
-            values_kernel<double><<<blocks_for(nnzb, 128), 128, 0, s>>>(keys, seg, nnzb, n, L[0], L[1], elem_n3, mass,
-                                                                      static_cast<double*>(bsr->vals), grad_base, grad_out);
+            values_kernel<double><<<blocks_for(nnzb, 128), 128, 0, s>>>(keys, seg, nnzb, order, n, L[0], L[1], elem_n3,
+                                                                      mass, static_cast<double*>(bsr->vals), grad_base,
+                                                                      grad_out);
         else
-            values_kernel<float><<<blocks_for(nnzb, 128), 128, 0, s>>>(keys, seg, nnzb, n, L[0], L[1], elem_n3, mass,
-                                                                     static_cast<float*>(bsr->vals), grad_base, grad_out);
+            values_kernel<float><<<blocks_for(nnzb, 128), 128, 0, s>>>(keys, seg, nnzb, order, n, L[0], L[1], elem_n3,
+                                                                     mass, static_cast<float*>(bsr->vals), grad_base,
+                                                                     grad_out);
     }
     ctx->prof.stop(GIPC_PROF_ASM_VALUES, s);
     return check_launch("gipc_assemble_bsr: values");
