@@ -295,7 +295,9 @@ typedef struct {
  * sum of squares and stays nonnegative on very ill-conditioned blocks.
  *
  *   A      BSR matrix (n = A->n block rows); FP64 or float32 values (MIXED: the
- *          products and row sums are float32, vectors, residual and dots float64)
+ *          products and row sums are float32, and so are the block-Jacobi factors,
+ *          s = P^-1 r and the direction c, whose exact float64 image updates x and
+ *          enters the dots; x, r, alpha, beta and the dots are float64)
  *   rhs    float64 [3][n]
  *   x      float64 [3][n]: initial guess in, solution out (fixed vertices: 0)
  *   fixed  uint8 [n] or NULL

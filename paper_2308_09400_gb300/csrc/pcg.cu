@@ -7,29 +7,37 @@
 // constrained vertices ("modified" PCG).  Unlike the paper, which multiplies the
 // local matrices directly, the matrix here is an assembled BSR.
 //
-// Per iteration three kernels run, all reading the solver scalars from device
+// Per iteration two kernels run, both reading the solver scalars from device
 // memory, so the host never waits inside the loop:
 //   A  q = S(H c) and the partial dots c.q      -> last CTA: alpha = delta/(c.q)
-//   B  x += alpha c; r -= alpha q; s = P^-1 r; partial dots r.s
-//                                               -> last CTA: delta_new, beta, done
-//   C  c = S(s + beta c)
-// Dots are reduced deterministically: every CTA writes one partial, the last
-// CTA to finish sums the partials in index order.  Once `done` is set every
-// kernel returns immediately, so surplus launched iterations are no-ops.
+//   B  x += alpha c; r -= alpha q; s = P^-1 r; partial dots r.s; grid barrier;
+//      delta_new, beta, done; c = S(s + beta c)
+// B is one cooperative launch; where its tiles do not fit in shared memory it
+// runs as an update and a direction kernel.  Dots are reduced deterministically:
+// every CTA writes one partial and the partials are summed in index order.  Once
+// `done` is set every kernel returns immediately, so surplus launched iterations
+// are no-ops.
 //
-// SpMV mapping: three lanes per block row, lane i of a row accumulates output
-// component i over the row's blocks (3 FMAs per block, each one useful), so no
-// cross-lane reduction is needed; ten rows per warp.  Rows are visited in an
-// order sorted by length (a stable bucket sort at set-up, longest first), so the
-// ten rows of a warp have similar lengths and few lanes idle: on GB300 an FP64
-// instruction costs the same whether 21 or 30 of its lanes are active.  gipc_pcg
-// copies the matrix once per solve into a sliced layout (ten rows per slice,
-// block j of the ten rows side by side) so every warp load is contiguous.  The
-// mixed path gathers a float32 copy of the search direction, so its inner loop
-// has no float64 operation at all.
+// Product: gipc_pcg copies the matrix once per solve into SELL-32 slices (32
+// block rows per slice, the rows in an order sorted by length by a stable bucket
+// sort, longest first; entry-major within a slice), one lane per block row.  Each
+// warp streams its slices into shared memory with cp.async.bulk and bounded
+// mbarrier waits while it multiplies the previous group, and the kernel is
+// launched with programmatic stream serialization, so it stages its first slice
+// while the previous kernel ends.  The first product H x0 and the allocation-free
+// solver use a plain kernel over the BSR rows (three lanes per block row).
+//
+// Mixed form: float32 blocks and a float32 product (row sums in float32); the
+// block-Jacobi factors, s = P^-1 r and the direction are float32 as well, the
+// direction kept with its exact float64 image for the x update and the dots;
+// x, r, alpha, beta and the dots stay float64.  On GB300 a float64 operation, or
+// a conversion between float64 and float32, issues at 1/64 of the float32 rate,
+// so the float32 preconditioner and direction take about half the float64 work
+// out of kernel B.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 #include <cmath>
 
@@ -617,9 +625,9 @@ pcg_spmv_kernel(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ 
 // substitution makes r . P^-1 r a sum of squares y_i^2 / d_i, nonnegative by
 // construction even when H_ii is very ill-conditioned (an explicit 3x3 inverse is not
 // numerically definite there).  A missing or non-positive-definite block falls back to I.
-template <typename VT>
+template <typename VT, typename FT>
 __global__ void pcg_factor_kernel(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
-                                  const VT* __restrict__ vals, int64_t n, double* __restrict__ fac) {
+                                  const VT* __restrict__ vals, int64_t n, FT* __restrict__ fac) {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
     double m[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
@@ -640,18 +648,18 @@ __global__ void pcg_factor_kernel(const int32_t* __restrict__ rowptr, const int3
     const double d1 = m[4] - l10 * l10 * d0;
     const double l21 = (m[7] - l20 * l10 * d0) / d1;
     const double d2 = m[8] - l20 * l20 * d0 - l21 * l21 * d1;
-    double* F = fac + r;
-    if (!(d0 > 0.0) || !(d1 > 0.0) || !(d2 > 0.0) || !isfinite(l10 + l20 + l21 + d2)) {
-        F[0] = F[n] = F[2 * n] = 0.0;
-        F[3 * n] = F[4 * n] = F[5 * n] = 1.0;
+    FT* F = fac + r;
+    const FT f[6] = {(FT)l10, (FT)l20, (FT)l21, (FT)(1.0 / d0), (FT)(1.0 / d1), (FT)(1.0 / d2)};
+    bool ok = d0 > 0.0 && d1 > 0.0 && d2 > 0.0 && isfinite(l10 + l20 + l21 + d2);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) ok = ok && isfinite((double)f[k]);   // also catches a float32 overflow
+    if (!ok) {
+        F[0] = F[n] = F[2 * n] = FT(0);
+        F[3 * n] = F[4 * n] = F[5 * n] = FT(1);
         return;
     }
-    F[0] = l10;
-    F[n] = l20;
-    F[2 * n] = l21;
-    F[3 * n] = 1.0 / d0;
-    F[4 * n] = 1.0 / d1;
-    F[5 * n] = 1.0 / d2;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) F[k * n] = f[k];
 }
 
 __device__ __forceinline__ void load_factor(const double* __restrict__ fac, int64_t n, int64_t v, double F[6]) {
@@ -672,23 +680,69 @@ __device__ __forceinline__ double precond_apply(const double* __restrict__ F, co
     return y0 * z0 + y1 * z1 + y2 * z2;
 }
 
+// The mixed form keeps the factors in float32 ([6][n] floats) and applies them in float32
+// arithmetic: the same substitutions, and r . s again a sum of squares y_i^2 / d_i.
+__device__ __forceinline__ void load_factor(const float* __restrict__ fac, int64_t n, int64_t v, float F[6]) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) F[k] = fac[k * n + v];
+}
+
+__device__ __forceinline__ float precond_apply(const float* __restrict__ F, const float r[3], float s[3]) {
+    const float l10 = F[0], l20 = F[1], l21 = F[2];
+    const float y0 = r[0];
+    const float y1 = r[1] - l10 * y0;
+    const float y2 = r[2] - l20 * y0 - l21 * y1;
+    const float z0 = y0 * F[3], z1 = y1 * F[4], z2 = y2 * F[5];
+    s[2] = z2;
+    s[1] = z1 - l21 * z2;
+    s[0] = z0 - l10 * s[1] - l20 * z2;
+    return y0 * z0 + y1 * z1 + y2 * z2;
+}
+
+// The form's factor type: float32 for the mixed form (MIX), float64 otherwise.
+template <bool MIX>
+using FacT = typename std::conditional<MIX, float, double>::type;
+
+template <bool MIX>
+__device__ __forceinline__ void load_factor_t(const double* __restrict__ fac, int64_t n, int64_t v, FacT<MIX> F[6]) {
+    load_factor(reinterpret_cast<const FacT<MIX>*>(fac), n, v, F);
+}
+
+// s = P^-1 r in the form's arithmetic: the mixed form rounds r to float32 and gives s in float32;
+// r . s is returned in float64 either way.
+template <bool MIX>
+__device__ __forceinline__ double precond_vertex(const FacT<MIX>* F, const double r[3], FacT<MIX> s[3]) {
+    if constexpr (MIX) {
+        const float rf[3] = {__double2float_rn(r[0]), __double2float_rn(r[1]), __double2float_rn(r[2])};
+        return (double)precond_apply(F, rf, s);
+    } else {
+        return precond_apply(F, r, s);
+    }
+}
+
 // x += alpha c; r -= alpha q; s = P^-1 r; delta_new = r . s; beta; termination.
 // Persistent CTAs walk tiles of kUpdT vertices.  A tile's 3 kUpdT entries of x, c, r, q and s are
 // read and written as flat coalesced runs and handed between the flat (axpy) and the per-vertex
 // (preconditioner) layouts through shared memory; the factors are [6][n].  The next tile's 18
 // loads per thread are issued before the current tile's FP64 work, so the FP64 pipe and HBM
 // overlap.  Each thread sums its vertices (one per tile, tiles in order) into its partial.
+// The mixed form (MIX) writes s in float32 over the first half of the s buffer.
+template <bool MIX>
 __global__ void __launch_bounds__(kUpdT, kUpdPerSm)
 pcg_update_kernel(double* __restrict__ x, double* __restrict__ r, const double* __restrict__ c,
                   const double* __restrict__ q, double* __restrict__ s, const double* __restrict__ fac,
                   int64_t n, double* __restrict__ part, PcgScalars* __restrict__ S) {
+    using ST = FacT<MIX>;
     if (S->done) return;
-    __shared__ double rt[3 * kUpdT], st[3 * kUpdT];
+    __shared__ double rt[3 * kUpdT];
+    __shared__ ST st[3 * kUpdT];
+    ST* __restrict__ so = reinterpret_cast<ST*>(s);
     const double alpha = S->alpha;
     const int t = threadIdx.x;
     const int64_t ntiles = (n + kUpdT - 1) / kUpdT, ne = 3 * n;
-    double xv[3], cv[3], rv[3], qv[3], F[6];
-    auto load = [&](int64_t tl, double* X, double* C, double* R, double* Q, double* Fv) {
+    double xv[3], cv[3], rv[3], qv[3];
+    ST F[6];
+    auto load = [&](int64_t tl, double* X, double* C, double* R, double* Q, ST* Fv) {
         const int64_t e0 = 3 * kUpdT * tl + t;
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
@@ -701,14 +755,15 @@ pcg_update_kernel(double* __restrict__ x, double* __restrict__ r, const double* 
             }
         }
         const int64_t v = kUpdT * tl + t;
-        if (v < n) load_factor(fac, n, v, Fv);
+        if (v < n) load_factor_t<MIX>(fac, n, v, Fv);
     };
     double d = 0.0;
     int64_t tl = blockIdx.x;
     if (tl < ntiles) load(tl, xv, cv, rv, qv, F);
     while (tl < ntiles) {   // uniform across the CTA
         const int64_t tn = tl + gridDim.x;
-        double xn[3], cn[3], rn[3], qn[3], Fn[6];
+        double xn[3], cn[3], rn[3], qn[3];
+        ST Fn[6];
         if (tn < ntiles) load(tn, xn, cn, rn, qn, Fn);
         const int64_t e0 = 3 * kUpdT * tl + t, v = kUpdT * tl + t;
 #pragma unroll
@@ -724,8 +779,8 @@ pcg_update_kernel(double* __restrict__ x, double* __restrict__ r, const double* 
         __syncthreads();
         if (v < n) {
             const double r3[3] = {rt[3 * t], rt[3 * t + 1], rt[3 * t + 2]};
-            double s3[3];
-            d += precond_apply(F, r3, s3);
+            ST s3[3];
+            d += precond_vertex<MIX>(F, r3, s3);
 #pragma unroll
             for (int i = 0; i < 3; ++i) st[3 * t + i] = s3[i];
         }
@@ -733,7 +788,7 @@ pcg_update_kernel(double* __restrict__ x, double* __restrict__ r, const double* 
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
             const int64_t e = e0 + j * kUpdT;
-            if (e < ne) s[e] = st[t + j * kUpdT];
+            if (e < ne) so[e] = st[t + j * kUpdT];
         }
         if (tn < ntiles) {
 #pragma unroll
@@ -771,8 +826,8 @@ pcg_update_kernel(double* __restrict__ x, double* __restrict__ r, const double* 
 // of r.s, as in pcg_update_kernel, but s and c stay in shared memory.  A grid barrier (the grid
 // is launched cooperatively, so every CTA is resident) then lets every CTA sum the partials in
 // the same fixed order -- identical totals everywhere -- and form beta and the stopping test;
-// phase 2 writes c = S(s + beta c) (and its float32 copy) for the same tiles while the solve
-// continues.  CTA 0 records the scalars.  The arithmetic is that of the two separate kernels.
+// phase 2 writes c = S(s + beta c) for the same tiles while the solve continues (the mixed form
+// forms it in float32 from the kept float32 s and c and writes it with its float64 image).  CTA 0 records the scalars.  The arithmetic is that of the two separate kernels.
 // The barrier wait is bounded: past kBarrierCycles it sets GIPC_ERR_TIMEOUT and stops the solve.
 constexpr long long kBarrierCycles = 4000000000LL;   // ~2 s at 2 GHz
 
@@ -804,6 +859,7 @@ __device__ __forceinline__ bool grid_barrier(PcgScalars* S) {
     return ok != 0;
 }
 
+template <bool MIX>
 __global__ void __launch_bounds__(kUpdT, kUpdPerSm)
 pcg_update_direction_kernel(double* __restrict__ x, double* __restrict__ r, double* __restrict__ c,
                             float* __restrict__ c32, fpair* __restrict__ c2, const double* __restrict__ q,
@@ -812,15 +868,19 @@ pcg_update_direction_kernel(double* __restrict__ x, double* __restrict__ r, doub
                             PcgScalars* __restrict__ S) {
     pdl_release();   // the next product may begin staging its matrix slices as SMs free up
     if (S->done) return;
-    extern __shared__ double keep[];   // per owned tile: s then c, flat order, 3 kUpdT each
-    __shared__ double rt[3 * kUpdT], st[3 * kUpdT];
+    using ST = FacT<MIX>;
+    extern __shared__ double keep[];   // per owned tile: s then c in the form's type, flat order, 3 kUpdT each
+    ST* const kp = reinterpret_cast<ST*>(keep);
+    __shared__ double rt[3 * kUpdT];
+    __shared__ ST st[3 * kUpdT];
     // every scalar this launch reads is read here, before the barrier: CTA 0 rewrites them after it
     const double alpha = S->alpha, delta_old = S->delta_new, tol = S->tol, delta0 = S->delta0;
     const int iters = S->iters + 1, max_iter = S->max_iter;
     const int t = threadIdx.x;
     const int64_t ntiles = (n + kUpdT - 1) / kUpdT, ne = 3 * n;
-    double xv[3], cv[3], rv[3], qv[3], F[6];
-    auto load = [&](int64_t tl, double* X, double* C, double* R, double* Q, double* Fv) {
+    double xv[3], cv[3], rv[3], qv[3];
+    ST kv[3], F[6];   // kv: the mixed form's float32 direction, kept for phase 2
+    auto load = [&](int64_t tl, double* X, double* C, double* R, double* Q, ST* K, ST* Fv) {
         const int64_t e0 = 3 * kUpdT * tl + t;
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
@@ -830,20 +890,22 @@ pcg_update_direction_kernel(double* __restrict__ x, double* __restrict__ r, doub
                 C[j] = c[e];
                 R[j] = r[e];
                 Q[j] = q[e];
+                if constexpr (MIX) K[j] = c32[e];
             }
         }
         const int64_t v = kUpdT * tl + t;
-        if (v < n) load_factor(fac, n, v, Fv);
+        if (v < n) load_factor_t<MIX>(fac, n, v, Fv);
     };
     double d = 0.0;
     int64_t tl = blockIdx.x;
     int slot = 0;
-    if (tl < ntiles) load(tl, xv, cv, rv, qv, F);
+    if (tl < ntiles) load(tl, xv, cv, rv, qv, kv, F);
     while (tl < ntiles) {
         const int64_t tn = tl + gridDim.x;
-        double xn[3], cn[3], rn[3], qn[3], Fn[6];
-        if (tn < ntiles) load(tn, xn, cn, rn, qn, Fn);
-        double* ks = keep + (int64_t)slot * 6 * kUpdT;
+        double xn[3], cn[3], rn[3], qn[3];
+        ST kn[3], Fn[6];
+        if (tn < ntiles) load(tn, xn, cn, rn, qn, kn, Fn);
+        ST* ks = kp + (int64_t)slot * 6 * kUpdT;
         const int64_t e0 = 3 * kUpdT * tl + t, v = kUpdT * tl + t;
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
@@ -853,14 +915,15 @@ pcg_update_direction_kernel(double* __restrict__ x, double* __restrict__ r, doub
                 const double re = rv[j] - alpha * qv[j];
                 r[e] = re;
                 rt[t + j * kUpdT] = re;
-                ks[3 * kUpdT + t + j * kUpdT] = cv[j];
+                if constexpr (MIX) ks[3 * kUpdT + t + j * kUpdT] = kv[j];
+                else ks[3 * kUpdT + t + j * kUpdT] = cv[j];
             }
         }
         __syncthreads();
         if (v < n) {
             const double r3[3] = {rt[3 * t], rt[3 * t + 1], rt[3 * t + 2]};
-            double s3[3];
-            d += precond_apply(F, r3, s3);
+            ST s3[3];
+            d += precond_vertex<MIX>(F, r3, s3);
 #pragma unroll
             for (int i = 0; i < 3; ++i) st[3 * t + i] = s3[i];
         }
@@ -874,6 +937,7 @@ pcg_update_direction_kernel(double* __restrict__ x, double* __restrict__ r, doub
                 cv[j] = cn[j];
                 rv[j] = rn[j];
                 qv[j] = qn[j];
+                if constexpr (MIX) kv[j] = kn[j];
             }
 #pragma unroll
             for (int k = 0; k < 6; ++k) F[k] = Fn[k];
@@ -896,6 +960,7 @@ pcg_update_direction_kernel(double* __restrict__ x, double* __restrict__ r, doub
     __syncthreads();
     const double dn = dn_sh;
     const double beta = dn / delta_old;
+    const float beta_f = (float)beta;
     int status = GIPC_OK, done = 0;
     if (!isfinite(dn) || !isfinite(alpha)) {
         status = GIPC_ERR_NONFINITE;
@@ -906,17 +971,22 @@ pcg_update_direction_kernel(double* __restrict__ x, double* __restrict__ r, doub
     if (!done) {
         slot = 0;
         for (int64_t tl2 = blockIdx.x; tl2 < ntiles; tl2 += gridDim.x, ++slot) {
-            const double* ks = keep + (int64_t)slot * 6 * kUpdT;
+            const ST* ks = kp + (int64_t)slot * 6 * kUpdT;
             const int64_t e0 = 3 * kUpdT * tl2 + t;
 #pragma unroll
             for (int j = 0; j < 3; ++j) {
                 const int64_t e = e0 + j * kUpdT;
                 if (e < ne) {
                     const bool fx = fixed && fixed[e / 3];
-                    const double ce = fx ? 0.0 : ks[t + j * kUpdT] + beta * ks[3 * kUpdT + t + j * kUpdT];
-                    c[e] = ce;
-                    if (c32) c32[e] = (float)ce;
-                    if (c2) c2[e] = split_double(ce);
+                    if constexpr (MIX) {   // the float32 direction and its exact float64 image
+                        const float ce = fx ? 0.0f : __fmaf_rn(beta_f, ks[3 * kUpdT + t + j * kUpdT], ks[t + j * kUpdT]);
+                        c32[e] = ce;
+                        c[e] = (double)ce;
+                    } else {
+                        const double ce = fx ? 0.0 : ks[t + j * kUpdT] + beta * ks[3 * kUpdT + t + j * kUpdT];
+                        c[e] = ce;
+                        if (c2) c2[e] = split_double(ce);
+                    }
                 }
             }
         }
@@ -933,27 +1003,32 @@ pcg_update_direction_kernel(double* __restrict__ x, double* __restrict__ r, doub
     }
 }
 
-// c = S(s + beta c) and its float32 copy, over the flat [3n] vectors with kDirEpt coalesced
-// entries per thread.
+// c = S(s + beta c) over the flat [3n] vectors with kDirEpt coalesced entries per thread.  The
+// mixed form (MIX) forms it in float32 from the float32 s and c32 and writes c32 and its exact
+// float64 image c.
+template <bool MIX>
 __global__ void __launch_bounds__(kPcgThreads)
 pcg_direction_kernel(double* __restrict__ c, float* __restrict__ c32, fpair* __restrict__ c2,
                      const double* __restrict__ s,
                      const uint8_t* __restrict__ fixed, int64_t n, const PcgScalars* __restrict__ S) {
+    using ST = FacT<MIX>;
     // runs after the update of the same iteration; `done` may now be set, but c is still refreshed
     // only while the solve continues
     if (S->done) return;
     const double beta = S->beta;
+    const ST* __restrict__ si = reinterpret_cast<const ST*>(s);
     const int64_t ne = 3 * n;
     const int64_t e0 = (int64_t)blockIdx.x * (kPcgThreads * kDirEpt) + threadIdx.x;
-    double sv[kDirEpt], cv[kDirEpt];
+    ST sv[kDirEpt], cv[kDirEpt];
     bool fx[kDirEpt];
 #pragma unroll
     for (int j = 0; j < kDirEpt; ++j) {
         const int64_t e = e0 + j * kPcgThreads;
         fx[j] = false;
         if (e < ne) {
-            sv[j] = s[e];
-            cv[j] = c[e];
+            sv[j] = si[e];
+            if constexpr (MIX) cv[j] = c32[e];
+            else cv[j] = c[e];
             fx[j] = fixed && fixed[e / 3];
         }
     }
@@ -961,10 +1036,15 @@ pcg_direction_kernel(double* __restrict__ c, float* __restrict__ c32, fpair* __r
     for (int j = 0; j < kDirEpt; ++j) {
         const int64_t e = e0 + j * kPcgThreads;
         if (e < ne) {
-            const double ce = fx[j] ? 0.0 : sv[j] + beta * cv[j];
-            c[e] = ce;
-            if (c32) c32[e] = (float)ce;
-            if (c2) c2[e] = split_double(ce);
+            if constexpr (MIX) {
+                const float ce = fx[j] ? 0.0f : __fmaf_rn((float)beta, cv[j], sv[j]);
+                c32[e] = ce;
+                c[e] = (double)ce;
+            } else {
+                const double ce = fx[j] ? 0.0 : sv[j] + beta * cv[j];
+                c[e] = ce;
+                if (c2) c2[e] = split_double(ce);
+            }
         }
     }
 }
@@ -988,13 +1068,16 @@ __global__ void aos_to_soa_kernel(const double* __restrict__ in, double* __restr
     out[comp * n + v] = in[e];
 }
 
-// Setup: r = S(b - H x0), s = P^-1 r, c = S(s), delta_0 = r.s (H x0 already in q)
+// Setup: r = S(b - H x0), s = P^-1 r, c = S(s), delta_0 = r.s (H x0 already in q).  The mixed form
+// (MIX) keeps s in float32 over the first half of the s buffer and c32 = S(s), c its float64 image.
+template <bool MIX>
 __global__ void __launch_bounds__(kPcgThreads)
 pcg_init_kernel(const double* __restrict__ b, const double* __restrict__ q, double* __restrict__ r,
                 double* __restrict__ s, double* __restrict__ c, float* __restrict__ c32, fpair* __restrict__ c2,
                 const double* __restrict__ pinv,
                 const uint8_t* __restrict__ fixed, int64_t n, double* __restrict__ part, PcgScalars* __restrict__ S) {
-    const int64_t ldf = n;
+    using ST = FacT<MIX>;
+    ST* __restrict__ so = reinterpret_cast<ST*>(s);
     double d = 0.0;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
         const bool fx = fixed && fixed[v];
@@ -1004,16 +1087,16 @@ pcg_init_kernel(const double* __restrict__ b, const double* __restrict__ q, doub
             rv[i] = fx ? 0.0 : b[3 * v + i] - q[3 * v + i];
             r[3 * v + i] = rv[i];
         }
-        double sv[3];
-        double F[6];
-        load_factor(pinv, ldf, v, F);
-        d += precond_apply(F, rv, sv);
+        ST sv[3], F[6];
+        load_factor_t<MIX>(pinv, n, v, F);
+        d += precond_vertex<MIX>(F, rv, sv);
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
-            s[3 * v + i] = sv[i];
-            c[3 * v + i] = fx ? 0.0 : sv[i];
-            if (c32) c32[3 * v + i] = fx ? 0.0f : (float)sv[i];
-            if (c2) c2[3 * v + i] = split_double(fx ? 0.0 : sv[i]);
+            so[3 * v + i] = sv[i];
+            const ST ce = fx ? ST(0) : sv[i];
+            c[3 * v + i] = (double)ce;
+            if constexpr (MIX) c32[3 * v + i] = ce;
+            else if (c2) c2[3 * v + i] = split_double(ce);
         }
     }
     const double bs = block_sum(d);
@@ -1063,31 +1146,35 @@ __device__ __forceinline__ void scene_stop(SceneScalars* SS, PcgScalars* S, int 
     if (atomicAdd(&S->scenes_done, 1u) + 1u == (unsigned)nscenes) S->done = 1;
 }
 
+template <bool MIX>
 __global__ void __launch_bounds__(kPcgThreads)
 pcg_scene_init_kernel(const double* __restrict__ b, const double* __restrict__ q, double* __restrict__ r,
                       double* __restrict__ s, double* __restrict__ c, float* __restrict__ c32,
                       const double* __restrict__ pinv, int64_t ldf, const uint8_t* __restrict__ fixed,
                       const int64_t* __restrict__ voff, int nscenes, SceneScalars* __restrict__ SS,
                       PcgScalars* __restrict__ S) {
+    using ST = FacT<MIX>;
+    ST* __restrict__ so = reinterpret_cast<ST*>(s);
     const int sc = blockIdx.x;
     const int64_t v0 = voff[sc], v1 = voff[sc + 1];
     double d = 0.0;
     for (int64_t v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
         const bool fx = fixed && fixed[v];
-        double rv[3], sv[3];
+        double rv[3];
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
             rv[i] = fx ? 0.0 : b[3 * v + i] - q[3 * v + i];
             r[3 * v + i] = rv[i];
         }
-        double F[6];
-        load_factor(pinv, ldf, v, F);
-        d += precond_apply(F, rv, sv);
+        ST sv[3], F[6];
+        load_factor_t<MIX>(pinv, ldf, v, F);
+        d += precond_vertex<MIX>(F, rv, sv);
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
-            s[3 * v + i] = sv[i];
-            c[3 * v + i] = fx ? 0.0 : sv[i];
-            if (c32) c32[3 * v + i] = fx ? 0.0f : (float)sv[i];
+            so[3 * v + i] = sv[i];
+            const ST ce = fx ? ST(0) : sv[i];
+            c[3 * v + i] = (double)ce;
+            if constexpr (MIX) c32[3 * v + i] = ce;
         }
     }
     const double d0 = block_sum_all(d);
@@ -1103,6 +1190,7 @@ pcg_scene_init_kernel(const double* __restrict__ b, const double* __restrict__ q
 
 // alpha = delta / (c.q); x += alpha c; r -= alpha q; s = P^-1 r; delta' = r.s; beta; stop test;
 // c = S(s + beta c) while the scene continues.
+template <bool MIX>
 __global__ void __launch_bounds__(kPcgThreads)
 pcg_scene_step_kernel(double* __restrict__ x, double* __restrict__ r, double* __restrict__ c, float* __restrict__ c32,
                       const double* __restrict__ q, double* __restrict__ s, const double* __restrict__ pinv,
@@ -1116,20 +1204,22 @@ pcg_scene_step_kernel(double* __restrict__ x, double* __restrict__ r, double* __
     pq = block_sum_all(pq);
     const double delta = SS[sc].delta;
     const double alpha = delta / pq;
+    using ST = FacT<MIX>;
+    ST* __restrict__ so = reinterpret_cast<ST*>(s);
     double d = 0.0;
     for (int64_t v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
-        double rv[3], sv[3];
+        double rv[3];
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
             x[3 * v + i] += alpha * c[3 * v + i];
             rv[i] = r[3 * v + i] - alpha * q[3 * v + i];
             r[3 * v + i] = rv[i];
         }
-        double F[6];
-        load_factor(pinv, ldf, v, F);
-        d += precond_apply(F, rv, sv);
+        ST sv[3], F[6];
+        load_factor_t<MIX>(pinv, ldf, v, F);
+        d += precond_vertex<MIX>(F, rv, sv);
 #pragma unroll
-        for (int i = 0; i < 3; ++i) s[3 * v + i] = sv[i];
+        for (int i = 0; i < 3; ++i) so[3 * v + i] = sv[i];
     }
     const double dn = block_sum_all(d);
     __shared__ int stop;
@@ -1153,9 +1243,14 @@ pcg_scene_step_kernel(double* __restrict__ x, double* __restrict__ r, double* __
         const bool fx = fixed && fixed[v];
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
-            const double ce = fx ? 0.0 : s[3 * v + i] + beta * c[3 * v + i];
-            c[3 * v + i] = ce;
-            if (c32) c32[3 * v + i] = (float)ce;
+            if constexpr (MIX) {   // the float32 direction and its exact float64 image
+                const float ce = fx ? 0.0f : __fmaf_rn((float)beta, c32[3 * v + i], so[3 * v + i]);
+                c32[3 * v + i] = ce;
+                c[3 * v + i] = (double)ce;
+            } else {
+                const double ce = fx ? 0.0 : so[3 * v + i] + beta * c[3 * v + i];
+                c[3 * v + i] = ce;
+            }
         }
     }
 }
@@ -1183,6 +1278,7 @@ struct FusePlan {
     size_t smem = 0;
 };
 
+template <bool MIX>
 inline FusePlan plan_fused(int64_t n) {
     FusePlan p;
     int dev = 0, sms = 0, coop = 0;
@@ -1197,13 +1293,13 @@ inline FusePlan plan_fused(int64_t n) {
     const size_t smem = (size_t)tpc * 6 * kUpdT * sizeof(double);
     static bool attr_set = false;
     if (!attr_set) {
-        if (cudaFuncSetAttribute(pcg_update_direction_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        if (cudaFuncSetAttribute(pcg_update_direction_kernel<MIX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(kFuseMaxTiles * 6 * kUpdT * sizeof(double))) != cudaSuccess)
             return p;
         attr_set = true;
     }
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pcg_update_direction_kernel, kUpdT, smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pcg_update_direction_kernel<MIX>, kUpdT, smem) != cudaSuccess)
         return p;
     if ((int64_t)per_sm * sms < grid) return p;
     p.ok = true;
@@ -1246,7 +1342,7 @@ gipc_status pcg_impl(gipc_ctx* ctx, const gipc_bsr* A, const double* rhs, double
     gipc_status s;
     const int64_t nvec = 3 * n;
     const unsigned vb = vec_blocks(n), sb = spmv_blocks(n), ub = upd_blocks(n), db = dir_blocks(n);
-    const FusePlan fuse = voff ? FusePlan{} : plan_fused(n);
+    const FusePlan fuse = voff ? FusePlan{} : (A->prec == GIPC_FP64 ? plan_fused<false>(n) : plan_fused<true>(n));
     const unsigned maxb = std::max(std::max(std::max(sb, vb), ub), fuse.grid);
     if ((s = ctx->slot[P_VEC].reserve(sizeof(double) * 6 * nvec)) != GIPC_OK) return s;
     if ((s = ctx->slot[P_PINV].reserve(sizeof(double) * 6 * n)) != GIPC_OK) return s;
@@ -1306,8 +1402,8 @@ gipc_status pcg_impl(gipc_ctx* ctx, const gipc_bsr* A, const double* rhs, double
                                      (!voff && (prm->flags & GIPC_PCG_STOP_ON_INDEFINITE)) ? 1 : 0);
     soa_to_aos_kernel<<<eb, 256, 0, st>>>(rhs, b, nullptr, n, fixed);
     soa_to_aos_kernel<<<eb, 256, 0, st>>>(x, xv, x32, n, fixed);
-    if (f64) pcg_factor_kernel<double><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(A->rowptr, A->colidx, (const double*)A->vals, n, pinv);
-    else pcg_factor_kernel<float><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(A->rowptr, A->colidx, (const float*)A->vals, n, pinv);
+    if (f64) pcg_factor_kernel<double, double><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(A->rowptr, A->colidx, (const double*)A->vals, n, pinv);
+    else pcg_factor_kernel<float, float><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(A->rowptr, A->colidx, (const float*)A->vals, n, reinterpret_cast<float*>(pinv));
     // q = S(H x0), reusing the spmv kernel with a scratch dot (alpha is overwritten at iteration 1)
     if (f64) pcg_spmv_kernel<double, double><<<sb, kPcgThreads, 0, st>>>(A->rowptr, A->colidx, (const double*)A->vals, xv, xv, perm, q, fixed, n, part, S, false);
     else pcg_spmv_kernel<float, float><<<sb, kPcgThreads, 0, st>>>(A->rowptr, A->colidx, (const float*)A->vals, x32, xv, perm, q, fixed, n, part, S, false);
@@ -1315,9 +1411,11 @@ gipc_status pcg_impl(gipc_ctx* ctx, const gipc_bsr* A, const double* rhs, double
     if (voff) {
         if ((s = ctx->slot[P_SCENE].reserve(sizeof(SceneScalars) * (nscenes + 1))) != GIPC_OK) return s;
         SS = ctx->slot[P_SCENE].as<SceneScalars>();
-        pcg_scene_init_kernel<<<nscenes, kPcgThreads, 0, st>>>(b, q, r, sv, c, c32, pinv, n, fixed, voff, nscenes, SS, S);
+        if (f64) pcg_scene_init_kernel<false><<<nscenes, kPcgThreads, 0, st>>>(b, q, r, sv, c, c32, pinv, n, fixed, voff, nscenes, SS, S);
+        else pcg_scene_init_kernel<true><<<nscenes, kPcgThreads, 0, st>>>(b, q, r, sv, c, c32, pinv, n, fixed, voff, nscenes, SS, S);
     } else {
-        pcg_init_kernel<<<vb, kPcgThreads, 0, st>>>(b, q, r, sv, c, c32, c2, pinv, fixed, n, part, S);
+        if (f64) pcg_init_kernel<false><<<vb, kPcgThreads, 0, st>>>(b, q, r, sv, c, c32, c2, pinv, fixed, n, part, S);
+        else pcg_init_kernel<true><<<vb, kPcgThreads, 0, st>>>(b, q, r, sv, c, c32, c2, pinv, fixed, n, part, S);
     }
     if ((s = check_launch("gipc_pcg: setup")) != GIPC_OK) return s;
 
@@ -1340,8 +1438,12 @@ gipc_status pcg_impl(gipc_ctx* ctx, const gipc_bsr* A, const double* rhs, double
             ctx->prof.stop(GIPC_PROF_PCG_SPMV, st);
             if (voff) {
                 ctx->prof.start(GIPC_PROF_PCG_UPDATE, st);
-                pcg_scene_step_kernel<<<nscenes, kPcgThreads, 0, st>>>(xv, r, c, c32, q, sv, pinv, n, fixed, voff,
-                                                                       nscenes, SS, S);
+                if (f64)
+                    pcg_scene_step_kernel<false><<<nscenes, kPcgThreads, 0, st>>>(xv, r, c, c32, q, sv, pinv, n, fixed,
+                                                                                  voff, nscenes, SS, S);
+                else
+                    pcg_scene_step_kernel<true><<<nscenes, kPcgThreads, 0, st>>>(xv, r, c, c32, q, sv, pinv, n, fixed,
+                                                                                 voff, nscenes, SS, S);
                 ctx->prof.stop(GIPC_PROF_PCG_UPDATE, st);
                 continue;
             }
@@ -1350,16 +1452,20 @@ gipc_status pcg_impl(gipc_ctx* ctx, const gipc_bsr* A, const double* rhs, double
                 int64_t n_arg = n;
                 const uint8_t* fixed_arg = fixed;
                 void* args[] = {&xv, &r, &c, &c32, &c2, &q, &pinv, &fixed_arg, &n_arg, &part, &S};
-                if (cudaLaunchCooperativeKernel((const void*)pcg_update_direction_kernel, dim3(fuse.grid), dim3(kUpdT), args,
+                const void* fused_fn = f64 ? (const void*)pcg_update_direction_kernel<false>
+                                           : (const void*)pcg_update_direction_kernel<true>;
+                if (cudaLaunchCooperativeKernel(fused_fn, dim3(fuse.grid), dim3(kUpdT), args,
                                                 fuse.smem, st) != cudaSuccess)
                     return check_launch("gipc_pcg: fused update");
                 ctx->prof.stop(GIPC_PROF_PCG_UPDATE, st);
                 continue;
             }
-            pcg_update_kernel<<<ub, kUpdT, 0, st>>>(xv, r, c, q, sv, pinv, n, part, S);
+            if (f64) pcg_update_kernel<false><<<ub, kUpdT, 0, st>>>(xv, r, c, q, sv, pinv, n, part, S);
+            else pcg_update_kernel<true><<<ub, kUpdT, 0, st>>>(xv, r, c, q, sv, pinv, n, part, S);
             ctx->prof.stop(GIPC_PROF_PCG_UPDATE, st);
             ctx->prof.start(GIPC_PROF_PCG_DIRECTION, st);
-            pcg_direction_kernel<<<db, kPcgThreads, 0, st>>>(c, c32, c2, sv, fixed, n, S);
+            if (f64) pcg_direction_kernel<false><<<db, kPcgThreads, 0, st>>>(c, c32, c2, sv, fixed, n, S);
+            else pcg_direction_kernel<true><<<db, kPcgThreads, 0, st>>>(c, c32, c2, sv, fixed, n, S);
             ctx->prof.stop(GIPC_PROF_PCG_DIRECTION, st);
         }
         launched += m;
@@ -1535,11 +1641,12 @@ extern "C" gipc_status gipc_pcg_noalloc(const gipc_bsr* A, const double* rhs, do
     pcg_set_scalars<<<1, 1, 0, st>>>(S, prm->rel_tol, max_iter, (prm->flags & GIPC_PCG_STOP_ON_INDEFINITE) ? 1 : 0);
     soa_to_aos_kernel<<<eb, 256, 0, st>>>(rhs, b, nullptr, n, fixed);
     soa_to_aos_kernel<<<eb, 256, 0, st>>>(x, xv, x32, n, fixed);
-    if (f64) pcg_factor_kernel<double><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(A->rowptr, A->colidx, (const double*)A->vals, n, pinv);
-    else pcg_factor_kernel<float><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(A->rowptr, A->colidx, (const float*)A->vals, n, pinv);
+    if (f64) pcg_factor_kernel<double, double><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(A->rowptr, A->colidx, (const double*)A->vals, n, pinv);
+    else pcg_factor_kernel<float, float><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(A->rowptr, A->colidx, (const float*)A->vals, n, reinterpret_cast<float*>(pinv));
     if (f64) pcg_spmv_kernel<double, double><<<sb, kPcgThreads, 0, st>>>(A->rowptr, A->colidx, (const double*)A->vals, xv, xv, perm, q, fixed, n, part, S, false);
     else pcg_spmv_kernel<float, float><<<sb, kPcgThreads, 0, st>>>(A->rowptr, A->colidx, (const float*)A->vals, x32, xv, perm, q, fixed, n, part, S, false);
-    pcg_init_kernel<<<vb, kPcgThreads, 0, st>>>(b, q, r, sv, c, c32, nullptr, pinv, fixed, n, part, S);
+    if (f64) pcg_init_kernel<false><<<vb, kPcgThreads, 0, st>>>(b, q, r, sv, c, c32, nullptr, pinv, fixed, n, part, S);
+    else pcg_init_kernel<true><<<vb, kPcgThreads, 0, st>>>(b, q, r, sv, c, c32, nullptr, pinv, fixed, n, part, S);
     if ((s = check_launch("gipc_pcg_noalloc: setup")) != GIPC_OK) return s;
 
     const int chunk = prm->check_every > 0 ? prm->check_every : (prm->rel_tol > 0.0 ? 16 : max_iter + 1);
@@ -1550,8 +1657,13 @@ extern "C" gipc_status gipc_pcg_noalloc(const gipc_bsr* A, const double* rhs, do
         for (int it = 0; it < m; ++it) {
             if (f64) pcg_spmv_kernel<double, double><<<sb, kPcgThreads, 0, st>>>(A->rowptr, A->colidx, (const double*)A->vals, c, c, perm, q, fixed, n, part, S, true);
             else pcg_spmv_kernel<float, float><<<sb, kPcgThreads, 0, st>>>(A->rowptr, A->colidx, (const float*)A->vals, c32, c, perm, q, fixed, n, part, S, true);
-            pcg_update_kernel<<<ub, kUpdT, 0, st>>>(xv, r, c, q, sv, pinv, n, part, S);
-            pcg_direction_kernel<<<db, kPcgThreads, 0, st>>>(c, c32, nullptr, sv, fixed, n, S);
+            if (f64) {
+                pcg_update_kernel<false><<<ub, kUpdT, 0, st>>>(xv, r, c, q, sv, pinv, n, part, S);
+                pcg_direction_kernel<false><<<db, kPcgThreads, 0, st>>>(c, c32, nullptr, sv, fixed, n, S);
+            } else {
+                pcg_update_kernel<true><<<ub, kUpdT, 0, st>>>(xv, r, c, q, sv, pinv, n, part, S);
+                pcg_direction_kernel<true><<<db, kPcgThreads, 0, st>>>(c, c32, nullptr, sv, fixed, n, S);
+            }
         }
         launched += m;
         if ((s = check_launch("gipc_pcg_noalloc: iteration")) != GIPC_OK) return s;
