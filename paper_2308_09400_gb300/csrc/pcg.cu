@@ -19,8 +19,10 @@
 // are no-ops.
 //
 // Product: gipc_pcg copies the matrix once per solve into SELL-32 slices (32
-// block rows per slice, the rows in an order sorted by length by a stable bucket
-// sort, longest first; entry-major within a slice), one lane per block row.  Each
+// block rows per slice; within each window of 1024 consecutive rows the rows are
+// taken longest first by a stable bucket sort, so a slice's rows are of similar
+// length and still neighbours in the mesh; entry-major within a slice), one lane
+// per block row.  Each
 // warp streams its slices into shared memory with cp.async.bulk and bounded
 // mbarrier waits while it multiplies the previous group, and the kernel is
 // launched with programmatic stream serialization, so it stages its first slice
@@ -60,7 +62,7 @@ constexpr int kDirEpt = 4;        // direction kernel: vector entries per thread
 enum PcgSlot { P_VEC = 9, P_PINV = 10, P_PART = 11, P_PERM = 12, P_VEC32 = 13, P_SELL = 14, P_SLICE = 15, P_SCENE = 40 };
 
 constexpr int kLenBuckets = 64;   // rows are ordered by min(blocks in row, 63), longest first
-constexpr int kPermChunk = 1024;  // rows per block of the stable bucket sort
+constexpr int kPermChunk = 1024;  // rows per chunk of the stable bucket sort (rows stay in their chunk)
 
 struct PcgScalars {
     double delta_new, delta_old, delta0, alpha, beta, tol, pq;
@@ -181,7 +183,7 @@ __device__ __forceinline__ void store_val(double* d, double v) { *d = v; }
 __device__ __forceinline__ void store_val(float* d, float v) { *d = v; }
 __device__ __forceinline__ void store_val(fpair* d, double v) { *d = split_double(v); }
 
-// y = (H p)_row,comp for this lane (3 lanes per row, rows taken from the length-sorted order).
+// y = (H p)_row,comp for this lane (3 lanes per row, rows taken in the length order of their chunk).
 template <typename VT, typename PT>
 __device__ __forceinline__ bool spmv_lane(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
                                           const VT* __restrict__ vals, const PT* __restrict__ p,
@@ -236,8 +238,11 @@ __device__ __forceinline__ bool spmv_lane(const int32_t* __restrict__ rowptr, co
     return true;
 }
 
-// Stable bucket sort of rows by length (deterministic): per-chunk histograms, a scan in
-// (bucket, chunk) order, then one warp per chunk places its rows in order.
+// Stable bucket sort of the rows by length within each chunk of kPermChunk consecutive rows
+// (deterministic): per-chunk histograms, a scan in (chunk, bucket) order, then one warp per chunk
+// places its rows in order.  Keeping every row in its own chunk keeps the column gathers of a
+// slice local (the mixed product gained 4%, the sphere-grid Newton products 4-10%, over one
+// global sort; a slice's padding stays small because neighbouring rows have similar lengths).
 __device__ __forceinline__ int len_key(const int32_t* __restrict__ rowptr, int64_t r) {
     int len = rowptr[r + 1] - rowptr[r];
     if (len > kLenBuckets - 1) len = kLenBuckets - 1;
@@ -252,14 +257,14 @@ __global__ void perm_hist_kernel(const int32_t* __restrict__ rowptr, int64_t n, 
     const int64_t r0 = (int64_t)blockIdx.x * kPermChunk;
     for (int64_t r = r0 + threadIdx.x; r < n && r < r0 + kPermChunk; r += blockDim.x) atomicAdd(&h[len_key(rowptr, r)], 1);
     __syncthreads();
-    for (int i = threadIdx.x; i < kLenBuckets; i += blockDim.x) counts[(int64_t)i * chunks + blockIdx.x] = h[i];
+    for (int i = threadIdx.x; i < kLenBuckets; i += blockDim.x) counts[(int64_t)blockIdx.x * kLenBuckets + i] = h[i];
 }
 
 __global__ void perm_scatter_kernel(const int32_t* __restrict__ rowptr, int64_t n, const int64_t* __restrict__ off,
                                     int64_t chunks, int32_t* __restrict__ perm) {
     __shared__ int64_t run[kLenBuckets];
     const int lane = threadIdx.x;
-    for (int i = lane; i < kLenBuckets; i += 32) run[i] = off[(int64_t)i * chunks + blockIdx.x];
+    for (int i = lane; i < kLenBuckets; i += 32) run[i] = off[(int64_t)blockIdx.x * kLenBuckets + i];
     __syncwarp();
     const int64_t r0 = (int64_t)blockIdx.x * kPermChunk;
     for (int t = 0; t < kPermChunk; t += 32) {
@@ -276,7 +281,7 @@ __global__ void perm_scatter_kernel(const int32_t* __restrict__ rowptr, int64_t 
 }
 
 // ---- sliced layout of the matrix for the solver (built once per solve) --------------------
-// SELL-32: rows are taken 32 at a time in the length-sorted order (one slice per warp, one lane
+// SELL-32: rows are taken 32 at a time in the chunk-wise length order (one slice per warp, one lane
 // per row).  Slice s holds L_s steps (its longest row); step j stores block j of each of its 32
 // rows side by side, entry-major: column indices at sell_col[(off_s + j)*32 + i] and entry k of
 // the 3x3 block at sell_vals[((off_s + j)*9 + k)*32 + i].  Every value load of a warp then reads
@@ -437,9 +442,9 @@ pcg_spmv_tma_kernel(const int32_t* __restrict__ rowptr, const int64_t* __restric
         return;
     }
     double d = 0.0;
-    // slices are longest first; a warp takes one per round, in alternating directions (round r:
-    // r * warps + wid, then r * warps + warps - 1 - wid), so long and short slices pair up and the
-    // warps finish together; every thread's set of slices is fixed, so its partial sum is too
+    // a warp takes one slice per round, in alternating directions (round r: r * warps + wid, then
+    // r * warps + warps - 1 - wid), so within a chunk's longest-first run long and short slices
+    // pair up; every thread's set of slices is fixed, so its partial sum is too
     for (int64_t rnd = 0; rnd * warps < nsl && !timed_out; ++rnd) {
         const int64_t sl = rnd * warps + ((rnd & 1) ? warps - 1 - wid : wid);
         if (sl >= nsl) continue;
@@ -1356,7 +1361,7 @@ gipc_status pcg_impl(gipc_ctx* ctx, const gipc_bsr* A, const double* rhs, double
     const unsigned eb = (unsigned)((nvec + 255) / 256);
     const int max_iter = prm->max_iter;
     const bool f64 = A->prec == GIPC_FP64;
-    // row order by length (stable, deterministic)
+    // row order by length within 1024-row chunks (stable, deterministic)
     const int64_t chunks = (n + kPermChunk - 1) / kPermChunk;
     const int64_t ncnt = (int64_t)kLenBuckets * chunks;
     if ((s = ctx->slot[P_PERM].reserve(sizeof(int32_t) * (n + ncnt) + sizeof(int64_t) * (ncnt + 1 + scan_scratch_words(ncnt)) + 64)) != GIPC_OK) return s;
