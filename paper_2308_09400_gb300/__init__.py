@@ -216,7 +216,9 @@ def pcg(A, rhs, x0=None, fixed=None, rel_tol=1e-4, max_iter=1000, check_every=0,
     """Modified block-Jacobi PCG on an assembled BSR (gipc_pcg).
 
     ``A`` is the dict returned by ``assemble_bsr``; ``rhs`` float64 [3, n].  Returns
-    (x [3, n], iterations, delta_new / delta_0).  A capped solve with rel_tol > 0
+    (x [3, n], iterations, delta_new / delta_0).  A mixed-precision ``A`` (float32 blocks) is
+    solved with a float32 product, float32 block-Jacobi factors, preconditioned residual and
+    direction, and float64 x, r and dot products.  A capped solve with rel_tol > 0
     returns its last iterate unless ``raise_on_nonconvergence``.  ``product`` selects the
     arithmetic of H c for FP64 matrices: "native" or "float_pair" (gipc_product).  With
     ``stop_on_indefinite`` a direction with c.Hc <= 0 raises GipcError (GIPC_ERR_INDEFINITE).
