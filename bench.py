@@ -56,6 +56,9 @@ def parse():
                     help="checkpointed steps of the beam-on-plate scene differentiated by the adjoint (0: skip)")
     ap.add_argument("--c2-steps", type=int, default=3,
                     help="time steps of the per-step FP64 / mixed converged-position comparison (0: skip)")
+    ap.add_argument("--per-type", type=int, default=0, metavar="K",
+                    help="instead of the step: evaluate K stencils of each type alone, FP64 and mixed, "
+                         "3x3 sub-block output, and print the rate per type (K-stencil launches)")
     return ap.parse_args()
 
 
@@ -718,10 +721,51 @@ def run_reference(args):
     }))
 
 
+def run_per_type(args):
+    """Stencil evaluation rate of each type alone (same recipe as the C1 mix, one type per launch).
+
+    Each type gets K stencils with their own vertices; eps_x, then ``warmup`` untimed and ``steps``
+    timed evaluations per precision, timed by CUDA events on the current stream.  The launches
+    come in the order of ``synth.TYPE_IDS``, FP64 before mixed, which is how an instruction-count
+    capture of this command is read per type."""
+    import torch
+    import synth
+    import paper_2308_09400_gb300 as g
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    k = args.per_type
+    rows = {}
+    for kind in synth.TYPE_IDS:
+        B = synth.batch_stencils(k, mix=((kind, 1.0),))
+        x = torch.tensor(B["x"], device=dev)
+        st = torch.tensor(B["stencils"], device=dev)
+        eps = g.compute_eps_x(x, st)
+        row = {}
+        for prec in ("fp64", "mixed"):
+            out = None
+            t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            for it in range(args.warmup + args.steps):
+                if it == args.warmup:
+                    torch.cuda.synchronize()
+                    t0.record()
+                out = g.eval_stencils(x, st, eps, B["dhat"], KAPPA, precision=prec, mode="blocks", out=out)
+            t1.record()
+            torch.cuda.synchronize()
+            ms = t0.elapsed_time(t1) / max(args.steps, 1)
+            active = int(((out["flags"] & 1) != 0).sum().item())
+            row[prec] = {"ms": ms, "stencils_per_s": k / ms * 1e3, "active": active}
+        rows[kind] = row
+    print(json.dumps({"per_type": rows, "stencils_per_type": k, "steps": args.steps, "warmup": args.warmup,
+                      "output": "energy, gradient, projected Hessian as 3x3 sub-blocks, flags"}))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.per_type > 0:
+        run_per_type(args)
     else:
         run_gpu(args)
 
