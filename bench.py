@@ -665,7 +665,9 @@ def run_diff_bench(g, dev, ctx, steps, fd_h=1e-6, eps_d=1e-5, eps_polish=1e-12):
 
 # ----------------------------------------------------------------------------- oracle (CPU) arm
 def oracle_step(args, Wh, sample, pool_procs):
-    """The oracle's whole path on the first ``sample`` stencils of the batch (full vertex space)."""
+    """The oracle's whole path on the first ``sample`` stencils of the batch (full vertex space).
+
+    Returns the PCG result and the seconds its stencil evaluation took."""
     import numpy as np
     from oracle import assembly as OA
     from oracle import pcg as OP
@@ -673,25 +675,39 @@ def oracle_step(args, Wh, sample, pool_procs):
     st = np.ascontiguousarray(Wh["st_own"][:, :sample])
     sh = np.ascontiguousarray(Wh["st_sheet"][:, :sample])
     eps = OS.compute_eps_x(Wh["x"], st)
+    t_eval = time.perf_counter()
     r = OS.eval_stencils(Wh["x"], st, eps, Wh["dhat"], KAPPA, processes=pool_procs)
+    eval_s = time.perf_counter() - t_eval
     if args.hess_mode == "rank1":
         sd = {"kind": "rank1", "lam": r["lam"], "w": r["w"], "grad": r["grad"]}
     else:
         sd = {"kind": "dense", "hess": r["hess"], "grad": r["grad"]}
     A = OA.assemble(Wh["n"], sh, sd, None, None, Wh["mass"])
     out = OP.pcg(A, Wh["n"], -A["grad"], tol=0.0, max_iter=PCG_ITERS)
-    return out
+    return out, eval_s
 
 
-def cpu_baseline(args, Wh, sample):
+def cpu_baseline(args, Wh, sample, single=500):
+    """The oracle's whole step on a sample of the batch on all host cores, and its stencil
+    evaluation alone on all cores and on one core (a smaller sample)."""
+    import numpy as np
+    from oracle import stencil as OS
     procs = os.cpu_count() or 1
     t = time.perf_counter()
-    oracle_step(args, Wh, sample, procs)
+    _, eval_s = oracle_step(args, Wh, sample, procs)
     dt = time.perf_counter() - t
+    eval_all = sample / eval_s
+    st = np.ascontiguousarray(Wh["st_own"][:, :single])
+    eps = OS.compute_eps_x(Wh["x"], st)
+    t1 = time.perf_counter()
+    OS.eval_stencils(Wh["x"], st, eps, Wh["dhat"], KAPPA, processes=1)
+    eval_one = single / (time.perf_counter() - t1)
     return {"value": sample / dt, "unit": "stencils/s", "cores": procs, "kind": "oracle",
             "sample": f"first {sample} of the {K_STENCILS} stencils: exact-geometry oracle eval "
                       f"({procs} spawn processes), plain assembly over all {Wh['n']} vertices, "
-                      f"{PCG_ITERS} PCG iterations; {dt:.1f} s"}
+                      f"{PCG_ITERS} PCG iterations; {dt:.1f} s",
+            "eval_only": {"all_cores": eval_all, "cores": procs, "single_thread": eval_one,
+                          "single_thread_sample": single, "unit": "stencils/s"}}
 
 
 def run_reference(args):
