@@ -46,10 +46,8 @@ enum DiffSlot { D_ELEM = 49, D_VEC = 50, D_RED = 51, D_CON = 52, D_HES = 53, D_A
 struct HD {
     double v, a, b, ab;
 };
-__device__ __forceinline__ HD hd(double v) { return {v, 0.0, 0.0, 0.0}; }
 __device__ __forceinline__ HD operator+(HD x, HD y) { return {x.v + y.v, x.a + y.a, x.b + y.b, x.ab + y.ab}; }
 __device__ __forceinline__ HD operator-(HD x, HD y) { return {x.v - y.v, x.a - y.a, x.b - y.b, x.ab - y.ab}; }
-__device__ __forceinline__ HD operator-(HD x) { return {-x.v, -x.a, -x.b, -x.ab}; }
 __device__ __forceinline__ HD operator*(HD x, HD y) {
     return {x.v * y.v, x.a * y.v + x.v * y.a, x.b * y.v + x.v * y.b, x.ab * y.v + x.a * y.b + x.b * y.a + x.v * y.ab};
 }
