@@ -172,7 +172,10 @@ def test_invalid_and_inactive_stencils(gipc):
 
 
 def test_full_size_batch_sampled(gipc):
-    """1M stencils in the launch configuration the benchmark times; 2000 sampled outputs vs the oracle."""
+    """1M stencils in the launch configurations the benchmark times; 2000 sampled outputs vs the
+    oracle: FP64 with entry-major and with 3x3 sub-block output (parity bar 1e-10), and the mixed
+    rank-one output (lambda, w in float32; per-block relative Frobenius error of lambda w w^T
+    <= 1e-4, energy and gradient 1e-6)."""
     d = synth.batch_stencils(1_000_000, seed=20230810)
     x, st = _dev(d["x"]), _dev(d["stencils"])
     eps = gipc.compute_eps_x(x, st)
@@ -185,3 +188,32 @@ def test_full_size_batch_sampled(gipc):
     ref = S.eval_stencils(d["x"], sub, eps_ref, d["dhat"], KAPPA, processes=NPROC)
     got = {k: (v.cpu().numpy()[..., idx]) for k, v in r.items()}
     assert_parity(got, ref, sub)
+    n3 = _n3(sub)
+    # FP64, 3x3 sub-blocks per stencil (the FP64 step's layout): the same values as the oracle's
+    ti = torch.tensor(idx, device=x.device)
+    blk = gipc.eval_stencils(x, st, eps, d["dhat"], KAPPA, mode="blocks")
+    hb = blk["hess"].index_select(0, ti).cpu().numpy()                   # [2000, 144]
+    dense = np.zeros((144, len(idx)))
+    for j, s3 in enumerate(n3):
+        for a in range(s3):
+            for b in range(s3):
+                dense[a * s3 + b, j] = hb[j, ((a // 3) * 4 + b // 3) * 9 + (a % 3) * 3 + b % 3]
+    got_b = {k: v.index_select(-1, ti).cpu().numpy() for k, v in blk.items() if k != "hess"}
+    got_b["hess"] = dense
+    assert_parity(got_b, ref, sub)
+    # mixed, rank-one output (the mixed step's configuration)
+    m = gipc.eval_stencils(x, st, eps, d["dhat"], KAPPA, precision="mixed", mode="rank1",
+                           want=("energy", "grad", "hess", "lam", "flags"))
+    mw = m["hess"].index_select(1, ti).cpu().numpy().astype(np.float64)   # w [12, 2000], float32
+    ml = m["lam"].index_select(0, ti).cpu().numpy().astype(np.float64)
+    np.testing.assert_array_equal(m["flags"].index_select(0, ti).cpu().numpy(), ref["flags"])
+    worst = 0.0
+    for j, s3 in enumerate(n3):
+        hr = ref["hess"][: s3 * s3, j].reshape(s3, s3)
+        nr = np.linalg.norm(hr)
+        if nr > 0:
+            hg = ml[j] * np.outer(mw[:s3, j], mw[:s3, j])
+            worst = max(worst, np.linalg.norm(hg - hr) / nr)
+    assert worst <= 1e-4, worst
+    got_m = {k: m[k].index_select(-1, ti).cpu().numpy() for k in ("energy", "grad", "flags")}
+    assert_parity(got_m, ref, sub, rtol=1e-6, what=("energy", "grad"))
