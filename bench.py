@@ -360,6 +360,7 @@ def run_gpu(args):
             line["batched"] = run_batch_bench(g, dev, ctx, args.batch_steps)
         if args.diff_steps > 0:
             line["differentiation"] = run_diff_bench(g, dev, ctx, args.diff_steps)
+            line["beam_plate"] = run_beam_forms(g, dev, args.diff_steps)
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args, Wh, sample=16000)
         print(json.dumps(line))
@@ -485,6 +486,43 @@ def run_newton(g, dev, ctx, steps, c2_steps=0):
                                "contacts_final": st["contacts"], "phase_ms_per_newton_iter": phase}
     if c2_steps > 0:
         out["converged_position_error"] = run_c2(g, scene, sc, prm, dev, c2_steps)
+    return out
+
+
+def run_beam_forms(g, dev, steps):
+    """Implicit time steps of the beam-on-plate scene (the differentiation workload) through
+    gipc_newton_step in the FP64 dense and mixed rank-one forms, from the same initial state, at
+    the forward settings of the sphere-grid scene (eps_d 1e-2, PCG tol 1e-4, no refinement)."""
+    import numpy as np
+    import torch
+    import synth
+
+    sc = synth.beam_on_plate()
+    T = lambda a: torch.tensor(np.ascontiguousarray(a), device=dev)
+    srf = g.Surface(T(sc["tris"]), T(sc["edges"]), T(sc["verts"]))
+    scene = g.Scene(T(sc["x"]), T(sc["tets"]), srf, 1000.0, fixed=T(sc["fixed"]), l=sc["l"])
+    mu, lam = g.snh_params(1e5, 0.4)
+    prm = dict(dt=0.01, mu=mu, lam=lam, dhat=sc["dhat"], kappa=KAPPA, eps_d=1e-2, pcg_tol=1e-4,
+               max_pcg=1000, max_newton=50)
+    out = {"workload": "tet beam 41x11x11 on a tet plate 65x65x4 (the differentiation scene)",
+           "vertices": int(sc["x"].shape[1]), "tets": int(sc["tets"].shape[1]), "eps_d": 1e-2, "pcg_tol": 1e-4}
+    for prec, hm in NEWTON_FORMS:
+        x, v = T(sc["x"]), T(sc["v"])
+        g.newton_step(scene, x.clone(), v.clone(), precision=prec, hess_mode=hm, **prm)   # warm-up
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        iters = pcg = 0
+        e0.record()
+        for _ in range(steps):
+            st = g.newton_step(scene, x, v, precision=prec, hess_mode=hm, **prm)
+            iters += st["newton_iters"]
+            pcg += st["pcg_iters"]
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        out[f"{prec}_{hm}"] = {"newton_iters_per_s": iters / (ms * 1e-3), "ms_per_newton_iter": ms / max(iters, 1),
+                               "time_steps": steps, "newton_iters": iters, "pcg_iters": pcg,
+                               "contacts_final": st["contacts"]}
     return out
 
 
