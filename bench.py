@@ -567,6 +567,18 @@ def run_batch_bench(g, dev, ctx, steps):
         torch.cuda.synchronize()
         ms_b = e0.elapsed_time(e1)
         its = sum(per_step)
+        # the same batched steps once more with the phase spans on (outside the timed region)
+        xp, vp = b.scene.rest_x.clone(), T(v_init)
+        torch.cuda.synchronize()
+        ctx.profile_begin()
+        for _ in range(steps):
+            g.newton_step_batch(b, xp, vp, precision=prec, hess_mode=hm, **prm)
+        torch.cuda.synchronize()
+        prof = ctx.profile_read()
+        ctx.profile_stop()
+        phases = {k: v[1] / steps for k, v in prof.items() if v[0] and k not in ("pcg_spmv", "pcg_update", "pcg_direction")}
+        pcg_spans = {k: {"spans": v[0], "mean_us": v[1] / v[0] * 1e3} for k, v in prof.items()
+                     if v[0] and k in ("pcg_spmv", "pcg_update", "pcg_direction")}
         # the same steps, every scene alone
         xs = [T(sc["x"]) for sc in scenes]
         vs = [T(sc["v"]) for sc in scenes]
@@ -584,7 +596,8 @@ def run_batch_bench(g, dev, ctx, steps):
                                "one_at_a_time_ms_per_step": ms_p / steps,
                                "one_at_a_time_scene_iters_per_s": its1 / (ms_p * 1e-3),
                                "scene_newton_iters": its, "scene_newton_iters_one_at_a_time": its1,
-                               "scene_newton_iters_per_step": per_step, "speedup": ms_p / ms_b}
+                               "scene_newton_iters_per_step": per_step, "speedup": ms_p / ms_b,
+                               "phase_ms_per_step": phases, "pcg_kernel_spans": pcg_spans}
     return out
 
 
