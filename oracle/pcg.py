@@ -38,8 +38,12 @@ def block_jacobi_inverse(A, n):
     return inv
 
 
-def pcg(A, n, b, fixed=None, tol=1e-4, max_iter=1000, x0=None, history=False):
-    """Returns dict(x (3,n), iters, rel (delta_new/delta_0), delta_0, [deltas])."""
+def pcg(A, n, b, fixed=None, tol=1e-4, max_iter=1000, x0=None, history=False, trace=False):
+    """Returns dict(x (3,n), iters, rel (delta_new/delta_0), delta_0, [deltas]).
+
+    trace=True also returns the iterates, residuals and search directions of every iteration
+    ("xs", "rs", "cs": lists of (n, 3) vertex-major arrays, index k after k iterations; "cs"[k]
+    is the direction used by iteration k + 1) for checks of the iteration itself."""
     M = bsr_to_scipy(A, n)
     Pinv = block_jacobi_inverse(A, n)
     free = np.ones((n, 3)) if fixed is None else np.repeat((~np.asarray(fixed, bool))[:, None], 3, 1).astype(float)
@@ -54,6 +58,7 @@ def pcg(A, n, b, fixed=None, tol=1e-4, max_iter=1000, x0=None, history=False):
     delta_new = float(np.sum(r * z))
     delta_0 = delta_new
     deltas = [delta_new]
+    xs, rs, cs = [x], [r], [c]
     k = 0
     while k < max_iter and delta_new > 0 and delta_new >= tol * delta_0:
         q = S(matvec(c))
@@ -66,7 +71,13 @@ def pcg(A, n, b, fixed=None, tol=1e-4, max_iter=1000, x0=None, history=False):
         c = S(s + (delta_new / delta_old) * c)
         k += 1
         deltas.append(delta_new)
+        if trace:
+            xs.append(x)
+            rs.append(r)
+            cs.append(c)
     out = {"x": x.T.copy(), "iters": k, "rel": delta_new / delta_0 if delta_0 > 0 else 0.0, "delta_0": delta_0}
     if history:
         out["deltas"] = deltas
+    if trace:
+        out.update(xs=xs, rs=rs, cs=cs)
     return out

@@ -110,6 +110,81 @@ def test_accd_is_conservative():
     assert C.accd(X, [(0, 0, 0.02)] + P[1:], "PT") == 1.0
 
 
+# ---- ACCD against the time of impact of linear motions --------------------------------------
+# For two primitives translating toward each other along the common normal, the distance falls
+# linearly, d(t) = h - v t, and the relative speed bound l_p of additive CCD equals v.  Its first
+# advance (1 - s) d0 / l_p then lands exactly at distance s d0, and the next advance would go
+# below s d0, so the returned step is (1 - s) TOI with TOI = h / v (capped at 1).  For an oblique
+# translation (speed |P| > normal speed a) the distance is still h - a t and the steps follow the
+# advance law t += 0.9 d / l_p until the next one would end below s d0.
+
+def _accd_expected(h, a, L, s=0.1, tmax=1.0):
+    """The ACCD step for the exact distance d(t) = h - a t and speed bound L."""
+    t = 0.0
+    tl = (1.0 - s) * h / L
+    while True:
+        d_next = h - a * (t + tl)
+        if t > 0.0 and d_next < s * h:
+            return t
+        t = t + tl
+        if t > tmax:
+            return tmax
+        tl = 0.9 * d_next / L
+
+
+def _head_on_cases():
+    tri = [(-1.0, -1.0, 0.0), (2.0, -1.0, 0.0), (-1.0, 2.0, 0.0)]
+    for h, vp, vt in ((0.01, 0.02, 0.0), (0.003, 0.01, 0.004), (0.2, 0.05, 0.0), (1e-4, 3e-3, 1e-3)):
+        X = [(0.2, 0.3, h)] + tri
+        P = [(0.0, 0.0, -vp)] + [(0.0, 0.0, vt)] * 3
+        yield "PT", X, P, h / (vp + vt)
+    for h, u, v in ((0.01, 0.01, 0.01), (0.004, 0.0, 0.02), (0.3, 0.1, 0.05)):
+        X = [(-1.0, 0.1, 0.0), (1.0, 0.1, 0.0), (0.2, -1.0, h), (0.2, 1.0, h)]
+        P = [(0.0, 0.0, u)] * 2 + [(0.0, 0.0, -v)] * 2
+        yield "EE", X, P, h / (u + v)
+
+
+def _check_head_on(accd):
+    worst = 0.0
+    for kind, X, P, toi in _head_on_cases():
+        want = min(1.0, 0.9 * toi)
+        worst = max(worst, abs(accd(X, P, kind) - want) / want)
+    return worst
+
+
+def _check_oblique(accd):
+    worst = 0.0
+    tri = [(-1.0, -1.0, 0.0), (2.0, -1.0, 0.0), (-1.0, 2.0, 0.0)]
+    for h, a, tang in ((0.01, 0.02, 0.03), (0.002, 0.001, 0.004), (0.05, 0.01, 0.002)):
+        X = [(0.1, 0.2, h)] + tri
+        P = [(tang, 0.0, -a)] + [(0.0, 0.0, 0.0)] * 3
+        want = _accd_expected(h, a, math.hypot(tang, a))
+        worst = max(worst, abs(accd(X, P, "PT") - want) / want)
+    return worst
+
+
+def test_accd_step_is_the_time_of_impact_law():
+    assert _check_head_on(C.accd) < 1e-12
+    assert _check_oblique(C.accd) < 1e-12
+
+
+def test_accd_pins_catch_planted_mistakes():
+    import inspect
+    src = inspect.getsource(C.accd)
+
+    def mutant(old, new):
+        assert src.count(old) == 1, old
+        ns = dict(vars(C))
+        exec(compile(src.replace(old, new), "<mutant>", "exec"), ns)
+        return ns["accd"]
+
+    halved = mutant("    return t\n", "    return 0.5 * t\n")
+    timid_first = mutant("tl = (1.0 - s) * d / lp", "tl = 0.5 * (1.0 - s) * d / lp")
+    timid_later = mutant("tl = 0.9 * d / lp", "tl = 0.5 * d / lp")
+    for m in (halved, timid_first, timid_later):
+        assert max(_check_head_on(m), _check_oblique(m)) > 1e-3
+
+
 def test_intersection_check():
     sc = synth.two_cubes()
     x = sc["x"].copy()
