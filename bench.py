@@ -97,9 +97,9 @@ def job_rate(units_per_rank, world, ms):
 def workload(seed_offset=0):
     import synth
     d = synth.batch_stencils(K_STENCILS, seed=20230810 + seed_offset)
-    st_sheet, n = synth.sheet_index_space(K_STENCILS, seed=20230811 + seed_offset)
+    st_sheet, n, ids = synth.sheet_index_space(K_STENCILS, seed=20230811 + seed_offset, return_ids=True)
     return {"x": d["x"], "st_own": d["stencils"], "dhat": d["dhat"], "st_sheet": st_sheet, "n": n,
-            "mass": synth.sheet_mass()}
+            "mass": synth.sheet_mass(), "sheet_ids": ids}
 
 
 def workload_desc(args):
@@ -191,7 +191,7 @@ def _scan_launches(m):
     return 1 if m <= 4096 else 2 + _scan_launches((m + 4095) // 4096)
 
 
-def launches_per_step(n, nnzb, sms=152):
+def launches_per_step(n, nnzb, loop_launches_per_step):
     """The library's kernel launches in one C1 step (the sequence a launch list shows).
 
     eps_x + evaluation; assembly: row init, count, cursor init, fill, three row sorts, rowptr,
@@ -199,13 +199,13 @@ def launches_per_step(n, nnzb, sms=152):
     the n rows and one over the 32 count bins x 1024-block chunks; solver: row-length
     histogram + scatter (+ scan of the 64 buckets x 1024-row chunks), slice lengths + fill (+ scan
     of the SELL-32 slices), scalars, two layout conversions, factors, the first product, setup, the
-    final layout conversion, and per iteration the product plus the fused update / direction (the
-    separate update and direction when the fused kernel's tiles do not fit: 8 x 256 vertices per
-    CTA, 2 CTAs per SM)."""
+    final layout conversion, and the iterations: one persistent launch for all of them (the
+    profiler's span count says whether it ran), else the product plus the fused update / direction
+    per iteration."""
     order = (2 + _scan_launches(32 * ((nnzb + 1023) // 1024))) if nnzb > 0 else 0
     scans = 2 * _scan_launches(n) + _scan_launches(64 * ((n + 1023) // 1024)) + _scan_launches((n + 31) // 32)
-    fused = (n + 255) // 256 <= 8 * 2 * sms
-    return 2 + 12 + order + 11 + scans + (2 if fused else 3) * PCG_ITERS
+    solver = 1 if loop_launches_per_step >= 1 else 2 * PCG_ITERS
+    return 2 + 12 + order + 11 + scans + solver
 
 
 def source_hash(*rel):
@@ -307,31 +307,8 @@ def run_gpu(args):
     e2e_ms = max_over_ranks(e2e_ms, world, dev)
 
     if rank == 0:
-        hbm, hbm_src = peaks()
         n = Wh["n"]
-        spmv_n, spmv_ms = prof["pcg_spmv"]
-        avg = spmv_ms / max(spmv_n, 1) * 1e-3
-        vb = 8 if args.precision == "fp64" else 4
-        bytes_l = nnzb * (9 * vb + 4) + n * (4 + 24 + 24)
-        flops_l = 18 * nnzb + 6 * n
-        ach_bw = bytes_l / avg / 1e9
-        ach_fl = flops_l / avg / 1e9
-        if args.precision == "fp64" and ach_fl / FP64_PEAK > ach_bw / hbm:
-            roof = {"bound": "alu", "achieved": ach_fl / 1e3, "peak": FP64_PEAK / 1e3, "unit": "TFLOP/s",
-                    "frac": ach_fl / FP64_PEAK, "kernel": "pcg_spmv_tma_kernel<double, double, 1, 16, 2>",
-                    "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2070 MHz (probe measured 1.26 TFLOP/s)",
-                    "hbm_frac": ach_bw / hbm}
-        else:
-            roof = {"bound": "hbm", "achieved": ach_bw, "peak": hbm, "unit": "GB/s", "frac": ach_bw / hbm,
-                    "kernel": ("pcg_spmv_tma_kernel<double, double, 1, 16, 2>" if args.precision == "fp64"
-                               else "pcg_spmv_tma_kernel<float, float, 2, 16, 2>"),
-                    "peak_source": f"{hbm_src} (MEASURED_PEAKS.json hbm_gbs)" if hbm_src == "measured" else hbm_src,
-                    "fp64_frac": ach_fl / FP64_PEAK if args.precision == "fp64" else None}
-        roof["algorithmic_bytes_per_launch"] = bytes_l
-        roof["algorithmic_flops_per_launch"] = flops_l
-        roof["avg_launch_us"] = avg * 1e6
-        roof["launches"] = spmv_n
-        roof["traffic"] = measured_traffic("pcg_spmv", args.precision)
+        roof = solver_roofline(prof, args.precision, n, nnzb)
         line = {
             "metric": METRIC, "value": job_rate(K_STENCILS, world, ms), "unit": "stencils/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
@@ -349,11 +326,12 @@ def run_gpu(args):
             "roofline": roof,
             "e2e": {"value": job_rate(K_STENCILS, world, e2e_ms), "unit": "stencils/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
-            "gpu_launches": launches_per_step(n, nnzb) * args.steps,
+            "gpu_launches": launches_per_step(n, nnzb, prof["pcg_loop"][0] / args.steps) * args.steps,
             "clocks": clk,
         }
         if args.precision == "fp64" and args.hess_mode == "dense" and args.product == "native":
-            line["float_pair_product"] = run_float_pair(g, dev, W, args, bufs, ctx, bytes_l, hbm)
+            line["float_pair_product"] = run_float_pair(g, dev, W, args, bufs, ctx)
+            line["mixed"] = run_mixed(g, dev, W, Wh, args, ctx)
         if args.newton_steps > 0:
             line["newton"] = run_newton(g, dev, ctx, args.newton_steps, args.c2_steps)
         if args.batch_steps > 0:
@@ -362,44 +340,155 @@ def run_gpu(args):
             line["differentiation"] = run_diff_bench(g, dev, ctx, args.diff_steps)
             line["beam_plate"] = run_beam_forms(g, dev, args.diff_steps)
         if world == 1 and not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(args, Wh, sample=16000)
+            line["cpu_baseline"] = cpu_baseline(args, Wh)
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
 
 
-def run_float_pair(g, dev, W, args, bufs, ctx, bytes_l, hbm):
-    """The same C1 step with the solver's H c in double-float arithmetic (gipc_product
-    GIPC_PRODUCT_FLOAT_PAIR): time per step, the SpMV against the HBM roof (same bytes as FP64),
-    and the Newton direction's deviation from the native FP64 result after the same iterations."""
-    import argparse
+# Algorithmic work of one solver iteration (FP64 flops count an FMA as two):
+#   product: 9 FMA per block (18 flops), per row 3 adds + 3 FMA for a0 + a1 and c . q (9 flops);
+#   vector phases per vertex: x += alpha c, r -= alpha q (12), the LDL^T solve and r . s (20),
+#   the partial sum (1), c = s + beta c (6): 39 flops;
+#   bytes: per block its values and column index, per row perm (4), q written (24) and c read
+#   (24); per vertex c, q, x, r read (96), the factors (48 FP64 / 24 float32), x, r, c written
+#   (72), and in the mixed form the float32 direction read and written (24).
+def iteration_work(precision, n, nnzb):
+    vb = 8 if precision == "fp64" else 4
+    flops = 18 * nnzb + 9 * n + 39 * n
+    bytes_ = nnzb * (9 * vb + 4) + n * (4 + 24 + 24) + n * (96 + (48 if precision == "fp64" else 24) + 72 +
+                                                           (0 if precision == "fp64" else 24))
+    return flops, bytes_
+
+
+def solver_roofline(prof, precision, n, nnzb, kernel=None):
+    """Roofline of the solver, the dominant kernel: algorithmic work of PCG_ITERS iterations over the
+    mean CUDA-event duration of the persistent solver launch (one per step); FP64 against the FP64
+    pipe, the mixed form against measured HBM bandwidth."""
+    hbm, hbm_src = peaks()
+    loop_n, loop_ms = prof["pcg_loop"]
+    flops_it, bytes_it = iteration_work(precision, n, nnzb)
+    if loop_n > 0:
+        avg = loop_ms / loop_n * 1e-3
+        its = PCG_ITERS
+        name = kernel or ("pcg_loop_kernel<double, double, 1, 2, false>" if precision == "fp64"
+                          else "pcg_loop_kernel<float, float, 2, 2, true>")
+    else:   # (fallback path) product + fused update per iteration, from their sampled spans
+        sp, up = prof["pcg_spmv"], prof["pcg_update"]
+        avg = (sp[1] / max(sp[0], 1) + up[1] / max(up[0], 1)) * 1e-3
+        its = 1
+        name = "pcg_spmv_tma_kernel + pcg_update_direction_kernel"
+    ach_fl = flops_it * its / avg / 1e9
+    ach_bw = bytes_it * its / avg / 1e9
+    if precision == "fp64":
+        roof = {"bound": "alu", "achieved": ach_fl / 1e3, "peak": FP64_PEAK / 1e3, "unit": "TFLOP/s",
+                "frac": ach_fl / FP64_PEAK,
+                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2070 MHz (an FMA probe measured 1.19-1.26 TFLOP/s)",
+                "hbm_frac": ach_bw / hbm}
+    else:
+        roof = {"bound": "hbm", "achieved": ach_bw, "peak": hbm, "unit": "GB/s", "frac": ach_bw / hbm,
+                "peak_source": f"{hbm_src} (MEASURED_PEAKS.json hbm_gbs)" if hbm_src == "measured" else hbm_src}
+    roof.update({"kernel": name, "launch_us": avg * 1e6, "iterations_per_launch": its,
+                 "us_per_iteration": avg * 1e6 / its, "algorithmic_flops_per_iteration": flops_it,
+                 "algorithmic_bytes_per_iteration": bytes_it, "launches": loop_n,
+                 "traffic": measured_traffic("pcg_loop", precision)})
+    return roof
+
+
+def timed_steps(g, dev, W, args, bufs, ctx, steps):
+    """`steps` C1 steps after two untimed ones: ms per step and the profiler's spans."""
     import torch
-    a2 = argparse.Namespace(**dict(vars(args), product="float_pair"))
-    d_native, _, _ = gpu_step(g, dev, W, args, bufs, ctx)   # the native solve of the same inputs
-    d_native = d_native.clone()
     for _ in range(2):
-        d2, _, _ = gpu_step(g, dev, W, a2, bufs, ctx)
+        gpu_step(g, dev, W, args, bufs, ctx)
     torch.cuda.synchronize()
     ctx.profile_begin()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
-    for _ in range(args.steps):
-        d2, _, _ = gpu_step(g, dev, W, a2, bufs, ctx)
+    for _ in range(steps):
+        d, A, marks = gpu_step(g, dev, W, args, bufs, ctx)
     e1.record()
     torch.cuda.synchronize()
     prof = ctx.profile_read()
     ctx.profile_stop()
-    ms = e0.elapsed_time(e1) / args.steps
-    spmv_n, spmv_ms = prof["pcg_spmv"]
-    avg = spmv_ms / max(spmv_n, 1) * 1e-3
+    return e0.elapsed_time(e1) / steps, prof, d, A, marks
+
+
+def run_float_pair(g, dev, W, args, bufs, ctx):
+    """The same C1 step with the solver's H c in double-float arithmetic (gipc_product
+    GIPC_PRODUCT_FLOAT_PAIR): time per step, the solver against the HBM roof (same bytes as FP64),
+    and the Newton direction's deviation from the native FP64 result after the same iterations."""
+    import argparse
+    a2 = argparse.Namespace(**dict(vars(args), product="float_pair"))
+    d_native, _, _ = gpu_step(g, dev, W, args, bufs, ctx)   # the native solve of the same inputs
+    d_native = d_native.clone()
+    ms, prof, d2, A, _ = timed_steps(g, dev, W, a2, bufs, ctx, args.steps)
+    import torch
     ok = bool(torch.isfinite(d_native).all().item()) and bool(torch.isfinite(d2).all().item())
     dev_rel = ((d2 - d_native).abs().max() / d_native.abs().max()).item() if ok else float("nan")
+    roof = solver_roofline(prof, "fp64", W["n"], A["nnzb"], kernel="pcg_loop_kernel<fpair, fpair, 2, 2, false>")
     return {"ms_per_step": ms, "stencils_per_s": K_STENCILS / (ms * 1e-3),
-            "spmv_us": avg * 1e6, "spmv_hbm_frac": bytes_l / avg / 1e9 / hbm,
-            "kernel": "pcg_spmv_tma_kernel<fpair, fpair, 2, 16, 2>",
+            "solver_us_per_iteration": roof["us_per_iteration"], "solver_hbm_frac": roof["hbm_frac"],
+            "kernel": roof["kernel"],
             "direction_max_rel_dev_from_native": dev_rel,
             "note": "FP64 matrix and vectors; H c products and sums as float32 pairs (about 2^-44 relative "
                     "per row); not the headline"}
+
+
+def run_mixed(g, dev, W, Wh, args, ctx):
+    """The mixed form of the same C1 step (float32 rank-one blocks, BSR, product, factors and
+    direction; FP64 distances, barrier log, mollifier, residual and dots): time per step, stencils
+    per second, end to end with host inputs, the solver's HBM roofline, the per-block relative
+    Frobenius error of the mixed Hessian blocks against the FP64 path's (which matches the oracle to
+    1e-10 in the tests) over all 1M stencils."""
+    import argparse
+    import torch
+    a2 = argparse.Namespace(**dict(vars(args), precision="mixed", hess_mode="rank1"))
+    bufs = {"eps": torch.empty(K_STENCILS, dtype=torch.float64, device=dev), "eval": {}, "bsr": {},
+            "rhs": torch.empty((3, Wh["n"]), dtype=torch.float64, device=dev)}
+    ms, prof, d, A, marks = timed_steps(g, dev, W, a2, bufs, ctx, args.steps)
+    roof = solver_roofline(prof, "mixed", Wh["n"], A["nnzb"])
+    # end to end: host inputs in, direction out
+    host = {k: torch.tensor(Wh[k]).pin_memory() for k in ("x", "st_own", "st_sheet", "mass")}
+    out_h = torch.empty((3, Wh["n"]), dtype=torch.float64).pin_memory()
+    Wd = dict(W)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(args.steps):
+        for key in host:
+            Wd[key] = host[key].to(dev, non_blocking=True)
+        dd, _, _ = gpu_step(g, dev, Wd, a2, bufs, ctx)
+        out_h.copy_(dd, non_blocking=True)
+    e1.record()
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / args.steps
+    # per-block error: mixed rank-one blocks lam w w^T (float32) against the FP64 dense blocks
+    eps = g.compute_eps_x(W["x"], W["st_own"])
+    f64 = g.eval_stencils(W["x"], W["st_own"], eps, W["dhat"], KAPPA, precision="fp64", mode="rank1",
+                          want=("hess", "lam"))
+    mx = g.eval_stencils(W["x"], W["st_own"], eps, W["dhat"], KAPPA, precision="mixed", mode="rank1",
+                         want=("hess", "lam"))
+    w64, l64 = f64["hess"].double(), f64["lam"].double()
+    w32, l32 = mx["hess"].double(), mx["lam"].double()
+    # ||l32 w32 w32^T - l64 w64 w64^T||_F / ||l64 w64 w64^T||_F, via inner products (no dense blocks)
+    a2n = (w32 * w32).sum(0)
+    b2n = (w64 * w64).sum(0)
+    ab = (w32 * w64).sum(0)
+    num2 = (l32 * a2n) ** 2 + (l64 * b2n) ** 2 - 2 * l32 * l64 * ab ** 2
+    den = (l64 * b2n).abs()
+    act = den > 0
+    rel = torch.sqrt(num2[act].clamp_min(0)) / den[act]
+    return {"ms_per_step": ms, "value": K_STENCILS / (ms * 1e-3), "unit": "stencils/s",
+            "e2e": {"value": K_STENCILS / (e2e_ms * 1e-3), "unit": "stencils/s", "ms_per_step": e2e_ms},
+            "phases_ms": {"eval": marks[0].elapsed_time(marks[1]), "assemble": marks[1].elapsed_time(marks[2]),
+                          "pcg": marks[2].elapsed_time(marks[3])},
+            "roofline": roof, "dtype": "f32+f64", "hess_mode": "rank1",
+            "block_rel_frobenius_err_vs_fp64": {"max": rel.max().item(), "mean": rel.mean().item(),
+                                                "blocks": int(act.sum().item()), "bar": 1e-4},
+            "note": "same inputs and iteration count as the FP64 line (200 iterations at tolerance 0 on a "
+                    "system with diagonal blocks of condition ~1e12, so the two forms' iterates are not "
+                    "compared); the converged-position error of the mixed form is under "
+                    "newton.converged_position_error"}
 
 
 # ----------------------------------------------------------------------------- Newton iterations/s
@@ -715,49 +804,108 @@ def run_diff_bench(g, dev, ctx, steps, fd_h=1e-6, eps_d=1e-5, eps_polish=1e-12):
 
 
 # ----------------------------------------------------------------------------- oracle (CPU) arm
-def oracle_step(args, Wh, sample, pool_procs):
-    """The oracle's whole path on the first ``sample`` stencils of the batch (full vertex space).
+ORACLE_EVAL_SAMPLE = 4000     # stencils evaluated by the oracle per measurement (all host cores)
+ORACLE_SINGLE_SAMPLE = 500    # stencils evaluated single-threaded (reported beside)
+ORACLE_PCG_ITERS = 20         # oracle PCG iterations timed per measurement (tolerance 0: equal cost each)
 
-    Returns the PCG result and the seconds its stencil evaluation took."""
+
+def full_pattern_system(Wh):
+    """A BSR system of the benchmark's full size and pattern (4.1M blocks over 301,088 rows) for
+    timing the oracle's solver: mass on the diagonal plus a rank-one PSD block per stencil, summed
+    per block by numpy from the stencils' plain vertex tuples (not by the library; the solver's cost
+    does not depend on the values)."""
+    import numpy as np
+    n = Wh["n"]
+    rng = np.random.default_rng(20230815)
+    rows, cols = [np.arange(n, dtype=np.int64)], [np.arange(n, dtype=np.int64)]
+    contrib = [np.asarray(Wh["mass"])[:, None, None] * np.eye(3)]
+    for ids in Wh["sheet_ids"]:
+        m, s = ids.shape
+        w = rng.normal(size=(m, s, 3))
+        lam = 10.0 ** rng.uniform(0, 4, m)
+        for a in range(s):
+            for b in range(s):
+                rows.append(ids[:, a])
+                cols.append(ids[:, b])
+                contrib.append(lam[:, None, None] * w[:, a, :, None] * w[:, b, None, :])
+    rows, cols = np.concatenate(rows), np.concatenate(cols)
+    contrib = np.concatenate(contrib).reshape(-1, 9)
+    key, inv = np.unique(rows * n + cols, return_inverse=True)
+    vals = np.stack([np.bincount(inv, weights=contrib[:, e], minlength=len(key)) for e in range(9)], 1)
+    rowptr = np.zeros(n + 1, np.int64)
+    np.add.at(rowptr, key // n + 1, 1)
+    return {"rowptr": np.cumsum(rowptr), "colidx": key % n, "vals": vals.reshape(-1, 3, 3)}, rng.normal(size=(3, n))
+
+
+def full_keys(Wh):
+    """Assembly keys of the whole batch: every ordered vertex pair of every stencil plus the diagonal."""
+    return Wh["n"] + sum(ids.shape[0] * ids.shape[1] ** 2 for ids in Wh["sheet_ids"])
+
+
+def oracle_step_costs(args, Wh, procs, system):
+    """The oracle's per-unit costs of one C1 step, each measured on a fixed amount of its own work:
+    the stencil evaluation on the first ORACLE_EVAL_SAMPLE stencils (``procs`` spawn processes),
+    the plain assembly of those stencils plus the mass over all n rows (seconds per assembly key),
+    and ORACLE_PCG_ITERS iterations of its PCG on a full-size system (tolerance 0, so every
+    iteration does the same work).  The whole step's time is then K x seconds per stencil + all keys
+    x seconds per key + PCG_ITERS x seconds per iteration, independent of the sample sizes."""
     import numpy as np
     from oracle import assembly as OA
     from oracle import pcg as OP
     from oracle import stencil as OS
-    st = np.ascontiguousarray(Wh["st_own"][:, :sample])
-    sh = np.ascontiguousarray(Wh["st_sheet"][:, :sample])
+    k = ORACLE_EVAL_SAMPLE
+    st = np.ascontiguousarray(Wh["st_own"][:, :k])
+    sh = np.ascontiguousarray(Wh["st_sheet"][:, :k])
     eps = OS.compute_eps_x(Wh["x"], st)
-    t_eval = time.perf_counter()
-    r = OS.eval_stencils(Wh["x"], st, eps, Wh["dhat"], KAPPA, processes=pool_procs)
-    eval_s = time.perf_counter() - t_eval
+    t = time.perf_counter()
+    r = OS.eval_stencils(Wh["x"], st, eps, Wh["dhat"], KAPPA, processes=procs)
+    t_eval = time.perf_counter() - t
     if args.hess_mode == "rank1":
         sd = {"kind": "rank1", "lam": r["lam"], "w": r["w"], "grad": r["grad"]}
     else:
         sd = {"kind": "dense", "hess": r["hess"], "grad": r["grad"]}
+    t = time.perf_counter()
     A = OA.assemble(Wh["n"], sh, sd, None, None, Wh["mass"])
-    out = OP.pcg(A, Wh["n"], -A["grad"], tol=0.0, max_iter=PCG_ITERS)
-    return out, eval_s
+    t_asm = time.perf_counter() - t
+    keys = Wh["n"] + sum(len(x) ** 2 for x in OA.element_vertices(sh, None))
+    R, b = system
+    t = time.perf_counter()
+    OP.pcg(R, Wh["n"], b, tol=0.0, max_iter=ORACLE_PCG_ITERS)
+    t_pcg = time.perf_counter() - t
+    s_eval, s_key, s_it = t_eval / k, t_asm / keys, t_pcg / ORACLE_PCG_ITERS
+    total = K_STENCILS * s_eval + full_keys(Wh) * s_key + PCG_ITERS * s_it
+    return {"eval_stencils_per_s": 1.0 / s_eval, "assembly_keys_per_s": 1.0 / s_key, "pcg_s_per_iteration": s_it,
+            "full_step_s": total, "stencils_per_s": K_STENCILS / total,
+            "measured_s": t_eval + t_asm + t_pcg, "nnzb_assembled_sample": int(len(A["colidx"]))}
 
 
-def cpu_baseline(args, Wh, sample, single=500):
-    """The oracle's whole step on a sample of the batch on all host cores, and its stencil
-    evaluation alone on all cores and on one core (a smaller sample)."""
+def _oracle_desc(procs, n, nnzb_full):
+    return (f"oracle per-unit costs scaled to the whole {K_STENCILS}-stencil step: exact-geometry evaluation of "
+            f"a fixed {ORACLE_EVAL_SAMPLE}-stencil sample on {procs} spawn processes (s per stencil x "
+            f"{K_STENCILS}), plain assembly of that sample plus the mass of all {n} rows (s per key x the "
+            f"batch's keys), and oracle PCG iterations on a full-size system of the benchmark's pattern "
+            f"({nnzb_full} blocks; {ORACLE_PCG_ITERS} timed, s per iteration x {PCG_ITERS})")
+
+
+def cpu_baseline(args, Wh):
+    """The oracle's whole step (per-unit costs, see oracle_step_costs) on all host cores, and its
+    stencil evaluation alone on all cores and on one core."""
     import numpy as np
     from oracle import stencil as OS
     procs = os.cpu_count() or 1
-    t = time.perf_counter()
-    _, eval_s = oracle_step(args, Wh, sample, procs)
-    dt = time.perf_counter() - t
-    eval_all = sample / eval_s
+    system = full_pattern_system(Wh)
+    c = oracle_step_costs(args, Wh, procs, system)
+    single = ORACLE_SINGLE_SAMPLE
     st = np.ascontiguousarray(Wh["st_own"][:, :single])
     eps = OS.compute_eps_x(Wh["x"], st)
     t1 = time.perf_counter()
     OS.eval_stencils(Wh["x"], st, eps, Wh["dhat"], KAPPA, processes=1)
     eval_one = single / (time.perf_counter() - t1)
-    return {"value": sample / dt, "unit": "stencils/s", "cores": procs, "kind": "oracle",
-            "sample": f"first {sample} of the {K_STENCILS} stencils: exact-geometry oracle eval "
-                      f"({procs} spawn processes), plain assembly over all {Wh['n']} vertices, "
-                      f"{PCG_ITERS} PCG iterations; {dt:.1f} s",
-            "eval_only": {"all_cores": eval_all, "cores": procs, "single_thread": eval_one,
+    return {"value": c["stencils_per_s"], "unit": "stencils/s", "cores": procs, "kind": "oracle",
+            "sample": _oracle_desc(procs, Wh["n"], len(system[0]["colidx"])) + f"; {c['measured_s']:.1f} s measured",
+            "phases": {"eval_stencils_per_s": c["eval_stencils_per_s"], "assembly_keys_per_s": c["assembly_keys_per_s"],
+                       "pcg_s_per_iteration": c["pcg_s_per_iteration"], "full_step_s": c["full_step_s"]},
+            "eval_only": {"all_cores": c["eval_stencils_per_s"], "cores": procs, "single_thread": eval_one,
                           "single_thread_sample": single, "unit": "stencils/s"}}
 
 
@@ -766,23 +914,24 @@ def run_reference(args):
     if rank != 0:
         return
     Wh = workload()
-    sample = 4000
     procs = os.cpu_count() or 1
+    system = full_pattern_system(Wh)
     for _ in range(args.warmup):
-        oracle_step(args, Wh, sample, procs)
+        oracle_step_costs(args, Wh, procs, system)
+    totals = []
     t = time.perf_counter()
     for _ in range(args.steps):
-        oracle_step(args, Wh, sample, procs)
-    dt = (time.perf_counter() - t) / args.steps
-    v = sample / dt
-    desc = (f"first {sample} of the {K_STENCILS} stencils per step: exact-geometry oracle eval ({procs} spawn "
-            f"processes), plain assembly over all {Wh['n']} vertices, {PCG_ITERS} PCG iterations")
+        totals.append(oracle_step_costs(args, Wh, procs, system)["full_step_s"])
+    wall = (time.perf_counter() - t) / args.steps
+    step_s = sum(totals) / len(totals)
+    v = K_STENCILS / step_s
+    desc = _oracle_desc(procs, Wh["n"], len(system[0]["colidx"]))
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": "stencils/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": workload_desc(args), "precision": args.precision, "hess_mode": args.hess_mode,
-                   "sample_stencils": sample},
+                   "oracle_eval_sample": ORACLE_EVAL_SAMPLE, "measured_wall_s_per_step": wall},
         "cpu_baseline": {"value": v, "unit": "stencils/s", "cores": procs, "kind": "oracle", "sample": desc},
         "e2e": {"value": v, "unit": "stencils/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))

@@ -324,16 +324,23 @@ gipc_status gipc_pcg(gipc_ctx* ctx, const gipc_bsr* A_h, const double* rhs, doub
  * framework that owns all device memory through its own pool and forbids
  * cudaMalloc, or a latency-critical loop in which cudaMalloc/cudaFree (which
  * can synchronise the device) would stall work on other streams.  It runs the
- * same solver as gipc_pcg with the same arguments and results, but keeps its
- * working vectors in one fixed array of about 7.2 MB in device global memory
- * that the library defines: every GPU that loads the library holds that array
- * until the process exits.  The caller still passes the matrix, rhs and x.
+ * same algorithm as gipc_pcg with the same arguments and results, with the
+ * matrix product taken row by row from the BSR arrays (no sliced copy of the
+ * matrix, no persistent launch), and keeps its working vectors in one fixed
+ * array of about 7.2 MB in device global memory that the library defines:
+ * every GPU that loads the library holds that array until the process exits.
+ * The caller still passes the matrix, rhs and x.  prm_h->product must be
+ * GIPC_PRODUCT_NATIVE or GIPC_PRODUCT_FLOAT_PAIR; both run the native FP64
+ * product here.
  *
  *  - Limit: A->n <= GIPC_PCG_NOALLOC_MAX_N; larger systems are rejected with
  *    GIPC_ERR_INVALID_ARG and a message naming the limit (nothing is enqueued).
  *  - The first call on a device looks up the array's device address (once per
  *    device, with that device current); make that first call before any
  *    stream capture.
+ *  - Like gipc_pcg, the call waits for its stream at the end (and every
+ *    check_every iterations when rel_tol > 0) to read the iteration count and
+ *    the status.
  *  - All calls share the one array, which keeps the last call's contents; each
  *    call clears what must start at zero (the solver's counters and flags).
  *    Calls that overlap on the GPU (e.g. issued on two streams at once, or from
@@ -571,7 +578,8 @@ typedef enum {
     GIPC_PROF_CCD = 6,           /* CCD step filter                               */
     GIPC_PROF_ELEMENTS = 7,      /* time step: element gradients + Hessians       */
     GIPC_PROF_ENERGY = 8,        /* time step: energies and their reductions      */
-    GIPC_PROF_KINDS = 9
+    GIPC_PROF_PCG_LOOP = 9,      /* persistent solver: all iterations of a solve  */
+    GIPC_PROF_KINDS = 10
 } gipc_prof_kind;
 
 typedef struct {

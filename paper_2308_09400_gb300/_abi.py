@@ -79,7 +79,7 @@ class KernelTime(ctypes.Structure):
 
 
 PROF_KINDS = {"pcg_spmv": 0, "pcg_update": 1, "pcg_direction": 2, "asm_pattern": 3, "asm_values": 4,
-              "contacts": 5, "ccd": 6, "elements": 7, "energy": 8}
+              "contacts": 5, "ccd": 6, "elements": 7, "energy": 8, "pcg_loop": 9}
 
 _P = ctypes.c_void_p
 _I64 = ctypes.c_int64

@@ -2,7 +2,10 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <tuple>
 
 #include "common.cuh"
 #include "context.cuh"
@@ -23,6 +26,65 @@ gipc_status check_launch(const char* what) {
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(GIPC_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
     return GIPC_OK;
+}
+
+namespace {
+std::mutex g_facts_mutex;
+std::map<int, DeviceFacts> g_device_facts;
+std::map<std::tuple<const void*, int, int, size_t>, int> g_occupancy;   // (kernel, device, threads, smem)
+std::map<std::pair<const void*, int>, size_t> g_smem_limit;             // (kernel, device) -> raised limit
+}  // namespace
+
+DeviceFacts device_facts() {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return DeviceFacts{};
+    std::lock_guard<std::mutex> lock(g_facts_mutex);
+    auto it = g_device_facts.find(dev);
+    if (it != g_device_facts.end()) return it->second;
+    DeviceFacts f;
+    int sms = 0, coop = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return DeviceFacts{};
+    }
+    f.device = dev;
+    f.sms = sms;
+    f.coop = coop != 0;
+    g_device_facts[dev] = f;
+    return f;
+}
+
+int kernel_occupancy(const void* fn, int threads, size_t smem) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return 0;
+    std::lock_guard<std::mutex> lock(g_facts_mutex);
+    const auto key = std::make_tuple(fn, dev, threads, smem);
+    auto it = g_occupancy.find(key);
+    if (it != g_occupancy.end()) return it->second;
+    size_t& limit = g_smem_limit[std::make_pair(fn, dev)];
+    if (smem > 48 * 1024 && smem > limit) {
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        limit = smem;
+    }
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    g_occupancy[key] = occ;
+    return occ;
+}
+
+unsigned grid_for(int64_t work, int64_t per_block, int per_sm) {
+    const int sms = device_facts().sms;
+    int64_t b = per_block > 0 ? (work + per_block - 1) / per_block : 1;
+    const int64_t cap = (int64_t)(sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+    if (b > cap) b = cap;
+    return (unsigned)(b < 1 ? 1 : b);
 }
 
 }  // namespace gipc

@@ -12,6 +12,23 @@ gipc_status fail(gipc_status st, const char* fmt, ...);
 // Map the last launch / runtime error to GIPC_ERR_CUDA with a message.
 gipc_status check_launch(const char* what);
 
+// Facts of the current device, looked up once per device (thread-safe): its ordinal, SM count and
+// whether it supports cooperative launches.  sms is 0 when no device is usable.
+struct DeviceFacts {
+    int device = -1;
+    int sms = 0;
+    bool coop = false;
+};
+DeviceFacts device_facts();
+// CTAs of `threads` threads with `smem` bytes of dynamic shared memory that one SM of the current
+// device holds at once for kernel `fn`; raises the kernel's dynamic shared memory limit on that
+// device to `smem` first when needed.  Computed once per (kernel, device, threads, smem) under a
+// lock; 0 on failure.
+int kernel_occupancy(const void* fn, int threads, size_t smem);
+// Grid size for `work` items at `per_block` items per CTA, capped at `per_sm` CTAs per SM of the
+// current device (at least 1).
+unsigned grid_for(int64_t work, int64_t per_block, int per_sm);
+
 constexpr int kMaxStencilVerts = 4;
 
 // Stencil type decoding from the sign pattern (paper Sec. 7.2).  Returns the

@@ -171,12 +171,6 @@ __device__ __forceinline__ fpair mac(fpair a, fpair b, fpair c) {
     return fast_two_sum(s.hi, __fadd_rn(c.lo, __fadd_rn(s.lo, t)));
 }
 
-__device__ __forceinline__ double ldg_(const double* p) { return __ldg(p); }
-__device__ __forceinline__ float ldg_(const float* p) { return __ldg(p); }
-__device__ __forceinline__ fpair ldg_(const fpair* p) {
-    const float2 v = __ldg(reinterpret_cast<const float2*>(p));
-    return fpair(v.x, v.y);
-}
 
 // matrix values as the product stores them
 __device__ __forceinline__ void store_val(double* d, double v) { *d = v; }
@@ -350,11 +344,12 @@ __device__ __forceinline__ void async_proxy_fence() { asm volatile("fence.proxy.
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_u32(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
-                 : "memory");
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, uint64_t* bar, uint64_t policy) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
+        : "memory");
 }
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
     unsigned ok;
@@ -383,68 +378,125 @@ struct StageLayout {
     static constexpr unsigned kBlockBytes = W * kWarpBytes + W * NS * 8;
 };
 
-// Pipeline per warp over the groups g of a slice: the copies of the next NS-1 groups are in
-// flight while group g is multiplied; with NS >= 3 the direction entries of group g+1 are also
-// gathered before group g is multiplied.
-template <typename VT, typename PT, int U, int W, int NS>
-__global__ void __launch_bounds__(W * 32)
-pcg_spmv_tma_kernel(const int32_t* __restrict__ rowptr, const int64_t* __restrict__ slice_off,
-                    const int32_t* __restrict__ sell_col, const VT* __restrict__ sell_vals, const PT* __restrict__ cg,
-                    const double* __restrict__ c, const int32_t* __restrict__ perm, double* __restrict__ q,
-                    const uint8_t* __restrict__ fixed, int64_t n, int64_t nsl, double* __restrict__ part,
-                    PcgScalars* __restrict__ S) {
+// Direction loads of the product.  Within one product launch the direction is read-only, so the
+// gathers take the read-only data path; the persistent solver rewrites it every iteration and
+// reads it with coherent loads (its grid barriers order the writes before them).
+template <bool COHERENT>
+__device__ __forceinline__ double ld_dir(const double* p) {
+    if constexpr (COHERENT) return *p;
+    else return __ldg(p);
+}
+template <bool COHERENT>
+__device__ __forceinline__ float ld_dir(const float* p) {
+    if constexpr (COHERENT) return *p;
+    else return __ldg(p);
+}
+template <bool COHERENT>
+__device__ __forceinline__ fpair ld_dir(const fpair* p) {
+    const float2 v = COHERENT ? *reinterpret_cast<const float2*>(p) : __ldg(reinterpret_cast<const float2*>(p));
+    return fpair(v.x, v.y);
+}
+
+// The dynamic shared memory of the launch (staging buffers, then the mbarriers).
+__device__ __forceinline__ unsigned char* dyn_smem() {
+    extern __shared__ __align__(128) unsigned char dsm[];
+    return dsm;
+}
+
+// Per-warp state of the staging ring.  Buffer b of the warp is refilled by bulk copies that
+// complete on mbarrier b; `parity` bit b is the phase parity to wait for next on buffer b and
+// `base` the ring position of the current slice's group 0.  `pre_sl` is a slice whose first
+// `pre_groups` groups are already in flight (-1: none).  The buffers' addresses are recomputed
+// from the warp index where they are used, so the ring costs four registers.
+template <typename VT, int U, int W, int NS>
+struct StageRing {
     using Lay = StageLayout<VT, U, W, NS>;
-    constexpr bool kPrefetchGather = NS >= 3;
-    extern __shared__ __align__(128) unsigned char stage[];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    unsigned char* wbuf = stage + w * Lay::kWarpBytes;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(stage + W * Lay::kWarpBytes) + NS * w;
-    if (lane == 0) {
-        for (int b = 0; b < NS; ++b) mbar_init(bars + b, 1);
-        mbar_init_fence();
+    unsigned parity, base;
+    int pre_sl, pre_groups;
+
+    __device__ __forceinline__ static unsigned char* wbuf() { return dyn_smem() + (threadIdx.x >> 5) * Lay::kWarpBytes; }
+    __device__ __forceinline__ static uint64_t* bars() {
+        return reinterpret_cast<uint64_t*>(dyn_smem() + W * Lay::kWarpBytes) + NS * (threadIdx.x >> 5);
     }
-    __syncwarp();
-    unsigned parity = 0;   // bit b: phase parity to wait for on buffer b
-    unsigned base = 0;     // buffer ring position of the current slice's group 0
-    bool timed_out = false;
-    // lane 0: stage group g of the slice (steps [g*U, min((g+1)*U, Ls))) into buffer b
-    auto issue = [&](unsigned b, int64_t off, int64_t Ls, int64_t g) {
+    __device__ __forceinline__ void init() {
+        if ((threadIdx.x & 31) == 0) {
+            for (int b = 0; b < NS; ++b) mbar_init(bars() + b, 1);
+            mbar_init_fence();
+        }
+        __syncwarp();
+        parity = 0;
+        base = 0;
+        pre_sl = -1;
+        pre_groups = 0;
+    }
+    // lane 0: stage group g of a slice (steps [g U, min((g+1) U, Ls)) at step offset off) into
+    // buffer b; the matrix stream is marked evict-first in L2, so the solver's vectors stay there
+    __device__ __forceinline__ void issue(unsigned b, const VT* sell_vals, const int32_t* sell_col, int64_t off,
+                                          int64_t Ls, int64_t g) {
         const int64_t j0 = g * U;
         const int64_t steps = (Ls - j0) < U ? (Ls - j0) : U;
         const unsigned vb = (unsigned)(steps * 9 * kSellC * sizeof(VT)), cb = (unsigned)(steps * kSellC * sizeof(int32_t));
-        unsigned char* dst = wbuf + b * Lay::kBuf;
+        unsigned char* dst = wbuf() + b * Lay::kBuf;
+        uint64_t* bar = bars() + b;
+        uint64_t policy;
+        asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(policy));
         async_proxy_fence();
-        mbar_expect_tx(bars + b, vb + cb);
-        bulk_load(dst, sell_vals + (off + j0) * 9 * kSellC, vb, bars + b);
-        bulk_load(dst + Lay::kValBytes, sell_col + (off + j0) * kSellC, cb, bars + b);
-    };
-    auto wait = [&](unsigned b) {   // warp-uniform outcome
-        const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(bars + b, (parity >> b) & 1));
+        mbar_expect_tx(bar, vb + cb);
+        bulk_load(dst, sell_vals + (off + j0) * 9 * kSellC, vb, bar, policy);
+        bulk_load(dst + Lay::kValBytes, sell_col + (off + j0) * kSellC, cb, bar, policy);
+    }
+    // put the leading NS - 1 groups of slice sl in flight (the matrix never changes, so this may
+    // run ahead of anything that the product itself waits for)
+    __device__ __forceinline__ void preissue(int64_t sl, int64_t nsl, const int64_t* slice_off, const VT* sell_vals,
+                                             const int32_t* sell_col) {
+        pre_sl = sl < nsl ? (int)sl : -1;
+        pre_groups = 0;
+        if (pre_sl < 0) return;
+        const int64_t off = slice_off[pre_sl], Ls = slice_off[pre_sl + 1] - off;
+        pre_groups = (int)std::min<int64_t>(NS - 1, (Ls + U - 1) / U);
+        if ((threadIdx.x & 31) == 0)
+            for (int g = 0; g < pre_groups; ++g) issue((base + (unsigned)g) % NS, sell_vals, sell_col, off, Ls, g);
+    }
+    __device__ __forceinline__ bool wait(unsigned b) {   // warp-uniform outcome
+        const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(bars() + b, (parity >> b) & 1));
         parity ^= 1u << b;
         return ok;
-    };
+    }
+    // let the pre-issued copies land (before the CTA may exit)
+    __device__ __forceinline__ void drain() {
+        for (int g = 0; g < pre_groups; ++g) wait((base + (unsigned)g) % NS);
+        pre_sl = -1;
+        pre_groups = 0;
+        __syncwarp();
+    }
+    // after a timed-out wait: let every copy that may still be in flight land
+    __device__ __forceinline__ void drain_all() {
+        for (int b = 0; b < NS; ++b) mbar_wait_bounded(bars() + b, (parity >> b) & 1);
+        __syncwarp();
+    }
+};
+
+// q = S(H c) over this warp's slices; returns this thread's part of c . q.  A warp takes one
+// slice per round, in alternating directions (round r: r * warps + wid, then
+// r * warps + warps - 1 - wid), so within a chunk's longest-first run long and short slices pair
+// up; every thread's set of slices is fixed, so its partial sum is too.  The arithmetic order is
+// that of the row-ordered kernel: block j of a row goes to accumulator j % 2 for j < 4 floor(L / 4)
+// and to accumulator 0 after that, each block adding its three products per entry in column order.
+// Pipeline per warp over the groups g of a slice: the copies of the next NS-1 groups are in flight
+// while group g is multiplied; with NS >= 3 the direction entries of group g+1 are also gathered
+// before group g is multiplied.
+template <typename VT, typename PT, int U, int W, int NS, bool COHERENT>
+__device__ __forceinline__ double spmv_slices(StageRing<VT, U, W, NS>& R, const int32_t* __restrict__ rowptr,
+                                              const int64_t* __restrict__ slice_off, const int32_t* __restrict__ sell_col,
+                                              const VT* __restrict__ sell_vals, const PT* cg, const double* c,
+                                              const int32_t* __restrict__ perm, double* q, const uint8_t* __restrict__ fixed,
+                                              int64_t n, int64_t nsl, bool& timed_out) {
+    using Lay = StageLayout<VT, U, W, NS>;
+    constexpr bool kPrefetchGather = NS >= 3;
+    const int lane = threadIdx.x & 31;
     const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    // The matrix does not depend on the previous kernel: the first slice's leading groups are put
-    // in flight before waiting for it (under a programmatic dependent launch they overlap its tail).
-    const int64_t pre_sl = wid < nsl ? wid : -1;
-    int64_t pre_groups = 0;
-    if (pre_sl >= 0) {
-        const int64_t off = slice_off[pre_sl], Ls = slice_off[pre_sl + 1] - off;
-        pre_groups = std::min<int64_t>(NS - 1, (Ls + U - 1) / U);
-        if (lane == 0)
-            for (int64_t g = 0; g < pre_groups; ++g) issue((unsigned)g, off, Ls, g);
-    }
-    pdl_wait();
-    if (S->done) {   // uniform: the solve has stopped; let the staged copies land, then leave
-        for (int64_t g = 0; g < pre_groups; ++g) mbar_wait_bounded(bars + g, 0);
-        __syncwarp();
-        return;
-    }
     double d = 0.0;
-    // a warp takes one slice per round, in alternating directions (round r: r * warps + wid, then
-    // r * warps + warps - 1 - wid), so within a chunk's longest-first run long and short slices
-    // pair up; every thread's set of slices is fixed, so its partial sum is too
     for (int64_t rnd = 0; rnd * warps < nsl && !timed_out; ++rnd) {
         const int64_t sl = rnd * warps + ((rnd & 1) ? warps - 1 - wid : wid);
         if (sl >= nsl) continue;
@@ -458,42 +510,46 @@ pcg_spmv_tma_kernel(const int32_t* __restrict__ rowptr, const int64_t* __restric
         VT a0[3] = {VT(0), VT(0), VT(0)}, a1[3] = {VT(0), VT(0), VT(0)};
         PT pc[U][3], pn[U][3];   // gathered direction of the current / next group
         auto gather = [&](unsigned b, int64_t g, PT (&pv)[U][3]) {
-            const int32_t* sc = reinterpret_cast<const int32_t*>(wbuf + b * Lay::kBuf + Lay::kValBytes);
+            const int32_t* sc = reinterpret_cast<const int32_t*>(R.wbuf() + b * Lay::kBuf + Lay::kValBytes);
 #pragma unroll
             for (int u = 0; u < U; ++u)
                 if (g * U + u < L) {
                     const int64_t cj = sc[u * kSellC + lane];
 #pragma unroll
-                    for (int k = 0; k < 3; ++k) pv[u][k] = ldg_(cg + 3 * cj + k);
+                    for (int k = 0; k < 3; ++k) pv[u][k] = ld_dir<COHERENT>(cg + 3 * cj + k);
                 }
         };
-        if (lane == 0 && sl != pre_sl)   // (the first slice's leading groups are already in flight)
-            for (int64_t g = 0; g < NS - 1 && g < G; ++g) issue((base + (unsigned)g) % NS, off, Ls, g);
+        if (lane == 0 && sl != R.pre_sl)   // (a pre-issued slice's leading groups are already in flight)
+            for (int64_t g = 0; g < NS - 1 && g < G; ++g)
+                R.issue((R.base + (unsigned)g) % NS, sell_vals, sell_col, off, Ls, g);
+        R.pre_sl = -1;
+        R.pre_groups = 0;
         if (kPrefetchGather && G > 0) {
-            if (!wait(base % NS)) timed_out = true;
-            else gather(base % NS, 0, pc);
+            if (!R.wait(R.base % NS)) timed_out = true;
+            else gather(R.base % NS, 0, pc);
         }
         for (int64_t g = 0; g < G && !timed_out; ++g) {
-            const unsigned b = (base + (unsigned)g) % NS;
+            const unsigned b = (R.base + (unsigned)g) % NS;
             // group g+NS-1 goes to the buffer group g-1 used (released at the end of iteration g-1)
-            if (g + NS - 1 < G && lane == 0) issue((base + (unsigned)(g + NS - 1)) % NS, off, Ls, g + NS - 1);
+            if (g + NS - 1 < G && lane == 0)
+                R.issue((R.base + (unsigned)(g + NS - 1)) % NS, sell_vals, sell_col, off, Ls, g + NS - 1);
             if (kPrefetchGather) {
                 if (g + 1 < G) {
-                    const unsigned bn = (base + (unsigned)g + 1) % NS;
-                    if (!wait(bn)) {
+                    const unsigned bn = (R.base + (unsigned)g + 1) % NS;
+                    if (!R.wait(bn)) {
                         timed_out = true;
                         break;
                     }
                     gather(bn, g + 1, pn);
                 }
             } else {
-                if (!wait(b)) {
+                if (!R.wait(b)) {
                     timed_out = true;
                     break;
                 }
                 gather(b, g, pc);
             }
-            const VT* sv = reinterpret_cast<const VT*>(wbuf + b * Lay::kBuf);
+            const VT* sv = reinterpret_cast<const VT*>(R.wbuf() + b * Lay::kBuf);
             const int64_t j0 = g * U;
 #pragma unroll
             for (int u = 0; u < U; ++u) {
@@ -515,7 +571,7 @@ pcg_spmv_tma_kernel(const int32_t* __restrict__ rowptr, const int64_t* __restric
             }
             __syncwarp();   // every lane is done with buffer b before it is refilled
         }
-        base = (base + (unsigned)G) % NS;
+        R.base = (R.base + (unsigned)G) % NS;
         if (timed_out) break;
         if (real) {
             const bool fx = fixed && fixed[row];
@@ -527,9 +583,39 @@ pcg_spmv_tma_kernel(const int32_t* __restrict__ rowptr, const int64_t* __restric
             }
         }
     }
+    return d;
+}
+
+// ---- q = S(H c) over the SELL-32 layout, slices streamed into shared memory by bulk async copies ----
+// Each warp owns NS staging buffers of U steps (U*9*32 values + U*32 column indices, both
+// contiguous in the SELL-32 layout) and one mbarrier per buffer.  Lane 0 issues the bulk copies
+// of the next groups (cp.async.bulk, completion counted on the buffer's mbarrier) before the warp
+// waits for the current one, so HBM streams while the warp gathers the direction and multiplies.
+// Waits are bounded: a wait that runs out records GIPC_ERR_TIMEOUT and the solve stops.
+template <typename VT, typename PT, int U, int W, int NS>
+__global__ void __launch_bounds__(W * 32)
+pcg_spmv_tma_kernel(const int32_t* __restrict__ rowptr, const int64_t* __restrict__ slice_off,
+                    const int32_t* __restrict__ sell_col, const VT* __restrict__ sell_vals, const PT* __restrict__ cg,
+                    const double* __restrict__ c, const int32_t* __restrict__ perm, double* __restrict__ q,
+                    const uint8_t* __restrict__ fixed, int64_t n, int64_t nsl, double* __restrict__ part,
+                    PcgScalars* __restrict__ S) {
+    StageRing<VT, U, W, NS> R;
+    R.init();
+    const int lane = threadIdx.x & 31;
+    // The matrix does not depend on the previous kernel: the first slice's leading groups are put
+    // in flight before waiting for it (under a programmatic dependent launch they overlap its tail).
+    R.preissue(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5, nsl, slice_off, sell_vals, sell_col);
+    pdl_wait();
+    if (S->done) {   // uniform: the solve has stopped; let the staged copies land, then leave
+        R.drain();
+        return;
+    }
+    bool timed_out = false;
+    const double d = spmv_slices<VT, PT, U, W, NS, false>(R, rowptr, slice_off, sell_col, sell_vals, cg, c, perm, q,
+                                                          fixed, n, nsl, timed_out);
     if (timed_out) {
         // let copies still in flight land before the CTA can exit, then stop the solve
-        for (int b = 0; b < NS; ++b) mbar_wait_bounded(bars + b, (parity >> b) & 1);
+        R.drain_all();
         if (lane == 0) {
             S->status = GIPC_ERR_TIMEOUT;
             S->done = 1;
@@ -561,19 +647,10 @@ void launch_spmv_tma(const int32_t* rowptr, const int64_t* slice_off, const int3
                      const PT* cg, const double* c, const int32_t* perm, double* q, const uint8_t* fixed, int64_t n,
                      int64_t nsl, double* part, PcgScalars* S, cudaStream_t st) {
     using Lay = StageLayout<VT, U, W, NS>;
-    static bool attr = false;
-    static int per_sm = 1, sms = 152;
-    if (!attr) {
-        cudaFuncSetAttribute(pcg_spmv_tma_kernel<VT, PT, U, W, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)Lay::kBlockBytes);
-        // persistent: as many CTAs as are resident at once (shared memory and registers)
-        int dev = 0, occ = 0;
-        if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pcg_spmv_tma_kernel<VT, PT, U, W, NS>, W * 32,
-                                                          Lay::kBlockBytes) == cudaSuccess)
-            per_sm = std::max(1, std::min(16, occ));
-        attr = true;
-    }
+    // persistent: as many CTAs as are resident at once (shared memory and registers)
+    const int sms = std::max(1, device_facts().sms);
+    const int per_sm = std::max(1, std::min(16, kernel_occupancy((const void*)pcg_spmv_tma_kernel<VT, PT, U, W, NS>,
+                                                                 W * 32, Lay::kBlockBytes)));
     const int64_t want = (nsl + W - 1) / W;   // at most one CTA per W slices
     const unsigned blocks = (unsigned)std::min<int64_t>(std::max<int64_t>(want, 1), (int64_t)sms * per_sm);
     // programmatic dependent launch: the CTAs may start (and stage matrix slices) while the previous
@@ -1008,6 +1085,227 @@ pcg_update_direction_kernel(double* __restrict__ x, double* __restrict__ r, doub
     }
 }
 
+// ---- persistent solver: every iteration of one solve in one cooperative launch -------------
+// The grid is resident for the whole solve.  An iteration is three phases separated by grid
+// barriers:
+//   A  q = S(H c) over the warp's SELL-32 slices (the product above) and the CTA's part of c . q;
+//   B  alpha = delta / (c . q), every CTA summing all the parts in the same fixed order (so every
+//      CTA holds the same alpha); x += alpha c; r -= alpha q; s = P^-1 r; the CTA's part of r . s;
+//   C  delta_new, beta and the stopping test, identical in every CTA for the same reason;
+//      c = S(s + beta c).
+// Each thread owns up to kLoopKeep vertices in phases B and C and keeps their s and c in
+// registers between the two.  As soon as a warp's product ends it stages the leading groups of
+// its first slice of the next product, so the matrix stream restarts while the barriers and the
+// vector phases run.  Every element is computed as in the separate product / update / direction
+// kernels; only the summation order of the dot products differs.  The direction changes during
+// the launch, so its gathers use coherent loads.  Barrier waits are bounded: one that runs out
+// records GIPC_ERR_TIMEOUT, and the other CTAs leave at their next barrier the same way.
+constexpr int kLoopW = 16;             // warps per CTA (staging as in the separate product)
+constexpr int kLoopT = kLoopW * 32;    // threads per CTA
+constexpr int kLoopKeep = 2;           // vertices per thread in the vector phases
+
+// Grid barrier on a monotonic arrival counter (zeroed per solve): the k-th barrier of a launch
+// completes once k * gridDim.x arrivals are counted.  False, in every thread of the CTA alike,
+// when the wait runs out (then GIPC_ERR_TIMEOUT is recorded) or when some CTA has recorded a
+// timeout before.
+__device__ __forceinline__ bool grid_sync(unsigned* count, unsigned target, int* status) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(count, 1u);
+        ok = 1;
+        volatile unsigned* vc = count;
+        const long long t0 = clock64();
+        while (*vc < target) {
+            if (clock64() - t0 > kBarrierCycles) {
+                ok = 0;
+                atomicExch(status, GIPC_ERR_TIMEOUT);
+                break;
+            }
+            __nanosleep(20);
+        }
+        __threadfence();
+        if (*(volatile int*)status == GIPC_ERR_TIMEOUT) ok = 0;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// Sum of every CTA's part in index order, broadcast to the whole CTA.
+__device__ __forceinline__ double grid_total(const double* part) {
+    __shared__ double tot;
+    const double s = sum_partials(part, gridDim.x);
+    if (threadIdx.x == 0) tot = s;
+    __syncthreads();
+    return tot;
+}
+
+// CTAs per SM the persistent solver is compiled for: two where two staging areas fit in shared
+// memory (the register budget then allows 64 per thread), else one.
+template <typename VT, int U, int NS>
+constexpr int loop_min_blocks() {
+    return 2 * (StageLayout<VT, U, kLoopW, NS>::kBlockBytes + 1024) <= 227 * 1024 ? 2 : 1;
+}
+
+template <typename VT, typename PT, int U, int NS, bool MIX>
+__global__ void __launch_bounds__(kLoopT, loop_min_blocks<VT, U, NS>())
+pcg_loop_kernel(const int32_t* __restrict__ rowptr, const int64_t* __restrict__ slice_off,
+                const int32_t* __restrict__ sell_col, const VT* __restrict__ sell_vals, const PT* cg, double* x,
+                double* r, double* c, float* c32, fpair* c2, double* q, const double* __restrict__ fac,
+                const int32_t* __restrict__ perm, const uint8_t* __restrict__ fixed, int64_t n, int64_t nsl,
+                double* part_a, double* part_b, PcgScalars* S, int iters) {
+    using ST = FacT<MIX>;
+    using CT = typename std::conditional<MIX, float, double>::type;   // the kept direction
+    // scalars every thread of the CTA shares, kept in shared memory rather than in registers
+    __shared__ double sh_tol, sh_delta0, sh_delta_prev, sh_beta, sh_alpha, sh_pq;
+    __shared__ int sh_max_iter, sh_stop_indefinite;
+    if (S->done) return;   // read before any CTA can change it: uniform
+    const int t = threadIdx.x;
+    if (t == 0) {
+        sh_tol = S->tol;
+        sh_delta0 = S->delta0;
+        sh_delta_prev = S->delta_old;
+        sh_beta = S->beta;
+        sh_alpha = S->alpha;
+        sh_pq = S->pq;
+        sh_max_iter = S->max_iter;
+        sh_stop_indefinite = S->stop_indefinite;
+    }
+    double delta = S->delta_new;
+    int it_total = S->iters, status = GIPC_OK, done = 0;
+    bool abort = false;
+    StageRing<VT, U, kLoopW, NS> R;
+    R.init();
+    R.preissue(((int64_t)blockIdx.x * blockDim.x + t) >> 5, nsl, slice_off, sell_vals, sell_col);
+    unsigned nbar = 0;
+    auto sync = [&]() { return grid_sync(&S->bar_count, ++nbar * gridDim.x, &S->status); };
+    for (int it = 0; it < iters; ++it) {
+        // A: q = S(H c), parts of c . q
+        bool timed_out = false;
+        const double d = spmv_slices<VT, PT, U, kLoopW, NS, true>(R, rowptr, slice_off, sell_col, sell_vals, cg, c,
+                                                                  perm, q, fixed, n, nsl, timed_out);
+        if (timed_out) {
+            R.drain_all();
+            if ((t & 31) == 0) atomicExch(&S->status, GIPC_ERR_TIMEOUT);
+        } else {
+            R.preissue(((int64_t)blockIdx.x * blockDim.x + t) >> 5, nsl, slice_off, sell_vals, sell_col);
+        }
+        {
+            const double bs = block_sum(d);
+            if (t == 0) part_a[blockIdx.x] = bs;
+        }
+        if (!sync()) {
+            abort = true;
+            break;
+        }
+        const double pq = grid_total(part_a);
+        const double alpha = delta / pq;
+        if (t == 0) {
+            sh_pq = pq;
+            sh_alpha = alpha;
+        }
+        if (sh_stop_indefinite && pq <= 0.0) {   // no descent along c: H not positive definite
+            status = GIPC_ERR_INDEFINITE;
+            done = 1;
+            break;
+        }
+        // B: x += alpha c; r -= alpha q; s = P^-1 r; parts of r . s
+        ST sk[kLoopKeep][3];
+        CT ck[kLoopKeep][3];
+        double d2 = 0.0;
+#pragma unroll
+        for (int j = 0; j < kLoopKeep; ++j) {
+            const int64_t v = ((int64_t)j * gridDim.x + blockIdx.x) * kLoopT + t;
+            if (v < n) {
+                double cv[3], qv[3], xv[3], rv[3];
+                ST F[6];
+#pragma unroll
+                for (int e = 0; e < 3; ++e) {
+                    cv[e] = c[3 * v + e];
+                    qv[e] = q[3 * v + e];
+                    xv[e] = x[3 * v + e];
+                    rv[e] = r[3 * v + e];
+                    if constexpr (MIX) ck[j][e] = c32[3 * v + e];
+                    else ck[j][e] = cv[e];
+                }
+                load_factor_t<MIX>(fac, n, v, F);
+#pragma unroll
+                for (int e = 0; e < 3; ++e) {
+                    x[3 * v + e] = xv[e] + alpha * cv[e];
+                    rv[e] = rv[e] - alpha * qv[e];
+                    r[3 * v + e] = rv[e];
+                }
+                d2 += precond_vertex<MIX>(F, rv, sk[j]);
+            }
+        }
+        {
+            const double bs = block_sum(d2);
+            if (t == 0) part_b[blockIdx.x] = bs;
+        }
+        if (!sync()) {
+            abort = true;
+            break;
+        }
+        const double dn = grid_total(part_b);
+        const double beta = dn / delta;
+        if (t == 0) {
+            sh_beta = beta;
+            sh_delta_prev = delta;
+        }
+        delta = dn;
+        it_total += 1;
+        if (!isfinite(dn) || !isfinite(alpha)) {
+            status = GIPC_ERR_NONFINITE;
+            done = 1;
+        } else if (!(dn > 0.0) || dn < sh_tol * sh_delta0 || it_total >= sh_max_iter) {
+            done = 1;
+        }
+        if (done) break;
+        // C: c = S(s + beta c)
+        const float beta_f = (float)beta;
+#pragma unroll
+        for (int j = 0; j < kLoopKeep; ++j) {
+            const int64_t v = ((int64_t)j * gridDim.x + blockIdx.x) * kLoopT + t;
+            if (v < n) {
+                const bool fx = fixed && fixed[v];
+#pragma unroll
+                for (int e = 0; e < 3; ++e) {
+                    if constexpr (MIX) {   // the float32 direction and its exact float64 image
+                        const float ce = fx ? 0.0f : __fmaf_rn(beta_f, ck[j][e], sk[j][e]);
+                        c32[3 * v + e] = ce;
+                        c[3 * v + e] = (double)ce;
+                    } else {
+                        const double ce = fx ? 0.0 : sk[j][e] + beta * ck[j][e];
+                        c[3 * v + e] = ce;
+                        if (c2) c2[3 * v + e] = split_double(ce);
+                    }
+                }
+            }
+        }
+        if (!sync()) {
+            abort = true;
+            break;
+        }
+    }
+    R.drain();   // copies staged for a product that will not run
+    __syncthreads();
+    if (blockIdx.x == 0 && t == 0) {
+        S->delta_old = sh_delta_prev;
+        S->delta_new = delta;
+        S->beta = sh_beta;
+        S->alpha = sh_alpha;
+        S->pq = sh_pq;
+        S->iters = it_total;
+        if (!abort && *(volatile int*)&S->status != GIPC_ERR_TIMEOUT) {
+            S->status = status;
+            S->done = done;
+        } else {
+            S->done = 1;
+        }
+    }
+}
+
 // c = S(s + beta c) over the flat [3n] vectors with kDirEpt coalesced entries per thread.  The
 // mixed form (MIX) forms it in float32 from the float32 s and c32 and writes c32 and its exact
 // float64 image c.
@@ -1265,10 +1563,7 @@ inline unsigned spmv_blocks(int64_t n) {
     return (unsigned)((warps * 32 + kPcgThreads - 1) / kPcgThreads);
 }
 
-inline unsigned upd_blocks(int64_t n) {
-    const int64_t tiles = (n + kUpdT - 1) / kUpdT;
-    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(tiles, 152 * kUpdPerSm));
-}
+inline unsigned upd_blocks(int64_t n) { return grid_for(n, kUpdT, kUpdPerSm); }
 
 inline unsigned dir_blocks(int64_t n) {
     const int64_t per = (int64_t)kPcgThreads * kDirEpt;
@@ -1286,38 +1581,55 @@ struct FusePlan {
 template <bool MIX>
 inline FusePlan plan_fused(int64_t n) {
     FusePlan p;
-    int dev = 0, sms = 0, coop = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return p;
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return p;
-    if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return p;
+    const DeviceFacts df = device_facts();
+    if (df.sms <= 0 || !df.coop) return p;
     const int64_t ntiles = (n + kUpdT - 1) / kUpdT;
     if (ntiles < 1) return p;
-    const int64_t grid = std::min<int64_t>(ntiles, (int64_t)sms * kUpdPerSm);
+    const int64_t grid = std::min<int64_t>(ntiles, (int64_t)df.sms * kUpdPerSm);
     const int64_t tpc = (ntiles + grid - 1) / grid;
     if (tpc > kFuseMaxTiles) return p;
     const size_t smem = (size_t)tpc * 6 * kUpdT * sizeof(double);
-    static bool attr_set = false;
-    if (!attr_set) {
-        if (cudaFuncSetAttribute(pcg_update_direction_kernel<MIX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(kFuseMaxTiles * 6 * kUpdT * sizeof(double))) != cudaSuccess)
-            return p;
-        attr_set = true;
-    }
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pcg_update_direction_kernel<MIX>, kUpdT, smem) != cudaSuccess)
+    // the limit is raised once to the largest tile count, so every smaller launch fits under it
+    if (kernel_occupancy((const void*)pcg_update_direction_kernel<MIX>, kUpdT,
+                         kFuseMaxTiles * 6 * kUpdT * sizeof(double)) <= 0)
         return p;
-    if ((int64_t)per_sm * sms < grid) return p;
+    const int per_sm = kernel_occupancy((const void*)pcg_update_direction_kernel<MIX>, kUpdT, smem);
+    if ((int64_t)per_sm * df.sms < grid) return p;
     p.ok = true;
     p.grid = (unsigned)grid;
     p.smem = smem;
     return p;
 }
 
-inline unsigned vec_blocks(int64_t n) {
-    int64_t b = (n + (int64_t)kPcgThreads * kVpt - 1) / ((int64_t)kPcgThreads * kVpt);
-    if (b > 152 * 8) b = 152 * 8;
-    return (unsigned)(b < 1 ? 1 : b);
+// Launch shape of the persistent solver, or ok = false when it does not apply (no cooperative
+// launch, or more vertices than the co-resident grid owns at kLoopKeep per thread).  The grid is
+// no larger than the product and the vector phases need, so small systems also synchronise
+// fewer CTAs.
+struct LoopPlan {
+    bool ok = false;
+    unsigned grid = 0;
+    size_t smem = 0;
+};
+
+template <typename VT, typename PT, int U, int NS, bool MIX>
+inline LoopPlan plan_loop(int64_t n, int64_t nsl) {
+    LoopPlan p;
+    const DeviceFacts df = device_facts();
+    if (df.sms <= 0 || !df.coop || n <= 0) return p;
+    const size_t smem = StageLayout<VT, U, kLoopW, NS>::kBlockBytes;
+    const int per_sm = kernel_occupancy((const void*)pcg_loop_kernel<VT, PT, U, NS, MIX>, kLoopT, smem);
+    if (per_sm <= 0) return p;
+    const int64_t cap = (int64_t)df.sms * per_sm;
+    const int64_t want = std::max<int64_t>((nsl + kLoopW - 1) / kLoopW, (n + (int64_t)kLoopKeep * kLoopT - 1) / ((int64_t)kLoopKeep * kLoopT));
+    const int64_t grid = std::max<int64_t>(1, std::min(cap, want));
+    if (grid * kLoopKeep * kLoopT < n) return p;
+    p.ok = true;
+    p.grid = (unsigned)grid;
+    p.smem = smem;
+    return p;
 }
+
+inline unsigned vec_blocks(int64_t n) { return grid_for(n, (int64_t)kPcgThreads * kVpt, 8); }
 
 }  // namespace
 }  // namespace gipc
@@ -1347,8 +1659,18 @@ gipc_status pcg_impl(gipc_ctx* ctx, const gipc_bsr* A, const double* rhs, double
     gipc_status s;
     const int64_t nvec = 3 * n;
     const unsigned vb = vec_blocks(n), sb = spmv_blocks(n), ub = upd_blocks(n), db = dir_blocks(n);
-    const FusePlan fuse = voff ? FusePlan{} : (A->prec == GIPC_FP64 ? plan_fused<false>(n) : plan_fused<true>(n));
-    const unsigned maxb = std::max(std::max(std::max(sb, vb), ub), fuse.grid);
+    const bool f64 = A->prec == GIPC_FP64;
+    const bool fp = f64 && !voff && prm->product == GIPC_PRODUCT_FLOAT_PAIR;
+    const int64_t nsl = (n + kSellC - 1) / kSellC;
+    // one persistent launch for all iterations of a single system where the grid holds it
+    LoopPlan loop;
+    if (!voff) {
+        if (fp) loop = plan_loop<fpair, fpair, kUfp, kNSfp, false>(n, nsl);
+        else if (f64) loop = plan_loop<double, double, kU64, kNS64, false>(n, nsl);
+        else loop = plan_loop<float, float, kU32, kNS32, true>(n, nsl);
+    }
+    const FusePlan fuse = (voff || loop.ok) ? FusePlan{} : (f64 ? plan_fused<false>(n) : plan_fused<true>(n));
+    const unsigned maxb = std::max(std::max(std::max(sb, vb), ub), std::max(fuse.grid, 2 * loop.grid));
     if ((s = ctx->slot[P_VEC].reserve(sizeof(double) * 6 * nvec)) != GIPC_OK) return s;
     if ((s = ctx->slot[P_PINV].reserve(sizeof(double) * 6 * n)) != GIPC_OK) return s;
     if ((s = ctx->slot[P_PART].reserve(sizeof(double) * (maxb + 8) + sizeof(PcgScalars) + 64)) != GIPC_OK) return s;
@@ -1360,7 +1682,6 @@ gipc_status pcg_impl(gipc_ctx* ctx, const gipc_bsr* A, const double* rhs, double
 
     const unsigned eb = (unsigned)((nvec + 255) / 256);
     const int max_iter = prm->max_iter;
-    const bool f64 = A->prec == GIPC_FP64;
     // row order by length within 1024-row chunks (stable, deterministic)
     const int64_t chunks = (n + kPermChunk - 1) / kPermChunk;
     const int64_t ncnt = (int64_t)kLenBuckets * chunks;
@@ -1371,7 +1692,6 @@ gipc_status pcg_impl(gipc_ctx* ctx, const gipc_bsr* A, const double* rhs, double
     int64_t* scan_tmp = offs + ncnt + 1;
     float* c32 = nullptr;
     fpair* c2 = nullptr;   // float-pair copy of the direction (float-pair product)
-    const bool fp = f64 && !voff && prm->product == GIPC_PRODUCT_FLOAT_PAIR;
     if (!f64) {
         if ((s = ctx->slot[P_VEC32].reserve(sizeof(float) * 2 * nvec)) != GIPC_OK) return s;
     } else if (fp) {
@@ -1384,7 +1704,6 @@ gipc_status pcg_impl(gipc_ctx* ctx, const gipc_bsr* A, const double* rhs, double
     if (exclusive_scan<int32_t>(counts, offs, ncnt, scan_tmp, st) != cudaSuccess) return check_launch("gipc_pcg: scan");
     perm_scatter_kernel<<<(unsigned)chunks, 32, 0, st>>>(A->rowptr, n, offs, chunks, perm);
     // sliced layout: slice lengths, their offsets, then the copy
-    const int64_t nsl = (n + kSellC - 1) / kSellC;
     if ((s = ctx->slot[P_SLICE].reserve(sizeof(int32_t) * (nsl + 1) + sizeof(int64_t) * (nsl + 2 + scan_scratch_words(nsl)) + 64)) != GIPC_OK) return s;
     int32_t* slice_len = ctx->slot[P_SLICE].as<int32_t>();
     int64_t* slice_off = reinterpret_cast<int64_t*>(ctx->slot[P_SLICE].as<char>() + ((sizeof(int32_t) * (nsl + 1) + 15) / 16) * 16);
@@ -1424,9 +1743,37 @@ gipc_status pcg_impl(gipc_ctx* ctx, const gipc_bsr* A, const double* rhs, double
     }
     if ((s = check_launch("gipc_pcg: setup")) != GIPC_OK) return s;
 
-    const int chunk = prm->check_every > 0 ? prm->check_every : (prm->rel_tol > 0.0 ? 16 : max_iter + 1);
     PcgScalars hs{};
     int launched = 0;
+    if (loop.ok && max_iter > 0) {
+        // every iteration in one cooperative launch; the stopping test runs on the device
+        double* part_b = part + loop.grid;
+        int64_t n_arg = n, nsl_arg = nsl;
+        int iters_arg = max_iter;
+        const uint8_t* fixed_arg = fixed;
+        const int32_t* rp = A->rowptr;
+        const void* fn;
+        const void* cg;
+        if (fp) {
+            fn = (const void*)pcg_loop_kernel<fpair, fpair, kUfp, kNSfp, false>;
+            cg = c2;
+        } else if (f64) {
+            fn = (const void*)pcg_loop_kernel<double, double, kU64, kNS64, false>;
+            cg = c;
+        } else {
+            fn = (const void*)pcg_loop_kernel<float, float, kU32, kNS32, true>;
+            cg = c32;
+        }
+        void* args[] = {&rp, &slice_off, &sell_col, &sell_vals, &cg, &xv, &r, &c, &c32, &c2, &q, &pinv, &perm,
+                        &fixed_arg, &n_arg, &nsl_arg, &part, &part_b, &S, &iters_arg};
+        ctx->prof.start(GIPC_PROF_PCG_LOOP, st);
+        if (cudaLaunchCooperativeKernel(fn, dim3(loop.grid), dim3(kLoopT), args, loop.smem, st) != cudaSuccess)
+            return check_launch("gipc_pcg: persistent solver");
+        ctx->prof.stop(GIPC_PROF_PCG_LOOP, st);
+        if ((s = check_launch("gipc_pcg: persistent solver")) != GIPC_OK) return s;
+        launched = max_iter;
+    }
+    const int chunk = prm->check_every > 0 ? prm->check_every : (prm->rel_tol > 0.0 ? 16 : max_iter + 1);
     while (launched < max_iter) {
         const int m = (max_iter - launched) < chunk ? (max_iter - launched) : chunk;
         for (int it = 0; it < m; ++it) {
@@ -1530,10 +1877,11 @@ extern "C" gipc_status gipc_pcg(gipc_ctx* ctx, const gipc_bsr* A, const double* 
 // Some callers may not allocate device memory: a host framework that owns every byte of
 // device memory through its own pool and forbids cudaMalloc, or a latency-critical loop in
 // which a cudaMalloc / cudaFree (which can synchronise the device) would stall work queued on
-// other streams.  This variant runs the same kernels as gipc_pcg, but its working vectors live
-// in one fixed-size array in device global memory defined below, so it needs neither a
-// context nor any allocation.  The caller still passes the matrix, right-hand side and
-// solution buffers.
+// other streams.  This variant runs the same algorithm as gipc_pcg with the row-ordered product
+// over the BSR arrays (no sliced copy of the matrix, no fused or persistent kernels), and its
+// working vectors live in one fixed-size array in device global memory defined below, so it
+// needs neither a context nor any allocation.  The caller still passes the matrix, right-hand
+// side and solution buffers.
 #include <mutex>
 
 namespace gipc {
@@ -1543,8 +1891,14 @@ constexpr int64_t kNoAllocMaxN = GIPC_PCG_NOALLOC_MAX_N;
 constexpr size_t na_align(size_t b) { return (b + 255) / 256 * 256; }
 constexpr int64_t kNaChunks = (kNoAllocMaxN + kPermChunk - 1) / kPermChunk;
 constexpr int64_t kNaCounts = (int64_t)kLenBuckets * kNaChunks;
-constexpr int kNaMaxBlocks = 152 * 8 + 16;  // >= spmv, vector and update grids for n <= kNoAllocMaxN
-static_assert((kNoAllocMaxN + kUpdT - 1) / kUpdT <= kNaMaxBlocks, "update grid must fit the partials");
+// The partials hold one value per CTA of the largest grid that writes them for n <= kNoAllocMaxN:
+// the row-ordered product, the update and the vector (setup) kernels.  The two grid-capped ones
+// (update, vector) never exceed their uncapped size, which is what is counted here.
+constexpr int64_t na_div_up(int64_t a, int64_t b) { return (a + b - 1) / b; }
+constexpr int64_t kNaSpmvBlocks = na_div_up(na_div_up(kNoAllocMaxN, kRowsPerWarp) * 32, kPcgThreads);
+constexpr int64_t kNaUpdBlocks = na_div_up(kNoAllocMaxN, kUpdT);
+constexpr int64_t kNaVecBlocks = na_div_up(kNoAllocMaxN, (int64_t)kPcgThreads * kVpt);
+constexpr int kNaMaxBlocks = (int)std::max(std::max(kNaSpmvBlocks, kNaUpdBlocks), kNaVecBlocks);
 // region sizes (bytes), each 256-byte aligned
 constexpr size_t kNaVec = na_align(sizeof(double) * 18 * kNoAllocMaxN);        // b, x, r, s, c, q
 constexpr size_t kNaFac = na_align(sizeof(double) * 6 * kNoAllocMaxN);         // LDL^T factors
@@ -1606,6 +1960,9 @@ extern "C" gipc_status gipc_pcg_noalloc(const gipc_bsr* A, const double* rhs, do
         return fail(GIPC_ERR_INVALID_ARG, "gipc_pcg_noalloc: bad precision");
     if (!(prm->rel_tol >= 0.0) || prm->max_iter < 0 || prm->check_every < 0)
         return fail(GIPC_ERR_INVALID_ARG, "gipc_pcg_noalloc: need rel_tol >= 0, max_iter >= 0, check_every >= 0");
+    // (the float-pair product is accepted and runs as the native one here)
+    if (prm->product != GIPC_PRODUCT_NATIVE && prm->product != GIPC_PRODUCT_FLOAT_PAIR)
+        return fail(GIPC_ERR_INVALID_ARG, "gipc_pcg_noalloc: unknown product arithmetic %d", prm->product);
     if (n == 0) {
         if (iters_out_h) *iters_out_h = 0;
         if (rel_out_h) *rel_out_h = 0.0;
@@ -1619,6 +1976,8 @@ extern "C" gipc_status gipc_pcg_noalloc(const gipc_bsr* A, const double* rhs, do
 
     const int64_t nvec = 3 * n;
     const unsigned vb = vec_blocks(n), sb = spmv_blocks(n), ub = upd_blocks(n), db = dir_blocks(n);
+    if (std::max(std::max(vb, sb), ub) > (unsigned)kNaMaxBlocks)   // cannot happen for n <= kNoAllocMaxN
+        return fail(GIPC_ERR_INVALID_ARG, "gipc_pcg_noalloc: grid exceeds the fixed partials");
     double* V = reinterpret_cast<double*>(base);
     double *b = V, *xv = V + nvec, *r = V + 2 * nvec, *sv = V + 3 * nvec, *c = V + 4 * nvec, *q = V + 5 * nvec;
     double* pinv = reinterpret_cast<double*>(base + kNaVec);

@@ -323,7 +323,7 @@ def batch_stencils(k, seed=20230810, mix=DEFAULT_MIX, dhat=UNIT_DHAT):
 
 
 # ----------------------------------------------------------------------------- two-sheet index space
-def sheet_index_space(k, seed=20230811, side=388, radius=0, mix=DEFAULT_MIX, ordered=True):
+def sheet_index_space(k, seed=20230811, side=388, radius=0, mix=DEFAULT_MIX, ordered=True, return_ids=False):
     """Stencil tuples over two triangulated side x side vertex grids (ids [0, 2 side^2)).
 
     Each stencil couples a primitive of one sheet with a primitive of the other
@@ -334,7 +334,9 @@ def sheet_index_space(k, seed=20230811, side=388, radius=0, mix=DEFAULT_MIX, ord
     With ``ordered`` the stencils of each type follow their cells in row-major
     order, the order in which a broad phase that walks the primitives emits them;
     otherwise they are in random order.
-    Returns (4, k) int32 tuples (same type order as ``type_counts``) and n.
+    Returns (4, k) int32 tuples (same type order as ``type_counts``) and n; with ``return_ids``
+    also the plain vertex ids of every stencil in slot order, a list of (count, s) int64 arrays
+    in the same order (the tuples before sign encoding).
     """
     rng = np.random.default_rng(seed)
     N = side
@@ -369,7 +371,7 @@ def sheet_index_space(k, seed=20230811, side=388, radius=0, mix=DEFAULT_MIX, ord
         c = np.where(up, vid(sheet, i + 1, j + 1), vid(sheet, i, j + 1))
         return np.stack([a, b, c], 1)
 
-    ts = []
+    ts, raw = [], []
     for kind, cnt in type_counts(k, mix):
         if cnt == 0:
             continue
@@ -389,7 +391,9 @@ def sheet_index_space(k, seed=20230811, side=388, radius=0, mix=DEFAULT_MIX, ord
         else:  # EE-derived: two edges
             ids = np.concatenate([edge(sa, i, j), edge(sb, pi, pj)], 1)
         ts.append(_v_encode(kind, ids.astype(np.int64)))
-    return np.ascontiguousarray(np.concatenate(ts, axis=1).astype(np.int32)), n
+        raw.append(ids.astype(np.int64))
+    st = np.ascontiguousarray(np.concatenate(ts, axis=1).astype(np.int32))
+    return (st, n, raw) if return_ids else (st, n)
 
 
 def sheet_mass(side=388, density=1000.0):

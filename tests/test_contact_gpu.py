@@ -155,10 +155,12 @@ def test_newton_step_matches_oracle(gipc):
     assert st["contacts"] == so["contacts"][-1]
     assert st["last_alpha"] == pytest.approx(so["alpha"][-1], rel=1e-8)
     assert abs(st["pcg_iters"] - sum(so["pcg"])) <= 2
+    # measured ~1e-12 of the step (the same iteration counts; only the reductions' summation order
+    # differs); the bound keeps a factor 1000 of margin
     scale = np.abs(xo - x0).max()
     err = np.abs(xg - xo).max() / scale
-    assert err <= 1e-6, f"position error {err:.3e} of the step"
-    assert np.abs(vg - vo).max() <= 1e-6 * np.abs(vo).max()
+    assert err <= 1e-9, f"position error {err:.3e} of the step"
+    assert np.abs(vg - vo).max() <= 1e-9 * np.abs(vo).max()
     assert st["energy"] == pytest.approx(so["energy"], rel=1e-9)
     assert C.count_intersections(xg, sc0["tris"], sc0["edges"]) == 0
 

@@ -156,6 +156,58 @@ def test_large_system_takes_the_split_update_kernels(gipc):
         assert rel == pytest.approx(ref["rel"], rel=1e-8)
 
 
+def _sheet_system(seed=47):
+    """The benchmark's system pattern with well-conditioned values.
+
+    Pattern: the 1M-stencil two-sheet index space of the benchmark (301,088 block rows,
+    4,120,784 blocks), so the solver runs in the benchmark's launch configuration (row order,
+    SELL-32 slices, persistent grid).  Values: mass uniform in [0.5, 1.5] on the diagonal plus a
+    rank-one PSD block lam w w^T per stencil, lam log-uniform in [1, 100], w standard normal,
+    summed per block (an input built here, not by the library).  With these values a relative
+    perturbation of 1e-16 in H moves the iterates by ~1e-14, so 1e-10 is a real bar; with the
+    benchmark's own values (barrier stiffness up to 1e12 times the mass inside one 3x3 diagonal
+    block) the same perturbation moves x_1 by ~5e-4 of its maximum, and two correct FP64
+    solvers differ at that level."""
+    st, n, raw = synth.sheet_index_space(1_000_000, return_ids=True)
+    rng = np.random.default_rng(seed)
+    rows, cols = [np.arange(n, dtype=np.int64)], [np.arange(n, dtype=np.int64)]
+    contrib = [rng.uniform(0.5, 1.5, n)[:, None, None] * np.eye(3)]
+    for ids in raw:
+        m, s = ids.shape
+        w = rng.normal(size=(m, s, 3))
+        lam = 10.0 ** rng.uniform(0, 2, m)
+        for a in range(s):
+            for b in range(s):
+                rows.append(ids[:, a])
+                cols.append(ids[:, b])
+                contrib.append(lam[:, None, None] * w[:, a, :, None] * w[:, b, None, :])
+    rows, cols = np.concatenate(rows), np.concatenate(cols)
+    contrib = np.concatenate(contrib).reshape(-1, 9)
+    key, inv = np.unique(rows * n + cols, return_inverse=True)
+    vals = np.stack([np.bincount(inv, weights=contrib[:, e], minlength=len(key)) for e in range(9)], 1)
+    rowptr = np.zeros(n + 1, np.int64)
+    np.add.at(rowptr, key // n + 1, 1)
+    return {"rowptr": np.cumsum(rowptr), "colidx": key % n, "vals": vals}, rng.normal(size=(3, n)), n
+
+
+def test_full_size_system_matches_oracle_at_fixed_iterations(gipc):
+    """The benchmark-size system (its pattern, 4.1M blocks) through the timed solver configuration:
+    iterates after 1 and 4 iterations elementwise within 1e-10 of the oracle's, for the native and
+    the float-pair product."""
+    R, b, n = _sheet_system()
+    assert len(R["colidx"]) == 4_120_784
+    A_gpu = _gpu_bsr(R, n)
+    bg = torch.tensor(b, device="cuda")
+    for iters in (1, 4):
+        ref = P.pcg(R, n, b, tol=0.0, max_iter=iters)
+        for product in ("native", "float_pair"):
+            x, k, rel = gipc.pcg(A_gpu, bg, rel_tol=0.0, max_iter=iters, product=product)
+            assert k == iters == ref["iters"]
+            err = np.abs(x.cpu().numpy() - ref["x"]).max() / np.abs(ref["x"]).max()
+            assert err <= 1e-10, (iters, product, err)
+            assert rel == pytest.approx(ref["rel"], rel=1e-8)
+
+
 def test_indefinite_matrix_reported(gipc):
     """On request, a direction of negative curvature stops the solve with GIPC_ERR_INDEFINITE
     (the last iterate kept) instead of continuing with a negative step length; by default the
