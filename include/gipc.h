@@ -81,7 +81,9 @@ typedef enum {
     GIPC_HESS_BLOCKS = 2   /* the same dense values, element-major as 16 contiguous 3x3
                             * sub-blocks: entry (3a+i, 3b+j) of element e at
                             * [(e * 16 + 4a + b) * 9 + 3i + j] ([count][16][9]; the
-                            * sub-blocks of slots >= s are not written)                */
+                            * sub-blocks of slots >= s are not written, except that
+                            * gipc_eval_stencils may set to zero the first entry of
+                            * such a sub-block that directly follows a written one)  */
 } gipc_hess_mode;
 
 /* Parameters of the barrier (paper Sec. 5.3-5.4, 6.1).  Lengths are in the

@@ -492,12 +492,10 @@ __global__ void scatter_rows_kernel(const uint64_t* __restrict__ keys, const int
     for (int i = 0; i < 3; ++i) out[(int64_t)i * n + r] = acc[i];
 }
 
-inline unsigned blocks_for(int64_t work, int threads, int64_t cap = 152 * 32) {
-    int64_t b = (work + threads - 1) / threads;
-    if (b < 1) b = 1;
-    if (b > cap) b = cap;
-    return (unsigned)b;
-}
+// Grid for `work` items at `threads` per CTA, capped at `per_sm` CTAs per SM of the current device.
+inline unsigned blocks_for(int64_t work, int threads, int per_sm = 32) { return grid_for(work, threads, per_sm); }
+// One CTA per SM of the current device (the long-row sorts walk their rows in a grid-stride loop).
+inline unsigned one_per_sm() { return (unsigned)std::max(1, device_facts().sms); }
 
 }  // namespace
 }  // namespace gipc
@@ -560,28 +558,25 @@ extern "C" gipc_status gipc_assemble_bsr(gipc_ctx* ctx, int64_t n, const gipc_el
     int64_t* rowptr64 = ctx->slot[S_ROWPTR64].as<int64_t>();
 
     ctx->prof.start(GIPC_PROF_ASM_PATTERN, s);
-    init_rows_kernel<<<blocks_for(n, 256, 1 << 30), 256, 0, s>>>(row_cnt, n, with_mass);
+    init_rows_kernel<<<blocks_for(n, 256, 1 << 20), 256, 0, s>>>(row_cnt, n, with_mass);
     if (ne > 0) count_kernel<<<blocks_for(ne, 256), 256, 0, s>>>(L[0], L[1], n, row_cnt, elem_n3);
     if (exclusive_scan<int32_t>(row_cnt, row_start, n, scan_tmp, s) != cudaSuccess)
         return check_launch("gipc_assemble_bsr: scan");
-    init_cursor_kernel<<<blocks_for(n, 256, 1 << 30), 256, 0, s>>>(row_start, cursor, keys, n, with_mass);
+    init_cursor_kernel<<<blocks_for(n, 256, 1 << 20), 256, 0, s>>>(row_start, cursor, keys, n, with_mass);
     if (ne > 0) fill_kernel<<<blocks_for(ne, 256), 256, 0, s>>>(L[0], L[1], n, elem_n3, cursor, keys);
     if (cudaMemsetAsync(n_long, 0, 2 * sizeof(int32_t), s) != cudaSuccess)
         return fail(GIPC_ERR_CUDA, "gipc_assemble_bsr: memset failed");
-    sort_rows_warp_kernel<<<blocks_for(n, kSortWarps, 152 * 64), 32 * kSortWarps, 0, s>>>(
+    sort_rows_warp_kernel<<<blocks_for(n, kSortWarps, 64), 32 * kSortWarps, 0, s>>>(
         row_start, keys, n, row_nnzb, long_rows, n_long);
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(sort_rows_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(kBlockRowMax * sizeof(uint64_t)));
-        attr_set = true;
-    }
-    sort_rows_block_kernel<<<152, 1024, kBlockRowMax * sizeof(uint64_t), s>>>(row_start, keys, row_nnzb, long_rows,
+    // raises the kernel's shared memory limit on this device (once per device)
+    if (kernel_occupancy((const void*)sort_rows_block_kernel, 1024, kBlockRowMax * sizeof(uint64_t)) <= 0)
+        return fail(GIPC_ERR_CUDA, "gipc_assemble_bsr: long-row sort does not fit the device");
+    sort_rows_block_kernel<<<one_per_sm(), 1024, kBlockRowMax * sizeof(uint64_t), s>>>(row_start, keys, row_nnzb, long_rows,
                                                                           n_long, huge_rows, n_huge);
-    sort_rows_global_kernel<<<152, 1024, 0, s>>>(row_start, keys, row_nnzb, huge_rows, n_huge);
+    sort_rows_global_kernel<<<one_per_sm(), 1024, 0, s>>>(row_start, keys, row_nnzb, huge_rows, n_huge);
     if (exclusive_scan<int32_t>(row_nnzb, rowptr64, n, scan_tmp, s) != cudaSuccess)
         return check_launch("gipc_assemble_bsr: scan");
-    rowptr32_kernel<<<blocks_for(n + 1, 256, 1 << 30), 256, 0, s>>>(rowptr64, bsr->rowptr, n);
+    rowptr32_kernel<<<blocks_for(n + 1, 256, 1 << 20), 256, 0, s>>>(rowptr64, bsr->rowptr, n);
     ctx->prof.stop(GIPC_PROF_ASM_PATTERN, s);
     if ((st = check_launch("gipc_assemble_bsr: pattern")) != GIPC_OK) return st;
     int64_t host_vals[2] = {0, 0};
@@ -608,7 +603,7 @@ extern "C" gipc_status gipc_assemble_bsr(gipc_ctx* ctx, int64_t n, const gipc_el
     int32_t* bin_hist = reinterpret_cast<int32_t*>(bin_off + nbin + 1);
     int32_t* order = bin_hist + nbin;
     ctx->prof.start(GIPC_PROF_ASM_VALUES, s);
-    emit_kernel<<<blocks_for(n, 8, 152 * 64), 256, 0, s>>>(row_start, keys, rowptr64, n, bsr->colidx, seg);
+    emit_kernel<<<blocks_for(n, 8, 64), 256, 0, s>>>(row_start, keys, rowptr64, n, bsr->colidx, seg);
     seg_end_kernel<<<1, 1, 0, s>>>(seg, rowptr64, row_start, n);
     if (grad_out) grad_init_kernel<<<blocks_for(3 * n, 256, 1 << 30), 256, 0, s>>>(grad_base, grad_out, 3 * n);
     if (nnzb > 0) {
@@ -667,21 +662,21 @@ extern "C" gipc_status gipc_scatter_elements(gipc_ctx* ctx, int64_t n, const gip
     int32_t* n_huge = n_long + 1;
     int32_t* huge_rows = n_huge + 1;
     int64_t* scan_tmp = ctx->slot[S_SCAN].as<int64_t>();
-    init_rows_kernel<<<blocks_for(n, 256, 1 << 30), 256, 0, s>>>(row_cnt, n, 0);
+    init_rows_kernel<<<blocks_for(n, 256, 1 << 20), 256, 0, s>>>(row_cnt, n, 0);
     if (ne > 0) count_kernel<<<blocks_for(ne, 256), 256, 0, s>>>(L[0], L[1], n, row_cnt, elem_n3);
     if (exclusive_scan<int32_t>(row_cnt, row_start, n, scan_tmp, s) != cudaSuccess)
         return check_launch("gipc_scatter_elements: scan");
-    init_cursor_kernel<<<blocks_for(n, 256, 1 << 30), 256, 0, s>>>(row_start, cursor, keys, n, 0);
+    init_cursor_kernel<<<blocks_for(n, 256, 1 << 20), 256, 0, s>>>(row_start, cursor, keys, n, 0);
     if (ne > 0) fill_kernel<<<blocks_for(ne, 256), 256, 0, s>>>(L[0], L[1], n, elem_n3, cursor, keys);
     if (cudaMemsetAsync(n_long, 0, 2 * sizeof(int32_t), s) != cudaSuccess)
         return fail(GIPC_ERR_CUDA, "gipc_scatter_elements: memset failed");
-    sort_rows_warp_kernel<<<blocks_for(n, kSortWarps, 152 * 64), 32 * kSortWarps, 0, s>>>(row_start, keys, n, row_nnzb,
+    sort_rows_warp_kernel<<<blocks_for(n, kSortWarps, 64), 32 * kSortWarps, 0, s>>>(row_start, keys, n, row_nnzb,
                                                                                        long_rows, n_long);
-    cudaFuncSetAttribute(sort_rows_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(kBlockRowMax * sizeof(uint64_t)));
-    sort_rows_block_kernel<<<152, 1024, kBlockRowMax * sizeof(uint64_t), s>>>(row_start, keys, row_nnzb, long_rows,
+    if (kernel_occupancy((const void*)sort_rows_block_kernel, 1024, kBlockRowMax * sizeof(uint64_t)) <= 0)
+        return fail(GIPC_ERR_CUDA, "gipc_scatter_elements: long-row sort does not fit the device");
+    sort_rows_block_kernel<<<one_per_sm(), 1024, kBlockRowMax * sizeof(uint64_t), s>>>(row_start, keys, row_nnzb, long_rows,
                                                                           n_long, huge_rows, n_huge);
-    sort_rows_global_kernel<<<152, 1024, 0, s>>>(row_start, keys, row_nnzb, huge_rows, n_huge);
-    scatter_rows_kernel<<<blocks_for(n, 256, 1 << 30), 256, 0, s>>>(keys, row_start, n, L[0], L[1], base, out);
+    sort_rows_global_kernel<<<one_per_sm(), 1024, 0, s>>>(row_start, keys, row_nnzb, huge_rows, n_huge);
+    scatter_rows_kernel<<<blocks_for(n, 256, 1 << 20), 256, 0, s>>>(keys, row_start, n, L[0], L[1], base, out);
     return check_launch("gipc_scatter_elements");
 }

@@ -725,7 +725,7 @@ __global__ void disp_kernel(const double* __restrict__ x, const double* __restri
 }
 
 // persistent warp-per-query grids: at most 16 blocks of kWarps warps per SM
-inline unsigned wblk(int64_t queries) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>((queries + kWarps - 1) / kWarps, 152 * 16)); }
+inline unsigned wblk(int64_t queries) { return grid_for(queries, kWarps, 16); }
 
 // Insert the m primitives (nv vertices each) into hashed grid g over their boxes (x, swept by
 // d if given, padded by pad).  Synchronises once per cell-size attempt.  `pts`: surface
@@ -843,7 +843,7 @@ gipc_status cache_disp(gipc_ctx* ctx, const double* x, const double* d, int64_t 
                        double* delta, double* dmax, cudaStream_t st) {
     unsigned long long* out = reinterpret_cast<unsigned long long*>(ctx->slot[C_MISC].as<double>() + kMiscDisp);
     cudaMemsetAsync(out, 0, 2 * sizeof(unsigned long long), st);
-    const unsigned blocks = std::min(nblk(srf.nvert, 256), 152u * 4u);
+    const unsigned blocks = grid_for(srf.nvert, 256, 4);
     disp_kernel<<<blocks, 256, 0, st>>>(x, ctx->slot[C_CX].as<double>(), d, n, srf.verts, srf.nvert, out);
     unsigned long long h[2] = {0, 0};
     cudaMemcpyAsync(h, out, sizeof(h), cudaMemcpyDeviceToHost, st);

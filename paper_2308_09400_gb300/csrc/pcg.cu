@@ -641,6 +641,9 @@ pcg_spmv_tma_kernel(const int32_t* __restrict__ rowptr, const int64_t* __restric
 constexpr int kU64 = 1, kW64 = 16, kNS64 = 2;
 constexpr int kU32 = 2, kW32 = 16, kNS32 = 2;
 constexpr int kUfp = 2, kWfp = 16, kNSfp = 2;   // float-pair product (8-byte values, FP32-pipe arithmetic)
+// The persistent solver's float-pair product stages one step per group, so that two CTAs fit on an SM
+// (the grid then owns two vertices per thread of the C1 system, as in the other forms).
+constexpr int kUfpLoop = 1;
 
 template <typename VT, typename PT, int U, int W, int NS>
 void launch_spmv_tma(const int32_t* rowptr, const int64_t* slice_off, const int32_t* sell_col, const VT* sell_vals,
@@ -1132,13 +1135,40 @@ __device__ __forceinline__ bool grid_sync(unsigned* count, unsigned target, int*
     return ok != 0;
 }
 
-// Sum of every CTA's part in index order, broadcast to the whole CTA.
-__device__ __forceinline__ double grid_total(const double* part) {
-    __shared__ double tot;
-    const double s = sum_partials(part, gridDim.x);
-    if (threadIdx.x == 0) tot = s;
+// FP64 sums with few FP64 warp-instructions.  On this part the FP64 pipe takes 16 cycles per warp
+// instruction whatever its active lanes, and scalar work repeated by every thread of the grid is
+// paid 32 warps per SM over: so the CTA sums below leave the shuffle tree to one warp, and the
+// solver's scalars (alpha, beta, the stopping test) are formed by one lane and shared.
+//
+// Sum of the CTA's values (blockDim.x <= kLoopT), in a fixed order: every thread stores its value,
+// warp 0 adds them lane-strided and reduces across its lanes.  Valid in warp 0.
+__device__ __forceinline__ double cta_sum_lean(double v, double* buf) {
+    buf[threadIdx.x] = v;
     __syncthreads();
-    return tot;
+    double s = 0.0;
+    if (threadIdx.x < 32) {
+        for (int i = threadIdx.x; i < (int)blockDim.x; i += 32) s += buf[i];
+        s = warp_sum(s);
+    }
+    return s;
+}
+
+// Sum of every CTA's part in index order (at most 16 x 32 parts), by warp 0 with all its loads in
+// flight at once.  Valid in warp 0.
+__device__ __forceinline__ double grid_sum_lean(const double* part) {
+    double s = 0.0;
+    if (threadIdx.x < 32) {
+        double v[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const int i = (int)threadIdx.x + 32 * j;
+            v[j] = i < (int)gridDim.x ? __ldcg(part + i) : 0.0;
+        }
+#pragma unroll
+        for (int j = 0; j < 16; ++j) s += v[j];
+        s = warp_sum(s);
+    }
+    return s;
 }
 
 // CTAs per SM the persistent solver is compiled for: two where two staging areas fit in shared
@@ -1157,23 +1187,26 @@ pcg_loop_kernel(const int32_t* __restrict__ rowptr, const int64_t* __restrict__ 
                 double* part_a, double* part_b, PcgScalars* S, int iters) {
     using ST = FacT<MIX>;
     using CT = typename std::conditional<MIX, float, double>::type;   // the kept direction
-    // scalars every thread of the CTA shares, kept in shared memory rather than in registers
-    __shared__ double sh_tol, sh_delta0, sh_delta_prev, sh_beta, sh_alpha, sh_pq;
-    __shared__ int sh_max_iter, sh_stop_indefinite;
+    // The solver's scalars, formed by thread 0 and shared with the CTA (every CTA forms the same
+    // values from the same parts): delta = r.s, alpha, beta (and beta in float32), the stopping
+    // state, and the constants of the stopping test.
+    __shared__ double sh_delta, sh_delta_prev, sh_beta, sh_alpha, sh_pq;
+    __shared__ float sh_beta_f;
+    __shared__ int sh_stop;   // 0: go on; 1: done after the update; 2: done before it (indefinite)
+    __shared__ double red[kLoopT];
     if (S->done) return;   // read before any CTA can change it: uniform
     const int t = threadIdx.x;
     if (t == 0) {
-        sh_tol = S->tol;
-        sh_delta0 = S->delta0;
+        sh_delta = S->delta_new;
         sh_delta_prev = S->delta_old;
         sh_beta = S->beta;
         sh_alpha = S->alpha;
         sh_pq = S->pq;
-        sh_max_iter = S->max_iter;
-        sh_stop_indefinite = S->stop_indefinite;
+        sh_stop = 0;
     }
-    double delta = S->delta_new;
-    int it_total = S->iters, status = GIPC_OK, done = 0;
+    const double tol = S->tol, delta0 = S->delta0;   // read by thread 0 only (below)
+    const int max_iter = S->max_iter, stop_indefinite = S->stop_indefinite;
+    int it_total = S->iters, status = GIPC_OK;
     bool abort = false;
     StageRing<VT, U, kLoopW, NS> R;
     R.init();
@@ -1192,24 +1225,27 @@ pcg_loop_kernel(const int32_t* __restrict__ rowptr, const int64_t* __restrict__ 
             R.preissue(((int64_t)blockIdx.x * blockDim.x + t) >> 5, nsl, slice_off, sell_vals, sell_col);
         }
         {
-            const double bs = block_sum(d);
+            const double bs = cta_sum_lean(d, red);
             if (t == 0) part_a[blockIdx.x] = bs;
         }
         if (!sync()) {
             abort = true;
             break;
         }
-        const double pq = grid_total(part_a);
-        const double alpha = delta / pq;
-        if (t == 0) {
-            sh_pq = pq;
-            sh_alpha = alpha;
+        {
+            const double pq = grid_sum_lean(part_a);
+            if (t == 0) {
+                sh_pq = pq;
+                sh_alpha = sh_delta / pq;
+                if (stop_indefinite && pq <= 0.0) sh_stop = 2;   // no descent along c: H not positive definite
+            }
         }
-        if (sh_stop_indefinite && pq <= 0.0) {   // no descent along c: H not positive definite
+        __syncthreads();
+        if (sh_stop == 2) {
             status = GIPC_ERR_INDEFINITE;
-            done = 1;
             break;
         }
+        const double alpha = sh_alpha;
         // B: x += alpha c; r -= alpha q; s = P^-1 r; parts of r . s
         ST sk[kLoopKeep][3];
         CT ck[kLoopKeep][3];
@@ -1240,30 +1276,34 @@ pcg_loop_kernel(const int32_t* __restrict__ rowptr, const int64_t* __restrict__ 
             }
         }
         {
-            const double bs = block_sum(d2);
+            const double bs = cta_sum_lean(d2, red);
             if (t == 0) part_b[blockIdx.x] = bs;
         }
         if (!sync()) {
             abort = true;
             break;
         }
-        const double dn = grid_total(part_b);
-        const double beta = dn / delta;
-        if (t == 0) {
-            sh_beta = beta;
-            sh_delta_prev = delta;
-        }
-        delta = dn;
         it_total += 1;
-        if (!isfinite(dn) || !isfinite(alpha)) {
-            status = GIPC_ERR_NONFINITE;
-            done = 1;
-        } else if (!(dn > 0.0) || dn < sh_tol * sh_delta0 || it_total >= sh_max_iter) {
-            done = 1;
+        {
+            const double dn = grid_sum_lean(part_b);
+            if (t == 0) {
+                const double beta = dn / sh_delta;
+                sh_beta = beta;
+                sh_beta_f = (float)beta;
+                sh_delta_prev = sh_delta;
+                sh_delta = dn;
+                if (!isfinite(dn) || !isfinite(sh_alpha)) sh_stop = 3;   // non-finite
+                else if (!(dn > 0.0) || dn < tol * delta0 || it_total >= max_iter) sh_stop = 1;
+            }
         }
-        if (done) break;
+        __syncthreads();
+        if (sh_stop) {
+            if (sh_stop == 3) status = GIPC_ERR_NONFINITE;
+            break;
+        }
         // C: c = S(s + beta c)
-        const float beta_f = (float)beta;
+        const double beta = sh_beta;
+        const float beta_f = sh_beta_f;
 #pragma unroll
         for (int j = 0; j < kLoopKeep; ++j) {
             const int64_t v = ((int64_t)j * gridDim.x + blockIdx.x) * kLoopT + t;
@@ -1292,14 +1332,14 @@ pcg_loop_kernel(const int32_t* __restrict__ rowptr, const int64_t* __restrict__ 
     __syncthreads();
     if (blockIdx.x == 0 && t == 0) {
         S->delta_old = sh_delta_prev;
-        S->delta_new = delta;
+        S->delta_new = sh_delta;
         S->beta = sh_beta;
         S->alpha = sh_alpha;
         S->pq = sh_pq;
         S->iters = it_total;
         if (!abort && *(volatile int*)&S->status != GIPC_ERR_TIMEOUT) {
             S->status = status;
-            S->done = done;
+            S->done = sh_stop != 0;
         } else {
             S->done = 1;
         }
@@ -1665,7 +1705,7 @@ gipc_status pcg_impl(gipc_ctx* ctx, const gipc_bsr* A, const double* rhs, double
     // one persistent launch for all iterations of a single system where the grid holds it
     LoopPlan loop;
     if (!voff) {
-        if (fp) loop = plan_loop<fpair, fpair, kUfp, kNSfp, false>(n, nsl);
+        if (fp) loop = plan_loop<fpair, fpair, kUfpLoop, kNSfp, false>(n, nsl);
         else if (f64) loop = plan_loop<double, double, kU64, kNS64, false>(n, nsl);
         else loop = plan_loop<float, float, kU32, kNS32, true>(n, nsl);
     }
@@ -1755,7 +1795,7 @@ gipc_status pcg_impl(gipc_ctx* ctx, const gipc_bsr* A, const double* rhs, double
         const void* fn;
         const void* cg;
         if (fp) {
-            fn = (const void*)pcg_loop_kernel<fpair, fpair, kUfp, kNSfp, false>;
+            fn = (const void*)pcg_loop_kernel<fpair, fpair, kUfpLoop, kNSfp, false>;
             cg = c2;
         } else if (f64) {
             fn = (const void*)pcg_loop_kernel<double, double, kU64, kNS64, false>;

@@ -275,18 +275,16 @@ __device__ __forceinline__ int64_t dense_at(int a, int b, int n3, int64_t k, int
     return (int64_t)(a * n3 + b) * k + e;
 }
 
-template <int PREC, int MODE>
-__global__ void __launch_bounds__(128)
-eval_stencils_kernel(const double* __restrict__ x, int64_t n, const int32_t* __restrict__ st, int64_t k,
-                     const double* __restrict__ eps_x, const BarrierConst K, double* __restrict__ energy,
-                     double* __restrict__ grad, void* __restrict__ hess_v, double* __restrict__ lam,
-                     uint8_t* __restrict__ flags) {
+// One stencil (paper Alg. 2): decode, gather, gap and barrier, projected eigensystem.  Returns
+// false for a malformed stencil (fl = GIPC_FLAG_INVALID, nothing else set).  Otherwise sets the
+// energy, the rank-one factors (H = lam_out w w^T), the gradient over the first n3 = 3s entries
+// and the flags; entries past n3 stay as the caller initialised them (zero).
+template <int PREC>
+__device__ __forceinline__ bool eval_one(const double* __restrict__ x, int64_t n, const int32_t* __restrict__ st,
+                                         int64_t k, const double* __restrict__ eps_x, const BarrierConst& K, int64_t i,
+                                         double& e_out, double& lam_out, double (&w)[12], double (&gr)[12],
+                                         uint8_t& fl, int& n3) {
     constexpr bool ACC = (PREC == GIPC_FP64);
-    using HT = typename std::conditional<PREC == GIPC_FP64, double, float>::type;
-    HT* __restrict__ hess = static_cast<HT*>(hess_v);
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= k) return;
-
     int32_t vid[4];
     const int type = decode_stencil(__ldg(st + i), __ldg(st + k + i), __ldg(st + 2 * k + i),
                                     __ldg(st + 3 * k + i), vid);
@@ -296,10 +294,8 @@ eval_stencils_kernel(const double* __restrict__ x, int64_t n, const int32_t* __r
     for (int j = 0; j < 4; ++j)
         if (j < s && vid[j] >= n) ok = false;
     if (!ok) {
-        if (energy) energy[i] = 0.0;
-        if (lam) lam[i] = 0.0;
-        if (flags) flags[i] = GIPC_FLAG_INVALID;
-        return;
+        fl = GIPC_FLAG_INVALID;
+        return false;
     }
     double X[4][3];
 #pragma unroll
@@ -342,14 +338,7 @@ eval_stencils_kernel(const double* __restrict__ x, int64_t n, const int32_t* __r
             break;
     }
 
-    const int n3 = 3 * s;
-    double e_out = 0.0, lam_out = 0.0, w[12], gr[12];
-    uint8_t fl = 0;
-#pragma unroll
-    for (int j = 0; j < 12; ++j) {
-        w[j] = 0.0;
-        gr[j] = 0.0;
-    }
+    n3 = 3 * s;
     if (g < 1.0) {
         fl = GIPC_FLAG_ACTIVE;
         double b, bg, bgg;
@@ -414,53 +403,139 @@ eval_stencils_kernel(const double* __restrict__ x, int64_t n, const int32_t* __r
             }
         }
     }
+    return true;
+}
 
-    if (energy) energy[i] = e_out;
-    if (flags) flags[i] = fl;
-    if (grad) {
+// Writes m staged stencils' 144-entry blocks (element-major 3x3 sub-blocks) as one contiguous run,
+// two entries per lane per store.  Stencil e of the stage holds t = lam w (12 values) then w (12
+// values) at e * kStageStride (an odd stride, so the lanes' staging writes fall in distinct
+// banks); entry (p, q) of its block is t_P w_Q with P = max(p, q), Q = min(p, q) -- the product
+// the per-stencil form computes.  Sub-blocks outside a stencil's 3s x 3s block are not written
+// (a stored pair that straddles the edge of the block writes a zero beside it).
+constexpr int kStageStride = 25;
+template <typename HT>
+__device__ __forceinline__ void write_staged_blocks(HT* out, int m, const HT* stage, const int* n3s, int lane) {
+    for (int wd = 2 * lane; wd < m * 144; wd += 64) {
+        HT v2[2];
+        bool used = false;
 #pragma unroll
-        for (int j = 0; j < 12; ++j)
-            if (j < n3) grad[j * k + i] = gr[j];
+        for (int u = 0; u < 2; ++u) {
+            const int ww = wd + u;
+            const int e = ww / 144, idx = ww - 144 * e;
+            const int b16 = idx / 9, w9 = idx - 9 * b16;
+            const int p = 3 * (b16 >> 2) + w9 / 3, q = 3 * (b16 & 3) + w9 % 3;
+            const int P = p > q ? p : q, Q = p > q ? q : p;
+            used |= P < n3s[e];
+            v2[u] = (P < n3s[e]) ? stage[e * kStageStride + P] * stage[e * kStageStride + 12 + Q] : HT(0);
+        }
+        if (!used) continue;   // both entries outside the stencil's 3s x 3s block: left as they are
+        if constexpr (std::is_same<HT, double>::value)
+            *reinterpret_cast<double2*>(out + wd) = make_double2(v2[0], v2[1]);
+        else
+            *reinterpret_cast<float2*>(out + wd) = make_float2(v2[0], v2[1]);
     }
-    if (MODE == GIPC_HESS_RANK1) {
-        if (lam) lam[i] = lam_out;
-        if (hess) {
+}
+
+constexpr int kEvalThreads = 128;
+
+template <int PREC, int MODE>
+__global__ void __launch_bounds__(kEvalThreads)
+eval_stencils_kernel(const double* __restrict__ x, int64_t n, const int32_t* __restrict__ st, int64_t k,
+                     const double* __restrict__ eps_x, const BarrierConst K, double* __restrict__ energy,
+                     double* __restrict__ grad, void* __restrict__ hess_v, double* __restrict__ lam,
+                     uint8_t* __restrict__ flags) {
+    using HT = typename std::conditional<PREC == GIPC_FP64, double, float>::type;
+    HT* __restrict__ hess = static_cast<HT*>(hess_v);
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    constexpr bool kCoop = (MODE == GIPC_HESS_BLOCKS);
+    if (!kCoop && i >= k) return;   // (the element-major output is written by whole warps)
+    const bool live = i < k;
+
+    double e_out = 0.0, lam_out = 0.0, w[12], gr[12];
+    uint8_t fl = 0;
+    int n3 = 0;
+#pragma unroll
+    for (int j = 0; j < 12; ++j) {
+        w[j] = 0.0;
+        gr[j] = 0.0;
+    }
+    const bool valid = live && eval_one<PREC>(x, n, st, k, eps_x, K, i, e_out, lam_out, w, gr, fl, n3);
+    if (live && !valid) {
+        if (energy) energy[i] = 0.0;
+        if (lam) lam[i] = 0.0;
+        if (flags) flags[i] = GIPC_FLAG_INVALID;
+        if (!kCoop) return;
+    }
+    if (valid) {
+        if (energy) energy[i] = e_out;
+        if (flags) flags[i] = fl;
+        if (grad) {
 #pragma unroll
             for (int j = 0; j < 12; ++j)
-                if (j < n3) st_out(hess, j * k + i, w[j]);
+                if (j < n3) grad[j * k + i] = gr[j];
         }
-    } else if (hess) {
-        if (PREC == GIPC_FP64) {
+        if (MODE == GIPC_HESS_RANK1) {
+            if (lam) lam[i] = lam_out;
+            if (hess) {
 #pragma unroll
-            for (int a = 0; a < 12; ++a) {
-                if (a < n3) {
-                    const double ta = lam_out * w[a];
+                for (int j = 0; j < 12; ++j)
+                    if (j < n3) st_out(hess, j * k + i, w[j]);
+            }
+        } else if (hess && !kCoop) {
+            if (PREC == GIPC_FP64) {
 #pragma unroll
-                    for (int bcol = 0; bcol <= a; ++bcol) {
-                        const double h = ta * w[bcol];
-                        hess[dense_at<MODE>(a, bcol, n3, k, i)] = h;
-                        if (bcol != a) hess[dense_at<MODE>(bcol, a, n3, k, i)] = h;
+                for (int a = 0; a < 12; ++a) {
+                    if (a < n3) {
+                        const double ta = lam_out * w[a];
+#pragma unroll
+                        for (int bcol = 0; bcol <= a; ++bcol) {
+                            const double h = ta * w[bcol];
+                            hess[dense_at<MODE>(a, bcol, n3, k, i)] = h;
+                            if (bcol != a) hess[dense_at<MODE>(bcol, a, n3, k, i)] = h;
+                        }
+                    }
+                }
+            } else {
+                float wf[12];
+#pragma unroll
+                for (int j = 0; j < 12; ++j) wf[j] = (float)w[j];
+                const float lf = (float)lam_out;
+#pragma unroll
+                for (int a = 0; a < 12; ++a) {
+                    if (a < n3) {
+                        const float ta = lf * wf[a];
+#pragma unroll
+                        for (int bcol = 0; bcol <= a; ++bcol) {
+                            const float h = ta * wf[bcol];
+                            hess[dense_at<MODE>(a, bcol, n3, k, i)] = h;
+                            if (bcol != a) hess[dense_at<MODE>(bcol, a, n3, k, i)] = h;
+                        }
                     }
                 }
             }
-        } else {
-            float wf[12];
-#pragma unroll
-            for (int j = 0; j < 12; ++j) wf[j] = (float)w[j];
-            const float lf = (float)lam_out;
-#pragma unroll
-            for (int a = 0; a < 12; ++a) {
-                if (a < n3) {
-                    const float ta = lf * wf[a];
-#pragma unroll
-                    for (int bcol = 0; bcol <= a; ++bcol) {
-                        const float h = ta * wf[bcol];
-                        hess[dense_at<MODE>(a, bcol, n3, k, i)] = h;
-                        if (bcol != a) hess[dense_at<MODE>(bcol, a, n3, k, i)] = h;
-                    }
-                }
-            }
         }
+
+    }
+    if constexpr (kCoop) {
+        // element-major 3x3 sub-blocks: stage each stencil's rank-one factors, then one coalesced
+        // run of the warp's 32 blocks
+        __shared__ HT stage[kEvalThreads / 32][32 * kStageStride];
+        __shared__ int stage_n3[kEvalThreads / 32][32];
+        if (!hess) return;   // (uniform)
+        const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+        const HT lf = (HT)lam_out;
+        HT* my = &stage[wi][lane * kStageStride];
+#pragma unroll
+        for (int j = 0; j < 12; ++j) {
+            const HT wj = (HT)w[j];
+            my[j] = lf * wj;
+            my[12 + j] = wj;
+        }
+        stage_n3[wi][lane] = valid ? n3 : 0;
+        __syncwarp();
+        const int64_t e0 = i - lane;
+        const int64_t m = k - e0 < 32 ? k - e0 : 32;
+        if (m > 0) write_staged_blocks<HT>(hess + e0 * 144, (int)m, stage[wi], stage_n3[wi], lane);
     }
 }
 
@@ -537,10 +612,10 @@ extern "C" gipc_status gipc_eval_stencils(const double* x, int64_t n, const int3
     K.lam1_thr = host_lambda1(K.eps_g, K.dhat4);
     K.kappa = prm->kappa;
 
-    const unsigned blocks = grid_for(k, 128);
+    const unsigned blocks = grid_for(k, kEvalThreads);
     cudaStream_t s = (cudaStream_t)stream;
 #define GIPC_LAUNCH(P, M) \
-    eval_stencils_kernel<P, M><<<blocks, 128, 0, s>>>(x, n, stencils, k, eps_x, K, energy, grad, hess, lam, flags)
+    eval_stencils_kernel<P, M><<<blocks, kEvalThreads, 0, s>>>(x, n, stencils, k, eps_x, K, energy, grad, hess, lam, flags)
     if (prec == GIPC_FP64 && mode == GIPC_HESS_DENSE) GIPC_LAUNCH(GIPC_FP64, GIPC_HESS_DENSE);
     else if (prec == GIPC_FP64 && mode == GIPC_HESS_BLOCKS) GIPC_LAUNCH(GIPC_FP64, GIPC_HESS_BLOCKS);
     else if (prec == GIPC_FP64) GIPC_LAUNCH(GIPC_FP64, GIPC_HESS_RANK1);
