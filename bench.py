@@ -804,9 +804,10 @@ def run_diff_bench(g, dev, ctx, steps, fd_h=1e-6, eps_d=1e-5, eps_polish=1e-12):
 
 
 # ----------------------------------------------------------------------------- oracle (CPU) arm
-ORACLE_EVAL_SAMPLE = 4000     # stencils evaluated by the oracle per measurement (all host cores)
-ORACLE_SINGLE_SAMPLE = 500    # stencils evaluated single-threaded (reported beside)
-ORACLE_PCG_ITERS = 20         # oracle PCG iterations timed per measurement (tolerance 0: equal cost each)
+ORACLE_EVAL_SAMPLE = 400       # stencils evaluated per measurement (one core, in process)
+ORACLE_ASM_SAMPLE = 2000       # stencils assembled per measurement (their own compact index space)
+ORACLE_MASS_ROWS = 20000       # mass rows assembled per measurement
+ORACLE_PCG_ITERS = 10         # oracle PCG iterations timed per measurement (tolerance 0: equal cost each)
 
 
 def full_pattern_system(Wh):
@@ -837,76 +838,105 @@ def full_pattern_system(Wh):
     return {"rowptr": np.cumsum(rowptr), "colidx": key % n, "vals": vals.reshape(-1, 3, 3)}, rng.normal(size=(3, n))
 
 
-def full_keys(Wh):
-    """Assembly keys of the whole batch: every ordered vertex pair of every stencil plus the diagonal."""
-    return Wh["n"] + sum(ids.shape[0] * ids.shape[1] ** 2 for ids in Wh["sheet_ids"])
+def full_stencil_keys(Wh):
+    """Assembly keys of the whole batch's stencils: every ordered vertex pair of every stencil."""
+    return sum(ids.shape[0] * ids.shape[1] ** 2 for ids in Wh["sheet_ids"])
 
 
-def oracle_step_costs(args, Wh, procs, system):
-    """The oracle's per-unit costs of one C1 step, each measured on a fixed amount of its own work:
-    the stencil evaluation on the first ORACLE_EVAL_SAMPLE stencils (``procs`` spawn processes),
-    the plain assembly of those stencils plus the mass over all n rows (seconds per assembly key),
-    and ORACLE_PCG_ITERS iterations of its PCG on a full-size system (tolerance 0, so every
-    iteration does the same work).  The whole step's time is then K x seconds per stencil + all keys
-    x seconds per key + PCG_ITERS x seconds per iteration, independent of the sample sizes."""
+def _decoded_ids(st):
+    """Vertex ids of sign-encoded stencil tuples (negative slot -(i + 1), null slots dropped)."""
+    import numpy as np
+    v = np.asarray(st, dtype=np.int64)
+    ids = np.where(v >= 0, v, -v - 1)
+    return ids[v != -2147483648]
+
+
+def _compact(st):
+    """The tuples renumbered onto the vertices they use (signs and null slots kept)."""
+    import numpy as np
+    v = np.asarray(st, dtype=np.int64)
+    null = v == -2147483648
+    ids = np.where(v >= 0, v, -v - 1)
+    uniq, inv = np.unique(np.where(null, -1, ids), return_inverse=True)
+    shift = 1 if uniq[0] == -1 else 0
+    new = inv.reshape(v.shape) - shift
+    out = np.where(null, v, np.where(v >= 0, new, -new - 1))
+    return np.ascontiguousarray(out.astype(np.int32)), len(uniq) - shift
+
+
+def oracle_step_costs(args, Wh, system):
+    """The oracle's cost of one C1 step from its costs per unit of work, each measured on one core
+    in this process on a fixed amount of that work, so the result does not depend on sample sizes:
+    the stencil evaluation per stencil (ORACLE_EVAL_SAMPLE stencils), the plain assembly per key
+    (ORACLE_ASM_SAMPLE stencils over the vertices they use) and per mass row (ORACLE_MASS_ROWS
+    rows), and the PCG per iteration (ORACLE_PCG_ITERS iterations at tolerance 0 on a full-size
+    system of the benchmark's pattern).  Step = K x s per stencil + the batch's keys x s per key +
+    n x s per row + PCG_ITERS x s per iteration."""
     import numpy as np
     from oracle import assembly as OA
     from oracle import pcg as OP
     from oracle import stencil as OS
-    k = ORACLE_EVAL_SAMPLE
-    st = np.ascontiguousarray(Wh["st_own"][:, :k])
-    sh = np.ascontiguousarray(Wh["st_sheet"][:, :k])
-    eps = OS.compute_eps_x(Wh["x"], st)
+    ke = ORACLE_EVAL_SAMPLE
+    st = np.ascontiguousarray(Wh["st_own"][:, :ke])
+    xs = np.ascontiguousarray(Wh["x"][:, :int(_decoded_ids(st).max()) + 1])
+    eps = OS.compute_eps_x(xs, st)
     t = time.perf_counter()
-    r = OS.eval_stencils(Wh["x"], st, eps, Wh["dhat"], KAPPA, processes=procs)
-    t_eval = time.perf_counter() - t
+    OS.eval_stencils(xs, st, eps, Wh["dhat"], KAPPA, processes=1)
+    s_eval = (time.perf_counter() - t) / ke
+    ka = ORACLE_ASM_SAMPLE
+    sh, m = _compact(Wh["st_sheet"][:, :ka])
+    rng = np.random.default_rng(20230816)
     if args.hess_mode == "rank1":
-        sd = {"kind": "rank1", "lam": r["lam"], "w": r["w"], "grad": r["grad"]}
+        sd = {"kind": "rank1", "lam": rng.uniform(1, 2, ka), "w": rng.normal(size=(12, ka)), "grad": rng.normal(size=(12, ka))}
     else:
-        sd = {"kind": "dense", "hess": r["hess"], "grad": r["grad"]}
+        sd = {"kind": "dense", "hess": rng.normal(size=(144, ka)), "grad": rng.normal(size=(12, ka))}
+    keys = sum(len(v) ** 2 for v in OA.element_vertices(sh, None))
     t = time.perf_counter()
-    A = OA.assemble(Wh["n"], sh, sd, None, None, Wh["mass"])
-    t_asm = time.perf_counter() - t
-    keys = Wh["n"] + sum(len(x) ** 2 for x in OA.element_vertices(sh, None))
+    OA.assemble(m, sh, sd, None, None, None)
+    s_key = (time.perf_counter() - t) / keys
+    nr = ORACLE_MASS_ROWS
+    t = time.perf_counter()
+    OA.assemble(nr, None, None, None, None, np.asarray(Wh["mass"])[:nr])
+    s_row = (time.perf_counter() - t) / nr
     R, b = system
     t = time.perf_counter()
     OP.pcg(R, Wh["n"], b, tol=0.0, max_iter=ORACLE_PCG_ITERS)
-    t_pcg = time.perf_counter() - t
-    s_eval, s_key, s_it = t_eval / k, t_asm / keys, t_pcg / ORACLE_PCG_ITERS
-    total = K_STENCILS * s_eval + full_keys(Wh) * s_key + PCG_ITERS * s_it
-    return {"eval_stencils_per_s": 1.0 / s_eval, "assembly_keys_per_s": 1.0 / s_key, "pcg_s_per_iteration": s_it,
-            "full_step_s": total, "stencils_per_s": K_STENCILS / total,
-            "measured_s": t_eval + t_asm + t_pcg, "nnzb_assembled_sample": int(len(A["colidx"]))}
+    s_it = (time.perf_counter() - t) / ORACLE_PCG_ITERS
+    total = K_STENCILS * s_eval + full_stencil_keys(Wh) * s_key + Wh["n"] * s_row + PCG_ITERS * s_it
+    return {"eval_stencils_per_s": 1.0 / s_eval, "assembly_keys_per_s": 1.0 / s_key, "mass_rows_per_s": 1.0 / s_row,
+            "pcg_s_per_iteration": s_it, "full_step_s": total, "stencils_per_s": K_STENCILS / total}
 
 
-def _oracle_desc(procs, n, nnzb_full):
-    return (f"oracle per-unit costs scaled to the whole {K_STENCILS}-stencil step: exact-geometry evaluation of "
-            f"a fixed {ORACLE_EVAL_SAMPLE}-stencil sample on {procs} spawn processes (s per stencil x "
-            f"{K_STENCILS}), plain assembly of that sample plus the mass of all {n} rows (s per key x the "
-            f"batch's keys), and oracle PCG iterations on a full-size system of the benchmark's pattern "
-            f"({nnzb_full} blocks; {ORACLE_PCG_ITERS} timed, s per iteration x {PCG_ITERS})")
+def _oracle_desc(n, nnzb_full):
+    return (f"oracle on one host core, its cost per unit of work scaled to the whole {K_STENCILS}-stencil step: "
+            f"exact-geometry evaluation of {ORACLE_EVAL_SAMPLE} stencils (s per stencil x {K_STENCILS}), plain "
+            f"assembly of {ORACLE_ASM_SAMPLE} stencils (s per key x the batch's keys) and of {ORACLE_MASS_ROWS} mass "
+            f"rows (s per row x {n}), and {ORACLE_PCG_ITERS} oracle PCG iterations on a full-size system of the "
+            f"benchmark's pattern ({nnzb_full} blocks; s per iteration x {PCG_ITERS})")
 
 
 def cpu_baseline(args, Wh):
-    """The oracle's whole step (per-unit costs, see oracle_step_costs) on all host cores, and its
-    stencil evaluation alone on all cores and on one core."""
+    """The oracle's whole step from its per-unit costs on one host core (see oracle_step_costs),
+    and, for reference, its stencil evaluation alone on all host cores (spawned processes)."""
     import numpy as np
     from oracle import stencil as OS
-    procs = os.cpu_count() or 1
     system = full_pattern_system(Wh)
-    c = oracle_step_costs(args, Wh, procs, system)
-    single = ORACLE_SINGLE_SAMPLE
-    st = np.ascontiguousarray(Wh["st_own"][:, :single])
-    eps = OS.compute_eps_x(Wh["x"], st)
-    t1 = time.perf_counter()
-    OS.eval_stencils(Wh["x"], st, eps, Wh["dhat"], KAPPA, processes=1)
-    eval_one = single / (time.perf_counter() - t1)
-    return {"value": c["stencils_per_s"], "unit": "stencils/s", "cores": procs, "kind": "oracle",
-            "sample": _oracle_desc(procs, Wh["n"], len(system[0]["colidx"])) + f"; {c['measured_s']:.1f} s measured",
+    c = oracle_step_costs(args, Wh, system)
+    procs = os.cpu_count() or 1
+    k = 4000
+    st = np.ascontiguousarray(Wh["st_own"][:, :k])
+    xs = np.ascontiguousarray(Wh["x"][:, :int(_decoded_ids(st).max()) + 1])
+    eps = OS.compute_eps_x(xs, st)
+    t = time.perf_counter()
+    OS.eval_stencils(xs, st, eps, Wh["dhat"], KAPPA, processes=procs)
+    eval_all = k / (time.perf_counter() - t)
+    return {"value": c["stencils_per_s"], "unit": "stencils/s", "cores": 1, "kind": "oracle",
+            "sample": _oracle_desc(Wh["n"], len(system[0]["colidx"])),
             "phases": {"eval_stencils_per_s": c["eval_stencils_per_s"], "assembly_keys_per_s": c["assembly_keys_per_s"],
-                       "pcg_s_per_iteration": c["pcg_s_per_iteration"], "full_step_s": c["full_step_s"]},
-            "eval_only": {"all_cores": c["eval_stencils_per_s"], "cores": procs, "single_thread": eval_one,
-                          "single_thread_sample": single, "unit": "stencils/s"}}
+                       "mass_rows_per_s": c["mass_rows_per_s"], "pcg_s_per_iteration": c["pcg_s_per_iteration"],
+                       "full_step_s": c["full_step_s"]},
+            "eval_only_all_cores": {"stencils_per_s": eval_all, "cores": procs, "sample": k,
+                                    "note": "pool start-up included"}}
 
 
 def run_reference(args):
@@ -914,25 +944,24 @@ def run_reference(args):
     if rank != 0:
         return
     Wh = workload()
-    procs = os.cpu_count() or 1
     system = full_pattern_system(Wh)
     for _ in range(args.warmup):
-        oracle_step_costs(args, Wh, procs, system)
+        oracle_step_costs(args, Wh, system)
     totals = []
     t = time.perf_counter()
     for _ in range(args.steps):
-        totals.append(oracle_step_costs(args, Wh, procs, system)["full_step_s"])
+        totals.append(oracle_step_costs(args, Wh, system)["full_step_s"])
     wall = (time.perf_counter() - t) / args.steps
     step_s = sum(totals) / len(totals)
     v = K_STENCILS / step_s
-    desc = _oracle_desc(procs, Wh["n"], len(system[0]["colidx"]))
+    desc = _oracle_desc(Wh["n"], len(system[0]["colidx"]))
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": "stencils/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": workload_desc(args), "precision": args.precision, "hess_mode": args.hess_mode,
                    "oracle_eval_sample": ORACLE_EVAL_SAMPLE, "measured_wall_s_per_step": wall},
-        "cpu_baseline": {"value": v, "unit": "stencils/s", "cores": procs, "kind": "oracle", "sample": desc},
+        "cpu_baseline": {"value": v, "unit": "stencils/s", "cores": 1, "kind": "oracle", "sample": desc},
         "e2e": {"value": v, "unit": "stencils/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 

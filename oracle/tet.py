@@ -3,7 +3,9 @@
 The paper's deformable bodies use the Stable neo-Hookean energy of Smith et al. (its
 Sec. 8, first paragraph; the analytic eigensystems of isotropic energies are the cited
 Smith et al. 2019, Sec. 2 "Eigen Analysis").  The energy is not restated in the paper;
-this module writes it from the Stable neo-Hookean paper (reading in the design notes):
+this module writes it from the Stable neo-Hookean paper (Smith, de Goes and Kim, ACM TOG
+2018): its energy with the rest-stable offset alpha and its match of (mu, lam) to the Lame
+parameters of linear elasticity:
 
     Psi(F) = mu/2 (I_C - 3) + lam/2 (J - alpha)^2 - mu/2 log(I_C + 1),
     I_C = ||F||_F^2,  J = det F,  alpha = 1 + mu/lam - mu/(4 lam)   (rest-stable: dPsi/dF(I) = 0)

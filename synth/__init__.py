@@ -589,12 +589,12 @@ def sphere_grid(nx=8, ny=8, radius=0.1, cells=14, gap=1e-3, floor_cells=64, jitt
 
 
 def beam_on_plate(beam=(41, 11, 11), plate=(65, 65, 4), beam_cell=0.025, plate_side=2.0, turn=0.3,
-                  gap_frac=0.5, velocity=(0.05, 0.0, -0.1)):
+                  gap_frac=0.5, velocity=(0.05, 0.0, -0.1), dhat_rel=1e-3):
     """A tet-meshed beam (vertex grid `beam`, cell `beam_cell`: 41 x 11 x 11 is 1.0 x 0.25 x 0.25)
     turned by `turn` rad about z and lying `gap_frac` dhat above a tet-meshed plate (vertex grid
     `plate` over a square of side `plate_side`, same cell height as width) whose bottom layer is
-    fixed; dhat = 1e-3 l.  The turn keeps the two grids out of alignment.  The beam moves at
-    `velocity`.  Returns the same dict as two_cubes plus "dhat"."""
+    fixed; dhat = dhat_rel l (l the bounding-box diagonal).  The turn keeps the two grids out of
+    alignment.  The beam moves at `velocity`.  Returns the same dict as two_cubes plus "dhat"."""
     px, pt = tet_box(*plate, spacing=1.0)
     px = px.copy()
     hp = plate_side / (plate[0] - 1)
@@ -609,7 +609,7 @@ def beam_on_plate(beam=(41, 11, 11), plate=(65, 65, 4), beam_cell=0.025, plate_s
     bx[2] -= bx[2].min()
     lo = np.minimum(px.min(axis=1), bx.min(axis=1))
     hi = np.maximum(px.max(axis=1), bx.max(axis=1))
-    dhat = 1e-3 * float(np.linalg.norm(hi - lo))
+    dhat = dhat_rel * float(np.linalg.norm(hi - lo))
     bx[2] += gap_frac * dhat
     x, tets = _merge([(bx, bt), (px, pt)])
     n, nb = x.shape[1], bx.shape[1]
@@ -620,7 +620,7 @@ def beam_on_plate(beam=(41, 11, 11), plate=(65, 65, 4), beam_cell=0.025, plate_s
     tris, edges, verts = surface_lists(x, tets)
     l = float(np.linalg.norm(x.max(axis=1) - x.min(axis=1)))
     return {"x": x, "v": v, "tets": tets, "fixed": fixed, "tris": tris, "edges": edges, "verts": verts, "l": l,
-            "dhat": 1e-3 * l}
+            "dhat": dhat_rel * l}
 
 
 def stack_scene(rng, n_bodies, target_verts, dhat, size=0.2):

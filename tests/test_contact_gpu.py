@@ -165,6 +165,33 @@ def test_newton_step_matches_oracle(gipc):
     assert C.count_intersections(xg, sc0["tris"], sc0["edges"]) == 0
 
 
+def test_literal_two_cube_step_has_no_contact_and_matches_oracle(gipc):
+    """The two-cube scene as configured: the top cube 0.5 above the bottom one (gap 0.5, far beyond
+    dhat = 1e-3 l) falling at 2 m/s.  One step of dt = 0.01 moves it 0.02, so no contact arises and
+    the step is elasticity, inertia and gravity alone; it must match the oracle's step."""
+    sc0 = synth.two_cubes()
+    x0 = sc0["x"].copy()
+    assert x0[2, 125:].min() - x0[2, :125].max() == pytest.approx(0.5)
+    mu, lam = TT.snh_params(1e5, 0.4)
+    dh = 1e-3 * sc0["l"]
+    prm = dict(dhat=dh, kappa=1e3, dt=0.01, mu=mu, lam=lam, gravity=(0.0, 0.0, -9.81), eps_d=1e-2,
+               pcg_tol=1e-4, max_pcg=500, max_newton=8, max_ls=30)
+    osc = N.build_scene(dict(sc0, x=x0), prm, 1000.0)
+    xo, vo, so = N.newton_step(osc, x0, sc0["v"], prm)
+    assert max(so["contacts"]) == 0
+    scene = gipc.Scene(_dev(x0), _dev(sc0["tets"]), _surface(gipc, sc0), 1000.0, fixed=_dev(sc0["fixed"]),
+                       l=osc["l"])
+    x, v = _dev(x0), _dev(sc0["v"])
+    st = gipc.newton_step(scene, x, v, dt=prm["dt"], mu=mu, lam=lam, dhat=dh, kappa=prm["kappa"],
+                          gravity=prm["gravity"], eps_d=prm["eps_d"], pcg_tol=prm["pcg_tol"], max_pcg=prm["max_pcg"],
+                          max_newton=prm["max_newton"], max_ls=prm["max_ls"])
+    assert st["contacts"] == 0 and st["newton_iters"] == so["newton"]
+    xg = x.cpu().numpy()
+    scale = np.abs(xo - x0).max()
+    assert np.abs(xg - xo).max() <= 1e-9 * scale
+    assert np.abs(v.cpu().numpy() - vo).max() <= 1e-9 * np.abs(vo).max()
+
+
 def test_newton_step_mixed_and_rank1_converge_to_the_same_positions(gipc):
     """float32 Hessian storage / SpMV and the rank-1 stencil form change the search directions,
     not the minimiser (the gradient stays float64): run to a tight Newton tolerance, both land
