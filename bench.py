@@ -259,7 +259,6 @@ def run_gpu(args):
     # warm-up (also sizes every buffer)
     for _ in range(args.warmup):
         d, A, _ = gpu_step(g, dev, W, args, bufs, ctx)
-    nnzb = A["nnzb"]
     barrier()
 
     clocks = ClockSampler()
@@ -278,6 +277,7 @@ def run_gpu(args):
     prof = ctx.profile_read()
     ctx.profile_stop()
     clk = clocks.stop(local)
+    nnzb = A["nnzb"]
     ms = t0.elapsed_time(t1) / args.steps
     for m in all_marks:
         phase += [m[0].elapsed_time(m[1]), m[1].elapsed_time(m[2]), m[2].elapsed_time(m[3])]
@@ -327,6 +327,7 @@ def run_gpu(args):
             "e2e": {"value": job_rate(K_STENCILS, world, e2e_ms), "unit": "stencils/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
             "gpu_launches": launches_per_step(n, nnzb, prof["pcg_loop"][0] / args.steps) * args.steps,
+            "solver_phases_us": solver_phases(g, dev, W, args, bufs, ctx) if prof["pcg_loop"][0] else None,
             "clocks": clk,
         }
         if args.precision == "fp64" and args.hess_mode == "dense" and args.product == "native":
@@ -395,6 +396,19 @@ def solver_roofline(prof, precision, n, nnzb, kernel=None):
     return roof
 
 
+def solver_phases(g, dev, W, args, bufs, ctx):
+    """One more C1 step with the persistent solver's phase stamps on (outside the timed region):
+    the median length of each phase of an iteration, in microseconds."""
+    ctx.solver_trace(True)
+    try:
+        gpu_step(g, dev, W, args, bufs, ctx)
+        ph, its = ctx.solver_phases()
+    finally:
+        ctx.solver_trace(False)
+    ph["iterations_used"] = its
+    return ph
+
+
 def timed_steps(g, dev, W, args, bufs, ctx, steps):
     """`steps` C1 steps after two untimed ones: ms per step and the profiler's spans."""
     import torch
@@ -447,6 +461,7 @@ def run_mixed(g, dev, W, Wh, args, ctx):
             "rhs": torch.empty((3, Wh["n"]), dtype=torch.float64, device=dev)}
     ms, prof, d, A, marks = timed_steps(g, dev, W, a2, bufs, ctx, args.steps)
     roof = solver_roofline(prof, "mixed", Wh["n"], A["nnzb"])
+    phases = solver_phases(g, dev, W, a2, bufs, ctx) if prof["pcg_loop"][0] else None
     # end to end: host inputs in, direction out
     host = {k: torch.tensor(Wh[k]).pin_memory() for k in ("x", "st_own", "st_sheet", "mass")}
     out_h = torch.empty((3, Wh["n"]), dtype=torch.float64).pin_memory()
@@ -482,7 +497,7 @@ def run_mixed(g, dev, W, Wh, args, ctx):
             "e2e": {"value": K_STENCILS / (e2e_ms * 1e-3), "unit": "stencils/s", "ms_per_step": e2e_ms},
             "phases_ms": {"eval": marks[0].elapsed_time(marks[1]), "assemble": marks[1].elapsed_time(marks[2]),
                           "pcg": marks[2].elapsed_time(marks[3])},
-            "roofline": roof, "dtype": "f32+f64", "hess_mode": "rank1",
+            "roofline": roof, "solver_phases_us": phases, "dtype": "f32+f64", "hess_mode": "rank1",
             "block_rel_frobenius_err_vs_fp64": {"max": rel.max().item(), "mean": rel.mean().item(),
                                                 "blocks": int(act.sum().item()), "bar": 1e-4},
             "note": "same inputs and iteration count as the FP64 line (200 iterations at tolerance 0 on a "
@@ -586,14 +601,14 @@ def run_beam_forms(g, dev, steps):
     import torch
     import synth
 
-    sc = synth.beam_on_plate()
+    sc = synth.beam_on_plate(dhat_rel=BEAM_DHAT_REL)
     T = lambda a: torch.tensor(np.ascontiguousarray(a), device=dev)
     srf = g.Surface(T(sc["tris"]), T(sc["edges"]), T(sc["verts"]))
     scene = g.Scene(T(sc["x"]), T(sc["tets"]), srf, 1000.0, fixed=T(sc["fixed"]), l=sc["l"])
     mu, lam = g.snh_params(1e5, 0.4)
     prm = dict(dt=0.01, mu=mu, lam=lam, dhat=sc["dhat"], kappa=KAPPA, eps_d=1e-2, pcg_tol=1e-4,
                max_pcg=1000, max_newton=50)
-    out = {"workload": "tet beam 41x11x11 on a tet plate 65x65x4 (the differentiation scene)",
+    out = {"workload": f"tet beam 41x11x11 on a tet plate 65x65x4 (the differentiation scene), dhat = {BEAM_DHAT_REL} l",
            "vertices": int(sc["x"].shape[1]), "tets": int(sc["tets"].shape[1]), "eps_d": 1e-2, "pcg_tol": 1e-4}
     for prec, hm in NEWTON_FORMS:
         x, v = T(sc["x"]), T(sc["v"])
@@ -692,9 +707,15 @@ def run_batch_bench(g, dev, ctx, steps):
 
 # ----------------------------------------------------------------------------- differentiation
 DIFF_SEED = 20230814
+# dhat of the beam-on-plate scene relative to its bounding-box diagonal.  The scene is described by
+# its contact load (about 30k contact stencils); its meshes reach that at the start near 6.5e-3 l
+# (initial contacts: 1e-3 l: 5.1k, 5e-3 l: 14.7k, 7e-3 l: 36.6k), but there the exact Hessian of
+# the projected-Newton result is indefinite and its refinement stalls at 3.7e-6 l dt, so the
+# differentiated steps use 5e-3 l: 14.7k contacts at the start, about 6k through the steps.
+BEAM_DHAT_REL = 5e-3
 
 
-def run_diff_bench(g, dev, ctx, steps, fd_h=1e-6, eps_d=1e-5, eps_polish=1e-12):
+def run_diff_bench(g, dev, ctx, steps, fd_h=1e-6, eps_d=1e-5, eps_polish=1e-12, polish_iters=30, dhat_rel=None):
     """Tet beam (41 x 11 x 11 vertices, 1.0 x 0.25 x 0.25) turned 0.3 rad about z and resting on a
     tet plate (65 x 65 x 4 vertices, 2 x 2, bottom layer fixed), the beam moving at (0.05, 0, -0.1)
     m/s; FP64 dense steps (dt 0.01, E 1e5, nu 0.4, rho 1000, dhat 1e-3 l, kappa 1e3).
@@ -707,7 +728,7 @@ def run_diff_bench(g, dev, ctx, steps, fd_h=1e-6, eps_d=1e-5, eps_polish=1e-12):
     import torch
     import synth
 
-    sc = synth.beam_on_plate()
+    sc = synth.beam_on_plate(dhat_rel=dhat_rel or BEAM_DHAT_REL)
     T = lambda a: torch.tensor(np.ascontiguousarray(a), device=dev)
     srf = g.Surface(T(sc["tris"]), T(sc["edges"]), T(sc["verts"]))
     scene = g.Scene(T(sc["x"]), T(sc["tets"]), srf, 1000.0, fixed=T(sc["fixed"]), l=sc["l"])
@@ -715,7 +736,7 @@ def run_diff_bench(g, dev, ctx, steps, fd_h=1e-6, eps_d=1e-5, eps_polish=1e-12):
     dt, dhat = 0.01, sc["dhat"]
     prm = dict(dt=dt, mu=mu, lam=lam, dhat=dhat, kappa=KAPPA, eps_d=eps_d, pcg_tol=1e-10, max_pcg=5000,
                max_newton=100)
-    pol = dict(eps_polish=eps_polish, max_iters=10, pcg_tol=1e-24, max_pcg=20000)
+    pol = dict(eps_polish=eps_polish, max_iters=polish_iters, pcg_tol=1e-24, max_pcg=20000)
     adj_tol = 1e-22     # r.P^-1 r relative to its start: an 1e-11 smaller residual
     x0, v0 = T(sc["x"]), T(sc["v"])
     g.newton_step(scene, x0.clone(), v0.clone(), **prm)      # warm-up (scratch sizing)
@@ -783,7 +804,7 @@ def run_diff_bench(g, dev, ctx, steps, fd_h=1e-6, eps_d=1e-5, eps_polish=1e-12):
     mm, lm = g.snh_params(1e5 * (1 - fd_h), 0.4)
     fd_E = (L(v0, mp, lp) - L(v0, mm, lm)) / (np.log1p(fd_h) - np.log1p(-fd_h))
     newton_its = sum(s["newton_iters"] for s in stats)
-    return {"workload": "tet beam 41x11x11 (turned 0.3 rad) resting on a tet plate 65x65x4, beam at "
+    return {"workload": f"tet beam 41x11x11 (turned 0.3 rad) resting on a tet plate 65x65x4, dhat = {BEAM_DHAT_REL} l, beam at "
                         "(0.05, 0, -0.1) m/s; L = w . x_T, w seeded normal",
             "vertices": int(sc["x"].shape[1]), "tets": ntet, "surface_tris": int(sc["tris"].shape[1]),
             "surface_edges": int(sc["edges"].shape[1]), "dhat": dhat, "eps_d": eps_d, "eps_polish": eps_polish,

@@ -602,6 +602,33 @@ gipc_status gipc_profile_stop(gipc_ctx* ctx);
  * Errors: GIPC_ERR_INVALID_ARG. */
 gipc_status gipc_profile_sampling(gipc_ctx* ctx, int kind, int every);
 
+/* Phases of the persistent solver (tracing of gipc_pcg's single-system solve, which runs every
+ * iteration in one launch).  With tracing on, every persistent solve of this context records, for
+ * each of its first GIPC_TRACE_MAX_ITERS iterations, the earliest and the latest globaltimer stamp
+ * over its CTAs at each phase boundary.  gipc_profile_solver_phases synchronises the device, reads
+ * the stamps of the context's last traced solve and returns, per phase, the median over its
+ * iterations (the first two and the last left out; at least four iterations are needed) of the
+ * phase's length in microseconds, in the order of gipc_solver_phase, and the number of iterations
+ * used.  A phase runs from the first CTA's start (the last CTA's for the barriers) to the last
+ * CTA's end (the first CTA's exit for the barriers).  The stamps add a few global atomics per CTA
+ * and phase: leave tracing off when timing.  Errors: GIPC_ERR_INVALID_ARG (null context or output;
+ * no traced solve of four or more iterations), GIPC_ERR_CUDA. */
+typedef enum {
+    GIPC_PHASE_PRODUCT = 0,      /* q = S(H c) and the CTA's part of c . q              */
+    GIPC_PHASE_BARRIER_A = 1,    /* grid barrier after the product                      */
+    GIPC_PHASE_TOTAL_A = 2,      /* c . q summed from the parts, alpha formed           */
+    GIPC_PHASE_VECTOR = 3,       /* x, r update, s = P^-1 r and the CTA's part of r . s */
+    GIPC_PHASE_BARRIER_B = 4,    /* grid barrier after the vector phase                 */
+    GIPC_PHASE_TOTAL_B = 5,      /* r . s summed, beta and the stopping test formed     */
+    GIPC_PHASE_DIRECTION = 6,    /* c = S(s + beta c)                                   */
+    GIPC_PHASE_BARRIER_C = 7,    /* grid barrier after the direction                    */
+    GIPC_PHASE_ITERATION = 8,    /* one whole iteration                                 */
+    GIPC_PHASE_COUNT = 9
+} gipc_solver_phase;
+#define GIPC_TRACE_MAX_ITERS 1024
+gipc_status gipc_profile_solver_trace(gipc_ctx* ctx, int enable);
+gipc_status gipc_profile_solver_phases(gipc_ctx* ctx, double* phase_us_h, int* iters_h);
+
 #ifdef __cplusplus
 }
 #endif

@@ -125,6 +125,18 @@ class Context:
         """Record one launch in `every` of the named kind (gipc_profile_sampling)."""
         _abi.call("gipc_profile_sampling", self._h, _abi.PROF_KINDS[kind], int(every))
 
+    def solver_trace(self, enable=True):
+        """Record the phase stamps of this context's persistent solves (gipc_profile_solver_trace)."""
+        _abi.call("gipc_profile_solver_trace", self._h, 1 if enable else 0)
+
+    def solver_phases(self):
+        """{phase: median microseconds} of the last traced persistent solve, and the iterations
+        used (gipc_profile_solver_phases)."""
+        out = (ctypes.c_double * len(_abi.SOLVER_PHASES))()
+        it = ctypes.c_int(0)
+        _abi.call("gipc_profile_solver_phases", self._h, out, ctypes.byref(it))
+        return dict(zip(_abi.SOLVER_PHASES, list(out))), it.value
+
     def close(self):
         if self._h:
             _abi.lib().gipc_destroy(self._h)

@@ -78,6 +78,9 @@ class KernelTime(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
 
 
+SOLVER_PHASES = ("product", "barrier_a", "total_a", "vector", "barrier_b", "total_b", "direction", "barrier_c",
+                 "iteration")
+
 PROF_KINDS = {"pcg_spmv": 0, "pcg_update": 1, "pcg_direction": 2, "asm_pattern": 3, "asm_values": 4,
               "contacts": 5, "ccd": 6, "elements": 7, "energy": 8, "pcg_loop": 9}
 
@@ -103,6 +106,8 @@ SIGNATURES = {
                         ctypes.POINTER(_INT), ctypes.POINTER(_D), _P]),
     "gipc_pcg_noalloc": (_INT, [ctypes.POINTER(Bsr), _P, _P, _P, ctypes.POINTER(PcgParams),
                                 ctypes.POINTER(_INT), ctypes.POINTER(_D), _P]),
+    "gipc_profile_solver_trace": (_INT, [_P, _INT]),
+    "gipc_profile_solver_phases": (_INT, [_P, ctypes.POINTER(_D), ctypes.POINTER(_INT)]),
     "gipc_find_contacts": (_INT, [_P, _P, _P, _I64, ctypes.POINTER(Surface), _D, _P, _P, _I64,
                                   ctypes.POINTER(_I64), _P]),
     "gipc_ccd_max_step": (_INT, [_P, _P, _P, _I64, ctypes.POINTER(Surface), _D, ctypes.POINTER(_D), _P]),

@@ -106,10 +106,12 @@ struct gipc_contact_cache {
 
 struct gipc_ctx {
     int device = 0;
-    static constexpr int kSlots = 64;   // assembly 0-8 and 61, pcg 9-15 and 40, contacts 16-19, 30-39, 45-46 and 59-60, time step 20-29, 41-44 and 47-48, derivatives 49-58
+    static constexpr int kSlots = 64;   // assembly 0-8 and 61, pcg 9-15, 40 and 62, contacts 16-19, 30-39, 45-46 and 59-60, time step 20-29, 41-44 and 47-48, derivatives 49-58
     gipc_scratch slot[kSlots];
     gipc_profiler prof;
     gipc_contact_cache ccache;   // filled and used by the time step only
+    bool solver_trace = false;   // persistent solves record phase stamps (gipc_profile_solver_trace)
+    int solver_trace_iters = 0;  // iterations of the last traced solve
     void release_all() {
         for (auto& s : slot) s.release();
         prof.release();

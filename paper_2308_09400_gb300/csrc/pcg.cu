@@ -59,7 +59,8 @@ constexpr int kUpdPerSm = 2;      // update kernel: resident CTAs per SM (persis
 constexpr int kFuseMaxTiles = 8;  // fused update / direction: tiles per CTA kept in shared memory
 constexpr int kDirEpt = 4;        // direction kernel: vector entries per thread
 
-enum PcgSlot { P_VEC = 9, P_PINV = 10, P_PART = 11, P_PERM = 12, P_VEC32 = 13, P_SELL = 14, P_SLICE = 15, P_SCENE = 40 };
+enum PcgSlot { P_VEC = 9, P_PINV = 10, P_PART = 11, P_PERM = 12, P_VEC32 = 13, P_SELL = 14, P_SLICE = 15, P_SCENE = 40,
+               P_TRACE = 62 };
 
 constexpr int kLenBuckets = 64;   // rows are ordered by min(blocks in row, 63), longest first
 constexpr int kPermChunk = 1024;  // rows per chunk of the stable bucket sort (rows stay in their chunk)
@@ -485,7 +486,12 @@ struct StageRing {
 // Pipeline per warp over the groups g of a slice: the copies of the next NS-1 groups are in flight
 // while group g is multiplied; with NS >= 3 the direction entries of group g+1 are also gathered
 // before group g is multiplied.
-template <typename VT, typename PT, int U, int W, int NS, bool COHERENT>
+// Slices of a warp: one per round over the whole grid's warps in snake order (above).  The
+// warps are numbered CTA-major (STRIDED = false: a CTA's warps take neighbouring slices) or
+// warp-major (STRIDED: warp w of CTA b is number w * gridDim.x + b, so every CTA samples the whole
+// matrix and the CTAs' totals even out: on the C1 system the busiest CTA carries 1.025 instead of
+// 1.046 times the mean, and the 319 warps with a single slice spread over the CTAs).
+template <typename VT, typename PT, int U, int W, int NS, bool COHERENT, bool STRIDED = false>
 __device__ __forceinline__ double spmv_slices(StageRing<VT, U, W, NS>& R, const int32_t* __restrict__ rowptr,
                                               const int64_t* __restrict__ slice_off, const int32_t* __restrict__ sell_col,
                                               const VT* __restrict__ sell_vals, const PT* cg, const double* c,
@@ -495,7 +501,8 @@ __device__ __forceinline__ double spmv_slices(StageRing<VT, U, W, NS>& R, const 
     constexpr bool kPrefetchGather = NS >= 3;
     const int lane = threadIdx.x & 31;
     const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t wid = STRIDED ? (int64_t)(threadIdx.x >> 5) * gridDim.x + blockIdx.x
+                                : ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     double d = 0.0;
     for (int64_t rnd = 0; rnd * warps < nsl && !timed_out; ++rnd) {
         const int64_t sl = rnd * warps + ((rnd & 1) ? warps - 1 - wid : wid);
@@ -1171,6 +1178,20 @@ __device__ __forceinline__ double grid_sum_lean(const double* part) {
     return s;
 }
 
+// Phase stamps of the persistent solver (tracing): thread 0 of every CTA folds the globaltimer at
+// boundary k of iteration it into the earliest (trace[(it * 9 + k)]) and the latest
+// (trace[kTraceMins + it * 9 + k]) stamp over the CTAs.  No-op when trace is null.
+constexpr int kTraceMarks = 9;
+constexpr int64_t kTraceMins = (int64_t)GIPC_TRACE_MAX_ITERS * kTraceMarks;
+__device__ __forceinline__ void phase_mark(unsigned long long* trace, int it, int k) {
+    if (trace && threadIdx.x == 0 && it < GIPC_TRACE_MAX_ITERS) {
+        unsigned long long now;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now)::"memory");
+        atomicMin(trace + it * kTraceMarks + k, now);
+        atomicMax(trace + kTraceMins + it * kTraceMarks + k, now);
+    }
+}
+
 // CTAs per SM the persistent solver is compiled for: two where two staging areas fit in shared
 // memory (the register budget then allows 64 per thread), else one.
 template <typename VT, int U, int NS>
@@ -1184,7 +1205,7 @@ pcg_loop_kernel(const int32_t* __restrict__ rowptr, const int64_t* __restrict__ 
                 const int32_t* __restrict__ sell_col, const VT* __restrict__ sell_vals, const PT* cg, double* x,
                 double* r, double* c, float* c32, fpair* c2, double* q, const double* __restrict__ fac,
                 const int32_t* __restrict__ perm, const uint8_t* __restrict__ fixed, int64_t n, int64_t nsl,
-                double* part_a, double* part_b, PcgScalars* S, int iters) {
+                double* part_a, double* part_b, PcgScalars* S, int iters, unsigned long long* trace) {
     using ST = FacT<MIX>;
     using CT = typename std::conditional<MIX, float, double>::type;   // the kept direction
     // The solver's scalars, formed by thread 0 and shared with the CTA (every CTA forms the same
@@ -1208,30 +1229,36 @@ pcg_loop_kernel(const int32_t* __restrict__ rowptr, const int64_t* __restrict__ 
     const int max_iter = S->max_iter, stop_indefinite = S->stop_indefinite;
     int it_total = S->iters, status = GIPC_OK;
     bool abort = false;
+    // the warp's slice of round 0 under the warp-major numbering (see spmv_slices)
+    const int64_t first_sl = (int64_t)(t >> 5) * gridDim.x + blockIdx.x;
     StageRing<VT, U, kLoopW, NS> R;
     R.init();
-    R.preissue(((int64_t)blockIdx.x * blockDim.x + t) >> 5, nsl, slice_off, sell_vals, sell_col);
+    R.preissue(first_sl, nsl, slice_off, sell_vals, sell_col);
     unsigned nbar = 0;
     auto sync = [&]() { return grid_sync(&S->bar_count, ++nbar * gridDim.x, &S->status); };
     for (int it = 0; it < iters; ++it) {
         // A: q = S(H c), parts of c . q
+        if (trace) __syncthreads();
+        phase_mark(trace, it, 0);
         bool timed_out = false;
-        const double d = spmv_slices<VT, PT, U, kLoopW, NS, true>(R, rowptr, slice_off, sell_col, sell_vals, cg, c,
-                                                                  perm, q, fixed, n, nsl, timed_out);
+        const double d = spmv_slices<VT, PT, U, kLoopW, NS, true, true>(R, rowptr, slice_off, sell_col, sell_vals, cg,
+                                                                        c, perm, q, fixed, n, nsl, timed_out);
         if (timed_out) {
             R.drain_all();
             if ((t & 31) == 0) atomicExch(&S->status, GIPC_ERR_TIMEOUT);
         } else {
-            R.preissue(((int64_t)blockIdx.x * blockDim.x + t) >> 5, nsl, slice_off, sell_vals, sell_col);
+            R.preissue(first_sl, nsl, slice_off, sell_vals, sell_col);
         }
         {
             const double bs = cta_sum_lean(d, red);
             if (t == 0) part_a[blockIdx.x] = bs;
         }
+        phase_mark(trace, it, 1);
         if (!sync()) {
             abort = true;
             break;
         }
+        phase_mark(trace, it, 2);
         {
             const double pq = grid_sum_lean(part_a);
             if (t == 0) {
@@ -1241,6 +1268,7 @@ pcg_loop_kernel(const int32_t* __restrict__ rowptr, const int64_t* __restrict__ 
             }
         }
         __syncthreads();
+        phase_mark(trace, it, 3);
         if (sh_stop == 2) {
             status = GIPC_ERR_INDEFINITE;
             break;
@@ -1279,10 +1307,12 @@ pcg_loop_kernel(const int32_t* __restrict__ rowptr, const int64_t* __restrict__ 
             const double bs = cta_sum_lean(d2, red);
             if (t == 0) part_b[blockIdx.x] = bs;
         }
+        phase_mark(trace, it, 4);
         if (!sync()) {
             abort = true;
             break;
         }
+        phase_mark(trace, it, 5);
         it_total += 1;
         {
             const double dn = grid_sum_lean(part_b);
@@ -1297,6 +1327,7 @@ pcg_loop_kernel(const int32_t* __restrict__ rowptr, const int64_t* __restrict__ 
             }
         }
         __syncthreads();
+        phase_mark(trace, it, 6);
         if (sh_stop) {
             if (sh_stop == 3) status = GIPC_ERR_NONFINITE;
             break;
@@ -1323,10 +1354,13 @@ pcg_loop_kernel(const int32_t* __restrict__ rowptr, const int64_t* __restrict__ 
                 }
             }
         }
+        if (trace) __syncthreads();
+        phase_mark(trace, it, 7);
         if (!sync()) {
             abort = true;
             break;
         }
+        phase_mark(trace, it, 8);
     }
     R.drain();   // copies staged for a product that will not run
     __syncthreads();
@@ -1804,8 +1838,17 @@ gipc_status pcg_impl(gipc_ctx* ctx, const gipc_bsr* A, const double* rhs, double
             fn = (const void*)pcg_loop_kernel<float, float, kU32, kNS32, true>;
             cg = c32;
         }
+        unsigned long long* trace = nullptr;
+        if (ctx->solver_trace) {   // earliest stamps start at the largest value, latest at zero
+            const size_t half = sizeof(unsigned long long) * (size_t)kTraceMins;
+            if ((s = ctx->slot[P_TRACE].reserve(2 * half)) != GIPC_OK) return s;
+            trace = ctx->slot[P_TRACE].as<unsigned long long>();
+            if (cudaMemsetAsync(trace, 0xff, half, st) != cudaSuccess ||
+                cudaMemsetAsync(trace + kTraceMins, 0, half, st) != cudaSuccess)
+                return check_launch("gipc_pcg: trace reset");
+        }
         void* args[] = {&rp, &slice_off, &sell_col, &sell_vals, &cg, &xv, &r, &c, &c32, &c2, &q, &pinv, &perm,
-                        &fixed_arg, &n_arg, &nsl_arg, &part, &part_b, &S, &iters_arg};
+                        &fixed_arg, &n_arg, &nsl_arg, &part, &part_b, &S, &iters_arg, &trace};
         ctx->prof.start(GIPC_PROF_PCG_LOOP, st);
         if (cudaLaunchCooperativeKernel(fn, dim3(loop.grid), dim3(kLoopT), args, loop.smem, st) != cudaSuccess)
             return check_launch("gipc_pcg: persistent solver");
@@ -1895,6 +1938,7 @@ gipc_status pcg_impl(gipc_ctx* ctx, const gipc_bsr* A, const double* rhs, double
     if (cudaStreamSynchronize(st) != cudaSuccess) return check_launch("gipc_pcg: final sync");
     if (iters_out_h) *iters_out_h = hs.iters;
     if (rel_out_h) *rel_out_h = hs.delta0 > 0.0 ? hs.delta_new / hs.delta0 : 0.0;
+    if (loop.ok && ctx->solver_trace) ctx->solver_trace_iters = hs.iters;
     if (hs.status == GIPC_ERR_NONFINITE) return fail(GIPC_ERR_NONFINITE, "gipc_pcg: non-finite residual");
     if (hs.status == GIPC_ERR_INDEFINITE)
         return fail(GIPC_ERR_INDEFINITE, "gipc_pcg: c . H c <= 0 after %d iterations (H not positive definite)", hs.iters);
@@ -1909,6 +1953,54 @@ extern "C" gipc_status gipc_pcg(gipc_ctx* ctx, const gipc_bsr* A, const double* 
                                 double* rel_out_h, void* stream) {
     return gipc::pcg_impl(ctx, A, rhs, x, fixed, prm, iters_out_h, rel_out_h, (cudaStream_t)stream, nullptr, 1, nullptr,
                           nullptr);
+}
+
+extern "C" gipc_status gipc_profile_solver_trace(gipc_ctx* ctx, int enable) {
+    if (!ctx) return gipc::fail(GIPC_ERR_INVALID_ARG, "gipc_profile_solver_trace: null context");
+    ctx->solver_trace = enable != 0;
+    ctx->solver_trace_iters = 0;
+    return GIPC_OK;
+}
+
+extern "C" gipc_status gipc_profile_solver_phases(gipc_ctx* ctx, double* phase_us_h, int* iters_h) {
+    using namespace gipc;
+    if (!ctx || !phase_us_h) return fail(GIPC_ERR_INVALID_ARG, "gipc_profile_solver_phases: null argument");
+    const int iters = std::min(ctx->solver_trace_iters, (int)GIPC_TRACE_MAX_ITERS);
+    if (iters < 4 || !ctx->slot[P_TRACE].ptr)
+        return fail(GIPC_ERR_INVALID_ARG, "gipc_profile_solver_phases: no traced solve of four or more iterations");
+    std::vector<unsigned long long> h(2 * (size_t)kTraceMins);
+    if (cudaDeviceSynchronize() != cudaSuccess ||
+        cudaMemcpy(h.data(), ctx->slot[P_TRACE].ptr, sizeof(unsigned long long) * h.size(), cudaMemcpyDeviceToHost) !=
+            cudaSuccess)
+        return check_launch("gipc_profile_solver_phases");
+    auto mn = [&](int it, int k) { return (double)h[(size_t)it * kTraceMarks + k]; };
+    auto mx = [&](int it, int k) { return (double)h[(size_t)kTraceMins + (size_t)it * kTraceMarks + k]; };
+    // phase p runs from boundary a (first CTA, or last CTA for a barrier) to boundary b (last CTA, or
+    // first CTA for a barrier); iterations 2 .. iters-2 (each has a successor)
+    std::vector<double> v;
+    for (int p = 0; p < GIPC_PHASE_COUNT; ++p) {
+        v.clear();
+        for (int it = 2; it < iters - 1; ++it) {
+            double len;
+            switch (p) {
+                case GIPC_PHASE_PRODUCT: len = mx(it, 1) - mn(it, 0); break;
+                case GIPC_PHASE_BARRIER_A: len = mn(it, 2) - mx(it, 1); break;
+                case GIPC_PHASE_TOTAL_A: len = mx(it, 3) - mn(it, 2); break;
+                case GIPC_PHASE_VECTOR: len = mx(it, 4) - mn(it, 3); break;
+                case GIPC_PHASE_BARRIER_B: len = mn(it, 5) - mx(it, 4); break;
+                case GIPC_PHASE_TOTAL_B: len = mx(it, 6) - mn(it, 5); break;
+                case GIPC_PHASE_DIRECTION: len = mx(it, 7) - mn(it, 6); break;
+                case GIPC_PHASE_BARRIER_C: len = mn(it, 8) - mx(it, 7); break;
+                default: len = mn(it + 1, 0) - mn(it, 0); break;
+            }
+            v.push_back(len * 1e-3);   // ns -> us
+        }
+        std::sort(v.begin(), v.end());
+        const size_t m = v.size();
+        phase_us_h[p] = m % 2 ? v[m / 2] : 0.5 * (v[m / 2 - 1] + v[m / 2]);
+    }
+    if (iters_h) *iters_h = iters - 3;
+    return GIPC_OK;
 }
 
 // ------------------------------------------------------------------------------------------

@@ -406,33 +406,49 @@ __device__ __forceinline__ bool eval_one(const double* __restrict__ x, int64_t n
     return true;
 }
 
-// Writes m staged stencils' 144-entry blocks (element-major 3x3 sub-blocks) as one contiguous run,
-// two entries per lane per store.  Stencil e of the stage holds t = lam w (12 values) then w (12
-// values) at e * kStageStride (an odd stride, so the lanes' staging writes fall in distinct
-// banks); entry (p, q) of its block is t_P w_Q with P = max(p, q), Q = min(p, q) -- the product
-// the per-stencil form computes.  Sub-blocks outside a stencil's 3s x 3s block are not written
-// (a stored pair that straddles the edge of the block writes a zero beside it).
+// Writes the blocks of m staged stencils (element-major 3x3 sub-blocks) with coalesced stores.
+// Stencil e of the stage holds t = lam w (12 values) then w (12 values) at e * kStageStride (an
+// odd stride, so the lanes' staging writes fall in distinct banks); entry (p, q) of its block is
+// t_P w_Q with P = max(p, q), Q = min(p, q) -- the product the per-stencil form computes.  Only
+// the sub-block rows and columns below smax (the largest stencil of the warp, in vertices) are
+// visited: for each stencil, block rows a < smax are runs of smax * 9 entries at a * 36.  Entries
+// outside a stencil's own 3s x 3s block are not written, except that a stored pair that straddles
+// the edge of the block writes a zero beside it (pairs are used when the runs have even length).
 constexpr int kStageStride = 25;
+
 template <typename HT>
+__device__ __forceinline__ HT staged_entry(const HT* stage, const int* n3s, int e, int idx, bool& used) {
+    const int b16 = idx / 9, w9 = idx - 9 * b16;
+    const int p = 3 * (b16 >> 2) + w9 / 3, q = 3 * (b16 & 3) + w9 % 3;
+    const int P = p > q ? p : q, Q = p > q ? q : p;
+    const bool in = P < n3s[e];
+    used |= in;
+    return in ? stage[e * kStageStride + P] * stage[e * kStageStride + 12 + Q] : HT(0);
+}
+
+template <typename HT, int SMAX>
 __device__ __forceinline__ void write_staged_blocks(HT* out, int m, const HT* stage, const int* n3s, int lane) {
-    for (int wd = 2 * lane; wd < m * 144; wd += 64) {
-        HT v2[2];
-        bool used = false;
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-            const int ww = wd + u;
-            const int e = ww / 144, idx = ww - 144 * e;
-            const int b16 = idx / 9, w9 = idx - 9 * b16;
-            const int p = 3 * (b16 >> 2) + w9 / 3, q = 3 * (b16 & 3) + w9 % 3;
-            const int P = p > q ? p : q, Q = p > q ? q : p;
-            used |= P < n3s[e];
-            v2[u] = (P < n3s[e]) ? stage[e * kStageStride + P] * stage[e * kStageStride + 12 + Q] : HT(0);
+    constexpr int run = SMAX * 9, per = SMAX * run;   // entries per block row, per stencil
+    if constexpr ((run & 1) == 0) {
+        for (int wd = 2 * lane; wd < m * per; wd += 64) {
+            const int e = wd / per, r = wd - e * per, a = r / run;
+            const int idx = a * 36 + (r - a * run);
+            bool used = false;
+            const HT v0 = staged_entry(stage, n3s, e, idx, used);
+            const HT v1 = staged_entry(stage, n3s, e, idx + 1, used);
+            if (!used) continue;
+            HT* dst = out + (int64_t)e * 144 + idx;
+            if constexpr (std::is_same<HT, double>::value) *reinterpret_cast<double2*>(dst) = make_double2(v0, v1);
+            else *reinterpret_cast<float2*>(dst) = make_float2(v0, v1);
         }
-        if (!used) continue;   // both entries outside the stencil's 3s x 3s block: left as they are
-        if constexpr (std::is_same<HT, double>::value)
-            *reinterpret_cast<double2*>(out + wd) = make_double2(v2[0], v2[1]);
-        else
-            *reinterpret_cast<float2*>(out + wd) = make_float2(v2[0], v2[1]);
+    } else {
+        for (int wd = lane; wd < m * per; wd += 32) {
+            const int e = wd / per, r = wd - e * per, a = r / run;
+            const int idx = a * 36 + (r - a * run);
+            bool used = false;
+            const HT v = staged_entry(stage, n3s, e, idx, used);
+            if (used) out[(int64_t)e * 144 + idx] = v;
+        }
     }
 }
 
@@ -532,10 +548,16 @@ eval_stencils_kernel(const double* __restrict__ x, int64_t n, const int32_t* __r
             my[12 + j] = wj;
         }
         stage_n3[wi][lane] = valid ? n3 : 0;
+        const int smax = (int)__reduce_max_sync(0xffffffffu, (unsigned)(valid ? n3 : 0)) / 3;
         __syncwarp();
         const int64_t e0 = i - lane;
         const int64_t m = k - e0 < 32 ? k - e0 : 32;
-        if (m > 0) write_staged_blocks<HT>(hess + e0 * 144, (int)m, stage[wi], stage_n3[wi], lane);
+        if (m > 0) {
+            HT* out = hess + e0 * 144;
+            if (smax == 4) write_staged_blocks<HT, 4>(out, (int)m, stage[wi], stage_n3[wi], lane);
+            else if (smax == 3) write_staged_blocks<HT, 3>(out, (int)m, stage[wi], stage_n3[wi], lane);
+            else if (smax == 2) write_staged_blocks<HT, 2>(out, (int)m, stage[wi], stage_n3[wi], lane);
+        }
     }
 }
 

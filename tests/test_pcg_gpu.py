@@ -208,6 +208,28 @@ def test_full_size_system_matches_oracle_at_fixed_iterations(gipc):
             assert rel == pytest.approx(ref["rel"], rel=1e-8)
 
 
+def test_solver_phase_trace(gipc):
+    """The persistent solver's phase stamps: every phase non-negative, the phases of an iteration
+    adding up to about its length, and the trace changing nothing in the result."""
+    n = 20000
+    R, b, _, _ = spd_system(n, 60000, 15000, seed=48)
+    A, bt = _gpu_bsr(R, n), torch.tensor(b, device="cuda")
+    ctx = gipc.Context()
+    x0, _, _ = gipc.pcg(A, bt, rel_tol=0.0, max_iter=30, ctx=ctx)
+    with pytest.raises(gipc.GipcError, match="INVALID_ARG"):
+        ctx.solver_phases()
+    ctx.solver_trace(True)
+    x1, k, _ = gipc.pcg(A, bt, rel_tol=0.0, max_iter=30, ctx=ctx)
+    ph, its = ctx.solver_phases()
+    ctx.solver_trace(False)
+    assert k == 30 and its == 27
+    assert np.array_equal(x0.cpu().numpy(), x1.cpu().numpy())
+    assert all(v >= 0.0 for v in ph.values()), ph
+    parts = sum(v for key, v in ph.items() if key != "iteration")
+    assert 0.5 * ph["iteration"] <= parts <= 1.5 * ph["iteration"], ph
+    ctx.close()
+
+
 def test_indefinite_matrix_reported(gipc):
     """On request, a direction of negative curvature stops the solve with GIPC_ERR_INDEFINITE
     (the last iterate kept) instead of continuing with a negative step length; by default the
