@@ -853,6 +853,68 @@ gipc_status cache_disp(gipc_ctx* ctx, const double* x, const double* d, int64_t 
     return check_launch("contact cache");
 }
 
+// Margin tuner (see gipc_contact_cache): GPU time of the cached detections and CCD steps.  A span
+// is read back at the next cached call, after the stream synchronisations in between.
+void tuner_harvest(gipc_contact_cache& C) {
+    for (int k = 0; k < 2; ++k) {
+        if (!C.pending[k]) continue;
+        C.pending[k] = false;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, C.ev[k][0], C.ev[k][1]) == cudaSuccess)
+            C.epoch_ms += ms;
+        else
+            cudaGetLastError();   // not complete: the sample is dropped
+    }
+}
+
+// Records the spans of one cached call of kind k (0 detection, 1 CCD) on the stream.
+struct TunerSpan {
+    gipc_contact_cache& C;
+    int k;
+    cudaStream_t st;
+    bool on = false;
+    TunerSpan(gipc_contact_cache& c, int kind, cudaStream_t s, bool enable) : C(c), k(kind), st(s) {
+        if (!enable) return;
+        tuner_harvest(C);
+        for (auto& e : C.ev[k])
+            if (!e && cudaEventCreate(&e) != cudaSuccess) {
+                cudaGetLastError();
+                e = nullptr;
+                return;
+            }
+        on = cudaEventRecord(C.ev[k][0], st) == cudaSuccess;
+    }
+    ~TunerSpan() {
+        if (on) C.pending[k] = cudaEventRecord(C.ev[k][1], st) == cudaSuccess;
+    }
+};
+
+// Ends the epoch of the current candidates (`outran`: the surface moved past their margin) and
+// picks the level of the next build.
+void tuner_close_epoch(gipc_contact_cache& C, bool outran, double dhat, bool batched) {
+    if (C.tuned_dhat != dhat || C.tuned_batch != batched) {   // another scene: start over
+        for (int l = 0; l < C.kLevels; ++l) C.cost[l] = C.dets[l] = 0.0;
+        C.level = 0;
+        C.tuned_dhat = dhat;
+        C.tuned_batch = batched;
+        C.epoch_ms = 0.0;
+        C.epoch_dets = 0;
+        return;
+    }
+    if (C.epoch_dets > 0) {
+        const int b = C.built;
+        C.cost[b] = 0.5 * C.cost[b] + C.epoch_ms;
+        C.dets[b] = 0.5 * C.dets[b] + C.epoch_dets;
+    }
+    C.epoch_ms = 0.0;
+    C.epoch_dets = 0;
+    int best = C.built;
+    for (int l = 0; l < C.kLevels; ++l)
+        if (C.dets[l] > 0.0 && (C.dets[best] <= 0.0 || C.cost[l] / C.dets[l] < C.cost[best] / C.dets[best])) best = l;
+    // widen into an untried level only from the best one, and only when its margin was outrun
+    C.level = (outran && best == C.built && C.built + 1 < C.kLevels && C.dets[C.built + 1] <= 0.0) ? C.built + 1 : best;
+}
+
 }  // namespace
 
 // Internal entry points shared with the time-step driver (newton.cu).
@@ -874,13 +936,25 @@ gipc_status find_contacts_impl(gipc_ctx* ctx, const double* x, const double* res
     // cached candidates: valid while no surface vertex has moved more than the margin since they
     // were collected (boxes padded by dhat + 2 margin); the classification below decides exactly
     const bool use_cache = cached;
-    const double margin = 0.5 * dhat;
-    bool hit = false;
+    gipc_contact_cache& CC = ctx->ccache;
+    TunerSpan tspan(CC, 0, st, use_cache);
+    bool hit = false, outran = false;
     if (use_cache && cache_matches(ctx, n, srf, dhat, vscene, nscenes)) {
         double delta = 0.0, dm = 0.0;
         if ((s = cache_disp(ctx, x, nullptr, n, srf, &delta, &dm, st)) != GIPC_OK) return s;
-        hit = delta * (1.0 + 1e-9) <= ctx->ccache.margin;
+        hit = delta * (1.0 + 1e-9) <= CC.margin;
+        outran = !hit;
     }
+    if (use_cache) {
+        if (hit) {
+            ++CC.epoch_dets;
+        } else {
+            tuner_close_epoch(CC, outran, dhat, vscene != nullptr);
+            CC.built = CC.level;
+            CC.epoch_dets = 1;
+        }
+    }
+    const double margin = CC.kMargin[use_cache ? CC.built : 0] * dhat;
     PairList L{};
     int64_t npt = 0, np = 0;
     if (hit) {
@@ -977,6 +1051,7 @@ gipc_status ccd_impl(gipc_ctx* ctx, const double* x, const double* d, int64_t n,
     const int ns = vscene ? nscenes : 1;
     fill_kernel<<<nblk(ns, 256), 256, 0, st>>>(amin_d, ns, 1.0);
     unsigned long long* amin = reinterpret_cast<unsigned long long*>(amin_d);
+    TunerSpan tspan(ctx->ccache, 1, st, cached);
     if (cached && cache_matches(ctx, n, srf, ctx->ccache.dhat, vscene, nscenes)) {
         double delta = 0.0, dm = 0.0;
         if ((s = cache_disp(ctx, x, d, n, srf, &delta, &dm, st)) != GIPC_OK) return s;

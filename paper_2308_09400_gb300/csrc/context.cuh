@@ -102,6 +102,33 @@ struct gipc_contact_cache {
     const int32_t* vscene = nullptr;         // batched scenes: the vertex -> scene map, and their count
     int nscenes = 1;
     double dhat = 0.0, margin = 0.0, pad = 0.0;
+
+    // Margin tuner.  A wider margin means fewer rebuilds but more candidates to classify and test,
+    // and which wins depends on the scene.  The detections between two builds form an epoch; its
+    // GPU time (detections and cached CCD steps, CUDA events on the stream) per detection is
+    // credited to the margin level it was built with.  A build picks the level with the lowest
+    // time per detection so far, after trying the next wider level once when the surface outran
+    // the margin.  Levels are kMargin[l] dhat.  The choice changes timing only: the contact sets
+    // and steps are those of a fresh broad phase whatever the margin.
+    static constexpr int kLevels = 4;
+    static constexpr double kMargin[kLevels] = {0.5, 1.0, 2.0, 4.0};
+    int level = 0;                                // level of the next build
+    int built = 0;                                // level of the current candidates
+    double cost[kLevels] = {}, dets[kLevels] = {};   // decayed GPU ms and detections per level
+    double epoch_ms = 0.0;
+    int epoch_dets = 0;
+    double tuned_dhat = -1.0;                     // scene key of the statistics (dhat, batched)
+    bool tuned_batch = false;
+    cudaEvent_t ev[2][2] = {};                    // [detection, CCD][start, stop]
+    bool pending[2] = {};
+    void release_events() {
+        for (auto& k : ev)
+            for (auto& e : k) {
+                if (e) cudaEventDestroy(e);
+                e = nullptr;
+            }
+        pending[0] = pending[1] = false;
+    }
 };
 
 struct gipc_ctx {
@@ -116,5 +143,6 @@ struct gipc_ctx {
         for (auto& s : slot) s.release();
         prof.release();
         ccache.valid = false;
+        ccache.release_events();
     }
 };
