@@ -696,12 +696,24 @@ def run_batch_bench(g, dev, ctx, steps):
         e1.record()
         torch.cuda.synchronize()
         ms_p = e0.elapsed_time(e1)
+        # the product's staging variant the run-time tuner chose per size class of the batch (the
+        # classes shrink as finished scenes are packed out)
+        tuning = []
+        for t in ctx.spmv_tunings():
+            if t["precision"] != prec:
+                continue
+            name = lambda v: f"U{v['U']}_W{v['W']}_NS{v['NS']}"
+            tuning.append({"size_class_log2_nnzb": t["size_class"],
+                           "chosen": name(t["variants"][t["chosen"]]) if t["chosen"] >= 0 else None,
+                           "mean_us": {name(v): round(v["mean_us"], 2) for v in t["variants"]},
+                           "samples": [v["samples"] for v in t["variants"]]})
         out[f"{prec}_{hm}"] = {"batched_ms_per_step": ms_b / steps, "batched_scene_iters_per_s": its / (ms_b * 1e-3),
                                "one_at_a_time_ms_per_step": ms_p / steps,
                                "one_at_a_time_scene_iters_per_s": its1 / (ms_p * 1e-3),
                                "scene_newton_iters": its, "scene_newton_iters_one_at_a_time": its1,
                                "scene_newton_iters_per_step": per_step, "speedup": ms_p / ms_b,
-                               "phase_ms_per_step": phases, "pcg_kernel_spans": pcg_spans}
+                               "phase_ms_per_step": phases, "pcg_kernel_spans": pcg_spans,
+                               "product_variant_tuning": tuning}
     return out
 
 

@@ -611,13 +611,14 @@ gipc_status gipc_profile_sampling(gipc_ctx* ctx, int kind, int every);
  * phase's length in microseconds, in the order of gipc_solver_phase, and the number of iterations
  * used.  A phase runs from the first CTA's start (the last CTA's for the barriers) to the last
  * CTA's end (the first CTA's exit for the barriers).  The stamps add a few global atomics per CTA
- * and phase: leave tracing off when timing.  Errors: GIPC_ERR_INVALID_ARG (null context or output;
+ * and phase: leave tracing off when timing.  The x update runs between a CTA's arrival at barrier
+ * B and its wait, so it counts to BARRIER_B.  Errors: GIPC_ERR_INVALID_ARG (null context or output;
  * no traced solve of four or more iterations), GIPC_ERR_CUDA. */
 typedef enum {
     GIPC_PHASE_PRODUCT = 0,      /* q = S(H c) and the CTA's part of c . q              */
     GIPC_PHASE_BARRIER_A = 1,    /* grid barrier after the product                      */
     GIPC_PHASE_TOTAL_A = 2,      /* c . q summed from the parts, alpha formed           */
-    GIPC_PHASE_VECTOR = 3,       /* x, r update, s = P^-1 r and the CTA's part of r . s */
+    GIPC_PHASE_VECTOR = 3,       /* r update, s = P^-1 r and the CTA's part of r . s    */
     GIPC_PHASE_BARRIER_B = 4,    /* grid barrier after the vector phase                 */
     GIPC_PHASE_TOTAL_B = 5,      /* r . s summed, beta and the stopping test formed     */
     GIPC_PHASE_DIRECTION = 6,    /* c = S(s + beta c)                                   */
@@ -628,6 +629,37 @@ typedef enum {
 #define GIPC_TRACE_MAX_ITERS 1024
 gipc_status gipc_profile_solver_trace(gipc_ctx* ctx, int enable);
 gipc_status gipc_profile_solver_phases(gipc_ctx* ctx, double* phase_us_h, int* iters_h);
+
+/* Run-time tuning of the batched solver's product (gipc_pcg over several scenes, and so
+ * gipc_newton_step_batch).  The product q = S(H c) streams the matrix in SELL-32 slices; how
+ * many block columns a warp stages per copy (U), how many warps share a CTA (W) and how many
+ * copies are in flight (NS) trade shared memory, occupancy and latency differently on different
+ * batches.  While tuning is on (the default), a context runs its first batched solves of each
+ * precision and size class floor(log2(nnzb)) with each of GIPC_SPMV_VARIANTS staging variants in
+ * turn, a whole chunk of iterations at a time (product and scene update, so the overlap of
+ * consecutive launches counts), timed by CUDA events on the stream; chunks after which the solve
+ * has ended are not counted.  Once every variant has GIPC_SPMV_TUNE_SAMPLES timed iterations the
+ * fastest per iteration is kept for that class.  The product of every row is formed in the same order whatever the variant, and
+ * the batched solver sums its dot products per scene itself, so results do not depend on the
+ * choice.  gipc_spmv_autotune(ctx, 0) fixes variant 0.  gipc_spmv_tunings copies up to `cap`
+ * classes the context has measured (precision, size class, chosen variant or -1 while measuring,
+ * each variant's U, W, NS, timed iterations and mean microseconds per iteration) to out_h and
+ * their count to count_h.
+ * Errors: GIPC_ERR_INVALID_ARG (null context; null out_h with cap > 0; null count_h). */
+#define GIPC_SPMV_VARIANTS 4
+#define GIPC_SPMV_TUNE_SAMPLES 32
+typedef struct {
+    int precision;                      /* GIPC_FP64 or GIPC_MIXED          */
+    int size_class;                     /* floor(log2(nnzb)) of the systems */
+    int chosen;                         /* variant in use; -1 while timing  */
+    int U[GIPC_SPMV_VARIANTS];          /* block columns per staged copy    */
+    int W[GIPC_SPMV_VARIANTS];          /* warps per CTA                    */
+    int NS[GIPC_SPMV_VARIANTS];         /* copies in flight per warp        */
+    int samples[GIPC_SPMV_VARIANTS];    /* timed iterations                 */
+    double mean_us[GIPC_SPMV_VARIANTS]; /* per iteration                    */
+} gipc_spmv_tuning;
+gipc_status gipc_spmv_autotune(gipc_ctx* ctx, int enable);
+gipc_status gipc_spmv_tunings(gipc_ctx* ctx, gipc_spmv_tuning* out_h, int cap, int* count_h);
 
 #ifdef __cplusplus
 }

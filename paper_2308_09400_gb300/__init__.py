@@ -137,6 +137,25 @@ class Context:
         _abi.call("gipc_profile_solver_phases", self._h, out, ctypes.byref(it))
         return dict(zip(_abi.SOLVER_PHASES, list(out))), it.value
 
+    def spmv_autotune(self, enable=True):
+        """Choose the batched product's staging variant at run time (gipc_spmv_autotune)."""
+        _abi.call("gipc_spmv_autotune", self._h, 1 if enable else 0)
+
+    def spmv_tunings(self):
+        """The batched product's staging choices so far, one dict per precision and size class
+        (gipc_spmv_tunings)."""
+        cnt = ctypes.c_int(0)
+        _abi.call("gipc_spmv_tunings", self._h, None, 0, ctypes.byref(cnt))
+        arr = (_abi.SpmvTuning * max(1, cnt.value))()
+        _abi.call("gipc_spmv_tunings", self._h, arr, cnt.value, ctypes.byref(cnt))
+        out = []
+        for t in arr[:cnt.value]:
+            out.append({"precision": "fp64" if t.precision == _abi.GIPC_FP64 else "mixed", "size_class": t.size_class,
+                        "chosen": t.chosen,
+                        "variants": [{"U": t.U[i], "W": t.W[i], "NS": t.NS[i], "samples": t.samples[i],
+                                      "mean_us": t.mean_us[i]} for i in range(_abi.SPMV_VARIANTS)]})
+        return out
+
     def close(self):
         if self._h:
             _abi.lib().gipc_destroy(self._h)

@@ -78,6 +78,16 @@ class KernelTime(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
 
 
+SPMV_VARIANTS = 4
+
+
+class SpmvTuning(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("size_class", ctypes.c_int), ("chosen", ctypes.c_int),
+                ("U", ctypes.c_int * SPMV_VARIANTS), ("W", ctypes.c_int * SPMV_VARIANTS),
+                ("NS", ctypes.c_int * SPMV_VARIANTS), ("samples", ctypes.c_int * SPMV_VARIANTS),
+                ("mean_us", ctypes.c_double * SPMV_VARIANTS)]
+
+
 SOLVER_PHASES = ("product", "barrier_a", "total_a", "vector", "barrier_b", "total_b", "direction", "barrier_c",
                  "iteration")
 
@@ -108,6 +118,8 @@ SIGNATURES = {
                                 ctypes.POINTER(_INT), ctypes.POINTER(_D), _P]),
     "gipc_profile_solver_trace": (_INT, [_P, _INT]),
     "gipc_profile_solver_phases": (_INT, [_P, ctypes.POINTER(_D), ctypes.POINTER(_INT)]),
+    "gipc_spmv_autotune": (_INT, [_P, _INT]),
+    "gipc_spmv_tunings": (_INT, [_P, _P, _INT, ctypes.POINTER(_INT)]),
     "gipc_find_contacts": (_INT, [_P, _P, _P, _I64, ctypes.POINTER(Surface), _D, _P, _P, _I64,
                                   ctypes.POINTER(_I64), _P]),
     "gipc_ccd_max_step": (_INT, [_P, _P, _P, _I64, ctypes.POINTER(Surface), _D, ctypes.POINTER(_D), _P]),

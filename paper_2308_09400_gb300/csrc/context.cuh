@@ -131,6 +131,14 @@ struct gipc_contact_cache {
     }
 };
 
+// Run-time choice of the batched product's staging variant for one (precision, size class).
+struct gipc_spmv_tune {
+    int prec = 0, size_class = 0, chosen = -1;
+    double sum_ms[GIPC_SPMV_VARIANTS] = {};
+    int cnt[GIPC_SPMV_VARIANTS] = {};
+};
+
+
 struct gipc_ctx {
     int device = 0;
     static constexpr int kSlots = 64;   // assembly 0-8 and 61, pcg 9-15, 40 and 62, contacts 16-19, 30-39, 45-46 and 59-60, time step 20-29, 41-44 and 47-48, derivatives 49-58
@@ -139,10 +147,17 @@ struct gipc_ctx {
     gipc_contact_cache ccache;   // filled and used by the time step only
     bool solver_trace = false;   // persistent solves record phase stamps (gipc_profile_solver_trace)
     int solver_trace_iters = 0;  // iterations of the last traced solve
+    bool spmv_autotune = true;   // batched product variant chosen at run time (gipc_spmv_autotune)
+    std::vector<gipc_spmv_tune> spmv_tunes;
+    cudaEvent_t spmv_ev[2] = {nullptr, nullptr};   // around one timed chunk of iterations
     void release_all() {
         for (auto& s : slot) s.release();
         prof.release();
         ccache.valid = false;
         ccache.release_events();
+        for (auto& e : spmv_ev) {
+            if (e) cudaEventDestroy(e);
+            e = nullptr;
+        }
     }
 };

@@ -679,6 +679,89 @@ void launch_spmv_tma(const int32_t* rowptr, const int64_t* slice_off, const int3
                        q, fixed, n, nsl, part, S);
 }
 
+// Staging variants of the batched product tried by the run-time tuner: (U, W, NS) per precision,
+// variant 0 the default of the single-system sweep above.  Every variant forms each row in the
+// same order, so they differ in time only.
+struct SpmvVariant {
+    int U, W, NS;
+};
+constexpr SpmvVariant kVar64[GIPC_SPMV_VARIANTS] = {{kU64, kW64, kNS64}, {1, 8, 2}, {2, 8, 2}, {1, 8, 3}};
+constexpr SpmvVariant kVar32[GIPC_SPMV_VARIANTS] = {{kU32, kW32, kNS32}, {1, 16, 2}, {2, 8, 2}, {4, 8, 2}};
+
+template <typename VT, typename PT>
+void launch_spmv_variant(int v, const int32_t* rowptr, const int64_t* slice_off, const int32_t* sell_col,
+                         const VT* sell_vals, const PT* cg, const double* c, const int32_t* perm, double* q,
+                         const uint8_t* fixed, int64_t n, int64_t nsl, double* part, PcgScalars* S, cudaStream_t st) {
+    constexpr bool d = std::is_same<VT, double>::value;
+    constexpr const SpmvVariant* T = d ? kVar64 : kVar32;
+#define GIPC_SPMV_CASE(i)                                                                                            \
+    case i:                                                                                                          \
+        launch_spmv_tma<VT, PT, T[i].U, T[i].W, T[i].NS>(rowptr, slice_off, sell_col, sell_vals, cg, c, perm, q, fixed, \
+                                                         n, nsl, part, S, st);                                       \
+        break;
+    switch (v) {
+        GIPC_SPMV_CASE(1)
+        GIPC_SPMV_CASE(2)
+        GIPC_SPMV_CASE(3)
+        default: GIPC_SPMV_CASE(0)
+    }
+#undef GIPC_SPMV_CASE
+}
+
+// The tuner's entry for a precision and a size class (created on first use).
+int spmv_tune_index(gipc_ctx* ctx, bool f64, int64_t nnzb) {
+    int cls = 0;
+    while (cls < 62 && (int64_t(2) << cls) <= nnzb) ++cls;
+    const int prec = f64 ? GIPC_FP64 : GIPC_MIXED;
+    for (size_t i = 0; i < ctx->spmv_tunes.size(); ++i)
+        if (ctx->spmv_tunes[i].prec == prec && ctx->spmv_tunes[i].size_class == cls) return (int)i;
+    gipc_spmv_tune t;
+    t.prec = prec;
+    t.size_class = cls;
+    ctx->spmv_tunes.push_back(t);
+    return (int)ctx->spmv_tunes.size() - 1;
+}
+
+// The variant of the next chunk: the chosen one, else the one with the fewest timed iterations.
+int spmv_tune_pick(const gipc_spmv_tune& t) {
+    if (t.chosen >= 0) return t.chosen;
+    int v = 0;
+    for (int i = 1; i < GIPC_SPMV_VARIANTS; ++i)
+        if (t.cnt[i] < t.cnt[v]) v = i;
+    return v;
+}
+
+// The context's event pair for timing a chunk (created on first use); false if unavailable.
+bool spmv_tune_events(gipc_ctx* ctx) {
+    for (auto& e : ctx->spmv_ev)
+        if (!e && cudaEventCreate(&e) != cudaSuccess) {
+            cudaGetLastError();
+            e = nullptr;
+            return false;
+        }
+    return true;
+}
+
+// After the synchronisation that ends a timed chunk of m iterations of variant v: add its time,
+// and choose once every variant has GIPC_SPMV_TUNE_SAMPLES timed iterations.
+void spmv_tune_add(gipc_ctx* ctx, int tune, int v, int m) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, ctx->spmv_ev[0], ctx->spmv_ev[1]) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    gipc_spmv_tune& t = ctx->spmv_tunes[tune];
+    if (t.chosen >= 0) return;
+    t.sum_ms[v] += ms;
+    t.cnt[v] += m;
+    for (int i = 0; i < GIPC_SPMV_VARIANTS; ++i)
+        if (t.cnt[i] < GIPC_SPMV_TUNE_SAMPLES) return;
+    int best = 0;
+    for (int i = 1; i < GIPC_SPMV_VARIANTS; ++i)
+        if (t.sum_ms[i] / t.cnt[i] < t.sum_ms[best] / t.cnt[best]) best = i;
+    t.chosen = best;
+}
+
 // q = S(H c); alpha = delta_new / (c . q)
 template <typename VT, typename PT>
 __global__ void __launch_bounds__(kPcgThreads)
@@ -1100,7 +1183,8 @@ pcg_update_direction_kernel(double* __restrict__ x, double* __restrict__ r, doub
 // barriers:
 //   A  q = S(H c) over the warp's SELL-32 slices (the product above) and the CTA's part of c . q;
 //   B  alpha = delta / (c . q), every CTA summing all the parts in the same fixed order (so every
-//      CTA holds the same alpha); x += alpha c; r -= alpha q; s = P^-1 r; the CTA's part of r . s;
+//      CTA holds the same alpha); r -= alpha q; s = P^-1 r; the CTA's part of r . s; x += alpha c
+//      between the CTA's arrival at the barrier and its wait (no other CTA reads x);
 //   C  delta_new, beta and the stopping test, identical in every CTA for the same reason;
 //      c = S(s + beta c).
 // Each thread owns up to kLoopKeep vertices in phases B and C and keeps their s and c in
@@ -1114,20 +1198,31 @@ constexpr int kLoopW = 16;             // warps per CTA (staging as in the separ
 constexpr int kLoopT = kLoopW * 32;    // threads per CTA
 constexpr int kLoopKeep = 2;           // vertices per thread in the vector phases
 
-// Grid barrier on a monotonic arrival counter (zeroed per solve): the k-th barrier of a launch
-// completes once k * gridDim.x arrivals are counted.  False, in every thread of the CTA alike,
-// when the wait runs out (then GIPC_ERR_TIMEOUT is recorded) or when some CTA has recorded a
-// timeout before.
-__device__ __forceinline__ bool grid_sync(unsigned* count, unsigned target, int* status) {
-    __shared__ int ok;
-    __syncthreads();
+// Grid barrier on a monotonic arrival counter (zeroed per solve), in two halves: thread 0 of
+// every CTA arrives (its fence makes the writes of the CTA that it has synchronised with visible
+// first), and the k-th barrier of a launch completes once k * gridDim.x arrivals are counted.
+// Work that no other CTA reads may run between the halves.  The wait is false, in every thread of
+// the CTA alike, when it runs out (then GIPC_ERR_TIMEOUT is recorded) or when some CTA has
+// recorded a timeout (a CTA that gave up never arrives, so the others see its record while they
+// wait).
+__device__ __forceinline__ void grid_arrive(unsigned* count) {
     if (threadIdx.x == 0) {
         __threadfence();
         atomicAdd(count, 1u);
+    }
+}
+__device__ __forceinline__ bool grid_wait(unsigned* count, unsigned target, int* status) {
+    __shared__ int ok;
+    if (threadIdx.x == 0) {
         ok = 1;
         volatile unsigned* vc = count;
+        volatile int* vs = status;
         const long long t0 = clock64();
         while (*vc < target) {
+            if (*vs == GIPC_ERR_TIMEOUT) {
+                ok = 0;
+                break;
+            }
             if (clock64() - t0 > kBarrierCycles) {
                 ok = 0;
                 atomicExch(status, GIPC_ERR_TIMEOUT);
@@ -1136,10 +1231,24 @@ __device__ __forceinline__ bool grid_sync(unsigned* count, unsigned target, int*
             __nanosleep(20);
         }
         __threadfence();
-        if (*(volatile int*)status == GIPC_ERR_TIMEOUT) ok = 0;
     }
     __syncthreads();
     return ok != 0;
+}
+__device__ __forceinline__ bool grid_sync(unsigned* count, unsigned target, int* status) {
+    __syncthreads();
+    grid_arrive(count);
+    return grid_wait(count, target, status);
+}
+
+// Pairwise sum of N (a power of two) values: log2 N dependent additions instead of N - 1.
+template <int N>
+__device__ __forceinline__ double tree_sum(double (&v)[N]) {
+#pragma unroll
+    for (int h = N / 2; h >= 1; h /= 2)
+#pragma unroll
+        for (int j = 0; j < h; ++j) v[j] += v[j + h];
+    return v[0];
 }
 
 // FP64 sums with few FP64 warp-instructions.  On this part the FP64 pipe takes 16 cycles per warp
@@ -1148,20 +1257,26 @@ __device__ __forceinline__ bool grid_sync(unsigned* count, unsigned target, int*
 // solver's scalars (alpha, beta, the stopping test) are formed by one lane and shared.
 //
 // Sum of the CTA's values (blockDim.x <= kLoopT), in a fixed order: every thread stores its value,
-// warp 0 adds them lane-strided and reduces across its lanes.  Valid in warp 0.
+// warp 0 adds them pairwise per lane (lane-strided) and reduces across its lanes.  Valid in warp 0.
 __device__ __forceinline__ double cta_sum_lean(double v, double* buf) {
     buf[threadIdx.x] = v;
     __syncthreads();
     double s = 0.0;
     if (threadIdx.x < 32) {
-        for (int i = threadIdx.x; i < (int)blockDim.x; i += 32) s += buf[i];
+        double w[kLoopW];
+#pragma unroll
+        for (int j = 0; j < kLoopW; ++j) {
+            const int i = (int)threadIdx.x + 32 * j;
+            w[j] = i < (int)blockDim.x ? buf[i] : 0.0;
+        }
+        s = tree_sum<kLoopW>(w);
         s = warp_sum(s);
     }
     return s;
 }
 
-// Sum of every CTA's part in index order (at most 16 x 32 parts), by warp 0 with all its loads in
-// flight at once.  Valid in warp 0.
+// Sum of every CTA's part (at most 16 x 32 parts) in a fixed order, by warp 0 with all its loads
+// in flight at once.  Valid in warp 0.
 __device__ __forceinline__ double grid_sum_lean(const double* part) {
     double s = 0.0;
     if (threadIdx.x < 32) {
@@ -1171,8 +1286,7 @@ __device__ __forceinline__ double grid_sum_lean(const double* part) {
             const int i = (int)threadIdx.x + 32 * j;
             v[j] = i < (int)gridDim.x ? __ldcg(part + i) : 0.0;
         }
-#pragma unroll
-        for (int j = 0; j < 16; ++j) s += v[j];
+        s = tree_sum<16>(v);
         s = warp_sum(s);
     }
     return s;
@@ -1223,6 +1337,7 @@ pcg_loop_kernel(const int32_t* __restrict__ rowptr, const int64_t* __restrict__ 
         sh_beta = S->beta;
         sh_alpha = S->alpha;
         sh_pq = S->pq;
+        sh_beta_f = (float)S->beta;
         sh_stop = 0;
     }
     const double tol = S->tol, delta0 = S->delta0;   // read by thread 0 only (below)
@@ -1231,6 +1346,7 @@ pcg_loop_kernel(const int32_t* __restrict__ rowptr, const int64_t* __restrict__ 
     bool abort = false;
     // the warp's slice of round 0 under the warp-major numbering (see spmv_slices)
     const int64_t first_sl = (int64_t)(t >> 5) * gridDim.x + blockIdx.x;
+    __syncthreads();   // the scalars above
     StageRing<VT, U, kLoopW, NS> R;
     R.init();
     R.preissue(first_sl, nsl, slice_off, sell_vals, sell_col);
@@ -1274,7 +1390,7 @@ pcg_loop_kernel(const int32_t* __restrict__ rowptr, const int64_t* __restrict__ 
             break;
         }
         const double alpha = sh_alpha;
-        // B: x += alpha c; r -= alpha q; s = P^-1 r; parts of r . s
+        // B: r -= alpha q; s = P^-1 r; parts of r . s; then x += alpha c while the barrier fills
         ST sk[kLoopKeep][3];
         CT ck[kLoopKeep][3];
         double d2 = 0.0;
@@ -1282,21 +1398,18 @@ pcg_loop_kernel(const int32_t* __restrict__ rowptr, const int64_t* __restrict__ 
         for (int j = 0; j < kLoopKeep; ++j) {
             const int64_t v = ((int64_t)j * gridDim.x + blockIdx.x) * kLoopT + t;
             if (v < n) {
-                double cv[3], qv[3], xv[3], rv[3];
+                double qv[3], rv[3];
                 ST F[6];
 #pragma unroll
                 for (int e = 0; e < 3; ++e) {
-                    cv[e] = c[3 * v + e];
                     qv[e] = q[3 * v + e];
-                    xv[e] = x[3 * v + e];
                     rv[e] = r[3 * v + e];
                     if constexpr (MIX) ck[j][e] = c32[3 * v + e];
-                    else ck[j][e] = cv[e];
+                    else ck[j][e] = c[3 * v + e];
                 }
                 load_factor_t<MIX>(fac, n, v, F);
 #pragma unroll
                 for (int e = 0; e < 3; ++e) {
-                    x[3 * v + e] = xv[e] + alpha * cv[e];
                     rv[e] = rv[e] - alpha * qv[e];
                     r[3 * v + e] = rv[e];
                 }
@@ -1304,11 +1417,26 @@ pcg_loop_kernel(const int32_t* __restrict__ rowptr, const int64_t* __restrict__ 
             }
         }
         {
+            // only the part is read by other CTAs: thread 0 arrives as soon as it is written
             const double bs = cta_sum_lean(d2, red);
             if (t == 0) part_b[blockIdx.x] = bs;
+            grid_arrive(&S->bar_count);
         }
         phase_mark(trace, it, 4);
-        if (!sync()) {
+#pragma unroll
+        for (int j = 0; j < kLoopKeep; ++j) {   // x is read by its owner only
+            const int64_t v = ((int64_t)j * gridDim.x + blockIdx.x) * kLoopT + t;
+            if (v < n) {
+#pragma unroll
+                for (int e = 0; e < 3; ++e) {
+                    // the mixed form reads the direction's float64 image (no conversion on the FP64 pipe)
+                    const double ce = MIX ? c[3 * v + e] : (double)ck[j][e];
+                    x[3 * v + e] = x[3 * v + e] + alpha * ce;
+                }
+            }
+        }
+        __syncthreads();
+        if (!grid_wait(&S->bar_count, ++nbar * gridDim.x, &S->status)) {
             abort = true;
             break;
         }
@@ -1857,19 +1985,27 @@ gipc_status pcg_impl(gipc_ctx* ctx, const gipc_bsr* A, const double* rhs, double
         launched = max_iter;
     }
     const int chunk = prm->check_every > 0 ? prm->check_every : (prm->rel_tol > 0.0 ? 16 : max_iter + 1);
+    // batched systems: the product's staging variant is chosen at run time (the scenes' dots are
+    // summed by the scene kernel, so the variant changes no result); single systems keep variant 0
+    // Variants are timed over whole chunks of iterations (product and scene step, with the overlap
+    // of consecutive launches), and only chunks after which the solve still runs count.
+    const int tune = (voff && !fp && ctx->spmv_autotune) ? spmv_tune_index(ctx, f64, A->nnzb) : -1;
     while (launched < max_iter) {
         const int m = (max_iter - launched) < chunk ? (max_iter - launched) : chunk;
+        const int var = tune >= 0 ? spmv_tune_pick(ctx->spmv_tunes[tune]) : 0;
+        const bool timed = tune >= 0 && ctx->spmv_tunes[tune].chosen < 0 && launched + m < max_iter &&
+                           spmv_tune_events(ctx) && cudaEventRecord(ctx->spmv_ev[0], st) == cudaSuccess;
         for (int it = 0; it < m; ++it) {
             ctx->prof.start(GIPC_PROF_PCG_SPMV, st);
             if (fp)
                 launch_spmv_tma<fpair, fpair, kUfp, kWfp, kNSfp>(A->rowptr, slice_off, sell_col, (const fpair*)sell_vals,
                                                                  c2, c, perm, q, fixed, n, nsl, part, S, st);
             else if (f64)
-                launch_spmv_tma<double, double, kU64, kW64, kNS64>(A->rowptr, slice_off, sell_col, (const double*)sell_vals,
-                                                                   c, c, perm, q, fixed, n, nsl, part, S, st);
+                launch_spmv_variant<double, double>(var, A->rowptr, slice_off, sell_col, (const double*)sell_vals, c, c,
+                                                    perm, q, fixed, n, nsl, part, S, st);
             else
-                launch_spmv_tma<float, float, kU32, kW32, kNS32>(A->rowptr, slice_off, sell_col, (const float*)sell_vals,
-                                                                 c32, c, perm, q, fixed, n, nsl, part, S, st);
+                launch_spmv_variant<float, float>(var, A->rowptr, slice_off, sell_col, (const float*)sell_vals, c32, c,
+                                                  perm, q, fixed, n, nsl, part, S, st);
             ctx->prof.stop(GIPC_PROF_PCG_SPMV, st);
             if (voff) {
                 ctx->prof.start(GIPC_PROF_PCG_UPDATE, st);
@@ -1904,10 +2040,12 @@ gipc_status pcg_impl(gipc_ctx* ctx, const gipc_bsr* A, const double* rhs, double
             ctx->prof.stop(GIPC_PROF_PCG_DIRECTION, st);
         }
         launched += m;
+        if (timed) cudaEventRecord(ctx->spmv_ev[1], st);
         if ((s = check_launch("gipc_pcg: iteration")) != GIPC_OK) return s;
         if (launched < max_iter) {
             cudaMemcpyAsync(&hs, S, sizeof(PcgScalars), cudaMemcpyDeviceToHost, st);
             if (cudaStreamSynchronize(st) != cudaSuccess) return check_launch("gipc_pcg: sync");
+            if (timed && !hs.done) spmv_tune_add(ctx, tune, var, m);
             if (hs.done) break;
         }
     }
@@ -1953,6 +2091,36 @@ extern "C" gipc_status gipc_pcg(gipc_ctx* ctx, const gipc_bsr* A, const double* 
                                 double* rel_out_h, void* stream) {
     return gipc::pcg_impl(ctx, A, rhs, x, fixed, prm, iters_out_h, rel_out_h, (cudaStream_t)stream, nullptr, 1, nullptr,
                           nullptr);
+}
+
+extern "C" gipc_status gipc_spmv_autotune(gipc_ctx* ctx, int enable) {
+    using namespace gipc;
+    if (!ctx) return fail(GIPC_ERR_INVALID_ARG, "gipc_spmv_autotune: null context");
+    ctx->spmv_autotune = enable != 0;
+    return GIPC_OK;
+}
+
+extern "C" gipc_status gipc_spmv_tunings(gipc_ctx* ctx, gipc_spmv_tuning* out_h, int cap, int* count_h) {
+    using namespace gipc;
+    if (!ctx || !count_h || (cap > 0 && !out_h)) return fail(GIPC_ERR_INVALID_ARG, "gipc_spmv_tunings: null argument");
+    const int m = std::min(cap, (int)ctx->spmv_tunes.size());
+    for (int k = 0; k < m; ++k) {
+        const gipc_spmv_tune& t = ctx->spmv_tunes[k];
+        const SpmvVariant* V = t.prec == GIPC_FP64 ? kVar64 : kVar32;
+        gipc_spmv_tuning& o = out_h[k];
+        o.precision = t.prec;
+        o.size_class = t.size_class;
+        o.chosen = t.chosen;
+        for (int i = 0; i < GIPC_SPMV_VARIANTS; ++i) {
+            o.U[i] = V[i].U;
+            o.W[i] = V[i].W;
+            o.NS[i] = V[i].NS;
+            o.samples[i] = t.cnt[i];
+            o.mean_us[i] = t.cnt[i] > 0 ? 1e3 * t.sum_ms[i] / t.cnt[i] : 0.0;
+        }
+    }
+    *count_h = (int)ctx->spmv_tunes.size();
+    return GIPC_OK;
 }
 
 extern "C" gipc_status gipc_profile_solver_trace(gipc_ctx* ctx, int enable) {

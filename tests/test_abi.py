@@ -64,7 +64,7 @@ def test_ctypes_struct_layouts_match_the_header(tmp_path):
                "gipc_elastic_params": _abi.ElasticParams, "gipc_pcg_params": _abi.PcgParams,
                "gipc_kernel_time": _abi.KernelTime, "gipc_surface": _abi.Surface, "gipc_scene": _abi.Scene,
                "gipc_step_params": _abi.StepParams, "gipc_step_stats": _abi.StepStats,
-               "gipc_scene_batch": _abi.SceneBatch}
+               "gipc_scene_batch": _abi.SceneBatch, "gipc_spmv_tuning": _abi.SpmvTuning}
     lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{os.path.join(ROOT, "include", "gipc.h")}"',
              'int main(void) {']
     for cname, py in structs.items():

@@ -164,3 +164,33 @@ def test_unordered_lists_are_rejected(gipc):
     v = torch.zeros_like(x)
     with pytest.raises(gipc.GipcError, match="ordered by scene"):
         gipc.newton_step_batch(b, x, v, dt=DT, mu=mu, lam=lam, dhat=dhat, kappa=KAPPA)
+
+
+@pytest.mark.parametrize("precision,hess_mode", [("fp64", "dense"), ("mixed", "rank1")])
+def test_product_variant_choice_changes_no_result(gipc, precision, hess_mode):
+    """The batched product's staging variant is chosen at run time from measured times; the
+    variants form every row in the same order and the scenes' dots are summed per scene, so the
+    choice changes time only: a batch stepped with the tuner on (every variant timed, the fastest
+    kept) and off (variant 0) gives bit-identical positions, velocities and statistics."""
+    scenes, dhat = _scenes(n=8, seed=3)
+    # a tight solver tolerance, so the solves run whole chunks of iterations to time
+    kw = dict(precision=precision, hess_mode=hess_mode, max_newton=12, pcg_tol=1e-10, max_pcg=400)
+    on, off = gipc.Context(), gipc.Context()
+    on.spmv_autotune(True)
+    off.spmv_autotune(False)
+    _, x1, v1, s1 = _batch(gipc, scenes, dhat, ctx=on, **kw)
+    _, x2, v2, s2 = _batch(gipc, scenes, dhat, ctx=off, **kw)
+    assert np.array_equal(x1, x2) and np.array_equal(v1, v2)
+    assert s1 == s2
+    tunings = on.spmv_tunings()
+    assert tunings and all(t["precision"] == precision for t in tunings)
+    timed = [v["samples"] for t in tunings for v in t["variants"]]
+    assert all(s >= 0 for s in timed)
+    # several variants ran and were timed
+    assert max(sum(v["samples"] > 0 for v in t["variants"]) for t in tunings) >= 2
+    for t in tunings:
+        if t["chosen"] >= 0:   # a choice is made only once every variant has its samples
+            assert all(v["samples"] >= 32 for v in t["variants"])
+            fastest = min(v["mean_us"] for v in t["variants"])
+            assert t["variants"][t["chosen"]]["mean_us"] <= fastest * (1 + 1e-12)
+    assert off.spmv_tunings() == []
