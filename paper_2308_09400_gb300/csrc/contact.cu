@@ -43,13 +43,15 @@ constexpr int kWarps = kThreads / 32;
 // context scratch slots: query counts (then cursors), query offsets, scalars, sort keys, candidate
 // pairs, pair codes; per grid (triangles,
 // edges): float64 target boxes, hash tables, per-target cell counts and their offsets
-enum ContactSlot { C_CNT = 16, C_QOFF = 17, C_MISC = 19, C_KEY = 37, C_PAIRS = 38, C_CODE = 39, C_CPAIRS = 59, C_CX = 60 };
+enum ContactSlot { C_CNT = 16, C_QOFF = 17, C_MISC = 19, C_KEY = 37, C_PAIRS = 38, C_CODE = 39, C_CPAIRS = 59, C_CX = 60,
+                   C_X32 = 63, C_LIST = 64 };
 constexpr int kGridSlots[2][5] = {{18, 30, 31, 32, 45}, {33, 34, 35, 36, 46}};
 // scalars in C_MISC: per grid g the largest cell count at 4g + 2; CCD minimum at 8, pair counter
 // at 9.  Per-scene extent sums, counts and inverse cell sizes live in the grid's last slot.
 constexpr int kMiscAmin = 8;
 constexpr int kMiscPairs = 9;
 constexpr int kMiscDisp = 10;   // cached candidates: max |x - x_b| at 10, max |d| at 11 (bit patterns)
+constexpr int kMiscList = 12;   // length of the prefilter's list (unsigned)
 
 struct V3 {
     double x, y, z;
@@ -468,11 +470,141 @@ scan_pairs_kernel(const double* __restrict__ x, const double* __restrict__ dx, i
 // Classify every candidate pair once: code = type | i << 2 | j << 4 (closest features) for a pair
 // closer than dhat, -1 otherwise; hits are counted per query (combined query index: surface
 // vertices first, then edges).
+// ------------------------------------------------------------- certified float32 prefilter
+// Most candidate pairs are not contacts: on the sphere-grid scene about 85% of the point-triangle
+// and edge-edge candidates are more than dhat apart, and classifying them costs the float64
+// closest-feature computation, whose branches leave half of each warp idle.  A float32 pass first
+// bounds each pair's distance from below, on float32 roundings of the float64 points, with
+// margins that cover that rounding and the float32 arithmetic.  A pair is dropped only when the
+// bound proves the float64 classification would find it farther than dhat (or, for the CCD, that
+// the additive CCD's first step would already pass t = 1), so every result stays bit-identical;
+// the rest are classified as before, densely, from a compacted list.
+//
+// The bound is certified only for well-shaped primitives: a triangle with |e0 x e1|^2 >= 0.02 a c
+// (a = |e0|^2, c = |e1|^2), an edge pair with |e1 x e2|^2 >= 0.02 a c.  There the float64
+// classification's region decisions err only within rounding of a region boundary, so the
+// distance it computes is the true distance to within rounding; near-degenerate triangles and
+// nearly parallel edges are always classified in float64.
+struct F3 {
+    float x, y, z;
+};
+__device__ __forceinline__ F3 ld3f(const float* __restrict__ X, int64_t n, int64_t i) {
+    return {X[i], X[n + i], X[2 * n + i]};
+}
+__device__ __forceinline__ F3 fsub(F3 a, F3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ __forceinline__ float fdot(F3 a, F3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ F3 fcross(F3 a, F3 b) {
+    return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+__device__ __forceinline__ float fabsmax(F3 a) { return fmaxf(fabsf(a.x), fmaxf(fabsf(a.y), fabsf(a.z))); }
+
+// Lower bound on the distance between the pair's primitives (point X[0] and triangle X[1..3], or
+// edges X[0..1] and X[2..3]), less the rounding margins; -1 where not certified.
+//   point-triangle: the point's offset from the triangle's plane, h, and its largest signed
+//   distance past an edge within the plane, s (outward normal of edge k: d_k x n), give
+//   dist^2 >= h^2 + max(s, 0)^2;
+//   edge-edge: the line-line distance h (along n = e1 x e2) and the in-plane gaps of each edge
+//   from the other's line (along e1 x n and e2 x n) give dist^2 >= h^2 + max(g1, g2, 0)^2.
+// Margins: rounding the points to float32 moves each by at most sqrt(3) 2^-24 max|x| (4e-7 max|x|
+// covers both primitives); the float32 arithmetic errs by far less than 1e-4 of the pair's extent
+// for the shapes certified (amplification below sqrt(a c / |n|^2) < 8).
+__device__ __forceinline__ float pair_lb32(const F3 (&X)[4], bool pt) {
+    float amax = 0.f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) amax = fmaxf(amax, fabsmax(X[k]));
+    float h, side = 0.f, ext;
+    if (pt) {
+        const F3 e0 = fsub(X[2], X[1]), e1 = fsub(X[3], X[1]), v = fsub(X[0], X[1]);
+        const float a = fdot(e0, e0), c = fdot(e1, e1);
+        const F3 nr = fcross(e0, e1);
+        const float nn = fdot(nr, nr);
+        if (!(nn >= 0.02f * a * c) || !(nn > 0.f)) return -1.f;
+        const float ln = sqrtf(nn);
+        h = fabsf(fdot(v, nr)) / ln;
+        const F3 d[3] = {e0, fsub(X[3], X[2]), fsub(X[1], X[3])};
+        const F3 w[3] = {v, fsub(X[0], X[2]), fsub(X[0], X[3])};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const F3 m = fcross(d[k], nr);
+            side = fmaxf(side, fdot(w[k], m) / (sqrtf(fdot(d[k], d[k])) * ln));
+        }
+        ext = sqrtf(fmaxf(fmaxf(a, c), fdot(v, v)));
+    } else {
+        const F3 e1 = fsub(X[1], X[0]), e2 = fsub(X[3], X[2]), w = fsub(X[0], X[2]);
+        const float a = fdot(e1, e1), c = fdot(e2, e2);
+        const F3 nr = fcross(e1, e2);
+        const float nn = fdot(nr, nr);
+        if (!(nn >= 0.02f * a * c) || !(nn > 0.f)) return -1.f;
+        const float ln = sqrtf(nn);
+        h = fabsf(fdot(w, nr)) / ln;
+        const F3 u1 = fcross(e1, nr), u2 = fcross(e2, nr);
+        // edge b relative to the line of edge a, edge a relative to the line of edge b
+        const float pb0 = -fdot(w, u1), pb1 = fdot(fsub(X[3], X[0]), u1);
+        const float qa0 = fdot(w, u2), qa1 = fdot(fsub(X[1], X[2]), u2);
+        const float g1 = fmaxf(fminf(pb0, pb1), -fmaxf(pb0, pb1)) / (sqrtf(a) * ln);
+        const float g2 = fmaxf(fminf(qa0, qa1), -fmaxf(qa0, qa1)) / (sqrtf(c) * ln);
+        side = fmaxf(g1, g2);
+        ext = sqrtf(fmaxf(fmaxf(a, c), fdot(w, w)));
+    }
+    side = fmaxf(side, 0.f);
+    const float lb = sqrtf(h * h + side * side) - 4e-7f * amax - 1e-4f * ext;
+    return lb == lb ? lb : -1.f;   // (a NaN certifies nothing)
+}
+
+// Appends r to the list when keep (one atomic per warp; the list's order does not matter).
+__device__ __forceinline__ void append_kept(bool keep, int64_t r, int32_t* __restrict__ list, unsigned* __restrict__ count) {
+    const unsigned mask = __ballot_sync(0xffffffffu, keep);
+    const int lane = threadIdx.x & 31;
+    unsigned base = 0;
+    if (lane == 0 && mask) base = atomicAdd(count, (unsigned)__popc(mask));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (keep) list[base + __popc(mask & ((1u << lane) - 1u))] = (int32_t)r;
+}
+
+__device__ __forceinline__ void pair_ids(const Surf& S, int32_t q, int32_t t, bool pt, int32_t (&ids)[4]) {
+    if (pt) {
+        ids[0] = S.verts[q]; ids[1] = S.tris[t]; ids[2] = S.tris[S.ntri + t]; ids[3] = S.tris[2 * S.ntri + t];
+    } else {
+        ids[0] = S.edges[q]; ids[1] = S.edges[S.nedge + q]; ids[2] = S.edges[t]; ids[3] = S.edges[S.nedge + t];
+    }
+}
+
+__global__ void to_f32_kernel(const double* __restrict__ a, int64_t m, float* __restrict__ b) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) b[i] = (float)a[i];
+}
+
+// Classification prefilter: pairs proven farther than thr (dhat plus a relative margin, rounded
+// up) get code -1; the others are listed for classify_pairs_kernel.  Launched with whole warps.
+__global__ void prefilter_pairs_kernel(const float* __restrict__ x32, int64_t n, Surf S, const int32_t* __restrict__ pq,
+                                       const int32_t* __restrict__ ptg, int64_t npt, int64_t np, float thr,
+                                       int32_t* __restrict__ code, int32_t* __restrict__ list, unsigned* __restrict__ count) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool keep = false;
+    if (r < np) {
+        int32_t ids[4];
+        pair_ids(S, pq[r], ptg[r], r < npt, ids);
+        F3 X[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) X[k] = ld3f(x32, n, ids[k]);
+        keep = !(pair_lb32(X, r < npt) > thr);
+        if (!keep) code[r] = -1;
+    }
+    append_kept(keep, r, list, count);
+}
+
+// Classifies the listed pairs (list[0 .. *count)), or every pair when list is null.
 __global__ void classify_pairs_kernel(const double* __restrict__ x, int64_t n, Surf S, const int32_t* __restrict__ pq,
                                       const int32_t* __restrict__ pt, int64_t npt, int64_t np, double dh2,
-                                      int32_t* __restrict__ code, int32_t* __restrict__ cnt) {
-    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= np) return;
+                                      int32_t* __restrict__ code, int32_t* __restrict__ cnt,
+                                      const int32_t* __restrict__ list, const unsigned* __restrict__ count) {
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (list) {
+        if (r >= (int64_t)*count) return;
+        r = list[r];
+    } else if (r >= np) {
+        return;
+    }
     const int32_t q = pq[r], t = pt[r];
     double d2;
     int type, i = 0, j = 0;
@@ -652,21 +784,61 @@ __device__ __forceinline__ void swept_box(const V3* X, const V3* P, int a0, int 
 // ACCD of every candidate pair (point-triangle pairs first); the step is the minimum over pairs.
 // With box_filter the pairs come from a superset (the time step's cached candidates) and only
 // those whose swept boxes overlap -- the pairs the swept grid would propose -- are tested.
+// CCD prefilter: a pair whose certified distance bound lb (float32 prefilter above) satisfies
+// (1 - s) lb > lp, lp the additive CCD's motion bound (recomputed in float32 with a margin), would
+// leave the CCD at its first step with t = 1: it cannot lower the step and is dropped.  The others
+// are listed for ccd_pairs_kernel.  omss = 1 - s rounded down.  Launched with whole warps.
+__global__ void prefilter_ccd_kernel(const float* __restrict__ x32, const float* __restrict__ d32, int64_t n, Surf S,
+                                     const int32_t* __restrict__ pq, const int32_t* __restrict__ ptg, int64_t npt,
+                                     int64_t np, float omss, int32_t* __restrict__ list, unsigned* __restrict__ count) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool keep = false;
+    if (r < np) {
+        const bool pt = r < npt;
+        int32_t ids[4];
+        pair_ids(S, pq[r], ptg[r], pt, ids);
+        F3 X[4], P[4];
+        float pmax = 0.f;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            X[k] = ld3f(x32, n, ids[k]);
+            P[k] = ld3f(d32, n, ids[k]);
+            pmax = fmaxf(pmax, fabsmax(P[k]));
+        }
+        const F3 pb = {0.25f * (P[0].x + P[1].x + P[2].x + P[3].x), 0.25f * (P[0].y + P[1].y + P[2].y + P[3].y),
+                       0.25f * (P[0].z + P[1].z + P[2].z + P[3].z)};
+        float nr[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const F3 c = fsub(P[k], pb);
+            nr[k] = sqrtf(fdot(c, c));
+        }
+        const float lp = pt ? nr[0] + fmaxf(fmaxf(nr[1], nr[2]), nr[3]) : fmaxf(nr[0], nr[1]) + fmaxf(nr[2], nr[3]);
+        const float lb = pair_lb32(X, pt);
+        keep = !(lb > 0.f && omss * lb > 1.0001f * lp + 1e-5f * pmax);
+    }
+    append_kept(keep, r, list, count);
+}
+
+// The listed pairs (list[0 .. *count)), or every pair when list is null.
 __global__ void ccd_pairs_kernel(const double* __restrict__ x, const double* __restrict__ dx, int64_t n, Surf S,
                                  const int32_t* __restrict__ pq, const int32_t* __restrict__ ptg, int64_t npt,
                                  int64_t np, double s, int max_iter, const int32_t* __restrict__ vscene,
-                                 unsigned long long* __restrict__ amin, bool box_filter) {
-    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+                                 unsigned long long* __restrict__ amin, bool box_filter,
+                                 const int32_t* __restrict__ list, const unsigned* __restrict__ count) {
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool valid;
+    if (list) {
+        valid = r < (int64_t)*count;
+        if (valid) r = list[r];
+    } else {
+        valid = r < np;
+    }
     double best = 1.0;
     int32_t scene = 0;
-    if (r < np) {
-        const int32_t q = pq[r], t = ptg[r];
+    if (valid) {
         int32_t ids[4];
-        if (r < npt) {
-            ids[0] = S.verts[q]; ids[1] = S.tris[t]; ids[2] = S.tris[S.ntri + t]; ids[3] = S.tris[2 * S.ntri + t];
-        } else {
-            ids[0] = S.edges[q]; ids[1] = S.edges[S.nedge + q]; ids[2] = S.edges[t]; ids[3] = S.edges[S.nedge + t];
-        }
+        pair_ids(S, pq[r], ptg[r], r < npt, ids);
         V3 X[4], P[4];
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
@@ -853,6 +1025,22 @@ gipc_status cache_disp(gipc_ctx* ctx, const double* x, const double* d, int64_t 
     return check_launch("contact cache");
 }
 
+// Float32 copies of x (and d) for the prefilters, the list they fill and its length (zeroed).
+gipc_status prefilter_setup(gipc_ctx* ctx, const double* x, const double* d, int64_t n, int64_t np, float** x32,
+                            float** d32, int32_t** list, unsigned** count, cudaStream_t st) {
+    gipc_status s;
+    if ((s = ctx->slot[C_X32].reserve(sizeof(float) * 6 * (n + 1))) != GIPC_OK) return s;
+    if ((s = ctx->slot[C_LIST].reserve(sizeof(int32_t) * (np + 32))) != GIPC_OK) return s;
+    *x32 = ctx->slot[C_X32].as<float>();
+    *d32 = *x32 + 3 * n;
+    *list = ctx->slot[C_LIST].as<int32_t>();
+    *count = reinterpret_cast<unsigned*>(ctx->slot[C_MISC].as<double>() + kMiscList);
+    cudaMemsetAsync(*count, 0, sizeof(unsigned), st);
+    to_f32_kernel<<<nblk(3 * n, 256), 256, 0, st>>>(x, 3 * n, *x32);
+    if (d) to_f32_kernel<<<nblk(3 * n, 256), 256, 0, st>>>(d, 3 * n, *d32);
+    return GIPC_OK;
+}
+
 // Margin tuner (see gipc_contact_cache): GPU time of the cached detections and CCD steps.  A span
 // is read back at the next cached call, after the stream synchronisations in between.
 void tuner_harvest(gipc_contact_cache& C) {
@@ -1009,7 +1197,15 @@ gipc_status find_contacts_impl(gipc_ctx* ctx, const double* x, const double* res
     int32_t* cnt = ctx->slot[C_CNT].as<int32_t>();
     int32_t* code = ctx->slot[C_CODE].as<int32_t>();
     cudaMemsetAsync(cnt, 0, sizeof(int32_t) * nq, st);
-    if (np > 0) classify_pairs_kernel<<<nblk(np, 128), 128, 0, st>>>(x, n, S, L.q, L.t, npt, np, dh2, code, cnt);
+    if (np > 0) {
+        float *x32, *d32;
+        int32_t* list;
+        unsigned* nlist;
+        if ((s = prefilter_setup(ctx, x, nullptr, n, np, &x32, &d32, &list, &nlist, st)) != GIPC_OK) return s;
+        const float thr = nextafterf((float)(dhat * (1.0 + 1e-4)), INFINITY);
+        prefilter_pairs_kernel<<<nblk(np, 128), 128, 0, st>>>(x32, n, S, L.q, L.t, npt, np, thr, code, list, nlist);
+        classify_pairs_kernel<<<nblk(np, 128), 128, 0, st>>>(x, n, S, L.q, L.t, npt, np, dh2, code, cnt, list, nlist);
+    }
     // offsets over both kinds (point-triangle pairs first)
     if ((s = ctx->slot[C_QOFF].reserve(sizeof(int64_t) * (nq + 2 + scan_scratch_words(nq + 1)))) != GIPC_OK) return s;
     int64_t* off = ctx->slot[C_QOFF].as<int64_t>();
@@ -1045,6 +1241,7 @@ gipc_status ccd_impl(gipc_ctx* ctx, const double* x, const double* d, int64_t n,
     gipc_prof_span span(ctx->prof, GIPC_PROF_CCD, st);
     Surf S{srf.tris, srf.ntri, srf.edges, srf.nedge, srf.verts, srf.nvert};
     const int max_iter = 100000;
+    const float omss = nextafterf((float)((1.0 - slack) * (1.0 - 1e-6)), 0.0f);   // 1 - s, rounded down
     gipc_status s;
     if ((s = ctx->slot[C_MISC].reserve(16 * sizeof(double))) != GIPC_OK) return s;
     double* amin_d = vscene ? amin_dev : ctx->slot[C_MISC].as<double>() + kMiscAmin;
@@ -1058,9 +1255,16 @@ gipc_status ccd_impl(gipc_ctx* ctx, const double* x, const double* d, int64_t n,
         if (2.0 * (delta + dm) * (1.0 + 1e-9) <= ctx->ccache.pad) {
             const int64_t np = ctx->ccache.np;
             const int32_t* cq = ctx->slot[C_CPAIRS].as<int32_t>();
-            if (np > 0)
+            if (np > 0) {
+                float *x32, *d32;
+                int32_t* list;
+                unsigned* nlist;
+                if ((s = prefilter_setup(ctx, x, d, n, np, &x32, &d32, &list, &nlist, st)) != GIPC_OK) return s;
+                prefilter_ccd_kernel<<<nblk(np, 128), 128, 0, st>>>(x32, d32, n, S, cq, cq + np, ctx->ccache.npt, np,
+                                                                     omss, list, nlist);
                 ccd_pairs_kernel<<<nblk(np, 128), 128, 0, st>>>(x, d, n, S, cq, cq + np, ctx->ccache.npt, np, slack,
-                                                                 max_iter, vscene, amin, true);
+                                                                 max_iter, vscene, amin, true, list, nlist);
+            }
             cudaMemcpyAsync(alpha_h, amin_d, sizeof(double) * ns, cudaMemcpyDeviceToHost, st);
             if (cudaStreamSynchronize(st) != cudaSuccess) return check_launch("gipc_ccd_max_step: sync");
             return check_launch("gipc_ccd_max_step");
@@ -1076,9 +1280,15 @@ gipc_status ccd_impl(gipc_ctx* ctx, const double* x, const double* d, int64_t n,
     if ((s = collect_pairs(ctx, x, d, n, S, pt ? &Gt : nullptr, S.nedge > 0 ? &Ge : nullptr, true, vscene, &npt, &np, L,
                            st)) != GIPC_OK)
         return s;
-    if (np > 0)
+    if (np > 0) {
+        float *x32, *d32;
+        int32_t* list;
+        unsigned* nlist;
+        if ((s = prefilter_setup(ctx, x, d, n, np, &x32, &d32, &list, &nlist, st)) != GIPC_OK) return s;
+        prefilter_ccd_kernel<<<nblk(np, 128), 128, 0, st>>>(x32, d32, n, S, L.q, L.t, npt, np, omss, list, nlist);
         ccd_pairs_kernel<<<nblk(np, 128), 128, 0, st>>>(x, d, n, S, L.q, L.t, npt, np, slack, max_iter, vscene, amin,
-                                                         false);
+                                                         false, list, nlist);
+    }
     cudaMemcpyAsync(alpha_h, amin_d, sizeof(double) * ns, cudaMemcpyDeviceToHost, st);
     if (cudaStreamSynchronize(st) != cudaSuccess) return check_launch("gipc_ccd_max_step: sync");
     return check_launch("gipc_ccd_max_step");

@@ -141,7 +141,7 @@ struct gipc_spmv_tune {
 
 struct gipc_ctx {
     int device = 0;
-    static constexpr int kSlots = 64;   // assembly 0-8 and 61, pcg 9-15, 40 and 62, contacts 16-19, 30-39, 45-46 and 59-60, time step 20-29, 41-44 and 47-48, derivatives 49-58
+    static constexpr int kSlots = 65;   // assembly 0-8 and 61, pcg 9-15, 40 and 62, contacts 16-19, 30-39, 45-46, 59-60 and 63-64, time step 20-29, 41-44 and 47-48, derivatives 49-58
     gipc_scratch slot[kSlots];
     gipc_profiler prof;
     gipc_contact_cache ccache;   // filled and used by the time step only

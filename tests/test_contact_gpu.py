@@ -232,3 +232,69 @@ def test_newton_steps_on_a_ball_grid_keep_the_exact_contact_set(gipc):
         xs = x.cpu().numpy()
         assert C.count_intersections(xs, sc["tris"], sc["edges"]) == 0
     assert total_iters > 4 and st["contacts"] > 0
+
+
+def _soup(seed, cells=(6, 6, 8), pitch=0.01, dh=2e-3):
+    """One independent, nearly flat triangle per cell of a lattice, against the ceiling of its cell
+    in even layers and the floor in odd ones, kept a random 0.2-1.5 dhat inside the cell, so that
+    the pairs of layers face each other 0.4-3 dhat apart and nothing intersects.  Generic
+    triangles (heights jittered by 0.3 dhat), slivers (third corner within 1e-4 of the size off
+    the line of the other two), needles (one edge 1e-6 of the size) and flat triangles dhat
+    (1 + 1e-7 j) / 2 from the wall (nearly parallel edges, distances within rounding of dhat)."""
+    rng = np.random.default_rng(seed)
+    corners = []
+    k = 0
+    for ix in range(cells[0]):
+        for iy in range(cells[1]):
+            for iz in range(cells[2]):
+                lo = np.array([ix, iy, iz], float) * pitch
+                g = rng.uniform(0.2, 1.5, size=(2, 3)) * dh
+                a, b = lo + g[0], lo + pitch - g[1]
+                up = iz % 2 == 0   # against the ceiling (facing the next layer up)
+
+                def u():
+                    q = a + (b - a) * rng.uniform(0.0, 1.0, 3)
+                    q[2] = b[2] - rng.uniform(0.0, 0.3) * dh if up else a[2] + rng.uniform(0.0, 0.3) * dh
+                    return q
+                kind = k % 4
+                if kind == 0:
+                    t = np.array([u(), u(), u()])
+                elif kind == 1:
+                    p0, p1 = u(), u()
+                    t = np.clip(np.array([p0, p1, p0 + rng.uniform(0.2, 0.8) * (p1 - p0) +
+                                          1e-4 * pitch * rng.normal(size=3)]), a, b)
+                elif kind == 2:
+                    p0 = u()
+                    t = np.clip(np.array([p0, p0 + 1e-6 * pitch * rng.normal(size=3), u()]), a, b)
+                else:
+                    t = np.array([u(), u(), u()])
+                    half = 0.5 * dh * (1.0 + 1e-7 * rng.integers(-3, 4))
+                    t[:, 2] = lo[2] + pitch - half if up else lo[2] + half
+                corners.append(t)
+                k += 1
+    x = np.ascontiguousarray(np.concatenate(corners).T)
+    m = x.shape[1]
+    tris = np.arange(m, dtype=np.int32).reshape(-1, 3).T.copy()
+    edges = np.concatenate([tris[[0, 1]], tris[[1, 2]], tris[[2, 0]]], axis=1).astype(np.int32)
+    return x, tris, np.ascontiguousarray(edges), np.arange(m, dtype=np.int32)
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_soup_contacts_and_ccd_bit_exact(gipc, seed):
+    """Degenerate and borderline shapes against the oracle: most candidate pairs are dropped by the
+    float32 prefilter before the float64 classification and CCD, which must change no result."""
+    dh = 2e-3
+    x, tris, edges, verts = _soup(seed, dh=dh)
+    ref_st, ref_eps = C.find_contacts(x, x, tris, edges, verts, dh)
+    srf = gipc.Surface(_dev(tris), _dev(edges), _dev(verts))
+    st, eps = gipc.find_contacts(_dev(x), _dev(x), srf, dh, capacity=None)
+    assert ref_st.shape[1] > 20
+    assert np.array_equal(st.cpu().numpy(), ref_st)
+    assert np.array_equal(eps.cpu().numpy(), ref_eps)
+    rng = np.random.default_rng(100 + seed)
+    for scale in (0.05 * dh, 0.5 * dh, 3 * dh):
+        d = scale * rng.normal(size=x.shape)
+        ref = C.max_step(x, d, tris, edges, verts)
+        got = gipc.ccd_max_step(_dev(x), _dev(d), srf)
+        assert got == ref, (scale, got, ref)
+        assert 0.0 < ref <= 1.0
