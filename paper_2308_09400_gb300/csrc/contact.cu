@@ -350,10 +350,21 @@ __global__ void bucket_kernel(const double* __restrict__ lo, const double* __res
 // Candidate pairs.  Each warp takes queries q = warp, warp + nw, ... and walks the cells of the
 // query box (the same box in every lane); each round every lane tests one bucket entry: the
 // float32 boxes, the float64 boxes, whether this cell is the pair's reference cell (the low
-// corner of the intersection of the two boxes) and the kind's index filters.  Survivors are
+// corner of the intersection of the two boxes; a float32 pre-check skips the float64 tests in
+// the cells that clearly are not) and the kind's index filters.  Survivors are
 // queued in shared memory (64 per warp) and appended to the global pair list 32 at a time with
 // one atomic.  The list order is arbitrary; the pair SET is fixed by the float64 tests.
 enum PairKind { K_PT = 0, K_EE = 1, K_PT_SWEPT = 2 };
+
+// Whether floor(v) can equal c for the float64 value v32 approximates: v32 is the corner in cell
+// units from the float32 boxes (each coordinate rounded down, within 2^-23 relative of the
+// float64 one) and the float32 inverse cell size, so it is within 1e-6 |v| of the float64 product;
+// the slack taken is ten times that plus 1e-3 of a cell.
+// fc is the cell index as a float (converted once per cell: int64 conversions run on the FP64 pipe).
+__device__ __forceinline__ bool ref_cell_possible(float v32, float fc) {
+    const float slack = 1e-5f * fabsf(v32) + 1e-3f;
+    return v32 + slack >= fc && v32 - slack < fc + 1.f;
+}
 
 struct PairList {
     int32_t* q;                  // [cap] query index (surface-vertex position, or edge id)
@@ -410,9 +421,11 @@ scan_pairs_kernel(const double* __restrict__ x, const double* __restrict__ dx, i
         if (box_cells(ql[0], ql[1], ql[2], qh[0], qh[1], qh[2], ih, c0, c1) > kMaxCellsPerBox) continue;
         const float fl[3] = {__double2float_rd(ql[0]), __double2float_rd(ql[1]), __double2float_rd(ql[2])};
         const float fh[3] = {__double2float_ru(qh[0]), __double2float_ru(qh[1]), __double2float_ru(qh[2])};
+        const float ih32 = (float)ih;
         for (int64_t cz = c0[2]; cz <= c1[2]; ++cz)
             for (int64_t cy = c0[1]; cy <= c1[1]; ++cy)
                 for (int64_t cx = c0[0]; cx <= c1[0]; ++cx) {
+                    const float fcx = (float)cx, fcy = (float)cy, fcz = (float)cz;
                     const uint64_t b = bucket_of(cx, cy, cz, qs, G.mask);
                     const int64_t e0 = G.boff[b], e1 = G.boff[b + 1];
                     for (int64_t base = e0; base < e1; base += 32) {
@@ -424,6 +437,11 @@ scan_pairs_kernel(const double* __restrict__ x, const double* __restrict__ dx, i
                             t = __float_as_int(A.w);
                             ok = __float_as_int(B.w) == qs && fl[0] <= B.x && fh[0] >= A.x && fl[1] <= B.y &&
                                  fh[1] >= A.y && fl[2] <= B.z && fh[2] >= A.z && (KIND != K_EE || t > q);
+                            // a pair's boxes share several cells and only its reference cell emits it:
+                            // skip the float64 tests where the float32 corner lies clearly outside this cell
+                            ok = ok && ref_cell_possible(fmaxf(fl[0], A.x) * ih32, fcx) &&
+                                 ref_cell_possible(fmaxf(fl[1], A.y) * ih32, fcy) &&
+                                 ref_cell_possible(fmaxf(fl[2], A.z) * ih32, fcz);
                             if (ok) {
                                 const double tl[3] = {G.lo[t], G.lo[G.m + t], G.lo[2 * G.m + t]};
                                 const double th[3] = {G.hi[t], G.hi[G.m + t], G.hi[2 * G.m + t]};
