@@ -31,8 +31,10 @@
 //
 // Mixed form: float32 blocks and a float32 product (row sums in float32); the
 // block-Jacobi factors, s = P^-1 r and the direction are float32 as well, the
-// direction kept with its exact float64 image for the x update and the dots;
-// x, r, alpha, beta and the dots stay float64.  On GB300 a float64 operation, or
+// direction's exact float64 image used for the x update and the dots (kept in memory
+// by the separate kernels, converted where it is used by the persistent solver, whose
+// phases are bound by memory rather than by the FP64 pipe); x, r, alpha, beta and
+// the dots stay float64.  On GB300 a float64 operation, or
 // a conversion between float64 and float32, issues at 1/64 of the float32 rate,
 // so the float32 preconditioner and direction take about half the float64 work
 // out of kernel B.
@@ -491,7 +493,10 @@ struct StageRing {
 // warp-major (STRIDED: warp w of CTA b is number w * gridDim.x + b, so every CTA samples the whole
 // matrix and the CTAs' totals even out: on the C1 system the busiest CTA carries 1.025 instead of
 // 1.046 times the mean, and the 319 warps with a single slice spread over the CTAs).
-template <typename VT, typename PT, int U, int W, int NS, bool COHERENT, bool STRIDED = false>
+// DOT_FROM_CG: the row's part of c . q takes c from the gathered float32 direction (exactly the
+// float64 image c holds), so the float64 image need not be kept (the mixed persistent solver).
+template <typename VT, typename PT, int U, int W, int NS, bool COHERENT, bool STRIDED = false,
+          bool DOT_FROM_CG = false>
 __device__ __forceinline__ double spmv_slices(StageRing<VT, U, W, NS>& R, const int32_t* __restrict__ rowptr,
                                               const int64_t* __restrict__ slice_off, const int32_t* __restrict__ sell_col,
                                               const VT* __restrict__ sell_vals, const PT* cg, const double* c,
@@ -586,7 +591,8 @@ __device__ __forceinline__ double spmv_slices(StageRing<VT, U, W, NS>& R, const 
             for (int e = 0; e < 3; ++e) {
                 const double y = fx ? 0.0 : (double)(a0[e] + a1[e]);
                 q[3 * row + e] = y;
-                d += c[3 * row + e] * y;
+                if constexpr (DOT_FROM_CG) d += (double)cg[3 * row + e] * y;
+                else d += c[3 * row + e] * y;
             }
         }
     }
@@ -1357,8 +1363,8 @@ pcg_loop_kernel(const int32_t* __restrict__ rowptr, const int64_t* __restrict__ 
         if (trace) __syncthreads();
         phase_mark(trace, it, 0);
         bool timed_out = false;
-        const double d = spmv_slices<VT, PT, U, kLoopW, NS, true, true>(R, rowptr, slice_off, sell_col, sell_vals, cg,
-                                                                        c, perm, q, fixed, n, nsl, timed_out);
+        const double d = spmv_slices<VT, PT, U, kLoopW, NS, true, true, MIX>(R, rowptr, slice_off, sell_col, sell_vals,
+                                                                             cg, c, perm, q, fixed, n, nsl, timed_out);
         if (timed_out) {
             R.drain_all();
             if ((t & 31) == 0) atomicExch(&S->status, GIPC_ERR_TIMEOUT);
@@ -1428,11 +1434,7 @@ pcg_loop_kernel(const int32_t* __restrict__ rowptr, const int64_t* __restrict__ 
             const int64_t v = ((int64_t)j * gridDim.x + blockIdx.x) * kLoopT + t;
             if (v < n) {
 #pragma unroll
-                for (int e = 0; e < 3; ++e) {
-                    // the mixed form reads the direction's float64 image (no conversion on the FP64 pipe)
-                    const double ce = MIX ? c[3 * v + e] : (double)ck[j][e];
-                    x[3 * v + e] = x[3 * v + e] + alpha * ce;
-                }
+                for (int e = 0; e < 3; ++e) x[3 * v + e] = x[3 * v + e] + alpha * (double)ck[j][e];
             }
         }
         __syncthreads();
@@ -1470,10 +1472,8 @@ pcg_loop_kernel(const int32_t* __restrict__ rowptr, const int64_t* __restrict__ 
                 const bool fx = fixed && fixed[v];
 #pragma unroll
                 for (int e = 0; e < 3; ++e) {
-                    if constexpr (MIX) {   // the float32 direction and its exact float64 image
-                        const float ce = fx ? 0.0f : __fmaf_rn(beta_f, ck[j][e], sk[j][e]);
-                        c32[3 * v + e] = ce;
-                        c[3 * v + e] = (double)ce;
+                    if constexpr (MIX) {   // the float32 direction (its float64 image is formed where used)
+                        c32[3 * v + e] = fx ? 0.0f : __fmaf_rn(beta_f, ck[j][e], sk[j][e]);
                     } else {
                         const double ce = fx ? 0.0 : sk[j][e] + beta * ck[j][e];
                         c[3 * v + e] = ce;
