@@ -22,6 +22,11 @@ gipc_status find_contacts_impl(gipc_ctx* ctx, const double* x, const double* res
 gipc_status ccd_impl(gipc_ctx* ctx, const double* x, const double* d, int64_t n, const gipc_surface& srf, double slack,
                      double* alpha_h, cudaStream_t st, const int32_t* vscene, int nscenes, double* amin_dev,
                      bool cached);
+gipc_status stencil_type_order(const int32_t* stencils, int64_t k, int32_t* order, unsigned* counts, cudaStream_t s);
+gipc_status eval_stencils_ordered(const double* x, int64_t n, const int32_t* stencils, int64_t k,
+                                  const double* eps_x, const gipc_barrier_params* prm, int prec, int mode,
+                                  double* energy, double* grad, void* hess, double* lam, uint8_t* flags,
+                                  const int32_t* order, cudaStream_t s);
 gipc_status pcg_impl(gipc_ctx* ctx, const gipc_bsr* A, const double* rhs, double* x, const uint8_t* fixed,
                      const gipc_pcg_params* prm, int* iters_out_h, double* rel_out_h, cudaStream_t st,
                      const int64_t* voff, int nscenes, int* scene_iters_h, int* scene_status_h);
@@ -152,7 +157,30 @@ struct ContactSet {
     int64_t cap = 0, k = 0;
     int32_t* st = nullptr;
     double* eps = nullptr;
+    int32_t* order = nullptr;   // the stencils grouped by type (stencil_type_order), for their evaluation
+    unsigned* tcnt = nullptr;   // its 16 counters
 };
+
+// The contact set's storage in its slot: eps [cap], stencils [4][cap], the type order [cap] and its
+// counters.  contact_storage grows it to `cap` stencils; contact_view takes what the slot holds.
+constexpr size_t kContactBytes = 5 * sizeof(int32_t) + sizeof(double), kContactExtra = 16 * sizeof(unsigned) + 16;
+void contact_pointers(gipc_ctx* ctx, ContactSet& cs, int64_t cap) {
+    cs.cap = cap;
+    cs.eps = ctx->slot[cs.slot].as<double>();
+    cs.st = reinterpret_cast<int32_t*>(cs.eps + cap);
+    cs.order = cs.st + 4 * cap;
+    cs.tcnt = reinterpret_cast<unsigned*>(cs.order + cap);
+}
+gipc_status contact_storage(gipc_ctx* ctx, ContactSet& cs, int64_t cap) {
+    const gipc_status r = ctx->slot[cs.slot].reserve((size_t)cap * kContactBytes + kContactExtra);
+    if (r != GIPC_OK) return r;
+    contact_pointers(ctx, cs, cap);
+    return GIPC_OK;
+}
+void contact_view(gipc_ctx* ctx, ContactSet& cs) {
+    const size_t b = ctx->slot[cs.slot].bytes;
+    contact_pointers(ctx, cs, b > kContactExtra ? (int64_t)((b - kContactExtra) / kContactBytes) : 0);
+}
 
 struct Step {
     gipc_ctx* ctx;
@@ -177,15 +205,11 @@ struct Step {
                                                      cs.cap, &cnt, true, nullptr, nullptr, st, 1, true);
             if (s == GIPC_OK) {
                 cs.k = cnt;
-                return GIPC_OK;
+                return stencil_type_order(cs.st, cs.k, cs.order, cs.tcnt, st);
             }
             if (s != GIPC_ERR_CAPACITY) return s;
-            const int64_t cap = cnt + cnt / 4 + 1024;
-            const gipc_status r = ctx->slot[cs.slot].reserve((size_t)cap * (4 * sizeof(int32_t) + sizeof(double)));
+            const gipc_status r = contact_storage(ctx, cs, cnt + cnt / 4 + 1024);
             if (r != GIPC_OK) return r;
-            cs.cap = cap;
-            cs.eps = ctx->slot[cs.slot].as<double>();
-            cs.st = reinterpret_cast<int32_t*>(cs.eps + cap);
         }
         return fail(GIPC_ERR_CUDA, "gipc_newton_step: contact count changed between passes");
     }
@@ -203,8 +227,8 @@ struct Step {
         ep.scale = prm.dt * prm.dt;
         if ((s = gipc_eval_tets(x, n, sc.tets, T, sc.Dm_inv, sc.vol, &ep, GIPC_FP64, GIPC_HESS_DENSE, te, nullptr, nullptr, st)) != GIPC_OK)
             return s;
-        if (k > 0 && (s = gipc_eval_stencils(x, n, cs.st, k, cs.eps, &prm.barrier, GIPC_FP64, GIPC_HESS_DENSE, se, nullptr,
-                                             nullptr, nullptr, nullptr, st)) != GIPC_OK)
+        if (k > 0 && (s = eval_stencils_ordered(x, n, cs.st, k, cs.eps, &prm.barrier, GIPC_FP64, GIPC_HESS_DENSE, se, nullptr,
+                                                nullptr, nullptr, nullptr, cs.order, st)) != GIPC_OK)
             return s;
         reduce(R_INERTIA, x, xt, sc.mass, n, n, partial, res + 0, st);
         reduce(R_ARRAY, te, nullptr, nullptr, 0, T, partial + kRedBlocks, res + 1, st);
@@ -234,11 +258,7 @@ struct Step {
         gb = rhs + m3;
         partial = ctx->slot[N_RED].as<double>();
         res = partial + 4 * kRedBlocks;
-        for (auto& cs : set) {
-            cs.cap = (int64_t)(ctx->slot[cs.slot].bytes / (4 * sizeof(int32_t) + sizeof(double)));
-            cs.eps = ctx->slot[cs.slot].as<double>();
-            cs.st = reinterpret_cast<int32_t*>(cs.eps + cs.cap);
-        }
+        for (auto& cs : set) contact_view(ctx, cs);
         const double dt = prm.dt;
         cudaMemcpyAsync(x0, x, sizeof(double) * m3, cudaMemcpyDeviceToDevice, st);
         inertia_target_kernel<<<nb(n, 256), 256, 0, st>>>(x0, v, sc.fixed, n, dt, (dt * dt) * prm.gravity[0],
@@ -270,8 +290,8 @@ struct Step {
             double* sl = sg + 12 * k;
             void* sh = sl + std::max<int64_t>(k, 1);
             if (k > 0 &&
-                (s = gipc_eval_stencils(x, n, A.st, k, A.eps, &prm.barrier, prm.prec, prm.hess_mode, nullptr, sg, sh,
-                                        rank1 ? sl : nullptr, nullptr, st)) != GIPC_OK)
+                (s = eval_stencils_ordered(x, n, A.st, k, A.eps, &prm.barrier, prm.prec, prm.hess_mode, nullptr, sg, sh,
+                                           rank1 ? sl : nullptr, nullptr, A.order, st)) != GIPC_OK)
                 return s;
             ctx->prof.stop(GIPC_PROF_ELEMENTS, st);
             grad_base_kernel<<<nb(m3, 256), 256, 0, st>>>(x, xt, sc.mass, n, gb);
@@ -639,15 +659,11 @@ struct BatchStep {
                                                      cs.cap, &cnt, true, vs, npt, st, ns, true);
             if (s == GIPC_OK) {
                 cs.k = cnt;
-                return GIPC_OK;
+                return stencil_type_order(cs.st, cs.k, cs.order, cs.tcnt, st);
             }
             if (s != GIPC_ERR_CAPACITY) return s;
-            const int64_t cap = cnt + cnt / 4 + 1024;
-            const gipc_status r = ctx->slot[cs.slot].reserve((size_t)cap * (4 * sizeof(int32_t) + sizeof(double)));
+            const gipc_status r = contact_storage(ctx, cs, cnt + cnt / 4 + 1024);
             if (r != GIPC_OK) return r;
-            cs.cap = cap;
-            cs.eps = ctx->slot[cs.slot].as<double>();
-            cs.st = reinterpret_cast<int32_t*>(cs.eps + cap);
         }
         return fail(GIPC_ERR_CUDA, "gipc_newton_step_batch: contact count changed between passes");
     }
@@ -665,8 +681,8 @@ struct BatchStep {
         ep.scale = prm.dt * prm.dt;
         if ((s = gipc_eval_tets(xc, n, sc.tets, T, sc.Dm_inv, sc.vol, &ep, GIPC_FP64, GIPC_HESS_DENSE, te, nullptr, nullptr, st)) != GIPC_OK)
             return s;
-        if (k > 0 && (s = gipc_eval_stencils(xc, n, cs.st, k, cs.eps, &prm.barrier, GIPC_FP64, GIPC_HESS_DENSE, se, nullptr,
-                                             nullptr, nullptr, nullptr, st)) != GIPC_OK)
+        if (k > 0 && (s = eval_stencils_ordered(xc, n, cs.st, k, cs.eps, &prm.barrier, GIPC_FP64, GIPC_HESS_DENSE, se, nullptr,
+                                                nullptr, nullptr, nullptr, cs.order, st)) != GIPC_OK)
             return s;
         scene_energy_kernel<<<ns, 256, 0, st>>>(xc, xt, sc.mass, n, voff, sc.tets, T, te, cs.st, k, *npt, se, vs, sI, sC);
         cudaMemcpyAsync(I_out.data(), sI, sizeof(double) * ns, cudaMemcpyDeviceToHost, st);
@@ -833,11 +849,7 @@ struct BatchStep {
         g = d + m3f;
         rhs = g + m3f;
         gb = rhs + m3f;
-        for (auto& cs : set) {
-            cs.cap = (int64_t)(ctx->slot[cs.slot].bytes / (4 * sizeof(int32_t) + sizeof(double)));
-            cs.eps = ctx->slot[cs.slot].as<double>();
-            cs.st = reinterpret_cast<int32_t*>(cs.eps + cs.cap);
-        }
+        for (auto& cs : set) contact_view(ctx, cs);
         // the unpacked working batch is the caller's
         ns = ns_full;
         n = nf;
@@ -925,8 +937,8 @@ struct BatchStep {
             double* sl = sg + 12 * k;
             void* sh = sl + std::max<int64_t>(k, 1);
             if (k > 0 &&
-                (s = gipc_eval_stencils(x, n, A.st, k, A.eps, &prm.barrier, prm.prec, prm.hess_mode, nullptr, sg, sh,
-                                        rank1 ? sl : nullptr, nullptr, st)) != GIPC_OK)
+                (s = eval_stencils_ordered(x, n, A.st, k, A.eps, &prm.barrier, prm.prec, prm.hess_mode, nullptr, sg, sh,
+                                           rank1 ? sl : nullptr, nullptr, A.order, st)) != GIPC_OK)
                 return s;
             ctx->prof.stop(GIPC_PROF_ELEMENTS, st);
             grad_base_kernel<<<nb(m3, 256), 256, 0, st>>>(x, xt, sc.mass, n, gb);

@@ -459,13 +459,16 @@ __global__ void __launch_bounds__(kEvalThreads)
 eval_stencils_kernel(const double* __restrict__ x, int64_t n, const int32_t* __restrict__ st, int64_t k,
                      const double* __restrict__ eps_x, const BarrierConst K, double* __restrict__ energy,
                      double* __restrict__ grad, void* __restrict__ hess_v, double* __restrict__ lam,
-                     uint8_t* __restrict__ flags) {
+                     uint8_t* __restrict__ flags, const int32_t* __restrict__ order) {
     using HT = typename std::conditional<PREC == GIPC_FP64, double, float>::type;
     HT* __restrict__ hess = static_cast<HT*>(hess_v);
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     constexpr bool kCoop = (MODE == GIPC_HESS_BLOCKS);
-    if (!kCoop && i >= k) return;   // (the element-major output is written by whole warps)
-    const bool live = i < k;
+    if (!kCoop && tid >= k) return;   // (the element-major output is written by whole warps)
+    const bool live = tid < k;
+    // thread tid evaluates stencil order[tid] (stencils grouped by type, so that a warp runs one
+    // type's branch) and writes its outputs at that stencil's own index
+    const int64_t i = (!kCoop && order) ? (int64_t)order[tid] : tid;
 
     double e_out = 0.0, lam_out = 0.0, w[12], gr[12];
     uint8_t fl = 0;
@@ -561,6 +564,47 @@ eval_stencils_kernel(const double* __restrict__ x, int64_t n, const int32_t* __r
     }
 }
 
+// Stencils grouped by type: counts[t] (t = 0..6, 7 for a malformed tuple) then, per type, the
+// stencil indices in order[counts[0] + ... + counts[t-1] ...].  The order within a type is
+// arbitrary (one atomic per type present in a warp); the evaluation writes every output at the
+// stencil's own index, so it changes no result.
+__device__ __forceinline__ int stencil_kind(const int32_t* __restrict__ st, int64_t k, int64_t i) {
+    int32_t v[4];
+    const int t = decode_stencil(st[i], st[k + i], st[2 * k + i], st[3 * k + i], v);
+    return t < 0 || t > 6 ? 7 : t;
+}
+__global__ void type_count_kernel(const int32_t* __restrict__ st, int64_t k, unsigned* __restrict__ counts) {
+    __shared__ unsigned c[8];
+    if (threadIdx.x < 8) c[threadIdx.x] = 0;
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&c[stencil_kind(st, k, i)], 1u);
+    __syncthreads();
+    if (threadIdx.x < 8 && c[threadIdx.x]) atomicAdd(&counts[threadIdx.x], c[threadIdx.x]);
+}
+// counts: [0, 8) the type counts, [8, 16) zeroed cursors.  Launched with whole warps.
+__global__ void type_scatter_kernel(const int32_t* __restrict__ st, int64_t k, unsigned* __restrict__ counts,
+                                    int32_t* __restrict__ order) {
+    __shared__ unsigned off[8];
+    if (threadIdx.x == 0) {
+        unsigned a = 0;
+        for (int t = 0; t < 8; ++t) {
+            off[t] = a;
+            a += counts[t];
+        }
+    }
+    __syncthreads();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int t = i < k ? stencil_kind(st, k, i) : 8;
+    const unsigned grp = __match_any_sync(0xffffffffu, t);
+    const int leader = __ffs(grp) - 1;
+    unsigned base = 0;
+    if (t < 8 && lane == leader) base = atomicAdd(&counts[8 + t], (unsigned)__popc(grp));
+    base = __shfl_sync(grp, base, leader);
+    if (t < 8) order[off[t] + base + __popc(grp & ((1u << lane) - 1u))] = (int32_t)i;
+}
+
 // eps_x = 1e-3 |x1-x0|^2 |x3-x2|^2 from rest positions, evaluated left to right without
 // contraction so the value is the plain IEEE float64 result of that expression.
 __global__ void eps_x_kernel(const double* __restrict__ x, int64_t n, const int32_t* __restrict__ st,
@@ -608,11 +652,22 @@ extern "C" gipc_status gipc_compute_eps_x(const double* rest_x, int64_t n, const
     return check_launch("gipc_compute_eps_x");
 }
 
-extern "C" gipc_status gipc_eval_stencils(const double* x, int64_t n, const int32_t* stencils, int64_t k,
-                                          const double* eps_x, const gipc_barrier_params* prm, int prec,
-                                          int mode, double* energy, double* grad, void* hess, double* lam,
-                                          uint8_t* flags, void* stream) {
-    using namespace gipc;
+namespace gipc {
+
+// The stencils' type grouping for eval_stencils_ordered: order [k], counts [16] device scratch.
+gipc_status stencil_type_order(const int32_t* stencils, int64_t k, int32_t* order, unsigned* counts, cudaStream_t s) {
+    if (k <= 0) return GIPC_OK;
+    cudaMemsetAsync(counts, 0, 16 * sizeof(unsigned), s);
+    type_count_kernel<<<std::min<unsigned>(grid_for(k, 256), 1024u), 256, 0, s>>>(stencils, k, counts);
+    type_scatter_kernel<<<grid_for(k, 256), 256, 0, s>>>(stencils, k, counts, order);
+    return check_launch("stencil type order");
+}
+
+// gipc_eval_stencils with thread t evaluating stencil order[t] (null: t) -- the same outputs.
+gipc_status eval_stencils_ordered(const double* x, int64_t n, const int32_t* stencils, int64_t k,
+                                  const double* eps_x, const gipc_barrier_params* prm, int prec, int mode,
+                                  double* energy, double* grad, void* hess, double* lam, uint8_t* flags,
+                                  const int32_t* order, cudaStream_t s) {
     if (n < 0 || k < 0) return fail(GIPC_ERR_INVALID_ARG, "gipc_eval_stencils: negative size");
     if (!prm) return fail(GIPC_ERR_INVALID_ARG, "gipc_eval_stencils: null parameters");
     if (!(prm->dhat > 0.0) || !(prm->kappa >= 0.0) || !(prm->d_thr_ratio > 0.0 && prm->d_thr_ratio < 1.0))
@@ -635,9 +690,10 @@ extern "C" gipc_status gipc_eval_stencils(const double* x, int64_t n, const int3
     K.kappa = prm->kappa;
 
     const unsigned blocks = grid_for(k, kEvalThreads);
-    cudaStream_t s = (cudaStream_t)stream;
+    if (mode == GIPC_HESS_BLOCKS) order = nullptr;   // (its output is written by whole warps in place)
 #define GIPC_LAUNCH(P, M) \
-    eval_stencils_kernel<P, M><<<blocks, kEvalThreads, 0, s>>>(x, n, stencils, k, eps_x, K, energy, grad, hess, lam, flags)
+    eval_stencils_kernel<P, M><<<blocks, kEvalThreads, 0, s>>>(x, n, stencils, k, eps_x, K, energy, grad, hess, lam, \
+                                                               flags, order)
     if (prec == GIPC_FP64 && mode == GIPC_HESS_DENSE) GIPC_LAUNCH(GIPC_FP64, GIPC_HESS_DENSE);
     else if (prec == GIPC_FP64 && mode == GIPC_HESS_BLOCKS) GIPC_LAUNCH(GIPC_FP64, GIPC_HESS_BLOCKS);
     else if (prec == GIPC_FP64) GIPC_LAUNCH(GIPC_FP64, GIPC_HESS_RANK1);
@@ -646,4 +702,14 @@ extern "C" gipc_status gipc_eval_stencils(const double* x, int64_t n, const int3
     else GIPC_LAUNCH(GIPC_MIXED, GIPC_HESS_RANK1);
 #undef GIPC_LAUNCH
     return check_launch("gipc_eval_stencils");
+}
+
+}  // namespace gipc
+
+extern "C" gipc_status gipc_eval_stencils(const double* x, int64_t n, const int32_t* stencils, int64_t k,
+                                          const double* eps_x, const gipc_barrier_params* prm, int prec,
+                                          int mode, double* energy, double* grad, void* hess, double* lam,
+                                          uint8_t* flags, void* stream) {
+    return gipc::eval_stencils_ordered(x, n, stencils, k, eps_x, prm, prec, mode, energy, grad, hess, lam, flags,
+                                       nullptr, (cudaStream_t)stream);
 }
