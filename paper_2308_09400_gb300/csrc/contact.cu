@@ -7,17 +7,20 @@
 // nearly-parallel types (Sec. 6.1).
 //
 // Broad phase: a uniform grid stored as a spatial hash.  Every target primitive (triangle or
-// edge) is inserted into each cell its float64 box (padded by dhat for detection, swept for CCD)
-// overlaps (at most once per hash bucket), as a 32-byte entry holding its id and its box rounded
-// outward to float32.  One warp serves one query (a surface vertex, or an edge i looking for edges
-// j > i): it walks the cells of the query box and scans each bucket 32 entries at a time with
-// coalesced loads, testing the float32 boxes first (conservative), then the float64 boxes.  A pair
-// is taken only in the cell holding the low corner of the intersection of the two boxes, so each
-// overlapping pair is met exactly once, whatever the cell size or hash collisions.  The cell size
-// is the mean target-box extent, doubled until no box spans more than a few hundred cells.  The
-// grid only proposes candidates: the float64 box test and the classification decide, written as a
-// fixed sequence of IEEE operations without contraction (__d*_rn), so they take exactly the
-// decisions of any implementation of the same formulas.  Two passes (count, then write at scanned
+// edge) is inserted into each cell its box (padded by dhat for detection, swept for CCD), rounded
+// outward to float32, overlaps (at most once per hash bucket), as a 32-byte entry holding its id
+// and that float32 box.  One warp serves one query (a surface vertex, or an edge i looking for
+// edges j > i): it walks the cells of the query's float32 box and scans each bucket 32 entries at
+// a time with coalesced loads, testing the float32 boxes.  A pair is taken only in the cell
+// holding the low corner of the intersection of the two boxes; targets, queries and this rule
+// compute cells with the same float32 expression, so each overlapping pair is met exactly once,
+// whatever the cell size or hash collisions.  The cell size is the mean target-box extent,
+// doubled until no box spans more than a few hundred cells.  The grid only proposes candidates
+// (every pair whose float64 boxes overlap, and a few whose float32 boxes alone do): the
+// classification decides contacts, and for the CCD the float64 swept-box test picks the pairs
+// whose step is evaluated, both written as fixed sequences of IEEE operations without
+// contraction (__d*_rn), so they take exactly the decisions of any implementation of the same
+// formulas.  Two passes (count, then write at scanned
 // offsets) and a per-query sort by target index give a deterministic list: point-triangle pairs
 // ordered by (surface vertex, triangle), then edge-edge pairs by (edge i, edge j > i).
 //
@@ -192,7 +195,6 @@ struct Grid {
     const Entry* ent;        // entries grouped by bucket
 };
 
-__device__ __forceinline__ int64_t cell_of(double v, double inv_h) { return (int64_t)floor(__dmul_rn(v, inv_h)); }
 
 __device__ __forceinline__ uint64_t bucket_of(int64_t cx, int64_t cy, int64_t cz, int32_t scene, uint64_t mask) {
     // Teschner et al. (2003) spatial hash of the three cell coordinates and the scene, then a
@@ -267,12 +269,27 @@ __global__ void cell_size_kernel(const double* __restrict__ ext_sum, const doubl
     inv_h[sc] = 1.0 / (h * scale);
 }
 
-__device__ __forceinline__ int64_t box_cells(double lx, double ly, double lz, double hx, double hy, double hz,
-                                             double ih, int64_t c0[3], int64_t c1[3]) {
-    c0[0] = cell_of(lx, ih); c0[1] = cell_of(ly, ih); c0[2] = cell_of(lz, ih);
-    c1[0] = cell_of(hx, ih); c1[1] = cell_of(hy, ih); c1[2] = cell_of(hz, ih);
-    const int64_t a = c1[0] - c0[0] + 1, b = c1[1] - c0[1] + 1, c = c1[2] - c0[2] + 1;
-    // saturate: a box this large asks for a coarser grid (a non-finite box never fits)
+// Grid cells in float32 (see the header): the cell of a float32 box bound v is floor(v ih) with
+// ih the float32 inverse cell size, clamped to +-2^30.
+__device__ __forceinline__ int cell32(float v, float ih) {
+    return (int)fminf(fmaxf(floorf(v * ih), -1073741824.f), 1073741824.f);
+}
+__device__ __forceinline__ void box32(const double* l, const double* h, float* fl, float* fh) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        fl[q] = __double2float_rd(l[q]);
+        fh[q] = __double2float_ru(h[q]);
+    }
+}
+__device__ __forceinline__ int64_t box_cells(const float* fl, const float* fh, float ih, int c0[3], int c1[3]) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        if (!(isfinite(fl[q]) && isfinite(fh[q]))) return kMaxCellsPerBox + 1;   // never fits
+        c0[q] = cell32(fl[q], ih);
+        c1[q] = cell32(fh[q], ih);
+    }
+    const int64_t a = (int64_t)c1[0] - c0[0] + 1, b = (int64_t)c1[1] - c0[1] + 1, c = (int64_t)c1[2] - c0[2] + 1;
+    // saturate: a box this large asks for a coarser grid
     if (!(a >= 1 && b >= 1 && c >= 1) || a > kMaxCellsPerBox || b > kMaxCellsPerBox || c > kMaxCellsPerBox)
         return kMaxCellsPerBox + 1;
     return a * b * c;
@@ -285,9 +302,12 @@ __global__ void cells_count_kernel(const double* __restrict__ lo, const double* 
                                    unsigned long long* __restrict__ max_cells) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= m) return;
-    int64_t c0[3], c1[3];
-    const double ih = inv_h[vscene ? vscene[prim[t]] : 0];
-    const int64_t c = box_cells(lo[t], lo[m + t], lo[2 * m + t], hi[t], hi[m + t], hi[2 * m + t], ih, c0, c1);
+    int c0[3], c1[3];
+    const float ih = (float)inv_h[vscene ? vscene[prim[t]] : 0];
+    const double l[3] = {lo[t], lo[m + t], lo[2 * m + t]}, h[3] = {hi[t], hi[m + t], hi[2 * m + t]};
+    float fl[3], fh[3];
+    box32(l, h, fl, fh);
+    const int64_t c = box_cells(fl, fh, ih, c0, c1);
     cnt[t] = (int32_t)std::min<int64_t>(c, kMaxCellsPerBox + 1);
     atomicMax(max_cells, (unsigned long long)c);
 }
@@ -306,9 +326,11 @@ __global__ void point_cells_kernel(const double* __restrict__ x, const double* _
         l[q] = fmin(a, b);
         h[q] = fmax(a, b);
     }
-    int64_t c0[3], c1[3];
-    const double ih = inv_h[vscene ? vscene[p] : 0];
-    atomicMax(max_cells, (unsigned long long)box_cells(l[0], l[1], l[2], h[0], h[1], h[2], ih, c0, c1));
+    int c0[3], c1[3];
+    float fl[3], fh[3];
+    box32(l, h, fl, fh);
+    const float ih = (float)inv_h[vscene ? vscene[p] : 0];
+    atomicMax(max_cells, (unsigned long long)box_cells(fl, fh, ih, c0, c1));
 }
 
 // Insert target t into the bucket of each cell its box overlaps, at most once per bucket (two
@@ -323,8 +345,10 @@ __global__ void bucket_kernel(const double* __restrict__ lo, const double* __res
     if (t >= m) return;
     const int32_t scene = vscene ? vscene[prim[t]] : 0;
     const double l[3] = {lo[t], lo[m + t], lo[2 * m + t]}, h[3] = {hi[t], hi[m + t], hi[2 * m + t]};
-    int64_t c0[3], c1[3];
-    const int64_t nc = box_cells(l[0], l[1], l[2], h[0], h[1], h[2], inv_h[scene], c0, c1);
+    float fl[3], fh[3];
+    box32(l, h, fl, fh);
+    int c0[3], c1[3];
+    const int64_t nc = box_cells(fl, fh, (float)inv_h[scene], c0, c1);
     if (nc > kMaxCellsPerBox) return;
     const int64_t nx = c1[0] - c0[0] + 1, ny = c1[1] - c0[1] + 1;
     auto bucket_at = [&](int64_t li) {
@@ -332,8 +356,8 @@ __global__ void bucket_kernel(const double* __restrict__ lo, const double* __res
     };
     Entry E;
     if (FILL) {
-        E.lx = __double2float_rd(l[0]); E.ly = __double2float_rd(l[1]); E.lz = __double2float_rd(l[2]);
-        E.hx = __double2float_ru(h[0]); E.hy = __double2float_ru(h[1]); E.hz = __double2float_ru(h[2]);
+        E.lx = fl[0]; E.ly = fl[1]; E.lz = fl[2];
+        E.hx = fh[0]; E.hy = fh[1]; E.hz = fh[2];
         E.id = (int32_t)t;
         E.scene = scene;
     }
@@ -349,22 +373,11 @@ __global__ void bucket_kernel(const double* __restrict__ lo, const double* __res
 
 // Candidate pairs.  Each warp takes queries q = warp, warp + nw, ... and walks the cells of the
 // query box (the same box in every lane); each round every lane tests one bucket entry: the
-// float32 boxes, the float64 boxes, whether this cell is the pair's reference cell (the low
-// corner of the intersection of the two boxes; a float32 pre-check skips the float64 tests in
-// the cells that clearly are not) and the kind's index filters.  Survivors are
-// queued in shared memory (64 per warp) and appended to the global pair list 32 at a time with
-// one atomic.  The list order is arbitrary; the pair SET is fixed by the float64 tests.
+// float32 boxes, whether this cell is the pair's reference cell (the low corner of the
+// intersection of the two boxes) and the kind's index filters.  Survivors are queued in shared
+// memory (64 per warp) and appended to the global pair list 32 at a time with one atomic.  The
+// list order is arbitrary; the pair SET is fixed by the float32 boxes.
 enum PairKind { K_PT = 0, K_EE = 1, K_PT_SWEPT = 2 };
-
-// Whether floor(v) can equal c for the float64 value v32 approximates: v32 is the corner in cell
-// units from the float32 boxes (each coordinate rounded down, within 2^-23 relative of the
-// float64 one) and the float32 inverse cell size, so it is within 1e-6 |v| of the float64 product;
-// the slack taken is ten times that plus 1e-3 of a cell.
-// fc is the cell index as a float (converted once per cell: int64 conversions run on the FP64 pipe).
-__device__ __forceinline__ bool ref_cell_possible(float v32, float fc) {
-    const float slack = 1e-5f * fabsf(v32) + 1e-3f;
-    return v32 + slack >= fc && v32 - slack < fc + 1.f;
-}
 
 struct PairList {
     int32_t* q;                  // [cap] query index (surface-vertex position, or edge id)
@@ -416,16 +429,14 @@ scan_pairs_kernel(const double* __restrict__ x, const double* __restrict__ dx, i
             }
         }
         const int32_t qs = vscene ? vscene[KIND == K_EE ? ia : p] : 0;   // the query's scene
-        const double ih = G.inv_h[qs];
-        int64_t c0[3], c1[3];
-        if (box_cells(ql[0], ql[1], ql[2], qh[0], qh[1], qh[2], ih, c0, c1) > kMaxCellsPerBox) continue;
-        const float fl[3] = {__double2float_rd(ql[0]), __double2float_rd(ql[1]), __double2float_rd(ql[2])};
-        const float fh[3] = {__double2float_ru(qh[0]), __double2float_ru(qh[1]), __double2float_ru(qh[2])};
-        const float ih32 = (float)ih;
-        for (int64_t cz = c0[2]; cz <= c1[2]; ++cz)
-            for (int64_t cy = c0[1]; cy <= c1[1]; ++cy)
-                for (int64_t cx = c0[0]; cx <= c1[0]; ++cx) {
-                    const float fcx = (float)cx, fcy = (float)cy, fcz = (float)cz;
+        const float ih = (float)G.inv_h[qs];
+        float fl[3], fh[3];
+        box32(ql, qh, fl, fh);
+        int c0[3], c1[3];
+        if (box_cells(fl, fh, ih, c0, c1) > kMaxCellsPerBox) continue;
+        for (int cz = c0[2]; cz <= c1[2]; ++cz)
+            for (int cy = c0[1]; cy <= c1[1]; ++cy)
+                for (int cx = c0[0]; cx <= c1[0]; ++cx) {
                     const uint64_t b = bucket_of(cx, cy, cz, qs, G.mask);
                     const int64_t e0 = G.boff[b], e1 = G.boff[b + 1];
                     for (int64_t base = e0; base < e1; base += 32) {
@@ -435,20 +446,11 @@ scan_pairs_kernel(const double* __restrict__ x, const double* __restrict__ dx, i
                         if (e < e1) {
                             const float4 A = __ldg(ent4 + 2 * e), B = __ldg(ent4 + 2 * e + 1);
                             t = __float_as_int(A.w);
+                            // the float32 boxes overlap, and this is the pair's reference cell
                             ok = __float_as_int(B.w) == qs && fl[0] <= B.x && fh[0] >= A.x && fl[1] <= B.y &&
-                                 fh[1] >= A.y && fl[2] <= B.z && fh[2] >= A.z && (KIND != K_EE || t > q);
-                            // a pair's boxes share several cells and only its reference cell emits it:
-                            // skip the float64 tests where the float32 corner lies clearly outside this cell
-                            ok = ok && ref_cell_possible(fmaxf(fl[0], A.x) * ih32, fcx) &&
-                                 ref_cell_possible(fmaxf(fl[1], A.y) * ih32, fcy) &&
-                                 ref_cell_possible(fmaxf(fl[2], A.z) * ih32, fcz);
-                            if (ok) {
-                                const double tl[3] = {G.lo[t], G.lo[G.m + t], G.lo[2 * G.m + t]};
-                                const double th[3] = {G.hi[t], G.hi[G.m + t], G.hi[2 * G.m + t]};
-                                ok = ql[0] <= th[0] && qh[0] >= tl[0] && ql[1] <= th[1] && qh[1] >= tl[1] &&
-                                     ql[2] <= th[2] && qh[2] >= tl[2] && cell_of(fmax(ql[0], tl[0]), ih) == cx &&
-                                     cell_of(fmax(ql[1], tl[1]), ih) == cy && cell_of(fmax(ql[2], tl[2]), ih) == cz;
-                            }
+                                 fh[1] >= A.y && fl[2] <= B.z && fh[2] >= A.z && (KIND != K_EE || t > q) &&
+                                 cell32(fmaxf(fl[0], A.x), ih) == cx && cell32(fmaxf(fl[1], A.y), ih) == cy &&
+                                 cell32(fmaxf(fl[2], A.z), ih) == cz;
                             if (ok) {   // no shared vertex
                                 if (KIND == K_EE) {
                                     const int32_t j0 = S.edges[t], j1 = S.edges[S.nedge + t];
@@ -1304,8 +1306,10 @@ gipc_status ccd_impl(gipc_ctx* ctx, const double* x, const double* d, int64_t n,
         unsigned* nlist;
         if ((s = prefilter_setup(ctx, x, d, n, np, &x32, &d32, &list, &nlist, st)) != GIPC_OK) return s;
         prefilter_ccd_kernel<<<nblk(np, 128), 128, 0, st>>>(x32, d32, n, S, L.q, L.t, npt, np, omss, list, nlist);
+        // the swept grid proposes every pair whose float32 swept boxes overlap: the float64 swept-box
+        // test picks the pairs whose step is taken
         ccd_pairs_kernel<<<nblk(np, 128), 128, 0, st>>>(x, d, n, S, L.q, L.t, npt, np, slack, max_iter, vscene, amin,
-                                                         false, list, nlist);
+                                                         true, list, nlist);
     }
     cudaMemcpyAsync(alpha_h, amin_d, sizeof(double) * ns, cudaMemcpyDeviceToHost, st);
     if (cudaStreamSynchronize(st) != cudaSuccess) return check_launch("gipc_ccd_max_step: sync");

@@ -50,8 +50,10 @@ __device__ __forceinline__ void jacobi_rot(CT (&a)[3][3], CT (&v)[3][3]) {
     constexpr int R = 3 - P - Q;
     const CT apq = a[P][Q];
     if (apq == CT(0)) return;
-    const CT theta = (a[Q][Q] - a[P][P]) / (CT(2) * apq);
-    const CT t = (theta >= CT(0) ? CT(1) : CT(-1)) / (fabs(theta) + sqrt(theta * theta + CT(1)));
+    // t = sign(theta) / (|theta| + sqrt(theta^2 + 1)), theta = tau / rho, with numerator and
+    // denominator scaled by |rho| (one division instead of two)
+    const CT tau = a[Q][Q] - a[P][P], rho = CT(2) * apq;
+    const CT t = (tau >= CT(0) ? rho : -rho) / (fabs(tau) + sqrt(tau * tau + rho * rho));
     const CT c = rsqrt(t * t + CT(1));
     const CT s = t * c;
     a[P][P] -= t * apq;
@@ -126,8 +128,9 @@ __device__ void svd3(const CT (&F)[3][3], CT (&U)[3][3], CT (&s)[3], CT (&V)[3][
     CT u0[3] = {B[0][0], B[1][0], B[2][0]};
     CT n0 = sqrt(u0[0] * u0[0] + u0[1] * u0[1] + u0[2] * u0[2]);
     if (n0 > CT(0)) {
+        const CT i0 = CT(1) / n0;
 #pragma unroll
-        for (int r = 0; r < 3; ++r) u0[r] /= n0;
+        for (int r = 0; r < 3; ++r) u0[r] *= i0;
     } else {
         u0[0] = CT(1); u0[1] = CT(0); u0[2] = CT(0);
     }
@@ -136,8 +139,9 @@ __device__ void svd3(const CT (&F)[3][3], CT (&U)[3][3], CT (&s)[3], CT (&V)[3][
     CT u1[3] = {b1[0] - p * u0[0], b1[1] - p * u0[1], b1[2] - p * u0[2]};
     CT n1 = sqrt(u1[0] * u1[0] + u1[1] * u1[1] + u1[2] * u1[2]);
     if (n1 > Num<CT>::tiny && n1 > Num<CT>::rel * n0) {
+        const CT i1 = CT(1) / n1;
 #pragma unroll
-        for (int r = 0; r < 3; ++r) u1[r] /= n1;
+        for (int r = 0; r < 3; ++r) u1[r] *= i1;
     } else {  // any unit vector orthogonal to u0
         const CT ax = fabs(u0[0]), ay = fabs(u0[1]), az = fabs(u0[2]);
         CT e[3] = {CT(0), CT(0), CT(0)};
