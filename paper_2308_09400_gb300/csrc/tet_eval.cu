@@ -184,20 +184,6 @@ __device__ __forceinline__ void map_to_x(const CT (&G)[3][3], const CT (&Dmi)[3]
     }
 }
 
-template <typename CT>
-__device__ __forceinline__ void add_mode(CT lam, const CT (&Q)[3][3], const CT (&Dmi)[3][3], CT (&H)[78]) {
-    if (!(lam > CT(0))) return;
-    CT w[12];
-    map_to_x(Q, Dmi, w);
-    int idx = 0;
-#pragma unroll
-    for (int a = 0; a < 12; ++a) {
-        const CT la = lam * w[a];
-#pragma unroll
-        for (int b = 0; b <= a; ++b) H[idx++] += la * w[b];
-    }
-}
-
 template <int PREC, int MODE>
 __global__ void __launch_bounds__(128)
 eval_tets_kernel(const double* __restrict__ x, int64_t n, const int32_t* __restrict__ tets, int64_t T,
@@ -289,29 +275,68 @@ eval_tets_kernel(const double* __restrict__ x, int64_t n, const int32_t* __restr
     const CT m1c = (CT)m1, lJ = (CT)(K.lam * Jm), muc = (CT)K.mu, lamc = (CT)K.lam, alc = (CT)K.alpha;
     CT U[3][3], sv[3], V[3][3];
     svd3(Fc, U, sv, V);
-    CT H[78];
+    // Modes in vertex blocks.  A mode's vector w (12 entries) has, for vertex a+1 (a = 0..2), the
+    // 3-vector Q Dm^-T e_a = U S z_a with Q = U S V^T and z_a = V^T (row a of Dm^-1), and minus
+    // their sum for vertex 0.  So only the blocks of vertices 1..3 are accumulated (l w_a w_b^T,
+    // a <= b, the diagonal ones as their 6 upper entries), and the blocks of vertex 0 follow
+    // from them at the end (H_0b = -sum_a H_ab, H_00 = -sum_b H_0b).
+    CT z[3][3];   // z[a][i] = (V^T Dm^-T e_a)_i
 #pragma unroll
-    for (int q = 0; q < 78; ++q) H[q] = CT(0);
-    const CT r2 = (CT)0.70710678118654752440;
-    // twist / flip modes for the pairs (1,2), (0,2), (0,1)
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) z[a][i] = V[0][i] * Dc[a][0] + V[1][i] * Dc[a][1] + V[2][i] * Dc[a][2];
+    CT Bd[3][6], Bo[3][9];   // blocks (a,a) upper entries; blocks (0,1), (0,2), (1,2)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+#pragma unroll
+        for (int e = 0; e < 6; ++e) Bd[a][e] = CT(0);
+#pragma unroll
+        for (int e = 0; e < 9; ++e) Bo[a][e] = CT(0);
+    }
+    auto add_mode_v = [&](CT lam, const CT (&w)[3][3]) {   // w[a][r]: vertex a+1's component r
+        if (!(lam > CT(0))) return;
+        CT tl[3][3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int r = 0; r < 3; ++r) tl[a][r] = lam * w[a][r];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            int e = 0;
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+#pragma unroll
+                for (int c = r; c < 3; ++c) Bd[a][e++] += tl[a][r] * w[a][c];
+        }
+#pragma unroll
+        for (int o = 0; o < 3; ++o) {
+            const int a = o == 2 ? 1 : 0, b = o == 0 ? 1 : 2;
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) Bo[o][3 * r + c] += tl[a][r] * w[b][c];
+        }
+    };
+    // twist / flip modes for the pairs (1,2), (0,2), (0,1): w = (u_i z_a[j] -+ u_j z_a[i]) / sqrt 2,
+    // the 1/2 of the square taken into the eigenvalue
 #pragma unroll
     for (int kk = 0; kk < 3; ++kk) {
         const int i = kk == 0 ? 1 : 0, j = kk == 2 ? 1 : 2;
-        const CT lt = m1c + lJ * sv[kk];
-        const CT lf = m1c - lJ * sv[kk];
-        CT Qt[3][3], Qf[3][3];
+        const CT lt = CT(0.5) * (m1c + lJ * sv[kk]);
+        const CT lf = CT(0.5) * (m1c - lJ * sv[kk]);
+        CT wt[3][3], wf[3][3];
 #pragma unroll
-        for (int r = 0; r < 3; ++r)
+        for (int a = 0; a < 3; ++a)
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const CT a = U[r][i] * V[c][j], b = U[r][j] * V[c][i];
-                Qt[r][c] = r2 * (a - b);
-                Qf[r][c] = r2 * (a + b);
+            for (int r = 0; r < 3; ++r) {
+                const CT p = U[r][i] * z[a][j], q = U[r][j] * z[a][i];
+                wt[a][r] = p - q;
+                wf[a][r] = p + q;
             }
-        add_mode(lt, Qt, Dc, H);
-        add_mode(lf, Qf, Dc, H);
+        add_mode_v(lt, wt);
+        add_mode_v(lf, wf);
     }
-    // scaling modes: eigenpairs of A = d2 Psi / ds ds
+    // scaling modes: eigenpairs (l, alpha) of A = d2 Psi / ds ds, w = U diag(alpha) z_a
     {
         CT A[3][3];
         const CT ip2 = (CT)(ip1 * ip1);
@@ -332,22 +357,45 @@ eval_tets_kernel(const double* __restrict__ x, int64_t n, const int32_t* __restr
         jacobi3(A, Avec);
 #pragma unroll
         for (int m = 0; m < 3; ++m) {
-            CT Q[3][3];
+            CT w[3][3];
 #pragma unroll
-            for (int r = 0; r < 3; ++r)
+            for (int a = 0; a < 3; ++a) {
+                const CT g0 = Avec[0][m] * z[a][0], g1 = Avec[1][m] * z[a][1], g2 = Avec[2][m] * z[a][2];
 #pragma unroll
-                for (int c = 0; c < 3; ++c)
-                    Q[r][c] = U[r][0] * Avec[0][m] * V[c][0] + U[r][1] * Avec[1][m] * V[c][1] + U[r][2] * Avec[2][m] * V[c][2];
-            add_mode(A[m][m], Q, Dc, H);
+                for (int r = 0; r < 3; ++r) w[a][r] = U[r][0] * g0 + U[r][1] * g1 + U[r][2] * g2;
+            }
+            add_mode_v(A[m][m], w);
         }
     }
+    // block (va, vb) entry (r, c) of the 12 x 12 matrix, vertices 0..3
+    auto blk = [&](int a, int b, int r, int c) -> CT {   // vertices 1..3 as a, b = 0..2
+        if (a == b) {
+            const int lo = r < c ? r : c, hi = r < c ? c : r;
+            return Bd[a][lo == 0 ? hi : (lo == 1 ? 2 + hi : 5)];
+        }
+        const int o = (a + b) - 1;   // (0,1) -> 0, (0,2) -> 1, (1,2) -> 2
+        return a < b ? Bo[o][3 * r + c] : Bo[o][3 * c + r];
+    };
+    CT H0[3][9];   // H_0b, b = vertex 1..3
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) H0[b][3 * r + c] = -((blk(0, b, r, c) + blk(1, b, r, c)) + blk(2, b, r, c));
+    auto hval = [&](int p, int q) -> CT {   // H(p, q), p >= q
+        const int va = p / 3, vb = q / 3, r = p % 3, c = q % 3;
+        if (va == 0 && vb == 0) return -((H0[0][3 * r + c] + H0[1][3 * r + c]) + H0[2][3 * r + c]);
+        if (vb == 0) return H0[va - 1][3 * c + r];   // H_a0 = H_0a^T
+        if (va == 0) return H0[vb - 1][3 * r + c];
+        return blk(va - 1, vb - 1, r, c);
+    };
     const CT kc = (CT)k;
-    int idx = 0;
 #pragma unroll
     for (int a = 0; a < 12; ++a)
 #pragma unroll
         for (int b = 0; b <= a; ++b) {
-            const HT h = kc * H[idx++];
+            const HT h = kc * hval(a, b);
             if (MODE == GIPC_HESS_BLOCKS) {   // element-major 3x3 sub-blocks
                 hess[(t * 16 + (a / 3) * 4 + b / 3) * 9 + (a % 3) * 3 + b % 3] = h;
                 if (a != b) hess[(t * 16 + (b / 3) * 4 + a / 3) * 9 + (b % 3) * 3 + a % 3] = h;
