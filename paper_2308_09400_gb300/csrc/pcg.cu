@@ -657,6 +657,13 @@ constexpr int kUfp = 2, kWfp = 16, kNSfp = 2;   // float-pair product (8-byte va
 // The persistent solver's float-pair product stages one step per group, so that two CTAs fit on an SM
 // (the grid then owns two vertices per thread of the C1 system, as in the other forms).
 constexpr int kUfpLoop = 1;
+// Systems that one CTA per SM holds (up to 2 x 512 rows per SM) take the persistent solver with
+// wider groups (FP64: 2 steps, mixed: 4), one CTA per SM: their slices are few per warp, so each
+// warp's chain of staged groups (and of direction gathers) sets the product's length, and wider
+// groups halve it.  On the sphere-grid system (131,906 rows) the solver's time per Newton
+// iteration went 2.89 -> 2.34 ms (FP64) and 1.43 -> 1.29 ms (mixed); the C1 system does not fit.
+constexpr int kU64Wide = 2, kNS64Wide = 2;
+constexpr int kU32Wide = 4, kNS32Wide = 2;
 
 template <typename VT, typename PT, int U, int W, int NS>
 void launch_spmv_tma(const int32_t* rowptr, const int64_t* slice_off, const int32_t* sell_col, const VT* sell_vals,
@@ -1866,10 +1873,19 @@ gipc_status pcg_impl(gipc_ctx* ctx, const gipc_bsr* A, const double* rhs, double
     const int64_t nsl = (n + kSellC - 1) / kSellC;
     // one persistent launch for all iterations of a single system where the grid holds it
     LoopPlan loop;
+    bool wide = false;   // the one-CTA-per-SM persistent solver (kU64Wide / kU32Wide)
     if (!voff) {
-        if (fp) loop = plan_loop<fpair, fpair, kUfpLoop, kNSfp, false>(n, nsl);
-        else if (f64) loop = plan_loop<double, double, kU64, kNS64, false>(n, nsl);
-        else loop = plan_loop<float, float, kU32, kNS32, true>(n, nsl);
+        if (fp) {
+            loop = plan_loop<fpair, fpair, kUfpLoop, kNSfp, false>(n, nsl);
+        } else if (f64) {
+            loop = plan_loop<double, double, kU64Wide, kNS64Wide, false>(n, nsl);
+            wide = loop.ok;
+            if (!wide) loop = plan_loop<double, double, kU64, kNS64, false>(n, nsl);
+        } else {
+            loop = plan_loop<float, float, kU32Wide, kNS32Wide, true>(n, nsl);
+            wide = loop.ok;
+            if (!wide) loop = plan_loop<float, float, kU32, kNS32, true>(n, nsl);
+        }
     }
     const FusePlan fuse = (voff || loop.ok) ? FusePlan{} : (f64 ? plan_fused<false>(n) : plan_fused<true>(n));
     const unsigned maxb = std::max(std::max(std::max(sb, vb), ub), std::max(fuse.grid, 2 * loop.grid));
@@ -1960,10 +1976,12 @@ gipc_status pcg_impl(gipc_ctx* ctx, const gipc_bsr* A, const double* rhs, double
             fn = (const void*)pcg_loop_kernel<fpair, fpair, kUfpLoop, kNSfp, false>;
             cg = c2;
         } else if (f64) {
-            fn = (const void*)pcg_loop_kernel<double, double, kU64, kNS64, false>;
+            fn = wide ? (const void*)pcg_loop_kernel<double, double, kU64Wide, kNS64Wide, false>
+                      : (const void*)pcg_loop_kernel<double, double, kU64, kNS64, false>;
             cg = c;
         } else {
-            fn = (const void*)pcg_loop_kernel<float, float, kU32, kNS32, true>;
+            fn = wide ? (const void*)pcg_loop_kernel<float, float, kU32Wide, kNS32Wide, true>
+                      : (const void*)pcg_loop_kernel<float, float, kU32, kNS32, true>;
             cg = c32;
         }
         unsigned long long* trace = nullptr;
