@@ -630,6 +630,17 @@ typedef enum {
 gipc_status gipc_profile_solver_trace(gipc_ctx* ctx, int enable);
 gipc_status gipc_profile_solver_phases(gipc_ctx* ctx, double* phase_us_h, int* iters_h);
 
+/* Batched solves (gipc_pcg over several scenes, and so gipc_newton_step_batch) run every
+ * iteration in one cooperative launch by default: the rows are spread over the CTAs by vertex,
+ * a scene cut by the CTAs' ranges gets its dots summed over them in a fixed order, and four
+ * bounded grid barriers separate the product, the dot parts, the update and the direction.
+ * Where the grid cannot hold the batch (more than 3 x 512 vertices per CTA slot) or a CTA would
+ * cut more than 64 scenes, and when gipc_pcg_batch_persistent(ctx, 0) turns it off, they run a
+ * product and a per-scene update kernel per iteration instead (the product's staging variant then
+ * tuned as described below).  The two differ in the summation order of the dots only.  Errors:
+ * GIPC_ERR_INVALID_ARG (null context). */
+gipc_status gipc_pcg_batch_persistent(gipc_ctx* ctx, int enable);
+
 /* Run-time tuning of the batched solver's product (gipc_pcg over several scenes, and so
  * gipc_newton_step_batch).  The product q = S(H c) streams the matrix in SELL-32 slices; how
  * many block columns a warp stages per copy (U), how many warps share a CTA (W) and how many

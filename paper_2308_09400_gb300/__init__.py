@@ -137,6 +137,10 @@ class Context:
         _abi.call("gipc_profile_solver_phases", self._h, out, ctypes.byref(it))
         return dict(zip(_abi.SOLVER_PHASES, list(out))), it.value
 
+    def batch_persistent(self, enable=True):
+        """Run batched solves as one persistent launch (gipc_pcg_batch_persistent)."""
+        _abi.call("gipc_pcg_batch_persistent", self._h, 1 if enable else 0)
+
     def spmv_autotune(self, enable=True):
         """Choose the batched product's staging variant at run time (gipc_spmv_autotune)."""
         _abi.call("gipc_spmv_autotune", self._h, 1 if enable else 0)

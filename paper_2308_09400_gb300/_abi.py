@@ -119,6 +119,7 @@ SIGNATURES = {
     "gipc_profile_solver_trace": (_INT, [_P, _INT]),
     "gipc_profile_solver_phases": (_INT, [_P, ctypes.POINTER(_D), ctypes.POINTER(_INT)]),
     "gipc_spmv_autotune": (_INT, [_P, _INT]),
+    "gipc_pcg_batch_persistent": (_INT, [_P, _INT]),
     "gipc_spmv_tunings": (_INT, [_P, _P, _INT, ctypes.POINTER(_INT)]),
     "gipc_find_contacts": (_INT, [_P, _P, _P, _I64, ctypes.POINTER(Surface), _D, _P, _P, _I64,
                                   ctypes.POINTER(_I64), _P]),

@@ -141,13 +141,14 @@ struct gipc_spmv_tune {
 
 struct gipc_ctx {
     int device = 0;
-    static constexpr int kSlots = 65;   // assembly 0-8 and 61, pcg 9-15, 40 and 62, contacts 16-19, 30-39, 45-46, 59-60 and 63-64, time step 20-29, 41-44 and 47-48, derivatives 49-58
+    static constexpr int kSlots = 66;   // assembly 0-8 and 61, pcg 9-15, 40, 62 and 65, contacts 16-19, 30-39, 45-46, 59-60 and 63-64, time step 20-29, 41-44 and 47-48, derivatives 49-58
     gipc_scratch slot[kSlots];
     gipc_profiler prof;
     gipc_contact_cache ccache;   // filled and used by the time step only
     bool solver_trace = false;   // persistent solves record phase stamps (gipc_profile_solver_trace)
     int solver_trace_iters = 0;  // iterations of the last traced solve
     bool spmv_autotune = true;   // batched product variant chosen at run time (gipc_spmv_autotune)
+    bool batch_loop = true;      // batched solves as one persistent launch (gipc_pcg_batch_persistent)
     std::vector<gipc_spmv_tune> spmv_tunes;
     cudaEvent_t spmv_ev[2] = {nullptr, nullptr};   // around one timed chunk of iterations
     void release_all() {

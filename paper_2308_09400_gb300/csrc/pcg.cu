@@ -62,7 +62,7 @@ constexpr int kFuseMaxTiles = 8;  // fused update / direction: tiles per CTA kep
 constexpr int kDirEpt = 4;        // direction kernel: vector entries per thread
 
 enum PcgSlot { P_VEC = 9, P_PINV = 10, P_PART = 11, P_PERM = 12, P_VEC32 = 13, P_SELL = 14, P_SLICE = 15, P_SCENE = 40,
-               P_TRACE = 62 };
+               P_TRACE = 62, P_BATCH = 65 };
 
 constexpr int kLenBuckets = 64;   // rows are ordered by min(blocks in row, 63), longest first
 constexpr int kPermChunk = 1024;  // rows per chunk of the stable bucket sort (rows stay in their chunk)
@@ -1767,6 +1767,242 @@ pcg_scene_step_kernel(double* __restrict__ x, double* __restrict__ r, double* __
     }
 }
 
+// ---- Persistent batched solver: every iteration of nscenes independent solves in one launch ----
+// The batch's rows are spread over the CTAs by vertex (CTA b owns the `chunk` vertices from
+// b chunk), whatever the scenes' sizes, so the vector phases are balanced; a scene cut by the
+// CTAs' ranges has a segment in each.  Per iteration, between bounded grid barriers:
+//   A   q = S(H c) over the SELL-32 slices (the product of the single-system solver);
+//   B1  per segment, its part of c . q (segment sums in a fixed order, one warp per segment);
+//   B2  per scene still running: alpha = delta / (c . q), the scene's parts summed in a fixed
+//       order by every CTA that holds part of it (so they all hold the same alpha); x += alpha c,
+//       r -= alpha q, s = P^-1 r, and the segments' parts of r . s;
+//   C   beta and the stopping test from the r . s parts, the same way; the scene's first CTA
+//       records its scalars; c = S(s + beta c).
+// Every element is computed as in the per-scene update kernel; only the summation order of the
+// two dots differs.  A CTA holds at most kBMaxSeg segments (the host checks before launching).
+constexpr int kBKeep = 3;      // vertices per thread
+constexpr int kBMaxSeg = 64;   // scene segments per CTA
+
+// Largest s with voff[s] <= v (the scene holding vertex v; empty scenes are skipped).
+__device__ __forceinline__ int scene_of(const int64_t* __restrict__ voff, int nscenes, int64_t v) {
+    int lo = 0, hi = nscenes - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (voff[mid] <= v) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// The most scene segments any CTA of a batched launch would hold.
+__global__ void batch_segments_kernel(const int64_t* __restrict__ voff, int nscenes, int64_t n, int64_t chunk,
+                                      int grid, int* __restrict__ most) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= grid) return;
+    const int64_t a = (int64_t)b * chunk;
+    if (a >= n) return;
+    const int64_t e = a + chunk < n ? a + chunk : n;
+    atomicMax(most, scene_of(voff, nscenes, e - 1) - scene_of(voff, nscenes, a) + 1);
+}
+
+// Sums of val over each segment (one warp per segment, lanes strided, then a fixed tree) into
+// out[j]; call with every thread of the CTA after val is complete.
+__device__ __forceinline__ void segment_sums(const double* val, const int* seg_lo, int nseg, double* out) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int j = w; j < nseg; j += kLoopW) {
+        double t = 0.0;
+        for (int li = seg_lo[j] + lane; li < seg_lo[j + 1]; li += 32) t += val[li];
+        t = warp_sum(t);
+        if (lane == 0) out[j] = t;
+    }
+}
+
+// Total of scene s over the CTAs holding part of it (part[cta + s], CTAs in order), in warp 0 lane 0
+// of the calling warp.
+__device__ __forceinline__ double scene_total(const double* part, const int64_t* __restrict__ voff, int s,
+                                             int64_t chunk) {
+    const int64_t v0 = voff[s], v1 = voff[s + 1];
+    const int lane = threadIdx.x & 31;
+    double t = 0.0;
+    if (v1 > v0) {
+        const int64_t c0 = v0 / chunk, c1 = (v1 - 1) / chunk;
+        for (int64_t cc = c0 + lane; cc <= c1; cc += 32) t += __ldcg(part + cc + s);
+    }
+    return warp_sum(t);
+}
+
+template <typename VT, typename PT, int U, int NS, bool MIX>
+__global__ void __launch_bounds__(kLoopT, loop_min_blocks<VT, U, NS>())
+pcg_batch_loop_kernel(const int32_t* __restrict__ rowptr, const int64_t* __restrict__ slice_off,
+                      const int32_t* __restrict__ sell_col, const VT* __restrict__ sell_vals, const PT* cg, double* x,
+                      double* r, double* c, float* c32, double* q, double* s_buf, const double* __restrict__ fac,
+                      const int32_t* __restrict__ perm, const uint8_t* __restrict__ fixed, int64_t n, int64_t nsl,
+                      const int64_t* __restrict__ voff, int nscenes, SceneScalars* SS, PcgScalars* S, double* part_a,
+                      double* part_b, int iters, int64_t chunk) {
+    using ST = FacT<MIX>;
+    ST* const so = reinterpret_cast<ST*>(s_buf);
+    __shared__ double val[kBKeep * kLoopT];
+    __shared__ int seg_lo[kBMaxSeg + 1];
+    __shared__ double seg_sum[kBMaxSeg], seg_alpha[kBMaxSeg], seg_beta[kBMaxSeg], seg_delta[kBMaxSeg];
+    __shared__ int seg_go[kBMaxSeg], seg_cont[kBMaxSeg], seg_iters[kBMaxSeg];
+    if (S->done) return;   // read before any CTA can change it: uniform
+    const int t = threadIdx.x, lane = t & 31, wq = t >> 5;
+    const int64_t a = (int64_t)blockIdx.x * chunk;
+    const int64_t e = a + chunk < n ? a + chunk : n;
+    const bool owns = a < n;
+    const int s0 = owns ? scene_of(voff, nscenes, a) : 0;
+    const int nseg = owns ? scene_of(voff, nscenes, e - 1) - s0 + 1 : 0;
+    for (int j = t; j <= nseg; j += kLoopT) {
+        const int64_t lo = j < nseg ? voff[s0 + j] : e;
+        seg_lo[j] = (int)((lo > a ? lo : a) - a);
+    }
+    __syncthreads();
+    int myseg[kBKeep];
+#pragma unroll
+    for (int k = 0; k < kBKeep; ++k) {
+        const int li = t + k * kLoopT;
+        int j = 0;
+        while (j + 1 < nseg && seg_lo[j + 1] <= li) ++j;
+        myseg[k] = j;
+    }
+    const double tol = S->tol;
+    const int max_iter = S->max_iter;
+    const int64_t first_sl = (int64_t)(t >> 5) * gridDim.x + blockIdx.x;
+    StageRing<VT, U, kLoopW, NS> R;
+    R.init();
+    R.preissue(first_sl, nsl, slice_off, sell_vals, sell_col);
+    unsigned nbar = 0;
+    auto sync = [&]() { return grid_sync(&S->bar_count, ++nbar * gridDim.x, &S->status); };
+    bool abort = false;
+    for (int it = 0; it < iters; ++it) {
+        // A: q = S(H c)
+        bool timed_out = false;
+        spmv_slices<VT, PT, U, kLoopW, NS, true, true>(R, rowptr, slice_off, sell_col, sell_vals, cg, c, perm, q, fixed,
+                                                       n, nsl, timed_out);
+        if (timed_out) {
+            R.drain_all();
+            if (lane == 0) atomicExch(&S->status, GIPC_ERR_TIMEOUT);
+        } else {
+            R.preissue(first_sl, nsl, slice_off, sell_vals, sell_col);
+        }
+        if (!sync()) {
+            abort = true;
+            break;
+        }
+        // B1: the segments' parts of c . q
+#pragma unroll
+        for (int k = 0; k < kBKeep; ++k) {
+            const int li = t + k * kLoopT;
+            const int64_t v = a + li;
+            if (v < e) val[li] = (c[3 * v] * q[3 * v] + c[3 * v + 1] * q[3 * v + 1]) + c[3 * v + 2] * q[3 * v + 2];
+        }
+        __syncthreads();
+        segment_sums(val, seg_lo, nseg, seg_sum);
+        __syncthreads();
+        for (int j = t; j < nseg; j += kLoopT) part_a[blockIdx.x + s0 + j] = seg_sum[j];
+        if (!sync()) {
+            abort = true;
+            break;
+        }
+        // B2: alpha per scene; x, r, s; the segments' parts of r . s
+        for (int j = wq; j < nseg; j += kLoopW) {
+            const int sc = s0 + j;
+            const double pq = scene_total(part_a, voff, sc, chunk);
+            if (lane == 0) {
+                const SceneScalars Z = SS[sc];
+                seg_go[j] = !Z.done;
+                seg_delta[j] = Z.delta;
+                seg_iters[j] = Z.iters;
+                seg_alpha[j] = Z.delta / pq;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kBKeep; ++k) {
+            const int li = t + k * kLoopT;
+            const int64_t v = a + li;
+            if (v >= e) continue;
+            double d = 0.0;
+            if (seg_go[myseg[k]]) {
+                const double alpha = seg_alpha[myseg[k]];
+                double rv[3];
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    x[3 * v + i] += alpha * c[3 * v + i];
+                    rv[i] = r[3 * v + i] - alpha * q[3 * v + i];
+                    r[3 * v + i] = rv[i];
+                }
+                ST sv[3], F[6];
+                load_factor_t<MIX>(fac, n, v, F);
+                d = precond_vertex<MIX>(F, rv, sv);
+#pragma unroll
+                for (int i = 0; i < 3; ++i) so[3 * v + i] = sv[i];
+            }
+            val[li] = d;
+        }
+        __syncthreads();
+        segment_sums(val, seg_lo, nseg, seg_sum);
+        __syncthreads();
+        for (int j = t; j < nseg; j += kLoopT) part_b[blockIdx.x + s0 + j] = seg_sum[j];
+        if (!sync()) {
+            abort = true;
+            break;
+        }
+        // C: beta and the stopping test per scene; the scene's first CTA records them; direction
+        for (int j = wq; j < nseg; j += kLoopW) {
+            const int sc = s0 + j;
+            const double dn = scene_total(part_b, voff, sc, chunk);
+            if (lane == 0) {
+                int cont = 0;
+                if (seg_go[j]) {
+                    const int its = seg_iters[j] + 1;
+                    const double alpha = seg_alpha[j];
+                    SceneScalars& Z = SS[sc];
+                    int stop = 0, nonfinite = 0;
+                    if (!isfinite(dn) || !isfinite(alpha)) stop = nonfinite = 1;
+                    else if (!(dn > 0.0) || dn < tol * Z.delta0 || its >= max_iter) stop = 1;
+                    if (voff[sc] / chunk == (int64_t)blockIdx.x) {   // the scene's first CTA
+                        Z.delta = dn;
+                        Z.iters = its;
+                        if (nonfinite) Z.status = GIPC_ERR_NONFINITE;
+                        if (stop) scene_stop(&Z, S, nscenes);
+                    }
+                    cont = !stop;
+                    seg_beta[j] = dn / seg_delta[j];
+                }
+                seg_cont[j] = cont;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kBKeep; ++k) {
+            const int li = t + k * kLoopT;
+            const int64_t v = a + li;
+            if (v >= e || !seg_cont[myseg[k]]) continue;
+            const double beta = seg_beta[myseg[k]];
+            const bool fx = fixed && fixed[v];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                if constexpr (MIX) {   // the float32 direction and its exact float64 image
+                    const float ce = fx ? 0.0f : __fmaf_rn((float)beta, c32[3 * v + i], so[3 * v + i]);
+                    c32[3 * v + i] = ce;
+                    c[3 * v + i] = (double)ce;
+                } else {
+                    const double ce = fx ? 0.0 : so[3 * v + i] + beta * c[3 * v + i];
+                    c[3 * v + i] = ce;
+                }
+            }
+        }
+        if (!sync()) {
+            abort = true;
+            break;
+        }
+        if (*(volatile int*)&S->done) break;   // every scene has stopped (read by all after the barrier)
+    }
+    R.drain();
+    (void)abort;
+}
+
 inline unsigned spmv_blocks(int64_t n) {
     const int64_t warps = (n + kRowsPerWarp - 1) / kRowsPerWarp;
     return (unsigned)((warps * 32 + kPcgThreads - 1) / kPcgThreads);
@@ -1835,6 +2071,33 @@ inline LoopPlan plan_loop(int64_t n, int64_t nsl) {
     p.ok = true;
     p.grid = (unsigned)grid;
     p.smem = smem;
+    return p;
+}
+
+struct BatchPlan {
+    bool ok = false;
+    unsigned grid = 0;
+    size_t smem = 0;
+    int64_t chunk = 0;
+};
+
+template <typename VT, typename PT, int U, int NS, bool MIX>
+inline BatchPlan plan_batch(int64_t n, int64_t nsl) {
+    BatchPlan p;
+    const DeviceFacts df = device_facts();
+    if (df.sms <= 0 || !df.coop || n <= 0) return p;
+    const size_t smem = StageLayout<VT, U, kLoopW, NS>::kBlockBytes;
+    const int per_sm = kernel_occupancy((const void*)pcg_batch_loop_kernel<VT, PT, U, NS, MIX>, kLoopT, smem);
+    if (per_sm <= 0) return p;
+    const int64_t cap = (int64_t)df.sms * per_sm, per_cta = (int64_t)kBKeep * kLoopT;
+    const int64_t want = std::max<int64_t>((nsl + kLoopW - 1) / kLoopW, (n + per_cta - 1) / per_cta);
+    const int64_t grid = std::max<int64_t>(1, std::min(cap, want));
+    const int64_t chunk = (n + grid - 1) / grid;
+    if (chunk > per_cta) return p;
+    p.ok = true;
+    p.grid = (unsigned)grid;
+    p.smem = smem;
+    p.chunk = chunk;
     return p;
 }
 
@@ -2002,6 +2265,42 @@ gipc_status pcg_impl(gipc_ctx* ctx, const gipc_bsr* A, const double* rhs, double
         if ((s = check_launch("gipc_pcg: persistent solver")) != GIPC_OK) return s;
         launched = max_iter;
     }
+    if (voff && !fp && max_iter > 0 && ctx->batch_loop) {
+        // every iteration of the batch in one cooperative launch, where the grid holds it and no CTA
+        // would cut more than kBMaxSeg scenes
+        const BatchPlan bp = f64 ? plan_batch<double, double, kU64, kNS64, false>(n, nsl)
+                                 : plan_batch<float, float, kU32, kNS32, true>(n, nsl);
+        if (bp.ok) {
+            if ((s = ctx->slot[P_BATCH].reserve(sizeof(double) * 2 * ((size_t)bp.grid + nscenes + 1) + 16)) != GIPC_OK)
+                return s;
+            double* part_a = ctx->slot[P_BATCH].as<double>();
+            double* part_b = part_a + bp.grid + nscenes + 1;
+            int* most = reinterpret_cast<int*>(part_b + bp.grid + nscenes + 1);
+            cudaMemsetAsync(most, 0, sizeof(int), st);
+            batch_segments_kernel<<<(bp.grid + 255) / 256, 256, 0, st>>>(voff, nscenes, n, bp.chunk, (int)bp.grid, most);
+            int most_h = 0;
+            cudaMemcpyAsync(&most_h, most, sizeof(int), cudaMemcpyDeviceToHost, st);
+            if (cudaStreamSynchronize(st) != cudaSuccess) return check_launch("gipc_pcg: batch plan");
+            if (most_h <= kBMaxSeg) {
+                int64_t n_arg = n, nsl_arg = nsl, chunk_arg = bp.chunk;
+                int ns_arg = nscenes, iters_arg = max_iter;
+                const uint8_t* fixed_arg = fixed;
+                const int32_t* rp = A->rowptr;
+                const void* fn = f64 ? (const void*)pcg_batch_loop_kernel<double, double, kU64, kNS64, false>
+                                     : (const void*)pcg_batch_loop_kernel<float, float, kU32, kNS32, true>;
+                const void* cg = f64 ? (const void*)c : (const void*)c32;
+                void* args[] = {&rp, &slice_off, &sell_col, &sell_vals, &cg, &xv, &r, &c, &c32, &q, &sv, &pinv, &perm,
+                                &fixed_arg, &n_arg, &nsl_arg, &voff, &ns_arg, &SS, &S, &part_a, &part_b, &iters_arg,
+                                &chunk_arg};
+                ctx->prof.start(GIPC_PROF_PCG_LOOP, st);
+                if (cudaLaunchCooperativeKernel(fn, dim3(bp.grid), dim3(kLoopT), args, bp.smem, st) != cudaSuccess)
+                    return check_launch("gipc_pcg: persistent batch solver");
+                ctx->prof.stop(GIPC_PROF_PCG_LOOP, st);
+                if ((s = check_launch("gipc_pcg: persistent batch solver")) != GIPC_OK) return s;
+                launched = max_iter;
+            }
+        }
+    }
     const int chunk = prm->check_every > 0 ? prm->check_every : (prm->rel_tol > 0.0 ? 16 : max_iter + 1);
     // batched systems: the product's staging variant is chosen at run time (the scenes' dots are
     // summed by the scene kernel, so the variant changes no result); single systems keep variant 0
@@ -2073,6 +2372,8 @@ gipc_status pcg_impl(gipc_ctx* ctx, const gipc_bsr* A, const double* rhs, double
         std::vector<SceneScalars> hz((size_t)nscenes);
         cudaMemcpyAsync(hz.data(), SS, sizeof(SceneScalars) * nscenes, cudaMemcpyDeviceToHost, st);
         if (cudaStreamSynchronize(st) != cudaSuccess) return check_launch("gipc_pcg: final sync");
+        if (hs.status == GIPC_ERR_TIMEOUT)
+            return fail(GIPC_ERR_TIMEOUT, "gipc_pcg: a grid barrier of the persistent batch solver timed out");
         int most = 0;
         bool nonfinite = false, short_of_tol = false;
         for (int k = 0; k < nscenes; ++k) {
@@ -2109,6 +2410,13 @@ extern "C" gipc_status gipc_pcg(gipc_ctx* ctx, const gipc_bsr* A, const double* 
                                 double* rel_out_h, void* stream) {
     return gipc::pcg_impl(ctx, A, rhs, x, fixed, prm, iters_out_h, rel_out_h, (cudaStream_t)stream, nullptr, 1, nullptr,
                           nullptr);
+}
+
+extern "C" gipc_status gipc_pcg_batch_persistent(gipc_ctx* ctx, int enable) {
+    using namespace gipc;
+    if (!ctx) return fail(GIPC_ERR_INVALID_ARG, "gipc_pcg_batch_persistent: null context");
+    ctx->batch_loop = enable != 0;
+    return GIPC_OK;
 }
 
 extern "C" gipc_status gipc_spmv_autotune(gipc_ctx* ctx, int enable) {

@@ -176,6 +176,8 @@ def test_product_variant_choice_changes_no_result(gipc, precision, hess_mode):
     # a tight solver tolerance, so the solves run whole chunks of iterations to time
     kw = dict(precision=precision, hess_mode=hess_mode, max_newton=12, pcg_tol=1e-10, max_pcg=400)
     on, off = gipc.Context(), gipc.Context()
+    for ctx in (on, off):   # the product kernel per iteration (the persistent batch solver has no variants)
+        ctx.batch_persistent(False)
     on.spmv_autotune(True)
     off.spmv_autotune(False)
     _, x1, v1, s1 = _batch(gipc, scenes, dhat, ctx=on, **kw)
@@ -194,3 +196,24 @@ def test_product_variant_choice_changes_no_result(gipc, precision, hess_mode):
             fastest = min(v["mean_us"] for v in t["variants"])
             assert t["variants"][t["chosen"]]["mean_us"] <= fastest * (1 + 1e-12)
     assert off.spmv_tunings() == []
+
+
+@pytest.mark.parametrize("precision,hess_mode", [("fp64", "dense"), ("mixed", "rank1")])
+def test_persistent_batch_solver_matches_the_per_iteration_kernels(gipc, precision, hess_mode):
+    """The batched solve as one persistent launch (rows spread over the CTAs by vertex, scenes cut
+    across CTAs, segmented dots) against the product + per-scene update kernels per iteration:
+    the same Newton and PCG iteration counts per scene and positions within the rounding of the
+    dots' summation order."""
+    scenes, dhat = _scenes(n=12, seed=9, vmax=2500)
+    kw = dict(precision=precision, hess_mode=hess_mode, max_newton=12)
+    per, loop = gipc.Context(), gipc.Context()
+    per.batch_persistent(False)
+    b, x1, v1, s1 = _batch(gipc, scenes, dhat, ctx=loop, **kw)
+    _, x2, v2, s2 = _batch(gipc, scenes, dhat, ctx=per, **kw)
+    for k, sc in enumerate(scenes):
+        assert s1[k]["newton_iters"] == s2[k]["newton_iters"], (k, s1[k], s2[k])
+        assert s1[k]["contacts"] == s2[k]["contacts"]
+        lo, hi = b.vert_off[k], b.vert_off[k + 1]
+        step = np.abs(x2[:, lo:hi] - sc["x"]).max()
+        rtol = 1e-7 if precision == "fp64" else 1e-5
+        assert np.abs(x1[:, lo:hi] - x2[:, lo:hi]).max() <= rtol * step + 1e-15, k
