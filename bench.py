@@ -732,6 +732,8 @@ def run_batch_bench(g, dev, ctx, steps):
                                "scene_newton_iters": its, "scene_newton_iters_one_at_a_time": its1,
                                "scene_newton_iters_per_step": per_step, "speedup": ms_p / ms_b,
                                "phase_ms_per_step": phases, "pcg_kernel_spans": pcg_spans,
+                               "solver": ("one persistent launch per solve" if "pcg_loop" in phases
+                                          else "a product and a per-scene update launch per iteration"),
                                "product_variant_tuning": tuning}
     return out
 

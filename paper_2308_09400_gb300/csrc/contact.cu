@@ -239,9 +239,21 @@ __global__ void target_boxes_kernel(const double* __restrict__ x, const double* 
     }
     // extent sums per scene (the cell size only steers the search): one scene -> one atomic per
     // warp; batched scenes -> one per target
-    if (vscene) {
-        if (t < m) {
-            const int32_t sc = vscene[prim[t]];
+    if (vscene) {   // the lists are ordered by scene: a warp whose targets share one scene adds once
+        const int32_t sc = t < m ? vscene[prim[t]] : -1;
+        const unsigned same = __match_any_sync(0xffffffffu, sc);
+        if (same == 0xffffffffu && sc >= 0) {
+            double c = 1.0, ex = ext;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                ex += __shfl_xor_sync(0xffffffffu, ex, o);
+                c += __shfl_xor_sync(0xffffffffu, c, o);
+            }
+            if ((threadIdx.x & 31) == 0) {
+                atomicAdd(ext_sum + sc, ex);
+                atomicAdd(ext_cnt + sc, c);
+            }
+        } else if (sc >= 0) {
             atomicAdd(ext_sum + sc, ext);
             atomicAdd(ext_cnt + sc, 1.0);
         }
@@ -309,7 +321,10 @@ __global__ void cells_count_kernel(const double* __restrict__ lo, const double* 
     box32(l, h, fl, fh);
     const int64_t c = box_cells(fl, fh, ih, c0, c1);
     cnt[t] = (int32_t)std::min<int64_t>(c, kMaxCellsPerBox + 1);
-    atomicMax(max_cells, (unsigned long long)c);
+    // one atomic per warp (counts are at most kMaxCellsPerBox + 1 after the saturation above)
+    const unsigned active = __activemask();
+    const unsigned wmax = __reduce_max_sync(active, (unsigned)std::min<int64_t>(c, kMaxCellsPerBox + 1));
+    if ((threadIdx.x & 31) == __ffs(active) - 1) atomicMax(max_cells, (unsigned long long)wmax);
 }
 
 // Swept point boxes of the surface vertices (CCD queries) only report their cell counts.
@@ -330,7 +345,9 @@ __global__ void point_cells_kernel(const double* __restrict__ x, const double* _
     float fl[3], fh[3];
     box32(l, h, fl, fh);
     const float ih = (float)inv_h[vscene ? vscene[p] : 0];
-    atomicMax(max_cells, (unsigned long long)box_cells(fl, fh, ih, c0, c1));
+    const unsigned active = __activemask();
+    const unsigned wmax = __reduce_max_sync(active, (unsigned)box_cells(fl, fh, ih, c0, c1));
+    if ((threadIdx.x & 31) == __ffs(active) - 1) atomicMax(max_cells, (unsigned long long)wmax);
 }
 
 // Insert target t into the bucket of each cell its box overlaps, at most once per bucket (two

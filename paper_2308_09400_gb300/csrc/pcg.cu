@@ -2306,7 +2306,7 @@ gipc_status pcg_impl(gipc_ctx* ctx, const gipc_bsr* A, const double* rhs, double
     // summed by the scene kernel, so the variant changes no result); single systems keep variant 0
     // Variants are timed over whole chunks of iterations (product and scene step, with the overlap
     // of consecutive launches), and only chunks after which the solve still runs count.
-    const int tune = (voff && !fp && ctx->spmv_autotune) ? spmv_tune_index(ctx, f64, A->nnzb) : -1;
+    const int tune = (voff && !fp && ctx->spmv_autotune && launched < max_iter) ? spmv_tune_index(ctx, f64, A->nnzb) : -1;
     while (launched < max_iter) {
         const int m = (max_iter - launched) < chunk ? (max_iter - launched) : chunk;
         const int var = tune >= 0 ? spmv_tune_pick(ctx->spmv_tunes[tune]) : 0;
