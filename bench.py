@@ -680,15 +680,19 @@ def run_batch_bench(g, dev, ctx, steps):
         x, v = b.scene.rest_x.clone(), T(v_init)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        marks = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
         e0.record()
         its = 0
-        per_step = []
-        for _ in range(steps):
+        per_step, longest = [], []
+        for i in range(steps):
             st = g.newton_step_batch(b, x, v, precision=prec, hess_mode=hm, **prm)
+            marks[i].record()
             per_step.append(sum(s["newton_iters"] for s in st))
+            longest.append(max(s["newton_iters"] for s in st))
         e1.record()
         torch.cuda.synchronize()
         ms_b = e0.elapsed_time(e1)
+        step_ms = [e0.elapsed_time(marks[0])] + [marks[i - 1].elapsed_time(marks[i]) for i in range(1, steps)]
         its = sum(per_step)
         # the same batched steps once more with the phase spans on (outside the timed region)
         xp, vp = b.scene.rest_x.clone(), T(v_init)
@@ -730,7 +734,9 @@ def run_batch_bench(g, dev, ctx, steps):
                                "one_at_a_time_ms_per_step": ms_p / steps,
                                "one_at_a_time_scene_iters_per_s": its1 / (ms_p * 1e-3),
                                "scene_newton_iters": its, "scene_newton_iters_one_at_a_time": its1,
-                               "scene_newton_iters_per_step": per_step, "speedup": ms_p / ms_b,
+                               "scene_newton_iters_per_step": per_step, "batched_iters_per_step": longest,
+                               "batched_ms_each_step": step_ms,
+                               "speedup": ms_p / ms_b,
                                "phase_ms_per_step": phases, "pcg_kernel_spans": pcg_spans,
                                "solver": ("one persistent launch per solve" if "pcg_loop" in phases
                                           else "a product and a per-scene update launch per iteration"),

@@ -495,13 +495,19 @@ struct StageRing {
 // 1.046 times the mean, and the 319 warps with a single slice spread over the CTAs).
 // DOT_FROM_CG: the row's part of c . q takes c from the gathered float32 direction (exactly the
 // float64 image c holds), so the float64 image need not be kept (the mixed persistent solver).
+// live(sl) (warp-uniform) tells whether slice sl is multiplied at all; a skipped slice leaves its
+// rows of q as they were and contributes nothing to the returned part.
+struct EverySlice {
+    __device__ __forceinline__ bool operator()(int64_t) const { return true; }
+};
+
 template <typename VT, typename PT, int U, int W, int NS, bool COHERENT, bool STRIDED = false,
-          bool DOT_FROM_CG = false>
+          bool DOT_FROM_CG = false, typename Live = EverySlice>
 __device__ __forceinline__ double spmv_slices(StageRing<VT, U, W, NS>& R, const int32_t* __restrict__ rowptr,
                                               const int64_t* __restrict__ slice_off, const int32_t* __restrict__ sell_col,
                                               const VT* __restrict__ sell_vals, const PT* cg, const double* c,
                                               const int32_t* __restrict__ perm, double* q, const uint8_t* __restrict__ fixed,
-                                              int64_t n, int64_t nsl, bool& timed_out) {
+                                              int64_t n, int64_t nsl, bool& timed_out, const Live& live = Live()) {
     using Lay = StageLayout<VT, U, W, NS>;
     constexpr bool kPrefetchGather = NS >= 3;
     const int lane = threadIdx.x & 31;
@@ -512,6 +518,10 @@ __device__ __forceinline__ double spmv_slices(StageRing<VT, U, W, NS>& R, const 
     for (int64_t rnd = 0; rnd * warps < nsl && !timed_out; ++rnd) {
         const int64_t sl = rnd * warps + ((rnd & 1) ? warps - 1 - wid : wid);
         if (sl >= nsl) continue;
+        if (!live(sl)) {
+            if (sl == R.pre_sl) R.drain();   // its leading groups were staged: let them land
+            continue;
+        }
         const int64_t off = slice_off[sl], Ls = slice_off[sl + 1] - off;
         const int64_t G = (Ls + U - 1) / U;
         const int64_t slot = sl * kSellC + lane;
@@ -1831,6 +1841,31 @@ __device__ __forceinline__ double scene_total(const double* part, const int64_t*
     return warp_sum(t);
 }
 
+// First and last scene of the rows of every kPermChunk-row chunk (a slice's rows all lie in one chunk).
+__global__ void chunk_scenes_kernel(const int64_t* __restrict__ voff, int nscenes, int64_t n, int64_t nchunks,
+                                    int2* __restrict__ out) {
+    const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= nchunks) return;
+    const int64_t a = w * kPermChunk, e = a + kPermChunk < n ? a + kPermChunk : n;
+    out[w] = make_int2(scene_of(voff, nscenes, a), scene_of(voff, nscenes, e - 1));
+}
+
+// A slice is multiplied while any scene its chunk touches still iterates.  A scene's flag is set
+// only between the last two barriers of an iteration and never cleared, so during the product
+// every warp of the grid reads the same flags, and a slice found stopped stays stopped.
+struct LiveSlice {
+    const int2* chunk_sc;
+    const SceneScalars* SS;
+    __device__ __forceinline__ bool operator()(int64_t sl) const {
+        int alive = 0;
+        if ((threadIdx.x & 31) == 0) {
+            const int2 w = chunk_sc[sl / (kPermChunk / kSellC)];
+            for (int s = w.x; s <= w.y && !alive; ++s) alive = !__ldcg(&SS[s].done);
+        }
+        return __shfl_sync(0xffffffffu, alive, 0) != 0;
+    }
+};
+
 template <typename VT, typename PT, int U, int NS, bool MIX>
 __global__ void __launch_bounds__(kLoopT, loop_min_blocks<VT, U, NS>())
 pcg_batch_loop_kernel(const int32_t* __restrict__ rowptr, const int64_t* __restrict__ slice_off,
@@ -1838,7 +1873,7 @@ pcg_batch_loop_kernel(const int32_t* __restrict__ rowptr, const int64_t* __restr
                       double* r, double* c, float* c32, double* q, double* s_buf, const double* __restrict__ fac,
                       const int32_t* __restrict__ perm, const uint8_t* __restrict__ fixed, int64_t n, int64_t nsl,
                       const int64_t* __restrict__ voff, int nscenes, SceneScalars* SS, PcgScalars* S, double* part_a,
-                      double* part_b, int iters, int64_t chunk) {
+                      double* part_b, int iters, int64_t chunk, const int2* __restrict__ chunk_sc) {
     using ST = FacT<MIX>;
     ST* const so = reinterpret_cast<ST*>(s_buf);
     __shared__ double val[kBKeep * kLoopT];
@@ -1868,33 +1903,38 @@ pcg_batch_loop_kernel(const int32_t* __restrict__ rowptr, const int64_t* __restr
     const double tol = S->tol;
     const int max_iter = S->max_iter;
     const int64_t first_sl = (int64_t)(t >> 5) * gridDim.x + blockIdx.x;
+    const LiveSlice live{chunk_sc, SS};
     StageRing<VT, U, kLoopW, NS> R;
     R.init();
-    R.preissue(first_sl, nsl, slice_off, sell_vals, sell_col);
+    if (first_sl < nsl && live(first_sl)) R.preissue(first_sl, nsl, slice_off, sell_vals, sell_col);
     unsigned nbar = 0;
     auto sync = [&]() { return grid_sync(&S->bar_count, ++nbar * gridDim.x, &S->status); };
     bool abort = false;
     for (int it = 0; it < iters; ++it) {
-        // A: q = S(H c)
+        // A: q = S(H c) over the slices of the scenes still iterating
         bool timed_out = false;
-        spmv_slices<VT, PT, U, kLoopW, NS, true, true>(R, rowptr, slice_off, sell_col, sell_vals, cg, c, perm, q, fixed,
-                                                       n, nsl, timed_out);
+        spmv_slices<VT, PT, U, kLoopW, NS, true, true, false, LiveSlice>(R, rowptr, slice_off, sell_col, sell_vals, cg,
+                                                                          c, perm, q, fixed, n, nsl, timed_out, live);
         if (timed_out) {
             R.drain_all();
             if (lane == 0) atomicExch(&S->status, GIPC_ERR_TIMEOUT);
-        } else {
+        } else if (first_sl < nsl && live(first_sl)) {
             R.preissue(first_sl, nsl, slice_off, sell_vals, sell_col);
         }
+        for (int j = t; j < nseg; j += kLoopT) seg_go[j] = !__ldcg(&SS[s0 + j].done);
         if (!sync()) {
             abort = true;
             break;
         }
-        // B1: the segments' parts of c . q
+        // B1: the segments' parts of c . q (zero for stopped scenes, whose rows of q are stale)
 #pragma unroll
         for (int k = 0; k < kBKeep; ++k) {
             const int li = t + k * kLoopT;
             const int64_t v = a + li;
-            if (v < e) val[li] = (c[3 * v] * q[3 * v] + c[3 * v + 1] * q[3 * v + 1]) + c[3 * v + 2] * q[3 * v + 2];
+            if (v < e)
+                val[li] = seg_go[myseg[k]]
+                              ? (c[3 * v] * q[3 * v] + c[3 * v + 1] * q[3 * v + 1]) + c[3 * v + 2] * q[3 * v + 2]
+                              : 0.0;
         }
         __syncthreads();
         segment_sums(val, seg_lo, nseg, seg_sum);
@@ -2271,13 +2311,17 @@ gipc_status pcg_impl(gipc_ctx* ctx, const gipc_bsr* A, const double* rhs, double
         const BatchPlan bp = f64 ? plan_batch<double, double, kU64, kNS64, false>(n, nsl)
                                  : plan_batch<float, float, kU32, kNS32, true>(n, nsl);
         if (bp.ok) {
-            if ((s = ctx->slot[P_BATCH].reserve(sizeof(double) * 2 * ((size_t)bp.grid + nscenes + 1) + 16)) != GIPC_OK)
+            const int64_t nchunks = (n + kPermChunk - 1) / kPermChunk;
+            if ((s = ctx->slot[P_BATCH].reserve(sizeof(double) * 2 * ((size_t)bp.grid + nscenes + 1) + 16 +
+                                                sizeof(int2) * (size_t)nchunks)) != GIPC_OK)
                 return s;
             double* part_a = ctx->slot[P_BATCH].as<double>();
             double* part_b = part_a + bp.grid + nscenes + 1;
             int* most = reinterpret_cast<int*>(part_b + bp.grid + nscenes + 1);
+            int2* chunk_sc = reinterpret_cast<int2*>(most + 4);
             cudaMemsetAsync(most, 0, sizeof(int), st);
             batch_segments_kernel<<<(bp.grid + 255) / 256, 256, 0, st>>>(voff, nscenes, n, bp.chunk, (int)bp.grid, most);
+            chunk_scenes_kernel<<<(unsigned)((nchunks + 255) / 256), 256, 0, st>>>(voff, nscenes, n, nchunks, chunk_sc);
             int most_h = 0;
             cudaMemcpyAsync(&most_h, most, sizeof(int), cudaMemcpyDeviceToHost, st);
             if (cudaStreamSynchronize(st) != cudaSuccess) return check_launch("gipc_pcg: batch plan");
@@ -2291,7 +2335,7 @@ gipc_status pcg_impl(gipc_ctx* ctx, const gipc_bsr* A, const double* rhs, double
                 const void* cg = f64 ? (const void*)c : (const void*)c32;
                 void* args[] = {&rp, &slice_off, &sell_col, &sell_vals, &cg, &xv, &r, &c, &c32, &q, &sv, &pinv, &perm,
                                 &fixed_arg, &n_arg, &nsl_arg, &voff, &ns_arg, &SS, &S, &part_a, &part_b, &iters_arg,
-                                &chunk_arg};
+                                &chunk_arg, &chunk_sc};
                 ctx->prof.start(GIPC_PROF_PCG_LOOP, st);
                 if (cudaLaunchCooperativeKernel(fn, dim3(bp.grid), dim3(kLoopT), args, bp.smem, st) != cudaSuccess)
                     return check_launch("gipc_pcg: persistent batch solver");
