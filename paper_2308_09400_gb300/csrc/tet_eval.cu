@@ -353,18 +353,42 @@ eval_tets_kernel(const double* __restrict__ x, int64_t n, const int32_t* __restr
                 const int l = 3 - i - j;
                 A[i][j] = A[j][i] = CT(2) * muc * sv[i] * sv[j] * ip2 + lamc * sv[l] * (CT(2) * sj - alc);
             }
-        CT Avec[3][3];
-        jacobi3(A, Avec);
+        // Where A is positive definite (the common case) its projection is A itself, and any
+        // factorisation A = sum_m d_m l_m l_m^T with d_m > 0 gives the same sum as the eigenpairs:
+        // sum_m d_m (U diag(l_m) z_a)(U diag(l_m) z_b)^T = U (A o z_a z_b^T) U^T.  A = L D L^T (unit
+        // lower L, no pivoting) exists with D > 0 exactly when A is positive definite; otherwise the
+        // eigenpairs come from the Jacobi iteration and the negative ones are dropped.
+        CT Lc[3][3] = {{CT(1), CT(0), CT(0)}, {CT(0), CT(1), CT(0)}, {CT(0), CT(0), CT(1)}};   // columns l_m
+        CT dm[3] = {A[0][0], CT(0), CT(0)};
+        bool pd = dm[0] > CT(0);
+        if (pd) {
+            const CT i0 = CT(1) / dm[0];
+            Lc[1][0] = A[1][0] * i0;
+            Lc[2][0] = A[2][0] * i0;
+            dm[1] = A[1][1] - Lc[1][0] * A[1][0];
+            pd = dm[1] > CT(0);
+            if (pd) {
+                const CT a21 = A[2][1] - Lc[2][0] * A[1][0];
+                Lc[2][1] = a21 / dm[1];
+                dm[2] = (A[2][2] - Lc[2][0] * A[2][0]) - Lc[2][1] * a21;
+                pd = dm[2] > CT(0);
+            }
+        }
+        if (!pd) {
+            jacobi3(A, Lc);
+#pragma unroll
+            for (int m = 0; m < 3; ++m) dm[m] = A[m][m];
+        }
 #pragma unroll
         for (int m = 0; m < 3; ++m) {
             CT w[3][3];
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                const CT g0 = Avec[0][m] * z[a][0], g1 = Avec[1][m] * z[a][1], g2 = Avec[2][m] * z[a][2];
+                const CT g0 = Lc[0][m] * z[a][0], g1 = Lc[1][m] * z[a][1], g2 = Lc[2][m] * z[a][2];
 #pragma unroll
                 for (int r = 0; r < 3; ++r) w[a][r] = U[r][0] * g0 + U[r][1] * g1 + U[r][2] * g2;
             }
-            add_mode_v(A[m][m], w);
+            add_mode_v(dm[m], w);
         }
     }
     // block (va, vb) entry (r, c) of the 12 x 12 matrix, vertices 0..3

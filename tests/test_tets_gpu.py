@@ -69,6 +69,42 @@ def test_eval_tets_fp64_parity(gipc, seed, invert):
     _compare({k: v.cpu().numpy() for k, v in g.items()}, ref, 1e-10)
 
 
+def _scaling_block_definite(x, tets, Dmi, mu, lam):
+    """Per element: is the 3x3 Hessian of the energy in the signed singular values positive
+    definite?  (Where it is, the kernel takes the projection of those modes from a triangular
+    factorisation, elsewhere from the eigenpairs.)"""
+    alpha = 1.0 + mu / lam - mu / (4.0 * lam)
+    out = []
+    for t in range(tets.shape[1]):
+        v = tets[:, t]
+        Ds = np.stack([x[:, v[a]] - x[:, v[0]] for a in (1, 2, 3)], axis=1)
+        F = Ds @ Dmi[:, t].reshape(3, 3)
+        s = np.linalg.svd(F, compute_uv=False)
+        if np.linalg.det(F) < 0:
+            s[2] = -s[2]
+        I2, J = (s * s).sum(), s.prod()
+        A = np.empty((3, 3))
+        for i in range(3):
+            j, l = (i + 1) % 3, (i + 2) % 3
+            A[i, i] = mu * (1 - 1 / (I2 + 1)) + 2 * mu * s[i] ** 2 / (I2 + 1) ** 2 + lam * (s[j] * s[l]) ** 2
+            A[i, j] = A[j, i] = 2 * mu * s[i] * s[j] / (I2 + 1) ** 2 + lam * s[l] * (2 * J - alpha)
+        out.append(np.linalg.eigvalsh(A).min() > 0)
+    return np.array(out)
+
+
+def test_eval_tets_fp64_parity_both_scaling_projections(gipc):
+    # a large smooth deformation: about half the elements have a definite scaling block
+    rest, x, tets = _mesh(4, amp=0.3)
+    mu, lam = O.snh_params(E, NU)
+    Dmi, vol, mass = O.rest_state(rest, tets, RHO)
+    pd = _scaling_block_definite(x, tets, Dmi, mu, lam)
+    assert pd.sum() >= 50 and (~pd).sum() >= 50
+    ref = O.eval_tets(x, tets, Dmi, vol, mu, lam, DT * DT)
+    g = gipc.eval_tets(_dev(x), _dev(tets), _dev(Dmi), _dev(vol), mu, lam, DT * DT)
+    torch.cuda.synchronize()
+    _compare({k: v.cpu().numpy() for k, v in g.items()}, ref, 1e-10)
+
+
 def test_rest_state_and_mass(gipc):
     rest, _, tets = _mesh(4)
     Dmi, vol, mass = O.rest_state(rest, tets, RHO)
