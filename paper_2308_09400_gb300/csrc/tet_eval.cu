@@ -50,11 +50,27 @@ __device__ __forceinline__ void jacobi_rot(CT (&a)[3][3], CT (&v)[3][3]) {
     constexpr int R = 3 - P - Q;
     const CT apq = a[P][Q];
     if (apq == CT(0)) return;
-    // t = sign(theta) / (|theta| + sqrt(theta^2 + 1)), theta = tau / rho, with numerator and
-    // denominator scaled by |rho| (one division instead of two)
+    // The angle phi (|phi| <= pi/4) with tan(2 phi) = rho / tau, tau = a_qq - a_pp, rho = 2 a_pq:
+    // cos(2 phi) = |tau| / h and sin(2 phi) = sign(tau) rho / h with h = sqrt(tau^2 + rho^2), and
+    // with u = cos^2(phi) = (1 + cos(2 phi)) / 2 in [1/2, 1]: t = tan(phi) = sin(2 phi) / (2 u),
+    // c = sqrt(u), s = t c.  Two reciprocal square roots and no division or square root (on
+    // GB300 each float64 division or square root is a sequence of several FP64 instructions).
+    // In float32 the same t comes from a division and a square root (cheap there, and exact for
+    // subnormal arguments, which the reciprocal square root is not).
     const CT tau = a[Q][Q] - a[P][P], rho = CT(2) * apq;
-    const CT t = (tau >= CT(0) ? rho : -rho) / (fabs(tau) + sqrt(tau * tau + rho * rho));
-    const CT c = rsqrt(t * t + CT(1));
+    const CT hh = tau * tau + rho * rho;
+    CT t, c;
+    if constexpr (std::is_same<CT, double>::value) {
+        if (!(hh > CT(0))) return;   // both below the square root of the smallest subnormal
+        const CT ih = rsqrt(hh);
+        const CT u = CT(0.5) + CT(0.5) * (fabs(tau) * ih);
+        const CT iu = rsqrt(u);
+        t = (CT(0.5) * ((tau >= CT(0) ? rho : -rho) * ih)) * (iu * iu);
+        c = u * iu;
+    } else {
+        t = (tau >= CT(0) ? rho : -rho) / (fabs(tau) + sqrt(hh));
+        c = rsqrt(t * t + CT(1));
+    }
     const CT s = t * c;
     a[P][P] -= t * apq;
     a[Q][Q] += t * apq;
@@ -125,10 +141,21 @@ __device__ void svd3(const CT (&F)[3][3], CT (&U)[3][3], CT (&s)[3], CT (&V)[3][
     for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int j = 0; j < 3; ++j) B[i][j] = F[i][0] * V[0][j] + F[i][1] * V[1][j] + F[i][2] * V[2][j];
+    // Column norm n and 1/n: in float64 as |b|^2 rsqrt(|b|^2) and rsqrt(|b|^2) (one FP64 sequence
+    // instead of a square root and a division), in float32 by a square root and a division.
+    auto norm_inv = [](CT nn, CT& nrm, CT& inv) {
+        if constexpr (std::is_same<CT, double>::value) {
+            inv = nn > CT(0) ? rsqrt(nn) : CT(0);
+            nrm = nn * inv;
+        } else {
+            nrm = sqrt(nn);
+            inv = nrm > CT(0) ? CT(1) / nrm : CT(0);
+        }
+    };
     CT u0[3] = {B[0][0], B[1][0], B[2][0]};
-    CT n0 = sqrt(u0[0] * u0[0] + u0[1] * u0[1] + u0[2] * u0[2]);
+    CT n0, i0;
+    norm_inv(u0[0] * u0[0] + u0[1] * u0[1] + u0[2] * u0[2], n0, i0);
     if (n0 > CT(0)) {
-        const CT i0 = CT(1) / n0;
 #pragma unroll
         for (int r = 0; r < 3; ++r) u0[r] *= i0;
     } else {
@@ -137,9 +164,9 @@ __device__ void svd3(const CT (&F)[3][3], CT (&U)[3][3], CT (&s)[3], CT (&V)[3][
     CT b1[3] = {B[0][1], B[1][1], B[2][1]};
     const CT p = u0[0] * b1[0] + u0[1] * b1[1] + u0[2] * b1[2];
     CT u1[3] = {b1[0] - p * u0[0], b1[1] - p * u0[1], b1[2] - p * u0[2]};
-    CT n1 = sqrt(u1[0] * u1[0] + u1[1] * u1[1] + u1[2] * u1[2]);
+    CT n1, i1;
+    norm_inv(u1[0] * u1[0] + u1[1] * u1[1] + u1[2] * u1[2], n1, i1);
     if (n1 > Num<CT>::tiny && n1 > Num<CT>::rel * n0) {
-        const CT i1 = CT(1) / n1;
 #pragma unroll
         for (int r = 0; r < 3; ++r) u1[r] *= i1;
     } else {  // any unit vector orthogonal to u0
@@ -184,11 +211,13 @@ __device__ __forceinline__ void map_to_x(const CT (&G)[3][3], const CT (&Dmi)[3]
     }
 }
 
-template <int PREC, int MODE>
+// The Hessian layout is a run-time flag (not a template parameter) so that both layouts run the
+// same compiled arithmetic and hold bit-identical values.
+template <int PREC>
 __global__ void __launch_bounds__(128)
 eval_tets_kernel(const double* __restrict__ x, int64_t n, const int32_t* __restrict__ tets, int64_t T,
                  const double* __restrict__ Dm_inv, const double* __restrict__ vol, const ElasticConst K,
-                 double* __restrict__ energy, double* __restrict__ grad, void* __restrict__ hess_v) {
+                 double* __restrict__ energy, double* __restrict__ grad, void* __restrict__ hess_v, bool blocks) {
     using HT = typename std::conditional<PREC == GIPC_FP64, double, float>::type;
     HT* __restrict__ hess = static_cast<HT*>(hess_v);
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -275,68 +304,32 @@ eval_tets_kernel(const double* __restrict__ x, int64_t n, const int32_t* __restr
     const CT m1c = (CT)m1, lJ = (CT)(K.lam * Jm), muc = (CT)K.mu, lamc = (CT)K.lam, alc = (CT)K.alpha;
     CT U[3][3], sv[3], V[3][3];
     svd3(Fc, U, sv, V);
-    // Modes in vertex blocks.  A mode's vector w (12 entries) has, for vertex a+1 (a = 0..2), the
-    // 3-vector Q Dm^-T e_a = U S z_a with Q = U S V^T and z_a = V^T (row a of Dm^-1), and minus
-    // their sum for vertex 0.  So only the blocks of vertices 1..3 are accumulated (l w_a w_b^T,
-    // a <= b, the diagonal ones as their 6 upper entries), and the blocks of vertex 0 follow
-    // from them at the end (H_0b = -sum_a H_ab, H_00 = -sum_b H_0b).
+    // Vertex blocks in the singular basis.  Mode m (F-space direction U D_m V^T) puts U D_m z_a on
+    // vertex a+1 (a = 0..2), z_a = V^T (row a of Dm^-1), and minus their sum on vertex 0, so the
+    // block of vertices a+1, b+1 is U M_ab U^T with M_ab = sum_m l_m+ D_m z_a z_b^T D_m^T.  With
+    // twist D = (e_i e_j^T - e_j e_i^T) / sqrt2, flip D = (e_i e_j^T + e_j e_i^T) / sqrt2 (pair i < j,
+    // k the third index) and the scaling modes D = diag(alpha_m):
+    //   M_ab[i][i] = Ah_ii za_i zb_i + sum_{j != i} sig_k(i,j) za_j zb_j
+    //   M_ab[i][j] = Ah_ij za_i zb_j + del_k(i,j) za_j zb_i                 (i != j)
+    // where sig_k = (lt+ + lf+) / 2, del_k = (lf+ - lt+) / 2 and Ah = sum_m l_m+ alpha_m alpha_m^T is
+    // the projected 3x3 scaling block.  Only the blocks of vertices 1..3 are formed (the diagonal
+    // ones as their 6 upper entries); those of vertex 0 follow from them at the end
+    // (H_0b = -sum_a H_ab, H_00 = -sum_b H_0b).
     CT z[3][3];   // z[a][i] = (V^T Dm^-T e_a)_i
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
         for (int i = 0; i < 3; ++i) z[a][i] = V[0][i] * Dc[a][0] + V[1][i] * Dc[a][1] + V[2][i] * Dc[a][2];
-    CT Bd[3][6], Bo[3][9];   // blocks (a,a) upper entries; blocks (0,1), (0,2), (1,2)
+    CT sg[3], dl[3];   // per pair, indexed by its third index k
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-#pragma unroll
-        for (int e = 0; e < 6; ++e) Bd[a][e] = CT(0);
-#pragma unroll
-        for (int e = 0; e < 9; ++e) Bo[a][e] = CT(0);
+    for (int k = 0; k < 3; ++k) {
+        const CT lt = CT(0.5) * (m1c + lJ * sv[k]), lf = CT(0.5) * (m1c - lJ * sv[k]);
+        const CT pt = lt > CT(0) ? lt : CT(0), pf = lf > CT(0) ? lf : CT(0);
+        sg[k] = pt + pf;
+        dl[k] = pf - pt;
     }
-    auto add_mode_v = [&](CT lam, const CT (&w)[3][3]) {   // w[a][r]: vertex a+1's component r
-        if (!(lam > CT(0))) return;
-        CT tl[3][3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-#pragma unroll
-            for (int r = 0; r < 3; ++r) tl[a][r] = lam * w[a][r];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            int e = 0;
-#pragma unroll
-            for (int r = 0; r < 3; ++r)
-#pragma unroll
-                for (int c = r; c < 3; ++c) Bd[a][e++] += tl[a][r] * w[a][c];
-        }
-#pragma unroll
-        for (int o = 0; o < 3; ++o) {
-            const int a = o == 2 ? 1 : 0, b = o == 0 ? 1 : 2;
-#pragma unroll
-            for (int r = 0; r < 3; ++r)
-#pragma unroll
-                for (int c = 0; c < 3; ++c) Bo[o][3 * r + c] += tl[a][r] * w[b][c];
-        }
-    };
-    // twist / flip modes for the pairs (1,2), (0,2), (0,1): w = (u_i z_a[j] -+ u_j z_a[i]) / sqrt 2,
-    // the 1/2 of the square taken into the eigenvalue
-#pragma unroll
-    for (int kk = 0; kk < 3; ++kk) {
-        const int i = kk == 0 ? 1 : 0, j = kk == 2 ? 1 : 2;
-        const CT lt = CT(0.5) * (m1c + lJ * sv[kk]);
-        const CT lf = CT(0.5) * (m1c - lJ * sv[kk]);
-        CT wt[3][3], wf[3][3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-#pragma unroll
-            for (int r = 0; r < 3; ++r) {
-                const CT p = U[r][i] * z[a][j], q = U[r][j] * z[a][i];
-                wt[a][r] = p - q;
-                wf[a][r] = p + q;
-            }
-        add_mode_v(lt, wt);
-        add_mode_v(lf, wf);
-    }
-    // scaling modes: eigenpairs (l, alpha) of A = d2 Psi / ds ds, w = U diag(alpha) z_a
+    // the scaling block A = d2 Psi / ds ds and its projection Ah
+    CT Ah[3][3];
     {
         CT A[3][3];
         const CT ip2 = (CT)(ip1 * ip1);
@@ -353,43 +346,77 @@ eval_tets_kernel(const double* __restrict__ x, int64_t n, const int32_t* __restr
                 const int l = 3 - i - j;
                 A[i][j] = A[j][i] = CT(2) * muc * sv[i] * sv[j] * ip2 + lamc * sv[l] * (CT(2) * sj - alc);
             }
-        // Where A is positive definite (the common case) its projection is A itself, and any
-        // factorisation A = sum_m d_m l_m l_m^T with d_m > 0 gives the same sum as the eigenpairs:
-        // sum_m d_m (U diag(l_m) z_a)(U diag(l_m) z_b)^T = U (A o z_a z_b^T) U^T.  A = L D L^T (unit
-        // lower L, no pivoting) exists with D > 0 exactly when A is positive definite; otherwise the
-        // eigenpairs come from the Jacobi iteration and the negative ones are dropped.
-        CT Lc[3][3] = {{CT(1), CT(0), CT(0)}, {CT(0), CT(1), CT(0)}, {CT(0), CT(0), CT(1)}};   // columns l_m
-        CT dm[3] = {A[0][0], CT(0), CT(0)};
-        bool pd = dm[0] > CT(0);
+        // Positive definite (the common case; A = L D L^T with D > 0 exists, unit lower L, no
+        // pivoting): the projection is A itself.  Otherwise the eigenpairs from the Jacobi
+        // iteration, the negative ones dropped.
+        bool pd = A[0][0] > CT(0);
         if (pd) {
-            const CT i0 = CT(1) / dm[0];
-            Lc[1][0] = A[1][0] * i0;
-            Lc[2][0] = A[2][0] * i0;
-            dm[1] = A[1][1] - Lc[1][0] * A[1][0];
-            pd = dm[1] > CT(0);
-            if (pd) {
-                const CT a21 = A[2][1] - Lc[2][0] * A[1][0];
-                Lc[2][1] = a21 / dm[1];
-                dm[2] = (A[2][2] - Lc[2][0] * A[2][0]) - Lc[2][1] * a21;
-                pd = dm[2] > CT(0);
-            }
+            const CT l10 = A[1][0] / A[0][0];
+            const CT d1 = A[1][1] - l10 * A[1][0];
+            pd = d1 > CT(0) && (A[2][2] - A[2][0] * (A[2][0] / A[0][0])) -
+                                       (A[2][1] - l10 * A[2][0]) * ((A[2][1] - l10 * A[2][0]) / d1) > CT(0);
         }
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) Ah[i][j] = A[i][j];
         if (!pd) {
-            jacobi3(A, Lc);
+            CT Avec[3][3];
+            jacobi3(A, Avec);
 #pragma unroll
-            for (int m = 0; m < 3; ++m) dm[m] = A[m][m];
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int j = i; j < 3; ++j) {
+                    CT h = CT(0);
+#pragma unroll
+                    for (int m = 0; m < 3; ++m)
+                        if (A[m][m] > CT(0)) h += A[m][m] * (Avec[i][m] * Avec[j][m]);
+                    Ah[i][j] = Ah[j][i] = h;
+                }
         }
+    }
+    // M_ab, then U M_ab U^T
+    auto m_ab = [&](int a, int b, CT (&M)[3][3]) {
 #pragma unroll
-        for (int m = 0; m < 3; ++m) {
-            CT w[3][3];
+        for (int i = 0; i < 3; ++i)
 #pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                const CT g0 = Lc[0][m] * z[a][0], g1 = Lc[1][m] * z[a][1], g2 = Lc[2][m] * z[a][2];
-#pragma unroll
-                for (int r = 0; r < 3; ++r) w[a][r] = U[r][0] * g0 + U[r][1] * g1 + U[r][2] * g2;
+            for (int j = 0; j < 3; ++j) {
+                if (i == j) {
+                    const int j1 = (i + 1) % 3, j2 = (i + 2) % 3;   // the pairs (i, j1), (i, j2): third index j2, j1
+                    M[i][i] = Ah[i][i] * (z[a][i] * z[b][i]) + sg[j2] * (z[a][j1] * z[b][j1]) + sg[j1] * (z[a][j2] * z[b][j2]);
+                } else {
+                    M[i][j] = Ah[i][j] * (z[a][i] * z[b][j]) + dl[3 - i - j] * (z[a][j] * z[b][i]);
+                }
             }
-            add_mode_v(dm[m], w);
-        }
+    };
+    CT Bd[3][6], Bo[3][9];   // blocks (a,a) upper entries; blocks (0,1), (0,2), (1,2)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        CT M[3][3], T[3][3];
+        m_ab(a, a, M);
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) T[r][j] = U[r][0] * M[0][j] + U[r][1] * M[1][j] + U[r][2] * M[2][j];
+        int e = 0;
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = r; c < 3; ++c) Bd[a][e++] = T[r][0] * U[c][0] + T[r][1] * U[c][1] + T[r][2] * U[c][2];
+    }
+#pragma unroll
+    for (int o = 0; o < 3; ++o) {
+        const int a = o == 2 ? 1 : 0, b = o == 0 ? 1 : 2;
+        CT M[3][3], T[3][3];
+        m_ab(a, b, M);
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) T[r][j] = U[r][0] * M[0][j] + U[r][1] * M[1][j] + U[r][2] * M[2][j];
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) Bo[o][3 * r + c] = T[r][0] * U[c][0] + T[r][1] * U[c][1] + T[r][2] * U[c][2];
     }
     // block (va, vb) entry (r, c) of the 12 x 12 matrix, vertices 0..3
     auto blk = [&](int a, int b, int r, int c) -> CT {   // vertices 1..3 as a, b = 0..2
@@ -415,17 +442,20 @@ eval_tets_kernel(const double* __restrict__ x, int64_t n, const int32_t* __restr
         return blk(va - 1, vb - 1, r, c);
     };
     const CT kc = (CT)k;
+    // entry (a, b) at base + slot(a, b) * stride: element-major 3x3 sub-blocks (slot = its place
+    // among the element's 144 values, stride 1) or entry-major (slot = 12 a + b, stride T)
+    HT* const base = blocks ? hess + t * 144 : hess + t;
+    const int64_t stride = blocks ? 1 : T;
 #pragma unroll
     for (int a = 0; a < 12; ++a)
 #pragma unroll
         for (int b = 0; b <= a; ++b) {
             const HT h = kc * hval(a, b);
-            if (MODE == GIPC_HESS_BLOCKS) {   // element-major 3x3 sub-blocks
-                hess[(t * 16 + (a / 3) * 4 + b / 3) * 9 + (a % 3) * 3 + b % 3] = h;
-                if (a != b) hess[(t * 16 + (b / 3) * 4 + a / 3) * 9 + (b % 3) * 3 + a % 3] = h;
-            } else {
-                hess[(int64_t)(a * 12 + b) * T + t] = h;
-                if (a != b) hess[(int64_t)(b * 12 + a) * T + t] = h;
+            const int sab = blocks ? ((a / 3) * 4 + b / 3) * 9 + (a % 3) * 3 + b % 3 : a * 12 + b;
+            base[sab * stride] = h;
+            if (a != b) {
+                const int sba = blocks ? ((b / 3) * 4 + a / 3) * 9 + (b % 3) * 3 + a % 3 : b * 12 + a;
+                base[sba * stride] = h;
             }
         }
 }
@@ -588,13 +618,9 @@ extern "C" gipc_status gipc_eval_tets(const double* x, int64_t n, const int32_t*
     ElasticConst K{prm->mu, prm->lambda, 1.0 + prm->mu / prm->lambda - prm->mu / (4.0 * prm->lambda), prm->scale};
     cudaStream_t st = (cudaStream_t)stream;
     const bool blk = hess_mode == GIPC_HESS_BLOCKS;
-    if (prec == GIPC_FP64 && blk)
-        eval_tets_kernel<GIPC_FP64, GIPC_HESS_BLOCKS><<<nb(T, 128), 128, 0, st>>>(x, n, tets, T, Dm_inv, vol, K, energy, grad, hess);
-    else if (prec == GIPC_FP64)
-        eval_tets_kernel<GIPC_FP64, GIPC_HESS_DENSE><<<nb(T, 128), 128, 0, st>>>(x, n, tets, T, Dm_inv, vol, K, energy, grad, hess);
-    else if (blk)
-        eval_tets_kernel<GIPC_MIXED, GIPC_HESS_BLOCKS><<<nb(T, 128), 128, 0, st>>>(x, n, tets, T, Dm_inv, vol, K, energy, grad, hess);
+    if (prec == GIPC_FP64)
+        eval_tets_kernel<GIPC_FP64><<<nb(T, 128), 128, 0, st>>>(x, n, tets, T, Dm_inv, vol, K, energy, grad, hess, blk);
     else
-        eval_tets_kernel<GIPC_MIXED, GIPC_HESS_DENSE><<<nb(T, 128), 128, 0, st>>>(x, n, tets, T, Dm_inv, vol, K, energy, grad, hess);
+        eval_tets_kernel<GIPC_MIXED><<<nb(T, 128), 128, 0, st>>>(x, n, tets, T, Dm_inv, vol, K, energy, grad, hess, blk);
     return check_launch("gipc_eval_tets");
 }
