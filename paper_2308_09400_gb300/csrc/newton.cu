@@ -23,6 +23,9 @@ gipc_status ccd_impl(gipc_ctx* ctx, const double* x, const double* d, int64_t n,
                      double* alpha_h, cudaStream_t st, const int32_t* vscene, int nscenes, double* amin_dev,
                      bool cached);
 gipc_status stencil_type_order(const int32_t* stencils, int64_t k, int32_t* order, unsigned* counts, cudaStream_t s);
+gipc_status eval_tets_live(const double* x, int64_t n, const int32_t* tets, int64_t T, const double* Dm_inv,
+                           const double* vol, const gipc_elastic_params* prm, int prec, int hess_mode, double* energy,
+                           double* grad, void* hess, const int32_t* vscene, const int32_t* live, cudaStream_t stream);
 gipc_status eval_stencils_ordered(const double* x, int64_t n, const int32_t* stencils, int64_t k,
                                   const double* eps_x, const gipc_barrier_params* prm, int prec, int mode,
                                   double* energy, double* grad, void* hess, double* lam, uint8_t* flags,
@@ -453,8 +456,13 @@ scene_energy_kernel(const double* __restrict__ x, const double* __restrict__ xt,
                     int64_t n, const int64_t* __restrict__ voff, const int32_t* __restrict__ tets, int64_t T,
                     const double* __restrict__ te, const int32_t* __restrict__ st, int64_t k, int64_t npt,
                     const double* __restrict__ se, const int32_t* __restrict__ vs, double* __restrict__ I,
-                    int64_t* __restrict__ contacts) {
+                    int64_t* __restrict__ contacts, const int32_t* __restrict__ live) {
     const int sc = blockIdx.x;
+    int64_t l1, h1, l2, h2;
+    scene_range<true>(st, 0, npt, vs, sc, l1, h1);
+    scene_range<true>(st, npt, k, vs, sc, l2, h2);
+    if (threadIdx.x == 0 && contacts) contacts[sc] = (h1 - l1) + (h2 - l2);
+    if (live && !live[sc]) return;   // (uniform in the block) I[sc] keeps its value
     double a = 0.0;
     for (int64_t i = voff[sc] + threadIdx.x; i < voff[sc + 1]; i += blockDim.x) {
         const double dx = __dsub_rn(x[i], xt[i]), dy = __dsub_rn(x[n + i], xt[n + i]), dz = __dsub_rn(x[2 * n + i], xt[2 * n + i]);
@@ -466,17 +474,11 @@ scene_energy_kernel(const double* __restrict__ x, const double* __restrict__ xt,
     a = 0.0;
     for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) a = __dadd_rn(a, te[i]);
     const double elastic = bsum_all(a);
-    int64_t l1, h1, l2, h2;
-    scene_range<true>(st, 0, npt, vs, sc, l1, h1);
-    scene_range<true>(st, npt, k, vs, sc, l2, h2);
     a = 0.0;
     for (int64_t i = l1 + threadIdx.x; i < h1; i += blockDim.x) a = __dadd_rn(a, se[i]);
     for (int64_t i = l2 + threadIdx.x; i < h2; i += blockDim.x) a = __dadd_rn(a, se[i]);
     const double barrier = bsum_all(a);
-    if (threadIdx.x == 0) {
-        I[sc] = __dadd_rn(__dadd_rn(__dmul_rn(0.5, inertia), elastic), barrier);
-        if (contacts) contacts[sc] = (h1 - l1) + (h2 - l2);
-    }
+    if (threadIdx.x == 0) I[sc] = __dadd_rn(__dadd_rn(__dmul_rn(0.5, inertia), elastic), barrier);
 }
 
 // Per-scene max |d| over the scene's vertices.
@@ -613,7 +615,8 @@ struct BatchStep {
     double *x0 = nullptr, *xt_full = nullptr, *xp = nullptr, *d = nullptr, *g = nullptr, *rhs = nullptr, *gb = nullptr;
     double *sI = nullptr, *sA = nullptr, *sD = nullptr;
     int64_t* sC = nullptr;
-    int32_t* sAct = nullptr;
+    int32_t* sAct = nullptr;      // device [ns] scenes still iterating
+    int32_t* sSearch = nullptr;   // device [ns] scenes still searching along their step
     uint8_t* mask = nullptr;
     ContactSet set[2];
     // element ranges of every original scene (host) for packing
@@ -640,8 +643,8 @@ struct BatchStep {
 
     gipc_status scene_scalars() {
         gipc_status s;
-        if ((s = ctx->slot[W_S].reserve(sizeof(double) * 3 * ns + sizeof(int64_t) * (2 * ns + 2) + sizeof(int32_t) * (ns + 4) +
-                                        64)) != GIPC_OK)
+        if ((s = ctx->slot[W_S].reserve(sizeof(double) * 3 * ns + sizeof(int64_t) * (2 * ns + 2) +
+                                        sizeof(int32_t) * (2 * ns + 6) + 64)) != GIPC_OK)
             return s;
         sI = ctx->slot[W_S].as<double>();
         sA = sI + ns;
@@ -649,6 +652,7 @@ struct BatchStep {
         sC = reinterpret_cast<int64_t*>(sD + ns);
         voff = sC + ns;
         sAct = reinterpret_cast<int32_t*>(voff + ns + 2);
+        sSearch = sAct + ns + 2;   // (sAct[ns] is the layout check's flag)
         return GIPC_OK;
     }
 
@@ -668,8 +672,10 @@ struct BatchStep {
         return fail(GIPC_ERR_CUDA, "gipc_newton_step_batch: contact count changed between passes");
     }
 
-    // per-scene I(x) into I_out (host) and the contacts at x
-    gipc_status potential_b(const double* xc, ContactSet& cs, int64_t* npt, std::vector<double>& I_out) {
+    // per-scene I(x) into I_out (host) and the contacts at x; with `live` (device, per scene) the
+    // energies of the other scenes are neither evaluated nor changed (their contacts still are)
+    gipc_status potential_b(const double* xc, ContactSet& cs, int64_t* npt, std::vector<double>& I_out,
+                            const int32_t* live = nullptr) {
         gipc_status s;
         if ((s = contacts_b(xc, cs, npt)) != GIPC_OK) return s;
         const int64_t T = sc.T, k = cs.k;
@@ -679,12 +685,14 @@ struct BatchStep {
         double* se = te + T;
         gipc_elastic_params ep = prm.elastic;
         ep.scale = prm.dt * prm.dt;
-        if ((s = gipc_eval_tets(xc, n, sc.tets, T, sc.Dm_inv, sc.vol, &ep, GIPC_FP64, GIPC_HESS_DENSE, te, nullptr, nullptr, st)) != GIPC_OK)
+        if ((s = eval_tets_live(xc, n, sc.tets, T, sc.Dm_inv, sc.vol, &ep, GIPC_FP64, GIPC_HESS_DENSE, te, nullptr, nullptr,
+                                vs, live, st)) != GIPC_OK)
             return s;
         if (k > 0 && (s = eval_stencils_ordered(xc, n, cs.st, k, cs.eps, &prm.barrier, GIPC_FP64, GIPC_HESS_DENSE, se, nullptr,
                                                 nullptr, nullptr, nullptr, cs.order, st)) != GIPC_OK)
             return s;
-        scene_energy_kernel<<<ns, 256, 0, st>>>(xc, xt, sc.mass, n, voff, sc.tets, T, te, cs.st, k, *npt, se, vs, sI, sC);
+        scene_energy_kernel<<<ns, 256, 0, st>>>(xc, xt, sc.mass, n, voff, sc.tets, T, te, cs.st, k, *npt, se, vs, sI, sC,
+                                                live);
         cudaMemcpyAsync(I_out.data(), sI, sizeof(double) * ns, cudaMemcpyDeviceToHost, st);
         cudaMemcpyAsync(cont_h.data(), sC, sizeof(int64_t) * ns, cudaMemcpyDeviceToHost, st);
         if (cudaStreamSynchronize(st) != cudaSuccess) return check_launch("gipc_newton_step_batch: energy");
@@ -921,13 +929,17 @@ struct BatchStep {
             const int64_t k = A.k;
             const int64_t m3 = 3 * n;
             const int T = (int)sc.T;
+            // the scenes still iterating: the others' elements give zero gradient and Hessian (their
+            // directions are filtered out below), so they are not evaluated
+            cudaMemcpyAsync(sAct, active_h.data(), sizeof(int32_t) * ns, cudaMemcpyHostToDevice, st);
             ctx->prof.start(GIPC_PROF_ELEMENTS, st);
             if ((s = ctx->slot[N_TEVAL].reserve(sizeof(double) * 12 * T + hb * 144 * T + 16)) != GIPC_OK) return s;
             double* tg = ctx->slot[N_TEVAL].as<double>();
             void* th = tg + 12 * (int64_t)T;
             gipc_elastic_params ep = prm.elastic;
             ep.scale = dt * dt;
-            if ((s = gipc_eval_tets(x, n, sc.tets, T, sc.Dm_inv, sc.vol, &ep, prm.prec, GIPC_HESS_DENSE, nullptr, tg, th, st)) != GIPC_OK)
+            if ((s = eval_tets_live(x, n, sc.tets, T, sc.Dm_inv, sc.vol, &ep, prm.prec, GIPC_HESS_DENSE, nullptr, tg, th, vs,
+                                    sAct, st)) != GIPC_OK)
                 return s;
             const bool rank1 = prm.hess_mode == GIPC_HESS_RANK1;
             const int64_t hper = rank1 ? 12 : 144;
@@ -962,7 +974,6 @@ struct BatchStep {
             }
             if (s != GIPC_OK) return s;
             // directions of the scenes still iterating; stopped scenes are filtered out (d = 0)
-            cudaMemcpyAsync(sAct, active_h.data(), sizeof(int32_t) * ns, cudaMemcpyHostToDevice, st);
             scene_mask_kernel<<<nb(n, 256), 256, 0, st>>>(sc.fixed, vs, sAct, n, mask);
             negate_kernel<<<nb(m3, 256), 256, 0, st>>>(g, m3, rhs);
             cudaMemsetAsync(d, 0, sizeof(double) * m3, st);
@@ -977,10 +988,14 @@ struct BatchStep {
             }
             cudaMemcpyAsync(xp, x, sizeof(double) * m3, cudaMemcpyDeviceToDevice, st);
             const int nxt = 1 - cur;
+            std::vector<int32_t> searching(ns);
             for (int ls = 0; ls < std::max(prm.max_ls, 1); ++ls) {
+                // the energies of the scenes still searching (an accepted scene's x stays as it is)
+                for (int q = 0; q < ns; ++q) searching[q] = accepted[q] ? 0 : 1;
+                cudaMemcpyAsync(sSearch, searching.data(), sizeof(int32_t) * ns, cudaMemcpyHostToDevice, st);
                 cudaMemcpyAsync(sA, alpha_h.data(), sizeof(double) * ns, cudaMemcpyHostToDevice, st);
                 axpy_scene_kernel<<<nb(m3, 256), 256, 0, st>>>(xp, d, sA, vs, n, x);
-                if ((s = potential_b(x, set[nxt], &npt_nxt, Inew_h)) != GIPC_OK) return s;
+                if ((s = potential_b(x, set[nxt], &npt_nxt, Inew_h, sSearch)) != GIPC_OK) return s;
                 bool all = true;
                 for (int q = 0; q < ns; ++q) {
                     if (accepted[q]) continue;

@@ -212,12 +212,14 @@ __device__ __forceinline__ void map_to_x(const CT (&G)[3][3], const CT (&Dmi)[3]
 }
 
 // The Hessian layout is a run-time flag (not a template parameter) so that both layouts run the
-// same compiled arithmetic and hold bit-identical values.
+// same compiled arithmetic and hold bit-identical values.  With `live` (per scene, the scene of
+// each vertex in vscene) the elements of scenes left out get zero outputs without evaluation.
 template <int PREC>
 __global__ void __launch_bounds__(128)
 eval_tets_kernel(const double* __restrict__ x, int64_t n, const int32_t* __restrict__ tets, int64_t T,
                  const double* __restrict__ Dm_inv, const double* __restrict__ vol, const ElasticConst K,
-                 double* __restrict__ energy, double* __restrict__ grad, void* __restrict__ hess_v, bool blocks) {
+                 double* __restrict__ energy, double* __restrict__ grad, void* __restrict__ hess_v, bool blocks,
+                 const int32_t* __restrict__ vscene, const int32_t* __restrict__ live) {
     using HT = typename std::conditional<PREC == GIPC_FP64, double, float>::type;
     HT* __restrict__ hess = static_cast<HT*>(hess_v);
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -231,6 +233,19 @@ eval_tets_kernel(const double* __restrict__ x, int64_t n, const int32_t* __restr
     }
     if (!ok) {
         if (energy) energy[t] = 0.0;
+        return;
+    }
+    if (live && !live[vscene[vid[0]]]) {
+        if (energy) energy[t] = 0.0;
+        if (grad) {
+#pragma unroll
+            for (int j = 0; j < 12; ++j) grad[j * T + t] = 0.0;
+        }
+        if (hess) {
+            HT* const z0 = blocks ? hess + t * 144 : hess + t;
+            const int64_t zs = blocks ? 1 : T;
+            for (int j = 0; j < 144; ++j) z0[j * zs] = HT(0);
+        }
         return;
     }
     double X[4][3];
@@ -603,10 +618,12 @@ extern "C" gipc_status gipc_tet_rest(gipc_ctx* ctx, const double* rest_x, int64_
     return check_launch("gipc_tet_rest");
 }
 
-extern "C" gipc_status gipc_eval_tets(const double* x, int64_t n, const int32_t* tets, int64_t T, const double* Dm_inv,
-                                      const double* vol, const gipc_elastic_params* prm, int prec, int hess_mode,
-                                      double* energy, double* grad, void* hess, void* stream) {
-    using namespace gipc;
+namespace gipc {
+// gipc_eval_tets, the elements of the scenes s with live[s] == 0 (vscene: the scene of every
+// vertex) left out with zero outputs; live == NULL evaluates every element.
+gipc_status eval_tets_live(const double* x, int64_t n, const int32_t* tets, int64_t T, const double* Dm_inv,
+                           const double* vol, const gipc_elastic_params* prm, int prec, int hess_mode, double* energy,
+                           double* grad, void* hess, const int32_t* vscene, const int32_t* live, cudaStream_t stream) {
     if (n < 0 || T < 0) return fail(GIPC_ERR_INVALID_ARG, "gipc_eval_tets: negative size");
     if (!prm || !(prm->mu > 0.0) || !(prm->lambda > 0.0) || !(prm->scale >= 0.0))
         return fail(GIPC_ERR_INVALID_ARG, "gipc_eval_tets: need mu > 0, lambda > 0, scale >= 0");
@@ -616,11 +633,22 @@ extern "C" gipc_status gipc_eval_tets(const double* x, int64_t n, const int32_t*
     if (T == 0) return GIPC_OK;
     if (!x || !tets || !Dm_inv || !vol) return fail(GIPC_ERR_INVALID_ARG, "gipc_eval_tets: null input");
     ElasticConst K{prm->mu, prm->lambda, 1.0 + prm->mu / prm->lambda - prm->mu / (4.0 * prm->lambda), prm->scale};
-    cudaStream_t st = (cudaStream_t)stream;
+    cudaStream_t st = stream;
     const bool blk = hess_mode == GIPC_HESS_BLOCKS;
+    if (live && !vscene) return fail(GIPC_ERR_INVALID_ARG, "gipc_eval_tets: scene mask without the vertex scenes");
     if (prec == GIPC_FP64)
-        eval_tets_kernel<GIPC_FP64><<<nb(T, 128), 128, 0, st>>>(x, n, tets, T, Dm_inv, vol, K, energy, grad, hess, blk);
+        eval_tets_kernel<GIPC_FP64><<<nb(T, 128), 128, 0, st>>>(x, n, tets, T, Dm_inv, vol, K, energy, grad, hess, blk,
+                                                                 vscene, live);
     else
-        eval_tets_kernel<GIPC_MIXED><<<nb(T, 128), 128, 0, st>>>(x, n, tets, T, Dm_inv, vol, K, energy, grad, hess, blk);
+        eval_tets_kernel<GIPC_MIXED><<<nb(T, 128), 128, 0, st>>>(x, n, tets, T, Dm_inv, vol, K, energy, grad, hess, blk,
+                                                                  vscene, live);
     return check_launch("gipc_eval_tets");
+}
+}  // namespace gipc
+
+extern "C" gipc_status gipc_eval_tets(const double* x, int64_t n, const int32_t* tets, int64_t T, const double* Dm_inv,
+                                      const double* vol, const gipc_elastic_params* prm, int prec, int hess_mode,
+                                      double* energy, double* grad, void* hess, void* stream) {
+    return gipc::eval_tets_live(x, n, tets, T, Dm_inv, vol, prm, prec, hess_mode, energy, grad, hess, nullptr, nullptr,
+                                (cudaStream_t)stream);
 }
