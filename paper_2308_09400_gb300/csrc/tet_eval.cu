@@ -120,7 +120,59 @@ __device__ void svd3(const CT (&F)[3][3], CT (&U)[3][3], CT (&s)[3], CT (&V)[3][
 #pragma unroll
         for (int j = 0; j < 3; ++j) S[i][j] = F[0][i] * F[0][j] + F[1][i] * F[1][j] + F[2][i] * F[2][j];
     CT W[3][3];
-    jacobi3(S, W);
+    if constexpr (std::is_same<CT, double>::value) {
+        // float32 pre-rotation: Jacobi in float32 (on the FP32 pipe) gives eigenvectors to about
+        // 1e-7; made orthonormal again in float64 they turn S into W0^T S W0 with off-diagonal
+        // entries of about 1e-7 |S|, which the float64 sweeps (quadratically convergent) finish in
+        // one or two sweeps instead of three or four.  Outside float32's range: no pre-rotation.
+        CT W0[3][3] = {{1.0, 0.0, 0.0}, {0.0, 1.0, 0.0}, {0.0, 0.0, 1.0}};
+        const float tr = (float)((S[0][0] + S[1][1]) + S[2][2]);
+        if (tr > 1e-30f && tr < 1e30f) {
+            float Sf[3][3], Wf[3][3];
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int j = 0; j < 3; ++j) Sf[i][j] = (float)S[i][j];
+            jacobi3(Sf, Wf);
+            // Gram-Schmidt on the columns in float64, third column as the cross product
+            CT a0[3] = {Wf[0][0], Wf[1][0], Wf[2][0]}, a1[3] = {Wf[0][1], Wf[1][1], Wf[2][1]}, a2[3];
+            const CT i0 = rsqrt(a0[0] * a0[0] + a0[1] * a0[1] + a0[2] * a0[2]);
+#pragma unroll
+            for (int r = 0; r < 3; ++r) a0[r] *= i0;
+            const CT p01 = a0[0] * a1[0] + a0[1] * a1[1] + a0[2] * a1[2];
+#pragma unroll
+            for (int r = 0; r < 3; ++r) a1[r] -= p01 * a0[r];
+            const CT i1 = rsqrt(a1[0] * a1[0] + a1[1] * a1[1] + a1[2] * a1[2]);
+#pragma unroll
+            for (int r = 0; r < 3; ++r) a1[r] *= i1;
+            cross(a0, a1, a2);
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                W0[r][0] = a0[r];
+                W0[r][1] = a1[r];
+                W0[r][2] = a2[r];
+            }
+            // S <- W0^T S W0 (symmetric)
+            CT T[3][3];
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int j = 0; j < 3; ++j) T[i][j] = S[i][0] * W0[0][j] + S[i][1] * W0[1][j] + S[i][2] * W0[2][j];
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int j = i; j < 3; ++j)
+                    S[i][j] = S[j][i] = W0[0][i] * T[0][j] + W0[1][i] * T[1][j] + W0[2][i] * T[2][j];
+        }
+        CT W1[3][3];
+        jacobi3(S, W1);
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) W[i][j] = W0[i][0] * W1[0][j] + W0[i][1] * W1[1][j] + W0[i][2] * W1[2][j];
+    } else {
+        jacobi3(S, W);
+    }
     CT ev[3] = {S[0][0], S[1][1], S[2][2]};
     int o[3] = {0, 1, 2};
     // sort descending
