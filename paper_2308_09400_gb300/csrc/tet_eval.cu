@@ -68,7 +68,11 @@ __device__ __forceinline__ void jacobi_rot(CT (&a)[3][3], CT (&v)[3][3]) {
         t = (CT(0.5) * ((tau >= CT(0) ? rho : -rho) * ih)) * (iu * iu);
         c = u * iu;
     } else {
-        t = (tau >= CT(0) ? rho : -rho) / (fabs(tau) + sqrt(hh));
+        // (equal diagonal entries and an off-diagonal entry whose square underflows: nothing to
+        // rotate at this precision, and the quotient would be 0 / 0)
+        const CT den = fabs(tau) + sqrt(hh);
+        if (!(den > CT(0))) return;
+        t = (tau >= CT(0) ? rho : -rho) / den;
         c = rsqrt(t * t + CT(1));
     }
     const CT s = t * c;
@@ -442,6 +446,17 @@ eval_tets_kernel(const double* __restrict__ x, int64_t n, const int32_t* __restr
                 }
         }
     }
+    // the element's factor scale * vol, taken into the weights (every block is linear in them)
+    {
+        const CT kc = (CT)k;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            sg[i] *= kc;
+            dl[i] *= kc;
+#pragma unroll
+            for (int j = 0; j < 3; ++j) Ah[i][j] *= kc;
+        }
+    }
     // M_ab, then U M_ab U^T
     auto m_ab = [&](int a, int b, CT (&M)[3][3]) {
 #pragma unroll
@@ -508,7 +523,6 @@ eval_tets_kernel(const double* __restrict__ x, int64_t n, const int32_t* __restr
         if (va == 0) return H0[vb - 1][3 * r + c];
         return blk(va - 1, vb - 1, r, c);
     };
-    const CT kc = (CT)k;
     // entry (a, b) at base + slot(a, b) * stride: element-major 3x3 sub-blocks (slot = its place
     // among the element's 144 values, stride 1) or entry-major (slot = 12 a + b, stride T)
     HT* const base = blocks ? hess + t * 144 : hess + t;
@@ -517,7 +531,7 @@ eval_tets_kernel(const double* __restrict__ x, int64_t n, const int32_t* __restr
     for (int a = 0; a < 12; ++a)
 #pragma unroll
         for (int b = 0; b <= a; ++b) {
-            const HT h = kc * hval(a, b);
+            const HT h = hval(a, b);
             const int sab = blocks ? ((a / 3) * 4 + b / 3) * 9 + (a % 3) * 3 + b % 3 : a * 12 + b;
             base[sab * stride] = h;
             if (a != b) {

@@ -105,6 +105,41 @@ def test_eval_tets_fp64_parity_both_scaling_projections(gipc):
     _compare({k: v.cpu().numpy() for k, v in g.items()}, ref, 1e-10)
 
 
+def test_eval_tets_equal_stretches_and_tiny_coupling(gipc):
+    # F^T F with two equal diagonal entries and an off-diagonal entry of 1e-25 (its square
+    # underflows in float32), a pure rotation, the identity and a uniform scaling: near-repeated
+    # singular values, where a rotation angle comes out as 0 / 0 unless guarded
+    rest = np.array([[0.0, 1.0, 0.0, 0.0], [0.0, 0.0, 1.0, 0.0], [0.0, 0.0, 0.0, 1.0]])
+    c, s = np.cos(0.3), np.sin(0.3)
+    Fs = [np.array([[1.0, 0.0, 0.1], [0.0, 1.0, 0.1], [1e-13, 1e-12, 1.4]]),
+          np.array([[c, -s, 0.0], [s, c, 0.0], [0.0, 0.0, 1.0]]),
+          np.eye(3), 0.9 * np.eye(3),
+          np.array([[1.0, 0.0, 0.0], [0.0, 1.0, 0.0], [1e-13, 1e-12, 1.0]])]
+    xs, tets = [], []
+    for e, F in enumerate(Fs):
+        xs.append(F @ rest + 2.0 * e)
+        tets.append(np.arange(4) + 4 * e)
+    x = np.concatenate(xs, axis=1)
+    rest_all = np.concatenate([rest + 2.0 * e for e in range(len(Fs))], axis=1)
+    tets = np.stack(tets, axis=1).astype(np.int32)
+    mu, lam = O.snh_params(E, NU)
+    Dmi, vol, _ = O.rest_state(rest_all, tets, RHO)
+    ref = O.eval_tets(x, tets, Dmi, vol, mu, lam, DT * DT)
+    for prec in ("fp64", "mixed"):
+        g = gipc.eval_tets(_dev(x), _dev(tets), _dev(Dmi), _dev(vol), mu, lam, DT * DT, precision=prec)
+        torch.cuda.synchronize()
+        got = {k: v.cpu().numpy() for k, v in g.items()}
+        assert np.isfinite(got["hess"]).all()
+        if prec == "fp64":
+            assert (np.abs(got["energy"] - ref["energy"]) <= 1e-10 * np.abs(ref["energy"])).all()
+            # the identity and the rotation are stress-free (zero gradient up to rounding): with
+            # unit edge lengths the gradient is held to the element's Hessian scale
+            hs = np.abs(ref["hess"]).max(axis=0)
+            assert (np.abs(got["hess"] - ref["hess"]).max(axis=0) <= 1e-10 * hs).all()
+            gs = np.maximum(np.abs(ref["grad"]).max(axis=0), hs)
+            assert (np.abs(got["grad"] - ref["grad"]).max(axis=0) <= 1e-10 * gs).all()
+
+
 def test_rest_state_and_mass(gipc):
     rest, _, tets = _mesh(4)
     Dmi, vol, mass = O.rest_state(rest, tets, RHO)
