@@ -32,7 +32,8 @@ gipc_status find_contacts_impl(gipc_ctx* ctx, const double* x, const double* res
                                bool cached);
 gipc_status pcg_impl(gipc_ctx* ctx, const gipc_bsr* A, const double* rhs, double* x, const uint8_t* fixed,
                      const gipc_pcg_params* prm, int* iters_out_h, double* rel_out_h, cudaStream_t st,
-                     const int64_t* voff, int nscenes, int* scene_iters_h, int* scene_status_h);
+                     const int64_t* voff, int nscenes, int* scene_iters_h, int* scene_status_h,
+                     const int64_t* voff_h);
 gipc_status ccd_impl(gipc_ctx* ctx, const double* x, const double* d, int64_t n, const gipc_surface& srf, double slack,
                      double* alpha_h, cudaStream_t st, const int32_t* vscene, int nscenes, double* amin_dev,
                      bool cached);
@@ -605,7 +606,7 @@ extern "C" gipc_status gipc_adjoint_step(gipc_ctx* ctx, const gipc_scene* sc, co
     cudaMemsetAsync(lam, 0, sizeof(double) * m3, st);
     gipc_pcg_params pp{prm->pcg_tol, std::max(prm->max_pcg, 1), 0, GIPC_PRODUCT_NATIVE, GIPC_PCG_STOP_ON_INDEFINITE};
     int pit = 0;
-    const gipc_status ps = pcg_impl(ctx, &H, a, lam, sc->fixed, &pp, &pit, nullptr, st, nullptr, 1, nullptr, nullptr);
+    const gipc_status ps = pcg_impl(ctx, &H, a, lam, sc->fixed, &pp, &pit, nullptr, st, nullptr, 1, nullptr, nullptr, nullptr);
     if (pcg_iters_h) *pcg_iters_h = pit;
     if (ps != GIPC_OK && ps != GIPC_ERR_NOT_CONVERGED) return ps;
     // H lambda (fixed rows), then the outputs
@@ -668,7 +669,7 @@ extern "C" gipc_status gipc_newton_polish(gipc_ctx* ctx, const gipc_scene* sc, d
         neg_free_kernel<<<nbk(m3, 256), 256, 0, st>>>(g, sc->fixed, n, rhs);
         cudaMemsetAsync(d, 0, sizeof(double) * m3, st);
         gipc_pcg_params pp{prm->pcg_tol, std::max(prm->max_pcg, 1), 0, GIPC_PRODUCT_NATIVE, GIPC_PCG_STOP_ON_INDEFINITE};
-        const gipc_status ps = pcg_impl(ctx, &H, rhs, d, sc->fixed, &pp, nullptr, nullptr, st, nullptr, 1, nullptr, nullptr);
+        const gipc_status ps = pcg_impl(ctx, &H, rhs, d, sc->fixed, &pp, nullptr, nullptr, st, nullptr, 1, nullptr, nullptr, nullptr);
         if (ps != GIPC_OK && ps != GIPC_ERR_NOT_CONVERGED && ps != GIPC_ERR_INDEFINITE) return ps;
         // a Newton direction of the exact Hessian descends only where that Hessian is positive
         // definite: stop (leaving x as it is) when it is not, or when the direction does not descend

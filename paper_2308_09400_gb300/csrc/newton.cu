@@ -32,7 +32,8 @@ gipc_status eval_stencils_ordered(const double* x, int64_t n, const int32_t* ste
                                   const int32_t* order, cudaStream_t s);
 gipc_status pcg_impl(gipc_ctx* ctx, const gipc_bsr* A, const double* rhs, double* x, const uint8_t* fixed,
                      const gipc_pcg_params* prm, int* iters_out_h, double* rel_out_h, cudaStream_t st,
-                     const int64_t* voff, int nscenes, int* scene_iters_h, int* scene_status_h);
+                     const int64_t* voff, int nscenes, int* scene_iters_h, int* scene_status_h,
+                     const int64_t* voff_h);
 
 namespace {
 
@@ -978,7 +979,8 @@ struct BatchStep {
             negate_kernel<<<nb(m3, 256), 256, 0, st>>>(g, m3, rhs);
             cudaMemsetAsync(d, 0, sizeof(double) * m3, st);
             gipc_pcg_params pp{prm.pcg_tol, prm.max_pcg, 0};
-            s = pcg_impl(ctx, &H, rhs, d, mask, &pp, nullptr, nullptr, st, voff, ns, piters.data(), pstat.data());
+            s = pcg_impl(ctx, &H, rhs, d, mask, &pp, nullptr, nullptr, st, voff, ns, piters.data(), pstat.data(),
+                         voff_h.data());
             if (s != GIPC_OK && s != GIPC_ERR_NOT_CONVERGED) return s;
             // per-scene step filter, then backtracking per scene
             if ((s = ccd_impl(ctx, x, d, n, sc.surface, 0.1, alpha_h.data(), st, vs, ns, sA, true)) != GIPC_OK) return s;

@@ -2149,10 +2149,12 @@ inline unsigned vec_blocks(int64_t n) { return grid_for(n, (int64_t)kPcgThreads 
 namespace gipc {
 // One solve, or (voff != NULL) nscenes independent solves on the vertex ranges voff (device,
 // [nscenes+1]) with per-scene scalars; scene_iters_h / scene_status_h (host, [nscenes]) report
-// each scene's iterations and status.
+// each scene's iterations and status.  voff_h (optional): the same ranges in host memory, so the
+// batched launch is planned without reading them back.
 gipc_status pcg_impl(gipc_ctx* ctx, const gipc_bsr* A, const double* rhs, double* x, const uint8_t* fixed,
                      const gipc_pcg_params* prm, int* iters_out_h, double* rel_out_h, cudaStream_t st,
-                     const int64_t* voff, int nscenes, int* scene_iters_h, int* scene_status_h) {
+                     const int64_t* voff, int nscenes, int* scene_iters_h, int* scene_status_h,
+                     const int64_t* voff_h) {
     if (!ctx || !A || !prm) return fail(GIPC_ERR_INVALID_ARG, "gipc_pcg: null context, matrix or parameters");
     const int64_t n = A->n;
     if (n < 0 || A->nnzb < 0) return fail(GIPC_ERR_INVALID_ARG, "gipc_pcg: negative sizes");
@@ -2319,12 +2321,29 @@ gipc_status pcg_impl(gipc_ctx* ctx, const gipc_bsr* A, const double* rhs, double
             double* part_b = part_a + bp.grid + nscenes + 1;
             int* most = reinterpret_cast<int*>(part_b + bp.grid + nscenes + 1);
             int2* chunk_sc = reinterpret_cast<int2*>(most + 4);
-            cudaMemsetAsync(most, 0, sizeof(int), st);
-            batch_segments_kernel<<<(bp.grid + 255) / 256, 256, 0, st>>>(voff, nscenes, n, bp.chunk, (int)bp.grid, most);
             chunk_scenes_kernel<<<(unsigned)((nchunks + 255) / 256), 256, 0, st>>>(voff, nscenes, n, nchunks, chunk_sc);
             int most_h = 0;
-            cudaMemcpyAsync(&most_h, most, sizeof(int), cudaMemcpyDeviceToHost, st);
-            if (cudaStreamSynchronize(st) != cudaSuccess) return check_launch("gipc_pcg: batch plan");
+            if (voff_h) {   // the most scene segments a CTA would hold, from the host copy of the ranges
+                auto scene_of_h = [&](int64_t v) {   // as scene_of
+                    int lo = 0, hi = nscenes - 1;
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (voff_h[mid] <= v) lo = mid;
+                        else hi = mid - 1;
+                    }
+                    return lo;
+                };
+                for (int64_t b = 0; b < (int64_t)bp.grid && b * bp.chunk < n; ++b) {
+                    const int64_t a = b * bp.chunk, e = std::min<int64_t>(a + bp.chunk, n);
+                    most_h = std::max(most_h, scene_of_h(e - 1) - scene_of_h(a) + 1);
+                }
+            } else {
+                cudaMemsetAsync(most, 0, sizeof(int), st);
+                batch_segments_kernel<<<(bp.grid + 255) / 256, 256, 0, st>>>(voff, nscenes, n, bp.chunk, (int)bp.grid,
+                                                                             most);
+                cudaMemcpyAsync(&most_h, most, sizeof(int), cudaMemcpyDeviceToHost, st);
+                if (cudaStreamSynchronize(st) != cudaSuccess) return check_launch("gipc_pcg: batch plan");
+            }
             if (most_h <= kBMaxSeg) {
                 int64_t n_arg = n, nsl_arg = nsl, chunk_arg = bp.chunk;
                 int ns_arg = nscenes, iters_arg = max_iter;
@@ -2453,7 +2472,7 @@ extern "C" gipc_status gipc_pcg(gipc_ctx* ctx, const gipc_bsr* A, const double* 
                                 const uint8_t* fixed, const gipc_pcg_params* prm, int* iters_out_h,
                                 double* rel_out_h, void* stream) {
     return gipc::pcg_impl(ctx, A, rhs, x, fixed, prm, iters_out_h, rel_out_h, (cudaStream_t)stream, nullptr, 1, nullptr,
-                          nullptr);
+                          nullptr, nullptr);
 }
 
 extern "C" gipc_status gipc_pcg_batch_persistent(gipc_ctx* ctx, int enable) {
