@@ -12,6 +12,9 @@
 //   scaling: eigenpairs (l, a) of the 3x3 matrix d2Psi/ds_i ds_j,            U diag(a) V^T
 // The projected block is scale * vol * sum over modes with l > 0 of l w w^T, w = dF/dx^T vec(Q),
 // where dF/dx^T maps a 3x3 G to forces (G Dm^-T columns on vertices 1..3, minus their sum on 0).
+// It is formed per pair of vertices in the singular basis (U M U^T, M from the clamped twist /
+// flip eigenvalues and the projected scaling block, which is the block itself where it is
+// positive definite); the float64 Jacobi starts from a float32 pre-rotation.
 // Energy and gradient are computed in float64 for both precisions; the projected Hessian in the
 // precision it is stored in (float64, or float32 for the mixed form, whose blocks are float32).
 #include <cmath>
