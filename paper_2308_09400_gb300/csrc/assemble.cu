@@ -156,13 +156,76 @@ __device__ __forceinline__ int next_pow2(int L) {
     return P;
 }
 
-// Sort each row bucket of at most kWarpRowMax keys with one warp; longer rows are queued.
+// Bitonic sort of the 32 K keys a warp holds in registers (position j 32 + lane in v[j]):
+// compare-exchanges between lanes by shuffles, between a lane's own keys in place.  The same
+// network as bitonic_sort, without shared memory (whose bandwidth bounded the staged version).
+template <int K>
+__device__ __forceinline__ void warp_sort_regs(uint64_t (&v)[K]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int size = 2; size <= 32 * K; size <<= 1) {
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            if (stride >= 32) {
+                const int js = stride >> 5;
+#pragma unroll
+                for (int j = 0; j < K; ++j) {
+                    if (j & js) continue;
+                    const bool up = ((j * 32 + lane) & size) == 0;
+                    const uint64_t a = v[j], b = v[j | js];
+                    const bool sw = (a > b) == up;
+                    v[j] = sw ? b : a;
+                    v[j | js] = sw ? a : b;
+                }
+            } else {
+                const bool lower = (lane & stride) == 0;
+#pragma unroll
+                for (int j = 0; j < K; ++j) {
+                    const uint64_t a = v[j], b = __shfl_xor_sync(0xffffffffu, a, stride);
+                    const bool up = ((j * 32 + lane) & size) == 0;
+                    const uint64_t lo = a < b ? a : b, hi = a < b ? b : a;
+                    v[j] = (lower == up) ? lo : hi;   // the pair's lower slot gets the minimum when ascending
+                }
+            }
+        }
+    }
+}
+
+// One row of L <= 32 K keys at keys[st ..): sort in registers, write back, count distinct columns.
+template <int K>
+__device__ __forceinline__ int sort_row_regs(uint64_t* __restrict__ keys, int64_t st, int L) {
+    const int lane = threadIdx.x & 31;
+    uint64_t v[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        const int p = j * 32 + lane;
+        v[j] = p < L ? keys[st + p] : ~0ull;
+    }
+    warp_sort_regs<K>(v);
+    int heads = 0;
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        const int p = j * 32 + lane;
+        const uint64_t up1 = __shfl_up_sync(0xffffffffu, v[j], 1);
+        const uint64_t wrap = j > 0 ? __shfl_sync(0xffffffffu, v[j > 0 ? j - 1 : 0], 31) : 0ull;
+        const uint64_t prev = lane > 0 ? up1 : wrap;
+        if (p < L) {
+            keys[st + p] = v[j];
+            heads += (p == 0 || key_col(prev) != key_col(v[j])) ? 1 : 0;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) heads += __shfl_xor_sync(0xffffffffu, heads, o);
+    return heads;
+}
+
+// Sort each row bucket of at most kWarpRowMax keys with one warp (keys in registers); longer rows
+// are queued.
 __global__ void __launch_bounds__(32 * kSortWarps)
 sort_rows_warp_kernel(const int64_t* __restrict__ row_start, uint64_t* __restrict__ keys, int64_t n,
                       int32_t* __restrict__ row_nnzb, int32_t* __restrict__ long_rows, int32_t* __restrict__ n_long) {
-    __shared__ uint64_t smem[kSortWarps][kWarpRowMax];
+    static_assert(kWarpRowMax == 512, "the register sort dispatch covers rows of up to 512 keys");
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    uint64_t* buf = smem[w];
     for (int64_t r = (int64_t)blockIdx.x * kSortWarps + w; r < n; r += (int64_t)gridDim.x * kSortWarps) {
         const int64_t st = row_start[r];
         const int L = (int)(row_start[r + 1] - st);
@@ -171,19 +234,13 @@ sort_rows_warp_kernel(const int64_t* __restrict__ row_start, uint64_t* __restric
             continue;
         }
         const int P = next_pow2(L);
-        for (int t = lane; t < P; t += 32) buf[t] = t < L ? keys[st + t] : ~0ull;
-        __syncwarp();
-        bitonic_sort<false>(buf, P, lane, 32);
-        int heads = 0;
-        for (int t = lane; t < L; t += 32) {
-            const uint64_t k = buf[t];
-            keys[st + t] = k;
-            heads += (t == 0 || key_col(buf[t - 1]) != key_col(k)) ? 1 : 0;
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) heads += __shfl_xor_sync(0xffffffffu, heads, o);
+        int heads;
+        if (P == 32) heads = sort_row_regs<1>(keys, st, L);
+        else if (P == 64) heads = sort_row_regs<2>(keys, st, L);
+        else if (P == 128) heads = sort_row_regs<4>(keys, st, L);
+        else if (P == 256) heads = sort_row_regs<8>(keys, st, L);
+        else heads = sort_row_regs<16>(keys, st, L);
         if (lane == 0) row_nnzb[r] = heads;
-        __syncwarp();
     }
 }
 
