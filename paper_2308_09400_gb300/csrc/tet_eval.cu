@@ -346,20 +346,20 @@ eval_tets_kernel(const double* __restrict__ x, int64_t n, const int32_t* __restr
         }
     }
     const double J = F[0][0] * cof[0][0] + F[1][0] * cof[1][0] + F[2][0] * cof[2][0];
-    const double ip1 = 1.0 / (I2 + 1.0);
     const double Jm = J - K.alpha;
-    const double psi = 0.5 * K.mu * (I2 - 3.0) + 0.5 * K.lam * Jm * Jm - 0.5 * K.mu * log(I2 + 1.0);
+    if (energy) energy[t] = k * (0.5 * K.mu * (I2 - 3.0) + 0.5 * K.lam * Jm * Jm - 0.5 * K.mu * log(I2 + 1.0));
+    if (!grad && !hess) return;   // (the line search's energy-only evaluations end here)
+    const double ip1 = 1.0 / (I2 + 1.0);
     const double m1 = K.mu * (1.0 - ip1);
-    // P = m1 F + lam (J - alpha) cof
-    double Pm[3][3];
-#pragma unroll
-    for (int r = 0; r < 3; ++r)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) Pm[r][c] = m1 * F[r][c] + K.lam * Jm * cof[r][c];
-    double g[12];
-    map_to_x(Pm, Dmi, g);
-    if (energy) energy[t] = k * psi;
     if (grad) {
+        // P = m1 F + lam (J - alpha) cof
+        double Pm[3][3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) Pm[r][c] = m1 * F[r][c] + K.lam * Jm * cof[r][c];
+        double g[12];
+        map_to_x(Pm, Dmi, g);
 #pragma unroll
         for (int j = 0; j < 12; ++j) grad[j * T + t] = k * g[j];
     }
